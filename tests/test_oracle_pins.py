@@ -1,0 +1,444 @@
+"""Pins of the FP64 oracle to what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed
+forms (the paper's two-particle oscillator, Eq. 6), finite differences of the
+potential (Eq. 1 vs Eq. 2), Newton's third law, energy conservation of
+velocity Verlet (Section 2.2), an independent linear static solve, the
+paper's spring table (Section 3.1), and brute-force enumeration of the
+lattice. A plausible slip in the oracle (a dropped term, a wrong sign, a
+wrong index or factor) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from gen.images import inclusion_image, one_phase_materials, two_phase_materials
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_kv(name):
+    out = {}
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, val = line.split()
+            out[key] = float(val)
+    return out
+
+
+def _read_table(name):
+    rows = {}
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            parts = line.split()
+            rows[parts[0]] = tuple(float(p) for p in parts[1:])
+    return rows
+
+
+# ------------------------------------------------------------ lattice build
+
+def _brute_springs(phase, k_tab, e_tab, k2_ratio, a):
+    """Every pair of occupied sites at squared lattice distance 1 or 2,
+    enumerated over all pairs (not via forward offsets)."""
+    if phase.ndim == 2:
+        phase = phase[None]
+    nz, ny, nx = phase.shape
+    sites = [(ix, iy, iz) for iz in range(nz) for iy in range(ny) for ix in range(nx)
+             if phase[iz, iy, ix]]
+    index = {s: t for t, s in enumerate(sites)}
+    springs = {}
+    for (i, si) in enumerate(sites):
+        for (j, sj) in enumerate(sites):
+            if j <= i:
+                continue
+            d2 = sum((u - w) ** 2 for u, w in zip(si, sj))
+            if d2 not in (1, 2):
+                continue
+            pi = phase[si[2], si[1], si[0]]
+            pj = phase[sj[2], sj[1], sj[0]]
+            k = k_tab[pi - 1, pj - 1] * (k2_ratio if d2 == 2 else 1.0)
+            r0 = a * math.sqrt(d2)
+            rc = r0 * (1.0 + e_tab[pi - 1, pj - 1])
+            springs[(i, j)] = (k, r0, rc * rc)
+    assert len(index) == len(sites)
+    return sites, springs
+
+
+@pytest.mark.parametrize("shape,seed", [((7, 6), 0), ((4, 3, 5), 1)])
+def test_build_matches_brute_force(oracle_mod, shape, seed):
+    rng = np.random.default_rng(seed)
+    phase = rng.integers(0, 3, size=shape).astype(np.uint8)  # voids included
+    k_tab = np.array([[1.0, 0.3], [0.3, 0.1]])
+    e_tab = np.array([[0.05, 0.2], [0.2, 0.3]])
+    o = oracle_mod.Oracle.from_image(phase, k_tab, e_tab, k2_ratio=0.5, a=1.5)
+    sites, springs = _brute_springs(phase, k_tab, e_tab, 0.5, 1.5)
+    t = o.topology()
+    assert o.n == len(sites)
+    assert o.m == len(springs)
+    keys = sorted(springs)
+    assert list(zip(t["si"].tolist(), t["sj"].tolist())) == keys  # canonical order
+    for s, key in enumerate(keys):
+        k, r0, rc2 = springs[key]
+        assert t["k"][s] == k
+        assert t["r0"][s] == pytest.approx(r0, rel=1e-15)
+        assert t["rc2"][s] == pytest.approx(rc2, rel=1e-14)
+    # reference positions of the raster-order particles
+    for p, (ix, iy, iz) in enumerate(sites):
+        assert t["X"][0, p] == ix * 1.5 and t["X"][1, p] == iy * 1.5
+
+
+def test_spring_count_closed_form(oracle_mod):
+    # full nx x ny image: (nx-1)ny + nx(ny-1) first + 2(nx-1)(ny-1) second neighbours
+    for nx, ny in [(64, 64), (5, 9)]:
+        o = oracle_mod.Oracle.from_image(np.ones((ny, nx), np.uint8), [[1.0]], [[0.1]])
+        assert o.m == (nx - 1) * ny + nx * (ny - 1) + 2 * (nx - 1) * (ny - 1)
+    # full cube: 3 face families + 6 edge-diagonal families
+    n = 5
+    o = oracle_mod.Oracle.from_image(np.ones((n, n, n), np.uint8), [[1.0]], [[0.1]])
+    assert o.m == 3 * (n - 1) * n * n + 6 * (n - 1) * (n - 1) * n
+    assert o.n == n ** 3
+
+
+def test_reference_config_sizes(oracle_mod):
+    img = inclusion_image(64, 64, 3.0, 8.0, 0.30, 0)
+    k, e, m = two_phase_materials()
+    o = oracle_mod.Oracle.from_image(img, k, e, m)
+    assert o.n == 4096 and o.m == 16002
+    assert 0.30 <= (img == 2).mean() < 0.40
+
+
+# ---------------------------------------------------------- force / energy
+
+def _perturbed_lattice(oracle_mod, shape, seed, amp=0.05):
+    rng = np.random.default_rng(seed)
+    phase = rng.integers(1, 3, size=shape).astype(np.uint8)
+    k_tab = np.array([[1.0, 0.4], [0.4, 0.1]])
+    e_tab = np.full((2, 2), 10.0)  # nothing breaks
+    o = oracle_mod.Oracle.from_image(phase, k_tab, e_tab, k2_ratio=0.7)
+    x, _, _ = o.state()
+    x = x + amp * rng.standard_normal(x.shape)
+    return o, x
+
+
+@pytest.mark.parametrize("shape,seed", [((5, 5), 3), ((3, 3, 3), 4)])
+def test_force_is_minus_energy_gradient(oracle_mod, shape, seed):
+    """Eq. 2 is the negative gradient of Eq. 1 (central differences)."""
+    o, x = _perturbed_lattice(oracle_mod, shape, seed)
+    F, U, _ = o.forces(x)
+    h = 1e-6
+    fd = np.zeros_like(x)
+    for c in range(x.shape[0]):
+        for p in range(x.shape[1]):
+            xp = x.copy(); xp[c, p] += h
+            xm = x.copy(); xm[c, p] -= h
+            fd[c, p] = -(o.forces(xp)[1] - o.forces(xm)[1]) / (2 * h)
+    scale = np.abs(F).max()
+    assert scale > 1e-3
+    assert np.abs(F - fd).max() <= 1e-7 * scale
+
+
+@pytest.mark.parametrize("shape,seed", [((6, 7), 5), ((3, 4, 3), 6)])
+def test_newton_third_law(oracle_mod, shape, seed):
+    o, x = _perturbed_lattice(oracle_mod, shape, seed)
+    F, _, _ = o.forces(x)
+    total = F.sum(axis=1)
+    assert np.abs(total).max() <= 1e-14 * np.abs(F).sum()
+
+
+def test_single_spring_direction_and_tension_sign(oracle_mod):
+    # one stretched spring along a random direction: the force on the lower
+    # particle points to the other one (tension), magnitude is linear in stretch
+    X = np.array([[0.0, 1.0], [0.0, 0.0]])
+    o = oracle_mod.Oracle.from_network(X, [0], [1], [2.0], [1.0], [np.inf])
+    th = 0.3
+    for r in (1.1, 1.2):
+        x = np.array([[0.0, r * math.cos(th)], [0.0, r * math.sin(th)]])
+        F, U, _ = o.forces(x)
+        f0 = F[:, 0]
+        assert f0 @ np.array([math.cos(th), math.sin(th)]) > 0
+        assert np.hypot(*f0) == pytest.approx(2.0 * (r - 1.0), rel=1e-13)
+        assert U == pytest.approx(0.5 * 2.0 * (r - 1.0) ** 2, rel=1e-13)
+        assert np.allclose(F[:, 1], -f0, rtol=0, atol=0)
+
+
+# -------------------------------------------------------------- integrator
+
+def test_paper_oscillator_closed_form(oracle_mod):
+    """The paper's two-particle oscillator (Eq. 6): velocity Verlet on a
+    linear spring gives y_n = y_0 cos(n theta) exactly, cos theta = 1 - (w dt)^2/2,
+    and stays within O((w dt)^2) of the continuous cosine over the run."""
+    g = _read_kv("paper_oscillator.txt")
+    X = np.array([[0.0, g["x_start"]], [0.0, 0.0]])
+    fix = np.array([[1, 0], [1, 0]], np.uint8)
+    o = oracle_mod.Oracle.from_network(X, [0], [1], [g["k"]], [g["r0"]], [np.inf],
+                                       mass=[g["m"], g["m"]], fix=fix, dt=g["dt"], damping=0.0)
+    w = math.sqrt(g["k"] / g["m"])
+    theta = math.acos(1.0 - 0.5 * (w * g["dt"]) ** 2)
+    y0 = g["x_start"] - g["r0"]
+    n_out = int(round(g["t_out"] / g["dt"]))
+    n_end = int(round(g["t_end"] / g["dt"]))
+    worst_exact, worst_cont = 0.0, 0.0
+    for n in range(n_out, n_end + 1, n_out):
+        o.step(n_out)
+        x, v, _ = o.state()
+        y = x[0, 1] - g["r0"]
+        worst_exact = max(worst_exact, abs(y - y0 * math.cos(n * theta)))
+        worst_cont = max(worst_cont, abs(y - y0 * math.cos(w * n * g["dt"])))
+        assert x[1, 1] == 0.0 and x[0, 0] == 0.0
+    assert worst_exact <= 1e-12 * y0
+    assert worst_cont <= 1e-3 * y0 and worst_cont > 1e-9 * y0
+
+
+def _damped_error(oracle_mod, dt, t_end=60.0, k=1.0, gamma=0.3):
+    X = np.array([[0.0, 2.0], [0.0, 0.0]])
+    fix = np.array([[1, 0], [1, 1]], np.uint8)
+    o = oracle_mod.Oracle.from_network(X, [0], [1], [k], [1.0], [np.inf], fix=fix, dt=dt,
+                                       damping=gamma)
+    nsteps = int(round(t_end / dt))
+    o.step(nsteps)
+    y = o.state()[0][0, 1] - 1.0
+    # m y'' + gamma y' + k y = 0, y(0)=1, y'(0)=0 (underdamped, m = 1)
+    wd = math.sqrt(k - 0.25 * gamma * gamma)
+    t = nsteps * dt
+    exact = math.exp(-0.5 * gamma * t) * (math.cos(wd * t) + 0.5 * gamma / wd * math.sin(wd * t))
+    return abs(y - exact), abs(exact)
+
+
+def test_viscous_damping_converges_to_damped_oscillator(oracle_mod):
+    """Damping -gamma*vh: the discrete solution tends to the continuous damped
+    oscillator as dt -> 0 (first order, since the drag uses the half-step
+    velocity). A wrong sign or factor on gamma gives an O(1) error instead."""
+    e1, scale = _damped_error(oracle_mod, 0.02)
+    e2, _ = _damped_error(oracle_mod, 0.01)
+    assert e1 < 5e-3 * max(scale, 1e-6) + 1e-5
+    assert 1.6 < e1 / e2 < 2.4
+
+
+def _energy_drift(oracle_mod, dt, t_end=40.0):
+    rng = np.random.default_rng(7)
+    phase = rng.integers(1, 3, size=(6, 6)).astype(np.uint8)
+    k_tab = np.array([[1.0, 0.4], [0.4, 0.2]])
+    o = oracle_mod.Oracle.from_image(phase, k_tab, np.full((2, 2), 10.0), grip_mode=1,
+                                     dt=dt, damping=0.0)
+    x, v, a = o.state()
+    _, _, _ = o.forces(x)
+    t = o.topology()
+    v = 0.05 * rng.standard_normal(v.shape) * (1 - t["fix"])
+    x = x + 0.02 * rng.standard_normal(x.shape) * (1 - t["fix"])
+    F, _, _ = o.forces(x)
+    o.set_state(x=x, v=v, a=F / t["mass"][None, :] * (1 - t["fix"]))
+    ob = o.observe()
+    e0 = ob["pe"] + ob["ke"]
+    worst = 0.0
+    n = int(round(t_end / dt))
+    for _ in range(20):
+        o.step(n // 20)
+        ob = o.observe()
+        worst = max(worst, abs(ob["pe"] + ob["ke"] - e0))
+    return worst / e0
+
+
+def test_energy_conserved_without_damping(oracle_mod):
+    """Velocity Verlet is symplectic: no secular drift and an O(dt^2) energy error."""
+    d1 = _energy_drift(oracle_mod, 0.1)
+    d2 = _energy_drift(oracle_mod, 0.05)
+    assert d1 < 5e-3
+    assert 3.0 < d1 / d2 < 5.0
+
+
+# --------------------------------------------------- statics and the modulus
+
+def _stiffness(t, x):
+    """Linear stiffness matrix of the intact network about positions x
+    (independent of the oracle's force routine)."""
+    dim, n = x.shape
+    K = np.zeros((dim * n, dim * n))
+    for s in range(t["si"].size):
+        i, j = int(t["si"][s]), int(t["sj"][s])
+        d = x[:, j] - x[:, i]
+        e = d / np.linalg.norm(d)
+        kk = t["k"][s] * np.outer(e, e)
+        ii = [c * n + i for c in range(dim)]
+        jj = [c * n + j for c in range(dim)]
+        K[np.ix_(ii, ii)] += kk
+        K[np.ix_(jj, jj)] += kk
+        K[np.ix_(ii, jj)] -= kk
+        K[np.ix_(jj, ii)] -= kk
+    return K
+
+
+@pytest.mark.parametrize("shape", [(8, 8), (4, 4, 4)])
+def test_relaxed_state_matches_linear_static_solve(oracle_mod, shape):
+    """At small strain the relaxed oracle state equals the solution of
+    K u = 0 with prescribed grip displacements, up to O(eps) geometric terms.
+    Also: the virial stress equals the grip traction at equilibrium."""
+    k_tab, e_tab, mass = one_phase_materials(1.0, 0.5)
+    o = oracle_mod.Oracle.from_image(np.ones(shape, np.uint8), k_tab, e_tab, mass,
+                                     dt=0.2, damping=0.35)
+    eps = 1e-6
+    o.apply_strain(eps)
+    st, taken = o.relax(tol=1e-13, max_steps=200000, check_every=50)
+    assert st == 0, taken
+    t = o.topology()
+    X = t["X"]
+    x, _, _ = o.state()
+    u = (x - X).reshape(-1)
+    K = _stiffness(t, X)
+    fixed = t["fix"].reshape(-1).astype(bool)
+    u_fix = np.zeros_like(u)
+    xc = 0.5 * (shape[-1] - 1)
+    u_fix[: X.shape[1]] = eps * (X[0] - xc)
+    u_fix[~fixed] = 0.0
+    free = ~fixed
+    rhs = -K[np.ix_(free, fixed)] @ u_fix[fixed]
+    u_free = np.linalg.lstsq(K[np.ix_(free, free)], rhs, rcond=None)[0]
+    u_lin = u_fix.copy()
+    u_lin[free] = u_free
+    # remove the zero-stiffness rigid translations the min-norm solve fixes
+    # differently (none are excited: the start is at rest and symmetric)
+    err = np.abs(u - u_lin).max() / np.abs(u_lin).max()
+    assert err < 1e-5
+    ob = o.observe()
+    R = -(K @ u_lin)  # reaction on the right grip, x components
+    right = (t["grip"] == 2)
+    area = np.prod(shape[:-1])
+    sig_lin = -(K @ u_lin)[: X.shape[1]][right].sum() * -1.0 / area
+    assert ob["sigma_grip"] == pytest.approx(sig_lin, rel=1e-5)
+    # static equilibrium: the internal virial equals the grip reaction times the
+    # current grip separation, so sigma_vir = sigma_grip (1 + eps) exactly
+    assert ob["sigma_vir"] == pytest.approx(ob["sigma_grip"] * (1 + eps), rel=1e-8)
+    assert R.shape == u.shape
+
+
+def test_square_lattice_modulus_tends_to_three_halves_k(oracle_mod):
+    """Uniform square lattice, equal first/second-neighbour k, roller grips:
+    the effective Young's modulus of the affine continuum limit is 1.5 k
+    (C11 = 2k, C12 = C66 = k, plane problem). A 32x32 specimen is within 1%."""
+    n = 32
+    k_tab, e_tab, mass = one_phase_materials(1.0, 0.5)
+    o = oracle_mod.Oracle.from_image(np.ones((n, n), np.uint8), k_tab, e_tab, mass,
+                                     dt=0.3, damping=0.15)
+    eps = 1e-6
+    o.apply_strain(eps)
+    st, taken = o.relax(tol=1e-13, max_steps=400000, check_every=100)
+    assert st == 0
+    ob = o.observe()
+    # sigma over the reference box is R / (ny a); R / (eps ny) -> E as n grows,
+    # with the grips' own stiffness contributing O(1/n)
+    modulus = ob["sigma_grip"] / eps
+    assert modulus == pytest.approx(1.5, rel=0.012)
+    assert ob["sigma_vir"] == pytest.approx(ob["sigma_grip"] * (1 + eps), rel=1e-8)
+
+
+def test_relaxed_energy_not_above_affine_energy(oracle_mod):
+    """Minimum potential energy: with the grips fixed, the relaxed two-phase
+    state stores no more energy than the affine field at the same strain."""
+    img = inclusion_image(16, 16, 2.0, 4.0, 0.3, 11)
+    k, e, m = two_phase_materials()
+    o = oracle_mod.Oracle.from_image(img, k, e, m, dt=0.2, damping=0.3)
+    o.apply_strain(0.01)
+    pe_aff = o.observe()["pe"]
+    st, _ = o.relax(tol=1e-12, max_steps=200000, check_every=50)
+    assert st == 0
+    ob = o.observe()
+    assert ob["n_broken"] == 0
+    assert ob["pe"] < pe_aff
+    assert ob["sigma_vir"] == pytest.approx(ob["sigma_grip"] * 1.01, rel=1e-8)
+
+
+# ---------------------------------------------------------------- breaking
+
+def test_break_is_strict_and_same_step(oracle_mod):
+    """A spring at exactly rc stays intact (strict '>' switch); just beyond it
+    breaks in the next step and gives zero force in that step."""
+    img = np.ones((1, 2), np.uint8)
+    o = oracle_mod.Oracle.from_image(img, [[1.0]], [[0.5]])  # rc = 1.5
+    o.step(3)
+    o.apply_strain(0.5)  # grips at -0.25 and 1.25: r = 1.5 exactly
+    o.step(1)
+    mask, bs, fb = o.broken()
+    assert mask[0] == 0 and fb == -1
+    o.apply_strain(0.5 + 2.0 ** -20)
+    o.step(1)
+    mask, bs, fb = o.broken()
+    assert mask[0] == 1 and bs[0] == 4 and fb == 4
+    F, U, _ = o.forces(o.state()[0])
+    assert np.all(F == 0.0) and U == 0.0
+
+
+def test_paper_spring_table_break_order_and_strains(oracle_mod):
+    """The paper's three fracture springs, stretched together: stiff-stiff
+    breaks first (rc = 10.1), then stiff-soft (10.4), then soft-soft (11.0)."""
+    tab = _read_table("paper_spring_table.txt")
+    names = ["stiff-stiff", "stiff-soft", "soft-soft"]
+    X = np.array([[0.0, 10.0, 0.0, 10.0, 0.0, 10.0], [0.0, 0.0, 20.0, 20.0, 40.0, 40.0]])
+    k = [tab[q][0] for q in names]
+    r0 = [tab[q][1] for q in names]
+    rc2 = [tab[q][2] ** 2 for q in names]
+    fix = np.zeros((2, 6), np.uint8)
+    fix[:, :] = 1
+    grip = np.array([1, 2, 1, 2, 1, 2], np.uint8)
+    o = oracle_mod.Oracle.from_network(X, [0, 2, 4], [1, 3, 5], k, r0, rc2, fix=fix, grip=grip,
+                                       xc=5.0, omega=10.0 * 40.0, grip_area=60.0, dt=0.1)
+    order = []
+    eps_at = {}
+    for i in range(1, 121):
+        eps = (i - 0.5) * 1e-3  # half-way between the critical strains' grid
+        o.apply_strain(eps)
+        o.step(1)
+        mask, _, _ = o.broken()
+        for s in range(3):
+            if mask[s] and names[s] not in order:
+                order.append(names[s])
+                eps_at[names[s]] = eps
+    assert order == names
+    for q in names:
+        crit = tab[q][2] / tab[q][1] - 1.0
+        assert crit < eps_at[q] <= crit + 1e-3 + 1e-12
+
+
+def test_break_is_irreversible(oracle_mod):
+    img = np.ones((1, 2), np.uint8)
+    o = oracle_mod.Oracle.from_image(img, [[1.0]], [[0.05]])
+    o.apply_strain(0.06)
+    o.step(1)
+    assert o.broken()[0][0] == 1
+    o.apply_strain(-0.02)  # compress the broken spring
+    o.step(5)
+    assert o.broken()[0][0] == 1
+    F, U, _ = o.forces(o.state()[0])
+    assert np.all(F == 0.0)
+
+
+def test_image_rc_from_paper_constants(oracle_mod):
+    """rc^2 = (r0 (1 + eps_c))^2 with r0 = a: the paper's springs (r0 = 10)
+    reproduce its printed rc values."""
+    tab = _read_table("paper_spring_table.txt")
+    k_tab = np.array([[tab["stiff-stiff"][0], tab["stiff-soft"][0]],
+                      [tab["stiff-soft"][0], tab["soft-soft"][0]]])
+    e_tab = np.array([[tab["stiff-stiff"][2] / 10 - 1, tab["stiff-soft"][2] / 10 - 1],
+                      [tab["stiff-soft"][2] / 10 - 1, tab["soft-soft"][2] / 10 - 1]])
+    img = np.array([[1, 1, 2, 2]], np.uint8)
+    o = oracle_mod.Oracle.from_image(img, k_tab, e_tab, a=10.0)
+    t = o.topology()
+    assert np.sqrt(t["rc2"]).tolist() == pytest.approx([10.1, 10.4, 11.0], rel=1e-14)
+    assert t["k"].tolist() == [2e-3, 1.25e-4, 2e-5]
+
+
+def test_virial_kinetic_term_sign(oracle_mod):
+    """Eq. 7: a moving, force-free particle lowers sigma_xx by m v_x^2 / Omega."""
+    X = np.array([[0.0, 1.0], [0.0, 0.0]])
+    o = oracle_mod.Oracle.from_network(X, [0], [1], [1.0], [1.0], [np.inf], omega=4.0,
+                                       mass=[2.0, 3.0])
+    o.set_state(v=np.array([[0.5, 0.0], [0.7, 0.0]]))
+    ob = o.observe()
+    assert ob["sigma_vir"] == pytest.approx(-(2.0 * 0.25) / 4.0, rel=1e-15)
+    assert ob["ke"] == pytest.approx(0.5 * 2.0 * (0.25 + 0.49), rel=1e-15)
