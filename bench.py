@@ -1,0 +1,269 @@
+#!/usr/bin/env python3
+"""Benchmark of the lattice-spring hot path on one GB300 (or N replicas).
+
+One bench step = one displacement-controlled load increment of the 2D
+2048 x 2048 two-phase composite (4,194,304 particles, 16,764,930 springs):
+lsm_apply_strain, 20 damped velocity-Verlet time steps with the break test,
+and the stress sample. The metric is spring-updates/s (springs x time steps
+per second), whole job over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision MODE]
+  python bench.py --impl reference ...   # the FP64 CPU oracle, timed on the host
+
+Under torchrun every rank steps its own replica of the specimen (the
+single-specimen path does not shard; replicas only), timing is max over
+ranks after a barrier, and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from gen.images import inclusion_image, two_phase_materials  # noqa: E402
+
+WORKLOAD = dict(name="2d_2048_two_phase", nx=2048, ny=2048, r=(10.0, 60.0), frac=0.30, seed=1,
+                dt=0.01, damping=0.1, steps_per_increment=20, eps_inc=1e-3)
+METRIC = "spring-updates/sec (% HBM roofline) at 1 GB300"
+UNIT = "spring-updates/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [q.strip() for q in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[5 + q].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def algorithmic_bytes(n, m, dim):
+    """Bytes a general spring-network step must move: positions and half-step
+    velocities read and written in FP64 (32 d bytes per particle) plus one
+    10-byte spring record per spring (2 x int32 endpoints, type, state)."""
+    return n * 32 * dim + 10 * m
+
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_2201_04565_gb300 import lsm
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    img = inclusion_image(WORKLOAD["nx"], WORKLOAD["ny"], *WORKLOAD["r"], WORKLOAD["frac"], WORKLOAD["seed"])
+    k, e, m = two_phase_materials()
+    spec = lsm.Specimen.from_image(img, k, e, m, dt=WORKLOAD["dt"], damping=WORKLOAD["damping"],
+                                   precision=args.precision, stream=stream.cuda_stream)
+    nst = WORKLOAD["steps_per_increment"]
+    inc = [0]
+
+    def increment():
+        inc[0] += 1
+        spec.apply_strain(inc[0] * WORKLOAD["eps_inc"])
+        spec.step(nst)
+
+    for _ in range(args.warmup):
+        increment()
+    spec.synchronize()
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+        td.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = spec.counters()[2]
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    t_all0.record(stream)
+    for q in range(args.steps):
+        inc[0] += 1
+        spec.apply_strain(inc[0] * WORKLOAD["eps_inc"])
+        ev[q][0].record(stream)
+        spec.step(nst)
+        ev[q][1].record(stream)
+    t_all1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    launches = spec.counters()[2] - launches0
+    clk = clocks.stop()
+    ms = t_all0.elapsed_time(t_all1)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    if dist:
+        import torch.distributed as td
+        t = torch.tensor([ms], device="cuda")
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        ms = float(t.item())
+        td.barrier()
+
+    # end-to-end through the public API: host strain in, host sample and
+    # broken mask out, every step
+    e2e_steps = max(2, min(args.steps, 5))
+    spec.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        inc[0] += 1
+        spec.apply_strain(inc[0] * WORKLOAD["eps_inc"])
+        spec.step(nst)
+        samples = spec.samples()
+        mask, _ = spec.broken()
+    t1 = time.perf_counter()
+    e2e_value = spec.m * nst * e2e_steps * world / (t1 - t0)
+    d2h = mask.nbytes + 64 * len(samples) // max(len(samples), 1)
+
+    hbm, peak_src = _peaks()
+    units = spec.m * nst * args.steps * world
+    value = units / (ms * 1e-3)
+    per_step_ms = statistics.mean(step_ms) / nst  # one time step (all its kernels)
+    algb = algorithmic_bytes(spec.n, spec.m, spec.dim)
+    achieved = algb / (per_step_ms * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"exact64": "f64", "fast64": "f64", "f32": "f32-force/f64-state"}.get(args.precision, args.precision),
+        "data": "synthetic (seeded two-phase inclusion image; paper's specimen files not used)",
+        "config": {"workload": WORKLOAD["name"], "image": "%dx%d" % (WORKLOAD["nx"], WORKLOAD["ny"]),
+                   "particles": spec.n, "springs": spec.m, "steps_per_bench_step": nst,
+                   "dt": WORKLOAD["dt"], "damping": WORKLOAD["damping"], "precision": args.precision,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (%.0f MB state+springs per time step)" % (algb / 1e6)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "algorithmic_bytes_per_time_step": algb, "time_step_ms": per_step_ms,
+                     "peak_source": peak_src},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8, "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    spec.close()
+    return out
+
+
+def run_oracle_sample(budget_s=12.0):
+    """The FP64 CPU oracle on the same workload: one strain increment, then as
+    many time steps as fit in about budget_s seconds (single thread)."""
+    import oracle
+    oracle.build_oracle()
+    img = inclusion_image(WORKLOAD["nx"], WORKLOAD["ny"], *WORKLOAD["r"], WORKLOAD["frac"], WORKLOAD["seed"])
+    k, e, m = two_phase_materials()
+    o = oracle.Oracle.from_image(img, k, e, m, dt=WORKLOAD["dt"], damping=WORKLOAD["damping"])
+    o.apply_strain(WORKLOAD["eps_inc"])
+    t0 = time.perf_counter()
+    o.step(1)
+    one = time.perf_counter() - t0
+    nsteps = max(1, int(budget_s / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    o.step(nsteps)
+    dt = time.perf_counter() - t0
+    return {"value": o.m * nsteps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d time steps of the full 2048x2048 workload after one 1e-3 strain increment "
+                      "(single-threaded plain C FP64 oracle)" % nsteps,
+            "seconds": dt, "steps": nsteps}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lsm", choices=["lsm", "reference"])
+    ap.add_argument("--precision", default="fast64", choices=["exact64", "fast64", "f32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        base = run_oracle_sample(budget_s=max(5.0, 2.0 * args.steps))
+        out = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT,
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": 1e3 * base["seconds"] / base["steps"] * WORKLOAD["steps_per_increment"],
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic (seeded two-phase inclusion image)",
+               "config": {"workload": WORKLOAD["name"], "image": "2048x2048"},
+               "cpu_baseline": base,
+               "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return 0
+
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        td.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    out = run_gpu(args, rank, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = run_oracle_sample()
+    if world > 1:
+        import torch.distributed as td
+        td.barrier()
+        td.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

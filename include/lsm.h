@@ -1,0 +1,240 @@
+/*
+ * lsm.h -- C ABI of the GB300 lattice-spring library (liblsm.so).
+ *
+ * The library runs the per-timestep update of a particle-spring network built
+ * from a 2D image or a 3D voxel volume (arXiv 2201.04565, "ImageMech"):
+ *   - spring force, Eq. 2 (harmonic spring, Eq. 1 potential);
+ *   - the sum of spring forces onto particles, done as a deterministic
+ *     particle-centric gather (no floating-point atomics; Section 2.3 uses
+ *     atomicAdd there);
+ *   - the irreversible break test (Section 2.3 force listing: a spring longer
+ *     than rc gives zero force from then on; Section 4: broken springs stay);
+ *   - damped velocity Verlet in the half-step-velocity form, Eqs. 3-5
+ *     (Section 2.2), under displacement-controlled loading along x
+ *     (Sections 2.3 and 3.1);
+ *   - the virial stress, Eq. 7, and the energies (Section 2.3, output step).
+ *
+ * Conventions for every call:
+ *   - Every function returns an lsm_status; LSM_OK is 0, errors are negative.
+ *     lsm_last_error() gives a one-line reason for the last failure on a
+ *     context. A context is not thread-safe.
+ *   - Host pointers are plain host memory owned by the caller. Inputs are
+ *     copied during the call; outputs are written into caller buffers of the
+ *     stated size. The context owns all device memory it allocates.
+ *   - Particle arrays are component-major: component c of particle p is at
+ *     [c * n + p]. Particles of an image build are the non-void pixels or
+ *     voxels in raster order (x fastest, then y, then z). Springs are in
+ *     canonical order: endpoints i < j, sorted by (i, j).
+ *   - Work is ordered on the context's CUDA stream. lsm_apply_strain and
+ *     lsm_step may return before the device work ends; query calls
+ *     (state, masks, samples) synchronise the stream. An asynchronous device
+ *     error (non-finite state) is recorded in a device status word and is
+ *     returned by the next synchronising call as LSM_ENONFINITE.
+ */
+#ifndef LSM_H
+#define LSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lsm_ctx lsm_ctx;
+
+typedef enum {
+    LSM_OK = 0,
+    LSM_EINVAL = -1,      /* bad argument, size or descriptor field */
+    LSM_ENOMEM = -2,      /* device or host allocation failed */
+    LSM_ECUDA = -3,       /* a CUDA runtime call failed */
+    LSM_ENOTCONV = -4,    /* relax hit max_steps before the tolerance */
+    LSM_ETIMEOUT = -5,    /* a bounded device wait gave up */
+    LSM_ENONFINITE = -6,  /* the state became non-finite */
+    LSM_ESTATE = -7       /* call not valid in the context's current state */
+} lsm_status;
+
+/* Arithmetic of the spring pass (force evaluation and gather).
+ *  LSM_PREC_EXACT64: IEEE double with correctly rounded sqrt and divide, no
+ *      fused multiply-add, gather in canonical spring order: the same
+ *      operations in the same order as the plain FP64 definition, so the
+ *      state is bit-identical to a sequential FP64 evaluation.
+ *  LSM_PREC_FAST64: double precision throughout, reassociated (fused
+ *      multiply-add, 1/r from a reciprocal square root); results agree with
+ *      the exact mode to a few ulps per step.
+ *  LSM_PREC_F32: spring vector formed in double, spring force evaluated in
+ *      single precision, forces gathered and positions/velocities integrated
+ *      in double. */
+enum { LSM_PREC_EXACT64 = 0, LSM_PREC_FAST64 = 1, LSM_PREC_F32 = 2 };
+
+/* Image build descriptor (the paper's Img2Particle stage, Section 1 and
+ * Fig. 6, on a square/cubic lattice with first and second neighbours).
+ *  dim          2 or 3.
+ *  nx, ny, nz   image size; nz is ignored (taken as 1) when dim == 2. nx >= 2.
+ *  phase        host, nx*ny*nz bytes, x fastest: 0 = void (no particle),
+ *               1..nphase = material phase. Copied during the build.
+ *  nphase       number of phases (1..255).
+ *  k_tab        host, nphase*nphase doubles, row-major, entry
+ *               [(pi-1)*nphase + (pj-1)]: spring constant between phases pi, pj.
+ *  epsc_tab     same layout: critical strain; rc = r0 (1 + eps_c) (Table of
+ *               spring constants, Section 3.1, gives rc per spring type).
+ *  mass_tab     host, nphase doubles, particle mass by phase (NULL = all 1).
+ *  k2_ratio     multiplier on k for second-neighbour (diagonal) springs.
+ *  a            lattice spacing; first-neighbour r0 = a, second = a sqrt 2.
+ *  dt           time step (Section 2.2).
+ *  damping      viscous coefficient gamma: a = (F - gamma vh) / m.
+ *  grip_mode    0 = roller grips (x component of the first and last image
+ *               column prescribed), 1 = clamped (all components).
+ *  load_mode    0 = each load increment remaps x of every particle affinely
+ *               about the specimen centre, then sets the grips;
+ *               1 = only the grips move.
+ *  precision    LSM_PREC_* (see above).
+ *  path         0 = automatic (2D images with up to 8 phases run the fused
+ *               tile kernel, everything else the general spring-list
+ *               kernels); 1 = always the general spring-list kernels.
+ *  stream       cudaStream_t to order work on (NULL = the library creates one). */
+typedef struct lsm_desc {
+    int32_t dim, nx, ny, nz;
+    const uint8_t *phase;
+    int32_t nphase;
+    const double *k_tab;
+    const double *epsc_tab;
+    const double *mass_tab;
+    double k2_ratio;
+    double a;
+    double dt;
+    double damping;
+    int32_t grip_mode;
+    int32_t load_mode;
+    int32_t precision;
+    int32_t path;
+    void *stream;
+} lsm_desc;
+
+/* General network descriptor (the paper's solver reads any particle/bond
+ * list, Section 3.1). Springs must be in canonical order (si < sj, sorted,
+ * unique). All arrays are host memory, copied during the build.
+ *  X        dim*n reference (and initial) positions, component-major.
+ *  mass     n masses (NULL = all 1).
+ *  fix      dim*n bytes, 1 = prescribed component (NULL = none).
+ *  grip     n bytes: 0 interior, 1 left grip, 2 right grip (NULL = none).
+ *  si, sj, k, r0, rc2   m springs; rc2 is the squared break length
+ *           (INFINITY = unbreakable).
+ *  xc       load centre for the affine remap and the grip law.
+ *  omega    reference volume of the virial stress, Eq. 7.
+ *  grip_area  area normalising the grip reaction. */
+typedef struct lsm_net_desc {
+    int32_t dim;
+    int64_t n, m;
+    const double *X;
+    const double *mass;
+    const uint8_t *fix;
+    const uint8_t *grip;
+    const int32_t *si, *sj;
+    const double *k, *r0, *rc2;
+    double dt, damping, xc, omega, grip_area;
+    int32_t load_mode;
+    int32_t precision;
+    void *stream;
+} lsm_net_desc;
+
+/* One stress-strain sample, recorded at the end of every lsm_step / lsm_relax
+ * call (the paper's output callback, Section 2.3 and Fig. 1).
+ *  eps         engineering strain of the last lsm_apply_strain.
+ *  sigma_vir   xx virial stress, Eq. 7, over the reference box, tension > 0.
+ *  sigma_grip  xx stress from the right-grip reaction over the grip area.
+ *  pe, ke      potential (Eq. 1, intact springs) and kinetic energy.
+ *  residual    max over free components of max(|F|, |v|).
+ *  n_broken    broken springs so far.
+ *  step        time steps taken so far. */
+typedef struct lsm_sample {
+    double eps, sigma_vir, sigma_grip, pe, ke, residual;
+    int64_t n_broken, step;
+} lsm_sample;
+
+/* Build a context from an image. On success *out owns device memory until
+ * lsm_destroy. Errors: LSM_EINVAL (bad descriptor), LSM_ENOMEM, LSM_ECUDA. */
+lsm_status lsm_build_from_image(const lsm_desc *desc, lsm_ctx **out);
+
+/* Build a context from an explicit spring network (see lsm_net_desc). */
+lsm_status lsm_build_network(const lsm_net_desc *desc, lsm_ctx **out);
+
+/* Release all device memory of the context. NULL is ignored. */
+void lsm_destroy(lsm_ctx *ctx);
+
+/* One-line description of the last error on ctx (never NULL). With ctx ==
+ * NULL, the last build error of the calling thread. */
+const char *lsm_last_error(const lsm_ctx *ctx);
+
+/* Sizes: particles n, springs m, dimension. Any output may be NULL. */
+lsm_status lsm_sizes(lsm_ctx *ctx, int64_t *n, int64_t *m, int32_t *dim);
+
+/* Displacement-controlled load increment (Sections 2.3, 3.1): set the
+ * engineering strain to eps (absolute, not a delta). In load_mode 0 the x
+ * coordinate of every particle is remapped x <- xc + (x - xc)(1+eps)/(1+eps_old);
+ * prescribed x components are then set to X + eps (X - xc) with zero
+ * velocity and acceleration. Stream-ordered. Errors: LSM_EINVAL if
+ * 1 + eps <= 0. */
+lsm_status lsm_apply_strain(lsm_ctx *ctx, double eps);
+
+/* Advance nsteps (>= 1) time steps of damped velocity Verlet with the break
+ * test (Eqs. 2-5), then record one lsm_sample. Stream-ordered (the step loop
+ * is a cached CUDA graph per nsteps). */
+lsm_status lsm_step(lsm_ctx *ctx, int64_t nsteps);
+
+/* Relax to a force residual: run steps in batches of check_every until the
+ * sample residual is <= tol; records one sample per batch... only the last
+ * batch's sample is kept. *taken = steps run. Synchronises after every batch.
+ * Returns LSM_OK, or LSM_ENOTCONV after max_steps. */
+lsm_status lsm_relax(lsm_ctx *ctx, double tol, int64_t max_steps, int64_t check_every,
+                     int64_t *taken);
+
+/* Copy up to cap recorded samples' (eps, sigma_vir) pairs; *count = number
+ * recorded (may exceed cap). Synchronises. */
+lsm_status lsm_stress_strain(lsm_ctx *ctx, double *eps, double *sigma, int64_t cap,
+                             int64_t *count);
+
+/* Copy up to cap full samples. Synchronises. */
+lsm_status lsm_samples(lsm_ctx *ctx, lsm_sample *out, int64_t cap, int64_t *count);
+
+/* Broken-spring mask in canonical spring order: out[s] = 1 if broken.
+ * cap >= m is required (LSM_EINVAL otherwise); *m = spring count;
+ * *first_break_step = index of the first step in which any spring broke,
+ * -1 if none. Any output pointer may be NULL except out. Synchronises. */
+lsm_status lsm_broken_mask(lsm_ctx *ctx, uint8_t *out, int64_t cap, int64_t *m,
+                           int64_t *first_break_step);
+
+/* Per-spring step index of the break (-1 = intact), canonical order, m
+ * entries. Synchronises. */
+lsm_status lsm_break_steps(lsm_ctx *ctx, int64_t *out, int64_t cap);
+
+/* Positions and velocities (dim*n doubles each, component-major; either may
+ * be NULL). Velocities are full-step velocities v(t). Synchronises. */
+lsm_status lsm_get_state(lsm_ctx *ctx, double *x, double *v);
+
+/* Replace positions and/or velocities (NULL keeps the current array); the
+ * acceleration is re-evaluated from the new state, Eq. 4. Synchronises. */
+lsm_status lsm_set_state(lsm_ctx *ctx, const double *x, const double *v);
+
+/* Spring topology in canonical order (m entries each; any may be NULL). */
+lsm_status lsm_topology(lsm_ctx *ctx, int32_t *si, int32_t *sj, double *k, double *r0,
+                        double *rc2);
+
+/* Observables of the current state without advancing (same fields as a
+ * recorded sample; the sample history is unchanged). Synchronises. */
+lsm_status lsm_observe(lsm_ctx *ctx, lsm_sample *out);
+
+/* Block until all work queued on the context's stream is done; returns any
+ * pending device status. */
+lsm_status lsm_synchronize(lsm_ctx *ctx);
+
+/* Counters for throughput accounting: time steps taken, spring updates
+ * (springs x steps) and CUDA kernels launched by the library (graph nodes
+ * included). Any output may be NULL. */
+lsm_status lsm_counters(lsm_ctx *ctx, int64_t *steps, int64_t *spring_updates,
+                        int64_t *kernel_launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSM_H */

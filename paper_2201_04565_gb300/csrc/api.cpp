@@ -1,0 +1,462 @@
+// api.cpp -- the extern "C" boundary of liblsm (declared in include/lsm.h).
+//
+// Argument checks, context lifetime, stream handling and host<->device
+// copies. Every compute step runs in the kernels of kernels.cu.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "lsm_internal.h"
+
+using lsm::Ctx;
+
+struct lsm_ctx : public Ctx {};
+
+namespace {
+
+thread_local std::string g_build_err;
+
+lsm_status fail(Ctx *c, lsm_status st, const std::string &msg)
+{
+    if (c)
+        c->err = msg;
+    else
+        g_build_err = msg;
+    return st;
+}
+
+lsm_status cuda_fail(Ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, LSM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Pending asynchronous device status (non-finite state).
+lsm_status device_status(Ctx *c)
+{
+    int st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+    if (st & 1) return fail(c, LSM_ENONFINITE, "non-finite position or velocity detected");
+    return LSM_OK;
+}
+
+// Slot of canonical spring s in the tile path's per-pixel layout:
+// 0 (+1,0), 1 (-1,+1), 2 (0,+1), 3 (+1,+1).
+int tile_slot(const lsm::HostNet &h, int64_t s, int64_t *pixel)
+{
+    const int64_t pi = h.pix[h.si[s]], pj = h.pix[h.sj[s]];
+    const int64_t dx = pj % h.nx - pi % h.nx, dy = pj / h.nx - pi / h.nx;
+    *pixel = pi;
+    if (dy == 0) return 0;
+    return dx < 0 ? 1 : (dx == 0 ? 2 : 3);
+}
+
+lsm_status finish_build(lsm_ctx *c, void *stream, lsm_ctx **out, int path = 0)
+{
+    c->tile = path != 1 && c->h.dim == 2 && c->h.nx > 0 && c->h.nphase >= 1 && c->h.nphase <= 8;
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            g_build_err = std::string("stream create: ") + cudaGetErrorString(e);
+            delete c;
+            return LSM_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    cudaGetLastError();  // clear an error left by an unrelated earlier call
+    cudaError_t e = lsm::upload(*c);
+    const char *site = "upload";
+    if (e != cudaSuccess) site = lsm::last_fail_site();
+    if (e == cudaSuccess) {
+        e = lsm::launch_init_accel(*c);
+        site = "initial acceleration";
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        g_build_err = std::string("build (") + site + "): " + cudaGetErrorString(e);
+        lsm_status st = e == cudaErrorMemoryAllocation ? LSM_ENOMEM : LSM_ECUDA;
+        lsm::free_device(*c);
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return LSM_OK;
+}
+
+lsm_status ensure_sample_room(Ctx *c)
+{
+    if (c->nsamples < c->sample_cap) return LSM_OK;
+    int64_t cap = c->sample_cap * 2;
+    lsm::DeviceSample *ns = nullptr;
+    cudaError_t e = cudaMalloc((void **)&ns, cap * sizeof(lsm::DeviceSample));
+    if (e != cudaSuccess) return fail(c, LSM_ENOMEM, "sample buffer growth failed");
+    e = cudaMemcpyAsync(ns, c->samples, c->sample_cap * sizeof(lsm::DeviceSample),
+                        cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(ns);
+        return cuda_fail(c, e, "sample buffer growth");
+    }
+    cudaFree(c->samples);
+    c->samples = ns;
+    c->sample_cap = cap;
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);  // graphs hold the old pointer
+    c->graphs.clear();
+    return LSM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lsm_status lsm_build_from_image(const lsm_desc *desc, lsm_ctx **out)
+{
+    if (!desc || !out) return fail(nullptr, LSM_EINVAL, "desc and out are required");
+    *out = nullptr;
+    if (desc->precision < LSM_PREC_EXACT64 || desc->precision > LSM_PREC_F32)
+        return fail(nullptr, LSM_EINVAL, "precision must be LSM_PREC_EXACT64, _FAST64 or _F32");
+    lsm_ctx *c = new (std::nothrow) lsm_ctx();
+    if (!c) return fail(nullptr, LSM_ENOMEM, "host allocation failed");
+    std::string err;
+    bool ok;
+    try {
+        ok = lsm::net_from_image(*desc, c->h, err);
+    } catch (const std::bad_alloc &) {
+        delete c;
+        return fail(nullptr, LSM_ENOMEM, "host allocation failed during build");
+    }
+    if (!ok) {
+        delete c;
+        return fail(nullptr, LSM_EINVAL, err);
+    }
+    if (desc->path != 0 && desc->path != 1) {
+        delete c;
+        return fail(nullptr, LSM_EINVAL, "path must be 0 (automatic) or 1 (spring-list kernels)");
+    }
+    return finish_build(c, desc->stream, out, desc->path);
+}
+
+lsm_status lsm_build_network(const lsm_net_desc *desc, lsm_ctx **out)
+{
+    if (!desc || !out) return fail(nullptr, LSM_EINVAL, "desc and out are required");
+    *out = nullptr;
+    if (desc->precision < LSM_PREC_EXACT64 || desc->precision > LSM_PREC_F32)
+        return fail(nullptr, LSM_EINVAL, "precision must be LSM_PREC_EXACT64, _FAST64 or _F32");
+    if (desc->load_mode != 0 && desc->load_mode != 1)
+        return fail(nullptr, LSM_EINVAL, "load_mode must be 0 or 1");
+    lsm_ctx *c = new (std::nothrow) lsm_ctx();
+    if (!c) return fail(nullptr, LSM_ENOMEM, "host allocation failed");
+    std::string err;
+    bool ok;
+    try {
+        ok = lsm::net_from_desc(*desc, c->h, err);
+    } catch (const std::bad_alloc &) {
+        delete c;
+        return fail(nullptr, LSM_ENOMEM, "host allocation failed during build");
+    }
+    if (!ok) {
+        delete c;
+        return fail(nullptr, LSM_EINVAL, err);
+    }
+    return finish_build(c, desc->stream, out, 1);
+}
+
+void lsm_destroy(lsm_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    lsm::free_device(*c);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char *lsm_last_error(const lsm_ctx *c)
+{
+    return c ? c->err.c_str() : g_build_err.c_str();
+}
+
+lsm_status lsm_sizes(lsm_ctx *c, int64_t *n, int64_t *m, int32_t *dim)
+{
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    if (n) *n = c->n;
+    if (m) *m = c->m;
+    if (dim) *dim = c->dim;
+    return LSM_OK;
+}
+
+lsm_status lsm_apply_strain(lsm_ctx *c, double eps)
+{
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    if (!(1.0 + eps > 0.0) || !std::isfinite(eps))
+        return fail(c, LSM_EINVAL, "strain must be finite with 1 + eps > 0");
+    cudaError_t e = lsm::launch_apply_strain(*c, c->eps, eps);
+    if (e != cudaSuccess) return cuda_fail(c, e, "apply_strain");
+    c->eps = eps;
+    return LSM_OK;
+}
+
+lsm_status lsm_step(lsm_ctx *c, int64_t nsteps)
+{
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    if (nsteps < 1) return fail(c, LSM_EINVAL, "nsteps must be >= 1");
+    if (nsteps > 100000) return fail(c, LSM_EINVAL, "nsteps per call is limited to 100000");
+    lsm_status st = ensure_sample_room(c);
+    if (st != LSM_OK) return st;
+    cudaError_t e = lsm::launch_steps(*c, nsteps, true);
+    if (e != cudaSuccess) return cuda_fail(c, e, "step");
+    c->nsamples += 1;
+    c->steps += nsteps;
+    return LSM_OK;
+}
+
+lsm_status lsm_relax(lsm_ctx *c, double tol, int64_t max_steps, int64_t check_every,
+                     int64_t *taken)
+{
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    if (!(tol >= 0) || max_steps < 0 || check_every < 1 || check_every > 100000)
+        return fail(c, LSM_EINVAL, "need tol >= 0, max_steps >= 0, 1 <= check_every <= 100000");
+    lsm_status st = ensure_sample_room(c);
+    if (st != LSM_OK) return st;
+    int64_t done = 0;
+    lsm_status result = LSM_ENOTCONV;
+    while (done < max_steps) {
+        const int64_t nb = max_steps - done < check_every ? max_steps - done : check_every;
+        cudaError_t e = lsm::launch_steps(*c, nb, false);
+        if (e != cudaSuccess) return cuda_fail(c, e, "relax");
+        done += nb;
+        c->steps += nb;
+        lsm::DeviceSample smp;
+        e = cudaMemcpyAsync(&smp, c->scratch_sample, sizeof(smp), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "relax readback");
+        st = device_status(c);
+        if (st != LSM_OK) {
+            if (taken) *taken = done;
+            return st;
+        }
+        if (smp.residual <= tol) {
+            result = LSM_OK;
+            break;
+        }
+    }
+    if (done > 0) {  // record the final state's sample
+        cudaError_t e = cudaMemcpyAsync(c->samples + c->nsamples, c->scratch_sample,
+                                        sizeof(lsm::DeviceSample), cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "relax record");
+        long long ns = c->nsamples + 1;
+        e = cudaMemcpyAsync(c->d_nsamples, &ns, sizeof(ns), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "relax record");
+        c->nsamples = ns;
+    }
+    if (taken) *taken = done;
+    if (result != LSM_OK) return fail(c, LSM_ENOTCONV, "residual above tolerance after max_steps");
+    return LSM_OK;
+}
+
+lsm_status lsm_samples(lsm_ctx *c, lsm_sample *out, int64_t cap, int64_t *count)
+{
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    if (cap < 0 || (cap > 0 && !out)) return fail(c, LSM_EINVAL, "bad output buffer");
+    lsm_status st = device_status(c);
+    if (st != LSM_OK) return st;
+    const int64_t k = c->nsamples < cap ? c->nsamples : cap;
+    if (k > 0) {
+        static_assert(sizeof(lsm::DeviceSample) == sizeof(lsm_sample), "sample layout");
+        cudaError_t e = cudaMemcpyAsync(out, c->samples, k * sizeof(lsm_sample),
+                                        cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "samples");
+    }
+    if (count) *count = c->nsamples;
+    return LSM_OK;
+}
+
+lsm_status lsm_stress_strain(lsm_ctx *c, double *eps, double *sigma, int64_t cap, int64_t *count)
+{
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    if (cap < 0 || (cap > 0 && (!eps || !sigma))) return fail(c, LSM_EINVAL, "bad output buffers");
+    std::vector<lsm_sample> tmp((size_t)(c->nsamples < cap ? c->nsamples : cap));
+    int64_t cnt = 0;
+    lsm_status st = lsm_samples(c, tmp.data(), (int64_t)tmp.size(), &cnt);
+    if (st != LSM_OK) return st;
+    for (size_t q = 0; q < tmp.size(); q++) {
+        eps[q] = tmp[q].eps;
+        sigma[q] = tmp[q].sigma_vir;
+    }
+    if (count) *count = cnt;
+    return LSM_OK;
+}
+
+lsm_status lsm_broken_mask(lsm_ctx *c, uint8_t *out, int64_t cap, int64_t *m,
+                           int64_t *first_break_step)
+{
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    if (!out || cap < c->m) return fail(c, LSM_EINVAL, "output buffer smaller than the spring count");
+    lsm_status st = device_status(c);
+    if (st != LSM_OK) return st;
+    unsigned long long fb = 0;
+    cudaError_t e = cudaSuccess;
+    std::vector<uint8_t> pm;
+    if (c->tile) {
+        pm.resize(c->tnp);
+        e = cudaMemcpyAsync(pm.data(), c->tmask, c->tnp, cudaMemcpyDeviceToHost, c->stream);
+    } else if (c->m) {
+        e = cudaMemcpyAsync(out, c->state, c->m, cudaMemcpyDeviceToHost, c->stream);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&fb, c->d_first_break, sizeof(fb), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "broken_mask");
+    if (c->tile) {
+        for (int64_t sp = 0; sp < c->m; sp++) {
+            int64_t g;
+            const int sl = tile_slot(c->h, sp, &g);
+            out[sp] = (uint8_t)((pm[g] >> sl) & 1u);
+        }
+    }
+    if (m) *m = c->m;
+    if (first_break_step) *first_break_step = fb == ~0ull ? -1 : (int64_t)fb;
+    return LSM_OK;
+}
+
+lsm_status lsm_break_steps(lsm_ctx *c, int64_t *out, int64_t cap)
+{
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    if (!out || cap < c->m) return fail(c, LSM_EINVAL, "output buffer smaller than the spring count");
+    cudaError_t e = cudaSuccess;
+    std::vector<int64_t> pb;
+    if (c->tile) {
+        pb.resize(4 * c->tnp);
+        e = cudaMemcpyAsync(pb.data(), c->tbrk, 4 * c->tnp * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+    } else if (c->m) {
+        e = cudaMemcpyAsync(out, c->brk, c->m * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "break_steps");
+    if (c->tile) {
+        for (int64_t sp = 0; sp < c->m; sp++) {
+            int64_t g;
+            const int sl = tile_slot(c->h, sp, &g);
+            out[sp] = pb[(int64_t)sl * c->tnp + g];
+        }
+    }
+    return LSM_OK;
+}
+
+lsm_status lsm_get_state(lsm_ctx *c, double *x, double *v)
+{
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    lsm_status st = device_status(c);
+    if (st != LSM_OK) return st;
+    const size_t bytes = (size_t)c->dim * c->n * sizeof(double);
+    cudaError_t e = cudaSuccess;
+    if (c->tile) {
+        std::vector<double> gx(x ? 2 * c->tnp : 0), gv(v ? 2 * c->tnp : 0);
+        if (x) e = cudaMemcpyAsync(gx.data(), c->tx[c->tcur], 2 * c->tnp * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess && v)
+            e = cudaMemcpyAsync(gv.data(), c->tvobs, 2 * c->tnp * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "get_state");
+        for (int cc = 0; cc < 2; cc++)
+            for (int64_t p = 0; p < c->n; p++) {
+                const int64_t g = c->h.pix[p];
+                if (x) x[cc * c->n + p] = gx[cc * c->tnp + g];
+                if (v) v[cc * c->n + p] = gv[cc * c->tnp + g];
+            }
+        return LSM_OK;
+    }
+    if (x) e = cudaMemcpyAsync(x, c->x, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && v) e = cudaMemcpyAsync(v, c->v, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get_state");
+    return LSM_OK;
+}
+
+lsm_status lsm_set_state(lsm_ctx *c, const double *x, const double *v)
+{
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    const size_t bytes = (size_t)c->dim * c->n * sizeof(double);
+    cudaError_t e = cudaSuccess;
+    if (c->tile) {
+        // scatter onto the pixel grid (void pixels keep their placeholder)
+        std::vector<double> gx, gv;
+        if (x) gx.resize(2 * c->tnp);
+        if (v) gv.resize(2 * c->tnp);
+        if (x) e = cudaMemcpyAsync(gx.data(), c->tx[c->tcur], 2 * c->tnp * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess && v)
+            e = cudaMemcpyAsync(gv.data(), c->tvobs, 2 * c->tnp * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
+        for (int cc = 0; cc < 2; cc++)
+            for (int64_t p = 0; p < c->n; p++) {
+                const int64_t g = c->h.pix[p];
+                if (x) gx[cc * c->tnp + g] = x[cc * c->n + p];
+                if (v) gv[cc * c->tnp + g] = v[cc * c->n + p];
+            }
+        if (x) e = cudaMemcpyAsync(c->tx[c->tcur], gx.data(), 2 * c->tnp * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess && v)
+            e = cudaMemcpyAsync(c->tvobs, gv.data(), 2 * c->tnp * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = lsm::launch_init_accel(*c);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
+        return LSM_OK;
+    }
+    if (x) e = cudaMemcpyAsync(c->x, x, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && v) e = cudaMemcpyAsync(c->v, v, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = lsm::launch_init_accel(*c);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
+    return LSM_OK;
+}
+
+lsm_status lsm_topology(lsm_ctx *c, int32_t *si, int32_t *sj, double *k, double *r0, double *rc2)
+{
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    const lsm::HostNet &h = c->h;
+    for (int64_t s = 0; s < h.m; s++) {
+        const lsm::SpringType &t = h.types[h.stype[s]];
+        if (si) si[s] = h.si[s];
+        if (sj) sj[s] = h.sj[s];
+        if (k) k[s] = t.k;
+        if (r0) r0[s] = t.r0;
+        if (rc2) rc2[s] = t.rc2;
+    }
+    return LSM_OK;
+}
+
+lsm_status lsm_observe(lsm_ctx *c, lsm_sample *out)
+{
+    if (!c || !out) return fail(c, LSM_EINVAL, "null argument");
+    cudaError_t e = lsm::launch_observe(*c, c->scratch_sample);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, c->scratch_sample, sizeof(lsm_sample), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "observe");
+    return device_status(c);
+}
+
+lsm_status lsm_synchronize(lsm_ctx *c)
+{
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
+    return device_status(c);
+}
+
+lsm_status lsm_counters(lsm_ctx *c, int64_t *steps, int64_t *spring_updates,
+                        int64_t *kernel_launches)
+{
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    if (steps) *steps = c->steps;
+    if (spring_updates) *spring_updates = c->steps * c->m;
+    if (kernel_launches) *kernel_launches = c->launches;
+    return LSM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,675 @@
+// kernels.cu -- sm_103a kernels of the general (CSR) lattice-spring path.
+//
+// One time step (Section 2.2, Eqs. 3-5, half-step velocity form) is two
+// launches:
+//   k_springs : one thread per spring. Spring vector, break test on the
+//               squared length (Section 2.3 force listing: a spring longer
+//               than rc is zeroed for good in the step the test fires), and
+//               the spring force of Eq. 2, written once per spring.
+//   k_gather  : one thread per particle. Sums the forces of its springs in
+//               ascending spring order (no atomics: the sum is the same on
+//               every run and equals the sequential canonical-order sum), then
+//               the second half-kick with viscous damping (Eqs. 4-5) and, when
+//               another step follows in the same call, the next half-kick and
+//               drift (Eq. 3), so a step costs one particle pass.
+// On the last step of a call both kernels also emit per-block partials of the
+// sample observables (virial sum, Eq. 7; PE, Eq. 1; KE; grip reaction;
+// residual), which k_reduce folds in a fixed order into one sample.
+//
+// Partials are per fixed block of TPB elements, so the reduction order does
+// not depend on the grid; every launch covers its range with one block per
+// chunk.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#include "lsm_internal.h"
+
+namespace lsm {
+
+constexpr int TPB = 256;
+constexpr int RED_THREADS = 1024;
+
+// ------------------------------------------------------------- arithmetic
+// EXACT64 uses only correctly rounded IEEE operations in a fixed order (no
+// contraction into fused multiply-add).
+__device__ __forceinline__ double ad(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sb(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double ml(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dv(double a, double b) { return __ddiv_rn(a, b); }
+
+// Fixed-order block sum of one value per thread (TPB threads): warp xor tree,
+// then the warps in order. Deterministic for a given TPB.
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < (int)(blockDim.x >> 5); q++) t += sh[q];
+    return t;
+}
+
+__device__ __forceinline__ double block_max(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < (int)(blockDim.x >> 5); q++) t = fmax(t, sh[q]);
+    return t;
+}
+
+// ------------------------------------------------------------ spring pass
+template <int DIM, int PREC, bool BREAK, bool SAMPLE>
+__global__ void __launch_bounds__(TPB)
+k_springs(int64_t m, int64_t n, const int32_t *__restrict__ si, const int32_t *__restrict__ sj,
+          const uint16_t *__restrict__ stype, const SpringType *__restrict__ types,
+          uint8_t *__restrict__ state, long long *__restrict__ brk, const double *__restrict__ x,
+          double *__restrict__ fs, const long long *__restrict__ d_step,
+          unsigned long long *__restrict__ first_break, unsigned long long *__restrict__ nbroken,
+          double *__restrict__ part, int64_t nblk)
+{
+    __shared__ double sh[TPB / 32];
+    const int64_t s = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    double w = 0.0, u = 0.0;
+    if (s < m && !state[s]) {
+        const int32_t i = si[s], j = sj[s];
+        const SpringType t = types[stype[s]];
+        double d[DIM];
+#pragma unroll
+        for (int c = 0; c < DIM; c++) d[c] = sb(x[c * n + j], x[c * n + i]);
+        double r2;
+        if constexpr (PREC == LSM_PREC_EXACT64) {
+            r2 = ad(ml(d[0], d[0]), ml(d[1], d[1]));
+            if constexpr (DIM == 3) r2 = ad(r2, ml(d[2], d[2]));
+        } else {
+            r2 = d[0] * d[0];
+#pragma unroll
+            for (int c = 1; c < DIM; c++) r2 = fma(d[c], d[c], r2);
+        }
+        if (BREAK && r2 > t.rc2) {
+            // Heaviside switch: the spring is broken for good and gives no
+            // force from this step on.
+            state[s] = 1;
+            const long long st = *d_step;
+            brk[s] = st;
+            atomicMin(first_break, (unsigned long long)st);
+            atomicAdd(nbroken, 1ull);
+#pragma unroll
+            for (int c = 0; c < DIM; c++) fs[c * m + s] = 0.0;
+        } else {
+            double cs;
+            if constexpr (PREC == LSM_PREC_EXACT64) {
+                const double r = __dsqrt_rn(r2);
+                cs = dv(ml(t.k, sb(r, t.r0)), r);
+                if (SAMPLE) {
+                    const double e = sb(r, t.r0);
+                    u = ml(ml(ml(0.5, t.k), e), e);
+                }
+#pragma unroll
+                for (int c = 0; c < DIM; c++) fs[c * m + s] = ml(cs, d[c]);
+                if (SAMPLE) w = ml(d[0], ml(cs, d[0]));
+            } else if constexpr (PREC == LSM_PREC_FAST64) {
+                const double ir = rsqrt(r2);
+                cs = fma(-t.kr0, ir, t.k);  // k (r - r0) / r = k - k r0 / r
+                if (SAMPLE) {
+                    const double e = fma(r2, ir, -t.r0);
+                    u = 0.5 * t.k * e * e;
+                }
+#pragma unroll
+                for (int c = 0; c < DIM; c++) fs[c * m + s] = cs * d[c];
+                if (SAMPLE) w = d[0] * (cs * d[0]);
+            } else {  // LSM_PREC_F32: spring vector in double, force in float
+                float df[DIM];
+#pragma unroll
+                for (int c = 0; c < DIM; c++) df[c] = (float)d[c];
+                float r2f = df[0] * df[0];
+#pragma unroll
+                for (int c = 1; c < DIM; c++) r2f = fmaf(df[c], df[c], r2f);
+                const float ir = rsqrtf(r2f);
+                const float csf = fmaf(-(float)t.kr0, ir, (float)t.k);
+                if (SAMPLE) {
+                    const float e = fmaf(r2f, ir, -(float)t.r0);
+                    u = 0.5 * t.k * (double)e * (double)e;
+                }
+#pragma unroll
+                for (int c = 0; c < DIM; c++) fs[c * m + s] = (double)(csf * df[c]);
+                if (SAMPLE) w = d[0] * (double)(csf * df[0]);
+            }
+        }
+    }
+    if (SAMPLE) {
+        const double tw = block_sum(w, sh);
+        const double tu = block_sum(u, sh);
+        if (threadIdx.x == 0) {
+            part[blockIdx.x] = tw;
+            part[nblk + blockIdx.x] = tu;
+        }
+    }
+}
+
+// ---------------------------------------------------------- particle pass
+enum { G_END = 0, G_DRIFT = 1, G_INIT = 2, G_OBSERVE = 3 };
+
+template <int DIM, int MODE, bool SAMPLE>
+__global__ void __launch_bounds__(TPB)
+k_gather(int64_t n, int64_t m, const int64_t *__restrict__ row, const uint32_t *__restrict__ inc,
+         const double *__restrict__ fs, double *__restrict__ x, double *__restrict__ v,
+         double *__restrict__ a, const double *__restrict__ mass, const uint8_t *__restrict__ fixm,
+         const uint8_t *__restrict__ grip, double dt, double hdt, double gamma,
+         double *__restrict__ part, int64_t nblk, int *__restrict__ status,
+         long long *__restrict__ d_step)
+{
+    __shared__ double sh[TPB / 32];
+    const int64_t p = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    double mvx2 = 0.0, ke = 0.0, react = 0.0, res = 0.0;
+    if ((MODE == G_END || MODE == G_DRIFT) && p == 0) *d_step += 1;
+    if (p < n) {
+        double F[DIM];
+#pragma unroll
+        for (int c = 0; c < DIM; c++) F[c] = 0.0;
+        const int64_t e0 = row[p], e1 = row[p + 1];
+        for (int64_t e = e0; e < e1; e++) {
+            const uint32_t word = inc[e];
+            const int64_t s = word >> 1;
+            if (word & 1u) {
+#pragma unroll
+                for (int c = 0; c < DIM; c++) F[c] = sb(F[c], fs[c * m + s]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < DIM; c++) F[c] = ad(F[c], fs[c * m + s]);
+            }
+        }
+        const uint8_t fx = fixm[p];
+        const double mp = mass[p];
+        bool bad = false;
+#pragma unroll
+        for (int c = 0; c < DIM; c++) {
+            const int64_t q = c * n + p;
+            if (SAMPLE && c == 0 && grip[p] == 2) react = sb(react, F[0]);
+            if (fx & (1u << c)) continue;
+            if constexpr (MODE == G_INIT) {
+                a[q] = dv(sb(F[c], ml(gamma, v[q])), mp);
+            } else if constexpr (MODE == G_OBSERVE) {
+                const double vn = v[q];
+                if (SAMPLE) {
+                    res = fmax(res, fmax(fabs(F[c]), fabs(vn)));
+                    ke += 0.5 * mp * vn * vn;
+                    if (c == 0) mvx2 += mp * vn * vn;
+                }
+            } else {
+                const double vh = v[q];
+                const double acc = dv(sb(F[c], ml(gamma, vh)), mp);
+                const double vn = ad(vh, ml(hdt, acc));
+                if (SAMPLE) {
+                    res = fmax(res, fmax(fabs(F[c]), fabs(vn)));
+                    ke += 0.5 * mp * vn * vn;
+                    if (c == 0) mvx2 += mp * vn * vn;
+                    bad |= !isfinite(vn) || !isfinite(x[q]);
+                }
+                if constexpr (MODE == G_DRIFT) {
+                    const double vh2 = ad(vn, ml(hdt, acc));
+                    v[q] = vh2;
+                    x[q] = ad(x[q], ml(dt, vh2));
+                } else {
+                    a[q] = acc;
+                    v[q] = vn;
+                }
+            }
+        }
+        if (SAMPLE && bad) atomicOr(status, 1);
+    }
+    if (SAMPLE) {
+        const double t0 = block_sum(mvx2, sh);
+        const double t1 = block_sum(ke, sh);
+        const double t2 = block_sum(react, sh);
+        const double t3 = block_max(res, sh);
+        if (threadIdx.x == 0) {
+            part[blockIdx.x] = t0;
+            part[nblk + blockIdx.x] = t1;
+            part[2 * nblk + blockIdx.x] = t2;
+            part[3 * nblk + blockIdx.x] = t3;
+        }
+    }
+}
+
+// First half-kick and drift of a call (Eq. 3): vh = v + dt/2 a; x += dt vh.
+template <int DIM>
+__global__ void __launch_bounds__(TPB)
+k_drift(int64_t n, double *__restrict__ x, double *__restrict__ v, const double *__restrict__ a,
+        const uint8_t *__restrict__ fixm, double dt, double hdt)
+{
+    const int64_t p = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (p >= n) return;
+    const uint8_t fx = fixm[p];
+#pragma unroll
+    for (int c = 0; c < DIM; c++) {
+        if (fx & (1u << c)) continue;
+        const int64_t q = c * n + p;
+        const double vh = ad(v[q], ml(hdt, a[q]));
+        v[q] = vh;
+        x[q] = ad(x[q], ml(dt, vh));
+    }
+}
+
+// Load increment (Sections 2.3, 3.1).
+__global__ void __launch_bounds__(TPB)
+k_apply_strain(int64_t n, double *__restrict__ x, double *__restrict__ v, double *__restrict__ a,
+               const double *__restrict__ Xx, const uint8_t *__restrict__ fixm, double xc,
+               double scale, double eps, int affine, double *__restrict__ d_eps)
+{
+    const int64_t p = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (p == 0) *d_eps = eps;
+    if (p >= n) return;
+    double xp = x[p];
+    if (affine) xp = ad(xc, ml(sb(xp, xc), scale));
+    if (fixm[p] & 1u) {
+        const double X = Xx[p];
+        xp = ad(X, ml(eps, sb(X, xc)));
+        v[p] = 0.0;
+        a[p] = 0.0;
+    }
+    x[p] = xp;
+}
+
+// Fold the per-block partials into one sample, in a fixed order.
+__global__ void __launch_bounds__(RED_THREADS)
+k_reduce(const double *__restrict__ ps, int64_t nbs, const double *__restrict__ pp, int64_t nbp,
+         const double *__restrict__ d_eps, const unsigned long long *__restrict__ nbroken,
+         long long *__restrict__ d_step, long long add_steps, double omega, double grip_area,
+         DeviceSample *__restrict__ dst, long long *__restrict__ counter, int64_t cap)
+{
+    __shared__ double sh[RED_THREADS / 32];
+    double acc[6];
+    for (int q = 0; q < 6; q++) acc[q] = 0.0;
+    for (int64_t b = threadIdx.x; b < nbs; b += RED_THREADS) {
+        acc[0] += ps[b];
+        acc[1] += ps[nbs + b];
+    }
+    for (int64_t b = threadIdx.x; b < nbp; b += RED_THREADS) {
+        acc[2] += pp[b];
+        acc[3] += pp[nbp + b];
+        acc[4] += pp[2 * nbp + b];
+        acc[5] = fmax(acc[5], pp[3 * nbp + b]);
+    }
+    const double W = block_sum(acc[0], sh);
+    const double U = block_sum(acc[1], sh);
+    const double MV = block_sum(acc[2], sh);
+    const double KE = block_sum(acc[3], sh);
+    const double R = block_sum(acc[4], sh);
+    const double RES = block_max(acc[5], sh);
+    if (threadIdx.x == 0) {
+        DeviceSample smp;
+        smp.eps = *d_eps;
+        smp.sigma_vir = (W - MV) / omega;
+        smp.sigma_grip = R / grip_area;
+        smp.pe = U;
+        smp.ke = KE;
+        smp.residual = RES;
+        smp.n_broken = (long long)*nbroken;
+        const long long stp = *d_step + add_steps;
+        *d_step = stp;
+        smp.step = stp;
+        if (counter) {
+            const long long k = *counter;
+            if (k < cap) dst[k] = smp;
+            *counter = k + 1;
+        } else {
+            dst[0] = smp;
+        }
+    }
+}
+
+// --------------------------------------------------------------- host side
+
+static inline unsigned grid_of(int64_t cnt) { return (unsigned)((cnt + TPB - 1) / TPB); }
+
+thread_local const char *g_fail_site = "";
+
+const char *last_fail_site() { return g_fail_site; }
+
+#define LSM_TRY(x)                                \
+    do {                                          \
+        cudaError_t e_ = (x);                     \
+        if (e_ != cudaSuccess) {                  \
+            g_fail_site = #x;                     \
+            return e_;                            \
+        }                                         \
+    } while (0)
+
+template <typename T>
+static cudaError_t dalloc(T **p, size_t count)
+{
+    return cudaMalloc((void **)p, (count ? count : 1) * sizeof(T));
+}
+
+void free_device(Ctx &c)
+{
+    for (auto &kv : c.graphs) cudaGraphExecDestroy(kv.second);
+    c.graphs.clear();
+    void *ptrs[] = {c.x, c.v, c.a, c.mass, c.Xx, c.fixm, c.grip, c.si, c.sj, c.stype, c.types,
+                    c.state, c.brk, c.row, c.inc, c.fs, c.part_s, c.part_p, c.d_step,
+                    c.d_first_break, c.d_nbroken, c.d_status, c.d_eps, c.d_nsamples, c.samples,
+                    c.scratch_sample};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    void *tptrs[] = {c.tx[0], c.tx[1], c.tvh[0], c.tvh[1], c.tvobs, c.tph, c.tmask, c.tbrk, c.tmass};
+    for (void *p : tptrs)
+        if (p) cudaFree(p);
+    c.tx[0] = c.tx[1] = c.tvh[0] = c.tvh[1] = c.tvobs = c.tmass = nullptr;
+    c.tph = c.tmask = nullptr;
+    c.tbrk = nullptr;
+    c.x = c.v = c.a = c.mass = c.Xx = nullptr;
+    c.fixm = c.grip = nullptr;
+    c.si = c.sj = nullptr;
+    c.stype = nullptr;
+    c.types = nullptr;
+    c.state = nullptr;
+    c.brk = nullptr;
+    c.row = nullptr;
+    c.inc = nullptr;
+    c.fs = c.part_s = c.part_p = nullptr;
+    c.d_step = nullptr;
+    c.d_first_break = c.d_nbroken = nullptr;
+    c.d_status = nullptr;
+    c.d_eps = nullptr;
+    c.d_nsamples = nullptr;
+    c.samples = c.scratch_sample = nullptr;
+}
+
+static cudaError_t upload_common(Ctx &c)
+{
+    LSM_TRY(dalloc(&c.d_step, 1));
+    LSM_TRY(dalloc(&c.d_first_break, 1));
+    LSM_TRY(dalloc(&c.d_nbroken, 1));
+    LSM_TRY(dalloc(&c.d_status, 1));
+    LSM_TRY(dalloc(&c.d_eps, 1));
+    LSM_TRY(dalloc(&c.d_nsamples, 1));
+    c.sample_cap = 1024;
+    LSM_TRY(dalloc(&c.samples, c.sample_cap));
+    LSM_TRY(dalloc(&c.scratch_sample, 1));
+    LSM_TRY(dalloc(&c.types, c.h.types.size()));
+    cudaStream_t st = c.stream;
+    LSM_TRY(cudaMemcpyAsync(c.types, c.h.types.data(), c.h.types.size() * sizeof(SpringType),
+                            cudaMemcpyHostToDevice, st));
+    LSM_TRY(cudaMemsetAsync(c.d_step, 0, sizeof(long long), st));
+    LSM_TRY(cudaMemsetAsync(c.d_first_break, 0xff, sizeof(unsigned long long), st));
+    LSM_TRY(cudaMemsetAsync(c.d_nbroken, 0, sizeof(unsigned long long), st));
+    LSM_TRY(cudaMemsetAsync(c.d_status, 0, sizeof(int), st));
+    LSM_TRY(cudaMemsetAsync(c.d_eps, 0, sizeof(double), st));
+    LSM_TRY(cudaMemsetAsync(c.d_nsamples, 0, sizeof(long long), st));
+    return cudaSuccess;
+}
+
+// Tile path: state on the 2D pixel grid, both ping-pong buffers at the
+// reference lattice, velocities zero, no spring broken.
+static cudaError_t upload_tile(Ctx &c)
+{
+    const HostNet &h = c.h;
+    const int64_t np = (int64_t)h.nx * h.ny;
+    c.tnp = np;
+    c.tile_nphase = h.nphase;
+    c.ntiles = tile_count(c);
+    std::vector<double> X(2 * np);
+    for (int64_t g = 0; g < np; g++) {
+        X[g] = (g % h.nx) * h.a;
+        X[np + g] = (g / h.nx) * h.a;
+    }
+    std::vector<double> mtab(h.nphase, 1.0);
+    for (int64_t p = 0; p < h.n; p++) mtab[h.phase[h.pix[p]] - 1] = h.mass[p];
+    for (int b = 0; b < 2; b++) {
+        LSM_TRY(dalloc(&c.tx[b], 2 * np));
+        LSM_TRY(dalloc(&c.tvh[b], 2 * np));
+    }
+    LSM_TRY(dalloc(&c.tvobs, 2 * np));
+    LSM_TRY(dalloc(&c.tph, np));
+    LSM_TRY(dalloc(&c.tmask, np));
+    LSM_TRY(dalloc(&c.tbrk, 4 * np));
+    LSM_TRY(dalloc(&c.tmass, h.nphase));
+    LSM_TRY(dalloc(&c.part_s, 2 * c.ntiles));
+    LSM_TRY(dalloc(&c.part_p, 4 * c.ntiles));
+    LSM_TRY(upload_common(c));
+    cudaStream_t st = c.stream;
+    for (int b = 0; b < 2; b++) {
+        LSM_TRY(cudaMemcpyAsync(c.tx[b], X.data(), 2 * np * sizeof(double), cudaMemcpyHostToDevice, st));
+        LSM_TRY(cudaMemsetAsync(c.tvh[b], 0, 2 * np * sizeof(double), st));
+    }
+    LSM_TRY(cudaMemsetAsync(c.tvobs, 0, 2 * np * sizeof(double), st));
+    LSM_TRY(cudaMemcpyAsync(c.tph, h.phase.data(), np, cudaMemcpyHostToDevice, st));
+    LSM_TRY(cudaMemsetAsync(c.tmask, 0, np, st));
+    LSM_TRY(cudaMemsetAsync(c.tbrk, 0xff, 4 * np * sizeof(long long), st));
+    LSM_TRY(cudaMemcpyAsync(c.tmass, mtab.data(), h.nphase * sizeof(double), cudaMemcpyHostToDevice, st));
+    c.tcur = 0;
+    LSM_TRY(cudaStreamSynchronize(st));
+    return cudaSuccess;
+}
+
+cudaError_t upload(Ctx &c)
+{
+    const HostNet &h = c.h;
+    c.dim = h.dim;
+    c.n = h.n;
+    c.m = h.m;
+    if (c.tile) return upload_tile(c);
+    const int64_t n = c.n, m = c.m, dn = (int64_t)h.dim * n;
+    c.nblk_s = (m + TPB - 1) / TPB;
+    c.nblk_p = (n + TPB - 1) / TPB;
+
+    // incidence CSR: each particle's springs by ascending spring index
+    std::vector<int64_t> row(n + 1, 0);
+    for (int64_t s = 0; s < m; s++) {
+        row[h.si[s] + 1]++;
+        row[h.sj[s] + 1]++;
+    }
+    for (int64_t p = 0; p < n; p++) row[p + 1] += row[p];
+    std::vector<uint32_t> inc(2 * m);
+    std::vector<int64_t> fill(row.begin(), row.end() - 1);
+    for (int64_t s = 0; s < m; s++) {
+        inc[fill[h.si[s]]++] = (uint32_t)(s << 1);
+        inc[fill[h.sj[s]]++] = (uint32_t)((s << 1) | 1);
+    }
+    std::vector<double> Xx(h.X.begin(), h.X.begin() + n);
+
+    LSM_TRY(dalloc(&c.x, dn));
+    LSM_TRY(dalloc(&c.v, dn));
+    LSM_TRY(dalloc(&c.a, dn));
+    LSM_TRY(dalloc(&c.mass, n));
+    LSM_TRY(dalloc(&c.Xx, n));
+    LSM_TRY(dalloc(&c.fixm, n));
+    LSM_TRY(dalloc(&c.grip, n));
+    LSM_TRY(dalloc(&c.si, m));
+    LSM_TRY(dalloc(&c.sj, m));
+    LSM_TRY(dalloc(&c.stype, m));
+    LSM_TRY(dalloc(&c.state, m));
+    LSM_TRY(dalloc(&c.brk, m));
+    LSM_TRY(dalloc(&c.row, n + 1));
+    LSM_TRY(dalloc(&c.inc, 2 * m));
+    LSM_TRY(dalloc(&c.fs, (size_t)h.dim * (m ? m : 1)));
+    LSM_TRY(dalloc(&c.part_s, 2 * (c.nblk_s > 0 ? c.nblk_s : 1)));
+    LSM_TRY(dalloc(&c.part_p, 4 * c.nblk_p));
+    LSM_TRY(upload_common(c));
+
+    cudaStream_t st = c.stream;
+    LSM_TRY(cudaMemcpyAsync(c.x, h.X.data(), dn * sizeof(double), cudaMemcpyHostToDevice, st));
+    LSM_TRY(cudaMemsetAsync(c.v, 0, dn * sizeof(double), st));
+    LSM_TRY(cudaMemsetAsync(c.a, 0, dn * sizeof(double), st));
+    LSM_TRY(cudaMemcpyAsync(c.mass, h.mass.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    LSM_TRY(cudaMemcpyAsync(c.Xx, Xx.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    LSM_TRY(cudaMemcpyAsync(c.fixm, h.fixm.data(), n, cudaMemcpyHostToDevice, st));
+    LSM_TRY(cudaMemcpyAsync(c.grip, h.grip.data(), n, cudaMemcpyHostToDevice, st));
+    if (m) {
+        LSM_TRY(cudaMemcpyAsync(c.si, h.si.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        LSM_TRY(cudaMemcpyAsync(c.sj, h.sj.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        LSM_TRY(cudaMemcpyAsync(c.stype, h.stype.data(), m * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
+        LSM_TRY(cudaMemcpyAsync(c.inc, inc.data(), 2 * m * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    }
+    LSM_TRY(cudaMemcpyAsync(c.row, row.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    LSM_TRY(cudaMemsetAsync(c.state, 0, m ? m : 1, st));
+    LSM_TRY(cudaMemsetAsync(c.brk, 0xff, (m ? m : 1) * sizeof(long long), st));
+    LSM_TRY(cudaMemsetAsync(c.fs, 0, (size_t)h.dim * (m ? m : 1) * sizeof(double), st));
+    // host vectors above must stay alive until the copies finish
+    LSM_TRY(cudaStreamSynchronize(st));
+    return cudaSuccess;
+}
+
+// Launch helpers --------------------------------------------------------------
+
+template <int DIM, bool BREAK, bool SAMPLE>
+static void springs(Ctx &c)
+{
+    if (c.m == 0) {
+        if (SAMPLE) cudaMemsetAsync(c.part_s, 0, 2 * sizeof(double), c.stream);
+        return;
+    }
+    const unsigned g = grid_of(c.m);
+#define LSM_SPR(P)                                                                              \
+    k_springs<DIM, P, BREAK, SAMPLE><<<g, TPB, 0, c.stream>>>(                                  \
+        c.m, c.n, c.si, c.sj, c.stype, c.types, c.state, c.brk, c.x, c.fs, c.d_step,           \
+        c.d_first_break, c.d_nbroken, c.part_s, c.nblk_s)
+    switch (c.h.precision) {
+    case LSM_PREC_FAST64: LSM_SPR(LSM_PREC_FAST64); break;
+    case LSM_PREC_F32: LSM_SPR(LSM_PREC_F32); break;
+    default: LSM_SPR(LSM_PREC_EXACT64); break;
+    }
+#undef LSM_SPR
+}
+
+template <int DIM, int MODE, bool SAMPLE>
+static void gather(Ctx &c)
+{
+    const double dt = c.h.dt, hdt = 0.5 * c.h.dt;
+    k_gather<DIM, MODE, SAMPLE><<<grid_of(c.n), TPB, 0, c.stream>>>(
+        c.n, c.m, c.row, c.inc, c.fs, c.x, c.v, c.a, c.mass, c.fixm, c.grip, dt, hdt,
+        c.h.damping, c.part_p, c.nblk_p, c.d_status, c.d_step);
+}
+
+static void reduce(Ctx &c, DeviceSample *dst, long long *counter, long long add_steps)
+{
+    const int64_t nbs = c.tile ? c.ntiles : (c.m ? c.nblk_s : 1);
+    const int64_t nbp = c.tile ? c.ntiles : c.nblk_p;
+    k_reduce<<<1, RED_THREADS, 0, c.stream>>>(c.part_s, nbs, c.part_p, nbp, c.d_eps, c.d_nbroken,
+                                              c.d_step, add_steps, c.h.omega, c.h.grip_area, dst,
+                                              counter, c.sample_cap);
+}
+
+template <int DIM>
+static void enqueue_steps(Ctx &c, int64_t nsteps, bool record)
+{
+    const double dt = c.h.dt, hdt = 0.5 * c.h.dt;
+    k_drift<DIM><<<grid_of(c.n), TPB, 0, c.stream>>>(c.n, c.x, c.v, c.a, c.fixm, dt, hdt);
+    for (int64_t t = 0; t < nsteps; t++) {
+        const bool last = t == nsteps - 1;
+        if (last) {
+            springs<DIM, true, true>(c);
+            gather<DIM, G_END, true>(c);
+        } else {
+            springs<DIM, true, false>(c);
+            gather<DIM, G_DRIFT, false>(c);
+        }
+    }
+    if (record)
+        reduce(c, c.samples, c.d_nsamples, 0);
+    else
+        reduce(c, c.scratch_sample, nullptr, 0);
+}
+
+static cudaError_t enqueue_tile_steps(Ctx &c, int64_t nsteps, bool record)
+{
+    cudaError_t e = tile_enqueue_steps(c, nsteps, c.tcur);
+    if (e != cudaSuccess) return e;
+    if (record)
+        reduce(c, c.samples, c.d_nsamples, nsteps);
+    else
+        reduce(c, c.scratch_sample, nullptr, nsteps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_steps(Ctx &c, int64_t nsteps, bool record)
+{
+    const int64_t key = nsteps * 4 + (record ? 2 : 0) + (c.tile ? c.tcur : 0);
+    auto it = c.graphs.find(key);
+    if (it == c.graphs.end()) {
+        cudaGraph_t g;
+        LSM_TRY(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ee = cudaSuccess;
+        if (c.tile)
+            ee = enqueue_tile_steps(c, nsteps, record);
+        else if (c.dim == 3)
+            enqueue_steps<3>(c, nsteps, record);
+        else
+            enqueue_steps<2>(c, nsteps, record);
+        cudaError_t e = cudaStreamEndCapture(c.stream, &g);
+        if (ee != cudaSuccess) {
+            if (e == cudaSuccess) cudaGraphDestroy(g);
+            return ee;
+        }
+        if (e != cudaSuccess) return e;
+        size_t nodes = 0;
+        cudaGraphGetNodes(g, nullptr, &nodes);
+        c.graph_nodes[key] = (int64_t)nodes;
+        cudaGraphExec_t ex;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return e;
+        it = c.graphs.emplace(key, ex).first;
+    }
+    LSM_TRY(cudaGraphLaunch(it->second, c.stream));
+    c.launches += c.graph_nodes[key];
+    if (c.tile) c.tcur ^= (int)(nsteps & 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_accel(Ctx &c)
+{
+    if (c.tile) return tile_init_accel(c);
+    if (c.dim == 3) {
+        springs<3, false, false>(c);
+        gather<3, G_INIT, false>(c);
+    } else {
+        springs<2, false, false>(c);
+        gather<2, G_INIT, false>(c);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_observe(Ctx &c, DeviceSample *dst)
+{
+    if (c.tile) {
+        cudaError_t e = tile_observe(c);
+        if (e != cudaSuccess) return e;
+        reduce(c, dst, nullptr, 0);
+        return cudaGetLastError();
+    }
+    if (c.dim == 3) {
+        springs<3, false, true>(c);
+        gather<3, G_OBSERVE, true>(c);
+    } else {
+        springs<2, false, true>(c);
+        gather<2, G_OBSERVE, true>(c);
+    }
+    reduce(c, dst, nullptr, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_strain(Ctx &c, double eps_old, double eps_new)
+{
+    if (c.tile) {
+        c.launches += 1;
+        return tile_apply_strain(c, eps_old, eps_new);
+    }
+    const double scale = (1.0 + eps_new) / (1.0 + eps_old);
+    k_apply_strain<<<grid_of(c.n), TPB, 0, c.stream>>>(c.n, c.x, c.v, c.a, c.Xx, c.fixm, c.h.xc,
+                                                       scale, eps_new, c.h.load_mode == 0,
+                                                       c.d_eps);
+    c.launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace lsm

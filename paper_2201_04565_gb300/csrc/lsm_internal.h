@@ -1,0 +1,148 @@
+// lsm_internal.h -- device data layout and internal entry points of liblsm.
+//
+// Layout in HBM (one context = one specimen):
+//   particles (n):   x[dim][n], v[dim][n], a[dim][n]   FP64, component-major
+//                    mass[n] FP64, fixm[n] u8 (bit c = component c prescribed),
+//                    grip[n] u8 (0 / 1 left / 2 right), Xx[n] FP64 reference x
+//   springs (m):     si[m], sj[m] int32 (si < sj, canonical order),
+//                    stype[m] u16 -> params table {k, r0, rc2, k*r0},
+//                    state[m] u8 (1 = broken), brk[m] int64 (step of break or -1)
+//   incidence CSR:   row[n+1] int64, inc[2m] u32 = (spring << 1) | side,
+//                    side 0: particle is the lower endpoint i, 1: upper j;
+//                    each row lists a particle's springs by ascending index
+//   spring forces:   fs[dim][m] FP64 force on the lower endpoint (force pass
+//                    output, gather input)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/lsm.h"
+
+namespace lsm {
+
+struct SpringType {
+    double k, r0, rc2, kr0;
+};
+
+// Reduction slots of one sample (partials are reduced in a fixed order).
+enum {
+    RED_W = 0,      // sum over intact springs of d_x * f_x (virial, Eq. 7)
+    RED_PE,         // potential energy, Eq. 1
+    RED_MVX2,       // sum m v_x^2
+    RED_KE,         // kinetic energy
+    RED_REACT,      // sum over right-grip particles of -F_x
+    RED_RES,        // max over free components of max(|F|, |v|)  (max, not sum)
+    RED_NSLOT
+};
+
+struct DeviceSample {  // mirrors lsm_sample
+    double eps, sigma_vir, sigma_grip, pe, ke, residual;
+    long long n_broken, step;
+};
+
+// Host-side description of a network before upload.
+struct HostNet {
+    int dim = 2;
+    int64_t n = 0, m = 0;
+    std::vector<double> X;       // dim*n
+    std::vector<double> mass;    // n
+    std::vector<uint8_t> fixm;   // n, bit c
+    std::vector<uint8_t> grip;   // n
+    std::vector<int32_t> si, sj;
+    std::vector<uint16_t> stype;
+    std::vector<SpringType> types;
+    double dt = 0.01, damping = 0.0, xc = 0.0, omega = 1.0, grip_area = 1.0;
+    int load_mode = 0;
+    int precision = LSM_PREC_EXACT64;
+    int grip_mode = 0;
+    double a = 1.0;
+    // image geometry (0 for network builds)
+    int nx = 0, ny = 0, nz = 0, nphase = 0;
+    std::vector<int64_t> pix;      // pixel of each particle (image builds)
+    std::vector<uint8_t> phase;    // nx*ny*nz phase image (image builds)
+};
+
+struct Ctx {
+    HostNet h;  // host copy of topology (kept for queries and rebuilds)
+    int dim = 2;
+    int64_t n = 0, m = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+
+    // device particle state
+    double *x = nullptr, *v = nullptr, *a = nullptr;
+    double *mass = nullptr, *Xx = nullptr;
+    uint8_t *fixm = nullptr, *grip = nullptr;
+    // device springs
+    int32_t *si = nullptr, *sj = nullptr;
+    uint16_t *stype = nullptr;
+    SpringType *types = nullptr;
+    uint8_t *state = nullptr;
+    long long *brk = nullptr;
+    int64_t *row = nullptr;
+    uint32_t *inc = nullptr;
+    double *fs = nullptr;
+    // reductions
+    double *part_s = nullptr;  // [2][nblk_s]   W, PE per spring block
+    double *part_p = nullptr;  // [4][nblk_p]   MVX2, KE, REACT, RES per particle block
+    int64_t nblk_s = 0, nblk_p = 0;
+    // device scalars: step counter, first break, broken count, status, eps,
+    // sample count
+    long long *d_step = nullptr;
+    unsigned long long *d_first_break = nullptr;
+    unsigned long long *d_nbroken = nullptr;
+    int *d_status = nullptr;
+    double *d_eps = nullptr;
+    long long *d_nsamples = nullptr;
+    DeviceSample *samples = nullptr;
+    int64_t sample_cap = 0;
+    int64_t nsamples = 0;  // host mirror
+    DeviceSample *scratch_sample = nullptr;
+
+    // 2D tile path (image lattices): state on the pixel grid, ping-pong
+    bool tile = false;
+    int tile_nphase = 0;
+    int64_t tnp = 0;                      // pixels
+    double *tx[2] = {nullptr, nullptr};   // [2][tnp] positions
+    double *tvh[2] = {nullptr, nullptr};  // [2][tnp] half-step velocities
+    double *tvobs = nullptr;              // [2][tnp] full-step velocities (queries)
+    uint8_t *tph = nullptr, *tmask = nullptr;
+    long long *tbrk = nullptr;            // [4][tnp]
+    double *tmass = nullptr;              // per phase
+    int tcur = 0;
+    int64_t ntiles = 0;
+
+    double eps = 0.0;  // host mirror of the applied strain
+    int64_t steps = 0; // host mirror of the step counter
+    int64_t launches = 0;  // kernels launched (graph nodes included)
+    std::map<int64_t, int64_t> graph_nodes;  // kernels per cached graph
+    std::map<int64_t, cudaGraphExec_t> graphs;
+};
+
+// build.cpp
+bool net_from_image(const lsm_desc &d, HostNet &out, std::string &err);
+bool net_from_desc(const lsm_net_desc &d, HostNet &out, std::string &err);
+
+// kernels.cu
+cudaError_t upload(Ctx &c);
+cudaError_t launch_init_accel(Ctx &c);
+cudaError_t launch_steps(Ctx &c, int64_t nsteps, bool record);
+cudaError_t launch_apply_strain(Ctx &c, double eps_old, double eps_new);
+cudaError_t launch_observe(Ctx &c, DeviceSample *dst);
+void free_device(Ctx &c);
+
+// tile2d.cu
+cudaError_t tile_enqueue_steps(Ctx &c, int64_t nsteps, int start_buf);
+cudaError_t tile_init_accel(Ctx &c);
+cudaError_t tile_observe(Ctx &c);
+cudaError_t tile_apply_strain(Ctx &c, double eps_old, double eps_new);
+int64_t tile_count(const Ctx &c);
+const char *last_fail_site();  // source text of the CUDA call that failed last
+
+}  // namespace lsm

@@ -1,0 +1,499 @@
+// tile2d.cu -- fused one-launch-per-time-step kernel for 2D image lattices.
+//
+// A CTA owns a TX x TY tile of pixels. Per time step it
+//   1. loads positions and half-step velocities of the tile plus a one-pixel
+//      halo into shared memory and drifts them, x(t+dt) = x + dt vh (Eq. 3);
+//   2. evaluates every spring that touches the tile once (Eq. 2, break test
+//      on the squared length), writing the force on the spring's lower
+//      endpoint into shared memory; springs that cross the tile edge are also
+//      evaluated by the neighbouring tile, with bit-identical results, so no
+//      cross-CTA communication is needed;
+//   3. gathers each owned particle's eight spring forces in a fixed order
+//      (the order of the canonical spring list: incoming springs by ascending
+//      source, then outgoing springs by ascending target), applies the viscous
+//      half-kick (Eqs. 4-5) and the next half-kick, and writes x(t+dt) and
+//      vh(t+3dt/2) to the other buffer of a ping-pong pair.
+// State lives on the pixel grid (void pixels carry no particle and are never
+// read). Springs of pixel p are the forward offsets sorted by raster distance:
+// slot 0 (+1,0), slot 1 (-1,+1), slot 2 (0,+1), slot 3 (+1,+1); their broken
+// flags are the low 4 bits of mask[p], written only by the tile owning p.
+//
+// Precision modes: EXACT64 performs the same correctly rounded operations in
+// the same order as the sequential FP64 definition (bit-identical state);
+// FAST64 uses fused multiply-add and a reciprocal square root; F32 forms the
+// spring vector in FP64 and evaluates the force in FP32 from the small
+// deviation from the lattice vector, gathering in FP32 and integrating in FP64.
+#include <cuda_runtime.h>
+
+#include "lsm_internal.h"
+
+namespace lsm {
+
+namespace {
+
+constexpr int TILE_THREADS = 256;
+
+__device__ __forceinline__ double ad(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sb(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double ml(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dv(double a, double b) { return __ddiv_rn(a, b); }
+
+__device__ __forceinline__ double bsum(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < TILE_THREADS / 32; q++) t += sh[q];
+    return t;
+}
+
+__device__ __forceinline__ double bmax(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < TILE_THREADS / 32; q++) t = fmax(t, sh[q]);
+    return t;
+}
+
+}  // namespace
+
+enum { T_STEP = 0, T_INIT = 1, T_OBSERVE = 2 };
+
+struct TileArgs {
+    int nx, ny, nphase;
+    int64_t np;
+    const double *x_in, *vh_in;
+    double *x_out, *vh_out, *v_obs;
+    const uint8_t *phase;
+    uint8_t *mask;
+    long long *brk;  // [4][np]
+    const SpringType *types;
+    const double *mass;  // per phase
+    double dt, hdt, gamma, a;
+    int grip_mode;
+    const long long *d_step;  // steps completed before this graph launch
+    int64_t t_off;            // index of this step within the launch
+    unsigned long long *first_break, *nbroken;
+    int *status;
+    double *part_s, *part_p;
+    int64_t ntiles;
+};
+
+template <int TX, int TY, int PREC, int MODE, bool SAMPLE>
+__global__ void __launch_bounds__(TILE_THREADS)
+k_tile2d(TileArgs A)
+{
+    constexpr int RX = TX + 2, RY = TY + 2;   // region = tile + 1-pixel halo
+    constexpr int SX = TX + 2, SY = TY + 1;   // spring sources: x0-1..x0+TX, y0-1..y0+TY-1
+    constexpr int NR = RX * RY, NS = SX * SY;
+    using FT = typename std::conditional<PREC == LSM_PREC_F32, float, double>::type;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *sx = (double *)smem_raw;               // [NR]
+    double *sy = sx + NR;                          // [NR]
+    FT *sf = (FT *)(sy + NR);                      // [2][4][NS]
+    int *snew = (int *)(sf + 8 * NS);              // [NS]
+    uint8_t *sph = (uint8_t *)(snew + NS);         // [NR]
+    uint8_t *smk = sph + NR;                       // [NR]
+    __shared__ double sred[TILE_THREADS / 32];
+    __shared__ SpringType stab[128];
+    __shared__ double smass[8];
+
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int64_t tile_id = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    const int nt = 2 * A.nphase * A.nphase;
+    for (int q = tid; q < nt; q += TILE_THREADS) stab[q] = A.types[q];
+    for (int q = tid; q < A.nphase; q += TILE_THREADS) smass[q] = A.mass[q];
+    const long long step_now = MODE == T_STEP ? *A.d_step + A.t_off : 0;
+
+    // 1. region load (+ drift)
+    for (int e = tid; e < NR; e += TILE_THREADS) {
+        const int gx = x0 - 1 + e % RX, gy = y0 - 1 + e / RX;
+        uint8_t ph = 0, mk = 0;
+        double px = 0.0, py = 0.0;
+        if (gx >= 0 && gx < A.nx && gy >= 0 && gy < A.ny) {
+            const int64_t g = (int64_t)gy * A.nx + gx;
+            ph = A.phase[g];
+            if (ph) {
+                mk = A.mask[g];
+                px = A.x_in[g];
+                py = A.x_in[A.np + g];
+                if (MODE == T_STEP) {
+                    const bool grip = gx == 0 || gx == A.nx - 1;
+                    if (!grip) {
+                        if constexpr (PREC == LSM_PREC_EXACT64) px = ad(px, ml(A.dt, A.vh_in[g]));
+                        else px = fma(A.dt, A.vh_in[g], px);
+                    }
+                    if (!(grip && A.grip_mode == 1)) {
+                        if constexpr (PREC == LSM_PREC_EXACT64) py = ad(py, ml(A.dt, A.vh_in[A.np + g]));
+                        else py = fma(A.dt, A.vh_in[A.np + g], py);
+                    }
+                }
+            }
+        }
+        sx[e] = px;
+        sy[e] = py;
+        sph[e] = ph;
+        smk[e] = mk;
+    }
+    for (int e = tid; e < NS; e += TILE_THREADS) snew[e] = 0;
+    __syncthreads();
+
+    // 2. springs touching the tile
+    double w_acc = 0.0, u_acc = 0.0;
+    for (int e = tid; e < 4 * NS; e += TILE_THREADS) {
+        const int slot = e / NS, si_ = e % NS;
+        const int rx = si_ % SX, ry = si_ / SX;
+        const int dx = slot == 0 ? 1 : (slot == 1 ? -1 : (slot == 2 ? 0 : 1));
+        const int dy = slot == 0 ? 0 : 1;
+        const int qx = rx + dx, qy = ry + dy;
+        FT fx = 0, fy = 0;
+        const bool p_in = rx >= 1 && rx <= TX && ry >= 1 && ry <= TY;
+        const bool q_in = qx >= 1 && qx <= TX && qy >= 1 && qy <= TY;
+        if ((p_in || q_in) && qx >= 0 && qx < RX) {
+            const int rp = ry * RX + rx, rq = qy * RX + qx;
+            const uint8_t pp = sph[rp], pq = sph[rq];
+            if (pp && pq && !((smk[rp] >> slot) & 1)) {
+                const SpringType t = stab[(((pp - 1) * A.nphase) + (pq - 1)) * 2 + (slot & 1)];
+                double ddx, ddy;
+                if constexpr (PREC == LSM_PREC_EXACT64) {
+                    ddx = sb(sx[rq], sx[rp]);
+                    ddy = sb(sy[rq], sy[rp]);
+                } else {
+                    ddx = sx[rq] - sx[rp];
+                    ddy = sy[rq] - sy[rp];
+                }
+                bool brk_now = false;
+                if constexpr (PREC == LSM_PREC_EXACT64) {
+                    const double r2 = ad(ml(ddx, ddx), ml(ddy, ddy));
+                    if (MODE == T_STEP && r2 > t.rc2) {
+                        brk_now = true;
+                    } else {
+                        const double r = __dsqrt_rn(r2);
+                        const double c = dv(ml(t.k, sb(r, t.r0)), r);
+                        fx = ml(c, ddx);
+                        fy = ml(c, ddy);
+                        if (SAMPLE && p_in) {
+                            const double st = sb(r, t.r0);
+                            u_acc += ml(ml(ml(0.5, t.k), st), st);
+                            w_acc += ml(ddx, ml(c, ddx));
+                        }
+                    }
+                } else if constexpr (PREC == LSM_PREC_FAST64) {
+                    const double r2 = fma(ddx, ddx, ddy * ddy);
+                    if (MODE == T_STEP && r2 > t.rc2) {
+                        brk_now = true;
+                    } else {
+                        const double ir = rsqrt(r2);
+                        const double c = fma(-t.kr0, ir, t.k);
+                        fx = c * ddx;
+                        fy = c * ddy;
+                        if (SAMPLE && p_in) {
+                            const double st = fma(r2, ir, -t.r0);
+                            u_acc += 0.5 * t.k * st * st;
+                            w_acc += ddx * fx;
+                        }
+                    }
+                } else {  // F32 force from the deviation from the lattice vector
+                    const double ox = dx * A.a, oy = dy * A.a;
+                    const float ex = (float)(ddx - ox), ey = (float)(ddy - oy);
+                    const float fox = (float)ox, foy = (float)oy;
+                    const float dxf = fox + ex, dyf = foy + ey;
+                    const float r2f = fmaf(dxf, dxf, dyf * dyf);
+                    if (MODE == T_STEP && r2f > (float)t.rc2) {
+                        brk_now = true;
+                    } else {
+                        const float r0f = (float)t.r0;
+                        const float rf = sqrtf(r2f);
+                        // r - r0 = (2 o.e + e.e) / (r + r0), without cancellation
+                        const float num = fmaf(2.0f * fox + ex, ex, (2.0f * foy + ey) * ey);
+                        const float st = num / (rf + r0f);
+                        const float c = (float)t.k * st / rf;
+                        fx = c * dxf;
+                        fy = c * dyf;
+                        if (SAMPLE && p_in) {
+                            u_acc += 0.5 * t.k * (double)st * (double)st;
+                            w_acc += ddx * (double)fx;
+                        }
+                    }
+                }
+                if (brk_now && p_in) {  // the tile owning the lower endpoint records it
+                    atomicOr(&snew[si_], 1 << slot);
+                    const int64_t g = (int64_t)(y0 - 1 + ry) * A.nx + (x0 - 1 + rx);
+                    A.brk[(int64_t)slot * A.np + g] = step_now;
+                    atomicMin(A.first_break, (unsigned long long)step_now);
+                    atomicAdd(A.nbroken, 1ull);
+                }
+            }
+        }
+        sf[(0 * 4 + slot) * NS + si_] = fx;
+        sf[(1 * 4 + slot) * NS + si_] = fy;
+    }
+    __syncthreads();
+
+    // 3. gather + integrate the owned particles
+    double mvx2 = 0.0, ke = 0.0, react = 0.0, res = 0.0;
+    bool bad = false;
+    for (int e = tid; e < TX * TY; e += TILE_THREADS) {
+        const int lx = e % TX, ly = e / TX;
+        const int gx = x0 + lx, gy = y0 + ly;
+        const int rx = lx + 1, ry = ly + 1;
+        const int rp = ry * RX + rx;
+        if (gx >= A.nx || gy >= A.ny || !sph[rp]) continue;
+        const int64_t g = (int64_t)gy * A.nx + gx;
+        const int sp = ry * SX + rx;
+        // incoming: sources p - o for slots 3, 2, 1, 0 (ascending source index)
+        const int s3 = (ry - 1) * SX + (rx - 1), s2 = (ry - 1) * SX + rx, s1 = (ry - 1) * SX + (rx + 1),
+                  s0 = ry * SX + (rx - 1);
+        FT Fx, Fy;
+        if constexpr (PREC == LSM_PREC_EXACT64) {
+            Fx = 0.0;
+            Fy = 0.0;
+            Fx = sb(Fx, sf[(0 * 4 + 3) * NS + s3]); Fy = sb(Fy, sf[(1 * 4 + 3) * NS + s3]);
+            Fx = sb(Fx, sf[(0 * 4 + 2) * NS + s2]); Fy = sb(Fy, sf[(1 * 4 + 2) * NS + s2]);
+            Fx = sb(Fx, sf[(0 * 4 + 1) * NS + s1]); Fy = sb(Fy, sf[(1 * 4 + 1) * NS + s1]);
+            Fx = sb(Fx, sf[(0 * 4 + 0) * NS + s0]); Fy = sb(Fy, sf[(1 * 4 + 0) * NS + s0]);
+#pragma unroll
+            for (int sl = 0; sl < 4; sl++) {
+                Fx = ad(Fx, sf[(0 * 4 + sl) * NS + sp]);
+                Fy = ad(Fy, sf[(1 * 4 + sl) * NS + sp]);
+            }
+        } else {
+            Fx = sf[(0 * 4 + 0) * NS + sp] - sf[(0 * 4 + 3) * NS + s3];
+            Fy = sf[(1 * 4 + 0) * NS + sp] - sf[(1 * 4 + 3) * NS + s3];
+            Fx += sf[(0 * 4 + 1) * NS + sp] - sf[(0 * 4 + 2) * NS + s2];
+            Fy += sf[(1 * 4 + 1) * NS + sp] - sf[(1 * 4 + 2) * NS + s2];
+            Fx += sf[(0 * 4 + 2) * NS + sp] - sf[(0 * 4 + 1) * NS + s1];
+            Fy += sf[(1 * 4 + 2) * NS + sp] - sf[(1 * 4 + 1) * NS + s1];
+            Fx += sf[(0 * 4 + 3) * NS + sp] - sf[(0 * 4 + 0) * NS + s0];
+            Fy += sf[(1 * 4 + 3) * NS + sp] - sf[(1 * 4 + 0) * NS + s0];
+        }
+        const bool grip = gx == 0 || gx == A.nx - 1;
+        const bool fixx = grip, fixy = grip && A.grip_mode == 1;
+        const double m = smass[sph[rp] - 1];
+        const double F[2] = {(double)Fx, (double)Fy};
+        const double xr[2] = {sx[rp], sy[rp]};
+        if (SAMPLE && gx == A.nx - 1) {
+            if constexpr (PREC == LSM_PREC_EXACT64) react = sb(react, F[0]);
+            else react -= F[0];
+        }
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            const bool fixed = c == 0 ? fixx : fixy;
+            const int64_t q = c * A.np + g;
+            if (MODE == T_STEP) A.x_out[q] = xr[c];
+            if (fixed) {
+                if (MODE == T_STEP) A.vh_out[q] = 0.0;
+                if (MODE == T_STEP && SAMPLE) A.v_obs[q] = 0.0;
+                continue;
+            }
+            if (MODE == T_OBSERVE) {
+                const double vn = A.v_obs[q];
+                if (SAMPLE) {
+                    res = fmax(res, fmax(fabs(F[c]), fabs(vn)));
+                    ke += 0.5 * m * vn * vn;
+                    if (c == 0) mvx2 += m * vn * vn;
+                }
+                continue;
+            }
+            const double vh = MODE == T_INIT ? A.v_obs[q] : A.vh_in[q];
+            double acc, vn, vh2;
+            if constexpr (PREC == LSM_PREC_EXACT64) {
+                acc = dv(sb(F[c], ml(A.gamma, vh)), m);
+                vn = ad(vh, ml(A.hdt, acc));
+                vh2 = ad(vn, ml(A.hdt, acc));
+            } else {
+                const double im = 1.0 / m;
+                acc = fma(-A.gamma * im, vh, F[c] * im);
+                vn = fma(A.hdt, acc, vh);
+                vh2 = fma(A.dt, acc, vh);
+            }
+            if (MODE == T_INIT) {
+                // vh = v + dt/2 a(t) with a from the forces at the current x
+                A.vh_out[q] = vn;
+                continue;
+            }
+            A.vh_out[q] = vh2;
+            if (SAMPLE) {
+                A.v_obs[q] = vn;
+                res = fmax(res, fmax(fabs(F[c]), fabs(vn)));
+                ke += 0.5 * m * vn * vn;
+                if (c == 0) mvx2 += m * vn * vn;
+                bad |= !isfinite(vn) || !isfinite(xr[c]);
+            }
+        }
+        if (MODE == T_STEP) {
+            const int nb = snew[sp];
+            if (nb) A.mask[g] = (uint8_t)(smk[rp] | nb);
+        }
+    }
+    if (SAMPLE) {
+        if (bad) atomicOr(A.status, 1);
+        const double t0 = bsum(w_acc, sred);
+        const double t1 = bsum(u_acc, sred);
+        const double t2 = bsum(mvx2, sred);
+        const double t3 = bsum(ke, sred);
+        const double t4 = bsum(react, sred);
+        const double t5 = bmax(res, sred);
+        if (tid == 0) {
+            A.part_s[tile_id] = t0;
+            A.part_s[A.ntiles + tile_id] = t1;
+            A.part_p[tile_id] = t2;
+            A.part_p[A.ntiles + tile_id] = t3;
+            A.part_p[2 * A.ntiles + tile_id] = t4;
+            A.part_p[3 * A.ntiles + tile_id] = t5;
+        }
+    }
+}
+
+// Load increment on the pixel grid (Sections 2.3, 3.1).
+__global__ void k_tile_strain(int nx, int ny, int64_t np, double *x, double *vh, double *v_obs,
+                              const uint8_t *phase, double a, double xc, double scale, double eps,
+                              int affine, double *d_eps)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g == 0) *d_eps = eps;
+    if (g >= np || !phase[g]) return;
+    const int gx = (int)(g % nx);
+    double xp = x[g];
+    if (affine) xp = ad(xc, ml(sb(xp, xc), scale));
+    if (gx == 0 || gx == nx - 1) {
+        const double X = gx * a;
+        xp = ad(X, ml(eps, sb(X, xc)));
+        vh[g] = 0.0;
+        v_obs[g] = 0.0;
+    }
+    x[g] = xp;
+}
+
+// ------------------------------------------------------------------ host
+
+template <int TX, int TY>
+static constexpr size_t tile_smem(int prec)
+{
+    constexpr int RX = TX + 2, RY = TY + 2, SX = TX + 2, SY = TY + 1;
+    return (size_t)2 * RX * RY * sizeof(double) +
+           (size_t)8 * SX * SY * (prec == LSM_PREC_F32 ? sizeof(float) : sizeof(double)) +
+           (size_t)SX * SY * sizeof(int) + (size_t)2 * RX * RY + 16;
+}
+
+constexpr int TILE_X = 32, TILE_Y = 16;
+
+static TileArgs tile_args(Ctx &c)
+{
+    TileArgs A;
+    A.nx = c.h.nx;
+    A.ny = c.h.ny;
+    A.nphase = c.tile_nphase;
+    A.np = c.tnp;
+    A.x_in = c.tx[c.tcur];
+    A.vh_in = c.tvh[c.tcur];
+    A.x_out = c.tx[c.tcur ^ 1];
+    A.vh_out = c.tvh[c.tcur ^ 1];
+    A.v_obs = c.tvobs;
+    A.phase = c.tph;
+    A.mask = c.tmask;
+    A.brk = c.tbrk;
+    A.types = c.types;
+    A.mass = c.tmass;
+    A.dt = c.h.dt;
+    A.hdt = 0.5 * c.h.dt;
+    A.gamma = c.h.damping;
+    A.a = c.h.a;
+    A.grip_mode = c.h.grip_mode;
+    A.d_step = c.d_step;
+    A.t_off = 0;
+    A.first_break = c.d_first_break;
+    A.nbroken = c.d_nbroken;
+    A.status = c.d_status;
+    A.part_s = c.part_s;
+    A.part_p = c.part_p;
+    A.ntiles = c.ntiles;
+    return A;
+}
+
+template <int PREC, int MODE, bool SAMPLE>
+static cudaError_t launch_tile(Ctx &c, TileArgs A)
+{
+    auto kern = k_tile2d<TILE_X, TILE_Y, PREC, MODE, SAMPLE>;
+    const size_t smem = tile_smem<TILE_X, TILE_Y>(PREC);
+    static bool configured = false;  // per template instance
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((c.h.nx + TILE_X - 1) / TILE_X, (c.h.ny + TILE_Y - 1) / TILE_Y);
+    kern<<<grid, TILE_THREADS, smem, c.stream>>>(A);
+    return cudaSuccess;
+}
+
+template <int MODE, bool SAMPLE>
+static cudaError_t launch_tile_prec(Ctx &c, TileArgs A)
+{
+    switch (c.h.precision) {
+    case LSM_PREC_FAST64: return launch_tile<LSM_PREC_FAST64, MODE, SAMPLE>(c, A);
+    case LSM_PREC_F32: return launch_tile<LSM_PREC_F32, MODE, SAMPLE>(c, A);
+    default: return launch_tile<LSM_PREC_EXACT64, MODE, SAMPLE>(c, A);
+    }
+}
+
+cudaError_t tile_enqueue_steps(Ctx &c, int64_t nsteps, int start_buf)
+{
+    int cur = start_buf;
+    for (int64_t t = 0; t < nsteps; t++) {
+        TileArgs A = tile_args(c);
+        A.t_off = t;
+        A.x_in = c.tx[cur];
+        A.vh_in = c.tvh[cur];
+        A.x_out = c.tx[cur ^ 1];
+        A.vh_out = c.tvh[cur ^ 1];
+        cudaError_t e = t == nsteps - 1 ? launch_tile_prec<T_STEP, true>(c, A)
+                                        : launch_tile_prec<T_STEP, false>(c, A);
+        if (e != cudaSuccess) return e;
+        cur ^= 1;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t tile_init_accel(Ctx &c)
+{
+    TileArgs A = tile_args(c);
+    A.vh_out = c.tvh[c.tcur];  // vh = v + dt/2 a, written in place of the current buffer
+    cudaError_t e = launch_tile_prec<T_INIT, false>(c, A);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t tile_observe(Ctx &c)
+{
+    TileArgs A = tile_args(c);
+    cudaError_t e = launch_tile_prec<T_OBSERVE, true>(c, A);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t tile_apply_strain(Ctx &c, double eps_old, double eps_new)
+{
+    const double scale = (1.0 + eps_new) / (1.0 + eps_old);
+    const unsigned g = (unsigned)((c.tnp + 255) / 256);
+    k_tile_strain<<<g, 256, 0, c.stream>>>(c.h.nx, c.h.ny, c.tnp, c.tx[c.tcur], c.tvh[c.tcur], c.tvobs,
+                                           c.tph, c.h.a, c.h.xc, scale, eps_new, c.h.load_mode == 0,
+                                           c.d_eps);
+    return cudaGetLastError();
+}
+
+int64_t tile_count(const Ctx &c)
+{
+    return (int64_t)((c.h.nx + TILE_X - 1) / TILE_X) * ((c.h.ny + TILE_Y - 1) / TILE_Y);
+}
+
+}  // namespace lsm

@@ -1,0 +1,261 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Bars (floating point; derived in the design notes):
+  - exact64 mode: positions, velocities, broken set and break steps
+    bit-identical to the oracle (same IEEE operations in the same order);
+    sample observables within 1e-12 relative (only the reduction order
+    differs);
+  - fast64 mode: positions within 1e-10 relative (normwise) after 1000+
+    steps, identical broken set and first-break step, stress-strain within
+    1e-6 relative before the first break;
+  - f32 force mode: error against the oracle reported, bounded loosely.
+"""
+import numpy as np
+import pytest
+
+from gen.images import inclusion_image, one_phase_materials, two_phase_materials
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_04565_gb300 import build, lsm
+    build.build()
+    lsm.load_library()
+    return lsm
+
+
+def _pair(oracle_mod, L, img, mats, precision="exact64", path=0, **kw):
+    k, e, m = mats
+    o = oracle_mod.Oracle.from_image(img, k, e, m, **kw)
+    g = L.Specimen.from_image(img, k, e, m, precision=precision, path=path, **kw)
+    assert (g.n, g.m, g.dim) == (o.n, o.m, o.dim)
+    return o, g
+
+
+def _run_schedule(o, g, incs, steps, eps_inc):
+    samples_o = []
+    for i in range(1, incs + 1):
+        o.apply_strain(i * eps_inc)
+        g.apply_strain(i * eps_inc)
+        o.step(steps)
+        g.step(steps)
+        samples_o.append(o.observe())
+    return samples_o
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def test_topology_matches_oracle(oracle_mod, L):
+    rng = np.random.default_rng(5)
+    for shape in [(9, 13), (5, 6, 7)]:
+        img = rng.integers(0, 3, size=shape).astype(np.uint8)
+        o, g = _pair(oracle_mod, L, img, two_phase_materials())
+        to, tg = o.topology(), g.topology()
+        for key in ("si", "sj", "k", "r0", "rc2"):
+            assert np.array_equal(to[key], tg[key]), key
+
+
+def test_paper_oscillator_on_gpu(oracle_mod, L):
+    """Section 3.1 two-particle oscillator, exact64: bit-identical to the
+    oracle, and on the exact discrete cosine."""
+    X = np.array([[0.0, 15.0], [0.0, 0.0]])
+    fix = np.array([[1, 0], [1, 0]], np.uint8)
+    args = ([0], [1], [1e-4], [10.0], [np.inf])
+    o = oracle_mod.Oracle.from_network(X, *args, fix=fix, dt=1.0, damping=0.0)
+    g = L.Specimen.from_network(X, *args, fix=fix, dt=1.0, damping=0.0)
+    theta = np.arccos(1.0 - 0.5 * 1e-4)
+    for n in range(10, 1001, 10):
+        o.step(10)
+        g.step(10)
+        xg, vg = g.state()
+        xo, vo, _ = o.state()
+        assert np.array_equal(xg, xo) and np.array_equal(vg, vo)
+        assert abs(xg[0, 1] - 10.0 - 5.0 * np.cos(n * theta)) <= 5e-12
+
+
+PATHS = [0, 1]  # 0: fused 2D tile kernel, 1: spring-list kernels
+
+
+def test_path_selection_by_launch_count(L):
+    img = inclusion_image(40, 24, 2.0, 4.0, 0.3, 2)
+    k, e, m = two_phase_materials()
+    launches = {}
+    for path in PATHS:
+        g = L.Specimen.from_image(img, k, e, m, path=path)
+        base = g.counters()[2]
+        g.step(20)
+        launches[path] = g.counters()[2] - base
+    assert launches[0] == 20 + 1      # one fused kernel per step + the sample reduction
+    assert launches[1] == 1 + 40 + 1  # drift, two kernels per step, reduction
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_c0_exact64_bit_identical(oracle_mod, L, path):
+    """2D 64x64 two-phase composite, tension to 10% in 100 increments of 20
+    damped steps (dt 0.01, gamma 0.1): the whole run, breaks included."""
+    img = inclusion_image(64, 64, 3.0, 8.0, 0.30, 0)
+    o, g = _pair(oracle_mod, L, img, two_phase_materials(), path=path, dt=0.01, damping=0.1)
+    so = _run_schedule(o, g, 100, 20, 1e-3)
+    xg, vg = g.state()
+    xo, vo, _ = o.state()
+    assert np.array_equal(xg, xo)
+    assert np.array_equal(vg, vo)
+    mo, bo, fo = o.broken()
+    mg, fg = g.broken()
+    assert fo >= 0, "the schedule must reach fracture"
+    assert np.array_equal(mg, mo) and fg == fo
+    assert np.array_equal(g.break_steps(), bo)
+    sg = g.samples()
+    assert len(sg) == len(so) == 100
+    for a, b in zip(sg, so):
+        assert a["eps"] == b["eps"] and a["n_broken"] == b["n_broken"] and a["step"] == b["step"]
+        for key in ("sigma_vir", "sigma_grip", "pe", "ke"):
+            assert a[key] == pytest.approx(b[key], rel=1e-12, abs=1e-300), key
+        assert a["residual"] == b["residual"]
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_c0_fast64_within_tolerance(oracle_mod, L, path):
+    img = inclusion_image(64, 64, 3.0, 8.0, 0.30, 0)
+    o, g = _pair(oracle_mod, L, img, two_phase_materials(), precision="fast64", path=path)
+    so = _run_schedule(o, g, 50, 20, 1e-3)  # 1000 steps
+    xg, _ = g.state()
+    xo, _, _ = o.state()
+    assert _rel(xg, xo) <= 1e-10
+    mo, _, fo = o.broken()
+    mg, fg = g.broken()
+    assert np.array_equal(mg, mo) and fg == fo
+    sg = g.samples()
+    first = next((i for i, s in enumerate(so) if s["n_broken"] > 0), len(so))
+    for a, b in zip(sg[:first], so[:first]):
+        assert a["sigma_vir"] == pytest.approx(b["sigma_vir"], rel=1e-6)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_c0_f32_force_error_is_bounded(oracle_mod, L, path):
+    img = inclusion_image(64, 64, 3.0, 8.0, 0.30, 0)
+    o, g = _pair(oracle_mod, L, img, two_phase_materials(), precision="f32", path=path)
+    so = _run_schedule(o, g, 20, 20, 1e-3)  # 400 steps, before fracture
+    xg, _ = g.state()
+    xo, _, _ = o.state()
+    X = o.topology()["X"]
+    rel_u = np.abs(xg - xo).max() / np.abs(xo - X).max()
+    assert rel_u < 1e-3  # displacement error of single-precision forces
+    sg = g.samples()
+    assert sg[-1]["sigma_vir"] == pytest.approx(so[-1]["sigma_vir"], rel=1e-3)
+
+
+@pytest.mark.parametrize("precision", ["exact64", "fast64"])
+def test_3d_foam_parity(oracle_mod, L, precision):
+    from gen.images import foam_volume
+    img = foam_volume(20, 2.0, 0.45, seed=9)
+    mats = one_phase_materials(1.0, 0.04)
+    o, g = _pair(oracle_mod, L, img, mats, precision=precision, grip_mode=1)
+    _run_schedule(o, g, 10, 20, -2e-3)
+    xg, vg = g.state()
+    xo, vo, _ = o.state()
+    if precision == "exact64":
+        assert np.array_equal(xg, xo) and np.array_equal(vg, vo)
+    else:
+        assert _rel(xg, xo) <= 1e-10
+    assert np.array_equal(g.broken()[0], o.broken()[0])
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_ragged_and_degenerate_sizes(oracle_mod, L, path):
+    k, e, m = two_phase_materials()
+    rng = np.random.default_rng(1)
+    cases = [np.ones((1, 2), np.uint8),                     # one spring, both grips
+             rng.integers(0, 3, size=(17, 33)).astype(np.uint8),  # voids, ragged tail
+             np.ones((3, 257), np.uint8)]                   # n just above a block
+    for img in cases:
+        if img.sum() == 0:
+            continue
+        o, g = _pair(oracle_mod, L, img, (k, e, m), path=path)
+        _run_schedule(o, g, 3, 7, 0.02)
+        assert np.array_equal(g.state()[0], o.state()[0])
+        assert np.array_equal(g.state()[1], o.state()[1])
+        assert np.array_equal(g.broken()[0], o.broken()[0])
+    # network without springs: a free particle at rest stays put
+    X = np.array([[0.0, 1.0], [0.0, 0.0]])
+    g = L.Specimen.from_network(X, [], [], [], [], [])
+    g.step(5)
+    assert np.array_equal(g.state()[0], X)
+    assert g.samples()[0]["pe"] == 0.0
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_relax_matches_oracle(oracle_mod, L, path):
+    img = inclusion_image(24, 24, 2.0, 4.0, 0.3, 3)
+    o, g = _pair(oracle_mod, L, img, two_phase_materials(), path=path, dt=0.2, damping=0.3)
+    o.apply_strain(0.01)
+    g.apply_strain(0.01)
+    st_o, to = o.relax(1e-9, 50000, 25)
+    st_g, tg = g.relax(1e-9, 50000, 25)
+    assert st_o == st_g == 0 and to == tg
+    assert np.array_equal(g.state()[0], o.state()[0])
+    ob = o.observe()
+    sg = g.samples()[-1]
+    assert sg["sigma_grip"] == pytest.approx(ob["sigma_grip"], rel=1e-12)
+    # not converged within the cap -> LSM_ENOTCONV, state still consistent
+    st, taken = g.relax(0.0, 10, 5)
+    assert st == L.LSM_ENOTCONV and taken == 10
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_deterministic_repeat(L, path):
+    img = inclusion_image(64, 64, 3.0, 8.0, 0.30, 0)
+    k, e, m = two_phase_materials()
+    outs = []
+    for _ in range(2):
+        g = L.Specimen.from_image(img, k, e, m, precision="fast64", path=path)
+        for i in range(1, 61):
+            g.apply_strain(i * 1e-3)
+            g.step(20)
+        outs.append((g.state()[0], g.broken()[0], g.samples()))
+        g.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert outs[0][2] == outs[1][2]
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_observe_and_set_state(oracle_mod, L, path):
+    img = inclusion_image(16, 16, 2.0, 4.0, 0.3, 4)
+    o, g = _pair(oracle_mod, L, img, two_phase_materials(), path=path)
+    rng = np.random.default_rng(0)
+    x, v, _ = o.state()
+    fixm = o.topology()["fix"]
+    x2 = x + 0.01 * rng.standard_normal(x.shape) * (1 - fixm)
+    v2 = 0.01 * rng.standard_normal(x.shape) * (1 - fixm)
+    o.set_state(x=x2, v=v2)
+    g.set_state(x2, v2)
+    ob, gb = o.observe(), g.observe()
+    for key in ("sigma_vir", "sigma_grip", "pe", "ke", "residual"):
+        assert gb[key] == pytest.approx(ob[key], rel=1e-12), key
+    o.step(30)
+    g.step(30)
+    assert np.array_equal(g.state()[0], o.state()[0])
+
+
+def test_tile_and_spring_list_paths_agree_bitwise(L):
+    """fast64 on both paths: the fused tile kernel and the spring-list kernels
+    sum each particle's springs in the same order, so their states agree."""
+    img = inclusion_image(96, 80, 3.0, 8.0, 0.30, 6)
+    k, e, m = two_phase_materials()
+    outs = []
+    for path in PATHS:
+        g = L.Specimen.from_image(img, k, e, m, precision="exact64", path=path)
+        for i in range(1, 41):
+            g.apply_strain(i * 2e-3)
+            g.step(10)
+        outs.append((g.state(), g.broken()))
+    assert np.array_equal(outs[0][0][0], outs[1][0][0])
+    assert np.array_equal(outs[0][1][0], outs[1][1][0])
