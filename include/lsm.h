@@ -61,10 +61,15 @@ typedef enum {
  *  LSM_PREC_FAST64: double precision throughout, reassociated (fused
  *      multiply-add, 1/r from a reciprocal square root); results agree with
  *      the exact mode to a few ulps per step.
- *  LSM_PREC_F32: spring vector formed in double, spring force evaluated in
- *      single precision, forces gathered and positions/velocities integrated
- *      in double. */
-enum { LSM_PREC_EXACT64 = 0, LSM_PREC_FAST64 = 1, LSM_PREC_F32 = 2 };
+ *  LSM_PREC_F32: spring vector formed exactly (positions in 64-bit fixed
+ *      point), spring force evaluated and gathered in single precision,
+ *      positions and velocities integrated in double.
+ *  LSM_PREC_DF: as LSM_PREC_F32, but the spring force and the gather use
+ *      double-float arithmetic (pairs of floats, 48 significant bits), so
+ *      forces carry about 1e-14 relative error while the FP64 pipe only does
+ *      the integration. DF and F32 run on the fused 2D tile kernel; elsewhere
+ *      they fall back to LSM_PREC_FAST64 arithmetic on the spring-list path. */
+enum { LSM_PREC_EXACT64 = 0, LSM_PREC_FAST64 = 1, LSM_PREC_F32 = 2, LSM_PREC_DF = 3 };
 
 /* Image build descriptor (the paper's Img2Particle stage, Section 1 and
  * Fig. 6, on a square/cubic lattice with first and second neighbours).

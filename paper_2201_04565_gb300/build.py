@@ -17,7 +17,7 @@ LIB = os.path.join(HERE, "liblsm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 SOURCES = ["kernels.cu", "batch.cu", "tile2d.cu", "nn.cu", "build.cpp", "api.cpp"]
-HEADERS = ["lsm_internal.h", "nn_internal.h"]
+HEADERS = ["lsm_internal.h", "dfloat.cuh", "nn_internal.h"]
 
 
 def _nvcc():

@@ -118,8 +118,8 @@ lsm_status lsm_build_from_image(const lsm_desc *desc, lsm_ctx **out)
 {
     if (!desc || !out) return fail(nullptr, LSM_EINVAL, "desc and out are required");
     *out = nullptr;
-    if (desc->precision < LSM_PREC_EXACT64 || desc->precision > LSM_PREC_F32)
-        return fail(nullptr, LSM_EINVAL, "precision must be LSM_PREC_EXACT64, _FAST64 or _F32");
+    if (desc->precision < LSM_PREC_EXACT64 || desc->precision > LSM_PREC_DF)
+        return fail(nullptr, LSM_EINVAL, "precision must be LSM_PREC_EXACT64, _FAST64, _F32 or _DF");
     lsm_ctx *c = new (std::nothrow) lsm_ctx();
     if (!c) return fail(nullptr, LSM_ENOMEM, "host allocation failed");
     std::string err;
@@ -145,8 +145,8 @@ lsm_status lsm_build_network(const lsm_net_desc *desc, lsm_ctx **out)
 {
     if (!desc || !out) return fail(nullptr, LSM_EINVAL, "desc and out are required");
     *out = nullptr;
-    if (desc->precision < LSM_PREC_EXACT64 || desc->precision > LSM_PREC_F32)
-        return fail(nullptr, LSM_EINVAL, "precision must be LSM_PREC_EXACT64, _FAST64 or _F32");
+    if (desc->precision < LSM_PREC_EXACT64 || desc->precision > LSM_PREC_DF)
+        return fail(nullptr, LSM_EINVAL, "precision must be LSM_PREC_EXACT64, _FAST64, _F32 or _DF");
     if (desc->load_mode != 0 && desc->load_mode != 1)
         return fail(nullptr, LSM_EINVAL, "load_mode must be 0 or 1");
     lsm_ctx *c = new (std::nothrow) lsm_ctx();

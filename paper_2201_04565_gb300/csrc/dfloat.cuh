@@ -1,0 +1,207 @@
+// dfloat.cuh -- integer-pipe conversions and double-float arithmetic.
+//
+// On GB300 the FP64 pipe (and every conversion to or from a 64-bit type) runs
+// at about 1/70 of the FP32 rate, so the spring arithmetic of the F32 and DF
+// modes avoids it:
+//   - positions (FP64) are converted to 64-bit fixed point value * 2^S with
+//     integer bit operations (exact when |x| >= 2^(52-S), truncated to 2^-S
+//     otherwise), so spring vectors are exact integer differences;
+//   - fixed-point values are turned into floats, or into unevaluated sums
+//     hi + lo of two floats ("double-float", 48 significant bits), with
+//     integer bit operations;
+//   - double-float sums and products use the error-free transformations of
+//     Dekker (1971) and Knuth (TAOCP vol. 2): TwoSum, Fast2Sum, and TwoProd
+//     via a fused multiply-add.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lsm_internal.h"
+
+namespace lsm {
+
+// x * 2^S as a signed 64-bit integer, truncated toward zero. Requires
+// |x| < 2^(62-S); *over is set when that bound is violated (or x is not
+// finite).
+__device__ __forceinline__ long long dbl_to_fix(double x, int S, bool &over)
+{
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    const long long m = (b & 0x000FFFFFFFFFFFFFLL) | 0x0010000000000000LL;
+    const int sh = e - 1075 + S;
+    over |= sh > 9;  // |x| >= 2^(62-S) (also catches inf / nan)
+    long long f;
+    if (sh >= 0)
+        f = m << (sh > 9 ? 9 : sh);
+    else
+        f = sh > -63 ? (m >> (-sh)) : 0LL;
+    if (e == 0) f = 0;  // zero or subnormal
+    return b < 0 ? -f : f;
+}
+
+// Float with the top 24 significant bits of u * 2^-S (u > 0), truncated;
+// *rem receives the bits below them (u - value * 2^S).
+__device__ __forceinline__ float ufix_top24(unsigned long long u, int S, unsigned long long &rem)
+{
+    const int t = 63 - __clzll((long long)u);  // index of the top bit
+    unsigned long long m24;
+    if (t >= 23) {
+        m24 = u >> (t - 23);
+        rem = u - (m24 << (t - 23));
+    } else {
+        m24 = u << (23 - t);
+        rem = 0;
+    }
+    const int ex = t - S + 127;  // biased exponent of the result
+    const unsigned bits = ((unsigned)ex << 23) | ((unsigned)m24 & 0x7FFFFFu);
+    return ex > 0 ? __uint_as_float(bits) : 0.0f;
+}
+
+// v * 2^-S as a float (truncated to 24 bits).
+__device__ __forceinline__ float fix_to_float(long long v, int S)
+{
+    if (v == 0) return 0.0f;
+    unsigned long long rem;
+    const unsigned long long u = (unsigned long long)(v < 0 ? -v : v);
+    const float f = ufix_top24(u, S, rem);
+    return v < 0 ? -f : f;
+}
+
+__device__ __forceinline__ ff fast_two_sum(float a, float b);
+
+// v * 2^-S as a double-float (top 48 significant bits, truncated).
+__device__ __forceinline__ ff fix_to_ff(long long v, int S)
+{
+    if (v == 0) return ff{0.0f, 0.0f};
+    unsigned long long rem, rem2;
+    const unsigned long long u = (unsigned long long)(v < 0 ? -v : v);
+    const float h = ufix_top24(u, S, rem);
+    const float l = rem ? ufix_top24(rem, S, rem2) : 0.0f;
+    const ff r = fast_two_sum(h, l);
+    return v < 0 ? ff{-r.hi, -r.lo} : r;
+}
+
+// v * 2^-S as a float via two 32-bit int->float conversions (fast path on
+// sm_103a, unlike the 64-bit ones). p24 = 2^(24-S), p0 = 2^-S. Exact split:
+// v = hi * 2^24 + lo with 0 <= lo < 2^24; one rounding in the final fma.
+__device__ __forceinline__ float fix_to_float_i2f(long long v, float p24, float p0)
+{
+    const int hi = (int)(v >> 24);
+    const int lo = (int)(v & 0xFFFFFFLL);
+    return __fmaf_rn(__int2float_rn(hi), p24, __fmul_rn(__int2float_rn(lo), p0));
+}
+
+// Exact float -> double with integer operations (subnormals flush to zero).
+__device__ __forceinline__ double f2d_bits(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xFFu;
+    unsigned long long bits = (unsigned long long)(u >> 31) << 63;
+    if (e == 0xFFu)
+        bits |= (0x7FFull << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    else if (e != 0)
+        bits |= ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+// -- error-free transformations and double-float arithmetic ----------------
+
+__device__ __forceinline__ ff two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return ff{s, e};
+}
+
+__device__ __forceinline__ ff fast_two_sum(float a, float b)  // |a| >= |b|
+{
+    const float s = __fadd_rn(a, b);
+    return ff{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ ff two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return ff{p, __fmaf_rn(a, b, -p)};
+}
+
+// Accurate double-float addition (both parts through TwoSum).
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    ff s = two_sum(a.hi, b.hi);
+    const ff t = two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    ff p = two_prod(a.hi, b.hi);
+    p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+    p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+    return fast_two_sum(p.hi, p.lo);
+}
+
+__device__ __forceinline__ ff ff_mul_f(ff a, float b)
+{
+    ff p = two_prod(a.hi, b);
+    p.lo = __fmaf_rn(a.lo, b, p.lo);
+    return fast_two_sum(p.hi, p.lo);
+}
+
+// a / b with one Newton correction of the single-precision quotient.
+__device__ __forceinline__ ff ff_div(ff a, ff b)
+{
+    const float rb = __frcp_rn(b.hi);
+    const float q1 = __fmul_rn(a.hi, rb);
+    const ff r = ff_sub(a, ff_mul_f(b, q1));
+    const float q2 = __fmul_rn(r.hi, rb);
+    ff q = fast_two_sum(q1, q2);
+    const ff r2 = ff_sub(a, ff_mul(b, q));
+    return fast_two_sum(q.hi, __fadd_rn(q.lo, __fmul_rn(r2.hi, rb)));
+}
+
+// sqrt(a), a > 0, from the single-precision reciprocal square root and one
+// double-float Newton correction.
+__device__ __forceinline__ ff ff_sqrt(ff a)
+{
+    const float y = rsqrtf(a.hi);
+    const float x = __fmul_rn(a.hi, y);
+    const ff xx = two_prod(x, x);
+    const ff d = ff_sub(a, xx);
+    return fast_two_sum(x, __fmul_rn(d.hi, __fmul_rn(0.5f, y)));
+}
+
+// v * 2^-S as a double-float from three exact 24-bit chunks
+// (p48 = 2^(48-S), p24 = 2^(24-S), p0 = 2^-S); |v| < 2^63.
+__device__ __forceinline__ ff fix_to_ff_i2f(long long v, float p48, float p24, float p0)
+{
+    const float a = __fmul_rn(__int2float_rn((int)(v >> 48)), p48);
+    const float b = __fmul_rn(__int2float_rn((int)((v >> 24) & 0xFFFFFFLL)), p24);
+    const float c = __fmul_rn(__int2float_rn((int)(v & 0xFFFFFFLL)), p0);
+    const ff s = two_sum(a, b);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, c));
+}
+
+// Double-float addition with one TwoSum on the high parts (Dekker's form):
+// absolute error within a few units of 2^-46 (|a| + |b|), enough for sums
+// whose accuracy is judged against the largest term.
+__device__ __forceinline__ ff ff_add_sloppy(ff a, ff b)
+{
+    const ff s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ bool ff_gt(ff a, ff b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+
+__device__ __forceinline__ double ff_to_double(ff a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
+
+}  // namespace lsm

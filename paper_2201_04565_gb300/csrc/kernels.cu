@@ -21,6 +21,7 @@
 // chunk.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
 
 #include "lsm_internal.h"
@@ -360,10 +361,12 @@ void free_device(Ctx &c)
                     c.scratch_sample};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    void *tptrs[] = {c.tx[0], c.tx[1], c.tvh[0], c.tvh[1], c.tvobs, c.tph, c.tmask, c.tbrk, c.tmass};
+    void *tptrs[] = {c.tx[0], c.tx[1], c.tvh[0], c.tvh[1], c.tvobs, c.tph, c.tmask, c.tbrk, c.tmass,
+                     c.tinvm, c.tdf};
     for (void *p : tptrs)
         if (p) cudaFree(p);
-    c.tx[0] = c.tx[1] = c.tvh[0] = c.tvh[1] = c.tvobs = c.tmass = nullptr;
+    c.tx[0] = c.tx[1] = c.tvh[0] = c.tvh[1] = c.tvobs = c.tmass = c.tinvm = nullptr;
+    c.tdf = nullptr;
     c.tph = c.tmask = nullptr;
     c.tbrk = nullptr;
     c.x = c.v = c.a = c.mass = c.Xx = nullptr;
@@ -408,6 +411,13 @@ static cudaError_t upload_common(Ctx &c)
     return cudaSuccess;
 }
 
+// Nearest double-float of a double: hi = float(v), lo = float(v - hi).
+static ff split_ff(double v)
+{
+    const float hi = (float)v;
+    return ff{hi, (float)(v - (double)hi)};
+}
+
 // Tile path: state on the 2D pixel grid, both ping-pong buffers at the
 // reference lattice, velocities zero, no spring broken.
 static cudaError_t upload_tile(Ctx &c)
@@ -422,8 +432,27 @@ static cudaError_t upload_tile(Ctx &c)
         X[g] = (g % h.nx) * h.a;
         X[np + g] = (g / h.nx) * h.a;
     }
-    std::vector<double> mtab(h.nphase, 1.0);
+    std::vector<double> mtab(h.nphase, 1.0), itab(h.nphase, 1.0);
     for (int64_t p = 0; p < h.n; p++) mtab[h.phase[h.pix[p]] - 1] = h.mass[p];
+    for (int q = 0; q < h.nphase; q++) itab[q] = 1.0 / mtab[q];
+    // fixed-point scale: |x| stays below 2^(62 - S) for strains up to +300%
+    const double extent = 4.0 * (double)(h.nx > h.ny ? h.nx : h.ny) * h.a + 16.0;
+    c.fix_S = 61 - (int)std::ceil(std::log2(extent));
+    if (c.fix_S > 52) c.fix_S = 52;
+    c.a_fix = std::llround(std::ldexp(h.a, c.fix_S));
+    std::vector<TypeDF> tdf(h.types.size());
+    for (size_t q = 0; q < h.types.size(); q++) {
+        const SpringType &t = h.types[q];
+        const double shell = (q & 1) ? 2.0 : 1.0;  // type id = pair * 2 + (shell - 1)
+        const double aa = (double)c.a_fix * std::ldexp(1.0, -c.fix_S);  // lattice spacing as used
+        // |o|^2 - r0^2 with the products' rounding errors kept (fma)
+        const double p = t.r0 * t.r0, pe = std::fma(t.r0, t.r0, -p);
+        const double o2 = shell * aa * aa, o2e = shell * std::fma(aa, aa, -(aa * aa));
+        tdf[q].k = split_ff(t.k);
+        tdf[q].r0 = split_ff(t.r0);
+        tdf[q].rc2 = split_ff(t.rc2);
+        tdf[q].cor = split_ff((o2 - p) + (o2e - pe));
+    }
     for (int b = 0; b < 2; b++) {
         LSM_TRY(dalloc(&c.tx[b], 2 * np));
         LSM_TRY(dalloc(&c.tvh[b], 2 * np));
@@ -433,6 +462,8 @@ static cudaError_t upload_tile(Ctx &c)
     LSM_TRY(dalloc(&c.tmask, np));
     LSM_TRY(dalloc(&c.tbrk, 4 * np));
     LSM_TRY(dalloc(&c.tmass, h.nphase));
+    LSM_TRY(dalloc(&c.tinvm, h.nphase));
+    LSM_TRY(dalloc(&c.tdf, tdf.size()));
     LSM_TRY(dalloc(&c.part_s, 2 * c.ntiles));
     LSM_TRY(dalloc(&c.part_p, 4 * c.ntiles));
     LSM_TRY(upload_common(c));
@@ -446,6 +477,8 @@ static cudaError_t upload_tile(Ctx &c)
     LSM_TRY(cudaMemsetAsync(c.tmask, 0, np, st));
     LSM_TRY(cudaMemsetAsync(c.tbrk, 0xff, 4 * np * sizeof(long long), st));
     LSM_TRY(cudaMemcpyAsync(c.tmass, mtab.data(), h.nphase * sizeof(double), cudaMemcpyHostToDevice, st));
+    LSM_TRY(cudaMemcpyAsync(c.tinvm, itab.data(), h.nphase * sizeof(double), cudaMemcpyHostToDevice, st));
+    LSM_TRY(cudaMemcpyAsync(c.tdf, tdf.data(), tdf.size() * sizeof(TypeDF), cudaMemcpyHostToDevice, st));
     c.tcur = 0;
     LSM_TRY(cudaStreamSynchronize(st));
     return cudaSuccess;
@@ -535,6 +568,7 @@ static void springs(Ctx &c)
         c.d_first_break, c.d_nbroken, c.part_s, c.nblk_s)
     switch (c.h.precision) {
     case LSM_PREC_FAST64: LSM_SPR(LSM_PREC_FAST64); break;
+    case LSM_PREC_DF: LSM_SPR(LSM_PREC_FAST64); break;
     case LSM_PREC_F32: LSM_SPR(LSM_PREC_F32); break;
     default: LSM_SPR(LSM_PREC_EXACT64); break;
     }

@@ -29,6 +29,17 @@ struct SpringType {
     double k, r0, rc2, kr0;
 };
 
+// A double-float: the unevaluated sum hi + lo of two floats.
+struct ff {
+    float hi, lo;
+};
+
+// Spring type in double-float form for the fixed-point spring modes:
+// cor = |o|^2 - r0^2 for the type's lattice vector o (0 up to rounding).
+struct TypeDF {
+    ff k, r0, rc2, cor;
+};
+
 // Reduction slots of one sample (partials are reduced in a fixed order).
 enum {
     RED_W = 0,      // sum over intact springs of d_x * f_x (virial, Eq. 7)
@@ -115,6 +126,10 @@ struct Ctx {
     uint8_t *tph = nullptr, *tmask = nullptr;
     long long *tbrk = nullptr;            // [4][tnp]
     double *tmass = nullptr;              // per phase
+    double *tinvm = nullptr;              // per phase, 1 / mass
+    TypeDF *tdf = nullptr;                // double-float spring types
+    int fix_S = 40;                       // fixed-point scale of positions
+    long long a_fix = 0;                  // lattice spacing * 2^fix_S
     int tcur = 0;
     int64_t ntiles = 0;
 

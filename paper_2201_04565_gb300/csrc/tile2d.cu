@@ -25,6 +25,10 @@
 // deviation from the lattice vector, gathering in FP32 and integrating in FP64.
 #include <cuda_runtime.h>
 
+#include <cmath>
+#include <type_traits>
+
+#include "dfloat.cuh"
 #include "lsm_internal.h"
 
 namespace lsm {
@@ -75,7 +79,12 @@ struct TileArgs {
     uint8_t *mask;
     long long *brk;  // [4][np]
     const SpringType *types;
-    const double *mass;  // per phase
+    const TypeDF *tdf;         // double-float copies of the spring types
+    const double *mass;        // per phase
+    const double *inv_mass;    // per phase
+    int S;                     // fixed-point scale: positions as x * 2^S
+    long long a_fix;           // lattice spacing in fixed point
+    float p48, p24, p0;        // 2^(48-S), 2^(24-S), 2^-S
     double dt, hdt, gamma, a;
     int grip_mode;
     const long long *d_step;  // steps completed before this graph launch
@@ -86,200 +95,312 @@ struct TileArgs {
     int64_t ntiles;
 };
 
+// Force on the lower endpoint of one spring (rp -> rq, forward slot), with
+// the break test. Writes the force into sf; OWNER adds the sample sums and
+// records a break (only the tile owning the lower endpoint does).
+template <int PREC, int MODE, bool SAMPLE, bool OWNER, int NR, int NS, typename FT>
+__device__ __forceinline__ void eval_spring(const TileArgs &A, int rp, int rq, int slot, const double *sx,
+                                            const double *sy, const long long *sxf, const long long *syf,
+                                            const uint8_t *sph, const uint8_t *smk, FT *sf,
+                                            const SpringType *stab, const TypeDF *sdf, const ff (*soff)[3],
+                                            int *snew, int64_t gsrc, long long step_now, double &w_acc,
+                                            double &u_acc)
+{
+    FT fx{}, fy{};
+    const uint8_t pp = sph[rp], pq = sph[rq];
+    const uint8_t mk = smk[rp];
+    if (pp && pq && !((mk >> slot) & 1)) {
+        const int ti = (((pp - 1) * A.nphase) + (pq - 1)) * 2 + (slot & 1);
+        bool brk_now = false;
+        if constexpr (PREC == LSM_PREC_EXACT64) {
+            const SpringType t = stab[ti];
+            const double ddx = sb(sx[rq], sx[rp]), ddy = sb(sy[rq], sy[rp]);
+            const double r2 = ad(ml(ddx, ddx), ml(ddy, ddy));
+            if (MODE == T_STEP && r2 > t.rc2) {
+                brk_now = true;
+            } else {
+                const double r = __dsqrt_rn(r2);
+                const double c = dv(ml(t.k, sb(r, t.r0)), r);
+                fx = ml(c, ddx);
+                fy = ml(c, ddy);
+                if (SAMPLE && OWNER) {
+                    const double st = sb(r, t.r0);
+                    u_acc += ml(ml(ml(0.5, t.k), st), st);
+                    w_acc += ml(ddx, ml(c, ddx));
+                }
+            }
+        } else if constexpr (PREC == LSM_PREC_FAST64) {
+            const SpringType t = stab[ti];
+            const double ddx = sx[rq] - sx[rp], ddy = sy[rq] - sy[rp];
+            const double r2 = fma(ddx, ddx, ddy * ddy);
+            if (MODE == T_STEP && r2 > t.rc2) {
+                brk_now = true;
+            } else {
+                const double ir = rsqrt(r2);
+                const double c = fma(-t.kr0, ir, t.k);
+                fx = c * ddx;
+                fy = c * ddy;
+                if (SAMPLE && OWNER) {
+                    const double st = fma(r2, ir, -t.r0);
+                    u_acc += 0.5 * t.k * st * st;
+                    w_acc += ddx * fx;
+                }
+            }
+        } else {
+            // exact spring vector d = o + e from the fixed-point positions; e
+            // is the deviation from the lattice vector o, so
+            // r^2 - |o|^2 = (2 o + e).e carries no cancellation
+            const TypeDF t = sdf[ti];
+            const int dx = slot == 0 ? 1 : (slot == 1 ? -1 : (slot == 2 ? 0 : 1));
+            const int dy = slot == 0 ? 0 : 1;
+            const long long exf = sxf[rq] - sxf[rp] - (long long)dx * A.a_fix;
+            const long long eyf = syf[rq] - syf[rp] - (long long)dy * A.a_fix;
+            if constexpr (PREC == LSM_PREC_F32) {
+                const float ex = fix_to_float_i2f(exf, A.p24, A.p0), ey = fix_to_float_i2f(eyf, A.p24, A.p0);
+                const float ox = soff[slot][0].hi, oy = soff[slot][1].hi;
+                const float dxf = ox + ex, dyf = oy + ey;
+                const float num = fmaf(2.0f * ox + ex, ex, fmaf(2.0f * oy + ey, ey, t.cor.hi));
+                const float r2f = soff[slot][2].hi + num;
+                if (MODE == T_STEP && r2f > t.rc2.hi) {
+                    brk_now = true;
+                } else {
+                    const float ir = rsqrtf(r2f);
+                    const float st = __fdividef(num, fmaf(r2f, ir, t.r0.hi));  // r - r0
+                    const float c = t.k.hi * st * ir;
+                    fx = c * dxf;
+                    fy = c * dyf;
+                    if (SAMPLE && OWNER) {
+                        u_acc += 0.5 * (double)t.k.hi * (double)st * (double)st;
+                        w_acc += (double)dxf * (double)fx;
+                    }
+                }
+            } else {  // LSM_PREC_DF
+                const ff ex = fix_to_ff_i2f(exf, A.p48, A.p24, A.p0);
+                const ff ey = fix_to_ff_i2f(eyf, A.p48, A.p24, A.p0);
+                const ff ox = soff[slot][0], oy = soff[slot][1];
+                const ff dxf = ff_add(ox, ex), dyf = ff_add(oy, ey);
+                const ff num = ff_add(ff_add(ff_mul(ff_add(ff_add(ox, ox), ex), ex),
+                                             ff_mul(ff_add(ff_add(oy, oy), ey), ey)), t.cor);
+                const ff r2 = ff_add(soff[slot][2], num);
+                if (MODE == T_STEP && ff_gt(r2, t.rc2)) {
+                    brk_now = true;
+                } else {
+                    const ff r = ff_sqrt(r2);
+                    const ff den = ff_mul(r, ff_add(r, t.r0));
+                    const ff c = ff_mul(t.k, ff_div(num, den));  // k (r - r0) / r
+                    fx = ff_mul(c, dxf);
+                    fy = ff_mul(c, dyf);
+                    if (SAMPLE && OWNER) {
+                        const double st = ff_to_double(ff_div(num, ff_add(r, t.r0)));
+                        u_acc += 0.5 * ff_to_double(t.k) * st * st;
+                        w_acc += ff_to_double(dxf) * ff_to_double(fx);
+                    }
+                }
+            }
+        }
+        if (OWNER && brk_now) {
+            atomicOr(&snew[rp], 1 << slot);
+            A.brk[(int64_t)slot * A.np + gsrc] = step_now;
+            atomicMin(A.first_break, (unsigned long long)step_now);
+            atomicAdd(A.nbroken, 1ull);
+        }
+    }
+    sf[(0 * 4 + slot) * NS + rp] = fx;
+    sf[(1 * 4 + slot) * NS + rp] = fy;
+}
+
+// Region pixel (rx, ry) -> shared memory: phase, broken mask, positions
+// drifted by dt vh (step mode), fixed-point copies.
+template <int PREC, int MODE, int RX>
+__device__ __forceinline__ void load_pixel(const TileArgs &A, int x0, int y0, int rx, int ry, double *sx,
+                                           double *sy, long long *sxf, long long *syf, uint8_t *sph,
+                                           uint8_t *smk, bool &over)
+{
+    constexpr bool FIX = PREC == LSM_PREC_F32 || PREC == LSM_PREC_DF;
+    const int gx = x0 - 1 + rx, gy = y0 - 1 + ry;
+    const int e = ry * RX + rx;
+    uint8_t ph = 0, mk = 0;
+    double px = 0.0, py = 0.0;
+    if (gx >= 0 && gx < A.nx && gy >= 0 && gy < A.ny) {
+        const int64_t g = (int64_t)gy * A.nx + gx;
+        ph = A.phase[g];
+        if (ph) {
+            mk = A.mask[g];
+            px = A.x_in[g];
+            py = A.x_in[A.np + g];
+            if (MODE == T_STEP) {
+                const bool grip = gx == 0 || gx == A.nx - 1;
+                if (!grip) {
+                    if constexpr (PREC == LSM_PREC_EXACT64) px = ad(px, ml(A.dt, A.vh_in[g]));
+                    else px = fma(A.dt, A.vh_in[g], px);
+                }
+                if (!(grip && A.grip_mode == 1)) {
+                    if constexpr (PREC == LSM_PREC_EXACT64) py = ad(py, ml(A.dt, A.vh_in[A.np + g]));
+                    else py = fma(A.dt, A.vh_in[A.np + g], py);
+                }
+            }
+        }
+    }
+    sx[e] = px;
+    sy[e] = py;
+    if constexpr (FIX) {
+        sxf[e] = dbl_to_fix(px, A.S, over);
+        syf[e] = dbl_to_fix(py, A.S, over);
+    }
+    sph[e] = ph;
+    smk[e] = mk;
+}
+
+// One CTA = one 32 x TY tile; warp w handles tile rows w, w + 8, ...
 template <int TX, int TY, int PREC, int MODE, bool SAMPLE>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_tile2d(TileArgs A)
 {
+    static_assert(TX == 32, "one warp per tile row");
     constexpr int RX = TX + 2, RY = TY + 2;   // region = tile + 1-pixel halo
-    constexpr int SX = TX + 2, SY = TY + 1;   // spring sources: x0-1..x0+TX, y0-1..y0+TY-1
-    constexpr int NR = RX * RY, NS = SX * SY;
-    using FT = typename std::conditional<PREC == LSM_PREC_F32, float, double>::type;
+    constexpr int NR = RX * RY;
+    constexpr int NS = RX * (TY + 1);         // spring sources: region rows 0..TY
+    constexpr int NW = TILE_THREADS / 32;
+    constexpr bool FIX = PREC == LSM_PREC_F32 || PREC == LSM_PREC_DF;
+    using FT = typename std::conditional<PREC == LSM_PREC_F32, float,
+               typename std::conditional<PREC == LSM_PREC_DF, ff, double>::type>::type;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *sx = (double *)smem_raw;               // [NR]
+    double *sx = (double *)smem_raw;               // [NR] drifted positions
     double *sy = sx + NR;                          // [NR]
-    FT *sf = (FT *)(sy + NR);                      // [2][4][NS]
-    int *snew = (int *)(sf + 8 * NS);              // [NS]
+    long long *sxf = (long long *)(sy + NR);       // [NR] fixed point (FIX modes only)
+    long long *syf = sxf + (FIX ? NR : 0);         // [NR]
+    FT *sf = (FT *)(syf + (FIX ? NR : 0));         // [2][4][NS] force on the lower end
+    int *snew = (int *)(sf + 8 * NS);              // [NS] springs broken in this step
     uint8_t *sph = (uint8_t *)(snew + NS);         // [NR]
     uint8_t *smk = sph + NR;                       // [NR]
-    __shared__ double sred[TILE_THREADS / 32];
+    __shared__ double sred[NW];
     __shared__ SpringType stab[128];
-    __shared__ double smass[8];
+    __shared__ TypeDF sdf[FIX ? 128 : 1];
+    __shared__ ff soff[4][3];  // per slot: o_x, o_y, |o|^2 as double-floats
+    __shared__ double smass[8], sinvm[8];
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int64_t tile_id = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
     const int nt = 2 * A.nphase * A.nphase;
-    for (int q = tid; q < nt; q += TILE_THREADS) stab[q] = A.types[q];
-    for (int q = tid; q < A.nphase; q += TILE_THREADS) smass[q] = A.mass[q];
+    for (int q = tid; q < nt; q += TILE_THREADS) {
+        stab[q] = A.types[q];
+        if constexpr (FIX) sdf[q] = A.tdf[q];
+    }
+    if (tid < A.nphase) {
+        smass[tid] = A.mass[tid];
+        sinvm[tid] = A.inv_mass[tid];
+    }
+    if (FIX && tid < 4) {
+        const int dx = tid == 0 ? 1 : (tid == 1 ? -1 : (tid == 2 ? 0 : 1));
+        const int dy = tid == 0 ? 0 : 1;
+        const ff ox = fix_to_ff((long long)dx * A.a_fix, A.S), oy = fix_to_ff((long long)dy * A.a_fix, A.S);
+        soff[tid][0] = ox;
+        soff[tid][1] = oy;
+        soff[tid][2] = ff_add(ff_mul(ox, ox), ff_mul(oy, oy));
+    }
     const long long step_now = MODE == T_STEP ? *A.d_step + A.t_off : 0;
 
-    // 1. region load (+ drift)
-    for (int e = tid; e < NR; e += TILE_THREADS) {
-        const int gx = x0 - 1 + e % RX, gy = y0 - 1 + e / RX;
-        uint8_t ph = 0, mk = 0;
-        double px = 0.0, py = 0.0;
-        if (gx >= 0 && gx < A.nx && gy >= 0 && gy < A.ny) {
-            const int64_t g = (int64_t)gy * A.nx + gx;
-            ph = A.phase[g];
-            if (ph) {
-                mk = A.mask[g];
-                px = A.x_in[g];
-                py = A.x_in[A.np + g];
-                if (MODE == T_STEP) {
-                    const bool grip = gx == 0 || gx == A.nx - 1;
-                    if (!grip) {
-                        if constexpr (PREC == LSM_PREC_EXACT64) px = ad(px, ml(A.dt, A.vh_in[g]));
-                        else px = fma(A.dt, A.vh_in[g], px);
-                    }
-                    if (!(grip && A.grip_mode == 1)) {
-                        if constexpr (PREC == LSM_PREC_EXACT64) py = ad(py, ml(A.dt, A.vh_in[A.np + g]));
-                        else py = fma(A.dt, A.vh_in[A.np + g], py);
-                    }
-                }
-            }
-        }
-        sx[e] = px;
-        sy[e] = py;
-        sph[e] = ph;
-        smk[e] = mk;
-    }
+    // 1. region load (+ drift): tile columns by lanes, halo columns apart
+    bool over = false;
+    for (int ry = warp; ry < RY; ry += NW)
+        load_pixel<PREC, MODE, RX>(A, x0, y0, lane + 1, ry, sx, sy, sxf, syf, sph, smk, over);
+    for (int q = tid; q < 2 * RY; q += TILE_THREADS)
+        load_pixel<PREC, MODE, RX>(A, x0, y0, (q & 1) ? TX + 1 : 0, q >> 1, sx, sy, sxf, syf, sph, smk, over);
+    if (FIX && over) atomicOr(A.status, 2);
     for (int e = tid; e < NS; e += TILE_THREADS) snew[e] = 0;
     __syncthreads();
 
-    // 2. springs touching the tile
+    // 2a. forward springs of the owned particles
     double w_acc = 0.0, u_acc = 0.0;
-    for (int e = tid; e < 4 * NS; e += TILE_THREADS) {
-        const int slot = e / NS, si_ = e % NS;
-        const int rx = si_ % SX, ry = si_ / SX;
-        const int dx = slot == 0 ? 1 : (slot == 1 ? -1 : (slot == 2 ? 0 : 1));
-        const int dy = slot == 0 ? 0 : 1;
-        const int qx = rx + dx, qy = ry + dy;
-        FT fx = 0, fy = 0;
-        const bool p_in = rx >= 1 && rx <= TX && ry >= 1 && ry <= TY;
-        const bool q_in = qx >= 1 && qx <= TX && qy >= 1 && qy <= TY;
-        if ((p_in || q_in) && qx >= 0 && qx < RX) {
-            const int rp = ry * RX + rx, rq = qy * RX + qx;
-            const uint8_t pp = sph[rp], pq = sph[rq];
-            if (pp && pq && !((smk[rp] >> slot) & 1)) {
-                const SpringType t = stab[(((pp - 1) * A.nphase) + (pq - 1)) * 2 + (slot & 1)];
-                double ddx, ddy;
-                if constexpr (PREC == LSM_PREC_EXACT64) {
-                    ddx = sb(sx[rq], sx[rp]);
-                    ddy = sb(sy[rq], sy[rp]);
-                } else {
-                    ddx = sx[rq] - sx[rp];
-                    ddy = sy[rq] - sy[rp];
-                }
-                bool brk_now = false;
-                if constexpr (PREC == LSM_PREC_EXACT64) {
-                    const double r2 = ad(ml(ddx, ddx), ml(ddy, ddy));
-                    if (MODE == T_STEP && r2 > t.rc2) {
-                        brk_now = true;
-                    } else {
-                        const double r = __dsqrt_rn(r2);
-                        const double c = dv(ml(t.k, sb(r, t.r0)), r);
-                        fx = ml(c, ddx);
-                        fy = ml(c, ddy);
-                        if (SAMPLE && p_in) {
-                            const double st = sb(r, t.r0);
-                            u_acc += ml(ml(ml(0.5, t.k), st), st);
-                            w_acc += ml(ddx, ml(c, ddx));
-                        }
-                    }
-                } else if constexpr (PREC == LSM_PREC_FAST64) {
-                    const double r2 = fma(ddx, ddx, ddy * ddy);
-                    if (MODE == T_STEP && r2 > t.rc2) {
-                        brk_now = true;
-                    } else {
-                        const double ir = rsqrt(r2);
-                        const double c = fma(-t.kr0, ir, t.k);
-                        fx = c * ddx;
-                        fy = c * ddy;
-                        if (SAMPLE && p_in) {
-                            const double st = fma(r2, ir, -t.r0);
-                            u_acc += 0.5 * t.k * st * st;
-                            w_acc += ddx * fx;
-                        }
-                    }
-                } else {  // F32 force from the deviation from the lattice vector
-                    const double ox = dx * A.a, oy = dy * A.a;
-                    const float ex = (float)(ddx - ox), ey = (float)(ddy - oy);
-                    const float fox = (float)ox, foy = (float)oy;
-                    const float dxf = fox + ex, dyf = foy + ey;
-                    const float r2f = fmaf(dxf, dxf, dyf * dyf);
-                    if (MODE == T_STEP && r2f > (float)t.rc2) {
-                        brk_now = true;
-                    } else {
-                        const float r0f = (float)t.r0;
-                        const float rf = sqrtf(r2f);
-                        // r - r0 = (2 o.e + e.e) / (r + r0), without cancellation
-                        const float num = fmaf(2.0f * fox + ex, ex, (2.0f * foy + ey) * ey);
-                        const float st = num / (rf + r0f);
-                        const float c = (float)t.k * st / rf;
-                        fx = c * dxf;
-                        fy = c * dyf;
-                        if (SAMPLE && p_in) {
-                            u_acc += 0.5 * t.k * (double)st * (double)st;
-                            w_acc += ddx * (double)fx;
-                        }
-                    }
-                }
-                if (brk_now && p_in) {  // the tile owning the lower endpoint records it
-                    atomicOr(&snew[si_], 1 << slot);
-                    const int64_t g = (int64_t)(y0 - 1 + ry) * A.nx + (x0 - 1 + rx);
-                    A.brk[(int64_t)slot * A.np + g] = step_now;
-                    atomicMin(A.first_break, (unsigned long long)step_now);
-                    atomicAdd(A.nbroken, 1ull);
-                }
-            }
+    constexpr int dq[4] = {1, RX - 1, RX, RX + 1};
+#pragma unroll
+    for (int k = 0; k < TY / NW; k++) {
+        const int ry = warp + k * NW + 1, rx = lane + 1;
+        const int rp = ry * RX + rx;
+        const int64_t g = (int64_t)(y0 + ry - 1) * A.nx + (x0 + lane);
+#pragma unroll
+        for (int slot = 0; slot < 4; slot++)
+            eval_spring<PREC, MODE, SAMPLE, true, NR, NS>(A, rp, rp + dq[slot], slot, sx, sy, sxf, syf, sph, smk,
+                                                          sf, stab, sdf, soff, snew, g, step_now, w_acc, u_acc);
+    }
+    // 2b. springs from halo sources into the tile (also evaluated, with the
+    // same result, by the tile that owns their lower endpoint)
+    constexpr int NH = 3 * TX + 3 * TY - 2;
+    for (int t = tid; t < NH; t += TILE_THREADS) {
+        int rx, ry, slot;
+        if (t < 3 * TX) {  // halo row above the tile, slots 1..3
+            slot = 1 + t / TX;
+            const int j = t % TX;
+            rx = slot == 2 ? j + 1 : (slot == 3 ? j : j + 2);
+            ry = 0;
+        } else if (t < 3 * TX + TY) {  // left halo column, slot 0
+            slot = 0; rx = 0; ry = 1 + (t - 3 * TX);
+        } else if (t < 3 * TX + 2 * TY - 1) {  // left halo column, slot 3
+            slot = 3; rx = 0; ry = 1 + (t - 3 * TX - TY);
+        } else {  // right halo column, slot 1
+            slot = 1; rx = TX + 1; ry = 1 + (t - 3 * TX - 2 * TY + 1);
         }
-        sf[(0 * 4 + slot) * NS + si_] = fx;
-        sf[(1 * 4 + slot) * NS + si_] = fy;
+        const int rp = ry * RX + rx;
+        eval_spring<PREC, MODE, SAMPLE, false, NR, NS>(A, rp, rp + dq[slot], slot, sx, sy, sxf, syf, sph, smk, sf,
+                                                       stab, sdf, soff, snew, 0, step_now, w_acc, u_acc);
     }
     __syncthreads();
 
     // 3. gather + integrate the owned particles
     double mvx2 = 0.0, ke = 0.0, react = 0.0, res = 0.0;
     bool bad = false;
-    for (int e = tid; e < TX * TY; e += TILE_THREADS) {
-        const int lx = e % TX, ly = e / TX;
-        const int gx = x0 + lx, gy = y0 + ly;
-        const int rx = lx + 1, ry = ly + 1;
+#pragma unroll
+    for (int k = 0; k < TY / NW; k++) {
+        const int ly = warp + k * NW;
+        const int gx = x0 + lane, gy = y0 + ly;
+        const int rx = lane + 1, ry = ly + 1;
         const int rp = ry * RX + rx;
         if (gx >= A.nx || gy >= A.ny || !sph[rp]) continue;
         const int64_t g = (int64_t)gy * A.nx + gx;
-        const int sp = ry * SX + rx;
-        // incoming: sources p - o for slots 3, 2, 1, 0 (ascending source index)
-        const int s3 = (ry - 1) * SX + (rx - 1), s2 = (ry - 1) * SX + rx, s1 = (ry - 1) * SX + (rx + 1),
-                  s0 = ry * SX + (rx - 1);
-        FT Fx, Fy;
+        // incoming springs come from p - o for slots 3, 2, 1, 0 (ascending
+        // source index), then the outgoing ones in slot order
+        const int s3 = rp - RX - 1, s2 = rp - RX, s1 = rp - RX + 1, s0 = rp - 1;
+        double F[2];
         if constexpr (PREC == LSM_PREC_EXACT64) {
-            Fx = 0.0;
-            Fy = 0.0;
-            Fx = sb(Fx, sf[(0 * 4 + 3) * NS + s3]); Fy = sb(Fy, sf[(1 * 4 + 3) * NS + s3]);
-            Fx = sb(Fx, sf[(0 * 4 + 2) * NS + s2]); Fy = sb(Fy, sf[(1 * 4 + 2) * NS + s2]);
-            Fx = sb(Fx, sf[(0 * 4 + 1) * NS + s1]); Fy = sb(Fy, sf[(1 * 4 + 1) * NS + s1]);
-            Fx = sb(Fx, sf[(0 * 4 + 0) * NS + s0]); Fy = sb(Fy, sf[(1 * 4 + 0) * NS + s0]);
 #pragma unroll
-            for (int sl = 0; sl < 4; sl++) {
-                Fx = ad(Fx, sf[(0 * 4 + sl) * NS + sp]);
-                Fy = ad(Fy, sf[(1 * 4 + sl) * NS + sp]);
+            for (int c = 0; c < 2; c++) {
+                double acc = 0.0;
+                acc = sb(acc, sf[(c * 4 + 3) * NS + s3]);
+                acc = sb(acc, sf[(c * 4 + 2) * NS + s2]);
+                acc = sb(acc, sf[(c * 4 + 1) * NS + s1]);
+                acc = sb(acc, sf[(c * 4 + 0) * NS + s0]);
+#pragma unroll
+                for (int sl = 0; sl < 4; sl++) acc = ad(acc, sf[(c * 4 + sl) * NS + rp]);
+                F[c] = acc;
+            }
+        } else if constexpr (PREC == LSM_PREC_DF) {
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                ff acc = ff_neg(sf[(c * 4 + 3) * NS + s3]);
+                acc = ff_add_sloppy(acc, ff_neg(sf[(c * 4 + 2) * NS + s2]));
+                acc = ff_add_sloppy(acc, ff_neg(sf[(c * 4 + 1) * NS + s1]));
+                acc = ff_add_sloppy(acc, ff_neg(sf[(c * 4 + 0) * NS + s0]));
+#pragma unroll
+                for (int sl = 0; sl < 4; sl++) acc = ff_add_sloppy(acc, sf[(c * 4 + sl) * NS + rp]);
+                F[c] = ff_to_double(acc);
             }
         } else {
-            Fx = sf[(0 * 4 + 0) * NS + sp] - sf[(0 * 4 + 3) * NS + s3];
-            Fy = sf[(1 * 4 + 0) * NS + sp] - sf[(1 * 4 + 3) * NS + s3];
-            Fx += sf[(0 * 4 + 1) * NS + sp] - sf[(0 * 4 + 2) * NS + s2];
-            Fy += sf[(1 * 4 + 1) * NS + sp] - sf[(1 * 4 + 2) * NS + s2];
-            Fx += sf[(0 * 4 + 2) * NS + sp] - sf[(0 * 4 + 1) * NS + s1];
-            Fy += sf[(1 * 4 + 2) * NS + sp] - sf[(1 * 4 + 1) * NS + s1];
-            Fx += sf[(0 * 4 + 3) * NS + sp] - sf[(0 * 4 + 0) * NS + s0];
-            Fy += sf[(1 * 4 + 3) * NS + sp] - sf[(1 * 4 + 0) * NS + s0];
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                FT acc = sf[(c * 4 + 0) * NS + rp] - sf[(c * 4 + 3) * NS + s3];
+                acc += sf[(c * 4 + 1) * NS + rp] - sf[(c * 4 + 2) * NS + s2];
+                acc += sf[(c * 4 + 2) * NS + rp] - sf[(c * 4 + 1) * NS + s1];
+                acc += sf[(c * 4 + 3) * NS + rp] - sf[(c * 4 + 0) * NS + s0];
+                if constexpr (PREC == LSM_PREC_F32) F[c] = f2d_bits(acc);
+                else F[c] = acc;
+            }
         }
         const bool grip = gx == 0 || gx == A.nx - 1;
         const bool fixx = grip, fixy = grip && A.grip_mode == 1;
-        const double m = smass[sph[rp] - 1];
-        const double F[2] = {(double)Fx, (double)Fy};
+        const int ph = sph[rp] - 1;
+        const double m = smass[ph];
         const double xr[2] = {sx[rp], sy[rp]};
         if (SAMPLE && gx == A.nx - 1) {
             if constexpr (PREC == LSM_PREC_EXACT64) react = sb(react, F[0]);
@@ -311,7 +432,7 @@ k_tile2d(TileArgs A)
                 vn = ad(vh, ml(A.hdt, acc));
                 vh2 = ad(vn, ml(A.hdt, acc));
             } else {
-                const double im = 1.0 / m;
+                const double im = sinvm[ph];
                 acc = fma(-A.gamma * im, vh, F[c] * im);
                 vn = fma(A.hdt, acc, vh);
                 vh2 = fma(A.dt, acc, vh);
@@ -331,7 +452,7 @@ k_tile2d(TileArgs A)
             }
         }
         if (MODE == T_STEP) {
-            const int nb = snew[sp];
+            const int nb = snew[rp];
             if (nb) A.mask[g] = (uint8_t)(smk[rp] | nb);
         }
     }
@@ -379,10 +500,11 @@ __global__ void k_tile_strain(int nx, int ny, int64_t np, double *x, double *vh,
 template <int TX, int TY>
 static constexpr size_t tile_smem(int prec)
 {
-    constexpr int RX = TX + 2, RY = TY + 2, SX = TX + 2, SY = TY + 1;
-    return (size_t)2 * RX * RY * sizeof(double) +
-           (size_t)8 * SX * SY * (prec == LSM_PREC_F32 ? sizeof(float) : sizeof(double)) +
-           (size_t)SX * SY * sizeof(int) + (size_t)2 * RX * RY + 16;
+    constexpr int RX = TX + 2, RY = TY + 2, SX = TX + 2, SY = TY + 1;  // sources: region rows 0..TY
+    const bool fix = prec == LSM_PREC_F32 || prec == LSM_PREC_DF;
+    const size_t fsz = prec == LSM_PREC_F32 ? sizeof(float) : sizeof(double);  // ff is 8 bytes
+    return (size_t)2 * RX * RY * sizeof(double) + (fix ? (size_t)2 * RX * RY * sizeof(long long) : 0) +
+           (size_t)8 * SX * SY * fsz + (size_t)SX * SY * sizeof(int) + (size_t)2 * RX * RY + 16;
 }
 
 constexpr int TILE_X = 32, TILE_Y = 16;
@@ -403,7 +525,14 @@ static TileArgs tile_args(Ctx &c)
     A.mask = c.tmask;
     A.brk = c.tbrk;
     A.types = c.types;
+    A.tdf = c.tdf;
     A.mass = c.tmass;
+    A.inv_mass = c.tinvm;
+    A.S = c.fix_S;
+    A.a_fix = c.a_fix;
+    A.p48 = ldexpf(1.0f, 48 - c.fix_S);
+    A.p24 = ldexpf(1.0f, 24 - c.fix_S);
+    A.p0 = ldexpf(1.0f, -c.fix_S);
     A.dt = c.h.dt;
     A.hdt = 0.5 * c.h.dt;
     A.gamma = c.h.damping;
@@ -442,6 +571,7 @@ static cudaError_t launch_tile_prec(Ctx &c, TileArgs A)
     switch (c.h.precision) {
     case LSM_PREC_FAST64: return launch_tile<LSM_PREC_FAST64, MODE, SAMPLE>(c, A);
     case LSM_PREC_F32: return launch_tile<LSM_PREC_F32, MODE, SAMPLE>(c, A);
+    case LSM_PREC_DF: return launch_tile<LSM_PREC_DF, MODE, SAMPLE>(c, A);
     default: return launch_tile<LSM_PREC_EXACT64, MODE, SAMPLE>(c, A);
     }
 }

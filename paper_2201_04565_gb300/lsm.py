@@ -17,8 +17,9 @@ LIB_PATH = os.path.join(HERE, "liblsm.so")
 
 LSM_OK, LSM_EINVAL, LSM_ENOMEM, LSM_ECUDA = 0, -1, -2, -3
 LSM_ENOTCONV, LSM_ETIMEOUT, LSM_ENONFINITE, LSM_ESTATE = -4, -5, -6, -7
-LSM_PREC_EXACT64, LSM_PREC_FAST64, LSM_PREC_F32 = 0, 1, 2
-PRECISIONS = {"exact64": LSM_PREC_EXACT64, "fast64": LSM_PREC_FAST64, "f32": LSM_PREC_F32}
+LSM_PREC_EXACT64, LSM_PREC_FAST64, LSM_PREC_F32, LSM_PREC_DF = 0, 1, 2, 3
+PRECISIONS = {"exact64": LSM_PREC_EXACT64, "fast64": LSM_PREC_FAST64, "f32": LSM_PREC_F32,
+              "df64": LSM_PREC_DF}
 STATUS_NAMES = {0: "LSM_OK", -1: "LSM_EINVAL", -2: "LSM_ENOMEM", -3: "LSM_ECUDA",
                 -4: "LSM_ENOTCONV", -5: "LSM_ETIMEOUT", -6: "LSM_ENONFINITE", -7: "LSM_ESTATE"}
 

@@ -121,10 +121,12 @@ def test_c0_exact64_bit_identical(oracle_mod, L, path):
         assert a["residual"] == b["residual"]
 
 
-@pytest.mark.parametrize("path", PATHS)
-def test_c0_fast64_within_tolerance(oracle_mod, L, path):
+@pytest.mark.parametrize("path,precision", [(0, "fast64"), (1, "fast64"), (0, "df64")])
+def test_c0_fast_modes_within_tolerance(oracle_mod, L, path, precision):
+    """fast64 (reassociated FP64) and df64 (fixed-point spring vectors with
+    double-float forces, FP64 integration) against the oracle."""
     img = inclusion_image(64, 64, 3.0, 8.0, 0.30, 0)
-    o, g = _pair(oracle_mod, L, img, two_phase_materials(), precision="fast64", path=path)
+    o, g = _pair(oracle_mod, L, img, two_phase_materials(), precision=precision, path=path)
     so = _run_schedule(o, g, 50, 20, 1e-3)  # 1000 steps
     xg, _ = g.state()
     xo, _, _ = o.state()
@@ -147,7 +149,8 @@ def test_c0_f32_force_error_is_bounded(oracle_mod, L, path):
     xo, _, _ = o.state()
     X = o.topology()["X"]
     rel_u = np.abs(xg - xo).max() / np.abs(xo - X).max()
-    assert rel_u < 1e-3  # displacement error of single-precision forces
+    print("f32 path %d: max displacement error / max displacement = %.3e" % (path, rel_u))
+    assert rel_u < 1e-4  # displacement error of single-precision forces
     sg = g.samples()
     assert sg[-1]["sigma_vir"] == pytest.approx(so[-1]["sigma_vir"], rel=1e-3)
 
