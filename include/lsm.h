@@ -238,6 +238,38 @@ lsm_status lsm_synchronize(lsm_ctx *ctx);
 lsm_status lsm_counters(lsm_ctx *ctx, int64_t *steps, int64_t *spring_updates,
                         int64_t *kernel_launches);
 
+/* Potential energy (Eq. 1) and virial sum of the intact springs of a network
+ * at given positions, with no device memory allocated by the library.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory -- code that runs inside a memory pool or
+ * budget owned by another framework, and code that must not trigger the
+ * implicit device-wide synchronisation of cudaFree. It never calls
+ * cudaMalloc, cudaFree or an allocating library routine.
+ *
+ * Arguments (all arrays are DEVICE pointers owned by the caller):
+ *   dim      2 or 3; n particles, m springs (0 <= m <= 268435456).
+ *   x        dim*n positions, component-major ([c * n + p]).
+ *   si, sj   m spring endpoints; k, r0 m spring constants and rest lengths.
+ *   broken   m bytes, nonzero = broken (skipped); NULL = all intact.
+ *   out      2 doubles written: out[0] = sum 1/2 k (r - r0)^2,
+ *            out[1] = sum (x_j - x_i)_x f_x with f = k (r - r0)/r (x_j - x_i)
+ *            (so sigma_xx = (out[1] - sum m v_x^2) / Omega, Eq. 7).
+ *   stream   cudaStream_t (NULL = default stream). The call is stream
+ *            ordered and returns before the result is ready.
+ * Scratch: per-chunk partial sums live in a file-scope device array of
+ * 65536 x 2 doubles (1 MiB) that every device loading the library keeps until
+ * exit. The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current, so make the first call on
+ * each device before any stream capture. Every call shares the array and
+ * fully rewrites the part it reads; calls that overlap on the GPU race on it.
+ * Errors: LSM_EINVAL for bad sizes or null arrays (message in
+ * lsm_last_error(NULL)), LSM_ECUDA if a launch fails. */
+lsm_status lsm_spring_energy_static(int32_t dim, int64_t n, int64_t m, const double *x,
+                                   const int32_t *si, const int32_t *sj, const double *k,
+                                   const double *r0, const uint8_t *broken, double *out,
+                                   void *stream);
+
 #ifdef __cplusplus
 }
 #endif

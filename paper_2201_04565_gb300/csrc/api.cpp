@@ -112,6 +112,8 @@ lsm_status ensure_sample_room(Ctx *c)
 
 }  // namespace
 
+void lsm::set_thread_error(const char *msg) { g_build_err = msg; }
+
 extern "C" {
 
 lsm_status lsm_build_from_image(const lsm_desc *desc, lsm_ctx **out)

@@ -140,6 +140,9 @@ struct Ctx {
     std::map<int64_t, cudaGraphExec_t> graphs;
 };
 
+// api.cpp: message returned by lsm_last_error(NULL) on this thread
+void set_thread_error(const char *msg);
+
 // build.cpp
 bool net_from_image(const lsm_desc &d, HostNet &out, std::string &err);
 bool net_from_desc(const lsm_net_desc &d, HostNet &out, std::string &err);

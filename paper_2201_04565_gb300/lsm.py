@@ -78,6 +78,7 @@ SIGNATURES = [
     ("lsm_observe", C.c_int, [_P, C.POINTER(lsm_sample)]),
     ("lsm_synchronize", C.c_int, [_P]),
     ("lsm_counters", C.c_int, [_P, _P, _P, _P]),
+    ("lsm_spring_energy_static", C.c_int, [_I32, _I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
 ]
 
 _lib = None
@@ -257,6 +258,14 @@ def lsm_counters(h):
     st, su, kl = C.c_int64(), C.c_int64(), C.c_int64()
     _check(load_library().lsm_counters(h, C.byref(st), C.byref(su), C.byref(kl)), h)
     return st.value, su.value, kl.value
+
+
+def lsm_spring_energy_static(dim, n, m, x, si, sj, k, r0, broken, out, stream=None):
+    """Device pointers in, device pointer out (see include/lsm.h); no
+    allocation by the library."""
+    st = load_library().lsm_spring_energy_static(int(dim), int(n), int(m), x, si, sj, k, r0, broken,
+                                                  out, stream)
+    _check(st)
 
 
 class Specimen:
