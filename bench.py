@@ -65,7 +65,8 @@ class ClockSampler:
             os.close(fd)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)  # let the sampler start before the timed region
         except Exception:
             self.proc = None
 
@@ -101,6 +102,50 @@ def algorithmic_bytes(n, m, dim):
     return n * 32 * dim + 10 * m
 
 
+# DRAM traffic of one time-step launch of the fused 2D tile kernel on the
+# 2048 x 2048 workload, from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by precision mode, with the sha1 prefix of the kernel source it was
+# taken on; once the kernel changes, traffic reports null until re-measured.
+NCU_TRAFFIC = {}
+
+# Binding unit of each mode's time-step kernel, from ncu on the same workload
+# (see the profile summaries), for the roofline's "limiter" note.
+LIMITER = {}
+
+
+def _kernel_tag():
+    import hashlib
+    path = os.path.join(ROOT, "paper_2201_04565_gb300", "csrc", "tile2d.cu")
+    with open(path, "rb") as f:
+        return hashlib.sha1(f.read()).hexdigest()[:12]
+
+
+def _build_specimen(lsm, precision, stream):
+    img = inclusion_image(WORKLOAD["nx"], WORKLOAD["ny"], *WORKLOAD["r"], WORKLOAD["frac"], WORKLOAD["seed"])
+    k, e, m = two_phase_materials()
+    return lsm.Specimen.from_image(img, k, e, m, dt=WORKLOAD["dt"], damping=WORKLOAD["damping"],
+                                   precision=precision, stream=stream.cuda_stream)
+
+
+def _time_increments(spec, stream, first_inc, count):
+    """Events around every lsm_step (one increment = nst time steps) on the
+    library's stream; returns (total ms, per-increment ms list)."""
+    import torch
+    nst = WORKLOAD["steps_per_increment"]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(count)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for q in range(count):
+        spec.apply_strain((first_inc + q) * WORKLOAD["eps_inc"])
+        ev[q][0].record(stream)
+        spec.step(nst)
+        ev[q][1].record(stream)
+    t1.record(stream)
+    stream.synchronize()
+    return t0.elapsed_time(t1), [a.elapsed_time(b) for a, b in ev]
+
+
 def run_gpu(args, rank, world):
     import torch
     from paper_2201_04565_gb300 import lsm
@@ -108,20 +153,13 @@ def run_gpu(args, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
-    img = inclusion_image(WORKLOAD["nx"], WORKLOAD["ny"], *WORKLOAD["r"], WORKLOAD["frac"], WORKLOAD["seed"])
-    k, e, m = two_phase_materials()
-    spec = lsm.Specimen.from_image(img, k, e, m, dt=WORKLOAD["dt"], damping=WORKLOAD["damping"],
-                                   precision=args.precision, stream=stream.cuda_stream)
+    spec = _build_specimen(lsm, args.precision, stream)
     nst = WORKLOAD["steps_per_increment"]
-    inc = [0]
-
-    def increment():
-        inc[0] += 1
-        spec.apply_strain(inc[0] * WORKLOAD["eps_inc"])
-        spec.step(nst)
-
+    inc = 0
     for _ in range(args.warmup):
-        increment()
+        inc += 1
+        spec.apply_strain(inc * WORKLOAD["eps_inc"])
+        spec.step(nst)
     spec.synchronize()
     dist = world > 1
     if dist:
@@ -130,24 +168,12 @@ def run_gpu(args, rank, world):
     torch.cuda.synchronize()
     clocks = ClockSampler(dev)
     clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = spec.counters()[2]
-    t_all0 = torch.cuda.Event(enable_timing=True)
-    t_all1 = torch.cuda.Event(enable_timing=True)
-    t_all0.record(stream)
-    for q in range(args.steps):
-        inc[0] += 1
-        spec.apply_strain(inc[0] * WORKLOAD["eps_inc"])
-        ev[q][0].record(stream)
-        spec.step(nst)
-        ev[q][1].record(stream)
-    t_all1.record(stream)
-    stream.synchronize()
+    ms, inc_ms = _time_increments(spec, stream, inc + 1, args.steps)
+    inc += args.steps
     torch.cuda.synchronize()
     launches = spec.counters()[2] - launches0
     clk = clocks.stop()
-    ms = t_all0.elapsed_time(t_all1)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
     if dist:
         import torch.distributed as td
         t = torch.tensor([ms], device="cuda")
@@ -155,46 +181,72 @@ def run_gpu(args, rank, world):
         ms = float(t.item())
         td.barrier()
 
-    # end-to-end through the public API: host strain in, host sample and
-    # broken mask out, every step
-    e2e_steps = max(2, min(args.steps, 5))
+    # end to end through the public API with host buffers: the strain goes in
+    # from the host, the step's stress sample and broken-spring mask come back
+    e2e_steps = max(3, min(args.steps, 10))
     spec.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        inc[0] += 1
-        spec.apply_strain(inc[0] * WORKLOAD["eps_inc"])
+        inc += 1
+        spec.apply_strain(inc * WORKLOAD["eps_inc"])
         spec.step(nst)
         samples = spec.samples()
         mask, _ = spec.broken()
     t1 = time.perf_counter()
     e2e_value = spec.m * nst * e2e_steps * world / (t1 - t0)
-    d2h = mask.nbytes + 64 * len(samples) // max(len(samples), 1)
+    d2h = mask.nbytes + 64  # broken mask + the new sample (the binding copies all samples)
 
     hbm, peak_src = _peaks()
     units = spec.m * nst * args.steps * world
     value = units / (ms * 1e-3)
-    per_step_ms = statistics.mean(step_ms) / nst  # one time step (all its kernels)
+    # one time step = one launch of the fused tile kernel; the increment's
+    # events also cover the sample reduction (one tiny kernel), so this
+    # slightly overstates the kernel's duration
+    per_step_ms = statistics.mean(inc_ms) / nst
     algb = algorithmic_bytes(spec.n, spec.m, spec.dim)
     achieved = algb / (per_step_ms * 1e-3) / 1e9
+    traffic = None
+    if args.precision in NCU_TRAFFIC and NCU_TRAFFIC[args.precision][1] == _kernel_tag():
+        traffic = NCU_TRAFFIC[args.precision][0]
+    dtype = {"exact64": "f64", "fast64": "f64", "f32": "f32 force / f64 state",
+             "df64": "f32x2 (double-float) force / f64 state"}[args.precision]
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"exact64": "f64", "fast64": "f64", "f32": "f32-force/f64-state"}.get(args.precision, args.precision),
-        "data": "synthetic (seeded two-phase inclusion image; paper's specimen files not used)",
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+        "data": "synthetic (seeded two-phase inclusion image; the paper's specimen files are not used)",
         "config": {"workload": WORKLOAD["name"], "image": "%dx%d" % (WORKLOAD["nx"], WORKLOAD["ny"]),
-                   "particles": spec.n, "springs": spec.m, "steps_per_bench_step": nst,
+                   "particles": spec.n, "springs": spec.m, "time_steps_per_bench_step": nst,
                    "dt": WORKLOAD["dt"], "damping": WORKLOAD["damping"], "precision": args.precision,
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (%.0f MB state+springs per time step)" % (algb / 1e6)},
+                   "l2": "inputs larger than L2 (%.0f MB of state and springs per time step)" % (algb / 1e6)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
-                     "algorithmic_bytes_per_time_step": algb, "time_step_ms": per_step_ms,
-                     "peak_source": peak_src},
+                     "frac": achieved / hbm, "traffic": traffic,
+                     "kernel": "k_tile2d (one launch per time step)",
+                     "algorithmic_bytes_per_launch": algb, "launch_ms": per_step_ms,
+                     "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
+                     "limiter": LIMITER.get(args.precision)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8, "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "clocks": clk,
     }
     spec.close()
+
+    if not args.no_variants and world == 1:
+        variants = {}
+        for mode in ("exact64", "fast64", "f32", "df64"):
+            if mode == args.precision:
+                variants[mode] = {"value": value, "time_step_ms": per_step_ms}
+                continue
+            sp = _build_specimen(lsm, mode, stream)
+            for q in range(1, 3):
+                sp.apply_strain(q * WORKLOAD["eps_inc"])
+                sp.step(nst)
+            sp.synchronize()
+            vm, vinc = _time_increments(sp, stream, 3, 5)
+            variants[mode] = {"value": sp.m * nst * 5 / (vm * 1e-3), "time_step_ms": statistics.mean(vinc) / nst}
+            sp.close()
+        out["variants"] = variants
     return out
 
 
@@ -223,11 +275,12 @@ def run_oracle_sample(budget_s=12.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lsm", choices=["lsm", "reference"])
-    ap.add_argument("--precision", default="fast64", choices=["exact64", "fast64", "f32"])
+    ap.add_argument("--precision", default="df64", choices=["exact64", "fast64", "f32", "df64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -42,17 +42,6 @@ lsm_status device_status(Ctx *c)
     return LSM_OK;
 }
 
-// Slot of canonical spring s in the tile path's per-pixel layout:
-// 0 (+1,0), 1 (-1,+1), 2 (0,+1), 3 (+1,+1).
-int tile_slot(const lsm::HostNet &h, int64_t s, int64_t *pixel)
-{
-    const int64_t pi = h.pix[h.si[s]], pj = h.pix[h.sj[s]];
-    const int64_t dx = pj % h.nx - pi % h.nx, dy = pj / h.nx - pi / h.nx;
-    *pixel = pi;
-    if (dy == 0) return 0;
-    return dx < 0 ? 1 : (dx == 0 ? 2 : 3);
-}
-
 lsm_status finish_build(lsm_ctx *c, void *stream, lsm_ctx **out, int path = 0)
 {
     c->tile = path != 1 && c->h.dim == 2 && c->h.nx > 0 && c->h.nphase >= 1 && c->h.nphase <= 8;
@@ -304,10 +293,10 @@ lsm_status lsm_broken_mask(lsm_ctx *c, uint8_t *out, int64_t cap, int64_t *m,
     if (st != LSM_OK) return st;
     unsigned long long fb = 0;
     cudaError_t e = cudaSuccess;
-    std::vector<uint8_t> pm;
     if (c->tile) {
-        pm.resize(c->tnp);
-        e = cudaMemcpyAsync(pm.data(), c->tmask, c->tnp, cudaMemcpyDeviceToHost, c->stream);
+        e = lsm::tile_export(*c, false);
+        if (e == cudaSuccess && c->m)
+            e = cudaMemcpyAsync(out, c->texport, c->m, cudaMemcpyDeviceToHost, c->stream);
     } else if (c->m) {
         e = cudaMemcpyAsync(out, c->state, c->m, cudaMemcpyDeviceToHost, c->stream);
     }
@@ -315,13 +304,6 @@ lsm_status lsm_broken_mask(lsm_ctx *c, uint8_t *out, int64_t cap, int64_t *m,
         e = cudaMemcpyAsync(&fb, c->d_first_break, sizeof(fb), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "broken_mask");
-    if (c->tile) {
-        for (int64_t sp = 0; sp < c->m; sp++) {
-            int64_t g;
-            const int sl = tile_slot(c->h, sp, &g);
-            out[sp] = (uint8_t)((pm[g] >> sl) & 1u);
-        }
-    }
     if (m) *m = c->m;
     if (first_break_step) *first_break_step = fb == ~0ull ? -1 : (int64_t)fb;
     return LSM_OK;
@@ -332,22 +314,15 @@ lsm_status lsm_break_steps(lsm_ctx *c, int64_t *out, int64_t cap)
     if (!c) return fail(nullptr, LSM_EINVAL, "null context");
     if (!out || cap < c->m) return fail(c, LSM_EINVAL, "output buffer smaller than the spring count");
     cudaError_t e = cudaSuccess;
-    std::vector<int64_t> pb;
     if (c->tile) {
-        pb.resize(4 * c->tnp);
-        e = cudaMemcpyAsync(pb.data(), c->tbrk, 4 * c->tnp * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+        e = lsm::tile_export(*c, true);
+        if (e == cudaSuccess && c->m)
+            e = cudaMemcpyAsync(out, c->texport_brk, c->m * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
     } else if (c->m) {
         e = cudaMemcpyAsync(out, c->brk, c->m * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "break_steps");
-    if (c->tile) {
-        for (int64_t sp = 0; sp < c->m; sp++) {
-            int64_t g;
-            const int sl = tile_slot(c->h, sp, &g);
-            out[sp] = pb[(int64_t)sl * c->tnp + g];
-        }
-    }
     return LSM_OK;
 }
 

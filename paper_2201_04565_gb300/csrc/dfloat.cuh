@@ -200,6 +200,22 @@ __device__ __forceinline__ ff ff_add_sloppy(ff a, ff b)
     return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
 
+// a + b for a float b.
+__device__ __forceinline__ ff ff_add_f(ff a, float b)
+{
+    const ff s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+// a / b with a single correction of the float quotient (about 2^-44 relative).
+__device__ __forceinline__ ff ff_div_fast(ff a, ff b)
+{
+    const float rb = __frcp_rn(b.hi);
+    const float q0 = __fmul_rn(a.hi, rb);
+    const ff r = ff_add_sloppy(a, ff_neg(ff_mul_f(b, q0)));
+    return fast_two_sum(q0, __fmul_rn(r.hi, rb));
+}
+
 __device__ __forceinline__ bool ff_gt(ff a, ff b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
 
 __device__ __forceinline__ double ff_to_double(ff a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }

@@ -362,9 +362,12 @@ void free_device(Ctx &c)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *tptrs[] = {c.tx[0], c.tx[1], c.tvh[0], c.tvh[1], c.tvobs, c.tph, c.tmask, c.tbrk, c.tmass,
-                     c.tinvm, c.tdf};
+                     c.tinvm, c.tdf, c.tsbase, c.texport, c.texport_brk};
     for (void *p : tptrs)
         if (p) cudaFree(p);
+    c.tsbase = nullptr;
+    c.texport = nullptr;
+    c.texport_brk = nullptr;
     c.tx[0] = c.tx[1] = c.tvh[0] = c.tvh[1] = c.tvobs = c.tmass = c.tinvm = nullptr;
     c.tdf = nullptr;
     c.tph = c.tmask = nullptr;
@@ -434,12 +437,26 @@ static cudaError_t upload_tile(Ctx &c)
     }
     std::vector<double> mtab(h.nphase, 1.0), itab(h.nphase, 1.0);
     for (int64_t p = 0; p < h.n; p++) mtab[h.phase[h.pix[p]] - 1] = h.mass[p];
-    for (int q = 0; q < h.nphase; q++) itab[q] = 1.0 / mtab[q];
+    itab.assign(4 * h.nphase, 0.0);  // per phase: 1 - dt g/m, dt/m, 1 - dt/2 g/m, dt/2 / m
+    for (int q = 0; q < h.nphase; q++) {
+        const double dt = h.dt, hdt = 0.5 * h.dt, g = h.damping, m = mtab[q];
+        itab[4 * q + 0] = 1.0 - dt * g / m;
+        itab[4 * q + 1] = dt / m;
+        itab[4 * q + 2] = 1.0 - hdt * g / m;
+        itab[4 * q + 3] = hdt / m;
+    }
     // fixed-point scale: |x| stays below 2^(62 - S) for strains up to +300%
     const double extent = 4.0 * (double)(h.nx > h.ny ? h.nx : h.ny) * h.a + 16.0;
     c.fix_S = 61 - (int)std::ceil(std::log2(extent));
     if (c.fix_S > 52) c.fix_S = 52;
     c.a_fix = std::llround(std::ldexp(h.a, c.fix_S));
+    {
+        const double aa = std::ldexp((double)c.a_fix, -c.fix_S);
+        c.o_exact = (double)(float)aa == aa && (double)(float)(aa * aa) == aa * aa &&
+                    (double)(float)(2.0 * aa * aa) == 2.0 * aa * aa && (double)(float)(2.0 * aa) == 2.0 * aa;
+    }
+    std::vector<int64_t> sbase(np, 0);
+    for (int64_t s = h.m - 1; s >= 0; s--) sbase[h.pix[h.si[s]]] = s;
     std::vector<TypeDF> tdf(h.types.size());
     for (size_t q = 0; q < h.types.size(); q++) {
         const SpringType &t = h.types[q];
@@ -462,8 +479,9 @@ static cudaError_t upload_tile(Ctx &c)
     LSM_TRY(dalloc(&c.tmask, np));
     LSM_TRY(dalloc(&c.tbrk, 4 * np));
     LSM_TRY(dalloc(&c.tmass, h.nphase));
-    LSM_TRY(dalloc(&c.tinvm, h.nphase));
+    LSM_TRY(dalloc(&c.tinvm, 4 * h.nphase));
     LSM_TRY(dalloc(&c.tdf, tdf.size()));
+    LSM_TRY(dalloc(&c.tsbase, np));
     LSM_TRY(dalloc(&c.part_s, 2 * c.ntiles));
     LSM_TRY(dalloc(&c.part_p, 4 * c.ntiles));
     LSM_TRY(upload_common(c));
@@ -477,8 +495,9 @@ static cudaError_t upload_tile(Ctx &c)
     LSM_TRY(cudaMemsetAsync(c.tmask, 0, np, st));
     LSM_TRY(cudaMemsetAsync(c.tbrk, 0xff, 4 * np * sizeof(long long), st));
     LSM_TRY(cudaMemcpyAsync(c.tmass, mtab.data(), h.nphase * sizeof(double), cudaMemcpyHostToDevice, st));
-    LSM_TRY(cudaMemcpyAsync(c.tinvm, itab.data(), h.nphase * sizeof(double), cudaMemcpyHostToDevice, st));
+    LSM_TRY(cudaMemcpyAsync(c.tinvm, itab.data(), 4 * h.nphase * sizeof(double), cudaMemcpyHostToDevice, st));
     LSM_TRY(cudaMemcpyAsync(c.tdf, tdf.data(), tdf.size() * sizeof(TypeDF), cudaMemcpyHostToDevice, st));
+    LSM_TRY(cudaMemcpyAsync(c.tsbase, sbase.data(), np * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     c.tcur = 0;
     LSM_TRY(cudaStreamSynchronize(st));
     return cudaSuccess;

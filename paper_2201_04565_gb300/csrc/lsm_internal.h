@@ -126,10 +126,14 @@ struct Ctx {
     uint8_t *tph = nullptr, *tmask = nullptr;
     long long *tbrk = nullptr;            // [4][tnp]
     double *tmass = nullptr;              // per phase
-    double *tinvm = nullptr;              // per phase, 1 / mass
+    double *tinvm = nullptr;              // per phase: 1 - dt g/m, dt/m, 1 - dt/2 g/m, dt/2 / m
     TypeDF *tdf = nullptr;                // double-float spring types
     int fix_S = 40;                       // fixed-point scale of positions
     long long a_fix = 0;                  // lattice spacing * 2^fix_S
+    bool o_exact = false;                 // lattice vectors and |o|^2 exact as floats
+    int64_t *tsbase = nullptr;            // [tnp] canonical index of each pixel's first spring
+    uint8_t *texport = nullptr;           // [m] staging for canonical-order exports
+    long long *texport_brk = nullptr;     // [m] staging for break steps
     int tcur = 0;
     int64_t ntiles = 0;
 
@@ -161,6 +165,7 @@ cudaError_t tile_init_accel(Ctx &c);
 cudaError_t tile_observe(Ctx &c);
 cudaError_t tile_apply_strain(Ctx &c, double eps_old, double eps_new);
 int64_t tile_count(const Ctx &c);
+cudaError_t tile_export(Ctx &c, bool steps);  // canonical-order mask or break steps into staging
 const char *last_fail_site();  // source text of the CUDA call that failed last
 
 }  // namespace lsm

@@ -70,6 +70,12 @@ __device__ __forceinline__ double bmax(double v, double *sh)
 
 enum { T_STEP = 0, T_INIT = 1, T_OBSERVE = 2 };
 
+// Per-phase integration coefficients: vh' = c1 vh + c2 F is vh + dt (F - g vh)/m,
+// and c1h, c2h the same for a half step.
+struct Coef4 {
+    double c1, c2, c1h, c2h;
+};
+
 struct TileArgs {
     int nx, ny, nphase;
     int64_t np;
@@ -81,7 +87,7 @@ struct TileArgs {
     const SpringType *types;
     const TypeDF *tdf;         // double-float copies of the spring types
     const double *mass;        // per phase
-    const double *inv_mass;    // per phase
+    const Coef4 *coef;         // per phase integration coefficients
     int S;                     // fixed-point scale: positions as x * 2^S
     long long a_fix;           // lattice spacing in fixed point
     float p48, p24, p0;        // 2^(48-S), 2^(24-S), 2^-S
@@ -98,7 +104,7 @@ struct TileArgs {
 // Force on the lower endpoint of one spring (rp -> rq, forward slot), with
 // the break test. Writes the force into sf; OWNER adds the sample sums and
 // records a break (only the tile owning the lower endpoint does).
-template <int PREC, int MODE, bool SAMPLE, bool OWNER, int NR, int NS, typename FT>
+template <int PREC, int MODE, bool SAMPLE, bool OWNER, bool ODY, int NR, int NS, typename FT>
 __device__ __forceinline__ void eval_spring(const TileArgs &A, int rp, int rq, int slot, const double *sx,
                                             const double *sy, const long long *sxf, const long long *syf,
                                             const uint8_t *sph, const uint8_t *smk, FT *sf,
@@ -174,7 +180,29 @@ __device__ __forceinline__ void eval_spring(const TileArgs &A, int rp, int rq, i
                         w_acc += (double)dxf * (double)fx;
                     }
                 }
-            } else {  // LSM_PREC_DF
+            } else if constexpr (ODY) {  // LSM_PREC_DF, lattice vectors exact in float
+                const ff ex = fix_to_ff_i2f(exf, A.p48, A.p24, A.p0);
+                const ff ey = fix_to_ff_i2f(eyf, A.p48, A.p24, A.p0);
+                const float ox = soff[slot][0].hi, oy = soff[slot][1].hi, oo = soff[slot][2].hi;
+                ff num = ff_add_sloppy(ff_mul(ff_add_f(ex, 2.0f * ox), ex), ff_mul(ff_add_f(ey, 2.0f * oy), ey));
+                num = fast_two_sum(num.hi, __fadd_rn(num.lo, t.cor.hi));
+                const ff r2 = ff_add_f(num, oo);
+                if (MODE == T_STEP && ff_gt(r2, t.rc2)) {
+                    brk_now = true;
+                } else {
+                    const ff r = ff_sqrt(r2);
+                    const ff rr0 = ff_add_sloppy(r, t.r0);
+                    const ff c = ff_mul(t.k, ff_div_fast(num, ff_mul(r, rr0)));  // k (r - r0) / r
+                    const ff dxf = ff_add_f(ex, ox), dyf = ff_add_f(ey, oy);
+                    fx = ff_mul(c, dxf);
+                    fy = ff_mul(c, dyf);
+                    if (SAMPLE && OWNER) {
+                        const double st = ff_to_double(ff_div(num, rr0));
+                        u_acc += 0.5 * ff_to_double(t.k) * st * st;
+                        w_acc += ff_to_double(dxf) * ff_to_double(fx);
+                    }
+                }
+            } else {  // LSM_PREC_DF, general lattice spacing
                 const ff ex = fix_to_ff_i2f(exf, A.p48, A.p24, A.p0);
                 const ff ey = fix_to_ff_i2f(eyf, A.p48, A.p24, A.p0);
                 const ff ox = soff[slot][0], oy = soff[slot][1];
@@ -252,7 +280,7 @@ __device__ __forceinline__ void load_pixel(const TileArgs &A, int x0, int y0, in
 }
 
 // One CTA = one 32 x TY tile; warp w handles tile rows w, w + 8, ...
-template <int TX, int TY, int PREC, int MODE, bool SAMPLE>
+template <int TX, int TY, int PREC, int MODE, bool SAMPLE, bool ODY>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_tile2d(TileArgs A)
 {
@@ -278,7 +306,8 @@ k_tile2d(TileArgs A)
     __shared__ SpringType stab[128];
     __shared__ TypeDF sdf[FIX ? 128 : 1];
     __shared__ ff soff[4][3];  // per slot: o_x, o_y, |o|^2 as double-floats
-    __shared__ double smass[8], sinvm[8];
+    __shared__ double smass[8];
+    __shared__ Coef4 scoef[8];  // per phase: c1, c2, c1h, c2h (vh' = c1 vh + c2 F)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -290,7 +319,7 @@ k_tile2d(TileArgs A)
     }
     if (tid < A.nphase) {
         smass[tid] = A.mass[tid];
-        sinvm[tid] = A.inv_mass[tid];
+        scoef[tid] = A.coef[tid];
     }
     if (FIX && tid < 4) {
         const int dx = tid == 0 ? 1 : (tid == 1 ? -1 : (tid == 2 ? 0 : 1));
@@ -322,7 +351,7 @@ k_tile2d(TileArgs A)
         const int64_t g = (int64_t)(y0 + ry - 1) * A.nx + (x0 + lane);
 #pragma unroll
         for (int slot = 0; slot < 4; slot++)
-            eval_spring<PREC, MODE, SAMPLE, true, NR, NS>(A, rp, rp + dq[slot], slot, sx, sy, sxf, syf, sph, smk,
+            eval_spring<PREC, MODE, SAMPLE, true, ODY, NR, NS>(A, rp, rp + dq[slot], slot, sx, sy, sxf, syf, sph, smk,
                                                           sf, stab, sdf, soff, snew, g, step_now, w_acc, u_acc);
     }
     // 2b. springs from halo sources into the tile (also evaluated, with the
@@ -343,7 +372,7 @@ k_tile2d(TileArgs A)
             slot = 1; rx = TX + 1; ry = 1 + (t - 3 * TX - 2 * TY + 1);
         }
         const int rp = ry * RX + rx;
-        eval_spring<PREC, MODE, SAMPLE, false, NR, NS>(A, rp, rp + dq[slot], slot, sx, sy, sxf, syf, sph, smk, sf,
+        eval_spring<PREC, MODE, SAMPLE, false, ODY, NR, NS>(A, rp, rp + dq[slot], slot, sx, sy, sxf, syf, sph, smk, sf,
                                                        stab, sdf, soff, snew, 0, step_now, w_acc, u_acc);
     }
     __syncthreads();
@@ -426,16 +455,16 @@ k_tile2d(TileArgs A)
                 continue;
             }
             const double vh = MODE == T_INIT ? A.v_obs[q] : A.vh_in[q];
-            double acc, vn, vh2;
+            double vn, vh2;
             if constexpr (PREC == LSM_PREC_EXACT64) {
-                acc = dv(sb(F[c], ml(A.gamma, vh)), m);
+                const double acc = dv(sb(F[c], ml(A.gamma, vh)), m);
                 vn = ad(vh, ml(A.hdt, acc));
                 vh2 = ad(vn, ml(A.hdt, acc));
             } else {
-                const double im = sinvm[ph];
-                acc = fma(-A.gamma * im, vh, F[c] * im);
-                vn = fma(A.hdt, acc, vh);
-                vh2 = fma(A.dt, acc, vh);
+                // vh + t (F - gamma vh) / m = (1 - t gamma / m) vh + (t / m) F
+                const Coef4 k4 = scoef[ph];
+                vn = fma(k4.c2h, F[c], k4.c1h * vh);
+                vh2 = fma(k4.c2, F[c], k4.c1 * vh);
             }
             if (MODE == T_INIT) {
                 // vh = v + dt/2 a(t) with a from the forces at the current x
@@ -495,6 +524,48 @@ __global__ void k_tile_strain(int nx, int ny, int64_t np, double *x, double *vh,
     x[g] = xp;
 }
 
+// Pixel-grid broken flags / break steps -> canonical spring order. sbase[g]
+// is the canonical index of pixel g's first forward spring; its springs follow
+// in slot order, which is the canonical order of their upper endpoints.
+__global__ void k_tile_export(int nx, int ny, int64_t np, const uint8_t *__restrict__ phase,
+                              const uint8_t *__restrict__ mask, const long long *__restrict__ brk,
+                              const int64_t *__restrict__ sbase, uint8_t *__restrict__ out_mask,
+                              long long *__restrict__ out_brk)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= np || !phase[g]) return;
+    const int gx = (int)(g % nx), gy = (int)(g / nx);
+    int64_t b = sbase[g];
+    const uint8_t mk = mask[g];
+#pragma unroll
+    for (int slot = 0; slot < 4; slot++) {
+        const int dx = slot == 0 ? 1 : (slot == 1 ? -1 : (slot == 2 ? 0 : 1));
+        const int dy = slot == 0 ? 0 : 1;
+        const int qx = gx + dx, qy = gy + dy;
+        if (qx < 0 || qx >= nx || qy >= ny || !phase[(int64_t)qy * nx + qx]) continue;
+        if (out_mask) out_mask[b] = (mk >> slot) & 1u;
+        if (out_brk) out_brk[b] = brk[(int64_t)slot * np + g];
+        b++;
+    }
+}
+
+cudaError_t tile_export(Ctx &c, bool steps)
+{
+    if (c.m == 0) return cudaSuccess;
+    if (!c.texport) {
+        cudaError_t e = cudaMalloc((void **)&c.texport, c.m);
+        if (e != cudaSuccess) return e;
+    }
+    if (steps && !c.texport_brk) {
+        cudaError_t e = cudaMalloc((void **)&c.texport_brk, c.m * sizeof(long long));
+        if (e != cudaSuccess) return e;
+    }
+    const unsigned g = (unsigned)((c.tnp + 255) / 256);
+    k_tile_export<<<g, 256, 0, c.stream>>>(c.h.nx, c.h.ny, c.tnp, c.tph, c.tmask, c.tbrk, c.tsbase,
+                                           steps ? nullptr : c.texport, steps ? c.texport_brk : nullptr);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ host
 
 template <int TX, int TY>
@@ -527,7 +598,7 @@ static TileArgs tile_args(Ctx &c)
     A.types = c.types;
     A.tdf = c.tdf;
     A.mass = c.tmass;
-    A.inv_mass = c.tinvm;
+    A.coef = (const Coef4 *)c.tinvm;
     A.S = c.fix_S;
     A.a_fix = c.a_fix;
     A.p48 = ldexpf(1.0f, 48 - c.fix_S);
@@ -549,10 +620,10 @@ static TileArgs tile_args(Ctx &c)
     return A;
 }
 
-template <int PREC, int MODE, bool SAMPLE>
+template <int PREC, int MODE, bool SAMPLE, bool ODY = false>
 static cudaError_t launch_tile(Ctx &c, TileArgs A)
 {
-    auto kern = k_tile2d<TILE_X, TILE_Y, PREC, MODE, SAMPLE>;
+    auto kern = k_tile2d<TILE_X, TILE_Y, PREC, MODE, SAMPLE, ODY>;
     const size_t smem = tile_smem<TILE_X, TILE_Y>(PREC);
     static bool configured = false;  // per template instance
     if (!configured) {
@@ -571,7 +642,9 @@ static cudaError_t launch_tile_prec(Ctx &c, TileArgs A)
     switch (c.h.precision) {
     case LSM_PREC_FAST64: return launch_tile<LSM_PREC_FAST64, MODE, SAMPLE>(c, A);
     case LSM_PREC_F32: return launch_tile<LSM_PREC_F32, MODE, SAMPLE>(c, A);
-    case LSM_PREC_DF: return launch_tile<LSM_PREC_DF, MODE, SAMPLE>(c, A);
+    case LSM_PREC_DF:
+        return c.o_exact ? launch_tile<LSM_PREC_DF, MODE, SAMPLE, true>(c, A)
+                         : launch_tile<LSM_PREC_DF, MODE, SAMPLE, false>(c, A);
     default: return launch_tile<LSM_PREC_EXACT64, MODE, SAMPLE>(c, A);
     }
 }

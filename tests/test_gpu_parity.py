@@ -262,3 +262,16 @@ def test_tile_and_spring_list_paths_agree_bitwise(L):
         outs.append((g.state(), g.broken()))
     assert np.array_equal(outs[0][0][0], outs[1][0][0])
     assert np.array_equal(outs[0][1][0], outs[1][1][0])
+
+
+@pytest.mark.parametrize("a", [1.3, 0.5])
+def test_df64_general_lattice_spacing(oracle_mod, L, a):
+    """df64 with a lattice spacing whose lattice vectors are not (1.3) or are
+    (0.5) exact floats: both double-float branches against the oracle."""
+    img = inclusion_image(40, 32, 2.0, 5.0, 0.3, 8)
+    o, g = _pair(oracle_mod, L, img, two_phase_materials(), precision="df64", a=a)
+    _run_schedule(o, g, 30, 20, 2e-3)
+    xg, _ = g.state()
+    xo, _, _ = o.state()
+    assert _rel(xg, xo) <= 1e-10
+    assert np.array_equal(g.broken()[0], o.broken()[0])
