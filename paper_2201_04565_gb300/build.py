@@ -17,7 +17,7 @@ LIB = os.path.join(HERE, "liblsm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 SOURCES = ["kernels.cu", "batch.cu", "tile2d.cu", "static_scratch.cu", "nn.cu", "build.cpp", "api.cpp"]
-HEADERS = ["lsm_internal.h", "dfloat.cuh", "nn_internal.h"]
+HEADERS = ["lsm_internal.h", "dfloat.cuh", "tile_body.cuh", "nn_internal.h"]
 
 
 def _nvcc():
@@ -45,7 +45,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     inc = os.path.join(os.path.dirname(HERE), "include")
-    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(inc, "lsm.h")]
+    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(inc, q) for q in os.listdir(inc)]
     procs, objs = [], []
     for src in _sources():
         path = os.path.join(CSRC, src)

@@ -20,488 +20,20 @@
 //
 // Precision modes: EXACT64 performs the same correctly rounded operations in
 // the same order as the sequential FP64 definition (bit-identical state);
-// FAST64 uses fused multiply-add and a reciprocal square root; F32 forms the
-// spring vector in FP64 and evaluates the force in FP32 from the small
-// deviation from the lattice vector, gathering in FP32 and integrating in FP64.
-#include <cuda_runtime.h>
-
-#include <cmath>
-#include <type_traits>
-
-#include "dfloat.cuh"
-#include "lsm_internal.h"
+// FAST64 uses fused multiply-add and a reciprocal square root; F32 and DF form
+// the spring vector exactly from 64-bit fixed-point positions and evaluate the
+// force in single precision or in double-float arithmetic, integrating in FP64.
+#include "tile_body.cuh"
 
 namespace lsm {
 
-namespace {
-
-constexpr int TILE_THREADS = 256;
-
-__device__ __forceinline__ double ad(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ double sb(double a, double b) { return __dsub_rn(a, b); }
-__device__ __forceinline__ double ml(double a, double b) { return __dmul_rn(a, b); }
-__device__ __forceinline__ double dv(double a, double b) { return __ddiv_rn(a, b); }
-
-__device__ __forceinline__ double bsum(double v, double *sh)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int q = 0; q < TILE_THREADS / 32; q++) t += sh[q];
-    return t;
-}
-
-__device__ __forceinline__ double bmax(double v, double *sh)
-{
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int q = 0; q < TILE_THREADS / 32; q++) t = fmax(t, sh[q]);
-    return t;
-}
-
-}  // namespace
-
-enum { T_STEP = 0, T_INIT = 1, T_OBSERVE = 2 };
-
-// Per-phase integration coefficients: vh' = c1 vh + c2 F is vh + dt (F - g vh)/m,
-// and c1h, c2h the same for a half step.
-struct Coef4 {
-    double c1, c2, c1h, c2h;
-};
-
-struct TileArgs {
-    int nx, ny, nphase;
-    int64_t np;
-    const double *x_in, *vh_in;
-    double *x_out, *vh_out, *v_obs;
-    const uint8_t *phase;
-    uint8_t *mask;
-    long long *brk;  // [4][np]
-    const SpringType *types;
-    const TypeDF *tdf;         // double-float copies of the spring types
-    const double *mass;        // per phase
-    const Coef4 *coef;         // per phase integration coefficients
-    int S;                     // fixed-point scale: positions as x * 2^S
-    long long a_fix;           // lattice spacing in fixed point
-    float p48, p24, p0;        // 2^(48-S), 2^(24-S), 2^-S
-    double dt, hdt, gamma, a;
-    int grip_mode;
-    const long long *d_step;  // steps completed before this graph launch
-    int64_t t_off;            // index of this step within the launch
-    unsigned long long *first_break, *nbroken;
-    int *status;
-    double *part_s, *part_p;
-    int64_t ntiles;
-};
-
-// Force on the lower endpoint of one spring (rp -> rq, forward slot), with
-// the break test. Writes the force into sf; OWNER adds the sample sums and
-// records a break (only the tile owning the lower endpoint does).
-template <int PREC, int MODE, bool SAMPLE, bool OWNER, bool ODY, int NR, int NS, typename FT>
-__device__ __forceinline__ void eval_spring(const TileArgs &A, int rp, int rq, int slot, const double *sx,
-                                            const double *sy, const long long *sxf, const long long *syf,
-                                            const uint8_t *sph, const uint8_t *smk, FT *sf,
-                                            const SpringType *stab, const TypeDF *sdf, const ff (*soff)[3],
-                                            int *snew, int64_t gsrc, long long step_now, double &w_acc,
-                                            double &u_acc)
-{
-    FT fx{}, fy{};
-    const uint8_t pp = sph[rp], pq = sph[rq];
-    const uint8_t mk = smk[rp];
-    if (pp && pq && !((mk >> slot) & 1)) {
-        const int ti = (((pp - 1) * A.nphase) + (pq - 1)) * 2 + (slot & 1);
-        bool brk_now = false;
-        if constexpr (PREC == LSM_PREC_EXACT64) {
-            const SpringType t = stab[ti];
-            const double ddx = sb(sx[rq], sx[rp]), ddy = sb(sy[rq], sy[rp]);
-            const double r2 = ad(ml(ddx, ddx), ml(ddy, ddy));
-            if (MODE == T_STEP && r2 > t.rc2) {
-                brk_now = true;
-            } else {
-                const double r = __dsqrt_rn(r2);
-                const double c = dv(ml(t.k, sb(r, t.r0)), r);
-                fx = ml(c, ddx);
-                fy = ml(c, ddy);
-                if (SAMPLE && OWNER) {
-                    const double st = sb(r, t.r0);
-                    u_acc += ml(ml(ml(0.5, t.k), st), st);
-                    w_acc += ml(ddx, ml(c, ddx));
-                }
-            }
-        } else if constexpr (PREC == LSM_PREC_FAST64) {
-            const SpringType t = stab[ti];
-            const double ddx = sx[rq] - sx[rp], ddy = sy[rq] - sy[rp];
-            const double r2 = fma(ddx, ddx, ddy * ddy);
-            if (MODE == T_STEP && r2 > t.rc2) {
-                brk_now = true;
-            } else {
-                const double ir = rsqrt(r2);
-                const double c = fma(-t.kr0, ir, t.k);
-                fx = c * ddx;
-                fy = c * ddy;
-                if (SAMPLE && OWNER) {
-                    const double st = fma(r2, ir, -t.r0);
-                    u_acc += 0.5 * t.k * st * st;
-                    w_acc += ddx * fx;
-                }
-            }
-        } else {
-            // exact spring vector d = o + e from the fixed-point positions; e
-            // is the deviation from the lattice vector o, so
-            // r^2 - |o|^2 = (2 o + e).e carries no cancellation
-            const TypeDF t = sdf[ti];
-            const int dx = slot == 0 ? 1 : (slot == 1 ? -1 : (slot == 2 ? 0 : 1));
-            const int dy = slot == 0 ? 0 : 1;
-            const long long exf = sxf[rq] - sxf[rp] - (long long)dx * A.a_fix;
-            const long long eyf = syf[rq] - syf[rp] - (long long)dy * A.a_fix;
-            if constexpr (PREC == LSM_PREC_F32) {
-                const float ex = fix_to_float_i2f(exf, A.p24, A.p0), ey = fix_to_float_i2f(eyf, A.p24, A.p0);
-                const float ox = soff[slot][0].hi, oy = soff[slot][1].hi;
-                const float dxf = ox + ex, dyf = oy + ey;
-                const float num = fmaf(2.0f * ox + ex, ex, fmaf(2.0f * oy + ey, ey, t.cor.hi));
-                const float r2f = soff[slot][2].hi + num;
-                if (MODE == T_STEP && r2f > t.rc2.hi) {
-                    brk_now = true;
-                } else {
-                    const float ir = rsqrtf(r2f);
-                    const float st = __fdividef(num, fmaf(r2f, ir, t.r0.hi));  // r - r0
-                    const float c = t.k.hi * st * ir;
-                    fx = c * dxf;
-                    fy = c * dyf;
-                    if (SAMPLE && OWNER) {
-                        u_acc += 0.5 * (double)t.k.hi * (double)st * (double)st;
-                        w_acc += (double)dxf * (double)fx;
-                    }
-                }
-            } else if constexpr (ODY) {  // LSM_PREC_DF, lattice vectors exact in float
-                const ff ex = fix_to_ff_i2f(exf, A.p48, A.p24, A.p0);
-                const ff ey = fix_to_ff_i2f(eyf, A.p48, A.p24, A.p0);
-                const float ox = soff[slot][0].hi, oy = soff[slot][1].hi, oo = soff[slot][2].hi;
-                ff num = ff_add_sloppy(ff_mul(ff_add_f(ex, 2.0f * ox), ex), ff_mul(ff_add_f(ey, 2.0f * oy), ey));
-                num = fast_two_sum(num.hi, __fadd_rn(num.lo, t.cor.hi));
-                const ff r2 = ff_add_f(num, oo);
-                if (MODE == T_STEP && ff_gt(r2, t.rc2)) {
-                    brk_now = true;
-                } else {
-                    const ff r = ff_sqrt(r2);
-                    const ff rr0 = ff_add_sloppy(r, t.r0);
-                    const ff c = ff_mul(t.k, ff_div_fast(num, ff_mul(r, rr0)));  // k (r - r0) / r
-                    const ff dxf = ff_add_f(ex, ox), dyf = ff_add_f(ey, oy);
-                    fx = ff_mul(c, dxf);
-                    fy = ff_mul(c, dyf);
-                    if (SAMPLE && OWNER) {
-                        const double st = ff_to_double(ff_div(num, rr0));
-                        u_acc += 0.5 * ff_to_double(t.k) * st * st;
-                        w_acc += ff_to_double(dxf) * ff_to_double(fx);
-                    }
-                }
-            } else {  // LSM_PREC_DF, general lattice spacing
-                const ff ex = fix_to_ff_i2f(exf, A.p48, A.p24, A.p0);
-                const ff ey = fix_to_ff_i2f(eyf, A.p48, A.p24, A.p0);
-                const ff ox = soff[slot][0], oy = soff[slot][1];
-                const ff dxf = ff_add(ox, ex), dyf = ff_add(oy, ey);
-                const ff num = ff_add(ff_add(ff_mul(ff_add(ff_add(ox, ox), ex), ex),
-                                             ff_mul(ff_add(ff_add(oy, oy), ey), ey)), t.cor);
-                const ff r2 = ff_add(soff[slot][2], num);
-                if (MODE == T_STEP && ff_gt(r2, t.rc2)) {
-                    brk_now = true;
-                } else {
-                    const ff r = ff_sqrt(r2);
-                    const ff den = ff_mul(r, ff_add(r, t.r0));
-                    const ff c = ff_mul(t.k, ff_div(num, den));  // k (r - r0) / r
-                    fx = ff_mul(c, dxf);
-                    fy = ff_mul(c, dyf);
-                    if (SAMPLE && OWNER) {
-                        const double st = ff_to_double(ff_div(num, ff_add(r, t.r0)));
-                        u_acc += 0.5 * ff_to_double(t.k) * st * st;
-                        w_acc += ff_to_double(dxf) * ff_to_double(fx);
-                    }
-                }
-            }
-        }
-        if (OWNER && brk_now) {
-            atomicOr(&snew[rp], 1 << slot);
-            A.brk[(int64_t)slot * A.np + gsrc] = step_now;
-            atomicMin(A.first_break, (unsigned long long)step_now);
-            atomicAdd(A.nbroken, 1ull);
-        }
-    }
-    sf[(0 * 4 + slot) * NS + rp] = fx;
-    sf[(1 * 4 + slot) * NS + rp] = fy;
-}
-
-// Region pixel (rx, ry) -> shared memory: phase, broken mask, positions
-// drifted by dt vh (step mode), fixed-point copies.
-template <int PREC, int MODE, int RX>
-__device__ __forceinline__ void load_pixel(const TileArgs &A, int x0, int y0, int rx, int ry, double *sx,
-                                           double *sy, long long *sxf, long long *syf, uint8_t *sph,
-                                           uint8_t *smk, bool &over)
-{
-    constexpr bool FIX = PREC == LSM_PREC_F32 || PREC == LSM_PREC_DF;
-    const int gx = x0 - 1 + rx, gy = y0 - 1 + ry;
-    const int e = ry * RX + rx;
-    uint8_t ph = 0, mk = 0;
-    double px = 0.0, py = 0.0;
-    if (gx >= 0 && gx < A.nx && gy >= 0 && gy < A.ny) {
-        const int64_t g = (int64_t)gy * A.nx + gx;
-        ph = A.phase[g];
-        if (ph) {
-            mk = A.mask[g];
-            px = A.x_in[g];
-            py = A.x_in[A.np + g];
-            if (MODE == T_STEP) {
-                const bool grip = gx == 0 || gx == A.nx - 1;
-                if (!grip) {
-                    if constexpr (PREC == LSM_PREC_EXACT64) px = ad(px, ml(A.dt, A.vh_in[g]));
-                    else px = fma(A.dt, A.vh_in[g], px);
-                }
-                if (!(grip && A.grip_mode == 1)) {
-                    if constexpr (PREC == LSM_PREC_EXACT64) py = ad(py, ml(A.dt, A.vh_in[A.np + g]));
-                    else py = fma(A.dt, A.vh_in[A.np + g], py);
-                }
-            }
-        }
-    }
-    sx[e] = px;
-    sy[e] = py;
-    if constexpr (FIX) {
-        sxf[e] = dbl_to_fix(px, A.S, over);
-        syf[e] = dbl_to_fix(py, A.S, over);
-    }
-    sph[e] = ph;
-    smk[e] = mk;
-}
-
-// One CTA = one 32 x TY tile; warp w handles tile rows w, w + 8, ...
 template <int TX, int TY, int PREC, int MODE, bool SAMPLE, bool ODY>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_tile2d(TileArgs A)
 {
-    static_assert(TX == 32, "one warp per tile row");
-    constexpr int RX = TX + 2, RY = TY + 2;   // region = tile + 1-pixel halo
-    constexpr int NR = RX * RY;
-    constexpr int NS = RX * (TY + 1);         // spring sources: region rows 0..TY
-    constexpr int NW = TILE_THREADS / 32;
-    constexpr bool FIX = PREC == LSM_PREC_F32 || PREC == LSM_PREC_DF;
-    using FT = typename std::conditional<PREC == LSM_PREC_F32, float,
-               typename std::conditional<PREC == LSM_PREC_DF, ff, double>::type>::type;
-
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *sx = (double *)smem_raw;               // [NR] drifted positions
-    double *sy = sx + NR;                          // [NR]
-    long long *sxf = (long long *)(sy + NR);       // [NR] fixed point (FIX modes only)
-    long long *syf = sxf + (FIX ? NR : 0);         // [NR]
-    FT *sf = (FT *)(syf + (FIX ? NR : 0));         // [2][4][NS] force on the lower end
-    int *snew = (int *)(sf + 8 * NS);              // [NS] springs broken in this step
-    uint8_t *sph = (uint8_t *)(snew + NS);         // [NR]
-    uint8_t *smk = sph + NR;                       // [NR]
-    __shared__ double sred[NW];
-    __shared__ SpringType stab[128];
-    __shared__ TypeDF sdf[FIX ? 128 : 1];
-    __shared__ ff soff[4][3];  // per slot: o_x, o_y, |o|^2 as double-floats
-    __shared__ double smass[8];
-    __shared__ Coef4 scoef[8];  // per phase: c1, c2, c1h, c2h (vh' = c1 vh + c2 F)
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int64_t tile_id = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
-    const int nt = 2 * A.nphase * A.nphase;
-    for (int q = tid; q < nt; q += TILE_THREADS) {
-        stab[q] = A.types[q];
-        if constexpr (FIX) sdf[q] = A.tdf[q];
-    }
-    if (tid < A.nphase) {
-        smass[tid] = A.mass[tid];
-        scoef[tid] = A.coef[tid];
-    }
-    if (FIX && tid < 4) {
-        const int dx = tid == 0 ? 1 : (tid == 1 ? -1 : (tid == 2 ? 0 : 1));
-        const int dy = tid == 0 ? 0 : 1;
-        const ff ox = fix_to_ff((long long)dx * A.a_fix, A.S), oy = fix_to_ff((long long)dy * A.a_fix, A.S);
-        soff[tid][0] = ox;
-        soff[tid][1] = oy;
-        soff[tid][2] = ff_add(ff_mul(ox, ox), ff_mul(oy, oy));
-    }
-    const long long step_now = MODE == T_STEP ? *A.d_step + A.t_off : 0;
-
-    // 1. region load (+ drift): tile columns by lanes, halo columns apart
-    bool over = false;
-    for (int ry = warp; ry < RY; ry += NW)
-        load_pixel<PREC, MODE, RX>(A, x0, y0, lane + 1, ry, sx, sy, sxf, syf, sph, smk, over);
-    for (int q = tid; q < 2 * RY; q += TILE_THREADS)
-        load_pixel<PREC, MODE, RX>(A, x0, y0, (q & 1) ? TX + 1 : 0, q >> 1, sx, sy, sxf, syf, sph, smk, over);
-    if (FIX && over) atomicOr(A.status, 2);
-    for (int e = tid; e < NS; e += TILE_THREADS) snew[e] = 0;
-    __syncthreads();
-
-    // 2a. forward springs of the owned particles
-    double w_acc = 0.0, u_acc = 0.0;
-    constexpr int dq[4] = {1, RX - 1, RX, RX + 1};
-#pragma unroll
-    for (int k = 0; k < TY / NW; k++) {
-        const int ry = warp + k * NW + 1, rx = lane + 1;
-        const int rp = ry * RX + rx;
-        const int64_t g = (int64_t)(y0 + ry - 1) * A.nx + (x0 + lane);
-#pragma unroll
-        for (int slot = 0; slot < 4; slot++)
-            eval_spring<PREC, MODE, SAMPLE, true, ODY, NR, NS>(A, rp, rp + dq[slot], slot, sx, sy, sxf, syf, sph, smk,
-                                                          sf, stab, sdf, soff, snew, g, step_now, w_acc, u_acc);
-    }
-    // 2b. springs from halo sources into the tile (also evaluated, with the
-    // same result, by the tile that owns their lower endpoint)
-    constexpr int NH = 3 * TX + 3 * TY - 2;
-    for (int t = tid; t < NH; t += TILE_THREADS) {
-        int rx, ry, slot;
-        if (t < 3 * TX) {  // halo row above the tile, slots 1..3
-            slot = 1 + t / TX;
-            const int j = t % TX;
-            rx = slot == 2 ? j + 1 : (slot == 3 ? j : j + 2);
-            ry = 0;
-        } else if (t < 3 * TX + TY) {  // left halo column, slot 0
-            slot = 0; rx = 0; ry = 1 + (t - 3 * TX);
-        } else if (t < 3 * TX + 2 * TY - 1) {  // left halo column, slot 3
-            slot = 3; rx = 0; ry = 1 + (t - 3 * TX - TY);
-        } else {  // right halo column, slot 1
-            slot = 1; rx = TX + 1; ry = 1 + (t - 3 * TX - 2 * TY + 1);
-        }
-        const int rp = ry * RX + rx;
-        eval_spring<PREC, MODE, SAMPLE, false, ODY, NR, NS>(A, rp, rp + dq[slot], slot, sx, sy, sxf, syf, sph, smk, sf,
-                                                       stab, sdf, soff, snew, 0, step_now, w_acc, u_acc);
-    }
-    __syncthreads();
-
-    // 3. gather + integrate the owned particles
-    double mvx2 = 0.0, ke = 0.0, react = 0.0, res = 0.0;
-    bool bad = false;
-#pragma unroll
-    for (int k = 0; k < TY / NW; k++) {
-        const int ly = warp + k * NW;
-        const int gx = x0 + lane, gy = y0 + ly;
-        const int rx = lane + 1, ry = ly + 1;
-        const int rp = ry * RX + rx;
-        if (gx >= A.nx || gy >= A.ny || !sph[rp]) continue;
-        const int64_t g = (int64_t)gy * A.nx + gx;
-        // incoming springs come from p - o for slots 3, 2, 1, 0 (ascending
-        // source index), then the outgoing ones in slot order
-        const int s3 = rp - RX - 1, s2 = rp - RX, s1 = rp - RX + 1, s0 = rp - 1;
-        double F[2];
-        if constexpr (PREC == LSM_PREC_EXACT64) {
-#pragma unroll
-            for (int c = 0; c < 2; c++) {
-                double acc = 0.0;
-                acc = sb(acc, sf[(c * 4 + 3) * NS + s3]);
-                acc = sb(acc, sf[(c * 4 + 2) * NS + s2]);
-                acc = sb(acc, sf[(c * 4 + 1) * NS + s1]);
-                acc = sb(acc, sf[(c * 4 + 0) * NS + s0]);
-#pragma unroll
-                for (int sl = 0; sl < 4; sl++) acc = ad(acc, sf[(c * 4 + sl) * NS + rp]);
-                F[c] = acc;
-            }
-        } else if constexpr (PREC == LSM_PREC_DF) {
-#pragma unroll
-            for (int c = 0; c < 2; c++) {
-                ff acc = ff_neg(sf[(c * 4 + 3) * NS + s3]);
-                acc = ff_add_sloppy(acc, ff_neg(sf[(c * 4 + 2) * NS + s2]));
-                acc = ff_add_sloppy(acc, ff_neg(sf[(c * 4 + 1) * NS + s1]));
-                acc = ff_add_sloppy(acc, ff_neg(sf[(c * 4 + 0) * NS + s0]));
-#pragma unroll
-                for (int sl = 0; sl < 4; sl++) acc = ff_add_sloppy(acc, sf[(c * 4 + sl) * NS + rp]);
-                F[c] = ff_to_double(acc);
-            }
-        } else {
-#pragma unroll
-            for (int c = 0; c < 2; c++) {
-                FT acc = sf[(c * 4 + 0) * NS + rp] - sf[(c * 4 + 3) * NS + s3];
-                acc += sf[(c * 4 + 1) * NS + rp] - sf[(c * 4 + 2) * NS + s2];
-                acc += sf[(c * 4 + 2) * NS + rp] - sf[(c * 4 + 1) * NS + s1];
-                acc += sf[(c * 4 + 3) * NS + rp] - sf[(c * 4 + 0) * NS + s0];
-                if constexpr (PREC == LSM_PREC_F32) F[c] = f2d_bits(acc);
-                else F[c] = acc;
-            }
-        }
-        const bool grip = gx == 0 || gx == A.nx - 1;
-        const bool fixx = grip, fixy = grip && A.grip_mode == 1;
-        const int ph = sph[rp] - 1;
-        const double m = smass[ph];
-        const double xr[2] = {sx[rp], sy[rp]};
-        if (SAMPLE && gx == A.nx - 1) {
-            if constexpr (PREC == LSM_PREC_EXACT64) react = sb(react, F[0]);
-            else react -= F[0];
-        }
-#pragma unroll
-        for (int c = 0; c < 2; c++) {
-            const bool fixed = c == 0 ? fixx : fixy;
-            const int64_t q = c * A.np + g;
-            if (MODE == T_STEP) A.x_out[q] = xr[c];
-            if (fixed) {
-                if (MODE == T_STEP) A.vh_out[q] = 0.0;
-                if (MODE == T_STEP && SAMPLE) A.v_obs[q] = 0.0;
-                continue;
-            }
-            if (MODE == T_OBSERVE) {
-                const double vn = A.v_obs[q];
-                if (SAMPLE) {
-                    res = fmax(res, fmax(fabs(F[c]), fabs(vn)));
-                    ke += 0.5 * m * vn * vn;
-                    if (c == 0) mvx2 += m * vn * vn;
-                }
-                continue;
-            }
-            const double vh = MODE == T_INIT ? A.v_obs[q] : A.vh_in[q];
-            double vn, vh2;
-            if constexpr (PREC == LSM_PREC_EXACT64) {
-                const double acc = dv(sb(F[c], ml(A.gamma, vh)), m);
-                vn = ad(vh, ml(A.hdt, acc));
-                vh2 = ad(vn, ml(A.hdt, acc));
-            } else {
-                // vh + t (F - gamma vh) / m = (1 - t gamma / m) vh + (t / m) F
-                const Coef4 k4 = scoef[ph];
-                vn = fma(k4.c2h, F[c], k4.c1h * vh);
-                vh2 = fma(k4.c2, F[c], k4.c1 * vh);
-            }
-            if (MODE == T_INIT) {
-                // vh = v + dt/2 a(t) with a from the forces at the current x
-                A.vh_out[q] = vn;
-                continue;
-            }
-            A.vh_out[q] = vh2;
-            if (SAMPLE) {
-                A.v_obs[q] = vn;
-                res = fmax(res, fmax(fabs(F[c]), fabs(vn)));
-                ke += 0.5 * m * vn * vn;
-                if (c == 0) mvx2 += m * vn * vn;
-                bad |= !isfinite(vn) || !isfinite(xr[c]);
-            }
-        }
-        if (MODE == T_STEP) {
-            const int nb = snew[rp];
-            if (nb) A.mask[g] = (uint8_t)(smk[rp] | nb);
-        }
-    }
-    if (SAMPLE) {
-        if (bad) atomicOr(A.status, 1);
-        const double t0 = bsum(w_acc, sred);
-        const double t1 = bsum(u_acc, sred);
-        const double t2 = bsum(mvx2, sred);
-        const double t3 = bsum(ke, sred);
-        const double t4 = bsum(react, sred);
-        const double t5 = bmax(res, sred);
-        if (tid == 0) {
-            A.part_s[tile_id] = t0;
-            A.part_s[A.ntiles + tile_id] = t1;
-            A.part_p[tile_id] = t2;
-            A.part_p[A.ntiles + tile_id] = t3;
-            A.part_p[2 * A.ntiles + tile_id] = t4;
-            A.part_p[3 * A.ntiles + tile_id] = t5;
-        }
-    }
+    tile_body<TX, TY, PREC, MODE, SAMPLE, ODY>(A, blockIdx.x, blockIdx.y,
+                                                (int64_t)blockIdx.y * gridDim.x + blockIdx.x, smem_raw);
 }
 
 // Load increment on the pixel grid (Sections 2.3, 3.1).
@@ -568,15 +100,6 @@ cudaError_t tile_export(Ctx &c, bool steps)
 
 // ------------------------------------------------------------------ host
 
-template <int TX, int TY>
-static constexpr size_t tile_smem(int prec)
-{
-    constexpr int RX = TX + 2, RY = TY + 2, SX = TX + 2, SY = TY + 1;  // sources: region rows 0..TY
-    const bool fix = prec == LSM_PREC_F32 || prec == LSM_PREC_DF;
-    const size_t fsz = prec == LSM_PREC_F32 ? sizeof(float) : sizeof(double);  // ff is 8 bytes
-    return (size_t)2 * RX * RY * sizeof(double) + (fix ? (size_t)2 * RX * RY * sizeof(long long) : 0) +
-           (size_t)8 * SX * SY * fsz + (size_t)SX * SY * sizeof(int) + (size_t)2 * RX * RY + 16;
-}
 
 constexpr int TILE_X = 32, TILE_Y = 16;
 
@@ -624,7 +147,7 @@ template <int PREC, int MODE, bool SAMPLE, bool ODY = false>
 static cudaError_t launch_tile(Ctx &c, TileArgs A)
 {
     auto kern = k_tile2d<TILE_X, TILE_Y, PREC, MODE, SAMPLE, ODY>;
-    const size_t smem = tile_smem<TILE_X, TILE_Y>(PREC);
+    const size_t smem = tile_smem_bytes<TILE_X, TILE_Y>(PREC);
     static bool configured = false;  // per template instance
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -1,0 +1,116 @@
+"""Batched 2D path vs single-specimen contexts and the oracle.
+
+The batch runs the same per-tile step as the single-specimen tile kernel, so
+with identical arithmetic its states are bit-identical to single-specimen
+runs regardless of the schedule (tile height, grid, tile order); exact64
+batches are bit-identical to the oracle.
+"""
+import numpy as np
+import pytest
+
+from gen.images import inclusion_image, two_phase_materials
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_04565_gb300 import batch, build, lsm
+    build.build()
+    lsm.load_library()
+    return batch, lsm
+
+
+def _images():
+    rng = np.random.default_rng(21)
+    imgs = [inclusion_image(40, 40, 3.0, 6.0, 0.3, 1), inclusion_image(70, 33, 2.0, 5.0, 0.2, 2),
+            inclusion_image(64, 96, 3.0, 8.0, 0.4, 3), inclusion_image(17, 9, 1.0, 2.0, 0.3, 4)]
+    holes = rng.integers(0, 3, size=(25, 31)).astype(np.uint8)  # voids included
+    imgs.append(holes)
+    return imgs
+
+
+@pytest.mark.parametrize("precision", ["exact64", "df64"])
+def test_batch_matches_single_specimens(B, oracle_mod, precision):
+    batch, lsm = B
+    imgs = _images()
+    k, e, m = two_phase_materials()
+    bt = batch.Batch(imgs, k, e, m, precision=precision)
+    singles = [lsm.Specimen.from_image(im, k, e, m, precision=precision) for im in imgs]
+    for i in range(1, 41):
+        bt.apply_strain(i * 2.5e-3)
+        bt.step(10)
+        for g in singles:
+            g.apply_strain(i * 2.5e-3)
+            g.step(10)
+    any_break = False
+    for q, g in enumerate(singles):
+        xb, vb = bt.state(q)
+        xs, vs = g.state()
+        assert np.array_equal(xb, xs) and np.array_equal(vb, vs), q
+        mb, fb = bt.broken(q)
+        ms, fs = g.broken()
+        assert np.array_equal(mb, ms) and fb == fs
+        any_break |= fs >= 0
+        sb, ss = bt.samples(q), g.samples()
+        assert len(sb) == len(ss) == 40
+        for a, b in zip(sb, ss):
+            assert a["step"] == b["step"] and a["n_broken"] == b["n_broken"] and a["eps"] == b["eps"]
+            assert a["sigma_vir"] == pytest.approx(b["sigma_vir"], rel=1e-12, abs=1e-300)
+    assert any_break
+    if precision == "exact64":  # and the oracle itself
+        o = oracle_mod.Oracle.from_image(imgs[2], k, e, m)
+        for i in range(1, 41):
+            o.apply_strain(i * 2.5e-3)
+            o.step(10)
+        assert np.array_equal(bt.state(2)[0], o.state()[0])
+
+
+def test_schedules_and_autotune_are_state_neutral(B):
+    batch, lsm = B
+    imgs = _images()
+    k, e, m = two_phase_materials()
+    outs = []
+    for sched in [(8, 0, 0), (32, 152 * 4, 1), None]:
+        bt = batch.Batch(imgs, k, e, m, precision="df64")
+        bt.apply_strain(0.01)
+        bt.step(7)
+        if sched is None:
+            info = bt.autotune(3)
+            assert info["tile_y"] in (8, 16, 32) and info["ms_per_step"] > 0
+        else:
+            bt.set_schedule(*sched)
+        for i in range(2, 20):
+            bt.apply_strain(i * 5e-3)
+            bt.step(9)
+        outs.append([bt.state(q)[0] for q in range(len(imgs))])
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+    for a, b in zip(outs[0], outs[2]):
+        assert np.array_equal(a, b)
+
+
+def test_batch_relax_matches_single_relax(B):
+    batch, lsm = B
+    imgs = [inclusion_image(24, 24, 2.0, 4.0, 0.3, 3), inclusion_image(40, 16, 2.0, 4.0, 0.2, 5),
+            inclusion_image(12, 30, 2.0, 3.0, 0.3, 6)]
+    k, e, m = two_phase_materials()
+    kw = dict(dt=0.2, damping=0.3, precision="exact64")
+    bt = batch.Batch(imgs, k, e, m, **kw)
+    bt.apply_strain(0.01)
+    st, taken, conv = bt.relax(1e-9, 50000, 25)
+    assert st == lsm.LSM_OK and conv.all()
+    for q, im in enumerate(imgs):
+        g = lsm.Specimen.from_image(im, k, e, m, **kw)
+        g.apply_strain(0.01)
+        st1, t1 = g.relax(1e-9, 50000, 25)
+        assert st1 == 0 and t1 == taken[q]
+        assert np.array_equal(g.state()[0], bt.state(q)[0])
+        assert bt.samples(q)[-1]["residual"] <= 1e-9
+    # a cap that stops before convergence reports LSM_ENOTCONV per specimen
+    bt.apply_strain(0.02)
+    st, taken, conv = bt.relax(0.0, 10, 5)
+    assert st == lsm.LSM_ENOTCONV and (taken == 10).all() and not conv.any()
