@@ -250,6 +250,63 @@ def run_gpu(args, rank, world):
     return out
 
 
+def run_batch512(args, plain_every=8):
+    """Uneven batch of 512 two-phase specimens (sides 32..512 px), tension to
+    8% in 80 increments of 20 steps. Batched arm: every specimen in one
+    lsm_batch (one tile-kernel launch per time step, graph-captured, autotuned
+    schedule). Plain arm: one single-specimen context per specimen, run one
+    after another through the same library (every plain_every-th specimen is
+    run, and its time is scaled by the spring count of the whole batch).
+    Build time is excluded from both arms; per-increment host work is
+    included. Returns curves/s for both."""
+    import torch
+    from gen.images import batch_specimens
+    from paper_2201_04565_gb300 import batch as bmod
+    from paper_2201_04565_gb300 import lsm
+
+    prec = args.precision
+    imgs = batch_specimens(512)
+    k, e, m = two_phase_materials()
+    incs, nst = 80, 20
+    stream = torch.cuda.Stream()
+    bt = bmod.Batch(imgs, k, e, m, dt=0.01, damping=0.1, precision=prec, stream=stream.cuda_stream)
+    msum = sum(mm for _, mm in bt.sizes)
+    tune = bt.autotune(4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(1, incs + 1):
+        bt.apply_strain(i * 1e-3)
+        bt.step(nst)
+    bt.synchronize()
+    t_batch = time.perf_counter() - t0
+    launches = bt.counters()[1]
+    bt.close()
+    sub = list(range(0, len(imgs), plain_every))
+    m_sub = 0
+    t_plain = 0.0
+    for q in sub:
+        sp = lsm.Specimen.from_image(imgs[q], k, e, m, dt=0.01, damping=0.1, precision=prec,
+                                     stream=stream.cuda_stream)
+        m_sub += sp.m
+        sp.synchronize()
+        t0 = time.perf_counter()
+        for i in range(1, incs + 1):
+            sp.apply_strain(i * 1e-3)
+            sp.step(nst)
+        sp.synchronize()
+        t_plain += time.perf_counter() - t0
+        sp.close()
+    t_plain_all = t_plain * msum / m_sub
+    return {"workload": "batch512_two_phase", "specimens": len(imgs), "springs_total": msum,
+            "increments": incs, "time_steps_per_increment": nst, "precision": prec,
+            "batched": {"curves_per_s": len(imgs) / t_batch, "seconds": t_batch,
+                        "spring_updates_per_s": msum * incs * nst / t_batch, "schedule": tune,
+                        "kernel_launches": launches},
+            "plain": {"curves_per_s": len(imgs) / t_plain_all, "seconds_extrapolated": t_plain_all,
+                      "sample": "%d of %d specimens run, time scaled by spring count" % (len(sub), len(imgs))},
+            "speedup": t_plain_all / t_batch}
+
+
 def run_oracle_sample(budget_s=12.0):
     """The FP64 CPU oracle on the same workload: one strain increment, then as
     many time steps as fit in about budget_s seconds (single thread)."""
@@ -281,6 +338,7 @@ def main():
     ap.add_argument("--precision", default="df64", choices=["exact64", "fast64", "f32", "df64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--workload", default="2d_2048", choices=["2d_2048", "batch512"])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -302,6 +360,10 @@ def main():
         print(json.dumps(out))
         return 0
 
+    if args.workload == "batch512":
+        if rank == 0:
+            print(json.dumps(run_batch512(args)))
+        return 0
     if world > 1:
         import torch
         import torch.distributed as td
