@@ -17,7 +17,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/lsm_batch.h"
+#include "../../include/lsm_nn.h"
 #include "tile_body.cuh"
 
 namespace lsm {
@@ -215,6 +215,52 @@ k_batch_strain(const BatchTile *__restrict__ tiles, int64_t T, int TY, SpecDesc 
                 VOBS[2 * P + g] = 0.0;
             }
             x[g] = xp;
+        }
+    }
+}
+
+// Displacement u = x - X (and phase) of every specimen, all H x W.
+__global__ void __launch_bounds__(256)
+k_batch_fields(const BatchTile *__restrict__ tiles, int64_t T, int TY, const SpecDesc *__restrict__ specs,
+               const double *X0, const double *X1, const uint8_t *__restrict__ PH, float *__restrict__ u,
+               uint8_t *__restrict__ phase, double a)
+{
+    for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
+        const BatchTile bt = tiles[t];
+        const SpecDesc &sd = specs[bt.spec];
+        const int64_t P = sd.pbase, np = (int64_t)sd.nx * sd.ny;
+        const double *x = (sd.cur ? X1 : X0) + 2 * P;
+        for (int e = threadIdx.x; e < 32 * TY; e += blockDim.x) {
+            const int gx = bt.bx * 32 + (e & 31), gy = bt.by * TY + (e >> 5);
+            if (gx >= sd.nx || gy >= sd.ny) continue;
+            const int64_t g = (int64_t)gy * sd.nx + gx;
+            const int64_t o = (int64_t)bt.spec * np;
+            u[2 * o + g] = (float)(x[g] - gx * a);
+            u[2 * o + np + g] = (float)(x[np + g] - gy * a);
+            if (phase) phase[o + g] = PH[P + g];
+        }
+    }
+}
+
+// x += du on the free components of every specimen (all H x W).
+__global__ void __launch_bounds__(256)
+k_batch_add_du(const BatchTile *__restrict__ tiles, int64_t T, int TY, const SpecDesc *__restrict__ specs,
+               double *X0, double *X1, const uint8_t *__restrict__ PH, const float *__restrict__ du, int grip_mode)
+{
+    for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
+        const BatchTile bt = tiles[t];
+        const SpecDesc &sd = specs[bt.spec];
+        const int64_t P = sd.pbase, np = (int64_t)sd.nx * sd.ny;
+        double *x = (sd.cur ? X1 : X0) + 2 * P;
+        for (int e = threadIdx.x; e < 32 * TY; e += blockDim.x) {
+            const int gx = bt.bx * 32 + (e & 31), gy = bt.by * TY + (e >> 5);
+            if (gx >= sd.nx || gy >= sd.ny) continue;
+            const int64_t g = (int64_t)gy * sd.nx + gx;
+            if (!PH[P + g]) continue;
+            const bool grip = gx == 0 || gx == sd.nx - 1;
+            const int64_t o = (int64_t)bt.spec * np;
+            if (!grip) x[g] += (double)du[2 * o + g];
+            if (!(grip && grip_mode == 1)) x[np + g] += (double)du[2 * o + np + g];
         }
     }
 }
@@ -936,6 +982,38 @@ lsm_status lsm_batch_synchronize(lsm_batch *b)
 {
     if (!b) return bfail(nullptr, LSM_EINVAL, "null batch");
     return lsm::batch_status(*b);
+}
+
+static bool uniform_size(lsm_batch *b, int32_t H, int32_t W)
+{
+    for (int s = 0; s < b->S; s++)
+        if (b->nx[s] != W || b->ny[s] != H) return false;
+    return true;
+}
+
+lsm_status lsm_batch_fields(lsm_batch *b, float *u, uint8_t *phase, int32_t H, int32_t W)
+{
+    if (!b || !u) return bfail(b, LSM_EINVAL, "null argument");
+    if (!uniform_size(b, H, W)) return bfail(b, LSM_EINVAL, "every specimen must be H x W");
+    const unsigned grid = (unsigned)std::min<int64_t>(b->T, 152 * 16);
+    lsm::k_batch_fields<<<grid, 256, 0, b->stream>>>(b->tiles, b->T, b->tile_y, b->specs, b->X[0], b->X[1], b->PH, u,
+                                                     phase, b->a);
+    b->launches += 1;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LSM_OK : bcuda(b, e, "fields");
+}
+
+lsm_status lsm_batch_add_displacements(lsm_batch *b, const float *du, int32_t H, int32_t W)
+{
+    if (!b || !du) return bfail(b, LSM_EINVAL, "null argument");
+    if (!uniform_size(b, H, W)) return bfail(b, LSM_EINVAL, "every specimen must be H x W");
+    const unsigned grid = (unsigned)std::min<int64_t>(b->T, 152 * 16);
+    lsm::k_batch_add_du<<<grid, 256, 0, b->stream>>>(b->tiles, b->T, b->tile_y, b->specs, b->X[0], b->X[1], b->PH, du,
+                                                     b->grip_mode);
+    b->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = lsm::launch_b<lsm::T_INIT, false>(*b, 0, b->T);
+    return e == cudaSuccess ? LSM_OK : bcuda(b, e, "add_displacements");
 }
 
 lsm_status lsm_batch_autotune(lsm_batch *b, int32_t steps_per_trial, int32_t *tile_y, int32_t *grid, int32_t *order,

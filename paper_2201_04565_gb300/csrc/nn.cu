@@ -1,0 +1,1075 @@
+// nn.cu -- BF16 tensor-core kernels and the U-Net of the learned warm start.
+//
+// The network predicts, for each strain increment of a 2D specimen, the
+// displacement the plain damped relaxation would add after the affine load
+// step (inputs: phase map, current non-affine displacement, strain
+// increment). It is trained on increments the method itself generates, and
+// its prediction only moves the starting point of the relaxation, which then
+// runs to the same force-residual tolerance as without it.
+//
+// Convolutions are implicit GEMMs on mma.sync m16n8k16 (BF16 in, FP32
+// accumulate), with cp.async double-buffered, XOR-swizzled shared tiles and
+// ldmatrix fragment loads:
+//   forward   M = pixels, N = Cout, K = taps x Cin   (bias + ReLU epilogue)
+//   dgrad     the forward kernel with 180-degree rotated, transposed weights
+//   wgrad     M = Cout, N = taps x Cin, K = pixels, split over pixel chunks,
+//             partial tiles folded in a fixed order (deterministic)
+// Everything else (pooling, upsampling, head, loss, Adam, data preparation)
+// is plain elementwise or fixed-order reduction kernels.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "../../include/lsm_nn.h"
+#include "nn_internal.h"
+
+namespace lsm {
+namespace nn {
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(unsigned dst, const void *src, bool valid)
+{
+    const int sz = valid ? 16 : 0;  // 0: fill the 16 bytes with zeros, read nothing
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(sz));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+__device__ __forceinline__ void ldm_x4(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3, unsigned addr)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldm_x4_t(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3, unsigned addr)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+__device__ __forceinline__ void mma16816(float *c, unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
+                                         unsigned b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// 64-byte rows of 4 16-byte chunks: chunk position XOR-ed with (row / 2) % 4,
+// so the 8 rows an ldmatrix reads hit 8 distinct bank groups.
+__device__ __forceinline__ int swz(int row, int chunk) { return row * 32 + ((chunk ^ ((row >> 1) & 3)) << 3); }
+
+// ---------------------------------------------------------- conv forward
+
+constexpr int CBM = 128, CBK = 32;
+
+template <int BN>
+__global__ void __launch_bounds__(256)
+k_conv_fwd(const bf16 *__restrict__ in, int in_cs, int in_c0, int Cin, const bf16 *__restrict__ W,
+           const float *__restrict__ bias, bf16 *__restrict__ out, int out_cs, int out_c0, int Cout, int B, int H,
+           int Wd, int taps, int relu)
+{
+    __shared__ __align__(128) bf16 sA[2][CBM * CBK];
+    __shared__ __align__(128) bf16 sB[2][BN * CBK];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int HW = H * Wd;
+    const int M = B * HW;
+    const int m0 = blockIdx.x * CBM, n0 = blockIdx.y * BN;
+    const int kchunks = Cin / CBK;
+    const int KT = taps * kchunks;
+
+    int arow[2], achk[2], ab[2], ay[2], ax[2];
+    bool am[2];
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+        const int c = tid + 256 * i;
+        arow[i] = c >> 2;
+        achk[i] = c & 3;
+        const int m = m0 + arow[i];
+        am[i] = m < M;
+        const int mm = am[i] ? m : 0;
+        ab[i] = mm / HW;
+        const int rem = mm - ab[i] * HW;
+        ay[i] = rem / Wd;
+        ax[i] = rem - ay[i] * Wd;
+    }
+    auto load = [&](int kt, int buf) {
+        const int tap = kt / kchunks, ci0 = (kt - tap * kchunks) * CBK;
+        const int dy = taps == 9 ? tap / 3 - 1 : 0, dx = taps == 9 ? tap % 3 - 1 : 0;
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            const int yy = ay[i] + dy, xx = ax[i] + dx;
+            const bool v = am[i] && yy >= 0 && yy < H && xx >= 0 && xx < Wd;
+            const bf16 *src = v ? in + ((int64_t)(ab[i] * H + yy) * Wd + xx) * in_cs + in_c0 + ci0 + achk[i] * 8 : in;
+            cp_async16(smem_u32(&sA[buf][swz(arow[i], achk[i])]), src, v);
+        }
+        if (tid < BN * 4) {
+            const int r = tid >> 2, ch = tid & 3, co = n0 + r;
+            const bool v = co < Cout;
+            const bf16 *src = v ? W + ((int64_t)co * taps + tap) * Cin + ci0 + ch * 8 : W;
+            cp_async16(smem_u32(&sB[buf][swz(r, ch)]), src, v);
+        }
+    };
+
+    constexpr int NT = BN / 16;  // n8 tiles per warp (warp covers BN / 2 columns)
+    float acc[2][NT][4];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < NT; j++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) acc[i][j][q] = 0.0f;
+    const int wm = warp & 3, wn = warp >> 2;
+
+    load(0, 0);
+    cp_commit();
+    for (int kt = 0; kt < KT; kt++) {
+        if (kt + 1 < KT) load(kt + 1, (kt + 1) & 1);
+        cp_commit();
+        cp_wait<1>();
+        __syncthreads();
+        const int buf = kt & 1;
+#pragma unroll
+        for (int ks = 0; ks < 2; ks++) {
+            unsigned a[2][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; mt++) {
+                const int row = wm * 32 + mt * 16 + (lane & 15);
+                const int chk = ks * 2 + (lane >> 4);
+                ldm_x4(a[mt][0], a[mt][1], a[mt][2], a[mt][3], smem_u32(&sA[buf][swz(row, chk)]));
+            }
+            unsigned b[NT][2];
+#pragma unroll
+            for (int jj = 0; jj < NT / 2; jj++) {
+                const int nrow = wn * (BN / 2) + jj * 16 + (lane & 7) + ((lane >> 4) << 3);
+                const int chk = ks * 2 + ((lane >> 3) & 1);
+                ldm_x4(b[2 * jj][0], b[2 * jj][1], b[2 * jj + 1][0], b[2 * jj + 1][1],
+                       smem_u32(&sB[buf][swz(nrow, chk)]));
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+                for (int j = 0; j < NT; j++) mma16816(acc[mt][j], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b[j][0], b[j][1]);
+        }
+        __syncthreads();
+    }
+    const int g = lane >> 2, tg = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+        for (int j = 0; j < NT; j++) {
+            const int n = n0 + wn * (BN / 2) + j * 8 + 2 * tg;
+            if (n >= Cout) continue;
+            const float b0 = bias ? bias[n] : 0.0f, b1 = bias ? bias[n + 1] : 0.0f;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const int m = m0 + wm * 32 + mt * 16 + g + 8 * h;
+                if (m >= M) continue;
+                float v0 = acc[mt][j][2 * h] + b0, v1 = acc[mt][j][2 * h + 1] + b1;
+                if (relu) {
+                    v0 = fmaxf(v0, 0.0f);
+                    v1 = fmaxf(v1, 0.0f);
+                }
+                *(__nv_bfloat162 *)(out + (int64_t)m * out_cs + out_c0 + n) = __floats2bfloat162_rn(v0, v1);
+            }
+        }
+}
+
+cudaError_t conv_fwd(const bf16 *in, int in_cs, int in_c0, int Cin, const bf16 *W, const float *bias, bf16 *out,
+                     int out_cs, int out_c0, int Cout, int B, int H, int Wd, int taps, bool relu, cudaStream_t st)
+{
+    if (Cin % CBK || Cout % 32 || (in_cs | in_c0 | out_cs | out_c0) % 8) return cudaErrorInvalidValue;
+    const int M = B * H * Wd;
+    const dim3 grid((M + CBM - 1) / CBM, Cout % 64 == 0 ? Cout / 64 : Cout / 32);
+    if (Cout % 64 == 0)
+        k_conv_fwd<64><<<grid, 256, 0, st>>>(in, in_cs, in_c0, Cin, W, bias, out, out_cs, out_c0, Cout, B, H, Wd, taps, relu);
+    else
+        k_conv_fwd<32><<<grid, 256, 0, st>>>(in, in_cs, in_c0, Cin, W, bias, out, out_cs, out_c0, Cout, B, H, Wd, taps, relu);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ conv wgrad
+
+constexpr int WPIX = 32;  // pixels per k step
+
+// part[split][co][tap * Cin + ci] = sum over the split's pixels of
+// grad[p][co] * in[p shifted by tap][ci]; 32 x 32 output tile per CTA.
+__global__ void __launch_bounds__(128)
+k_conv_wgrad(const bf16 *__restrict__ grad, int g_cs, int Cout, const bf16 *__restrict__ in, int in_cs, int in_c0,
+             int Cin, int B, int H, int Wd, int taps, int pix_per_split, float *__restrict__ part)
+{
+    __shared__ __align__(128) bf16 sG[2][WPIX * 32];
+    __shared__ __align__(128) bf16 sI[2][WPIX * 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int HW = H * Wd, M = B * HW;
+    const int cit = Cin / 32;
+    const int tap = blockIdx.x / cit, ci0 = (blockIdx.x - tap * cit) * 32;
+    const int co0 = blockIdx.y * 32;
+    const int p0 = blockIdx.z * pix_per_split, p1 = min(M, p0 + pix_per_split);
+    const int dy = taps == 9 ? tap / 3 - 1 : 0, dx = taps == 9 ? tap % 3 - 1 : 0;
+    const int lrow = tid >> 2, lchk = tid & 3;  // one 16-byte chunk of each tile per thread
+    auto load = [&](int p, int buf) {
+        const int m = p + lrow;
+        const bool vm = m < p1;
+        const int mm = vm ? m : 0;
+        const int b = mm / HW, rem = mm - b * HW, y = rem / Wd, x = rem - (rem / Wd) * Wd;
+        const bf16 *sg = vm ? grad + (int64_t)mm * g_cs + co0 + lchk * 8 : grad;
+        cp_async16(smem_u32(&sG[buf][swz(lrow, lchk)]), sg, vm);
+        const int yy = y + dy, xx = x + dx;
+        const bool vi = vm && yy >= 0 && yy < H && xx >= 0 && xx < Wd;
+        const bf16 *si = vi ? in + ((int64_t)(b * H + yy) * Wd + xx) * in_cs + in_c0 + ci0 + lchk * 8 : in;
+        cp_async16(smem_u32(&sI[buf][swz(lrow, lchk)]), si, vi);
+    };
+    float acc[2][4];
+#pragma unroll
+    for (int j = 0; j < 2; j++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) acc[j][q] = 0.0f;
+    const int wm = warp & 1, wn = warp >> 1;  // 2 x 2 warps of 16 x 16
+    const int nk = (p1 - p0 + WPIX - 1) / WPIX;
+    if (nk > 0) {
+        load(p0, 0);
+        cp_commit();
+    }
+    for (int k = 0; k < nk; k++) {
+        if (k + 1 < nk) load(p0 + (k + 1) * WPIX, (k + 1) & 1);
+        cp_commit();
+        cp_wait<1>();
+        __syncthreads();
+        const int buf = k & 1;
+#pragma unroll
+        for (int ks = 0; ks < 2; ks++) {
+            unsigned a0, a1, a2, a3, b0, b1, b2, b3;
+            {  // A = grad^T: rows co, k = pixels; stored [pixel][co]
+                const int prow = ks * 16 + (lane & 7) + ((lane >> 4) << 3);
+                const int chk = wm * 2 + ((lane >> 3) & 1);
+                ldm_x4_t(a0, a1, a2, a3, smem_u32(&sG[buf][swz(prow, chk)]));
+            }
+            {  // B = shifted input: k = pixels, n = ci; stored [pixel][ci]
+                const int prow = ks * 16 + (lane & 7) + (((lane >> 3) & 1) << 3);
+                const int chk = wn * 2 + (lane >> 4);
+                ldm_x4_t(b0, b1, b2, b3, smem_u32(&sI[buf][swz(prow, chk)]));
+            }
+            mma16816(acc[0], a0, a1, a2, a3, b0, b1);
+            mma16816(acc[1], a0, a1, a2, a3, b2, b3);
+        }
+        __syncthreads();
+    }
+    const int g = lane >> 2, tg = lane & 3;
+    const int64_t K = (int64_t)taps * Cin;
+    float *dst = part + (int64_t)blockIdx.z * Cout * K;
+#pragma unroll
+    for (int j = 0; j < 2; j++)
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int co = co0 + wm * 16 + g + 8 * h;
+            const int ci = ci0 + wn * 16 + j * 8 + 2 * tg;
+            dst[(int64_t)co * K + (int64_t)tap * Cin + ci] = acc[j][2 * h];
+            dst[(int64_t)co * K + (int64_t)tap * Cin + ci + 1] = acc[j][2 * h + 1];
+        }
+}
+
+// out[i] = sum over splits s (in order) of part[s][i].
+__global__ void k_fold(const float *__restrict__ part, int64_t n, int splits, float *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.0f;
+    for (int q = 0; q < splits; q++) s += part[(int64_t)q * n + i];
+    out[i] = s;
+}
+
+// Per-split column sums of grad (bias gradient): part[split][c].
+__global__ void k_bias_part(const bf16 *__restrict__ grad, int g_cs, int C, int M, int pix_per_split,
+                            float *__restrict__ part)
+{
+    const int p0 = blockIdx.x * pix_per_split, p1 = min(M, p0 + pix_per_split);
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float s = 0.0f;
+        for (int p = p0; p < p1; p++) s += __bfloat162float(grad[(int64_t)p * g_cs + c]);
+        part[(int64_t)blockIdx.x * C + c] = s;
+    }
+}
+
+cudaError_t conv_wgrad(const bf16 *grad, int g_cs, int Cout, const bf16 *in, int in_cs, int in_c0, int Cin, int B,
+                       int H, int Wd, int taps, float *dW, float *db, float *scratch, size_t scratch_floats,
+                       cudaStream_t st)
+{
+    if (Cin % 32 || Cout % 32 || (g_cs | in_cs | in_c0) % 8) return cudaErrorInvalidValue;
+    const int M = B * H * Wd;
+    const int64_t K = (int64_t)taps * Cin;
+    const int64_t per = (int64_t)Cout * K;
+    int splits = (M + 4095) / 4096;
+    if (splits > 256) splits = 256;
+    while (splits > 1 && (size_t)splits * per > scratch_floats) splits /= 2;
+    if ((size_t)per > scratch_floats) return cudaErrorMemoryAllocation;
+    const int pps = ((M + splits - 1) / splits + WPIX - 1) / WPIX * WPIX;
+    const dim3 grid((unsigned)(taps * (Cin / 32)), (unsigned)(Cout / 32), (unsigned)splits);
+    k_conv_wgrad<<<grid, 128, 0, st>>>(grad, g_cs, Cout, in, in_cs, in_c0, Cin, B, H, Wd, taps, pps, scratch);
+    k_fold<<<(unsigned)((per + 255) / 256), 256, 0, st>>>(scratch, per, splits, dW);
+    if (db) {
+        int bs = (M + 1023) / 1024;
+        if (bs > 1024) bs = 1024;
+        const int bpp = (M + bs - 1) / bs;
+        k_bias_part<<<bs, 256, 0, st>>>(grad, g_cs, Cout, M, bpp, scratch);
+        k_fold<<<(unsigned)((Cout + 255) / 256), 256, 0, st>>>(scratch, Cout, bs, db);
+    }
+    return cudaGetLastError();
+}
+
+// Wr[ci][tap'][co] = W[co][taps - 1 - tap'][ci]
+__global__ void k_rotate(const bf16 *__restrict__ W, bf16 *__restrict__ Wr, int Cout, int Cin, int taps)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n = (int64_t)Cout * Cin * taps;
+    if (i >= n) return;
+    const int co = (int)(i % Cout);
+    const int64_t r = i / Cout;
+    const int tp = (int)(r % taps);
+    const int ci = (int)(r / taps);
+    Wr[i] = W[((int64_t)co * taps + (taps - 1 - tp)) * Cin + ci];
+}
+
+cudaError_t rotate_weights(const bf16 *W, bf16 *Wr, int Cout, int Cin, int taps, cudaStream_t st)
+{
+    const int64_t n = (int64_t)Cout * Cin * taps;
+    k_rotate<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(W, Wr, Cout, Cin, taps);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- small kernels
+
+// grad *= (act > 0), on a channel slice (grad dense C, act with stride/offset)
+__global__ void k_relu_bwd(bf16 *__restrict__ grad, int C, const bf16 *__restrict__ act, int a_cs, int a_c0, int64_t M)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * C) return;
+    const int64_t m = i / C;
+    const int c = (int)(i - m * C);
+    if (!(__bfloat162float(act[m * a_cs + a_c0 + c]) > 0.0f)) grad[i] = __float2bfloat16(0.0f);
+}
+
+// 2x2 max pool: out[b,y,x,c] = max over the window of in (channel slice)
+__global__ void k_pool_fwd(const bf16 *__restrict__ in, int in_cs, int in_c0, bf16 *__restrict__ out, int C, int B,
+                           int H, int Wd)
+{
+    const int Ho = H / 2, Wo = Wd / 2;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)B * Ho * Wo * C) return;
+    const int c = (int)(i % C);
+    const int64_t p = i / C;
+    const int x = (int)(p % Wo), y = (int)((p / Wo) % Ho), b = (int)(p / ((int64_t)Wo * Ho));
+    float mx = -INFINITY;
+    for (int q = 0; q < 4; q++) {
+        const int yy = 2 * y + (q >> 1), xx = 2 * x + (q & 1);
+        mx = fmaxf(mx, __bfloat162float(in[((int64_t)(b * H + yy) * Wd + xx) * in_cs + in_c0 + c]));
+    }
+    out[i] = __float2bfloat16(mx);
+}
+
+// Gradient of the pool routed to the first maximum of each window, plus the
+// skip-connection gradient (channel slice of a concat gradient), written to
+// a dense [B][H][Wd][C] gradient.
+__global__ void k_pool_bwd(const bf16 *__restrict__ gout, const bf16 *__restrict__ in, int in_cs, int in_c0,
+                           const bf16 *__restrict__ gskip, int s_cs, int s_c0, bf16 *__restrict__ gin, int C, int B,
+                           int H, int Wd)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)B * H * Wd * C) return;
+    const int c = (int)(i % C);
+    const int64_t p = i / C;
+    const int x = (int)(p % Wd), y = (int)((p / Wd) % H), b = (int)(p / ((int64_t)Wd * H));
+    const int yo = y / 2, xo = x / 2, Ho = H / 2, Wo = Wd / 2;
+    float g = 0.0f;
+    if (yo < Ho && xo < Wo) {
+        float mx = -INFINITY;
+        int arg = 0;
+        for (int q = 0; q < 4; q++) {
+            const int yy = 2 * yo + (q >> 1), xx = 2 * xo + (q & 1);
+            const float v = __bfloat162float(in[((int64_t)(b * H + yy) * Wd + xx) * in_cs + in_c0 + c]);
+            if (v > mx) {
+                mx = v;
+                arg = q;
+            }
+        }
+        if (arg == (y - 2 * yo) * 2 + (x - 2 * xo))
+            g = __bfloat162float(gout[((int64_t)(b * Ho + yo) * Wo + xo) * C + c]);
+    }
+    if (gskip) g += __bfloat162float(gskip[p * s_cs + s_c0 + c]);
+    gin[i] = __float2bfloat16(g);
+}
+
+// nearest x2 upsampling into a channel slice of a concat tensor
+__global__ void k_up_fwd(const bf16 *__restrict__ in, int C, bf16 *__restrict__ out, int out_cs, int out_c0, int B,
+                         int Hin, int Win)
+{
+    const int H = 2 * Hin, Wd = 2 * Win;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)B * H * Wd * C) return;
+    const int c = (int)(i % C);
+    const int64_t p = i / C;
+    const int x = (int)(p % Wd), y = (int)((p / Wd) % H), b = (int)(p / ((int64_t)Wd * H));
+    out[p * out_cs + out_c0 + c] = in[((int64_t)(b * Hin + y / 2) * Win + x / 2) * C + c];
+}
+
+// gradient of nearest upsampling: sum of the 2x2 block (from a concat-gradient slice)
+__global__ void k_up_bwd(const bf16 *__restrict__ g, int g_cs, int g_c0, bf16 *__restrict__ gin, int C, int B,
+                         int Hin, int Win)
+{
+    const int H = 2 * Hin, Wd = 2 * Win;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)B * Hin * Win * C) return;
+    const int c = (int)(i % C);
+    const int64_t p = i / C;
+    const int x = (int)(p % Win), y = (int)((p / Win) % Hin), b = (int)(p / ((int64_t)Win * Hin));
+    float s = 0.0f;
+    for (int q = 0; q < 4; q++) {
+        const int yy = 2 * y + (q >> 1), xx = 2 * x + (q & 1);
+        s += __bfloat162float(g[((int64_t)(b * H + yy) * Wd + xx) * g_cs + g_c0 + c]);
+    }
+    gin[i] = __float2bfloat16(s);
+}
+
+// head: out[m][j] = b[j] + sum_c W[j][c] act[m][c], two outputs, FP32
+__global__ void k_head_fwd(const bf16 *__restrict__ act, int C, const float *__restrict__ W,
+                           const float *__restrict__ b, float *__restrict__ out, int64_t M)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    float s0 = b[0], s1 = b[1];
+    for (int c = 0; c < C; c++) {
+        const float a = __bfloat162float(act[m * C + c]);
+        s0 = fmaf(W[c], a, s0);
+        s1 = fmaf(W[C + c], a, s1);
+    }
+    out[2 * m] = s0;
+    out[2 * m + 1] = s1;
+}
+
+// head backward: gact[m][c] = sum_j W[j][c] g[m][j] (masked by ReLU of act)
+__global__ void k_head_bwd_act(const float *__restrict__ g, const float *__restrict__ W, const bf16 *__restrict__ act,
+                               bf16 *__restrict__ gact, int C, int64_t M)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M * C) return;
+    const int64_t m = i / C;
+    const int c = (int)(i - m * C);
+    const float v = W[c] * g[2 * m] + W[C + c] * g[2 * m + 1];
+    gact[i] = __float2bfloat16(__bfloat162float(act[i]) > 0.0f ? v : 0.0f);
+}
+
+// head weight gradient partials: part[split][j * C + c] and bias part[split][2 C + j]
+__global__ void k_head_bwd_w(const float *__restrict__ g, const bf16 *__restrict__ act, int C, int64_t M, int pps,
+                             float *__restrict__ part)
+{
+    const int64_t p0 = (int64_t)blockIdx.x * pps, p1 = min(M, p0 + pps);
+    const int n = 2 * C + 2;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+        float s = 0.0f;
+        if (q < 2 * C) {
+            const int j = q / C, c = q - j * C;
+            for (int64_t m = p0; m < p1; m++) s += g[2 * m + j] * __bfloat162float(act[m * C + c]);
+        } else {
+            const int j = q - 2 * C;
+            for (int64_t m = p0; m < p1; m++) s += g[2 * m + j];
+        }
+        part[(int64_t)blockIdx.x * n + q] = s;
+    }
+}
+
+// MSE: g = 2 (pred - target) / count; per-block partial sums of squares
+__global__ void k_mse(const float *__restrict__ pred, const float *__restrict__ tgt, float *__restrict__ g, int64_t n,
+                      float *__restrict__ part)
+{
+    __shared__ float sh[256];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float d = 0.0f;
+    if (i < n) {
+        d = pred[i] - tgt[i];
+        g[i] = 2.0f * d / (float)n;
+    }
+    sh[threadIdx.x] = d * d;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sum_to(const float *__restrict__ part, int n, float scale, float *__restrict__ out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        float s = 0.0f;
+        for (int q = 0; q < n; q++) s += part[q];
+        *out = s * scale;
+    }
+}
+
+// Adam on FP32 master parameters, refreshing the BF16 copies of the conv
+// weights (bf_off < 0: the parameter has no BF16 copy).
+__global__ void k_adam(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m1,
+                       float *__restrict__ m2, int64_t n, float lr, float b1, float b2, float eps, float c1, float c2,
+                       bf16 *__restrict__ wb, const int64_t *__restrict__ bfmap)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float a = b1 * m1[i] + (1.0f - b1) * gi;
+    const float v = b2 * m2[i] + (1.0f - b2) * gi * gi;
+    m1[i] = a;
+    m2[i] = v;
+    const float wi = w[i] - lr * (a / c1) / (sqrtf(v / c2) + eps);
+    w[i] = wi;
+    const int64_t j = bfmap[i];
+    if (j >= 0) wb[j] = __float2bfloat16(wi);
+}
+
+__global__ void k_to_bf16(const float *__restrict__ w, bf16 *__restrict__ wb, const int64_t *__restrict__ bfmap,
+                          int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t j = bfmap[i];
+    if (j >= 0) wb[j] = __float2bfloat16(w[i]);
+}
+
+// ----------------------------------------------------- data preparation
+
+// Network input (NHWC, 32 channels, 4 used): phase - 1.5, the current
+// non-affine displacement (x minus the affine field eps (X - xc), y as is)
+// over u_scale, and the strain increment over de_scale.
+__global__ void k_prep_input(const uint8_t *__restrict__ phase, const float *__restrict__ u, const float *__restrict__ eps,
+                             float deps, int S, int H, int Wd, float a, float u_scale, float de_scale,
+                             bf16 *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t HW = (int64_t)H * Wd;
+    if (i >= S * HW) return;
+    const int s = (int)(i / HW);
+    const int64_t g = i - s * HW;
+    const int x = (int)(g % Wd);
+    const float xc = 0.5f * (Wd - 1) * a;
+    const float ux = u[(2 * s) * HW + g] - eps[s] * (x * a - xc), uy = u[(2 * s + 1) * HW + g];
+    bf16 *o = out + i * 32;
+    o[0] = __float2bfloat16((float)phase[i] - 1.5f);
+    o[1] = __float2bfloat16(ux / u_scale);
+    o[2] = __float2bfloat16(uy / u_scale);
+    o[3] = __float2bfloat16(deps / de_scale);
+    for (int c = 4; c < 32; c++) o[c] = __float2bfloat16(0.0f);
+}
+
+// Training target: the relaxation's displacement after the affine load step,
+// (u_relaxed - u_loaded) / (deps * w_scale), NHWC with 2 channels.
+__global__ void k_prep_target(const float *__restrict__ u_loaded, const float *__restrict__ u_relaxed, float deps,
+                              float w_scale, int S, int64_t HW, float *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S * HW) return;
+    const int s = (int)(i / HW);
+    const int64_t g = i - s * HW;
+    for (int c = 0; c < 2; c++)
+        out[2 * i + c] = (u_relaxed[(2 * s + c) * HW + g] - u_loaded[(2 * s + c) * HW + g]) / (deps * w_scale);
+}
+
+// Prediction -> displacement increment [S][2][H][W]
+__global__ void k_pred_to_du(const float *__restrict__ pred, float deps, float w_scale, int S, int64_t HW,
+                             float *__restrict__ du)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S * HW) return;
+    const int s = (int)(i / HW);
+    const int64_t g = i - s * HW;
+    for (int c = 0; c < 2; c++) du[(2 * s + c) * HW + g] = pred[2 * i + c] * deps * w_scale;
+}
+
+// ------------------------------------------------------------- the U-Net
+
+struct Conv {
+    int Cin, Cout, taps;
+    int64_t w_off, b_off, wb_off;  // offsets in params (FP32) and in the BF16 weight copy
+};
+
+static inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+struct UNet {
+    int H = 0, W = 0, maxB = 0;
+    uint64_t seed = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::string err;
+    std::vector<Conv> convs;  // e1a e1 e2a e2 e3a e3 e4a e4 d3a d3 d2a d2 d1a d1
+    int64_t head_w = 0, head_b = 0;
+    int64_t nparam = 0, nbf = 0;
+    float *P = nullptr, *G = nullptr, *M1 = nullptr, *M2 = nullptr;
+    bf16 *WB = nullptr, *WR = nullptr;  // BF16 weights, rotated scratch
+    int64_t *bfmap = nullptr;
+    int64_t step = 0;
+    // activations (NHWC bf16); the encoder outputs e1, e2, e3 live in the
+    // skip slices of the decoder's concat tensors
+    bf16 *e1a = nullptr, *d1c = nullptr;                 // 32; concat 96 = [up d2 0..63 | e1 64..95]
+    bf16 *p1 = nullptr, *e2a = nullptr, *d2c = nullptr;  // 32 @H/2; 64; concat 192 = [up d3 | e2 128..191]
+    bf16 *p2 = nullptr, *e3a = nullptr, *d3c = nullptr;  // 64 @H/4; 128; concat 384 = [up e4 | e3 256..383]
+    bf16 *p3 = nullptr, *e4a = nullptr, *e4 = nullptr;   // 128 @H/8; 256; 256
+    bf16 *d3a = nullptr, *d3 = nullptr, *d2a = nullptr, *d2 = nullptr, *d1a = nullptr, *d1 = nullptr;
+    const bf16 *xin = nullptr;  // the last forward's input (kept for the first conv's wgrad)
+    float *out = nullptr, *gout = nullptr;
+    bf16 *gd1c = nullptr, *gd2c = nullptr, *gd3c = nullptr;  // gradients of the concat tensors
+    bf16 *ta = nullptr, *tb = nullptr;                       // gradient ping-pong (L1 x 32 each)
+    float *ws = nullptr;  // wgrad / reduction scratch
+    size_t ws_floats = 0;
+    float *loss = nullptr;
+};
+
+static const int NCONV = 14;
+
+static void unet_free(UNet &u)
+{
+    void *ptrs[] = {u.P,   u.G,   u.M1,  u.M2,  u.WB,  u.WR,  u.bfmap, u.e1a, u.d1c,  u.p1,   u.e2a,
+                    u.d2c, u.p2,  u.e3a, u.d3c, u.p3,  u.e4a, u.e4,    u.d3a, u.d3,   u.d2a,  u.d2,
+                    u.d1a, u.d1,  u.out, u.gout, u.gd1c, u.gd2c, u.gd3c, u.ta, u.tb, u.ws, u.loss};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+#define NN_TRY(x)                             \
+    do {                                      \
+        cudaError_t e_ = (x);                 \
+        if (e_ != cudaSuccess) return e_;     \
+    } while (0)
+
+template <typename T>
+static cudaError_t nalloc(T **p, size_t n)
+{
+    return cudaMalloc((void **)p, (n ? n : 1) * sizeof(T));
+}
+
+static cudaError_t unet_setup(UNet &u)
+{
+    // conv list: (Cin, Cout); every conv is 3x3, pad 1, bias + ReLU
+    const int spec[NCONV][2] = {{32, 32},  {32, 32},   {32, 64},  {64, 64},  {64, 128}, {128, 128}, {128, 256},
+                                {256, 256}, {384, 128}, {128, 128}, {192, 64}, {64, 64},  {96, 32},   {32, 32}};
+    int64_t off = 0, boff = 0;
+    for (int q = 0; q < NCONV; q++) {
+        Conv c{spec[q][0], spec[q][1], 9, 0, 0, 0};
+        c.w_off = off;
+        off += (int64_t)c.Cout * 9 * c.Cin;
+        c.b_off = off;
+        off += c.Cout;
+        c.wb_off = boff;
+        boff += (int64_t)c.Cout * 9 * c.Cin;
+        u.convs.push_back(c);
+    }
+    u.head_w = off;
+    off += 2 * 32;
+    u.head_b = off;
+    off += 2;
+    u.nparam = off;
+    u.nbf = boff;
+    // He-normal init (seeded), zero biases; the first conv sees 4 real channels
+    std::vector<float> P(u.nparam, 0.0f);
+    std::vector<int64_t> map(u.nparam, -1);
+    std::mt19937_64 rng(u.seed);
+    for (int q = 0; q < NCONV; q++) {
+        const Conv &c = u.convs[q];
+        const int fan_in = 9 * (q == 0 ? 4 : c.Cin);
+        std::normal_distribution<float> nd(0.0f, std::sqrt(2.0f / fan_in));
+        for (int64_t i = 0; i < (int64_t)c.Cout * 9 * c.Cin; i++) {
+            const int ci = (int)(i % c.Cin);
+            P[c.w_off + i] = (q == 0 && ci >= 4) ? 0.0f : nd(rng);
+            map[c.w_off + i] = c.wb_off + i;
+        }
+    }
+    {
+        std::normal_distribution<float> nd(0.0f, 0.1f * std::sqrt(1.0f / 32));
+        for (int i = 0; i < 64; i++) P[u.head_w + i] = nd(rng);
+    }
+    const int B = u.maxB, H = u.H, W = u.W;
+    const int64_t L1 = (int64_t)B * H * W, L2 = L1 / 4, L3 = L1 / 16, L4 = L1 / 64;
+    NN_TRY(nalloc(&u.P, u.nparam));
+    NN_TRY(nalloc(&u.G, u.nparam));
+    NN_TRY(nalloc(&u.M1, u.nparam));
+    NN_TRY(nalloc(&u.M2, u.nparam));
+    NN_TRY(nalloc(&u.bfmap, u.nparam));
+    NN_TRY(nalloc(&u.WB, u.nbf));
+    NN_TRY(nalloc(&u.WR, 9 * 256 * 384));
+    NN_TRY(nalloc(&u.e1a, L1 * 32));
+    NN_TRY(nalloc(&u.d1c, L1 * 96));
+    NN_TRY(nalloc(&u.p1, L2 * 32));
+    NN_TRY(nalloc(&u.e2a, L2 * 64));
+    NN_TRY(nalloc(&u.d2c, L2 * 192));
+    NN_TRY(nalloc(&u.p2, L3 * 64));
+    NN_TRY(nalloc(&u.e3a, L3 * 128));
+    NN_TRY(nalloc(&u.d3c, L3 * 384));
+    NN_TRY(nalloc(&u.p3, L4 * 128));
+    NN_TRY(nalloc(&u.e4a, L4 * 256));
+    NN_TRY(nalloc(&u.e4, L4 * 256));
+    NN_TRY(nalloc(&u.d3a, L3 * 128));
+    NN_TRY(nalloc(&u.d3, L3 * 128));
+    NN_TRY(nalloc(&u.d2a, L2 * 64));
+    NN_TRY(nalloc(&u.d2, L2 * 64));
+    NN_TRY(nalloc(&u.d1a, L1 * 32));
+    NN_TRY(nalloc(&u.d1, L1 * 32));
+    NN_TRY(nalloc(&u.out, L1 * 2));
+    NN_TRY(nalloc(&u.gout, L1 * 2));
+    NN_TRY(nalloc(&u.gd1c, L1 * 96));
+    NN_TRY(nalloc(&u.gd2c, L2 * 192));
+    NN_TRY(nalloc(&u.gd3c, L3 * 384));
+    NN_TRY(nalloc(&u.ta, L1 * 32));
+    NN_TRY(nalloc(&u.tb, L1 * 32));
+    u.ws_floats = 16u << 20;  // 64 MiB of split partials
+    NN_TRY(nalloc(&u.ws, u.ws_floats));
+    NN_TRY(nalloc(&u.loss, 1));
+    NN_TRY(cudaMemcpyAsync(u.P, P.data(), u.nparam * 4, cudaMemcpyHostToDevice, u.st));
+    NN_TRY(cudaMemcpyAsync(u.bfmap, map.data(), u.nparam * 8, cudaMemcpyHostToDevice, u.st));
+    NN_TRY(cudaMemsetAsync(u.M1, 0, u.nparam * 4, u.st));
+    NN_TRY(cudaMemsetAsync(u.M2, 0, u.nparam * 4, u.st));
+    NN_TRY(cudaMemsetAsync(u.G, 0, u.nparam * 4, u.st));
+    k_to_bf16<<<nblk(u.nparam), 256, 0, u.st>>>(u.P, u.WB, u.bfmap, u.nparam);
+    NN_TRY(cudaStreamSynchronize(u.st));
+    return cudaGetLastError();
+}
+
+static cudaError_t conv_f(UNet &u, int q, const bf16 *in, int in_cs, int in_c0, bf16 *out, int out_cs, int out_c0,
+                          int B, int H, int W)
+{
+    const Conv &c = u.convs[q];
+    return conv_fwd(in, in_cs, in_c0, c.Cin, u.WB + c.wb_off, u.P + c.b_off, out, out_cs, out_c0, c.Cout, B, H, W, 9,
+                    true, u.st);
+}
+
+static cudaError_t unet_forward(UNet &u, int B, const bf16 *x0)
+{
+    const int H = u.H, W = u.W, H2 = H / 2, W2 = W / 2, H3 = H / 4, W3 = W / 4, H4 = H / 8, W4 = W / 8;
+    const int64_t L1 = (int64_t)B * H * W, L2 = L1 / 4, L3 = L1 / 16, L4 = L1 / 64;
+    u.xin = x0;
+    NN_TRY(conv_f(u, 0, x0, 32, 0, u.e1a, 32, 0, B, H, W));
+    NN_TRY(conv_f(u, 1, u.e1a, 32, 0, u.d1c, 96, 64, B, H, W));  // e1 -> skip slice
+    k_pool_fwd<<<nblk(L2 * 32), 256, 0, u.st>>>(u.d1c, 96, 64, u.p1, 32, B, H, W);
+    NN_TRY(conv_f(u, 2, u.p1, 32, 0, u.e2a, 64, 0, B, H2, W2));
+    NN_TRY(conv_f(u, 3, u.e2a, 64, 0, u.d2c, 192, 128, B, H2, W2));  // e2
+    k_pool_fwd<<<nblk(L3 * 64), 256, 0, u.st>>>(u.d2c, 192, 128, u.p2, 64, B, H2, W2);
+    NN_TRY(conv_f(u, 4, u.p2, 64, 0, u.e3a, 128, 0, B, H3, W3));
+    NN_TRY(conv_f(u, 5, u.e3a, 128, 0, u.d3c, 384, 256, B, H3, W3));  // e3
+    k_pool_fwd<<<nblk(L4 * 128), 256, 0, u.st>>>(u.d3c, 384, 256, u.p3, 128, B, H3, W3);
+    NN_TRY(conv_f(u, 6, u.p3, 128, 0, u.e4a, 256, 0, B, H4, W4));
+    NN_TRY(conv_f(u, 7, u.e4a, 256, 0, u.e4, 256, 0, B, H4, W4));
+    k_up_fwd<<<nblk(L3 * 256), 256, 0, u.st>>>(u.e4, 256, u.d3c, 384, 0, B, H4, W4);
+    NN_TRY(conv_f(u, 8, u.d3c, 384, 0, u.d3a, 128, 0, B, H3, W3));
+    NN_TRY(conv_f(u, 9, u.d3a, 128, 0, u.d3, 128, 0, B, H3, W3));
+    k_up_fwd<<<nblk(L2 * 128), 256, 0, u.st>>>(u.d3, 128, u.d2c, 192, 0, B, H3, W3);
+    NN_TRY(conv_f(u, 10, u.d2c, 192, 0, u.d2a, 64, 0, B, H2, W2));
+    NN_TRY(conv_f(u, 11, u.d2a, 64, 0, u.d2, 64, 0, B, H2, W2));
+    k_up_fwd<<<nblk(L1 * 64), 256, 0, u.st>>>(u.d2, 64, u.d1c, 96, 0, B, H2, W2);
+    NN_TRY(conv_f(u, 12, u.d1c, 96, 0, u.d1a, 32, 0, B, H, W));
+    NN_TRY(conv_f(u, 13, u.d1a, 32, 0, u.d1, 32, 0, B, H, W));
+    k_head_fwd<<<nblk(L1), 256, 0, u.st>>>(u.d1, 32, u.P + u.head_w, u.P + u.head_b, u.out, L1);
+    return cudaGetLastError();
+}
+
+// Backward of conv q: gpre = gradient at its output (already masked by its
+// ReLU); writes dW/db into G and, if gin != nullptr, the dense input gradient.
+static cudaError_t conv_b(UNet &u, int q, const bf16 *gpre, const bf16 *in, int in_cs, int in_c0, bf16 *gin, int B,
+                          int H, int W)
+{
+    const Conv &c = u.convs[q];
+    NN_TRY(conv_wgrad(gpre, c.Cout, c.Cout, in, in_cs, in_c0, c.Cin, B, H, W, 9, u.G + c.w_off, u.G + c.b_off, u.ws,
+                      u.ws_floats, u.st));
+    if (gin) {
+        NN_TRY(rotate_weights(u.WB + c.wb_off, u.WR, c.Cout, c.Cin, 9, u.st));
+        NN_TRY(conv_fwd(gpre, c.Cout, 0, c.Cout, u.WR, nullptr, gin, c.Cin, 0, c.Cin, B, H, W, 9, false, u.st));
+    }
+    return cudaSuccess;
+}
+
+static void relu_b(UNet &u, bf16 *g, int C, const bf16 *act, int a_cs, int a_c0, int64_t M)
+{
+    k_relu_bwd<<<nblk(M * C), 256, 0, u.st>>>(g, C, act, a_cs, a_c0, M);
+}
+
+// Mean squared error against target and its gradient w.r.t. every
+// parameter, into G (the loss goes to u.loss).
+static cudaError_t unet_backward(UNet &u, int B, const float *target)
+{
+    const int H = u.H, W = u.W, H2 = H / 2, W2 = W / 2, H3 = H / 4, W3 = W / 4, H4 = H / 8, W4 = W / 8;
+    const int64_t L1 = (int64_t)B * H * W, L2 = L1 / 4, L3 = L1 / 16, L4 = L1 / 64;
+    const int64_t nout = L1 * 2;
+    const unsigned mb = nblk(nout);
+    k_mse<<<mb, 256, 0, u.st>>>(u.out, target, u.gout, nout, u.ws);
+    k_sum_to<<<1, 32, 0, u.st>>>(u.ws, (int)mb, 1.0f / (float)nout, u.loss);
+    {  // head: weights, bias (contiguous in P), and the masked gradient of d1
+        int bs = (int)((L1 + 4095) / 4096);
+        if (bs > 1024) bs = 1024;
+        const int pps = (int)((L1 + bs - 1) / bs);
+        k_head_bwd_w<<<bs, 128, 0, u.st>>>(u.gout, u.d1, 32, L1, pps, u.ws);
+        k_fold<<<1, 128, 0, u.st>>>(u.ws, 66, bs, u.G + u.head_w);
+        k_head_bwd_act<<<nblk(L1 * 32), 256, 0, u.st>>>(u.gout, u.P + u.head_w, u.d1, u.ta, 32, L1);
+    }
+    // decoder
+    NN_TRY(conv_b(u, 13, u.ta, u.d1a, 32, 0, u.tb, B, H, W));
+    relu_b(u, u.tb, 32, u.d1a, 32, 0, L1);
+    NN_TRY(conv_b(u, 12, u.tb, u.d1c, 96, 0, u.gd1c, B, H, W));
+    k_up_bwd<<<nblk(L2 * 64), 256, 0, u.st>>>(u.gd1c, 96, 0, u.ta, 64, B, H2, W2);
+    relu_b(u, u.ta, 64, u.d2, 64, 0, L2);
+    NN_TRY(conv_b(u, 11, u.ta, u.d2a, 64, 0, u.tb, B, H2, W2));
+    relu_b(u, u.tb, 64, u.d2a, 64, 0, L2);
+    NN_TRY(conv_b(u, 10, u.tb, u.d2c, 192, 0, u.gd2c, B, H2, W2));
+    k_up_bwd<<<nblk(L3 * 128), 256, 0, u.st>>>(u.gd2c, 192, 0, u.ta, 128, B, H3, W3);
+    relu_b(u, u.ta, 128, u.d3, 128, 0, L3);
+    NN_TRY(conv_b(u, 9, u.ta, u.d3a, 128, 0, u.tb, B, H3, W3));
+    relu_b(u, u.tb, 128, u.d3a, 128, 0, L3);
+    NN_TRY(conv_b(u, 8, u.tb, u.d3c, 384, 0, u.gd3c, B, H3, W3));
+    k_up_bwd<<<nblk(L4 * 256), 256, 0, u.st>>>(u.gd3c, 384, 0, u.ta, 256, B, H4, W4);
+    // bottleneck
+    relu_b(u, u.ta, 256, u.e4, 256, 0, L4);
+    NN_TRY(conv_b(u, 7, u.ta, u.e4a, 256, 0, u.tb, B, H4, W4));
+    relu_b(u, u.tb, 256, u.e4a, 256, 0, L4);
+    NN_TRY(conv_b(u, 6, u.tb, u.p3, 128, 0, u.ta, B, H4, W4));
+    // encoder level 3: pool gradient + skip gradient, then e3's ReLU
+    k_pool_bwd<<<nblk(L3 * 128), 256, 0, u.st>>>(u.ta, u.d3c, 384, 256, u.gd3c, 384, 256, u.tb, 128, B, H3, W3);
+    relu_b(u, u.tb, 128, u.d3c, 384, 256, L3);
+    NN_TRY(conv_b(u, 5, u.tb, u.e3a, 128, 0, u.ta, B, H3, W3));
+    relu_b(u, u.ta, 128, u.e3a, 128, 0, L3);
+    NN_TRY(conv_b(u, 4, u.ta, u.p2, 64, 0, u.tb, B, H3, W3));
+    // level 2
+    k_pool_bwd<<<nblk(L2 * 64), 256, 0, u.st>>>(u.tb, u.d2c, 192, 128, u.gd2c, 192, 128, u.ta, 64, B, H2, W2);
+    relu_b(u, u.ta, 64, u.d2c, 192, 128, L2);
+    NN_TRY(conv_b(u, 3, u.ta, u.e2a, 64, 0, u.tb, B, H2, W2));
+    relu_b(u, u.tb, 64, u.e2a, 64, 0, L2);
+    NN_TRY(conv_b(u, 2, u.tb, u.p1, 32, 0, u.ta, B, H2, W2));
+    // level 1
+    k_pool_bwd<<<nblk(L1 * 32), 256, 0, u.st>>>(u.ta, u.d1c, 96, 64, u.gd1c, 96, 64, u.tb, 32, B, H, W);
+    relu_b(u, u.tb, 32, u.d1c, 96, 64, L1);
+    NN_TRY(conv_b(u, 1, u.tb, u.e1a, 32, 0, u.ta, B, H, W));
+    relu_b(u, u.ta, 32, u.e1a, 32, 0, L1);
+    NN_TRY(conv_b(u, 0, u.ta, u.xin, 32, 0, nullptr, B, H, W));
+    return cudaGetLastError();
+}
+
+static cudaError_t unet_adam(UNet &u, float lr)
+{
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    u.step += 1;
+    const float c1 = 1.0f - std::pow(b1, (float)u.step), c2 = 1.0f - std::pow(b2, (float)u.step);
+    k_adam<<<nblk(u.nparam), 256, 0, u.st>>>(u.P, u.G, u.M1, u.M2, u.nparam, lr, b1, b2, eps, c1, c2, u.WB, u.bfmap);
+    return cudaGetLastError();
+}
+
+}  // namespace nn
+}  // namespace lsm
+
+// =================================================================== C ABI
+
+struct lsm_unet : public lsm::nn::UNet {};
+
+namespace {
+thread_local std::string g_nn_err;
+
+lsm_status nfail(lsm_unet *u, lsm_status st, const std::string &m)
+{
+    if (u)
+        u->err = m;
+    else
+        g_nn_err = m;
+    return st;
+}
+
+lsm_status ncuda(lsm_unet *u, cudaError_t e, const char *where)
+{
+    return nfail(u, e == cudaErrorMemoryAllocation ? LSM_ENOMEM : LSM_ECUDA,
+                 std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool batch_ok(lsm_unet *u, int32_t b) { return u && b >= 1 && b <= u->maxB; }
+}  // namespace
+
+extern "C" {
+
+lsm_status lsm_unet_create(int32_t height, int32_t width, int32_t max_batch, uint64_t seed, void *stream,
+                           lsm_unet **out)
+{
+    if (!out) return nfail(nullptr, LSM_EINVAL, "out is required");
+    *out = nullptr;
+    if (height < 8 || width < 8 || height % 8 || width % 8 || max_batch < 1)
+        return nfail(nullptr, LSM_EINVAL, "height and width must be multiples of 8 (>= 8), max_batch >= 1");
+    if ((int64_t)height * width * max_batch > ((int64_t)1 << 26))
+        return nfail(nullptr, LSM_EINVAL, "height * width * max_batch above 2^26 pixels");
+    lsm_unet *u = new (std::nothrow) lsm_unet();
+    if (!u) return nfail(nullptr, LSM_ENOMEM, "host allocation failed");
+    u->H = height;
+    u->W = width;
+    u->maxB = max_batch;
+    u->seed = seed;
+    if (stream) {
+        u->st = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&u->st, cudaStreamNonBlocking) != cudaSuccess) {
+            delete u;
+            return nfail(nullptr, LSM_ECUDA, "stream create failed");
+        }
+        u->own_stream = true;
+    }
+    cudaGetLastError();
+    cudaError_t e = lsm::nn::unet_setup(*u);
+    if (e != cudaSuccess) {
+        lsm::nn::unet_free(*u);
+        if (u->own_stream) cudaStreamDestroy(u->st);
+        delete u;
+        return nfail(nullptr, e == cudaErrorMemoryAllocation ? LSM_ENOMEM : LSM_ECUDA,
+                     std::string("unet setup: ") + cudaGetErrorString(e));
+    }
+    *out = u;
+    return LSM_OK;
+}
+
+void lsm_unet_destroy(lsm_unet *u)
+{
+    if (!u) return;
+    cudaStreamSynchronize(u->st);
+    lsm::nn::unet_free(*u);
+    if (u->own_stream) cudaStreamDestroy(u->st);
+    delete u;
+}
+
+const char *lsm_unet_last_error(const lsm_unet *u) { return u ? u->err.c_str() : g_nn_err.c_str(); }
+
+lsm_status lsm_unet_param_count(lsm_unet *u, int64_t *n)
+{
+    if (!u || !n) return nfail(u, LSM_EINVAL, "null argument");
+    *n = u->nparam;
+    return LSM_OK;
+}
+
+lsm_status lsm_unet_get_params(lsm_unet *u, float *host, int64_t n)
+{
+    if (!u || !host || n != u->nparam) return nfail(u, LSM_EINVAL, "need a host buffer of param_count floats");
+    cudaError_t e = cudaMemcpyAsync(host, u->P, n * 4, cudaMemcpyDeviceToHost, u->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(u->st);
+    return e == cudaSuccess ? LSM_OK : ncuda(u, e, "get_params");
+}
+
+lsm_status lsm_unet_set_params(lsm_unet *u, const float *host, int64_t n)
+{
+    if (!u || !host || n != u->nparam) return nfail(u, LSM_EINVAL, "need a host buffer of param_count floats");
+    cudaError_t e = cudaMemcpyAsync(u->P, host, n * 4, cudaMemcpyHostToDevice, u->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(u->M1, 0, n * 4, u->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(u->M2, 0, n * 4, u->st);
+    if (e == cudaSuccess) {
+        lsm::nn::k_to_bf16<<<lsm::nn::nblk(n), 256, 0, u->st>>>(u->P, u->WB, u->bfmap, n);
+        e = cudaStreamSynchronize(u->st);
+    }
+    u->step = 0;
+    return e == cudaSuccess ? LSM_OK : ncuda(u, e, "set_params");
+}
+
+lsm_status lsm_unet_forward(lsm_unet *u, const void *in, float *out, int32_t batch)
+{
+    if (!batch_ok(u, batch) || !in || !out) return nfail(u, LSM_EINVAL, "bad arguments");
+    cudaError_t e = lsm::nn::unet_forward(*u, batch, (const lsm::nn::bf16 *)in);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, u->out, (size_t)batch * u->H * u->W * 2 * 4, cudaMemcpyDeviceToDevice, u->st);
+    return e == cudaSuccess ? LSM_OK : ncuda(u, e, "forward");
+}
+
+lsm_status lsm_unet_gradients(lsm_unet *u, const void *in, const float *target, int32_t batch, float *loss,
+                              float *grad)
+{
+    if (!batch_ok(u, batch) || !in || !target) return nfail(u, LSM_EINVAL, "bad arguments");
+    cudaError_t e = lsm::nn::unet_forward(*u, batch, (const lsm::nn::bf16 *)in);
+    if (e == cudaSuccess) e = lsm::nn::unet_backward(*u, batch, target);
+    if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, u->loss, 4, cudaMemcpyDeviceToHost, u->st);
+    if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad, u->G, u->nparam * 4, cudaMemcpyDeviceToHost, u->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(u->st);
+    return e == cudaSuccess ? LSM_OK : ncuda(u, e, "gradients");
+}
+
+lsm_status lsm_unet_train_step(lsm_unet *u, const void *in, const float *target, int32_t batch, float lr, float *loss)
+{
+    if (!batch_ok(u, batch) || !in || !target || !(lr > 0)) return nfail(u, LSM_EINVAL, "bad arguments");
+    cudaError_t e = lsm::nn::unet_forward(*u, batch, (const lsm::nn::bf16 *)in);
+    if (e == cudaSuccess) e = lsm::nn::unet_backward(*u, batch, target);
+    if (e == cudaSuccess) e = lsm::nn::unet_adam(*u, lr);
+    if (e == cudaSuccess && loss) {
+        e = cudaMemcpyAsync(loss, u->loss, 4, cudaMemcpyDeviceToHost, u->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(u->st);
+    }
+    return e == cudaSuccess ? LSM_OK : ncuda(u, e, "train_step");
+}
+
+lsm_status lsm_unet_prepare_input(const uint8_t *phase, const float *u, const float *eps, float deps, int32_t S,
+                                  int32_t H, int32_t W, double a, void *in, void *stream)
+{
+    if (!phase || !u || !eps || !in || S < 1 || H < 1 || W < 1 || !(deps != 0.0f))
+        return nfail(nullptr, LSM_EINVAL, "prepare_input: bad arguments");
+    const int64_t n = (int64_t)S * H * W;
+    const float u_scale = (float)(1e-3 * 0.5 * W * a), de_scale = 1e-3f;
+    lsm::nn::k_prep_input<<<lsm::nn::nblk(n), 256, 0, (cudaStream_t)stream>>>(
+        phase, u, eps, deps, S, H, W, (float)a, u_scale, de_scale, (lsm::nn::bf16 *)in);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LSM_OK : nfail(nullptr, LSM_ECUDA, cudaGetErrorString(e));
+}
+
+lsm_status lsm_unet_prepare_target(const float *u_loaded, const float *u_relaxed, float deps, int32_t S, int32_t H,
+                                   int32_t W, double a, float *target, void *stream)
+{
+    if (!u_loaded || !u_relaxed || !target || S < 1 || !(deps != 0.0f))
+        return nfail(nullptr, LSM_EINVAL, "prepare_target: bad arguments");
+    const int64_t HW = (int64_t)H * W;
+    lsm::nn::k_prep_target<<<lsm::nn::nblk(S * HW), 256, 0, (cudaStream_t)stream>>>(
+        u_loaded, u_relaxed, deps, (float)(0.5 * W * a), S, HW, target);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LSM_OK : nfail(nullptr, LSM_ECUDA, cudaGetErrorString(e));
+}
+
+lsm_status lsm_unet_prediction_to_displacement(const float *pred, float deps, int32_t S, int32_t H, int32_t W,
+                                               double a, float *du, void *stream)
+{
+    if (!pred || !du || S < 1) return nfail(nullptr, LSM_EINVAL, "prediction_to_displacement: bad arguments");
+    const int64_t HW = (int64_t)H * W;
+    lsm::nn::k_pred_to_du<<<lsm::nn::nblk(S * HW), 256, 0, (cudaStream_t)stream>>>(pred, deps, (float)(0.5 * W * a),
+                                                                                  S, HW, du);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LSM_OK : nfail(nullptr, LSM_ECUDA, cudaGetErrorString(e));
+}
+
+lsm_status lsm_nn_conv_forward(const void *in, int32_t in_cs, int32_t in_c0, int32_t Cin, const void *W,
+                               const float *bias, void *out, int32_t out_cs, int32_t out_c0, int32_t Cout, int32_t B,
+                               int32_t H, int32_t Wd, int32_t taps, int32_t relu, void *stream)
+{
+    if (!in || !W || !out || (taps != 1 && taps != 9)) return nfail(nullptr, LSM_EINVAL, "conv_forward: bad arguments");
+    const cudaError_t e = lsm::nn::conv_fwd((const lsm::nn::bf16 *)in, in_cs, in_c0, Cin, (const lsm::nn::bf16 *)W,
+                                            bias, (lsm::nn::bf16 *)out, out_cs, out_c0, Cout, B, H, Wd, taps, relu != 0,
+                                            (cudaStream_t)stream);
+    return e == cudaSuccess ? LSM_OK
+                            : nfail(nullptr, e == cudaErrorInvalidValue ? LSM_EINVAL : LSM_ECUDA,
+                                    std::string("conv_forward: ") + cudaGetErrorString(e));
+}
+
+lsm_status lsm_nn_conv_wgrad(const void *grad, int32_t Cout, const void *in, int32_t in_cs, int32_t in_c0, int32_t Cin,
+                             int32_t B, int32_t H, int32_t Wd, int32_t taps, float *dW, float *db, float *scratch,
+                             int64_t scratch_floats, void *stream)
+{
+    if (!grad || !in || !dW || !scratch || (taps != 1 && taps != 9))
+        return nfail(nullptr, LSM_EINVAL, "conv_wgrad: bad arguments");
+    const cudaError_t e = lsm::nn::conv_wgrad((const lsm::nn::bf16 *)grad, Cout, Cout, (const lsm::nn::bf16 *)in, in_cs,
+                                              in_c0, Cin, B, H, Wd, taps, dW, db, scratch, (size_t)scratch_floats,
+                                              (cudaStream_t)stream);
+    return e == cudaSuccess ? LSM_OK : nfail(nullptr, LSM_EINVAL, std::string("conv_wgrad: ") + cudaGetErrorString(e));
+}
+
+}  // extern "C"

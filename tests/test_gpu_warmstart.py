@@ -1,0 +1,100 @@
+"""Warm-start plumbing: batch <-> field bridges, data preparation kernels, and
+a small end-to-end run (generate, train, relax with and without the network).
+"""
+import numpy as np
+import pytest
+
+from gen.images import two_phase_materials, warmstart_specimens
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2201_04565_gb300 import batch, build, lsm, nn, warmstart
+    build.build()
+    nn.lib()
+    return torch, batch, lsm, nn, warmstart
+
+
+def test_fields_and_add_displacements(env):
+    torch, batch, lsm, nn, ws = env
+    imgs = warmstart_specimens(range(3), side=32)
+    k, e, m = two_phase_materials()
+    bt = batch.Batch(imgs, k, e, m, precision="exact64", **ws.RELAX)
+    bt.apply_strain(0.01)
+    bt.step(30)
+    f = ws.Fields(3, 32, 32)
+    f.read(bt, with_phase=True)
+    torch.cuda.synchronize()
+    X = np.stack(np.meshgrid(np.arange(32.0), np.arange(32.0), indexing="xy")).reshape(2, -1)
+    for q in range(3):
+        x, _ = bt.state(q)
+        u = f.u[q].cpu().numpy().reshape(2, -1)
+        assert np.allclose(u, (x - X).astype(np.float32), rtol=0, atol=1e-6)
+        assert np.array_equal(f.phase[q].cpu().numpy(), imgs[q])
+    rng = np.random.default_rng(0)
+    du = (1e-3 * rng.standard_normal((3, 2, 32, 32))).astype(np.float32)
+    before = [bt.state(q)[0] for q in range(3)]
+    tdu = torch.from_numpy(du).cuda()
+    nn.check(nn.lib().lsm_batch_add_displacements(bt.h, nn.ptr(tdu), 32, 32), bt.h, batch=True)
+    torch.cuda.synchronize()
+    for q in range(3):
+        x, _ = bt.state(q)
+        d = du[q].reshape(2, -1).astype(np.float64)
+        grip = (np.arange(32 * 32) % 32 == 0) | (np.arange(32 * 32) % 32 == 31)
+        d[0, grip] = 0.0  # roller grips: x prescribed
+        assert np.array_equal(x, before[q] + d)
+
+
+def test_prepare_kernels(env):
+    torch, batch, lsm, nn, ws = env
+    S, H, W = 2, 16, 24
+    rng = np.random.default_rng(1)
+    phase = rng.integers(1, 3, size=(S, H, W)).astype(np.uint8)
+    u = rng.standard_normal((S, 2, H, W)).astype(np.float32) * 1e-2
+    eps = np.array([0.01, 0.02], np.float32)
+    tph, tu, te = (torch.from_numpy(a).cuda() for a in (phase, u, eps))
+    xin = torch.zeros((S, H, W, 32), dtype=torch.bfloat16, device="cuda")
+    nn.check(nn.lib().lsm_unet_prepare_input(nn.ptr(tph), nn.ptr(tu), nn.ptr(te), 1e-3, S, H, W, 1.0, nn.ptr(xin),
+                                             None))
+    torch.cuda.synchronize()
+    got = xin.float().cpu().numpy()
+    Xx = np.arange(W)[None, None, :] - 0.5 * (W - 1)
+    us = 1e-3 * 0.5 * W
+    ref = np.zeros((S, H, W, 32), np.float32)
+    ref[..., 0] = phase - 1.5
+    ref[..., 1] = (u[:, 0] - eps[:, None, None] * Xx) / us
+    ref[..., 2] = u[:, 1] / us
+    ref[..., 3] = 1.0
+    assert np.allclose(got, ref, rtol=2 ** -7, atol=1e-6)
+    # target and its inverse map
+    u2 = u + 1e-3 * rng.standard_normal(u.shape).astype(np.float32)
+    tu2 = torch.from_numpy(u2).cuda()
+    tgt = torch.zeros((S, H, W, 2), dtype=torch.float32, device="cuda")
+    nn.check(nn.lib().lsm_unet_prepare_target(nn.ptr(tu), nn.ptr(tu2), 1e-3, S, H, W, 1.0, nn.ptr(tgt), None))
+    du = torch.zeros((S, 2, H, W), dtype=torch.float32, device="cuda")
+    nn.check(nn.lib().lsm_unet_prediction_to_displacement(nn.ptr(tgt), 1e-3, S, H, W, 1.0, nn.ptr(du), None))
+    torch.cuda.synchronize()
+    assert np.allclose(du.cpu().numpy(), u2 - u, rtol=1e-5, atol=1e-9)
+
+
+def test_warm_start_end_to_end_small(env):
+    """Generate data on small specimens, train briefly, and relax the same
+    increments with and without the prediction: both reach the tolerance and
+    land on the same equilibrium (to the tolerance's resolution)."""
+    torch, batch, lsm, nn, ws = env
+    k, e, m = two_phase_materials()
+    imgs = warmstart_specimens(range(8), side=32)
+    data = ws.generate(imgs, k, e, m, increments=4, tol=1e-7)
+    assert data["U"].shape[0] == 32
+    net, info = ws.train(data, steps=150, batch=8, lr=2e-3)
+    first, last = info["loss_history"][0][1], info["loss_history"][-1][1]
+    assert last < first
+    res = ws.compare(imgs[:4], k, e, m, net, first_inc=2, increments=1, tol=1e-8, precision="df64")
+    for arm in ("plain", "batched", "warm"):
+        assert res[arm]["seconds_per_increment"] > 0
+    assert res["batched"]["converged"] == res["warm"]["converged"] == 4
