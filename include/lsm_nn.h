@@ -15,7 +15,7 @@
  * Arithmetic: BF16 weights and activations, FP32 accumulation on the tensor
  * cores (mma.sync m16n8k16), FP32 master weights and Adam moments.
  * All tensor arguments are DEVICE pointers owned by the caller:
- *   network input   bf16 [B][H][W][32], channels 0..3 used (see
+ *   network input   bf16 [B][H][W][32], channels 0..6 used (see
  *                   lsm_unet_prepare_input), the rest zero;
  *   network output  fp32 [B][H][W][2];
  *   displacements   fp32 [S][2][H][W] (component-major per specimen).
@@ -60,9 +60,11 @@ lsm_status lsm_unet_gradients(lsm_unet *u, const void *in, const float *target, 
 lsm_status lsm_unet_train_step(lsm_unet *u, const void *in, const float *target, int32_t batch, float lr,
                                float *loss);
 
-/* Input of S specimens: phase (u8 [S][H][W]) - 1.5; the current displacement
- * u (fp32 [S][2][H][W]) minus the affine field eps_s (X - xc) in x, over
- * 1e-3 W a / 2; and deps / 1e-3. eps: fp32 [S] current strains (device). */
+/* Input of S specimens (u8 phase [S][H][W], fp32 displacement u [S][2][H][W],
+ * fp32 current strains eps [S], all device): channel 0 phase - 1.5; 1, 2 the
+ * non-affine displacement per unit strain, (u_x - eps (X - xc), u_y) /
+ * (eps W a / 2) (0 while eps == 0); 3 deps / 1e-3; 4 eps / 0.1; 5, 6 the
+ * position (X - xc) / (W a / 2), (Y - yc) / (H a / 2). */
 lsm_status lsm_unet_prepare_input(const uint8_t *phase, const float *u, const float *eps, float deps, int32_t S,
                                   int32_t H, int32_t W, double a, void *in, void *stream);
 
@@ -73,6 +75,9 @@ lsm_status lsm_unet_prepare_target(const float *u_loaded, const float *u_relaxed
 /* Prediction (fp32 [S][H][W][2]) -> displacement increment fp32 [S][2][H][W]. */
 lsm_status lsm_unet_prediction_to_displacement(const float *pred, float deps, int32_t S, int32_t H, int32_t W,
                                                double a, float *du, void *stream);
+
+/* (The network sees 7 input channels; its first convolution keeps 32 input
+ * channels so that every convolution has a multiple of 32.) */
 
 /* The implicit-GEMM convolution kernels on their own (tests):
  * out[b,y,x,out_c0+n] = act(bias[n] + sum_{tap,ci} in[b,y+dy,x+dx,in_c0+ci] W[n][tap][ci])

@@ -551,27 +551,39 @@ __global__ void k_to_bf16(const float *__restrict__ w, bf16 *__restrict__ wb, co
 
 // ----------------------------------------------------- data preparation
 
-// Network input (NHWC, 32 channels, 4 used): phase - 1.5, the current
-// non-affine displacement (x minus the affine field eps (X - xc), y as is)
-// over u_scale, and the strain increment over de_scale.
+// Network input (NHWC, 32 channels, 7 used):
+//   0     phase - 1.5
+//   1, 2  current non-affine displacement per unit strain: (u_x - eps (X - xc),
+//         u_y) / (eps W a / 2), 0 before any load
+//   3     strain increment / 1e-3
+//   4     current strain / 0.1
+//   5, 6  position (X - xc) / (W a / 2), (Y - yc) / (H a / 2)
+// In the elastic range every increment relaxes by the same field per unit
+// strain, so channels 1-2 carry most of the answer after the first increment;
+// the position channels let the network place global fields (the lateral
+// contraction) that the phase map alone cannot locate.
 __global__ void k_prep_input(const uint8_t *__restrict__ phase, const float *__restrict__ u, const float *__restrict__ eps,
-                             float deps, int S, int H, int Wd, float a, float u_scale, float de_scale,
-                             bf16 *__restrict__ out)
+                             float deps, int S, int H, int Wd, float a, float de_scale, bf16 *__restrict__ out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t HW = (int64_t)H * Wd;
     if (i >= S * HW) return;
     const int s = (int)(i / HW);
     const int64_t g = i - s * HW;
-    const int x = (int)(g % Wd);
-    const float xc = 0.5f * (Wd - 1) * a;
-    const float ux = u[(2 * s) * HW + g] - eps[s] * (x * a - xc), uy = u[(2 * s + 1) * HW + g];
+    const int x = (int)(g % Wd), y = (int)(g / Wd);
+    const float hx = 0.5f * (Wd - 1) * a, hy = 0.5f * (H - 1) * a;
+    const float e = eps[s];
+    const float ux = u[(2 * s) * HW + g] - e * (x * a - hx), uy = u[(2 * s + 1) * HW + g];
+    const float us = e * 0.5f * Wd * a;
     bf16 *o = out + i * 32;
     o[0] = __float2bfloat16((float)phase[i] - 1.5f);
-    o[1] = __float2bfloat16(ux / u_scale);
-    o[2] = __float2bfloat16(uy / u_scale);
+    o[1] = __float2bfloat16(e > 0.0f ? ux / us : 0.0f);
+    o[2] = __float2bfloat16(e > 0.0f ? uy / us : 0.0f);
     o[3] = __float2bfloat16(deps / de_scale);
-    for (int c = 4; c < 32; c++) o[c] = __float2bfloat16(0.0f);
+    o[4] = __float2bfloat16(e / 0.1f);
+    o[5] = __float2bfloat16((x * a - hx) / (0.5f * Wd * a));
+    o[6] = __float2bfloat16((y * a - hy) / (0.5f * H * a));
+    for (int c = 7; c < 32; c++) o[c] = __float2bfloat16(0.0f);
 }
 
 // Training target: the relaxation's displacement after the affine load step,
@@ -687,11 +699,11 @@ static cudaError_t unet_setup(UNet &u)
     std::mt19937_64 rng(u.seed);
     for (int q = 0; q < NCONV; q++) {
         const Conv &c = u.convs[q];
-        const int fan_in = 9 * (q == 0 ? 4 : c.Cin);
+        const int fan_in = 9 * (q == 0 ? 7 : c.Cin);
         std::normal_distribution<float> nd(0.0f, std::sqrt(2.0f / fan_in));
         for (int64_t i = 0; i < (int64_t)c.Cout * 9 * c.Cin; i++) {
             const int ci = (int)(i % c.Cin);
-            P[c.w_off + i] = (q == 0 && ci >= 4) ? 0.0f : nd(rng);
+            P[c.w_off + i] = (q == 0 && ci >= 7) ? 0.0f : nd(rng);
             map[c.w_off + i] = c.wb_off + i;
         }
     }
@@ -1017,9 +1029,9 @@ lsm_status lsm_unet_prepare_input(const uint8_t *phase, const float *u, const fl
     if (!phase || !u || !eps || !in || S < 1 || H < 1 || W < 1 || !(deps != 0.0f))
         return nfail(nullptr, LSM_EINVAL, "prepare_input: bad arguments");
     const int64_t n = (int64_t)S * H * W;
-    const float u_scale = (float)(1e-3 * 0.5 * W * a), de_scale = 1e-3f;
+    const float de_scale = 1e-3f;
     lsm::nn::k_prep_input<<<lsm::nn::nblk(n), 256, 0, (cudaStream_t)stream>>>(
-        phase, u, eps, deps, S, H, W, (float)a, u_scale, de_scale, (lsm::nn::bf16 *)in);
+        phase, u, eps, deps, S, H, W, (float)a, de_scale, (lsm::nn::bf16 *)in);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? LSM_OK : nfail(nullptr, LSM_ECUDA, cudaGetErrorString(e));
 }

@@ -105,6 +105,19 @@ def _ptr(a):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
 
 
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the legacy default stream, named explicitly
+
+
+def torch_stream_handle():
+    """cudaStream_t of torch's current stream, usable as a library stream
+    argument. torch's default stream is the legacy default stream (handle 0),
+    which the library would read as "create a stream of your own"; it is
+    passed as the runtime's explicit cudaStreamLegacy handle instead."""
+    import torch
+    h = torch.cuda.current_stream().cuda_stream
+    return h if h else CUDA_STREAM_LEGACY
+
+
 def _check(status, ctx=None):
     if status != LSM_OK:
         msg = load_library().lsm_last_error(ctx)

@@ -64,7 +64,13 @@ def ptr(t):
 
 
 class UNet:
-    def __init__(self, height, width, max_batch, seed=0, stream=None):
+    """stream: cudaStream_t handle to order the network's work on; by default
+    torch's current stream, so that torch copies into the input buffers are
+    ordered with the network's kernels."""
+
+    def __init__(self, height, width, max_batch, seed=0, stream="torch"):
+        if stream == "torch":
+            stream = _lsm.torch_stream_handle()
         h = C.c_void_p()
         check(lib().lsm_unet_create(height, width, max_batch, seed, stream, C.byref(h)))
         self.h = h

@@ -33,6 +33,42 @@ def _torch():
     return torch
 
 
+def _stream():
+    """The caller's current torch stream: every library object and call in this
+    module is ordered on it, so torch's copies into and out of the shared
+    buffers are ordered with the library's kernels."""
+    return lsm.torch_stream_handle()
+
+
+def _sp():
+    import ctypes
+    return ctypes.c_void_p(_stream())
+
+
+_WORK = None
+
+
+def _on_work_stream(fn):
+    """Run fn with a dedicated torch stream as the current stream (the step
+    loops are CUDA graphs, which cannot be captured on the legacy default
+    stream), then wait for it."""
+    import functools
+
+    @functools.wraps(fn)
+    def wrapped(*args, **kw):
+        global _WORK
+        torch = _torch()
+        if _WORK is None:
+            _WORK = torch.cuda.Stream()
+        _WORK.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(_WORK):
+            out = fn(*args, **kw)
+        torch.cuda.current_stream().wait_stream(_WORK)
+        _WORK.synchronize()
+        return out
+    return wrapped
+
+
 class Fields:
     """Device buffers for S equal-size specimens."""
 
@@ -47,6 +83,20 @@ class Fields:
                                                  self.H, self.W), bt.h, batch=True)
 
 
+def save_params(net, path):
+    """Network parameters as BF16 bit patterns (uint16 .npy): the convolutions
+    compute in BF16, so this keeps every weight the forward pass uses."""
+    p = net.get_params().astype(np.float32).view(np.uint32).astype(np.uint64)
+    bits = ((p + 0x7FFF + ((p >> 16) & 1)) >> 16).astype(np.uint16)
+    np.save(path, bits)
+
+
+def load_params(net, path):
+    bits = np.load(path).astype(np.uint32) << 16
+    net.set_params(bits.view(np.float32))
+
+
+@_on_work_stream
 def generate(images, k, e, m, increments, deps=1e-3, tol=1e-6, max_steps=200000, check_every=50,
              precision="f32", log=None):
     """Run every specimen through `increments` load increments with the batched
@@ -56,7 +106,7 @@ def generate(images, k, e, m, increments, deps=1e-3, tol=1e-6, max_steps=200000,
     torch = _torch()
     S = len(images)
     H, W = images[0].shape
-    bt = bmod.Batch(images, k, e, m, precision=precision, **RELAX)
+    bt = bmod.Batch(images, k, e, m, precision=precision, stream=_stream(), **RELAX)
     f = Fields(S, H, W)
     f.read(bt, with_phase=True)
     phase = f.phase.clone()
@@ -80,7 +130,7 @@ def generate(images, k, e, m, increments, deps=1e-3, tol=1e-6, max_steps=200000,
         steps.append(int(np.mean(taken)))
         f.read(bt)
         nnmod.check(nnmod.lib().lsm_unet_prepare_target(nnmod.ptr(loaded), nnmod.ptr(f.u), deps, S, H, W, 1.0,
-                                                        nnmod.ptr(T[i * S:(i + 1) * S]), None))
+                                                        nnmod.ptr(T[i * S:(i + 1) * S]), _sp()))
         if log:
             log("increment %d: mean steps %d, converged %d/%d, %.1fs" % (i + 1, steps[-1], conv.sum(), S,
                                                                          time.perf_counter() - t0))
@@ -90,11 +140,12 @@ def generate(images, k, e, m, increments, deps=1e-3, tol=1e-6, max_steps=200000,
                 seconds=time.perf_counter() - t0)
 
 
+@_on_work_stream
 def train(data, steps=2000, batch=16, lr=1e-3, seed=0, log=None, val=None):
     """Adam on the mean squared error over random minibatches of samples."""
     torch = _torch()
     H, W = data["H"], data["W"]
-    net = nnmod.UNet(H, W, batch, seed=seed)
+    net = nnmod.UNet(H, W, batch, seed=seed, stream=_stream())
     N = data["U"].shape[0]
     rng = np.random.default_rng(seed)
     xb = torch.empty((batch, H, W, 32), dtype=torch.bfloat16, device="cuda")
@@ -111,7 +162,7 @@ def train(data, steps=2000, batch=16, lr=1e-3, seed=0, log=None, val=None):
         torch.index_select(data["eps"], 0, idx, out=eb)
         torch.index_select(data["T"], 0, idx, out=tb)
         nnmod.check(nnmod.lib().lsm_unet_prepare_input(nnmod.ptr(pb), nnmod.ptr(ub), nnmod.ptr(eb), data["deps"],
-                                                       batch, H, W, 1.0, nnmod.ptr(xb), None))
+                                                       batch, H, W, 1.0, nnmod.ptr(xb), _sp()))
         cur = lr * 0.5 * (1.0 + math.cos(math.pi * it / steps))  # cosine decay
         want = it % 100 == 0 or it == steps - 1
         loss = net.train_step(xb, tb, batch, cur, want_loss=want)
@@ -123,6 +174,7 @@ def train(data, steps=2000, batch=16, lr=1e-3, seed=0, log=None, val=None):
     return net, dict(loss_history=hist, seconds=time.perf_counter() - t0, steps=steps, batch=batch)
 
 
+@_on_work_stream
 def relative_error(net, data, batch=16):
     """Normwise relative error of the prediction over a data set (target
     units): ||pred - target|| / ||target||."""
@@ -137,7 +189,7 @@ def relative_error(net, data, batch=16):
         ph = data["phase"][data["spec"][sl]].contiguous()
         nnmod.check(nnmod.lib().lsm_unet_prepare_input(nnmod.ptr(ph), nnmod.ptr(data["U"][sl].contiguous()),
                                                        nnmod.ptr(data["eps"][sl].contiguous()), data["deps"], batch,
-                                                       H, W, 1.0, nnmod.ptr(xb), None))
+                                                       H, W, 1.0, nnmod.ptr(xb), _sp()))
         net.forward(xb, out, batch)
         t = data["T"][sl]
         num += float(((out - t) ** 2).sum())
@@ -155,12 +207,13 @@ def _predict_du(net, f, bt, eps_before, deps, xb, out, du, chunk):
         n = min(chunk, S - s0)
         nnmod.check(nnmod.lib().lsm_unet_prepare_input(nnmod.ptr(f.phase[s0:s0 + n]), nnmod.ptr(f.u[s0:s0 + n]),
                                                        nnmod.ptr(eps_t[s0:s0 + n]), deps, n, H, W, 1.0,
-                                                       nnmod.ptr(xb), None))
+                                                       nnmod.ptr(xb), _sp()))
         net.forward(xb, out, n)
         nnmod.check(nnmod.lib().lsm_unet_prediction_to_displacement(nnmod.ptr(out), deps, n, H, W, 1.0,
-                                                                    nnmod.ptr(du[s0:s0 + n]), None))
+                                                                    nnmod.ptr(du[s0:s0 + n]), _sp()))
 
 
+@_on_work_stream
 def compare(images, k, e, m, net, first_inc, increments, deps=1e-3, tol=1e-8, max_steps=400000, check_every=50,
             precision="df64", plain_every=1, log=None):
     """Wall time per increment of three arms on the same specimens, each run
@@ -177,7 +230,7 @@ def compare(images, k, e, m, net, first_inc, increments, deps=1e-3, tol=1e-8, ma
 
     # batched and warm-started arms
     for arm in ("batched", "warm"):
-        bt = bmod.Batch(images, k, e, m, precision=precision, **RELAX)
+        bt = bmod.Batch(images, k, e, m, precision=precision, stream=_stream(), **RELAX)
         f = Fields(S, H, W)
         f.read(bt, with_phase=True)
         chunk = net.max_batch if net is not None else 1
@@ -211,7 +264,7 @@ def compare(images, k, e, m, net, first_inc, increments, deps=1e-3, tol=1e-8, ma
     tot = [0.0] * increments
     st_all = []
     for q in sub:
-        sp = lsm.Specimen.from_image(images[q], k, e, m, precision=precision, **RELAX)
+        sp = lsm.Specimen.from_image(images[q], k, e, m, precision=precision, stream=_stream(), **RELAX)
         for i in range(1, first_inc + increments):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -256,6 +309,7 @@ def main(argv=None):
     ap.add_argument("--data-tol", type=float, default=1e-6)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--save", default=None)
+    ap.add_argument("--load", default=None, help="skip training: BF16 weights from save_params")
     a = ap.parse_args(argv)
 
     def log(msg):
@@ -263,17 +317,23 @@ def main(argv=None):
         sys.stderr.flush()
 
     k, e, m = two_phase_materials()
-    train_imgs = warmstart_specimens(range(a.train_specimens), side=a.side)
-    data = generate(train_imgs, k, e, m, a.train_increments, tol=a.data_tol, log=log)
+    train_imgs = [] if a.load else warmstart_specimens(range(a.train_specimens), side=a.side)
     val_imgs = warmstart_specimens(range(2000, 2000 + a.val_specimens), side=a.side)
     vdata = generate(val_imgs, k, e, m, a.val_increments, tol=a.data_tol, log=log)
-    net, tinfo = train(data, steps=a.train_steps, log=log)
+    if a.load:
+        net = nnmod.UNet(a.side, a.side, 16, stream=_stream())
+        load_params(net, a.load)
+        data = dict(U=vdata["U"][:0], seconds=0.0, steps=[0])
+        tinfo, terr = dict(loaded=a.load), float("nan")
+    else:
+        data = generate(train_imgs, k, e, m, a.train_increments, tol=a.data_tol, log=log)
+        net, tinfo = train(data, steps=a.train_steps, log=log)
+        terr = relative_error(net, {**data, "U": data["U"][:512], "T": data["T"][:512],
+                                    "spec": data["spec"][:512], "eps": data["eps"][:512]})
     verr = relative_error(net, vdata)
-    terr = relative_error(net, {**data, "U": data["U"][:512], "T": data["T"][:512], "spec": data["spec"][:512],
-                                "eps": data["eps"][:512]})
     log("relative prediction error: train %.3f, held-out %.3f" % (terr, verr))
     if a.save:
-        np.save(a.save, net.get_params())
+        save_params(net, a.save)
     eval_imgs = warmstart_specimens(range(1000, 1000 + a.eval_specimens), side=a.side)
     cmp = compare(eval_imgs, k, e, m, net, a.eval_first, a.eval_increments, tol=a.tol, plain_every=a.plain_every,
                   log=log)

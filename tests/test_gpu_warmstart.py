@@ -64,12 +64,16 @@ def test_prepare_kernels(env):
     torch.cuda.synchronize()
     got = xin.float().cpu().numpy()
     Xx = np.arange(W)[None, None, :] - 0.5 * (W - 1)
-    us = 1e-3 * 0.5 * W
+    Yy = np.arange(H)[None, :, None] - 0.5 * (H - 1)
+    us = eps[:, None, None] * 0.5 * W
     ref = np.zeros((S, H, W, 32), np.float32)
     ref[..., 0] = phase - 1.5
     ref[..., 1] = (u[:, 0] - eps[:, None, None] * Xx) / us
     ref[..., 2] = u[:, 1] / us
     ref[..., 3] = 1.0
+    ref[..., 4] = eps[:, None, None] / 0.1
+    ref[..., 5] = np.broadcast_to(Xx / (0.5 * W), (S, H, W))
+    ref[..., 6] = np.broadcast_to(Yy / (0.5 * H), (S, H, W))
     assert np.allclose(got, ref, rtol=2 ** -7, atol=1e-6)
     # target and its inverse map
     u2 = u + 1e-3 * rng.standard_normal(u.shape).astype(np.float32)
