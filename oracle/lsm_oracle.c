@@ -37,11 +37,23 @@
  * springs sorted by (i, j) with i < j.
  *
  * Layout: component-major arrays, component c of particle p at [c*n + p].
+ *
+ * Threads (orc_set_threads, OpenMP when compiled with -fopenmp): the spring
+ * pass is then split into a per-spring loop (break test and force, stored
+ * per spring) and a per-particle loop that adds each particle's springs in
+ * ascending spring order (acc + f as the lower endpoint, acc - f as the
+ * upper one, from +0). Every particle receives the same operations on the
+ * same operands in the same order as in the sequential scatter, so the
+ * result is bit-identical to the single-threaded pass; only the host time
+ * changes.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_EINVAL -1
@@ -62,6 +74,9 @@ typedef struct orc {
     double dt, gamma, xc, omega, grip_area, eps;
     int load_mode;
     int64_t step, first_break;
+    int nthreads;              /* > 1: the threaded spring pass below */
+    int64_t *row, *inc;        /* [n+1], [2m]: springs of each particle, ascending, (s << 1) | upper */
+    double *fs;                /* [dim*m] force of each spring on its lower endpoint */
 } orc;
 
 void orc_forces(const orc *o, const double *xs, double *F, double *U, double *W);
@@ -74,6 +89,7 @@ void orc_free(orc *o)
     free(o->mass); free(o->fix); free(o->grip);
     free(o->si); free(o->sj); free(o->k); free(o->r0); free(o->rc2);
     free(o->broken); free(o->brk_step);
+    free(o->row); free(o->inc); free(o->fs);
     free(o);
 }
 
@@ -384,6 +400,87 @@ static void orc_spring_pass(orc *o)
     }
 }
 
+/* Number of host threads for the spring pass (1 = the sequential loop
+ * above). Returns the number in use: 1 when built without OpenMP. */
+int orc_set_threads(orc *o, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#else
+    nthreads = 1;
+#endif
+    if (nthreads > 1 && !o->row) {
+        const int64_t n = o->n, m = o->m;
+        o->row = calloc((size_t)n + 1, sizeof(int64_t));
+        o->inc = calloc((size_t)(2 * m > 0 ? 2 * m : 1), sizeof(int64_t));
+        o->fs = calloc((size_t)o->dim * (size_t)(m > 0 ? m : 1), sizeof(double));
+        int64_t *fill = calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+        if (!o->row || !o->inc || !o->fs || !fill) {
+            free(fill);
+            return -1;
+        }
+        for (int64_t s = 0; s < m; s++) {
+            o->row[o->si[s] + 1]++;
+            o->row[o->sj[s] + 1]++;
+        }
+        for (int64_t p = 0; p < n; p++) o->row[p + 1] += o->row[p];
+        for (int64_t p = 0; p < n; p++) fill[p] = o->row[p];
+        for (int64_t s = 0; s < m; s++) { /* ascending s: each row comes out sorted */
+            o->inc[fill[o->si[s]]++] = s << 1;
+            o->inc[fill[o->sj[s]]++] = (s << 1) | 1;
+        }
+        free(fill);
+    }
+    o->nthreads = nthreads;
+    return nthreads;
+}
+
+/* The threaded form of orc_spring_pass (see the header comment). */
+static void orc_spring_pass_threads(orc *o)
+{
+    const int64_t n = o->n, m = o->m;
+    const int dim = o->dim;
+    const int64_t step = o->step;
+    int64_t nbroke = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(o->nthreads) reduction(+ : nbroke)
+#endif
+    for (int64_t s = 0; s < m; s++) {
+        for (int c = 0; c < dim; c++) o->fs[c * m + s] = 0.0;
+        if (o->broken[s]) continue;
+        int64_t i = o->si[s], j = o->sj[s];
+        double d[3] = {0.0, 0.0, 0.0};
+        for (int c = 0; c < dim; c++) d[c] = o->x[c * n + j] - o->x[c * n + i];
+        double r2 = d[0] * d[0] + d[1] * d[1];
+        if (dim == 3) r2 = r2 + d[2] * d[2];
+        if (r2 > o->rc2[s]) {
+            o->broken[s] = 1;
+            o->brk_step[s] = step;
+            nbroke += 1;
+            continue;
+        }
+        double r = sqrt(r2);
+        double c_s = o->k[s] * (r - o->r0[s]) / r;
+        for (int c = 0; c < dim; c++) o->fs[c * m + s] = c_s * d[c];
+    }
+    if (nbroke > 0 && o->first_break < 0) o->first_break = step;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(o->nthreads)
+#endif
+    for (int64_t p = 0; p < n; p++) {
+        for (int c = 0; c < dim; c++) {
+            double acc = 0.0;
+            for (int64_t e = o->row[p]; e < o->row[p + 1]; e++) {
+                const int64_t w = o->inc[e], s = w >> 1;
+                if (o->broken[s]) continue; /* no term, as in the scatter */
+                if (w & 1) acc -= o->fs[c * m + s];
+                else acc += o->fs[c * m + s];
+            }
+            o->F[c * n + p] = acc;
+        }
+    }
+}
+
 /* nsteps of damped velocity Verlet (Eqs. 3-5, half-step velocity form). */
 void orc_step(orc *o, int64_t nsteps)
 {
@@ -392,14 +489,23 @@ void orc_step(orc *o, int64_t nsteps)
     for (int64_t t = 0; t < nsteps; t++) {
         /* Eq. 3 via the half-step velocity: vh = v + dt/2 a; x += dt vh.
          * o->v holds vh until the end of the step. */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) if (o->nthreads > 1) num_threads(o->nthreads)
+#endif
         for (int64_t e = 0; e < dn; e++) {
             if (o->fix[e]) continue;
             double vh = o->v[e] + hdt * o->a[e];
             o->v[e] = vh;
             o->x[e] = o->x[e] + dt * vh;
         }
-        orc_spring_pass(o);
+        if (o->nthreads > 1)
+            orc_spring_pass_threads(o);
+        else
+            orc_spring_pass(o);
         /* Eq. 4 with viscous damping, then Eq. 5: v = vh + dt/2 a(t+dt). */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) if (o->nthreads > 1) num_threads(o->nthreads)
+#endif
         for (int64_t e = 0; e < dn; e++) {
             if (o->fix[e]) continue;
             int64_t p = e % o->n;

@@ -28,8 +28,12 @@ def build_oracle(force: bool = False) -> str:
             and os.path.getmtime(ORACLE_SO) >= os.path.getmtime(ORACLE_SRC)):
         return ORACLE_SO
     tmp = ORACLE_SO + ".tmp.%d" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11",
-                           "-fPIC", "-shared", "-o", tmp, ORACLE_SRC, "-lm"])
+    base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC", "-shared", "-o", tmp,
+            ORACLE_SRC, "-lm"]
+    try:  # OpenMP only serves orc_set_threads; without it the oracle is single-threaded
+        subprocess.check_call(base + ["-fopenmp"], stderr=subprocess.DEVNULL)
+    except (subprocess.CalledProcessError, OSError):
+        subprocess.check_call(base)
     os.replace(tmp, ORACLE_SO)
     return ORACLE_SO
 
@@ -59,6 +63,8 @@ def _load():
     lib.orc_observe.argtypes = [P, P]
     lib.orc_relax.restype = I
     lib.orc_relax.argtypes = [P, D, I64, I64, P]
+    lib.orc_set_threads.restype = I
+    lib.orc_set_threads.argtypes = [P, I]
     _lib = lib
     return lib
 
@@ -162,6 +168,14 @@ class Oracle:
 
     def step(self, nsteps: int):
         self._lib.orc_step(self._h, int(nsteps))
+
+    def set_threads(self, nthreads: int) -> int:
+        """Host threads of the spring pass (bit-identical results); returns
+        the number in use (1 without OpenMP)."""
+        got = self._lib.orc_set_threads(self._h, int(nthreads))
+        if got < 0:
+            raise MemoryError("oracle: incidence lists")
+        return got
 
     def apply_strain(self, eps: float):
         self._lib.orc_apply_strain(self._h, float(eps))

@@ -39,6 +39,7 @@ lsm_status device_status(Ctx *c)
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "synchronize");
     if (st & 1) return fail(c, LSM_ENONFINITE, "non-finite position or velocity detected");
+    if (st & 2) return fail(c, LSM_ENONFINITE, "position outside the fixed-point range of the F32/DF modes");
     return LSM_OK;
 }
 

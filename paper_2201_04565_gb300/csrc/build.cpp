@@ -90,6 +90,14 @@ bool net_from_image(const lsm_desc &d, HostNet &net, std::string &err)
             }
 
     const std::vector<Offset> offs = forward_offsets(d.dim, nx, ny);
+    net.offs.clear();
+    for (const Offset &o : offs) {
+        net.offs.push_back(o.dx);
+        net.offs.push_back(o.dy);
+        net.offs.push_back(o.dz);
+    }
+    net.sdir.clear();
+    net.sdir.reserve((size_t)n * offs.size());
     net.dim = d.dim;
     net.n = n;
     net.X.assign((size_t)d.dim * n, 0.0);
@@ -116,12 +124,14 @@ bool net_from_image(const lsm_desc &d, HostNet &net, std::string &err)
                     net.grip[p] = ix == 0 ? 1 : 2;
                     net.fixm[p] = d.grip_mode == 1 ? all : 1;
                 }
-                for (const Offset &o : offs) {
+                for (size_t oi = 0; oi < offs.size(); oi++) {
+                    const Offset &o = offs[oi];
                     const int jx = ix + o.dx, jy = iy + o.dy, jz = iz + o.dz;
                     if (jx < 0 || jx >= nx || jy < 0 || jy >= ny || jz < 0 || jz >= nz) continue;
                     const int64_t q = pid[v + o.lin];
                     if (q < 0) continue;
                     const int pq = d.phase[v + o.lin];
+                    net.sdir.push_back((uint8_t)oi);
                     net.si.push_back((int32_t)p);
                     net.sj.push_back((int32_t)q);
                     net.stype.push_back((uint16_t)((((ph - 1) * np) + (pq - 1)) * 2 + (o.shell - 1)));

@@ -362,10 +362,14 @@ void free_device(Ctx &c)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *tptrs[] = {c.tx[0], c.tx[1], c.tvh[0], c.tvh[1], c.tvobs, c.tph, c.tmask, c.tbrk, c.tmass,
-                     c.tinvm, c.tdf, c.tsbase, c.texport, c.texport_brk};
+                     c.tinvm, c.tdf, c.tsbase, c.texport, c.texport_brk, c.xf, c.sdir, c.imass, c.fsx};
     for (void *p : tptrs)
         if (p) cudaFree(p);
     c.tsbase = nullptr;
+    c.xf = nullptr;
+    c.sdir = nullptr;
+    c.imass = nullptr;
+    c.fsx = nullptr;
     c.texport = nullptr;
     c.texport_brk = nullptr;
     c.tx[0] = c.tx[1] = c.tvh[0] = c.tvh[1] = c.tvobs = c.tmass = c.tinvm = nullptr;
@@ -568,6 +572,9 @@ cudaError_t upload(Ctx &c)
     LSM_TRY(cudaMemsetAsync(c.fs, 0, (size_t)h.dim * (m ? m : 1) * sizeof(double), st));
     // host vectors above must stay alive until the copies finish
     LSM_TRY(cudaStreamSynchronize(st));
+    c.fixcsr = (h.precision == LSM_PREC_F32 || h.precision == LSM_PREC_DF) && !h.offs.empty() &&
+               (int64_t)h.sdir.size() == m;
+    if (c.fixcsr) LSM_TRY(fixcsr_upload(c));
     return cudaSuccess;
 }
 
@@ -576,6 +583,10 @@ cudaError_t upload(Ctx &c)
 template <int DIM, bool BREAK, bool SAMPLE>
 static void springs(Ctx &c)
 {
+    if (c.fixcsr) {
+        springs_fix<DIM, BREAK, SAMPLE>(c);
+        return;
+    }
     if (c.m == 0) {
         if (SAMPLE) cudaMemsetAsync(c.part_s, 0, 2 * sizeof(double), c.stream);
         return;
@@ -597,6 +608,10 @@ static void springs(Ctx &c)
 template <int DIM, int MODE, bool SAMPLE>
 static void gather(Ctx &c)
 {
+    if (c.fixcsr) {
+        gather_fix<DIM, MODE, SAMPLE>(c);
+        return;
+    }
     const double dt = c.h.dt, hdt = 0.5 * c.h.dt;
     k_gather<DIM, MODE, SAMPLE><<<grid_of(c.n), TPB, 0, c.stream>>>(
         c.n, c.m, c.row, c.inc, c.fs, c.x, c.v, c.a, c.mass, c.fixm, c.grip, dt, hdt,
@@ -617,6 +632,7 @@ static void enqueue_steps(Ctx &c, int64_t nsteps, bool record)
 {
     const double dt = c.h.dt, hdt = 0.5 * c.h.dt;
     k_drift<DIM><<<grid_of(c.n), TPB, 0, c.stream>>>(c.n, c.x, c.v, c.a, c.fixm, dt, hdt);
+    if (c.fixcsr) fixcsr_refresh(c);
     for (int64_t t = 0; t < nsteps; t++) {
         const bool last = t == nsteps - 1;
         if (last) {
@@ -682,6 +698,10 @@ cudaError_t launch_steps(Ctx &c, int64_t nsteps, bool record)
 cudaError_t launch_init_accel(Ctx &c)
 {
     if (c.tile) return tile_init_accel(c);
+    if (c.fixcsr) {
+        const cudaError_t e = fixcsr_refresh(c);  // positions may have been replaced
+        if (e != cudaSuccess) return e;
+    }
     if (c.dim == 3) {
         springs<3, false, false>(c);
         gather<3, G_INIT, false>(c);
@@ -722,6 +742,10 @@ cudaError_t launch_apply_strain(Ctx &c, double eps_old, double eps_new)
                                                        scale, eps_new, c.h.load_mode == 0,
                                                        c.d_eps);
     c.launches += 1;
+    if (c.fixcsr) {
+        c.launches += 1;
+        return fixcsr_refresh(c);
+    }
     return cudaGetLastError();
 }
 

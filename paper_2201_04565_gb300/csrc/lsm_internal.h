@@ -76,6 +76,8 @@ struct HostNet {
     int nx = 0, ny = 0, nz = 0, nphase = 0;
     std::vector<int64_t> pix;      // pixel of each particle (image builds)
     std::vector<uint8_t> phase;    // nx*ny*nz phase image (image builds)
+    std::vector<uint8_t> sdir;     // per spring: index of its lattice offset (image builds)
+    std::vector<int> offs;         // lattice offsets (dx, dy, dz) by index (image builds)
 };
 
 struct Ctx {
@@ -132,6 +134,12 @@ struct Ctx {
     long long a_fix = 0;                  // lattice spacing * 2^fix_S
     bool o_exact = false;                 // lattice vectors and |o|^2 exact as floats
     int64_t *tsbase = nullptr;            // [tnp] canonical index of each pixel's first spring
+    // spring-list path in the fixed-point modes (image builds, F32 / DF)
+    bool fixcsr = false;
+    long long *xf = nullptr;              // [dim][n] positions * 2^fix_S
+    uint8_t *sdir = nullptr;              // [m] lattice offset index of each spring
+    double *imass = nullptr;              // [n] 1 / mass
+    void *fsx = nullptr;                  // [dim][m] spring forces (float or double-float)
     uint8_t *texport = nullptr;           // [m] staging for canonical-order exports
     long long *texport_brk = nullptr;     // [m] staging for break steps
     int tcur = 0;
@@ -158,6 +166,14 @@ cudaError_t launch_steps(Ctx &c, int64_t nsteps, bool record);
 cudaError_t launch_apply_strain(Ctx &c, double eps_old, double eps_new);
 cudaError_t launch_observe(Ctx &c, DeviceSample *dst);
 void free_device(Ctx &c);
+
+// csr_fix.cu: spring-list path in the fixed-point modes (F32, DF)
+cudaError_t fixcsr_upload(Ctx &c);   // scale, tables, fixed-point copy of x
+cudaError_t fixcsr_refresh(Ctx &c);  // xf = x 2^S after x changed outside the step kernels
+template <int DIM, bool BREAK, bool SAMPLE>
+void springs_fix(Ctx &c);
+template <int DIM, int MODE, bool SAMPLE>  // MODE: end / drift / init / observe, as the FP64 gather
+void gather_fix(Ctx &c);
 
 // tile2d.cu
 cudaError_t tile_enqueue_steps(Ctx &c, int64_t nsteps, int start_buf);

@@ -8,6 +8,7 @@ Bars (floating point; derived in the design notes):
   - fast64 mode: positions within 1e-10 relative (normwise) after 1000+
     steps, identical broken set and first-break step, stress-strain within
     1e-6 relative before the first break;
+  - df64 mode (fixed-point spring vectors, double-float forces): as fast64;
   - f32 force mode: error against the oracle reported, bounded loosely.
 """
 import numpy as np
@@ -121,7 +122,7 @@ def test_c0_exact64_bit_identical(oracle_mod, L, path):
         assert a["residual"] == b["residual"]
 
 
-@pytest.mark.parametrize("path,precision", [(0, "fast64"), (1, "fast64"), (0, "df64")])
+@pytest.mark.parametrize("path,precision", [(0, "fast64"), (1, "fast64"), (0, "df64"), (1, "df64")])
 def test_c0_fast_modes_within_tolerance(oracle_mod, L, path, precision):
     """fast64 (reassociated FP64) and df64 (fixed-point spring vectors with
     double-float forces, FP64 integration) against the oracle."""
@@ -155,8 +156,10 @@ def test_c0_f32_force_error_is_bounded(oracle_mod, L, path):
     assert sg[-1]["sigma_vir"] == pytest.approx(so[-1]["sigma_vir"], rel=1e-3)
 
 
-@pytest.mark.parametrize("precision", ["exact64", "fast64"])
+@pytest.mark.parametrize("precision", ["exact64", "fast64", "df64", "f32"])
 def test_3d_foam_parity(oracle_mod, L, precision):
+    """3D foam under compression on the spring-list kernels; df64 and f32 run
+    the fixed-point spring vectors (the 2D tile kernel's arithmetic) there."""
     from gen.images import foam_volume
     img = foam_volume(20, 2.0, 0.45, seed=9)
     mats = one_phase_materials(1.0, 0.04)
@@ -166,6 +169,12 @@ def test_3d_foam_parity(oracle_mod, L, precision):
     xo, vo, _ = o.state()
     if precision == "exact64":
         assert np.array_equal(xg, xo) and np.array_equal(vg, vo)
+    elif precision == "f32":
+        X = o.topology()["X"]
+        rel_u = np.abs(xg - xo).max() / np.abs(xo - X).max()
+        print("3D f32: max displacement error / max displacement = %.3e" % rel_u)
+        assert rel_u < 1e-4
+        return
     else:
         assert _rel(xg, xo) <= 1e-10
     assert np.array_equal(g.broken()[0], o.broken()[0])
@@ -264,12 +273,13 @@ def test_tile_and_spring_list_paths_agree_bitwise(L):
     assert np.array_equal(outs[0][1][0], outs[1][1][0])
 
 
-@pytest.mark.parametrize("a", [1.3, 0.5])
-def test_df64_general_lattice_spacing(oracle_mod, L, a):
+@pytest.mark.parametrize("path,a", [(0, 1.3), (0, 0.5), (1, 1.3)])
+def test_df64_general_lattice_spacing(oracle_mod, L, path, a):
     """df64 with a lattice spacing whose lattice vectors are not (1.3) or are
-    (0.5) exact floats: both double-float branches against the oracle."""
+    (0.5) exact floats: both double-float branches of the tile kernel, and the
+    spring-list kernels, against the oracle."""
     img = inclusion_image(40, 32, 2.0, 5.0, 0.3, 8)
-    o, g = _pair(oracle_mod, L, img, two_phase_materials(), precision="df64", a=a)
+    o, g = _pair(oracle_mod, L, img, two_phase_materials(), precision="df64", a=a, path=path)
     _run_schedule(o, g, 30, 20, 2e-3)
     xg, _ = g.state()
     xo, _, _ = o.state()
