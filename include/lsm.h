@@ -228,6 +228,27 @@ lsm_status lsm_topology(lsm_ctx *ctx, int32_t *si, int32_t *sj, double *k, doubl
  * recorded sample; the sample history is unchanged). Synchronises. */
 lsm_status lsm_observe(lsm_ctx *ctx, lsm_sample *out);
 
+/* Per-particle fields of the current state (Section 3.2, Eqs. 7-8), for
+ * post-processing such as the paper's stress and strain maps.
+ *   stress  host, [ncomp][n] (ncomp = 3 in 2D: xx, yy, xy; 6 in 3D: xx, yy,
+ *           zz, xy, xz, yz), particle order as lsm_get_state: the virial
+ *           stress of Eq. 7 with the domain taken as one particle's cell,
+ *           (1/cell) [1/2 sum over the particle's intact springs of
+ *           (x_l - x_k)_a f_b - m v_a v_b], f the spring's force on the
+ *           particle; tension positive.
+ *   strain  host, [ncomp][n]: the Lagrangian strain (J^T J - I)/2 of Eq. 8,
+ *           J the least-squares affine map of the particle's first-neighbour
+ *           vectors (its springs with the smallest rest length, broken or
+ *           not) from the reference lattice to the current positions; NaN
+ *           where those vectors do not span the space.
+ *   cell_volume  the per-particle volume; <= 0 selects a^dim for image
+ *           builds and 1 for network builds.
+ * Either output may be NULL. Computed on the GPU in FP64 (correctly rounded
+ * operations); the first call allocates the spring lists a 2D tile-path
+ * context does not otherwise keep. Synchronises. Errors: LSM_EINVAL (null
+ * context), LSM_ENOMEM, LSM_ECUDA, or a pending device status. */
+lsm_status lsm_fields(lsm_ctx *ctx, double cell_volume, double *stress, double *strain);
+
 /* Block until all work queued on the context's stream is done; returns any
  * pending device status. */
 lsm_status lsm_synchronize(lsm_ctx *ctx);

@@ -575,6 +575,133 @@ void orc_observe(const orc *o, double *out)
     free(F);
 }
 
+/* Per-particle fields of Section 3.2 at the current state.
+ *
+ * stress, Eq. 7 with the domain taken as one particle's cell (volume cell):
+ *   sigma_ab(k) = (1/cell) [ 1/2 sum over the intact springs (k, l) of
+ *                 (x_l - x_k)_a f^{kl}_b  -  m_k v_a v_b ],
+ * f^{kl} the force on k from that spring (Eq. 2). With d = x_j - x_i and
+ * c = k (r - r0) / r, the force on i is c d and on j is -c d, so each
+ * endpoint receives 1/2 c d_a d_b.
+ *
+ * strain, Eq. 8 read as the Lagrangian strain 1/2 (J^T J - I) of the locally
+ * affine map J: the least-squares J with (x_l - x_k) ~ J (X_l - X_k) over
+ * the first-neighbour shell of k (its springs with the smallest rest
+ * length, broken or not), J = B A^-1 with A = sum X X^T, B = sum d X^T. NaN
+ * where the shell vectors do not span the space (|det A| tiny).
+ *
+ * Components, each an [n] block: 2D xx, yy, xy; 3D xx, yy, zz, xy, xz, yz.
+ * Either output may be NULL. */
+static const int ORC_PAIR[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+static const int ORC_PAIR2[3][2] = {{0, 0}, {1, 1}, {0, 1}};
+
+void orc_fields(const orc *o, double cell, double *stress, double *strain)
+{
+    const int64_t n = o->n, m = o->m;
+    const int dim = o->dim;
+    const int nq = dim == 3 ? 6 : 3;
+    const int (*pairs)[2] = dim == 3 ? ORC_PAIR : ORC_PAIR2;
+    if (stress) {
+        memset(stress, 0, (size_t)nq * n * sizeof(double));
+        for (int64_t s = 0; s < m; s++) {
+            if (o->broken[s]) continue;
+            int64_t i = o->si[s], j = o->sj[s];
+            double d[3] = {0.0, 0.0, 0.0};
+            for (int c = 0; c < dim; c++) d[c] = o->x[c * n + j] - o->x[c * n + i];
+            double r2 = d[0] * d[0] + d[1] * d[1];
+            if (dim == 3) r2 = r2 + d[2] * d[2];
+            double r = sqrt(r2);
+            double c_s = o->k[s] * (r - o->r0[s]) / r;
+            for (int q = 0; q < nq; q++) {
+                double t = 0.5 * (d[pairs[q][0]] * (c_s * d[pairs[q][1]]));
+                stress[q * n + i] += t;
+                stress[q * n + j] += t;
+            }
+        }
+        for (int64_t p = 0; p < n; p++)
+            for (int q = 0; q < nq; q++) {
+                double vv = o->mass[p] * o->v[pairs[q][0] * n + p] * o->v[pairs[q][1] * n + p];
+                stress[q * n + p] = (stress[q * n + p] - vv) / cell;
+            }
+    }
+    if (strain) {
+        double *rmin = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+        double *A = (double *)calloc((size_t)(n > 0 ? n : 1) * 9, sizeof(double));
+        double *B = (double *)calloc((size_t)(n > 0 ? n : 1) * 9, sizeof(double));
+        if (!rmin || !A || !B) {
+            free(rmin); free(A); free(B);
+            for (int64_t e = 0; e < (int64_t)nq * n; e++) strain[e] = NAN;
+            return;
+        }
+        for (int64_t p = 0; p < n; p++) rmin[p] = INFINITY;
+        for (int64_t s = 0; s < m; s++) {
+            if (o->r0[s] < rmin[o->si[s]]) rmin[o->si[s]] = o->r0[s];
+            if (o->r0[s] < rmin[o->sj[s]]) rmin[o->sj[s]] = o->r0[s];
+        }
+        for (int64_t s = 0; s < m; s++) {
+            int64_t i = o->si[s], j = o->sj[s];
+            double X[3] = {0.0, 0.0, 0.0}, d[3] = {0.0, 0.0, 0.0};
+            for (int c = 0; c < dim; c++) {
+                X[c] = o->X[c * n + j] - o->X[c * n + i];
+                d[c] = o->x[c * n + j] - o->x[c * n + i];
+            }
+            /* the products are the same seen from either endpoint */
+            for (int end = 0; end < 2; end++) {
+                int64_t p = end ? j : i;
+                if (o->r0[s] > rmin[p] * (1.0 + 1e-12)) continue;
+                for (int a = 0; a < dim; a++)
+                    for (int b = 0; b < dim; b++) {
+                        A[p * 9 + a * 3 + b] += X[a] * X[b];
+                        B[p * 9 + a * 3 + b] += d[a] * X[b];
+                    }
+            }
+        }
+        for (int64_t p = 0; p < n; p++) {
+            const double *Ap = A + p * 9, *Bp = B + p * 9;
+            double inv[9] = {0}, J[9] = {0};
+            double det, scale;
+            if (dim == 2) {
+                det = Ap[0] * Ap[4] - Ap[1] * Ap[3];
+                scale = 0.5 * (Ap[0] + Ap[4]);
+                inv[0] = Ap[4] / det; inv[1] = -Ap[1] / det;
+                inv[3] = -Ap[3] / det; inv[4] = Ap[0] / det;
+            } else {
+                double c00 = Ap[4] * Ap[8] - Ap[5] * Ap[7];
+                double c01 = Ap[5] * Ap[6] - Ap[3] * Ap[8];
+                double c02 = Ap[3] * Ap[7] - Ap[4] * Ap[6];
+                det = Ap[0] * c00 + Ap[1] * c01 + Ap[2] * c02;
+                scale = (Ap[0] + Ap[4] + Ap[8]) / 3.0;
+                inv[0] = c00 / det; inv[3] = c01 / det; inv[6] = c02 / det;
+                inv[1] = (Ap[2] * Ap[7] - Ap[1] * Ap[8]) / det;
+                inv[4] = (Ap[0] * Ap[8] - Ap[2] * Ap[6]) / det;
+                inv[7] = (Ap[1] * Ap[6] - Ap[0] * Ap[7]) / det;
+                inv[2] = (Ap[1] * Ap[5] - Ap[2] * Ap[4]) / det;
+                inv[5] = (Ap[2] * Ap[3] - Ap[0] * Ap[5]) / det;
+                inv[8] = (Ap[0] * Ap[4] - Ap[1] * Ap[3]) / det;
+            }
+            double sp = 1.0;
+            for (int c = 0; c < dim; c++) sp *= scale;
+            if (!(fabs(det) > 1e-12 * sp)) {
+                for (int q = 0; q < nq; q++) strain[q * n + p] = NAN;
+                continue;
+            }
+            for (int a = 0; a < dim; a++) /* J = B A^-1 */
+                for (int b = 0; b < dim; b++) {
+                    double t = 0.0;
+                    for (int c = 0; c < dim; c++) t += Bp[a * 3 + c] * inv[c * 3 + b];
+                    J[a * 3 + b] = t;
+                }
+            for (int q = 0; q < nq; q++) {
+                int a = pairs[q][0], b = pairs[q][1];
+                double t = 0.0;
+                for (int c = 0; c < dim; c++) t += J[c * 3 + a] * J[c * 3 + b];
+                strain[q * n + p] = 0.5 * (t - (a == b ? 1.0 : 0.0));
+            }
+        }
+        free(rmin); free(A); free(B);
+    }
+}
+
 /* Steps in batches of check_every until the residual is <= tol.
  * Returns ORC_OK, or ORC_ENOTCONV once max_steps were taken. */
 int orc_relax(orc *o, double tol, int64_t max_steps, int64_t check_every, int64_t *taken)

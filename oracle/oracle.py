@@ -65,6 +65,7 @@ def _load():
     lib.orc_relax.argtypes = [P, D, I64, I64, P]
     lib.orc_set_threads.restype = I
     lib.orc_set_threads.argtypes = [P, I]
+    lib.orc_fields.argtypes = [P, D, P, P]
     _lib = lib
     return lib
 
@@ -168,6 +169,15 @@ class Oracle:
 
     def step(self, nsteps: int):
         self._lib.orc_step(self._h, int(nsteps))
+
+    def fields(self, cell: float = 1.0):
+        """Per-particle virial stress and Lagrangian strain, each [ncomp, n]
+        (2D: xx, yy, xy; 3D: xx, yy, zz, xy, xz, yz)."""
+        nq = 6 if self.dim == 3 else 3
+        st = np.empty((nq, self.n))
+        sn = np.empty((nq, self.n))
+        self._lib.orc_fields(self._h, float(cell), _ptr(st), _ptr(sn))
+        return st, sn
 
     def set_threads(self, nthreads: int) -> int:
         """Host threads of the spring pass (bit-identical results); returns

@@ -419,6 +419,26 @@ lsm_status lsm_observe(lsm_ctx *c, lsm_sample *out)
     return device_status(c);
 }
 
+lsm_status lsm_fields(lsm_ctx *c, double cell_volume, double *stress, double *strain)
+{
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    lsm_status st = device_status(c);
+    if (st != LSM_OK) return st;
+    double cell = cell_volume;
+    if (!(cell > 0.0)) cell = c->h.nx > 0 ? std::pow(c->h.a, (double)c->h.dim) : 1.0;
+    cudaError_t e = lsm::fields_compute(*c, cell);
+    const int nq = c->h.dim == 3 ? 6 : 3;
+    const size_t bytes = (size_t)nq * c->n * sizeof(double);
+    if (e == cudaSuccess && stress && c->n)
+        e = cudaMemcpyAsync(stress, c->fout, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && strain && c->n)
+        e = cudaMemcpyAsync(strain, c->fout + (size_t)nq * c->n, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaErrorMemoryAllocation) return fail(c, LSM_ENOMEM, "fields: device allocation failed");
+    if (e != cudaSuccess) return cuda_fail(c, e, "fields");
+    return LSM_OK;
+}
+
 lsm_status lsm_synchronize(lsm_ctx *c)
 {
     if (!c) return fail(nullptr, LSM_EINVAL, "null context");

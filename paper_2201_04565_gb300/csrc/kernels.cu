@@ -353,6 +353,7 @@ static cudaError_t dalloc(T **p, size_t count)
 
 void free_device(Ctx &c)
 {
+    fields_free(c);
     for (auto &kv : c.graphs) cudaGraphExecDestroy(kv.second);
     c.graphs.clear();
     void *ptrs[] = {c.x, c.v, c.a, c.mass, c.Xx, c.fixm, c.grip, c.si, c.sj, c.stype, c.types,

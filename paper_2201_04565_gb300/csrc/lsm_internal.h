@@ -140,6 +140,16 @@ struct Ctx {
     uint8_t *sdir = nullptr;              // [m] lattice offset index of each spring
     double *imass = nullptr;              // [n] 1 / mass
     void *fsx = nullptr;                  // [dim][m] spring forces (float or double-float)
+    // per-particle fields (allocated by the first lsm_fields call)
+    double *fX = nullptr;                 // [dim][n] reference positions
+    double *fx = nullptr, *fv = nullptr;  // [dim][n] compact x, v (tile path)
+    double *fout = nullptr;               // [2][6][n] stress and strain
+    int64_t *frow = nullptr;              // [n+1] (tile path; the spring-list path uses row)
+    uint32_t *finc = nullptr;             // [2m]
+    int32_t *fsi = nullptr, *fsj = nullptr;
+    uint16_t *fstype = nullptr;
+    double *fmass = nullptr;              // [n]
+    int64_t *fpix = nullptr;              // [n] pixel of each particle
     uint8_t *texport = nullptr;           // [m] staging for canonical-order exports
     long long *texport_brk = nullptr;     // [m] staging for break steps
     int tcur = 0;
@@ -174,6 +184,10 @@ template <int DIM, bool BREAK, bool SAMPLE>
 void springs_fix(Ctx &c);
 template <int DIM, int MODE, bool SAMPLE>  // MODE: end / drift / init / observe, as the FP64 gather
 void gather_fix(Ctx &c);
+
+// fields.cu
+cudaError_t fields_compute(Ctx &c, double cell);  // -> fout (device), stream ordered
+void fields_free(Ctx &c);
 
 // tile2d.cu
 cudaError_t tile_enqueue_steps(Ctx &c, int64_t nsteps, int start_buf);

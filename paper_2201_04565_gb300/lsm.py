@@ -77,6 +77,7 @@ SIGNATURES = [
     ("lsm_topology", C.c_int, [_P, _P, _P, _P, _P, _P]),
     ("lsm_observe", C.c_int, [_P, C.POINTER(lsm_sample)]),
     ("lsm_synchronize", C.c_int, [_P]),
+    ("lsm_fields", C.c_int, [_P, C.c_double, _P, _P]),
     ("lsm_counters", C.c_int, [_P, _P, _P, _P]),
     ("lsm_spring_energy_static", C.c_int, [_I32, _I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
 ]
@@ -263,6 +264,17 @@ def lsm_observe(h):
     return s.as_dict()
 
 
+def lsm_fields(h, cell_volume=0.0, stress=True, strain=True):
+    """Per-particle virial stress and Lagrangian strain, each [ncomp, n]
+    (2D: xx, yy, xy; 3D: xx, yy, zz, xy, xz, yz); None for an output not asked for."""
+    n, m, dim = lsm_sizes(h)
+    nq = 6 if dim == 3 else 3
+    st = np.empty((nq, n)) if stress else None
+    sn = np.empty((nq, n)) if strain else None
+    _check(load_library().lsm_fields(h, float(cell_volume), _ptr(st), _ptr(sn)), h)
+    return st, sn
+
+
 def lsm_synchronize(h):
     _check(load_library().lsm_synchronize(h), h)
 
@@ -339,6 +351,9 @@ class Specimen:
 
     def observe(self):
         return lsm_observe(self.h)
+
+    def fields(self, cell_volume=0.0):
+        return lsm_fields(self.h, cell_volume)
 
     def synchronize(self):
         lsm_synchronize(self.h)

@@ -285,3 +285,37 @@ def test_df64_general_lattice_spacing(oracle_mod, L, path, a):
     xo, _, _ = o.state()
     assert _rel(xg, xo) <= 1e-10
     assert np.array_equal(g.broken()[0], o.broken()[0])
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_fields_match_oracle(oracle_mod, L, path):
+    """Per-particle virial stress and Lagrangian strain (Eqs. 7-8) after a run
+    through fracture (exact64: the same state), 2D on both paths and a voided
+    image with NaN shells; 1e-12 relative to each field's largest entry."""
+    img = inclusion_image(48, 40, 2.0, 5.0, 0.3, 12)
+    img[18:21, 10:30] = 0  # a slot of void pixels
+    img[5, 5:8] = 0
+    o, g = _pair(oracle_mod, L, img, two_phase_materials(), path=path)
+    _run_schedule(o, g, 12, 20, 6e-3)
+    assert o.broken()[0].sum() > 0
+    so, eo = o.fields(1.0)
+    sg, eg = g.fields()
+    assert sg.shape == so.shape == (3, o.n)
+    assert np.array_equal(np.isnan(eg), np.isnan(eo))
+    ok = ~np.isnan(eo)
+    assert np.abs(sg - so).max() <= 1e-12 * np.abs(so).max()
+    assert np.abs(eg[ok] - eo[ok]).max() <= 1e-12 * np.abs(eo[ok]).max()
+
+
+def test_fields_3d_match_oracle(oracle_mod, L):
+    from gen.images import foam_volume
+    img = foam_volume(12, 1.5, 0.5, seed=3)
+    o, g = _pair(oracle_mod, L, img, one_phase_materials(1.0, 0.04), grip_mode=1, a=1.5)
+    _run_schedule(o, g, 5, 20, -4e-3)
+    so, eo = o.fields(1.5 ** 3)
+    sg, eg = g.fields()
+    assert sg.shape == (6, o.n)
+    assert np.array_equal(np.isnan(eg), np.isnan(eo))
+    ok = ~np.isnan(eo)
+    assert np.abs(sg - so).max() <= 1e-12 * np.abs(so).max()
+    assert np.abs(eg[ok] - eo[ok]).max() <= 1e-12 * np.abs(eo[ok]).max()

@@ -34,6 +34,12 @@ MUTATIONS = {
     "affine remap sign": ("o->x[p] = o->xc + (o->x[p] - o->xc) * s;", "o->x[p] = o->xc - (o->x[p] - o->xc) * s;"),
     "grip set without eps": ("o->x[p] = o->X[p] + eps_new * (o->X[p] - o->xc);",
                              "o->x[p] = o->X[p] + eps_new * o->X[p];"),
+    "field stress missing half": ("double t = 0.5 * (d[pairs[q][0]] * (c_s * d[pairs[q][1]]));",
+                                  "double t = d[pairs[q][0]] * (c_s * d[pairs[q][1]]);"),
+    "field strain J J^T": ("for (int c = 0; c < dim; c++) t += J[c * 3 + a] * J[c * 3 + b];",
+                           "for (int c = 0; c < dim; c++) t += J[a * 3 + c] * J[b * 3 + c];"),
+    "field kinetic sign": ("stress[q * n + p] = (stress[q * n + p] - vv) / cell;",
+                           "stress[q * n + p] = (stress[q * n + p] + vv) / cell;"),
     "dropped z term": ("if (dim == 3) r2 = r2 + d[2] * d[2];\n        double r = sqrt(r2);\n        double c_s",
                        "double r = sqrt(r2);\n        double c_s"),
 }

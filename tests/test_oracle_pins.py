@@ -469,3 +469,95 @@ def test_threaded_spring_pass_is_bit_identical(oracle_mod):
         mb, sb, fb = b.broken()
         assert np.array_equal(ma, mb) and np.array_equal(sa, sb) and fa == fb
         assert ma.sum() > 0  # the run crossed breaks
+
+
+# ----------------------------------------------------- fields (Eqs. 7-8)
+
+def _interior(o, shape):
+    """Indices of particles two or more sites away from every image edge
+    (full images: particle index = raster index)."""
+    idx = np.arange(o.n).reshape(shape)
+    sl = tuple(slice(2, s - 2) for s in shape)
+    return idx[sl].ravel()
+
+
+def test_fields_closed_form_uniaxial_stretch(oracle_mod):
+    """Uniform square lattice (k = 1, a = 1) stretched affinely by eps along x,
+    at rest: an interior particle's virial stress is
+      xx = k eps (1 + eps) + 2 (1 + eps)^2 k (r - sqrt 2) / r,
+      yy = 2 k (r - sqrt 2) / r,  xy = 0,   r = sqrt((1 + eps)^2 + 1)
+    (two axial springs and four diagonals, half of each per endpoint) and its
+    Lagrangian strain is ((1 + eps)^2 - 1) / 2, 0, 0."""
+    img = np.ones((10, 12), np.uint8)
+    k, e, m = two_phase_materials()
+    o = oracle_mod.Oracle.from_image(img, k, e, m)
+    X = o.topology()["X"]
+    for eps in (0.01, -0.02, 0.05):
+        x = X.copy()
+        x[0] *= 1.0 + eps
+        o.set_state(x, np.zeros_like(x))
+        st, sn = o.fields()
+        r = math.sqrt((1 + eps) ** 2 + 1)
+        g = (r - math.sqrt(2.0)) / r
+        want_s = [eps * (1 + eps) + 2 * (1 + eps) ** 2 * g, 2 * g, 0.0]
+        want_e = [((1 + eps) ** 2 - 1) / 2, 0.0, 0.0]
+        for p in _interior(o, img.shape):
+            assert np.allclose(st[:, p], want_s, rtol=1e-12, atol=1e-15)
+            assert np.allclose(sn[:, p], want_e, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fields_strain_of_rotated_stretch(oracle_mod, dim):
+    """x = R U X (stretch U, then rotation R): every particle whose first
+    shell spans the space has Lagrangian strain (U^2 - I) / 2 exactly,
+    unaffected by R (a J J^T or transposed fit would see the rotation)."""
+    rng = np.random.default_rng(11)
+    shape = (6, 7) if dim == 2 else (4, 5, 6)
+    img = np.ones(shape, np.uint8)
+    from gen.images import one_phase_materials
+    k, e, m = one_phase_materials(1.0, 0.5)
+    o = oracle_mod.Oracle.from_image(img, k, e, m)
+    X = o.topology()["X"]
+    Msym = rng.standard_normal((dim, dim)) * 0.05
+    U = np.eye(dim) + 0.5 * (Msym + Msym.T)
+    Q, _ = np.linalg.qr(rng.standard_normal((dim, dim)))
+    x = Q @ U @ X + rng.standard_normal((dim, 1))
+    o.set_state(x, np.zeros_like(x))
+    _, sn = o.fields()
+    E = 0.5 * (U.T @ U - np.eye(dim))
+    pairs = [(0, 0), (1, 1), (0, 1)] if dim == 2 else [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    want = np.array([E[a, b] for a, b in pairs])
+    assert np.all(np.isfinite(sn))  # full lattice: every first shell spans
+    assert np.allclose(sn, want[:, None], rtol=0, atol=1e-12)
+
+
+def test_fields_sum_to_the_global_virial(oracle_mod):
+    """Sum over particles of cell x stress_xx equals the numerator of the
+    global virial stress (Eq. 7 over the whole body), taken from the
+    independent observable code, through dynamics and breaks, in 2D and 3D."""
+    from gen.images import foam_volume, one_phase_materials
+    cases = [(inclusion_image(20, 16, 2.0, 4.0, 0.3, 5), two_phase_materials(), 1.5e-2, 1.0),
+             (foam_volume(8, 1.5, 0.55, seed=6), one_phase_materials(1.0, 0.03), 8e-3, 2.0)]
+    for img, mats, inc, a in cases:
+        k, e, m = mats
+        o = oracle_mod.Oracle.from_image(img, k, e, m, a=a)
+        for i in range(1, 6):
+            o.apply_strain(i * inc)
+            o.step(10)
+        cell = a ** o.dim
+        st, _ = o.fields(cell)
+        obs = o.observe()
+        omega = (img.shape[-1] - 1) * a * np.prod([s * a for s in img.shape[:-1]])
+        assert st[0].sum() * cell / omega == pytest.approx(obs["sigma_vir"], rel=1e-11, abs=1e-14)
+        assert o.broken()[0].sum() > 0 or o.dim == 3
+
+
+def test_fields_degenerate_shell_is_nan(oracle_mod):
+    """A one-pixel-high strip: the first shell of each particle lies on a line,
+    so the affine fit is undefined (NaN); the stress stays finite."""
+    img = np.ones((1, 9), np.uint8)
+    k, e, m = two_phase_materials()
+    o = oracle_mod.Oracle.from_image(img, k, e, m)
+    o.apply_strain(0.01)
+    st, sn = o.fields()
+    assert np.all(np.isnan(sn)) and np.all(np.isfinite(st))
