@@ -67,8 +67,11 @@ typedef enum {
  *  LSM_PREC_DF: as LSM_PREC_F32, but the spring force and the gather use
  *      double-float arithmetic (pairs of floats, 48 significant bits), so
  *      forces carry about 1e-14 relative error while the FP64 pipe only does
- *      the integration. DF and F32 run on the fused 2D tile kernel; elsewhere
- *      they fall back to LSM_PREC_FAST64 arithmetic on the spring-list path. */
+ *      the integration. For image builds DF and F32 run on the fused 2D tile
+ *      kernel or, for 3D and path 1, on the spring-list kernels with the same
+ *      fixed-point spring vectors. Network builds have no lattice vectors:
+ *      there F32 forms the spring vector in double and DF runs as
+ *      LSM_PREC_FAST64. */
 enum { LSM_PREC_EXACT64 = 0, LSM_PREC_FAST64 = 1, LSM_PREC_F32 = 2, LSM_PREC_DF = 3 };
 
 /* Image build descriptor (the paper's Img2Particle stage, Section 1 and

@@ -90,11 +90,11 @@ bool net_from_image(const lsm_desc &d, HostNet &net, std::string &err)
             }
 
     const std::vector<Offset> offs = forward_offsets(d.dim, nx, ny);
-    net.offs.clear();
+    net.offv.clear();
     for (const Offset &o : offs) {
-        net.offs.push_back(o.dx);
-        net.offs.push_back(o.dy);
-        net.offs.push_back(o.dz);
+        net.offv.push_back(o.dx * d.a);
+        net.offv.push_back(o.dy * d.a);
+        net.offv.push_back(o.dz * d.a);
     }
     net.sdir.clear();
     net.sdir.reserve((size_t)n * offs.size());

@@ -92,6 +92,7 @@ k_springs_fix(int64_t m, int64_t n, const int32_t *__restrict__ si, const int32_
         for (int c = 0; c < DIM; c++) ef[c] = xf[c * n + j] - xf[c * n + i] - T.o[dir][c];
         bool brk_now = false;
         FT f[DIM];
+        const ff cor = ff_add(T.oo[dir], t.cor);  // |o|^2 - r0^2 (t.cor holds -r0^2)
         if constexpr (PREC == LSM_PREC_F32) {
             float e[DIM], d[DIM], s2 = 0.0f;
 #pragma unroll
@@ -102,7 +103,7 @@ k_springs_fix(int64_t m, int64_t n, const int32_t *__restrict__ si, const int32_
                 s2 = fmaf(2.0f * o + e[c], e[c], s2);
             }
             const float r2 = T.oo[dir].hi + s2;  // r^2 = |o|^2 + (2 o + e).e
-            const float num = s2 + t.cor.hi;     // r^2 - r0^2
+            const float num = s2 + cor.hi;       // r^2 - r0^2
             if (BREAK && r2 > t.rc2.hi) {
                 brk_now = true;
             } else {
@@ -127,7 +128,7 @@ k_springs_fix(int64_t m, int64_t n, const int32_t *__restrict__ si, const int32_
                 s2 = ff_add(s2, ff_mul(ff_add(ff_add(o, o), e[c]), e[c]));
             }
             const ff r2 = ff_add(T.oo[dir], s2);  // r^2 = |o|^2 + (2 o + e).e
-            const ff num = ff_add(s2, t.cor);     // r^2 - r0^2
+            const ff num = ff_add(s2, cor);       // r^2 - r0^2
             if (BREAK && ff_gt(r2, t.rc2)) {
                 brk_now = true;
             } else {
@@ -277,17 +278,16 @@ static FixTab fix_tab(const Ctx &c)
     T.p48 = ldexpf(1.0f, 48 - c.fix_S);
     T.p24 = ldexpf(1.0f, 24 - c.fix_S);
     T.p0 = ldexpf(1.0f, -c.fix_S);
-    const double aa = std::ldexp((double)c.a_fix, -c.fix_S);
-    const int no = (int)c.h.offs.size() / 3;
+    const int no = (int)c.h.offv.size() / 3;
     for (int q = 0; q < no && q < 9; q++) {
         double oo = 0.0;
         for (int k = 0; k < 3; k++) {
-            const int d = c.h.offs[3 * q + k];
-            T.o[q][k] = (long long)d * c.a_fix;
-            T.of[q][k] = split_ff_c(d * aa);
-            oo += (double)(d * d);
+            T.o[q][k] = std::llround(std::ldexp(c.h.offv[3 * q + k], c.fix_S));
+            const double of = std::ldexp((double)T.o[q][k], -c.fix_S);  // exact
+            T.of[q][k] = split_ff_c(of);
+            oo += of * of;
         }
-        T.oo[q] = split_ff_c(oo * aa * aa);
+        T.oo[q] = split_ff_c(oo);
     }
     return T;
 }
@@ -301,16 +301,15 @@ cudaError_t fixcsr_upload(Ctx &c)
     c.fix_S = std::min(52, 61 - (int)std::ceil(std::log2(extent)));
     c.a_fix = std::llround(std::ldexp(h.a, c.fix_S));
     std::vector<TypeDF> tdf(h.types.size());
-    const double aa = std::ldexp((double)c.a_fix, -c.fix_S);
     for (size_t q = 0; q < h.types.size(); q++) {
         const SpringType &t = h.types[q];
-        const double shell = (q & 1) ? 2.0 : 1.0;
-        const double pr = t.r0 * t.r0, pe = std::fma(t.r0, t.r0, -pr);
-        const double o2 = shell * aa * aa, o2e = shell * std::fma(aa, aa, -(aa * aa));
+        // -r0^2 to double-float accuracy: r0^2 = p + pe exactly (fma)
+        const double p = t.r0 * t.r0, pe = std::fma(t.r0, t.r0, -p);
+        const float hi = (float)(-p);
         tdf[q].k = split_ff_c(t.k);
         tdf[q].r0 = split_ff_c(t.r0);
         tdf[q].rc2 = split_ff_c(t.rc2);
-        tdf[q].cor = split_ff_c((o2 - pr) + (o2e - pe));
+        tdf[q].cor = ff{hi, (float)((-p - (double)hi) - pe)};
     }
     std::vector<double> im(n);
     for (int64_t p = 0; p < n; p++) im[p] = 1.0 / h.mass[p];

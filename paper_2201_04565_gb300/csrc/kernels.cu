@@ -573,7 +573,7 @@ cudaError_t upload(Ctx &c)
     LSM_TRY(cudaMemsetAsync(c.fs, 0, (size_t)h.dim * (m ? m : 1) * sizeof(double), st));
     // host vectors above must stay alive until the copies finish
     LSM_TRY(cudaStreamSynchronize(st));
-    c.fixcsr = (h.precision == LSM_PREC_F32 || h.precision == LSM_PREC_DF) && !h.offs.empty() &&
+    c.fixcsr = (h.precision == LSM_PREC_F32 || h.precision == LSM_PREC_DF) && !h.offv.empty() &&
                (int64_t)h.sdir.size() == m;
     if (c.fixcsr) LSM_TRY(fixcsr_upload(c));
     return cudaSuccess;

@@ -77,7 +77,7 @@ struct HostNet {
     std::vector<int64_t> pix;      // pixel of each particle (image builds)
     std::vector<uint8_t> phase;    // nx*ny*nz phase image (image builds)
     std::vector<uint8_t> sdir;     // per spring: index of its lattice offset (image builds)
-    std::vector<int> offs;         // lattice offsets (dx, dy, dz) by index (image builds)
+    std::vector<double> offv;      // lattice vectors (x, y, z) by offset index (image builds)
 };
 
 struct Ctx {
