@@ -99,7 +99,17 @@ enum { LSM_PREC_EXACT64 = 0, LSM_PREC_FAST64 = 1, LSM_PREC_F32 = 2, LSM_PREC_DF 
  *  path         0 = automatic (2D images with up to 8 phases run the fused
  *               tile kernel, everything else the general spring-list
  *               kernels); 1 = always the general spring-list kernels.
- *  stream       cudaStream_t to order work on (NULL = the library creates one). */
+ *  stream       cudaStream_t to order work on (NULL = the library creates one).
+ *  lattice      0 = square (2D) / cubic (3D) lattice as above; 1 = the
+ *               paper's triangular packing (2D only, Section 1: six first
+ *               neighbours per interior particle, r0 = a, k2_ratio unused).
+ *               Rows iy = 0..R-1 at y = iy h, h = (a sqrt 3) 0.5, for every
+ *               iy with iy sqrt(3)/2 <= ny - 1; row iy has nx sites at
+ *               x = ix a (even iy) or nx - 1 sites at x = (ix + 0.5) a (odd
+ *               iy). A site takes the phase of its nearest pixel (column
+ *               ix + (iy odd), row round(iy sqrt(3)/2)). Grips are the first
+ *               and last site of each row; Omega = (nx - 1) a R h; the grip
+ *               area is R h. Runs on the spring-list kernels. */
 typedef struct lsm_desc {
     int32_t dim, nx, ny, nz;
     const uint8_t *phase;
@@ -116,6 +126,7 @@ typedef struct lsm_desc {
     int32_t precision;
     int32_t path;
     void *stream;
+    int32_t lattice;
 } lsm_desc;
 
 /* General network descriptor (the paper's solver reads any particle/bond

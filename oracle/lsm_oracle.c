@@ -81,6 +81,9 @@ typedef struct orc {
 
 void orc_forces(const orc *o, const double *xs, double *F, double *U, double *W);
 static void orc_init_accel(orc *o);
+static orc *orc_build_tri(int nx, int ny, const uint8_t *phase, int nphase, const double *k_tab,
+                          const double *epsc_tab, const double *mass_tab, double a, double dt,
+                          double gamma, int grip_mode, int load_mode);
 
 void orc_free(orc *o)
 {
@@ -131,14 +134,20 @@ static const int OFF3[9][4] = {{1, 0, 0, 1},  {0, 1, 0, 1},  {0, 0, 1, 1},
                                {-1, 0, 1, 2}, {0, 1, 1, 2},  {0, -1, 1, 2}};
 
 /* Image -> particles and springs (the paper's Img2Particle step, on a square
- * or cubic lattice). phase: nx*ny*nz bytes, x fastest; 0 = void, 1..nphase.
+ * or cubic lattice; lattice 1 selects the triangular packing below). phase: nx*ny*nz bytes, x fastest; 0 = void, 1..nphase.
  * k_tab, epsc_tab: nphase*nphase, row-major, indexed (phase_i-1, phase_j-1).
  * mass_tab: nphase. grip_mode 0 = roller (x prescribed), 1 = clamped. */
 orc *orc_build_image(int dim, int nx, int ny, int nz, const uint8_t *phase, int nphase,
                      const double *k_tab, const double *epsc_tab, const double *mass_tab,
                      double k2_ratio, double a, double dt, double gamma, int grip_mode,
-                     int load_mode)
+                     int load_mode, int lattice)
 {
+    if (lattice == 1) {
+        if (dim != 2) return NULL;
+        return orc_build_tri(nx, ny, phase, nphase, k_tab, epsc_tab, mass_tab, a, dt, gamma, grip_mode,
+                             load_mode);
+    }
+    if (lattice != 0) return NULL;
     if (dim != 2 && dim != 3) return NULL;
     if (dim == 2) nz = 1;
     if (nx < 2 || ny < 1 || nz < 1 || nphase < 1 || !phase || !k_tab || !epsc_tab) return NULL;
@@ -232,6 +241,123 @@ orc *orc_build_image(int dim, int nx, int ny, int nz, const uint8_t *phase, int 
         o->omega = o->omega * (nz * a);
         o->grip_area = o->grip_area * (nz * a);
     }
+    o->load_mode = load_mode;
+    orc_init_accel(o);
+    return o;
+}
+
+/* ------------------------------------------------- triangular packing -- */
+
+/* floor(sqrt(v)) for v >= 0, exactly. */
+static int64_t orc_isqrt(int64_t v)
+{
+    int64_t r = (int64_t)sqrt((double)v);
+    while (r > 0 && r * r > v) r--;
+    while ((r + 1) * (r + 1) <= v) r++;
+    return r;
+}
+
+/* Image -> particles and springs on the triangular packing that the paper's
+ * Img2Particle emits (Section 1; first neighbours only, six per interior
+ * particle, Section 1 on the spring count). Reading of the paper (which
+ * gives no formula): lattice rows iy = 0..R-1 at height y = iy h with
+ * h = (a sqrt 3) 0.5; row iy holds sites ix = 0..C-1, C = nx (even iy) or
+ * nx - 1 (odd iy), at x = (ix + 0.5 (iy odd)) a; R is the number of rows
+ * with iy sqrt(3)/2 <= ny - 1 (in pixels). A site takes the phase of the
+ * pixel nearest to it: column ix + (iy odd), row round(iy sqrt(3)/2),
+ * evaluated in integers. Springs join each site to its forward neighbours
+ * (same row +1; the two sites of row iy + 1 at x -+ a/2), r0 = a. Grips are
+ * the first and last site of each row. Omega = (nx - 1) a R h, grip area
+ * R h. */
+static orc *orc_build_tri(int nx, int ny, const uint8_t *phase, int nphase, const double *k_tab,
+                          const double *epsc_tab, const double *mass_tab, double a, double dt,
+                          double gamma, int grip_mode, int load_mode)
+{
+    if (nx < 2 || ny < 1 || nphase < 1 || !phase || !k_tab || !epsc_tab) return NULL;
+    int64_t R = 0;
+    while (3 * (R + 1) * (R + 1) <= 4 * (int64_t)(ny - 1) * (ny - 1)) R++;
+    R += 1; /* rows 0..R-1 */
+    /* site (ix, iy) -> particle index or -1; sites in row-major order */
+    int64_t *base = (int64_t *)malloc((size_t)(R + 1) * sizeof(int64_t));
+    if (!base) return NULL;
+    base[0] = 0;
+    for (int64_t iy = 0; iy < R; iy++) base[iy + 1] = base[iy] + (iy & 1 ? nx - 1 : nx);
+    const int64_t nsite = base[R];
+    int64_t *idx = (int64_t *)malloc((size_t)nsite * sizeof(int64_t));
+    uint8_t *sph = (uint8_t *)malloc((size_t)nsite);
+    if (!idx || !sph) { free(base); free(idx); free(sph); return NULL; }
+    int64_t n = 0;
+    for (int64_t iy = 0; iy < R; iy++) {
+        const int64_t row = (orc_isqrt(3 * iy * iy) + 1) / 2;
+        for (int64_t ix = 0; ix < base[iy + 1] - base[iy]; ix++) {
+            const int64_t col = ix + (iy & 1);
+            const uint8_t ph = phase[row * nx + col];
+            if (ph > nphase) { free(base); free(idx); free(sph); return NULL; }
+            sph[base[iy] + ix] = ph;
+            idx[base[iy] + ix] = ph ? n++ : -1;
+        }
+    }
+    /* forward neighbours of site (ix, iy) in ascending site order */
+#define TRI_NB(ix, iy, t, jx, jy)                                               \
+    do {                                                                        \
+        if ((t) == 0) { jx = (ix) + 1; jy = (iy); }                             \
+        else { jy = (iy) + 1; jx = (ix) + ((iy) & 1 ? 0 : -1) + ((t) == 2); }   \
+    } while (0)
+    int64_t m = 0;
+    for (int64_t iy = 0; iy < R; iy++)
+        for (int64_t ix = 0; ix < base[iy + 1] - base[iy]; ix++) {
+            if (idx[base[iy] + ix] < 0) continue;
+            for (int t = 0; t < 3; t++) {
+                int64_t jx, jy;
+                TRI_NB(ix, iy, t, jx, jy);
+                if (jy >= R || jx < 0 || jx >= base[jy + 1] - base[jy]) continue;
+                if (idx[base[jy] + jx] >= 0) m++;
+            }
+        }
+    orc *o = orc_alloc(2, n, m);
+    if (!o) { free(base); free(idx); free(sph); return NULL; }
+    const double h = a * sqrt(3.0) * 0.5;
+    int64_t s = 0;
+    for (int64_t iy = 0; iy < R; iy++) {
+        const int64_t C = base[iy + 1] - base[iy];
+        for (int64_t ix = 0; ix < C; ix++) {
+            const int64_t p = idx[base[iy] + ix];
+            if (p < 0) continue;
+            const int ph = sph[base[iy] + ix];
+            o->X[p] = (ix + 0.5 * (double)(iy & 1)) * a;
+            o->X[n + p] = iy * h;
+            o->mass[p] = mass_tab ? mass_tab[ph - 1] : 1.0;
+            o->grip[p] = ix == 0 ? 1 : (ix == C - 1 ? 2 : 0);
+            if (o->grip[p]) {
+                o->fix[p] = 1;
+                if (grip_mode == 1) o->fix[n + p] = 1;
+            }
+            for (int t = 0; t < 3; t++) { /* targets ascend with t */
+                int64_t jx, jy;
+                TRI_NB(ix, iy, t, jx, jy);
+                if (jy >= R || jx < 0 || jx >= base[jy + 1] - base[jy]) continue;
+                const int64_t q = idx[base[jy] + jx];
+                if (q < 0) continue;
+                const int pq = sph[base[jy] + jx];
+                const double ec = epsc_tab[(ph - 1) * nphase + (pq - 1)];
+                const double rc = a * (1.0 + ec);
+                o->si[s] = (int32_t)p;
+                o->sj[s] = (int32_t)q;
+                o->k[s] = k_tab[(ph - 1) * nphase + (pq - 1)];
+                o->r0[s] = a;
+                o->rc2[s] = rc * rc;
+                s++;
+            }
+        }
+    }
+#undef TRI_NB
+    free(base); free(idx); free(sph);
+    memcpy(o->x, o->X, (size_t)2 * n * sizeof(double));
+    o->dt = dt;
+    o->gamma = gamma;
+    o->xc = 0.5 * (nx - 1) * a;
+    o->omega = (nx - 1) * a * (R * h);
+    o->grip_area = R * h;
     o->load_mode = load_mode;
     orc_init_accel(o);
     return o;

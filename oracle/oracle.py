@@ -48,7 +48,7 @@ def _load():
     lib = C.CDLL(build_oracle())
     P, D, I64, I = C.c_void_p, C.c_double, C.c_int64, C.c_int
     lib.orc_build_image.restype = P
-    lib.orc_build_image.argtypes = [I, I, I, I, P, I, P, P, P, D, D, D, D, I, I]
+    lib.orc_build_image.argtypes = [I, I, I, I, P, I, P, P, P, D, D, D, D, I, I, I]
     lib.orc_build_network.restype = P
     lib.orc_build_network.argtypes = [I, I64, I64, P, P, P, P, P, P, P, P, P, D, D, D, D, D, I]
     lib.orc_free.argtypes = [P]
@@ -95,7 +95,7 @@ class Oracle:
     # ------------------------------------------------------------ builds
     @classmethod
     def from_image(cls, phase, k_tab, epsc_tab, mass=None, k2_ratio=1.0, a=1.0, dt=0.01,
-                   damping=0.1, grip_mode=0, load_mode=0):
+                   damping=0.1, grip_mode=0, load_mode=0, lattice=0):
         lib = _load()
         ph = np.ascontiguousarray(phase, dtype=np.uint8)
         if ph.ndim == 2:
@@ -110,7 +110,7 @@ class Oracle:
         ms = None if mass is None else np.ascontiguousarray(mass, dtype=np.float64)
         h = lib.orc_build_image(dim, nx, ny, nz, _ptr(ph), nphase, _ptr(kt), _ptr(et), _ptr(ms),
                                 float(k2_ratio), float(a), float(dt), float(damping),
-                                int(grip_mode), int(load_mode))
+                                int(grip_mode), int(load_mode), int(lattice))
         return cls(h)
 
     @classmethod

@@ -45,7 +45,8 @@ lsm_status device_status(Ctx *c)
 
 lsm_status finish_build(lsm_ctx *c, void *stream, lsm_ctx **out, int path = 0)
 {
-    c->tile = path != 1 && c->h.dim == 2 && c->h.nx > 0 && c->h.nphase >= 1 && c->h.nphase <= 8;
+    c->tile = path != 1 && c->h.dim == 2 && c->h.nx > 0 && c->h.lattice == 0 && c->h.nphase >= 1 &&
+              c->h.nphase <= 8;
     if (stream) {
         c->stream = (cudaStream_t)stream;
     } else {
@@ -425,7 +426,7 @@ lsm_status lsm_fields(lsm_ctx *c, double cell_volume, double *stress, double *st
     lsm_status st = device_status(c);
     if (st != LSM_OK) return st;
     double cell = cell_volume;
-    if (!(cell > 0.0)) cell = c->h.nx > 0 ? std::pow(c->h.a, (double)c->h.dim) : 1.0;
+    if (!(cell > 0.0)) cell = c->h.cell;
     cudaError_t e = lsm::fields_compute(*c, cell);
     const int nq = c->h.dim == 3 ? 6 : 3;
     const size_t bytes = (size_t)nq * c->n * sizeof(double);

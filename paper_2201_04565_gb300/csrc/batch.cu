@@ -359,6 +359,13 @@ static TileArgs batch_base_args(BatchCtx &b)
     A.p48 = ldexpf(1.0f, 48 - b.fix_S);
     A.p24 = ldexpf(1.0f, 24 - b.fix_S);
     A.p0 = ldexpf(1.0f, -b.fix_S);
+    {
+        const double aa = std::ldexp((double)b.a_fix, -b.fix_S);  // lattice spacing as used
+        A.fa = (float)aa;
+        A.fa2 = (float)(2.0 * aa);
+        A.fo2a = (float)(aa * aa);
+        A.fo2d = (float)(2.0 * aa * aa);
+    }
     A.status = b.status;
     A.part_s = b.part_s;
     A.part_p = b.part_p;
@@ -678,10 +685,10 @@ lsm_status lsm_build_batch(const lsm_desc *descs, int32_t count, lsm_batch **out
     b->eps.assign(count, 0.0);
     for (int s = 0; s < count; s++) {
         const lsm_desc &d = descs[s];
-        if (d.dim != 2 || d.nphase != d0.nphase || d.dt != d0.dt || d.damping != d0.damping || d.a != d0.a ||
+        if (d.dim != 2 || d.lattice != 0 || d.nphase != d0.nphase || d.dt != d0.dt || d.damping != d0.damping || d.a != d0.a ||
             d.grip_mode != d0.grip_mode || d.load_mode != d0.load_mode || d.precision != d0.precision) {
             delete b;
-            return bfail(nullptr, LSM_EINVAL, "batch specimens must be 2D and share nphase, dt, damping, a, "
+            return bfail(nullptr, LSM_EINVAL, "batch specimens must be 2D square-lattice images and share nphase, dt, damping, a, "
                                               "grip/load modes and precision");
         }
         lsm_desc dd = d;

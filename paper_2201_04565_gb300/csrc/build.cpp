@@ -48,8 +48,123 @@ std::vector<Offset> forward_offsets(int dim, int nx, int ny)
 
 }  // namespace
 
+// Exact floor(sqrt(v)), v >= 0.
+int64_t isqrt64(int64_t v)
+{
+    int64_t r = (int64_t)std::sqrt((double)v);
+    while (r > 0 && r * r > v) r--;
+    while ((r + 1) * (r + 1) <= v) r++;
+    return r;
+}
+
+// Triangular packing (lattice 1, 2D). Rows iy = 0..R-1 at y = iy h,
+// h = (a sqrt 3) 0.5, R the number of rows with iy sqrt(3)/2 <= ny - 1
+// pixels; row iy has nx sites (even iy) or nx - 1 (odd iy, shifted by a/2).
+// Each site takes the phase of its nearest pixel (column ix + (iy odd), row
+// round(iy sqrt(3)/2), in integers). Forward neighbours, in ascending site
+// order: the next site of the row, then the two sites of row iy + 1 at
+// x - a/2 and x + a/2; all first neighbours, r0 = a.
+bool net_from_image_tri(const lsm_desc &d, HostNet &net, std::string &err)
+{
+    const int nx = d.nx, ny = d.ny, np = d.nphase;
+    int64_t R = 0;
+    while (3 * (R + 1) * (R + 1) <= 4 * (int64_t)(ny - 1) * (ny - 1)) R++;
+    R += 1;
+    std::vector<int64_t> rowbase(R + 1, 0);
+    for (int64_t iy = 0; iy < R; iy++) rowbase[iy + 1] = rowbase[iy] + ((iy & 1) ? nx - 1 : nx);
+    const int64_t nsite = rowbase[R];
+    if (nsite > ((int64_t)1 << 31) - 1) { err = "lattice larger than 2^31 - 1 sites"; return false; }
+    std::vector<int64_t> pid(nsite), pixel(nsite);
+    int64_t n = 0;
+    for (int64_t iy = 0; iy < R; iy++) {
+        const int64_t prow = (isqrt64(3 * iy * iy) + 1) / 2;
+        for (int64_t ix = 0; ix < rowbase[iy + 1] - rowbase[iy]; ix++) {
+            const int64_t g = prow * nx + ix + (iy & 1);
+            const uint8_t ph = d.phase[g];
+            if (ph > np) { err = "phase value above nphase"; return false; }
+            pixel[rowbase[iy] + ix] = g;
+            pid[rowbase[iy] + ix] = ph ? n++ : -1;
+        }
+    }
+    if (n == 0) { err = "image has no particles"; return false; }
+    net.types.assign((size_t)np * np * 2, SpringType{});
+    for (int pi = 0; pi < np; pi++)
+        for (int pj = 0; pj < np; pj++) {
+            const double k = d.k_tab[pi * np + pj], ec = d.epsc_tab[pi * np + pj];
+            if (!(k >= 0) || !(ec > -1.0)) { err = "k_tab must be >= 0 and epsc_tab > -1"; return false; }
+            const double rc = d.a * (1.0 + ec);
+            SpringType &t = net.types[((size_t)pi * np + pj) * 2];
+            t.k = k;
+            t.r0 = d.a;
+            t.rc2 = rc * rc;
+            t.kr0 = k * d.a;
+            net.types[((size_t)pi * np + pj) * 2 + 1] = t;  // no second shell; kept for the type layout
+        }
+    const double h = d.a * std::sqrt(3.0) * 0.5;
+    net.offv = {d.a, 0.0, 0.0, -0.5 * d.a, h, 0.0, 0.5 * d.a, h, 0.0};
+    net.dim = 2;
+    net.n = n;
+    net.X.assign((size_t)2 * n, 0.0);
+    net.mass.assign(n, 1.0);
+    net.fixm.assign(n, 0);
+    net.grip.assign(n, 0);
+    net.si.clear(); net.sj.clear(); net.stype.clear(); net.sdir.clear();
+    net.pix.resize(n);
+    for (int64_t iy = 0; iy < R; iy++) {
+        const int64_t C = rowbase[iy + 1] - rowbase[iy];
+        for (int64_t ix = 0; ix < C; ix++) {
+            const int64_t p = pid[rowbase[iy] + ix];
+            if (p < 0) continue;
+            const int ph = d.phase[pixel[rowbase[iy] + ix]];
+            net.pix[p] = pixel[rowbase[iy] + ix];
+            net.X[p] = (ix + 0.5 * (double)(iy & 1)) * d.a;
+            net.X[n + p] = iy * h;
+            if (d.mass_tab) net.mass[p] = d.mass_tab[ph - 1];
+            if (ix == 0 || ix == C - 1) {
+                net.grip[p] = ix == 0 ? 1 : 2;
+                net.fixm[p] = d.grip_mode == 1 ? 3 : 1;
+            }
+            // same row, then row iy + 1 at x - a/2 and x + a/2
+            const int64_t up = ix + ((iy & 1) ? 0 : -1);
+            const int64_t tx[3] = {ix + 1, up, up + 1}, ty[3] = {iy, iy + 1, iy + 1};
+            for (int t = 0; t < 3; t++) {
+                if (ty[t] >= R || tx[t] < 0 || tx[t] >= rowbase[ty[t] + 1] - rowbase[ty[t]]) continue;
+                const int64_t site = rowbase[ty[t]] + tx[t];
+                const int64_t q = pid[site];
+                if (q < 0) continue;
+                const int pq = d.phase[pixel[site]];
+                net.sdir.push_back((uint8_t)t);
+                net.si.push_back((int32_t)p);
+                net.sj.push_back((int32_t)q);
+                net.stype.push_back((uint16_t)(((ph - 1) * np + (pq - 1)) * 2));
+            }
+        }
+    }
+    net.m = (int64_t)net.si.size();
+    if (net.m >= ((int64_t)1 << 31)) { err = "more than 2^31 - 1 springs"; return false; }
+    for (double m : net.mass)
+        if (!(m > 0)) { err = "mass must be > 0"; return false; }
+    net.dt = d.dt;
+    net.damping = d.damping;
+    net.xc = 0.5 * (nx - 1) * d.a;
+    net.omega = (nx - 1) * d.a * (R * h);
+    net.grip_area = R * h;
+    net.cell = d.a * h;
+    net.load_mode = d.load_mode;
+    net.precision = d.precision;
+    net.grip_mode = d.grip_mode;
+    net.a = d.a;
+    net.lattice = 1;
+    net.nx = nx; net.ny = ny; net.nz = 1;
+    net.nphase = np;
+    net.phase.assign(d.phase, d.phase + (int64_t)nx * ny);
+    return true;
+}
+
 bool net_from_image(const lsm_desc &d, HostNet &net, std::string &err)
 {
+    if (d.lattice != 0 && d.lattice != 1) { err = "lattice must be 0 (square/cubic) or 1 (triangular)"; return false; }
+    if (d.lattice == 1 && d.dim != 2) { err = "the triangular packing is 2D"; return false; }
     if (d.dim != 2 && d.dim != 3) { err = "dim must be 2 or 3"; return false; }
     const int nx = d.nx, ny = d.ny, nz = d.dim == 2 ? 1 : d.nz;
     if (nx < 2 || ny < 1 || nz < 1) { err = "image needs nx >= 2, ny >= 1, nz >= 1"; return false; }
@@ -60,6 +175,7 @@ bool net_from_image(const lsm_desc &d, HostNet &net, std::string &err)
     if (d.load_mode != 0 && d.load_mode != 1) { err = "load_mode must be 0 or 1"; return false; }
     const int64_t nvox = (int64_t)nx * ny * nz;
     if (nvox > ((int64_t)1 << 31) - 1) { err = "image larger than 2^31 - 1 voxels"; return false; }
+    if (d.lattice == 1) return net_from_image_tri(d, net, err);
     const int np = d.nphase;
 
     std::vector<int64_t> pid(nvox);
@@ -150,10 +266,12 @@ bool net_from_image(const lsm_desc &d, HostNet &net, std::string &err)
         net.omega = net.omega * (nz * d.a);
         net.grip_area = net.grip_area * (nz * d.a);
     }
+    net.cell = std::pow(d.a, (double)d.dim);
     net.load_mode = d.load_mode;
     net.precision = d.precision;
     net.grip_mode = d.grip_mode;
     net.a = d.a;
+    net.lattice = 0;
     net.nx = nx; net.ny = ny; net.nz = nz;
     net.nphase = np;
     net.phase.assign(d.phase, d.phase + nvox);

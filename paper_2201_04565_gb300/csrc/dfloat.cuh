@@ -191,6 +191,48 @@ __device__ __forceinline__ ff fix_to_ff_i2f(long long v, float p48, float p24, f
     return fast_two_sum(s.hi, __fadd_rn(s.lo, c));
 }
 
+// Same value as fix_to_ff_i2f; |v| < 2^47 (the common case for spring
+// deviations) takes two 24-bit chunks, whose float sum Fast2Sum represents
+// exactly because the chunks do not overlap.
+__device__ __forceinline__ ff fix_to_ff_i2f2(long long v, float p48, float p24, float p0)
+{
+    const long long h = v >> 24;
+    if ((unsigned long long)(h + 0x800000LL) < 0x1000000ULL) {
+        const float a = __fmul_rn(__int2float_rn((int)h), p24);
+        const float b = __fmul_rn(__int2float_rn((int)(v & 0xFFFFFFLL)), p0);
+        return fast_two_sum(a, b);
+    }
+    return fix_to_ff_i2f(v, p48, p24, p0);
+}
+
+// a^2 for a double-float a.
+__device__ __forceinline__ ff ff_sqr(ff a)
+{
+    ff p = two_prod(a.hi, a.hi);
+    p.lo = __fmaf_rn(__fadd_rn(a.hi, a.hi), a.lo, p.lo);
+    return fast_two_sum(p.hi, p.lo);
+}
+
+// 1 / sqrt(a), a > 0: the float estimate, one float Newton step, then one
+// Newton step in double-float, y1 = y0 + y0 (1 - a y0^2) / 2 (relative error
+// about 2^-46; the residual 1 - a y0^2 is formed exactly up to the final
+// rounding because a y0^2 is within a few float ulps of 1).
+__device__ __forceinline__ ff ff_rsqrt(ff a)
+{
+    float y0 = rsqrtf(a.hi);
+    y0 = __fmul_rn(y0, __fmaf_rn(-0.5f * a.hi, __fmul_rn(y0, y0), 1.5f));
+    const ff t = ff_mul(a, two_prod(y0, y0));
+    const float rho = __fsub_rn(__fsub_rn(1.0f, t.hi), t.lo);
+    return fast_two_sum(y0, __fmul_rn(__fmul_rn(0.5f, y0), rho));
+}
+
+// 1 - a for a double-float a (exact TwoSum on the high part).
+__device__ __forceinline__ ff ff_one_minus(ff a)
+{
+    ff s = two_sum(1.0f, -a.hi);
+    return fast_two_sum(s.hi, __fsub_rn(s.lo, a.lo));
+}
+
 // Double-float addition with one TwoSum on the high parts (Dekker's form):
 // absolute error within a few units of 2^-46 (|a| + |b|), enough for sums
 // whose accuracy is judged against the largest term.

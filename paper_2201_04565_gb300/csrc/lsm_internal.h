@@ -72,6 +72,8 @@ struct HostNet {
     int precision = LSM_PREC_EXACT64;
     int grip_mode = 0;
     double a = 1.0;
+    int lattice = 0;               // 0 square / cubic, 1 triangular packing (image builds)
+    double cell = 1.0;             // volume per particle (lsm_fields default)
     // image geometry (0 for network builds)
     int nx = 0, ny = 0, nz = 0, nphase = 0;
     std::vector<int64_t> pix;      // pixel of each particle (image builds)

@@ -127,6 +127,13 @@ static TileArgs tile_args(Ctx &c)
     A.p48 = ldexpf(1.0f, 48 - c.fix_S);
     A.p24 = ldexpf(1.0f, 24 - c.fix_S);
     A.p0 = ldexpf(1.0f, -c.fix_S);
+    {
+        const double aa = std::ldexp((double)c.a_fix, -c.fix_S);  // lattice spacing as used
+        A.fa = (float)aa;
+        A.fa2 = (float)(2.0 * aa);
+        A.fo2a = (float)(aa * aa);
+        A.fo2d = (float)(2.0 * aa * aa);
+    }
     A.dt = c.h.dt;
     A.hdt = 0.5 * c.h.dt;
     A.gamma = c.h.damping;

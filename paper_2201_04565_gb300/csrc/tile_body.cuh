@@ -71,6 +71,7 @@ struct TileArgs {
     int S;                     // fixed-point scale: positions as x * 2^S
     long long a_fix;           // lattice spacing in fixed point
     float p48, p24, p0;        // 2^(48-S), 2^(24-S), 2^-S
+    float fa, fa2, fo2a, fo2d;  // a, 2a, a^2, 2a^2 as floats (exact when the lattice is)
     double dt, hdt, gamma, a;
     int grip_mode;
     const long long *d_step;  // steps completed before this graph launch
@@ -84,13 +85,13 @@ struct TileArgs {
 // Force on the lower endpoint of one spring (rp -> rq, forward slot), with
 // the break test. Writes the force into sf; OWNER adds the sample sums and
 // records a break (only the tile owning the lower endpoint does).
-template <int PREC, int MODE, bool SAMPLE, bool OWNER, bool ODY, int NR, int NS, typename FT>
+template <int PREC, int MODE, bool SAMPLE, bool OWNER, bool ODY, int NR, int NS, typename FT, typename AT>
 __device__ __forceinline__ void eval_spring(const TileArgs &A, int rp, int rq, int slot, const double *sx,
                                             const double *sy, const long long *sxf, const long long *syf,
                                             const uint8_t *sph, const uint8_t *smk, FT *sf,
                                             const SpringType *stab, const TypeDF *sdf, const ff (*soff)[3],
-                                            int *snew, int64_t gsrc, long long step_now, double &w_acc,
-                                            double &u_acc)
+                                            int *snew, int64_t gsrc, long long step_now, AT &w_acc,
+                                            AT &u_acc)
 {
     FT fx{}, fy{};
     const uint8_t pp = sph[rp], pq = sph[rq];
@@ -155,31 +156,36 @@ __device__ __forceinline__ void eval_spring(const TileArgs &A, int rp, int rq, i
                     const float c = t.k.hi * st * ir;
                     fx = c * dxf;
                     fy = c * dyf;
-                    if (SAMPLE && OWNER) {
-                        u_acc += 0.5 * (double)t.k.hi * (double)st * (double)st;
-                        w_acc += (double)dxf * (double)fx;
+                    if (SAMPLE && OWNER) {  // double-float sums: no FP64 pipe work per spring
+                        u_acc = ff_add_f(u_acc, 0.5f * t.k.hi * st * st);
+                        w_acc = ff_add_f(w_acc, dxf * fx);
                     }
                 }
             } else if constexpr (ODY) {  // LSM_PREC_DF, lattice vectors exact in float
-                const ff ex = fix_to_ff_i2f(exf, A.p48, A.p24, A.p0);
-                const ff ey = fix_to_ff_i2f(eyf, A.p48, A.p24, A.p0);
-                const float ox = soff[slot][0].hi, oy = soff[slot][1].hi, oo = soff[slot][2].hi;
-                ff num = ff_add_sloppy(ff_mul(ff_add_f(ex, 2.0f * ox), ex), ff_mul(ff_add_f(ey, 2.0f * oy), ey));
-                num = fast_two_sum(num.hi, __fadd_rn(num.lo, t.cor.hi));
-                const ff r2 = ff_add_f(num, oo);
+                // o = (dx a, dy a) with a, 2a, a^2 and 2a^2 exact floats; the
+                // slot is a compile-time constant for the owned springs, so
+                // zero components of o cost nothing there
+                const ff ex = fix_to_ff_i2f2(exf, A.p48, A.p24, A.p0);
+                const ff ey = fix_to_ff_i2f2(eyf, A.p48, A.p24, A.p0);
+                const ff qx = dx == 0 ? ff_sqr(ex) : ff_mul(ff_add_f(ex, dx > 0 ? A.fa2 : -A.fa2), ex);
+                const ff qy = dy == 0 ? ff_sqr(ey) : ff_mul(ff_add_f(ey, A.fa2), ey);
+                const ff r2 = ff_add_f(ff_add_sloppy(qx, qy), (dx != 0 && dy != 0) ? A.fo2d : A.fo2a);
                 if (MODE == T_STEP && ff_gt(r2, t.rc2)) {
                     brk_now = true;
                 } else {
-                    const ff r = ff_sqrt(r2);
-                    const ff rr0 = ff_add_sloppy(r, t.r0);
-                    const ff c = ff_mul(t.k, ff_div_fast(num, ff_mul(r, rr0)));  // k (r - r0) / r
-                    const ff dxf = ff_add_f(ex, ox), dyf = ff_add_f(ey, oy);
+                    // k (r - r0) / r = k (1 - r0 y) with y = 1/r to ~2^-46: the
+                    // same cancellation as FP64's k (r - r0) / r, at 2^-46
+                    const ff y = ff_rsqrt(r2);
+                    const ff g = ff_one_minus(ff_mul(t.r0, y));
+                    const ff c = ff_mul(t.k, g);
+                    const ff dxf = dx == 0 ? ex : ff_add_f(ex, dx > 0 ? A.fa : -A.fa);
+                    const ff dyf = dy == 0 ? ey : ff_add_f(ey, A.fa);
                     fx = ff_mul(c, dxf);
                     fy = ff_mul(c, dyf);
-                    if (SAMPLE && OWNER) {
-                        const double st = ff_to_double(ff_div(num, rr0));
-                        u_acc += 0.5 * ff_to_double(t.k) * st * st;
-                        w_acc += ff_to_double(dxf) * ff_to_double(fx);
+                    if (SAMPLE && OWNER) {  // double-float sums: no FP64 pipe work per spring
+                        const ff st = ff_mul(ff_mul(r2, y), g);  // r - r0
+                        u_acc = ff_add_sloppy(u_acc, ff_mul(ff_mul_f(t.k, 0.5f), ff_sqr(st)));
+                        w_acc = ff_add_sloppy(w_acc, ff_mul(dxf, fx));
                     }
                 }
             } else {  // LSM_PREC_DF, general lattice spacing
@@ -199,9 +205,9 @@ __device__ __forceinline__ void eval_spring(const TileArgs &A, int rp, int rq, i
                     fx = ff_mul(c, dxf);
                     fy = ff_mul(c, dyf);
                     if (SAMPLE && OWNER) {
-                        const double st = ff_to_double(ff_div(num, ff_add(r, t.r0)));
-                        u_acc += 0.5 * ff_to_double(t.k) * st * st;
-                        w_acc += ff_to_double(dxf) * ff_to_double(fx);
+                        const ff st = ff_div(num, ff_add(r, t.r0));
+                        u_acc = ff_add_sloppy(u_acc, ff_mul(ff_mul_f(t.k, 0.5f), ff_sqr(st)));
+                        w_acc = ff_add_sloppy(w_acc, ff_mul(dxf, fx));
                     }
                 }
             }
@@ -321,7 +327,8 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
     __syncthreads();
 
     // 2a. forward springs of the owned particles
-    double w_acc = 0.0, u_acc = 0.0;
+    using AT = typename std::conditional<FIX, ff, double>::type;  // per-thread sample sums
+    AT w_acc{}, u_acc{};
     constexpr int dq[4] = {1, RX - 1, RX, RX + 1};
 #pragma unroll
     for (int k = 0; k < TY / NW; k++) {
@@ -384,15 +391,32 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
                 F[c] = acc;
             }
         } else if constexpr (PREC == LSM_PREC_DF) {
+            // cascaded summation (Ogita, Rump and Oishi, 2005): a TwoSum
+            // chain over the high parts, their errors and the low parts summed
+            // in float; same fixed order as above
 #pragma unroll
             for (int c = 0; c < 2; c++) {
-                ff acc = ff_neg(sf[(c * 4 + 3) * NS + s3]);
-                acc = ff_add_sloppy(acc, ff_neg(sf[(c * 4 + 2) * NS + s2]));
-                acc = ff_add_sloppy(acc, ff_neg(sf[(c * 4 + 1) * NS + s1]));
-                acc = ff_add_sloppy(acc, ff_neg(sf[(c * 4 + 0) * NS + s0]));
+                const ff t3 = sf[(c * 4 + 3) * NS + s3];
+                float hs = -t3.hi, el = -t3.lo;
+                const ff in2 = sf[(c * 4 + 2) * NS + s2], in1 = sf[(c * 4 + 1) * NS + s1],
+                         in0 = sf[(c * 4 + 0) * NS + s0];
+                ff t = two_sum(hs, -in2.hi);
+                hs = t.hi;
+                el = __fadd_rn(el, __fsub_rn(t.lo, in2.lo));
+                t = two_sum(hs, -in1.hi);
+                hs = t.hi;
+                el = __fadd_rn(el, __fsub_rn(t.lo, in1.lo));
+                t = two_sum(hs, -in0.hi);
+                hs = t.hi;
+                el = __fadd_rn(el, __fsub_rn(t.lo, in0.lo));
 #pragma unroll
-                for (int sl = 0; sl < 4; sl++) acc = ff_add_sloppy(acc, sf[(c * 4 + sl) * NS + rp]);
-                F[c] = ff_to_double(acc);
+                for (int sl = 0; sl < 4; sl++) {
+                    const ff o = sf[(c * 4 + sl) * NS + rp];
+                    t = two_sum(hs, o.hi);
+                    hs = t.hi;
+                    el = __fadd_rn(el, __fadd_rn(t.lo, o.lo));
+                }
+                F[c] = f2d_bits(hs) + f2d_bits(el);
             }
         } else {
 #pragma unroll
@@ -466,8 +490,16 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
     }
     if (SAMPLE) {
         if (bad) atomicOr(A.status, 1);
-        const double t0 = bsum(w_acc, sred);
-        const double t1 = bsum(u_acc, sred);
+        double wd, ud;
+        if constexpr (FIX) {
+            wd = ff_to_double(w_acc);
+            ud = ff_to_double(u_acc);
+        } else {
+            wd = w_acc;
+            ud = u_acc;
+        }
+        const double t0 = bsum(wd, sred);
+        const double t1 = bsum(ud, sred);
         const double t2 = bsum(mvx2, sred);
         const double t3 = bsum(ke, sred);
         const double t4 = bsum(react, sred);

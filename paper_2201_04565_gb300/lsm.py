@@ -36,7 +36,8 @@ class lsm_desc(C.Structure):
                 ("k_tab", C.c_void_p), ("epsc_tab", C.c_void_p), ("mass_tab", C.c_void_p),
                 ("k2_ratio", C.c_double), ("a", C.c_double), ("dt", C.c_double),
                 ("damping", C.c_double), ("grip_mode", C.c_int32), ("load_mode", C.c_int32),
-                ("precision", C.c_int32), ("path", C.c_int32), ("stream", C.c_void_p)]
+                ("precision", C.c_int32), ("path", C.c_int32), ("stream", C.c_void_p),
+                ("lattice", C.c_int32)]
 
 
 class lsm_net_desc(C.Structure):
@@ -130,8 +131,9 @@ def _check(status, ctx=None):
 
 def lsm_build_from_image(phase, k_tab, epsc_tab, mass_tab=None, k2_ratio=1.0, a=1.0, dt=0.01,
                          damping=0.1, grip_mode=0, load_mode=0, precision="exact64", stream=None,
-                         path=0):
-    """Image -> context handle. phase: uint8 [ny, nx] or [nz, ny, nx]."""
+                         path=0, lattice=0):
+    """Image -> context handle. phase: uint8 [ny, nx] or [nz, ny, nx];
+    lattice 0 square/cubic, 1 triangular packing (2D)."""
     lib = load_library()
     ph = np.ascontiguousarray(phase, dtype=np.uint8)
     if ph.ndim == 2:
@@ -149,7 +151,8 @@ def lsm_build_from_image(phase, k_tab, epsc_tab, mass_tab=None, k2_ratio=1.0, a=
     d = lsm_desc(dim=dim, nx=nx, ny=ny, nz=nz, phase=_ptr(ph), nphase=nphase, k_tab=_ptr(kt),
                  epsc_tab=_ptr(et), mass_tab=_ptr(mt), k2_ratio=k2_ratio, a=a, dt=dt,
                  damping=damping, grip_mode=grip_mode, load_mode=load_mode,
-                 precision=PRECISIONS.get(precision, precision), path=path, stream=stream)
+                 precision=PRECISIONS.get(precision, precision), path=path, stream=stream,
+                 lattice=lattice)
     h = C.c_void_p()
     _check(lib.lsm_build_from_image(C.byref(d), C.byref(h)))
     return h

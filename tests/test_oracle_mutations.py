@@ -40,6 +40,9 @@ MUTATIONS = {
                            "for (int c = 0; c < dim; c++) t += J[a * 3 + c] * J[b * 3 + c];"),
     "field kinetic sign": ("stress[q * n + p] = (stress[q * n + p] - vv) / cell;",
                            "stress[q * n + p] = (stress[q * n + p] + vv) / cell;"),
+    "triangular row height": ("const double h = a * sqrt(3.0) * 0.5;", "const double h = a * sqrt(2.0) * 0.5;"),
+    "triangular neighbour parity": ("jx = (ix) + ((iy) & 1 ? 0 : -1) + ((t) == 2);",
+                                    "jx = (ix) + ((iy) & 1 ? -1 : 0) + ((t) == 2);"),
     "dropped z term": ("if (dim == 3) r2 = r2 + d[2] * d[2];\n        double r = sqrt(r2);\n        double c_s",
                        "double r = sqrt(r2);\n        double c_s"),
 }

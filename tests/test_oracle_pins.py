@@ -561,3 +561,92 @@ def test_fields_degenerate_shell_is_nan(oracle_mod):
     o.apply_strain(0.01)
     st, sn = o.fields()
     assert np.all(np.isnan(sn)) and np.all(np.isfinite(st))
+
+
+# --------------------------------------------- triangular packing (lattice 1)
+
+def _tri_sites(img):
+    """Sites of the triangular packing of an image, straight from the rule
+    (rows at y = iy sqrt(3)/2 pixels up to ny - 1; odd rows shifted by half a
+    pixel and one site shorter; each site takes its nearest pixel), with
+    floating-point geometry in place of the build's integer arithmetic."""
+    ny, nx = img.shape
+    out = []
+    iy = 0
+    while iy * math.sqrt(3) / 2 <= ny - 1 + 1e-12:
+        y = iy * math.sqrt(3) / 2
+        for ix in range(nx - (iy & 1)):
+            x = ix + 0.5 * (iy & 1)
+            ph = img[int(math.floor(y + 0.5)), int(math.floor(x + 0.5))]
+            if ph:
+                out.append((x, y, ph))
+        iy += 1
+    return out, iy
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_triangular_build_matches_brute_force(oracle_mod, seed):
+    """Triangular packing: particles where the rule puts them, in raster
+    order, and springs = every pair of particles at distance a (all-pairs
+    search), in canonical order, with k and rc from the endpoint phases."""
+    rng = np.random.default_rng(40 + seed)
+    img = rng.integers(0, 3, size=(9, 11)).astype(np.uint8)
+    k, e, m = two_phase_materials()
+    a = 1.7
+    o = oracle_mod.Oracle.from_image(img, k, e, m, a=a, lattice=1)
+    sites, _ = _tri_sites(img)
+    t = o.topology()
+    assert o.n == len(sites)
+    want_X = np.array([[x * a for x, _, _ in sites], [y * a for _, y, _ in sites]])
+    assert np.allclose(t["X"], want_X, rtol=0, atol=1e-12)
+    ph = np.array([p for _, _, p in sites])
+    pairs = []
+    for i in range(o.n):
+        for j in range(i + 1, o.n):
+            if abs(np.sum((want_X[:, j] - want_X[:, i]) ** 2) - a * a) < 1e-9:
+                pairs.append((i, j))
+    assert list(zip(t["si"].tolist(), t["sj"].tolist())) == pairs
+    for s, (i, j) in enumerate(pairs):
+        assert t["k"][s] == k[ph[i] - 1, ph[j] - 1]
+        assert t["r0"][s] == a
+        assert t["rc2"][s] == pytest.approx((a * (1 + e[ph[i] - 1, ph[j] - 1])) ** 2, rel=1e-15)
+
+
+def test_triangular_counts_closed_form(oracle_mod):
+    """Full image: R rows alternate nx and nx - 1 sites; springs are
+    (sites - R) within rows plus 2 (nx - 1) between each pair of rows."""
+    k, e, m = two_phase_materials()
+    for nx, ny in [(6, 5), (13, 30), (40, 2)]:
+        o = oracle_mod.Oracle.from_image(np.ones((ny, nx), np.uint8), k, e, m, lattice=1)
+        R = 1 + max(r for r in range(ny * 2) if 3 * r * r <= 4 * (ny - 1) ** 2)
+        sites = R * nx - R // 2
+        assert o.n == sites
+        assert o.m == (sites - R) + (R - 1) * 2 * (nx - 1)
+
+
+def test_triangular_lattice_modulus_and_poisson_ratio(oracle_mod):
+    """Uniform triangular lattice of central springs (first neighbours, k):
+    the plane continuum has lambda = mu = sqrt(3) k / 4, so E = 2 k / sqrt 3
+    and nu = 1/3. Under roller grips with free edges the homogeneous
+    uniaxial-stress field meets every boundary condition to first order (the
+    inclined springs are unstretched when nu = 1/3), so the relaxed specimen
+    shows E and nu up to O(eps)."""
+    from gen.images import one_phase_materials
+    k_tab, e_tab, mass = one_phase_materials(1.0, 0.5)
+    img = np.ones((14, 16), np.uint8)
+    o = oracle_mod.Oracle.from_image(img, k_tab, e_tab, mass, dt=0.3, damping=0.2, lattice=1)
+    eps = 1e-5
+    o.apply_strain(eps)
+    st, _ = o.relax(tol=1e-13, max_steps=400000, check_every=100)
+    assert st == 0
+    ob = o.observe()
+    assert ob["sigma_grip"] / eps == pytest.approx(2.0 / math.sqrt(3.0), rel=1e-3)
+    x, _, _ = o.state()
+    X = o.topology()["X"]
+    lat = (x[1].max() - x[1].min()) / (X[1].max() - X[1].min()) - 1.0
+    assert -lat / eps == pytest.approx(1.0 / 3.0, rel=1e-3)
+    # per-particle stress of an interior particle (cell a h) equals E eps
+    st_f, _ = o.fields(math.sqrt(3.0) / 2)
+    mid = np.argmin((X[0] - X[0].mean()) ** 2 + (X[1] - X[1].mean()) ** 2)
+    assert st_f[0, mid] / eps == pytest.approx(2.0 / math.sqrt(3.0), rel=1e-3)
+    assert abs(st_f[1, mid]) < 1e-3 * eps
