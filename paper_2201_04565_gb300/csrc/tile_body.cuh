@@ -223,12 +223,14 @@ __device__ __forceinline__ void eval_spring(const TileArgs &A, int rp, int rq, i
     sf[(1 * 4 + slot) * NS + rp] = fy;
 }
 
-// Region pixel (rx, ry) -> shared memory: phase, broken mask, positions
-// drifted by dt vh (step mode), fixed-point copies.
+// Region pixel (rx, ry) -> shared memory: phase, broken mask, and the
+// positions drifted by dt vh (step mode): as doubles in the FP64 modes, as
+// fixed-point copies in the F32/DF modes. The drifted position is also
+// returned (the owning thread keeps it in registers for the integration).
 template <int PREC, int MODE, int RX>
 __device__ __forceinline__ void load_pixel(const TileArgs &A, int x0, int y0, int rx, int ry, double *sx,
                                            double *sy, long long *sxf, long long *syf, uint8_t *sph,
-                                           uint8_t *smk, bool &over)
+                                           uint8_t *smk, bool &over, double &opx, double &opy)
 {
     constexpr bool FIX = PREC == LSM_PREC_F32 || PREC == LSM_PREC_DF;
     const int gx = x0 - 1 + rx, gy = y0 - 1 + ry;
@@ -255,11 +257,14 @@ __device__ __forceinline__ void load_pixel(const TileArgs &A, int x0, int y0, in
             }
         }
     }
-    sx[e] = px;
-    sy[e] = py;
+    opx = px;
+    opy = py;
     if constexpr (FIX) {
         sxf[e] = dbl_to_fix(px, A.S, over);
         syf[e] = dbl_to_fix(py, A.S, over);
+    } else {
+        sx[e] = px;
+        sy[e] = py;
     }
     sph[e] = ph;
     smk[e] = mk;
@@ -280,16 +285,17 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
     using FT = typename std::conditional<PREC == LSM_PREC_F32, float,
                typename std::conditional<PREC == LSM_PREC_DF, ff, double>::type>::type;
 
-    double *sx = (double *)smem_raw;               // [NR] drifted positions
-    double *sy = sx + NR;                          // [NR]
-    long long *sxf = (long long *)(sy + NR);       // [NR] fixed point (FIX modes only)
+    constexpr int NRD = FIX ? 0 : NR;              // FP64 modes: positions as doubles
+    double *sx = (double *)smem_raw;               // [NRD] drifted positions
+    double *sy = sx + NRD;                         // [NRD]
+    long long *sxf = (long long *)(sy + NRD);      // [NR] fixed point (FIX modes only)
     long long *syf = sxf + (FIX ? NR : 0);         // [NR]
     FT *sf = (FT *)(syf + (FIX ? NR : 0));         // [2][4][NS] force on the lower end
     int *snew = (int *)(sf + 8 * NS);              // [NS] springs broken in this step
     uint8_t *sph = (uint8_t *)(snew + NS);         // [NR]
     uint8_t *smk = sph + NR;                       // [NR]
     __shared__ double sred[NW];
-    __shared__ SpringType stab[128];
+    __shared__ SpringType stab[FIX ? 1 : 128];
     __shared__ TypeDF sdf[FIX ? 128 : 1];
     __shared__ ff soff[4][3];  // per slot: o_x, o_y, |o|^2 as double-floats
     __shared__ double smass[8];
@@ -299,8 +305,10 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
     const int x0 = bx * TX, y0 = by * TY;
     const int nt = 2 * A.nphase * A.nphase;
     for (int q = tid; q < nt; q += TILE_THREADS) {
-        stab[q] = A.types[q];
-        if constexpr (FIX) sdf[q] = A.tdf[q];
+        if constexpr (FIX)
+            sdf[q] = A.tdf[q];
+        else
+            stab[q] = A.types[q];
     }
     if (tid < A.nphase) {
         smass[tid] = A.mass[tid];
@@ -317,11 +325,22 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
     const long long step_now = MODE == T_STEP ? *A.d_step + A.t_off : 0;
 
     // 1. region load (+ drift): tile columns by lanes, halo columns apart
+    // region rows warp, warp + NW, ...: the thread keeps its column's
+    // drifted positions in registers for phase 3 (it owns those pixels)
+    constexpr int KR = (RY + NW - 1) / NW;
+    double opx[KR], opy[KR];
     bool over = false;
-    for (int ry = warp; ry < RY; ry += NW)
-        load_pixel<PREC, MODE, RX>(A, x0, y0, lane + 1, ry, sx, sy, sxf, syf, sph, smk, over);
-    for (int q = tid; q < 2 * RY; q += TILE_THREADS)
-        load_pixel<PREC, MODE, RX>(A, x0, y0, (q & 1) ? TX + 1 : 0, q >> 1, sx, sy, sxf, syf, sph, smk, over);
+#pragma unroll
+    for (int k = 0; k < KR; k++) {
+        const int ry = warp + k * NW;
+        if (ry < RY)
+            load_pixel<PREC, MODE, RX>(A, x0, y0, lane + 1, ry, sx, sy, sxf, syf, sph, smk, over, opx[k], opy[k]);
+    }
+    for (int q = tid; q < 2 * RY; q += TILE_THREADS) {
+        double hx, hy;
+        load_pixel<PREC, MODE, RX>(A, x0, y0, (q & 1) ? TX + 1 : 0, q >> 1, sx, sy, sxf, syf, sph, smk, over, hx,
+                                   hy);
+    }
     if (FIX && over) atomicOr(A.status, 2);
     for (int e = tid; e < NS; e += TILE_THREADS) snew[e] = 0;
     __syncthreads();
@@ -367,10 +386,11 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
     double mvx2 = 0.0, ke = 0.0, react = 0.0, res = 0.0;
     bool bad = false;
 #pragma unroll
-    for (int k = 0; k < TY / NW; k++) {
-        const int ly = warp + k * NW;
+    for (int k = 0; k < KR; k++) {
+        const int ry = warp + k * NW, ly = ry - 1;  // the rows loaded into registers above
+        if (ry < 1 || ry > TY) continue;
         const int gx = x0 + lane, gy = y0 + ly;
-        const int rx = lane + 1, ry = ly + 1;
+        const int rx = lane + 1;
         const int rp = ry * RX + rx;
         if (gx >= A.nx || gy >= A.ny || !sph[rp]) continue;
         const int64_t g = (int64_t)gy * A.nx + gx;
@@ -433,7 +453,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
         const bool fixx = grip, fixy = grip && A.grip_mode == 1;
         const int ph = sph[rp] - 1;
         const double m = smass[ph];
-        const double xr[2] = {sx[rp], sy[rp]};
+        const double xr[2] = {opx[k], opy[k]};
         if (SAMPLE && gx == A.nx - 1) {
             if constexpr (PREC == LSM_PREC_EXACT64) react = sb(react, F[0]);
             else react -= F[0];
@@ -529,7 +549,7 @@ constexpr size_t tile_smem_bytes(int prec)
     constexpr int RX = TX + 2, RY = TY + 2, SX = TX + 2, SY = TY + 1;  // sources: region rows 0..TY
     const bool fix = prec == LSM_PREC_F32 || prec == LSM_PREC_DF;
     const size_t fsz = prec == LSM_PREC_F32 ? sizeof(float) : sizeof(double);  // ff is 8 bytes
-    return (size_t)2 * RX * RY * sizeof(double) + (fix ? (size_t)2 * RX * RY * sizeof(long long) : 0) +
+    return (fix ? 0 : (size_t)2 * RX * RY * sizeof(double)) + (fix ? (size_t)2 * RX * RY * sizeof(long long) : 0) +
            (size_t)8 * SX * SY * fsz + (size_t)SX * SY * sizeof(int) + (size_t)2 * RX * RY + 16;
 }
 
