@@ -105,6 +105,27 @@ __device__ __forceinline__ double f2d_bits(float f)
     return __longlong_as_double((long long)bits);
 }
 
+// Double -> float with integer operations, truncating the significand
+// (|x| below the float range gives a signed zero, above it infinity).
+__device__ __forceinline__ float d2f_bits(double d)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7FFu);
+    const int fe = e - 1023 + 127;
+    if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (((hi & 0xFFFFFu) | lo) ? 0x400000u : 0u));
+    if (fe <= 0) return __uint_as_float(sign);
+    if (fe >= 255) return __uint_as_float(sign | 0x7F800000u);
+    return __uint_as_float(sign | ((unsigned)fe << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+
+// isfinite for a double, from its exponent bits.
+__device__ __forceinline__ bool dbl_finite_bits(double d)
+{
+    return ((unsigned)(__double_as_longlong(d) >> 32) & 0x7FF00000u) != 0x7FF00000u;
+}
+
 // -- error-free transformations and double-float arithmetic ----------------
 
 __device__ __forceinline__ ff two_sum(float a, float b)

@@ -299,6 +299,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
     __shared__ TypeDF sdf[FIX ? 128 : 1];
     __shared__ ff soff[4][3];  // per slot: o_x, o_y, |o|^2 as double-floats
     __shared__ double smass[8];
+    __shared__ float smassf[8];
     __shared__ Coef4 scoef[8];  // per phase: c1, c2, c1h, c2h (vh' = c1 vh + c2 F)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -312,6 +313,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
     }
     if (tid < A.nphase) {
         smass[tid] = A.mass[tid];
+        smassf[tid] = (float)A.mass[tid];
         scoef[tid] = A.coef[tid];
     }
     if (FIX && tid < 4) {
@@ -384,6 +386,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
 
     // 3. gather + integrate the owned particles
     double mvx2 = 0.0, ke = 0.0, react = 0.0, res = 0.0;
+    float mvx2f = 0.0f, kef = 0.0f, resf = 0.0f;  // fixed-point modes
     bool bad = false;
 #pragma unroll
     for (int k = 0; k < KR; k++) {
@@ -398,6 +401,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
         // source index), then the outgoing ones in slot order
         const int s3 = rp - RX - 1, s2 = rp - RX, s1 = rp - RX + 1, s0 = rp - 1;
         double F[2];
+        float Ff[2];  // F as floats (fixed-point modes: sample statistics without FP64 work)
         if constexpr (PREC == LSM_PREC_EXACT64) {
 #pragma unroll
             for (int c = 0; c < 2; c++) {
@@ -437,6 +441,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
                     el = __fadd_rn(el, __fadd_rn(t.lo, o.lo));
                 }
                 F[c] = f2d_bits(hs) + f2d_bits(el);
+                Ff[c] = __fadd_rn(hs, el);
             }
         } else {
 #pragma unroll
@@ -445,8 +450,12 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
                 acc += sf[(c * 4 + 1) * NS + rp] - sf[(c * 4 + 2) * NS + s2];
                 acc += sf[(c * 4 + 2) * NS + rp] - sf[(c * 4 + 1) * NS + s1];
                 acc += sf[(c * 4 + 3) * NS + rp] - sf[(c * 4 + 0) * NS + s0];
-                if constexpr (PREC == LSM_PREC_F32) F[c] = f2d_bits(acc);
-                else F[c] = acc;
+                if constexpr (PREC == LSM_PREC_F32) {
+                    F[c] = f2d_bits(acc);
+                    Ff[c] = acc;
+                } else {
+                    F[c] = acc;
+                }
             }
         }
         const bool grip = gx == 0 || gx == A.nx - 1;
@@ -471,9 +480,16 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
             if (MODE == T_OBSERVE) {
                 const double vn = A.v_obs[q];
                 if (SAMPLE) {
-                    res = fmax(res, fmax(fabs(F[c]), fabs(vn)));
-                    ke += 0.5 * m * vn * vn;
-                    if (c == 0) mvx2 += m * vn * vn;
+                    if constexpr (FIX) {
+                        const float vf = d2f_bits(vn);
+                        resf = fmaxf(resf, fmaxf(fabsf(Ff[c]), fabsf(vf)));
+                        kef = fmaf(0.5f * smassf[ph] * vf, vf, kef);
+                        if (c == 0) mvx2f = fmaf(smassf[ph] * vf, vf, mvx2f);
+                    } else {
+                        res = fmax(res, fmax(fabs(F[c]), fabs(vn)));
+                        ke += 0.5 * m * vn * vn;
+                        if (c == 0) mvx2 += m * vn * vn;
+                    }
                 }
                 continue;
             }
@@ -497,10 +513,20 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
             A.vh_out[q] = vh2;
             if (SAMPLE) {
                 A.v_obs[q] = vn;
-                res = fmax(res, fmax(fabs(F[c]), fabs(vn)));
-                ke += 0.5 * m * vn * vn;
-                if (c == 0) mvx2 += m * vn * vn;
-                bad |= !isfinite(vn) || !isfinite(xr[c]);
+                if constexpr (FIX) {
+                    // float statistics (residual, KE, m v_x^2): 2^-24 relative,
+                    // and the FP64 pipe is left to the integration
+                    const float vf = d2f_bits(vn);
+                    resf = fmaxf(resf, fmaxf(fabsf(Ff[c]), fabsf(vf)));
+                    kef = fmaf(0.5f * smassf[ph] * vf, vf, kef);
+                    if (c == 0) mvx2f = fmaf(smassf[ph] * vf, vf, mvx2f);
+                    bad |= !dbl_finite_bits(vn) || !dbl_finite_bits(xr[c]);
+                } else {
+                    res = fmax(res, fmax(fabs(F[c]), fabs(vn)));
+                    ke += 0.5 * m * vn * vn;
+                    if (c == 0) mvx2 += m * vn * vn;
+                    bad |= !isfinite(vn) || !isfinite(xr[c]);
+                }
             }
         }
         if (MODE == T_STEP) {
@@ -509,6 +535,11 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
         }
     }
     if (SAMPLE) {
+        if constexpr (FIX) {
+            mvx2 = f2d_bits(mvx2f);
+            ke = f2d_bits(kef);
+            res = f2d_bits(resf);
+        }
         if (bad) atomicOr(A.status, 1);
         double wd, ud;
         if constexpr (FIX) {
