@@ -77,7 +77,6 @@ struct BatchCtx {
     int64_t cap = 0, nsamples = 0;
     int fix_S = 40;
     long long a_fix = 0;
-    bool o_exact = false;
     int64_t spring_updates = 0, launches = 0;
     std::map<int64_t, cudaGraphExec_t> graphs;
     std::map<int64_t, int64_t> graph_nodes;
@@ -86,7 +85,7 @@ struct BatchCtx {
 
 // ----------------------------------------------------------------- kernels
 
-template <int TY, int PREC, int MODE, bool SAMPLE, bool ODY>
+template <int TY, int PREC, int MODE, bool SAMPLE>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_tile2d_batch(TileArgs base, const BatchTile *__restrict__ tiles, int64_t t0, int64_t t1,
                const SpecDesc *__restrict__ specs, double *X0, double *X1, double *V0, double *V1, double *VOBS,
@@ -117,7 +116,7 @@ k_tile2d_batch(TileArgs base, const BatchTile *__restrict__ tiles, int64_t t0, i
         A.nbroken = nb + bt.spec;
         A.d_step = &specs[bt.spec].steps;
         A.t_off = 0;
-        tile_body<32, TY, PREC, MODE, SAMPLE, ODY>(A, bt.bx, bt.by, t, smem_raw);
+        tile_body<32, TY, PREC, MODE, SAMPLE>(A, bt.bx, bt.by, t, smem_raw);
         __syncthreads();
     }
 }
@@ -359,13 +358,6 @@ static TileArgs batch_base_args(BatchCtx &b)
     A.p48 = ldexpf(1.0f, 48 - b.fix_S);
     A.p24 = ldexpf(1.0f, 24 - b.fix_S);
     A.p0 = ldexpf(1.0f, -b.fix_S);
-    {
-        const double aa = std::ldexp((double)b.a_fix, -b.fix_S);  // lattice spacing as used
-        A.fa = (float)aa;
-        A.fa2 = (float)(2.0 * aa);
-        A.fo2a = (float)(aa * aa);
-        A.fo2d = (float)(2.0 * aa * aa);
-    }
     A.status = b.status;
     A.part_s = b.part_s;
     A.part_p = b.part_p;
@@ -373,10 +365,10 @@ static TileArgs batch_base_args(BatchCtx &b)
     return A;
 }
 
-template <int TY, int PREC, int MODE, bool SAMPLE, bool ODY>
+template <int TY, int PREC, int MODE, bool SAMPLE>
 static cudaError_t launch_bt(BatchCtx &b, int64_t t0, int64_t t1)
 {
-    auto kern = k_tile2d_batch<TY, PREC, MODE, SAMPLE, ODY>;
+    auto kern = k_tile2d_batch<TY, PREC, MODE, SAMPLE>;
     const size_t smem = tile_smem_bytes<32, TY>(PREC);
     static bool configured = false;
     if (!configured) {
@@ -397,12 +389,10 @@ static cudaError_t launch_b(BatchCtx &b, int64_t t0, int64_t t1)
 {
 #define BT_PREC(TYV)                                                                              \
     switch (b.prec) {                                                                             \
-    case LSM_PREC_EXACT64: return launch_bt<TYV, LSM_PREC_EXACT64, MODE, SAMPLE, false>(b, t0, t1); \
-    case LSM_PREC_FAST64: return launch_bt<TYV, LSM_PREC_FAST64, MODE, SAMPLE, false>(b, t0, t1);   \
-    case LSM_PREC_F32: return launch_bt<TYV, LSM_PREC_F32, MODE, SAMPLE, false>(b, t0, t1);         \
-    default:                                                                                      \
-        return b.o_exact ? launch_bt<TYV, LSM_PREC_DF, MODE, SAMPLE, true>(b, t0, t1)              \
-                         : launch_bt<TYV, LSM_PREC_DF, MODE, SAMPLE, false>(b, t0, t1);            \
+    case LSM_PREC_EXACT64: return launch_bt<TYV, LSM_PREC_EXACT64, MODE, SAMPLE>(b, t0, t1);      \
+    case LSM_PREC_FAST64: return launch_bt<TYV, LSM_PREC_FAST64, MODE, SAMPLE>(b, t0, t1);        \
+    case LSM_PREC_F32: return launch_bt<TYV, LSM_PREC_F32, MODE, SAMPLE>(b, t0, t1);              \
+    default: return launch_bt<TYV, LSM_PREC_DF, MODE, SAMPLE>(b, t0, t1);                         \
     }
     if (b.tile_y == 8) { BT_PREC(8) }
     if (b.tile_y == 32) { BT_PREC(32) }
@@ -484,13 +474,8 @@ static cudaError_t batch_upload(BatchCtx &b, const std::vector<HostNet> &nets, c
     int maxext = 0;
     for (int s = 0; s < S; s++) maxext = std::max(maxext, std::max(b.nx[s], b.ny[s]));
     const double extent = 4.0 * maxext * b.a + 16.0;
-    b.fix_S = std::min(52, 61 - (int)std::ceil(std::log2(extent)));
+    b.fix_S = std::min(61 - (int)std::ceil(std::log2(extent)), 47 - (int)std::ceil(std::log2(b.a * std::sqrt(2.0))));
     b.a_fix = std::llround(std::ldexp(b.a, b.fix_S));
-    {
-        const double aa = std::ldexp((double)b.a_fix, -b.fix_S);
-        b.o_exact = (double)(float)aa == aa && (double)(float)(aa * aa) == aa * aa &&
-                    (double)(float)(2.0 * aa * aa) == 2.0 * aa * aa && (double)(float)(2.0 * aa) == 2.0 * aa;
-    }
     for (int q = 0; q < 2; q++) {
         BT_TRY(balloc(&b.X[q], 2 * NP));
         BT_TRY(balloc(&b.VH[q], 2 * NP));

@@ -21,6 +21,7 @@
 // chunk.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 
@@ -450,16 +451,14 @@ static cudaError_t upload_tile(Ctx &c)
         itab[4 * q + 2] = 1.0 - hdt * g / m;
         itab[4 * q + 3] = hdt / m;
     }
-    // fixed-point scale: |x| stays below 2^(62 - S) for strains up to +300%
+    // fixed-point scale: |x| stays below 2^(62 - S) for strains up to +300%,
+    // and spring vectors up to 2 r0 of the diagonal spring (a sqrt 2) stay
+    // below 2^(48 - S), where their conversion to double-float takes the
+    // two-chunk path
     const double extent = 4.0 * (double)(h.nx > h.ny ? h.nx : h.ny) * h.a + 16.0;
     c.fix_S = 61 - (int)std::ceil(std::log2(extent));
-    if (c.fix_S > 52) c.fix_S = 52;
+    c.fix_S = std::min(c.fix_S, 47 - (int)std::ceil(std::log2(h.a * std::sqrt(2.0))));
     c.a_fix = std::llround(std::ldexp(h.a, c.fix_S));
-    {
-        const double aa = std::ldexp((double)c.a_fix, -c.fix_S);
-        c.o_exact = (double)(float)aa == aa && (double)(float)(aa * aa) == aa * aa &&
-                    (double)(float)(2.0 * aa * aa) == 2.0 * aa * aa && (double)(float)(2.0 * aa) == 2.0 * aa;
-    }
     std::vector<int64_t> sbase(np, 0);
     for (int64_t s = h.m - 1; s >= 0; s--) sbase[h.pix[h.si[s]]] = s;
     std::vector<TypeDF> tdf(h.types.size());

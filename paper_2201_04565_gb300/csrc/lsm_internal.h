@@ -134,7 +134,6 @@ struct Ctx {
     TypeDF *tdf = nullptr;                // double-float spring types
     int fix_S = 40;                       // fixed-point scale of positions
     long long a_fix = 0;                  // lattice spacing * 2^fix_S
-    bool o_exact = false;                 // lattice vectors and |o|^2 exact as floats
     int64_t *tsbase = nullptr;            // [tnp] canonical index of each pixel's first spring
     // spring-list path in the fixed-point modes (image builds, F32 / DF)
     bool fixcsr = false;

@@ -27,12 +27,12 @@
 
 namespace lsm {
 
-template <int TX, int TY, int PREC, int MODE, bool SAMPLE, bool ODY>
+template <int TX, int TY, int PREC, int MODE, bool SAMPLE>
 __global__ void __launch_bounds__(TILE_THREADS)
 k_tile2d(TileArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    tile_body<TX, TY, PREC, MODE, SAMPLE, ODY>(A, blockIdx.x, blockIdx.y,
+    tile_body<TX, TY, PREC, MODE, SAMPLE>(A, blockIdx.x, blockIdx.y,
                                                 (int64_t)blockIdx.y * gridDim.x + blockIdx.x, smem_raw);
 }
 
@@ -127,13 +127,6 @@ static TileArgs tile_args(Ctx &c)
     A.p48 = ldexpf(1.0f, 48 - c.fix_S);
     A.p24 = ldexpf(1.0f, 24 - c.fix_S);
     A.p0 = ldexpf(1.0f, -c.fix_S);
-    {
-        const double aa = std::ldexp((double)c.a_fix, -c.fix_S);  // lattice spacing as used
-        A.fa = (float)aa;
-        A.fa2 = (float)(2.0 * aa);
-        A.fo2a = (float)(aa * aa);
-        A.fo2d = (float)(2.0 * aa * aa);
-    }
     A.dt = c.h.dt;
     A.hdt = 0.5 * c.h.dt;
     A.gamma = c.h.damping;
@@ -150,10 +143,10 @@ static TileArgs tile_args(Ctx &c)
     return A;
 }
 
-template <int PREC, int MODE, bool SAMPLE, bool ODY = false>
+template <int PREC, int MODE, bool SAMPLE>
 static cudaError_t launch_tile(Ctx &c, TileArgs A)
 {
-    auto kern = k_tile2d<TILE_X, TILE_Y, PREC, MODE, SAMPLE, ODY>;
+    auto kern = k_tile2d<TILE_X, TILE_Y, PREC, MODE, SAMPLE>;
     const size_t smem = tile_smem_bytes<TILE_X, TILE_Y>(PREC);
     static bool configured = false;  // per template instance
     if (!configured) {
@@ -172,9 +165,7 @@ static cudaError_t launch_tile_prec(Ctx &c, TileArgs A)
     switch (c.h.precision) {
     case LSM_PREC_FAST64: return launch_tile<LSM_PREC_FAST64, MODE, SAMPLE>(c, A);
     case LSM_PREC_F32: return launch_tile<LSM_PREC_F32, MODE, SAMPLE>(c, A);
-    case LSM_PREC_DF:
-        return c.o_exact ? launch_tile<LSM_PREC_DF, MODE, SAMPLE, true>(c, A)
-                         : launch_tile<LSM_PREC_DF, MODE, SAMPLE, false>(c, A);
+    case LSM_PREC_DF: return launch_tile<LSM_PREC_DF, MODE, SAMPLE>(c, A);
     default: return launch_tile<LSM_PREC_EXACT64, MODE, SAMPLE>(c, A);
     }
 }

@@ -46,6 +46,36 @@ __device__ __forceinline__ double bmax(double v, double *sh)
     return t;
 }
 
+// Fixed-order block sum of a double-float per thread: the warp tree in
+// double-float arithmetic (FP32 pipe), then the warps' totals in FP64 by
+// thread 0. Deterministic for a given block size.
+__device__ __forceinline__ double bsum_ff(ff v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const ff w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = ff_add_sloppy(v, w);
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = ff_to_double(v);
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < TILE_THREADS / 32; q++) t += sh[q];
+    return t;
+}
+
+__device__ __forceinline__ double bmax_f(float v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = f2d_bits(v);
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int q = 0; q < TILE_THREADS / 32; q++) t = fmax(t, sh[q]);
+    return t;
+}
+
 }  // namespace
 
 enum { T_STEP = 0, T_INIT = 1, T_OBSERVE = 2 };
@@ -71,7 +101,6 @@ struct TileArgs {
     int S;                     // fixed-point scale: positions as x * 2^S
     long long a_fix;           // lattice spacing in fixed point
     float p48, p24, p0;        // 2^(48-S), 2^(24-S), 2^-S
-    float fa, fa2, fo2a, fo2d;  // a, 2a, a^2, 2a^2 as floats (exact when the lattice is)
     double dt, hdt, gamma, a;
     int grip_mode;
     const long long *d_step;  // steps completed before this graph launch
@@ -85,7 +114,7 @@ struct TileArgs {
 // Force on the lower endpoint of one spring (rp -> rq, forward slot), with
 // the break test. Writes the force into sf; OWNER adds the sample sums and
 // records a break (only the tile owning the lower endpoint does).
-template <int PREC, int MODE, bool SAMPLE, bool OWNER, bool ODY, int NR, int NS, typename FT, typename AT>
+template <int PREC, int MODE, bool SAMPLE, bool OWNER, int NR, int NS, typename FT, typename AT>
 __device__ __forceinline__ void eval_spring(const TileArgs &A, int rp, int rq, int slot, const double *sx,
                                             const double *sy, const long long *sxf, const long long *syf,
                                             const uint8_t *sph, const uint8_t *smk, FT *sf,
@@ -134,15 +163,15 @@ __device__ __forceinline__ void eval_spring(const TileArgs &A, int rp, int rq, i
                 }
             }
         } else {
-            // exact spring vector d = o + e from the fixed-point positions; e
-            // is the deviation from the lattice vector o, so
-            // r^2 - |o|^2 = (2 o + e).e carries no cancellation
             const TypeDF t = sdf[ti];
-            const int dx = slot == 0 ? 1 : (slot == 1 ? -1 : (slot == 2 ? 0 : 1));
-            const int dy = slot == 0 ? 0 : 1;
-            const long long exf = sxf[rq] - sxf[rp] - (long long)dx * A.a_fix;
-            const long long eyf = syf[rq] - syf[rp] - (long long)dy * A.a_fix;
             if constexpr (PREC == LSM_PREC_F32) {
+                // exact spring vector d = o + e from the fixed-point positions;
+                // e is the deviation from the lattice vector o, so
+                // r^2 - |o|^2 = (2 o + e).e carries no cancellation in float
+                const int dx = slot == 0 ? 1 : (slot == 1 ? -1 : (slot == 2 ? 0 : 1));
+                const int dy = slot == 0 ? 0 : 1;
+                const long long exf = sxf[rq] - sxf[rp] - (long long)dx * A.a_fix;
+                const long long eyf = syf[rq] - syf[rp] - (long long)dy * A.a_fix;
                 const float ex = fix_to_float_i2f(exf, A.p24, A.p0), ey = fix_to_float_i2f(eyf, A.p24, A.p0);
                 const float ox = soff[slot][0].hi, oy = soff[slot][1].hi;
                 const float dxf = ox + ex, dyf = oy + ey;
@@ -161,51 +190,24 @@ __device__ __forceinline__ void eval_spring(const TileArgs &A, int rp, int rq, i
                         w_acc = ff_add_f(w_acc, dxf * fx);
                     }
                 }
-            } else if constexpr (ODY) {  // LSM_PREC_DF, lattice vectors exact in float
-                // o = (dx a, dy a) with a, 2a, a^2 and 2a^2 exact floats; the
-                // slot is a compile-time constant for the owned springs, so
-                // zero components of o cost nothing there
-                const ff ex = fix_to_ff_i2f2(exf, A.p48, A.p24, A.p0);
-                const ff ey = fix_to_ff_i2f2(eyf, A.p48, A.p24, A.p0);
-                const ff qx = dx == 0 ? ff_sqr(ex) : ff_mul(ff_add_f(ex, dx > 0 ? A.fa2 : -A.fa2), ex);
-                const ff qy = dy == 0 ? ff_sqr(ey) : ff_mul(ff_add_f(ey, A.fa2), ey);
-                const ff r2 = ff_add_f(ff_add_sloppy(qx, qy), (dx != 0 && dy != 0) ? A.fo2d : A.fo2a);
+            } else {  // LSM_PREC_DF
+                // the spring vector d = x_j - x_i as an exact fixed-point
+                // difference, converted to a double-float; 1/r by Newton and
+                // k (r - r0) / r = k (1 - r0 / r), the same cancellation as
+                // FP64's k (r - r0) / r, resolved at 2^-46 instead of 2^-53
+                const ff dxf = fix_to_ff_i2f2(sxf[rq] - sxf[rp], A.p48, A.p24, A.p0);
+                const ff dyf = fix_to_ff_i2f2(syf[rq] - syf[rp], A.p48, A.p24, A.p0);
+                const ff r2 = ff_add_sloppy(ff_sqr(dxf), ff_sqr(dyf));
                 if (MODE == T_STEP && ff_gt(r2, t.rc2)) {
                     brk_now = true;
                 } else {
-                    // k (r - r0) / r = k (1 - r0 y) with y = 1/r to ~2^-46: the
-                    // same cancellation as FP64's k (r - r0) / r, at 2^-46
                     const ff y = ff_rsqrt(r2);
                     const ff g = ff_one_minus(ff_mul(t.r0, y));
                     const ff c = ff_mul(t.k, g);
-                    const ff dxf = dx == 0 ? ex : ff_add_f(ex, dx > 0 ? A.fa : -A.fa);
-                    const ff dyf = dy == 0 ? ey : ff_add_f(ey, A.fa);
                     fx = ff_mul(c, dxf);
                     fy = ff_mul(c, dyf);
                     if (SAMPLE && OWNER) {  // double-float sums: no FP64 pipe work per spring
                         const ff st = ff_mul(ff_mul(r2, y), g);  // r - r0
-                        u_acc = ff_add_sloppy(u_acc, ff_mul(ff_mul_f(t.k, 0.5f), ff_sqr(st)));
-                        w_acc = ff_add_sloppy(w_acc, ff_mul(dxf, fx));
-                    }
-                }
-            } else {  // LSM_PREC_DF, general lattice spacing
-                const ff ex = fix_to_ff_i2f(exf, A.p48, A.p24, A.p0);
-                const ff ey = fix_to_ff_i2f(eyf, A.p48, A.p24, A.p0);
-                const ff ox = soff[slot][0], oy = soff[slot][1];
-                const ff dxf = ff_add(ox, ex), dyf = ff_add(oy, ey);
-                const ff num = ff_add(ff_add(ff_mul(ff_add(ff_add(ox, ox), ex), ex),
-                                             ff_mul(ff_add(ff_add(oy, oy), ey), ey)), t.cor);
-                const ff r2 = ff_add(soff[slot][2], num);
-                if (MODE == T_STEP && ff_gt(r2, t.rc2)) {
-                    brk_now = true;
-                } else {
-                    const ff r = ff_sqrt(r2);
-                    const ff den = ff_mul(r, ff_add(r, t.r0));
-                    const ff c = ff_mul(t.k, ff_div(num, den));  // k (r - r0) / r
-                    fx = ff_mul(c, dxf);
-                    fy = ff_mul(c, dyf);
-                    if (SAMPLE && OWNER) {
-                        const ff st = ff_div(num, ff_add(r, t.r0));
                         u_acc = ff_add_sloppy(u_acc, ff_mul(ff_mul_f(t.k, 0.5f), ff_sqr(st)));
                         w_acc = ff_add_sloppy(w_acc, ff_mul(dxf, fx));
                     }
@@ -272,7 +274,7 @@ __device__ __forceinline__ void load_pixel(const TileArgs &A, int x0, int y0, in
 
 // One CTA step of one 32 x TY tile (tile coordinates bx, by; tile_id indexes
 // the per-tile partial sums); warp w handles tile rows w, w + 8, ...
-template <int TX, int TY, int PREC, int MODE, bool SAMPLE, bool ODY>
+template <int TX, int TY, int PREC, int MODE, bool SAMPLE>
 __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int64_t tile_id,
                                           unsigned char *smem_raw)
 {
@@ -358,7 +360,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
         const int64_t g = (int64_t)(y0 + ry - 1) * A.nx + (x0 + lane);
 #pragma unroll
         for (int slot = 0; slot < 4; slot++)
-            eval_spring<PREC, MODE, SAMPLE, true, ODY, NR, NS>(A, rp, rp + dq[slot], slot, sx, sy, sxf, syf, sph, smk,
+            eval_spring<PREC, MODE, SAMPLE, true, NR, NS>(A, rp, rp + dq[slot], slot, sx, sy, sxf, syf, sph, smk,
                                                           sf, stab, sdf, soff, snew, g, step_now, w_acc, u_acc);
     }
     // 2b. springs from halo sources into the tile (also evaluated, with the
@@ -379,7 +381,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
             slot = 1; rx = TX + 1; ry = 1 + (t - 3 * TX - 2 * TY + 1);
         }
         const int rp = ry * RX + rx;
-        eval_spring<PREC, MODE, SAMPLE, false, ODY, NR, NS>(A, rp, rp + dq[slot], slot, sx, sy, sxf, syf, sph, smk, sf,
+        eval_spring<PREC, MODE, SAMPLE, false, NR, NS>(A, rp, rp + dq[slot], slot, sx, sy, sxf, syf, sph, smk, sf,
                                                        stab, sdf, soff, snew, 0, step_now, w_acc, u_acc);
     }
     __syncthreads();
@@ -387,6 +389,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
     // 3. gather + integrate the owned particles
     double mvx2 = 0.0, ke = 0.0, react = 0.0, res = 0.0;
     float mvx2f = 0.0f, kef = 0.0f, resf = 0.0f;  // fixed-point modes
+    ff reactf{0.0f, 0.0f};
     bool bad = false;
 #pragma unroll
     for (int k = 0; k < KR; k++) {
@@ -402,6 +405,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
         const int s3 = rp - RX - 1, s2 = rp - RX, s1 = rp - RX + 1, s0 = rp - 1;
         double F[2];
         float Ff[2];  // F as floats (fixed-point modes: sample statistics without FP64 work)
+        ff Fd[2];     // F as double-floats (fixed-point modes: the grip reaction)
         if constexpr (PREC == LSM_PREC_EXACT64) {
 #pragma unroll
             for (int c = 0; c < 2; c++) {
@@ -442,6 +446,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
                 }
                 F[c] = f2d_bits(hs) + f2d_bits(el);
                 Ff[c] = __fadd_rn(hs, el);
+                Fd[c] = ff{hs, el};
             }
         } else {
 #pragma unroll
@@ -453,6 +458,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
                 if constexpr (PREC == LSM_PREC_F32) {
                     F[c] = f2d_bits(acc);
                     Ff[c] = acc;
+                    Fd[c] = ff{acc, 0.0f};
                 } else {
                     F[c] = acc;
                 }
@@ -465,6 +471,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
         const double xr[2] = {opx[k], opy[k]};
         if (SAMPLE && gx == A.nx - 1) {
             if constexpr (PREC == LSM_PREC_EXACT64) react = sb(react, F[0]);
+            else if constexpr (FIX) reactf = ff_add_sloppy(reactf, ff_neg(Fd[0]));
             else react -= F[0];
         }
 #pragma unroll
@@ -535,26 +542,23 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
         }
     }
     if (SAMPLE) {
-        if constexpr (FIX) {
-            mvx2 = f2d_bits(mvx2f);
-            ke = f2d_bits(kef);
-            res = f2d_bits(resf);
-        }
         if (bad) atomicOr(A.status, 1);
-        double wd, ud;
-        if constexpr (FIX) {
-            wd = ff_to_double(w_acc);
-            ud = ff_to_double(u_acc);
+        double t0, t1, t2, t3, t4, t5;
+        if constexpr (FIX) {  // warp trees on the FP32 pipe
+            t0 = bsum_ff(w_acc, sred);
+            t1 = bsum_ff(u_acc, sred);
+            t2 = bsum_ff(ff{mvx2f, 0.0f}, sred);
+            t3 = bsum_ff(ff{kef, 0.0f}, sred);
+            t4 = bsum_ff(reactf, sred);
+            t5 = bmax_f(resf, sred);
         } else {
-            wd = w_acc;
-            ud = u_acc;
+            t0 = bsum(w_acc, sred);
+            t1 = bsum(u_acc, sred);
+            t2 = bsum(mvx2, sred);
+            t3 = bsum(ke, sred);
+            t4 = bsum(react, sred);
+            t5 = bmax(res, sred);
         }
-        const double t0 = bsum(wd, sred);
-        const double t1 = bsum(ud, sred);
-        const double t2 = bsum(mvx2, sred);
-        const double t3 = bsum(ke, sred);
-        const double t4 = bsum(react, sred);
-        const double t5 = bmax(res, sred);
         if (tid == 0) {
             A.part_s[tile_id] = t0;
             A.part_s[A.ntiles + tile_id] = t1;
