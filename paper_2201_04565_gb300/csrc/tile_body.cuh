@@ -15,13 +15,21 @@ namespace lsm {
 
 namespace {
 
-constexpr int TILE_THREADS = 256;
+// Threads per CTA for a tile of height TY: one warp per tile row, up to 16
+// warps in the double-float mode (measured best: occupancy is limited by
+// registers and shared memory) and 8 otherwise (fewer warps per barrier).
+template <int TY, int PREC>
+__host__ __device__ constexpr int tile_threads()
+{
+    return 32 * (TY < (PREC == LSM_PREC_DF ? 16 : 8) ? TY : (PREC == LSM_PREC_DF ? 16 : 8));
+}
 
 __device__ __forceinline__ double ad(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double sb(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double ml(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double dv(double a, double b) { return __ddiv_rn(a, b); }
 
+template <int NWARP>
 __device__ __forceinline__ double bsum(double v, double *sh)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -30,10 +38,11 @@ __device__ __forceinline__ double bsum(double v, double *sh)
     __syncthreads();
     double t = 0.0;
     if (threadIdx.x == 0)
-        for (int q = 0; q < TILE_THREADS / 32; q++) t += sh[q];
+        for (int q = 0; q < NWARP; q++) t += sh[q];
     return t;
 }
 
+template <int NWARP>
 __device__ __forceinline__ double bmax(double v, double *sh)
 {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -42,13 +51,14 @@ __device__ __forceinline__ double bmax(double v, double *sh)
     __syncthreads();
     double t = 0.0;
     if (threadIdx.x == 0)
-        for (int q = 0; q < TILE_THREADS / 32; q++) t = fmax(t, sh[q]);
+        for (int q = 0; q < NWARP; q++) t = fmax(t, sh[q]);
     return t;
 }
 
 // Fixed-order block sum of a double-float per thread: the warp tree in
 // double-float arithmetic (FP32 pipe), then the warps' totals in FP64 by
 // thread 0. Deterministic for a given block size.
+template <int NWARP>
 __device__ __forceinline__ double bsum_ff(ff v, double *sh)
 {
     for (int o = 16; o > 0; o >>= 1) {
@@ -60,10 +70,11 @@ __device__ __forceinline__ double bsum_ff(ff v, double *sh)
     __syncthreads();
     double t = 0.0;
     if (threadIdx.x == 0)
-        for (int q = 0; q < TILE_THREADS / 32; q++) t += sh[q];
+        for (int q = 0; q < NWARP; q++) t += sh[q];
     return t;
 }
 
+template <int NWARP>
 __device__ __forceinline__ double bmax_f(float v, double *sh)
 {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -72,7 +83,7 @@ __device__ __forceinline__ double bmax_f(float v, double *sh)
     __syncthreads();
     double t = 0.0;
     if (threadIdx.x == 0)
-        for (int q = 0; q < TILE_THREADS / 32; q++) t = fmax(t, sh[q]);
+        for (int q = 0; q < NWARP; q++) t = fmax(t, sh[q]);
     return t;
 }
 
@@ -282,7 +293,9 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
     constexpr int RX = TX + 2, RY = TY + 2;   // region = tile + 1-pixel halo
     constexpr int NR = RX * RY;
     constexpr int NS = RX * (TY + 1);         // spring sources: region rows 0..TY
-    constexpr int NW = TILE_THREADS / 32;
+    constexpr int NT = tile_threads<TY, PREC>();
+    constexpr int NW = NT / 32;
+    static_assert(TY % NW == 0, "whole rows per warp");
     constexpr bool FIX = PREC == LSM_PREC_F32 || PREC == LSM_PREC_DF;
     using FT = typename std::conditional<PREC == LSM_PREC_F32, float,
                typename std::conditional<PREC == LSM_PREC_DF, ff, double>::type>::type;
@@ -307,7 +320,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int x0 = bx * TX, y0 = by * TY;
     const int nt = 2 * A.nphase * A.nphase;
-    for (int q = tid; q < nt; q += TILE_THREADS) {
+    for (int q = tid; q < nt; q += NT) {
         if constexpr (FIX)
             sdf[q] = A.tdf[q];
         else
@@ -340,13 +353,13 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
         if (ry < RY)
             load_pixel<PREC, MODE, RX>(A, x0, y0, lane + 1, ry, sx, sy, sxf, syf, sph, smk, over, opx[k], opy[k]);
     }
-    for (int q = tid; q < 2 * RY; q += TILE_THREADS) {
+    for (int q = tid; q < 2 * RY; q += NT) {
         double hx, hy;
         load_pixel<PREC, MODE, RX>(A, x0, y0, (q & 1) ? TX + 1 : 0, q >> 1, sx, sy, sxf, syf, sph, smk, over, hx,
                                    hy);
     }
     if (FIX && over) atomicOr(A.status, 2);
-    for (int e = tid; e < NS; e += TILE_THREADS) snew[e] = 0;
+    for (int e = tid; e < NS; e += NT) snew[e] = 0;
     __syncthreads();
 
     // 2a. forward springs of the owned particles
@@ -366,7 +379,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
     // 2b. springs from halo sources into the tile (also evaluated, with the
     // same result, by the tile that owns their lower endpoint)
     constexpr int NH = 3 * TX + 3 * TY - 2;
-    for (int t = tid; t < NH; t += TILE_THREADS) {
+    for (int t = tid; t < NH; t += NT) {
         int rx, ry, slot;
         if (t < 3 * TX) {  // halo row above the tile, slots 1..3
             slot = 1 + t / TX;
@@ -545,19 +558,19 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
         if (bad) atomicOr(A.status, 1);
         double t0, t1, t2, t3, t4, t5;
         if constexpr (FIX) {  // warp trees on the FP32 pipe
-            t0 = bsum_ff(w_acc, sred);
-            t1 = bsum_ff(u_acc, sred);
-            t2 = bsum_ff(ff{mvx2f, 0.0f}, sred);
-            t3 = bsum_ff(ff{kef, 0.0f}, sred);
-            t4 = bsum_ff(reactf, sred);
-            t5 = bmax_f(resf, sred);
+            t0 = bsum_ff<NW>(w_acc, sred);
+            t1 = bsum_ff<NW>(u_acc, sred);
+            t2 = bsum_ff<NW>(ff{mvx2f, 0.0f}, sred);
+            t3 = bsum_ff<NW>(ff{kef, 0.0f}, sred);
+            t4 = bsum_ff<NW>(reactf, sred);
+            t5 = bmax_f<NW>(resf, sred);
         } else {
-            t0 = bsum(w_acc, sred);
-            t1 = bsum(u_acc, sred);
-            t2 = bsum(mvx2, sred);
-            t3 = bsum(ke, sred);
-            t4 = bsum(react, sred);
-            t5 = bmax(res, sred);
+            t0 = bsum<NW>(w_acc, sred);
+            t1 = bsum<NW>(u_acc, sred);
+            t2 = bsum<NW>(mvx2, sred);
+            t3 = bsum<NW>(ke, sred);
+            t4 = bsum<NW>(react, sred);
+            t5 = bmax<NW>(res, sred);
         }
         if (tid == 0) {
             A.part_s[tile_id] = t0;
