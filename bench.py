@@ -114,10 +114,14 @@ LIMITER = {}
 
 
 def _kernel_tag():
+    """sha1 prefix of the tile kernel's sources (the kernel body lives in the
+    header shared with the batched kernel)."""
     import hashlib
-    path = os.path.join(ROOT, "paper_2201_04565_gb300", "csrc", "tile2d.cu")
-    with open(path, "rb") as f:
-        return hashlib.sha1(f.read()).hexdigest()[:12]
+    h = hashlib.sha1()
+    for name in ("tile2d.cu", "tile_body.cuh", "dfloat.cuh"):
+        with open(os.path.join(ROOT, "paper_2201_04565_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
 
 
 def _build_specimen(lsm, precision, stream):
