@@ -86,7 +86,7 @@ struct BatchCtx {
 // ----------------------------------------------------------------- kernels
 
 template <int TY, int PREC, int MODE, bool SAMPLE>
-__global__ void __launch_bounds__(tile_threads<TY, PREC>())
+__global__ void __launch_bounds__(tile_threads<TY, PREC, SAMPLE>())
 k_tile2d_batch(TileArgs base, const BatchTile *__restrict__ tiles, int64_t t0, int64_t t1,
                const SpecDesc *__restrict__ specs, double *X0, double *X1, double *V0, double *V1, double *VOBS,
                const uint8_t *PH, uint8_t *MASK, long long *BRK, unsigned long long *fb,
@@ -378,7 +378,7 @@ static cudaError_t launch_bt(BatchCtx &b, int64_t t0, int64_t t1)
     const int64_t ntl = t1 - t0;
     if (ntl <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)(b.grid > 0 && b.grid < ntl ? b.grid : ntl);
-    kern<<<grid, tile_threads<TY, PREC>(), smem, b.stream>>>(batch_base_args(b), b.tiles, t0, t1, b.specs, b.X[0], b.X[1],
+    kern<<<grid, tile_threads<TY, PREC, SAMPLE>(), smem, b.stream>>>(batch_base_args(b), b.tiles, t0, t1, b.specs, b.X[0], b.X[1],
                                                  b.VH[0], b.VH[1], b.VOBS, b.PH, b.MASK, b.BRK, b.fb, b.nb);
     b.launches += 1;
     return cudaGetLastError();

@@ -28,7 +28,7 @@
 namespace lsm {
 
 template <int TX, int TY, int PREC, int MODE, bool SAMPLE>
-__global__ void __launch_bounds__(tile_threads<TY, PREC>())
+__global__ void __launch_bounds__(tile_threads<TY, PREC, SAMPLE>())
 k_tile2d(TileArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -155,7 +155,7 @@ static cudaError_t launch_tile(Ctx &c, TileArgs A)
         configured = true;
     }
     dim3 grid((c.h.nx + TILE_X - 1) / TILE_X, (c.h.ny + TILE_Y - 1) / TILE_Y);
-    kern<<<grid, tile_threads<TILE_Y, PREC>(), smem, c.stream>>>(A);
+    kern<<<grid, tile_threads<TILE_Y, PREC, SAMPLE>(), smem, c.stream>>>(A);
     return cudaSuccess;
 }
 

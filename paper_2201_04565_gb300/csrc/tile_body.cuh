@@ -16,12 +16,13 @@ namespace lsm {
 namespace {
 
 // Threads per CTA for a tile of height TY: one warp per tile row, up to 16
-// warps in the double-float mode (measured best: occupancy is limited by
-// registers and shared memory) and 8 otherwise (fewer warps per barrier).
-template <int TY, int PREC>
+// warps for the double-float time step (measured best: occupancy is limited
+// by registers and shared memory) and 8 otherwise (fewer warps per barrier;
+// the sample step needs more registers).
+template <int TY, int PREC, bool SAMPLE>
 __host__ __device__ constexpr int tile_threads()
 {
-    return 32 * (TY < (PREC == LSM_PREC_DF ? 16 : 8) ? TY : (PREC == LSM_PREC_DF ? 16 : 8));
+    return 32 * (TY < (PREC == LSM_PREC_DF && !SAMPLE ? 16 : 8) ? TY : (PREC == LSM_PREC_DF && !SAMPLE ? 16 : 8));
 }
 
 __device__ __forceinline__ double ad(double a, double b) { return __dadd_rn(a, b); }
@@ -293,7 +294,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
     constexpr int RX = TX + 2, RY = TY + 2;   // region = tile + 1-pixel halo
     constexpr int NR = RX * RY;
     constexpr int NS = RX * (TY + 1);         // spring sources: region rows 0..TY
-    constexpr int NT = tile_threads<TY, PREC>();
+    constexpr int NT = tile_threads<TY, PREC, SAMPLE>();
     constexpr int NW = NT / 32;
     static_assert(TY % NW == 0, "whole rows per warp");
     constexpr bool FIX = PREC == LSM_PREC_F32 || PREC == LSM_PREC_DF;
