@@ -106,11 +106,19 @@ def algorithmic_bytes(n, m, dim):
 # 2048 x 2048 workload, from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by precision mode, with the sha1 prefix of the kernel source it was
 # taken on; once the kernel changes, traffic reports null until re-measured.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/k_tile2d_df64_2d_2048_two_phase.md: 142.7 MB read + 96.6 MB written
+    "df64": (239.29e6, "9805704431aa"),
+}
 
 # Binding unit of each mode's time-step kernel, from ncu on the same workload
 # (see the profile summaries), for the roofline's "limiter" note.
-LIMITER = {}
+LIMITER = {
+    "df64": "instruction issue (ncu: 74% of issue slots busy, FP64 pipe 32%, DRAM 16% of peak)",
+    "f32": "instruction issue and latency (ncu: 70% issue, LSU 47%, DRAM 27% of peak)",
+    "fast64": "FP64 pipe (ncu: 86% busy)",
+    "exact64": "FP64 pipe (ncu: 88% busy; correctly rounded sqrt and divide)",
+}
 
 
 def _kernel_tag():
@@ -339,8 +347,8 @@ def cpu_baseline():
     """The oracle on all host cores (threaded spring pass), with the
     single-threaded figure beside it."""
     cores = os.cpu_count() or 1
-    out = run_oracle_sample(budget_s=10.0, threads=cores)
-    one = run_oracle_sample(budget_s=8.0, threads=1)
+    out = run_oracle_sample(budget_s=15.0, threads=cores)
+    one = run_oracle_sample(budget_s=10.0, threads=1)
     out["single_thread"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
     return out
 
