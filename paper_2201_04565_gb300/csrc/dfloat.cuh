@@ -247,6 +247,37 @@ __device__ __forceinline__ ff ff_rsqrt(ff a)
     return fast_two_sum(y0, __fmul_rn(__fmul_rn(0.5f, y0), rho));
 }
 
+// a^2 + b^2 for double-floats a, b: exact float squares of the high parts
+// (TwoProd), one TwoSum, and the small terms in float (about 2^-46 relative).
+__device__ __forceinline__ ff ff_norm2(ff a, ff b)
+{
+    const float p1 = __fmul_rn(a.hi, a.hi), e1 = __fmaf_rn(a.hi, a.hi, -p1);
+    const float p2 = __fmul_rn(b.hi, b.hi), e2 = __fmaf_rn(b.hi, b.hi, -p2);
+    const ff s = two_sum(p1, p2);
+    float l = __fmaf_rn(__fadd_rn(a.hi, a.hi), a.lo, __fadd_rn(e1, e2));
+    l = __fmaf_rn(__fadd_rn(b.hi, b.hi), b.lo, l);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, l));
+}
+
+// The spring factor g = 1 - r0 / r from r^2 (double-float) and r0, with
+// y = 1/r to about 2^-46: the float reciprocal square root y0 (one float
+// Newton step), rho = 1 - r^2 y0^2 formed in double-float arithmetic, and
+// r0 / r = r0 y0 (1 + rho / 2). The product r0.hi y0 is exact (TwoProd), so
+// 1 - r0 y0 is exact up to the small terms summed in float. *y receives 1/r.
+__device__ __forceinline__ ff ff_spring_g(ff r2, ff r0, ff *y)
+{
+    float y0 = rsqrtf(r2.hi);
+    y0 = __fmul_rn(y0, __fmaf_rn(-0.5f * r2.hi, __fmul_rn(y0, y0), 1.5f));
+    const ff t = ff_mul(r2, two_prod(y0, y0));
+    const float rho = __fsub_rn(__fsub_rn(1.0f, t.hi), t.lo);
+    const ff p = two_prod(r0.hi, y0);
+    float t2 = __fmaf_rn(-r0.lo, y0, -p.lo);
+    t2 = __fmaf_rn(-0.5f * p.hi, rho, t2);
+    const ff s = two_sum(1.0f, -p.hi);
+    if (y) *y = fast_two_sum(y0, __fmul_rn(__fmul_rn(0.5f, y0), rho));
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, t2));
+}
+
 // 1 - a for a double-float a (exact TwoSum on the high part).
 __device__ __forceinline__ ff ff_one_minus(ff a)
 {

@@ -209,12 +209,12 @@ __device__ __forceinline__ void eval_spring(const TileArgs &A, int rp, int rq, i
                 // FP64's k (r - r0) / r, resolved at 2^-46 instead of 2^-53
                 const ff dxf = fix_to_ff_i2f2(sxf[rq] - sxf[rp], A.p48, A.p24, A.p0);
                 const ff dyf = fix_to_ff_i2f2(syf[rq] - syf[rp], A.p48, A.p24, A.p0);
-                const ff r2 = ff_add_sloppy(ff_sqr(dxf), ff_sqr(dyf));
+                const ff r2 = ff_norm2(dxf, dyf);
                 if (MODE == T_STEP && ff_gt(r2, t.rc2)) {
                     brk_now = true;
                 } else {
-                    const ff y = ff_rsqrt(r2);
-                    const ff g = ff_one_minus(ff_mul(t.r0, y));
+                    ff y;
+                    const ff g = ff_spring_g(r2, t.r0, SAMPLE && OWNER ? &y : nullptr);
                     const ff c = ff_mul(t.k, g);
                     fx = ff_mul(c, dxf);
                     fy = ff_mul(c, dyf);
