@@ -45,8 +45,12 @@ lsm_status device_status(Ctx *c)
 
 lsm_status finish_build(lsm_ctx *c, void *stream, lsm_ctx **out, int path = 0)
 {
-    c->tile = path != 1 && c->h.dim == 2 && c->h.nx > 0 && c->h.lattice == 0 && c->h.nphase >= 1 &&
-              c->h.nphase <= 8;
+    // 2D square-lattice images: the fused tile kernel in every mode; 3D images:
+    // the voxel tile kernel in the fixed-point modes (the FP64 modes stay on
+    // the spring-list kernels, see tile3d.cu)
+    const bool fixmode = c->h.precision == LSM_PREC_F32 || c->h.precision == LSM_PREC_DF;
+    c->tile = path != 1 && c->h.nx > 0 && c->h.lattice == 0 && c->h.nphase >= 1 && c->h.nphase <= 8 &&
+              (c->h.dim == 2 || (c->h.dim == 3 && fixmode));
     if (stream) {
         c->stream = (cudaStream_t)stream;
     } else {
@@ -336,13 +340,13 @@ lsm_status lsm_get_state(lsm_ctx *c, double *x, double *v)
     const size_t bytes = (size_t)c->dim * c->n * sizeof(double);
     cudaError_t e = cudaSuccess;
     if (c->tile) {
-        std::vector<double> gx(x ? 2 * c->tnp : 0), gv(v ? 2 * c->tnp : 0);
-        if (x) e = cudaMemcpyAsync(gx.data(), c->tx[c->tcur], 2 * c->tnp * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        std::vector<double> gx(x ? (size_t)c->dim * c->tnp : 0), gv(v ? (size_t)c->dim * c->tnp : 0);
+        if (x) e = cudaMemcpyAsync(gx.data(), c->tx[c->tcur], (size_t)c->dim * c->tnp * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess && v)
-            e = cudaMemcpyAsync(gv.data(), c->tvobs, 2 * c->tnp * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+            e = cudaMemcpyAsync(gv.data(), c->tvobs, (size_t)c->dim * c->tnp * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "get_state");
-        for (int cc = 0; cc < 2; cc++)
+        for (int cc = 0; cc < c->dim; cc++)
             for (int64_t p = 0; p < c->n; p++) {
                 const int64_t g = c->h.pix[p];
                 if (x) x[cc * c->n + p] = gx[cc * c->tnp + g];
@@ -365,22 +369,22 @@ lsm_status lsm_set_state(lsm_ctx *c, const double *x, const double *v)
     if (c->tile) {
         // scatter onto the pixel grid (void pixels keep their placeholder)
         std::vector<double> gx, gv;
-        if (x) gx.resize(2 * c->tnp);
-        if (v) gv.resize(2 * c->tnp);
-        if (x) e = cudaMemcpyAsync(gx.data(), c->tx[c->tcur], 2 * c->tnp * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (x) gx.resize((size_t)c->dim * c->tnp);
+        if (v) gv.resize((size_t)c->dim * c->tnp);
+        if (x) e = cudaMemcpyAsync(gx.data(), c->tx[c->tcur], (size_t)c->dim * c->tnp * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess && v)
-            e = cudaMemcpyAsync(gv.data(), c->tvobs, 2 * c->tnp * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+            e = cudaMemcpyAsync(gv.data(), c->tvobs, (size_t)c->dim * c->tnp * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
-        for (int cc = 0; cc < 2; cc++)
+        for (int cc = 0; cc < c->dim; cc++)
             for (int64_t p = 0; p < c->n; p++) {
                 const int64_t g = c->h.pix[p];
                 if (x) gx[cc * c->tnp + g] = x[cc * c->n + p];
                 if (v) gv[cc * c->tnp + g] = v[cc * c->n + p];
             }
-        if (x) e = cudaMemcpyAsync(c->tx[c->tcur], gx.data(), 2 * c->tnp * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (x) e = cudaMemcpyAsync(c->tx[c->tcur], gx.data(), (size_t)c->dim * c->tnp * sizeof(double), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess && v)
-            e = cudaMemcpyAsync(c->tvobs, gv.data(), 2 * c->tnp * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+            e = cudaMemcpyAsync(c->tvobs, gv.data(), (size_t)c->dim * c->tnp * sizeof(double), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = lsm::launch_init_accel(*c);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "set_state");

@@ -167,17 +167,18 @@ k_fields(int64_t n, const int64_t *__restrict__ row, const uint32_t *__restrict_
     }
 }
 
-// pixel-grid state of the 2D tile path -> compact particle order
-__global__ void k_fields_compact(int64_t n, int64_t np, const int64_t *__restrict__ pix, const double *__restrict__ gx,
-                                 const double *__restrict__ gv, double *__restrict__ x, double *__restrict__ v)
+// pixel/voxel-grid state of the tile paths -> compact particle order
+__global__ void k_fields_compact(int64_t n, int64_t np, int dim, const int64_t *__restrict__ pix,
+                                 const double *__restrict__ gx, const double *__restrict__ gv, double *__restrict__ x,
+                                 double *__restrict__ v)
 {
     const int64_t p = (int64_t)blockIdx.x * FB + threadIdx.x;
     if (p >= n) return;
     const int64_t g = pix[p];
-    x[p] = gx[g];
-    x[n + p] = gx[np + g];
-    v[p] = gv[g];
-    v[n + p] = gv[np + g];
+    for (int c = 0; c < dim; c++) {
+        x[c * n + p] = gx[c * np + g];
+        v[c * n + p] = gv[c * np + g];
+    }
 }
 
 template <typename T>
@@ -233,8 +234,8 @@ cudaError_t fields_compute(Ctx &c, double cell)
             if ((e = up(&c.fstype, h.stype.data(), h.stype.size(), st)) != cudaSuccess) return e;
             if ((e = up(&c.fmass, h.mass.data(), h.mass.size(), st)) != cudaSuccess) return e;
             if ((e = up(&c.fpix, h.pix.data(), h.pix.size(), st)) != cudaSuccess) return e;
-            if ((e = cudaMalloc((void **)&c.fx, (size_t)2 * (n ? n : 1) * sizeof(double))) != cudaSuccess) return e;
-            if ((e = cudaMalloc((void **)&c.fv, (size_t)2 * (n ? n : 1) * sizeof(double))) != cudaSuccess) return e;
+            if ((e = cudaMalloc((void **)&c.fx, (size_t)h.dim * (n ? n : 1) * sizeof(double))) != cudaSuccess) return e;
+            if ((e = cudaMalloc((void **)&c.fv, (size_t)h.dim * (n ? n : 1) * sizeof(double))) != cudaSuccess) return e;
             // the host vectors above must outlive their copies
             if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
         }
@@ -248,7 +249,7 @@ cudaError_t fields_compute(Ctx &c, double cell)
     const uint16_t *stype = c.stype;
     const uint8_t *state = c.state;
     if (c.tile) {
-        k_fields_compact<<<g, FB, 0, st>>>(n, c.tnp, c.fpix, c.tx[c.tcur], c.tvobs, c.fx, c.fv);
+        k_fields_compact<<<g, FB, 0, st>>>(n, c.tnp, h.dim, c.fpix, c.tx[c.tcur], c.tvobs, c.fx, c.fv);
         if ((e = tile_export(c, false)) != cudaSuccess) return e;  // canonical broken flags -> texport
         x = c.fx;
         v = c.fv;

@@ -364,7 +364,8 @@ void free_device(Ctx &c)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     void *tptrs[] = {c.tx[0], c.tx[1], c.tvh[0], c.tvh[1], c.tvobs, c.tph, c.tmask, c.tbrk, c.tmass,
-                     c.tinvm, c.tdf, c.tsbase, c.texport, c.texport_brk, c.xf, c.sdir, c.imass, c.fsx};
+                     c.tinvm, c.tdf, c.tsbase, c.texport, c.texport_brk, c.xf, c.sdir, c.imass, c.fsx,
+                     c.tmask3};
     for (void *p : tptrs)
         if (p) cudaFree(p);
     c.tsbase = nullptr;
@@ -377,6 +378,7 @@ void free_device(Ctx &c)
     c.tx[0] = c.tx[1] = c.tvh[0] = c.tvh[1] = c.tvobs = c.tmass = c.tinvm = nullptr;
     c.tdf = nullptr;
     c.tph = c.tmask = nullptr;
+    c.tmask3 = nullptr;
     c.tbrk = nullptr;
     c.x = c.v = c.a = c.mass = c.Xx = nullptr;
     c.fixm = c.grip = nullptr;
@@ -513,6 +515,10 @@ cudaError_t upload(Ctx &c)
     c.dim = h.dim;
     c.n = h.n;
     c.m = h.m;
+    if (c.tile && c.dim == 3) {
+        LSM_TRY(upload_common(c));
+        return tile3_upload(c);
+    }
     if (c.tile) return upload_tile(c);
     const int64_t n = c.n, m = c.m, dn = (int64_t)h.dim * n;
     c.nblk_s = (m + TPB - 1) / TPB;
@@ -651,7 +657,7 @@ static void enqueue_steps(Ctx &c, int64_t nsteps, bool record)
 
 static cudaError_t enqueue_tile_steps(Ctx &c, int64_t nsteps, bool record)
 {
-    cudaError_t e = tile_enqueue_steps(c, nsteps, c.tcur);
+    cudaError_t e = c.dim == 3 ? tile3_enqueue_steps(c, nsteps, c.tcur) : tile_enqueue_steps(c, nsteps, c.tcur);
     if (e != cudaSuccess) return e;
     if (record)
         reduce(c, c.samples, c.d_nsamples, nsteps);
@@ -697,7 +703,7 @@ cudaError_t launch_steps(Ctx &c, int64_t nsteps, bool record)
 
 cudaError_t launch_init_accel(Ctx &c)
 {
-    if (c.tile) return tile_init_accel(c);
+    if (c.tile) return c.dim == 3 ? tile3_init_accel(c) : tile_init_accel(c);
     if (c.fixcsr) {
         const cudaError_t e = fixcsr_refresh(c);  // positions may have been replaced
         if (e != cudaSuccess) return e;
@@ -715,7 +721,7 @@ cudaError_t launch_init_accel(Ctx &c)
 cudaError_t launch_observe(Ctx &c, DeviceSample *dst)
 {
     if (c.tile) {
-        cudaError_t e = tile_observe(c);
+        cudaError_t e = c.dim == 3 ? tile3_observe(c) : tile_observe(c);
         if (e != cudaSuccess) return e;
         reduce(c, dst, nullptr, 0);
         return cudaGetLastError();

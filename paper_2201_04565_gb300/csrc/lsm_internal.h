@@ -128,6 +128,7 @@ struct Ctx {
     double *tvh[2] = {nullptr, nullptr};  // [2][tnp] half-step velocities
     double *tvobs = nullptr;              // [2][tnp] full-step velocities (queries)
     uint8_t *tph = nullptr, *tmask = nullptr;
+    uint16_t *tmask3 = nullptr;           // 3D tile path: 9 broken flags per voxel
     long long *tbrk = nullptr;            // [4][tnp]
     double *tmass = nullptr;              // per phase
     double *tinvm = nullptr;              // per phase: 1 - dt g/m, dt/m, 1 - dt/2 g/m, dt/2 / m
@@ -189,6 +190,14 @@ void gather_fix(Ctx &c);
 // fields.cu
 cudaError_t fields_compute(Ctx &c, double cell);  // -> fout (device), stream ordered
 void fields_free(Ctx &c);
+
+// tile3d.cu: 3D voxel lattices in the fixed-point modes (state on the voxel grid)
+cudaError_t tile3_upload(Ctx &c);
+cudaError_t tile3_enqueue_steps(Ctx &c, int64_t nsteps, int start_buf);
+cudaError_t tile3_init_accel(Ctx &c);
+cudaError_t tile3_observe(Ctx &c);
+cudaError_t tile3_export(Ctx &c, bool steps);
+int64_t tile3_count(const Ctx &c);
 
 // tile2d.cu
 cudaError_t tile_enqueue_steps(Ctx &c, int64_t nsteps, int start_buf);

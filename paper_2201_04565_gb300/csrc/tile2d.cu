@@ -83,6 +83,7 @@ __global__ void k_tile_export(int nx, int ny, int64_t np, const uint8_t *__restr
 
 cudaError_t tile_export(Ctx &c, bool steps)
 {
+    if (c.dim == 3) return tile3_export(c, steps);
     if (c.m == 0) return cudaSuccess;
     if (!c.texport) {
         cudaError_t e = cudaMalloc((void **)&c.texport, c.m);

@@ -156,14 +156,16 @@ def test_c0_f32_force_error_is_bounded(oracle_mod, L, path):
     assert sg[-1]["sigma_vir"] == pytest.approx(so[-1]["sigma_vir"], rel=1e-3)
 
 
-@pytest.mark.parametrize("precision", ["exact64", "fast64", "df64", "f32"])
-def test_3d_foam_parity(oracle_mod, L, precision):
-    """3D foam under compression on the spring-list kernels; df64 and f32 run
-    the fixed-point spring vectors (the 2D tile kernel's arithmetic) there."""
+@pytest.mark.parametrize("precision,path", [("exact64", 0), ("fast64", 0), ("df64", 0), ("f32", 0),
+                                            ("df64", 1), ("f32", 1)])
+def test_3d_foam_parity(oracle_mod, L, precision, path):
+    """3D foam under compression. exact64/fast64 run the spring-list kernels;
+    df64/f32 run the voxel tile kernel (path 0) or the spring-list kernels
+    with the same fixed-point spring vectors (path 1)."""
     from gen.images import foam_volume
     img = foam_volume(20, 2.0, 0.45, seed=9)
     mats = one_phase_materials(1.0, 0.04)
-    o, g = _pair(oracle_mod, L, img, mats, precision=precision, grip_mode=1)
+    o, g = _pair(oracle_mod, L, img, mats, precision=precision, grip_mode=1, path=path)
     _run_schedule(o, g, 10, 20, -2e-3)
     xg, vg = g.state()
     xo, vo, _ = o.state()
@@ -370,3 +372,35 @@ def test_triangular_fields_match_oracle(oracle_mod, L):
     ok = ~np.isnan(eo)
     assert np.abs(sg - so).max() <= 1e-12 * np.abs(so).max()
     assert np.abs(eg[ok] - eo[ok]).max() <= 1e-12 * np.abs(eo[ok]).max()
+
+
+def test_3d_tile_kernel_through_fracture(oracle_mod, L):
+    """The voxel tile kernel (df64) against the oracle on a ragged volume
+    (sizes not multiples of the 32 x 4 x 4 block) stretched through
+    fracture: positions at the 1e-10 bar, identical broken set, break steps
+    and first break, stress before the first break within 1e-6, and the
+    per-particle fields within 1e-8 of the largest entry."""
+    from gen.images import foam_volume
+    img = foam_volume(22, 1.5, 0.55, seed=13)[:, :19, :]  # 22 x 19 x 22, ragged in every axis
+    img = np.ascontiguousarray(img[:18])
+    mats = one_phase_materials(1.0, 0.03)
+    o, g = _pair(oracle_mod, L, img, mats, precision="df64")
+    so = _run_schedule(o, g, 20, 20, 3e-3)
+    xg, _ = g.state()
+    xo, _, _ = o.state()
+    assert _rel(xg, xo) <= 1e-10
+    mo, bo, fo = o.broken()
+    mg, fg = g.broken()
+    assert mo.sum() > 0
+    assert np.array_equal(mg, mo) and fg == fo
+    assert np.array_equal(g.break_steps(), bo)
+    sg = g.samples()
+    first = next((i for i, s_ in enumerate(so) if s_["n_broken"] > 0), len(so))
+    for a_, b_ in zip(sg[:first], so[:first]):
+        assert a_["sigma_vir"] == pytest.approx(b_["sigma_vir"], rel=1e-6)
+    st_o, sn_o = o.fields(1.0)
+    st_g, sn_g = g.fields()
+    ok = ~np.isnan(sn_o)
+    assert np.array_equal(np.isnan(sn_g), np.isnan(sn_o))
+    assert np.abs(st_g - st_o).max() <= 1e-8 * np.abs(st_o).max()
+    assert np.abs(sn_g[ok] - sn_o[ok]).max() <= 1e-8 * np.abs(sn_o[ok]).max()
