@@ -262,7 +262,7 @@ def run_gpu(args, rank, world):
     return out
 
 
-def run_batch512(args, plain_every=8):
+def run_batch512(args, rank=0, world=1, plain_every=8):
     """Uneven batch of 512 two-phase specimens (sides 32..512 px), tension to
     8% in 80 increments of 20 steps. Batched arm: every specimen in one
     lsm_batch (one tile-kernel launch per time step, graph-captured, autotuned
@@ -270,14 +270,22 @@ def run_batch512(args, plain_every=8):
     after another through the same library (every plain_every-th specimen is
     run, and its time is scaled by the spring count of the whole batch).
     Build time is excluded from both arms; per-increment host work is
-    included. Returns curves/s for both."""
+    included. Returns curves/s for both.
+
+    Under torchrun the specimens are sharded across ranks (longest first to
+    the lightest rank, by pixel count; no collective on the data path), each
+    rank steps its share in its own batch, and the time is the maximum over
+    ranks; the plain arm then runs on rank 0's share only."""
     import torch
     from gen.images import batch_specimens
     from paper_2201_04565_gb300 import batch as bmod
     from paper_2201_04565_gb300 import lsm
+    from paper_2201_04565_gb300 import shard
 
     prec = args.precision
-    imgs = batch_specimens(512)
+    imgs_all = batch_specimens(512)
+    share = shard.my_share([im.size for im in imgs_all], rank, world)
+    imgs = [imgs_all[q] for q in share]
     k, e, m = two_phase_materials()
     incs, nst = 80, 20
     stream = torch.cuda.Stream()
@@ -285,12 +293,15 @@ def run_batch512(args, plain_every=8):
     msum = sum(mm for _, mm in bt.sizes)
     tune = bt.autotune(4)
     torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as td
+        td.barrier()
     t0 = time.perf_counter()
     for i in range(1, incs + 1):
         bt.apply_strain(i * 1e-3)
         bt.step(nst)
     bt.synchronize()
-    t_batch = time.perf_counter() - t0
+    t_batch = shard.max_over_ranks(time.perf_counter() - t0)
     launches = bt.counters()[1]
     bt.close()
     sub = list(range(0, len(imgs), plain_every))
@@ -308,14 +319,16 @@ def run_batch512(args, plain_every=8):
         sp.synchronize()
         t_plain += time.perf_counter() - t0
         sp.close()
-    t_plain_all = t_plain * msum / m_sub
-    return {"workload": "batch512_two_phase", "specimens": len(imgs), "springs_total": msum,
+    t_plain_all = t_plain * msum / m_sub * world  # rank 0's share, scaled to the whole batch on one GPU
+    return {"workload": "batch512_two_phase", "specimens": len(imgs_all), "n_gpus": world,
+            "scaling": "strong" if world > 1 else "weak", "springs_total_rank0": msum,
             "increments": incs, "time_steps_per_increment": nst, "precision": prec,
-            "batched": {"curves_per_s": len(imgs) / t_batch, "seconds": t_batch,
-                        "spring_updates_per_s": msum * incs * nst / t_batch, "schedule": tune,
-                        "kernel_launches": launches},
-            "plain": {"curves_per_s": len(imgs) / t_plain_all, "seconds_extrapolated": t_plain_all,
-                      "sample": "%d of %d specimens run, time scaled by spring count" % (len(sub), len(imgs))},
+            "batched": {"curves_per_s": len(imgs_all) / t_batch, "seconds": t_batch,
+                        "spring_updates_per_s_rank0": msum * incs * nst / t_batch, "schedule_rank0": tune,
+                        "kernel_launches_rank0": launches},
+            "plain": {"curves_per_s": len(imgs_all) / t_plain_all, "seconds_extrapolated": t_plain_all,
+                      "sample": "%d of rank 0's %d specimens run, time scaled by spring count%s"
+                                % (len(sub), len(imgs), " and by the rank count" if world > 1 else "")},
             "speedup": t_plain_all / t_batch}
 
 
@@ -434,18 +447,27 @@ def main():
         print(json.dumps(out))
         return 0
 
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        if torch.cuda.is_available():
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        td.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     if args.workload == "batch512":
+        res = run_batch512(args, rank, world)
         if rank == 0:
-            print(json.dumps(run_batch512(args)))
+            print(json.dumps(res))
+        if world > 1:
+            import torch.distributed as td
+            td.destroy_process_group()
         return 0
     if args.workload == "foam256":
         if rank == 0:
             print(json.dumps(run_foam256(args)))
+        if world > 1:
+            import torch.distributed as td
+            td.destroy_process_group()
         return 0
-    if world > 1:
-        import torch
-        import torch.distributed as td
-        td.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     out = run_gpu(args, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
