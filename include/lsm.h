@@ -68,8 +68,9 @@ typedef enum {
  *      double-float arithmetic (pairs of floats, 48 significant bits), so
  *      forces carry about 1e-14 relative error while the FP64 pipe only does
  *      the integration. For image builds DF and F32 run on the fused 2D tile
- *      kernel or, for 3D and path 1, on the spring-list kernels with the same
- *      fixed-point spring vectors. Network builds have no lattice vectors:
+ *      kernel, on the 3D voxel tile kernel, or (path 1, triangular packing)
+ *      on the spring-list kernels with the same fixed-point spring vectors.
+ *      Network builds have no lattice vectors:
  *      there F32 forms the spring vector in double and DF runs as
  *      LSM_PREC_FAST64. */
 enum { LSM_PREC_EXACT64 = 0, LSM_PREC_FAST64 = 1, LSM_PREC_F32 = 2, LSM_PREC_DF = 3 };
@@ -96,8 +97,9 @@ enum { LSM_PREC_EXACT64 = 0, LSM_PREC_FAST64 = 1, LSM_PREC_F32 = 2, LSM_PREC_DF 
  *               about the specimen centre, then sets the grips;
  *               1 = only the grips move.
  *  precision    LSM_PREC_* (see above).
- *  path         0 = automatic (2D images with up to 8 phases run the fused
- *               tile kernel, everything else the general spring-list
+ *  path         0 = automatic (square-lattice images with up to 8 phases
+ *               run the fused tile kernels: every mode in 2D, the F32 and DF
+ *               modes in 3D; everything else runs the general spring-list
  *               kernels); 1 = always the general spring-list kernels.
  *  stream       cudaStream_t to order work on (NULL = the library creates one).
  *  lattice      0 = square (2D) / cubic (3D) lattice as above; 1 = the

@@ -404,3 +404,23 @@ def test_3d_tile_kernel_through_fracture(oracle_mod, L):
     assert np.array_equal(np.isnan(sn_g), np.isnan(sn_o))
     assert np.abs(st_g - st_o).max() <= 1e-8 * np.abs(st_o).max()
     assert np.abs(sn_g[ok] - sn_o[ok]).max() <= 1e-8 * np.abs(sn_o[ok]).max()
+
+
+@pytest.mark.parametrize("a,grip_mode,precision", [(1.3, 0, "df64"), (0.5, 1, "f32")])
+def test_3d_tile_kernel_spacing_and_grips(oracle_mod, L, a, grip_mode, precision):
+    """The voxel tile kernel with a non-dyadic (1.3) and a dyadic (0.5)
+    lattice spacing, roller and clamped grips, tension: df64 at the 1e-10 bar
+    with the same broken set, f32 within its stated bound."""
+    from gen.images import foam_volume
+    img = foam_volume(14, 1.5, 0.6, seed=17)
+    mats = one_phase_materials(1.0, 0.05)
+    o, g = _pair(oracle_mod, L, img, mats, precision=precision, grip_mode=grip_mode, a=a)
+    _run_schedule(o, g, 10, 20, 4e-3)
+    xg, _ = g.state()
+    xo, _, _ = o.state()
+    if precision == "f32":
+        X = o.topology()["X"]
+        assert np.abs(xg - xo).max() / np.abs(xo - X).max() < 1e-3
+        return
+    assert _rel(xg, xo) <= 1e-10
+    assert np.array_equal(g.broken()[0], o.broken()[0])
