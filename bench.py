@@ -111,6 +111,13 @@ NCU_TRAFFIC = {
     "df64": (239.29e6, "9805704431aa"),
 }
 
+# Warp instructions executed by one time-step launch (ncu smsp__inst_executed.sum,
+# same workload and kernel tag as NCU_TRAFFIC): with the issue peak of the
+# part (152 SMs x 4 schedulers x 1 warp instruction per cycle at the SM clock)
+# this gives the instruction-issue roofline, the one the fixed-point modes
+# are bound by.
+NCU_INSTRUCTIONS = {}
+
 # Binding unit of each mode's time-step kernel, from ncu on the same workload
 # (see the profile summaries), for the roofline's "limiter" note.
 LIMITER = {
@@ -130,6 +137,22 @@ def _kernel_tag():
         with open(os.path.join(ROOT, "paper_2201_04565_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
+
+
+def _issue_roofline(precision, launch_ms, clk):
+    """Issue rate of the time-step kernel against the part's issue peak
+    (152 SMs x 4 warp schedulers x one warp instruction per cycle at the SM
+    clock seen during the run), from the ncu instruction count of the same
+    kernel source; None when no count matches the current source."""
+    if precision not in NCU_INSTRUCTIONS or NCU_INSTRUCTIONS[precision][1] != _kernel_tag():
+        return None
+    inst = NCU_INSTRUCTIONS[precision][0]
+    mhz = (clk or {}).get("sm_mhz") or 2070.0
+    peak = 152 * 4 * mhz * 1e6
+    achieved = inst / (launch_ms * 1e-3)
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "warp instructions/s",
+            "frac": achieved / peak, "instructions_per_launch": inst,
+            "peak_source": "152 SMs x 4 schedulers x 1 warp instruction/cycle x %.0f MHz (sampled)" % mhz}
 
 
 def _build_specimen(lsm, precision, stream):
@@ -238,6 +261,7 @@ def run_gpu(args, rank, world):
                      "algorithmic_bytes_per_launch": algb, "launch_ms": per_step_ms,
                      "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
                      "limiter": LIMITER.get(args.precision)},
+        "issue_roofline": _issue_roofline(args.precision, per_step_ms, clk),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8, "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(launches),
         "clocks": clk,
