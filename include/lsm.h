@@ -244,6 +244,18 @@ lsm_status lsm_topology(lsm_ctx *ctx, int32_t *si, int32_t *sj, double *k, doubl
  * recorded sample; the sample history is unchanged). Synchronises. */
 lsm_status lsm_observe(lsm_ctx *ctx, lsm_sample *out);
 
+/* Constant strain-rate loading (Section 3.1: the boundary particles are
+ * displaced apart at a fixed engineering strain rate, every time step).
+ * From the next lsm_step on, the time step that completes step count s
+ * first prescribes the grip components to X + eps (X - xc) with zero
+ * velocity, eps = eps_set + (s - s_set) (rate dt) (eps_set, s_set: the
+ * applied strain and the step count when the rate was set, or at the last
+ * lsm_apply_strain), then advances as usual; only the grips move. rate = 0
+ * stops the ramp (the strain stays where it is). Samples report the applied
+ * strain. Not available on batched contexts. Errors: LSM_EINVAL for a null
+ * context or a non-finite rate. */
+lsm_status lsm_set_strain_rate(lsm_ctx *ctx, double rate);
+
 /* Per-particle fields of the current state (Section 3.2, Eqs. 7-8), for
  * post-processing such as the paper's stress and strain maps.
  *   stress  host, [ncomp][n] (ncomp = 3 in 2D: xx, yy, xy; 6 in 3D: xx, yy,

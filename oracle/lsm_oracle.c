@@ -74,6 +74,9 @@ typedef struct orc {
     double dt, gamma, xc, omega, grip_area, eps;
     int load_mode;
     int64_t step, first_break;
+    int rate_on;               /* constant strain-rate loading (orc_set_strain_rate) */
+    double rate_eps0, rate_dt; /* strain when the rate was set, rate * dt */
+    int64_t rate_step0;        /* step count when the rate was set */
     int nthreads;              /* > 1: the threaded spring pass below */
     int64_t *row, *inc;        /* [n+1], [2m]: springs of each particle, ascending, (s << 1) | upper */
     double *fs;                /* [dim*m] force of each spring on its lower endpoint */
@@ -613,6 +616,20 @@ void orc_step(orc *o, int64_t nsteps)
     const int64_t dn = (int64_t)o->dim * o->n;
     const double dt = o->dt, hdt = 0.5 * o->dt;
     for (int64_t t = 0; t < nsteps; t++) {
+        /* Constant strain rate (Section 3.1: the boundary particles are
+         * displaced apart at a fixed strain rate): the grips take the strain
+         * of the step being computed, eps0 + (steps since the rate was set)
+         * rate dt, before the positions advance; only the grips move. */
+        if (o->rate_on) {
+            const double eps = o->rate_eps0 + (double)(o->step + 1 - o->rate_step0) * o->rate_dt;
+            for (int64_t p = 0; p < o->n; p++) {
+                if (!o->fix[p]) continue;
+                o->x[p] = o->X[p] + eps * (o->X[p] - o->xc);
+                o->v[p] = 0.0;
+                o->a[p] = 0.0;
+            }
+            o->eps = eps;
+        }
         /* Eq. 3 via the half-step velocity: vh = v + dt/2 a; x += dt vh.
          * o->v holds vh until the end of the step. */
 #ifdef _OPENMP
@@ -658,6 +675,19 @@ void orc_apply_strain(orc *o, double eps_new)
         o->a[p] = 0.0;
     }
     o->eps = eps_new;
+    if (o->rate_on) { /* the rate continues from the new strain */
+        o->rate_eps0 = eps_new;
+        o->rate_step0 = o->step;
+    }
+}
+
+/* Constant strain-rate loading from the next step on (rate 0 stops it). */
+void orc_set_strain_rate(orc *o, double rate)
+{
+    o->rate_on = rate != 0.0;
+    o->rate_eps0 = o->eps;
+    o->rate_step0 = o->step;
+    o->rate_dt = rate * o->dt;
 }
 
 /* Observables of the current state:

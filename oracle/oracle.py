@@ -66,6 +66,7 @@ def _load():
     lib.orc_set_threads.restype = I
     lib.orc_set_threads.argtypes = [P, I]
     lib.orc_fields.argtypes = [P, D, P, P]
+    lib.orc_set_strain_rate.argtypes = [P, D]
     _lib = lib
     return lib
 
@@ -189,6 +190,10 @@ class Oracle:
 
     def apply_strain(self, eps: float):
         self._lib.orc_apply_strain(self._h, float(eps))
+
+    def set_strain_rate(self, rate: float):
+        """Grips move every step at this engineering strain rate (0 stops)."""
+        self._lib.orc_set_strain_rate(self._h, float(rate))
 
     def observe(self):
         out = np.empty(8)

@@ -186,6 +186,20 @@ lsm_status lsm_sizes(lsm_ctx *c, int64_t *n, int64_t *m, int32_t *dim)
     return LSM_OK;
 }
 
+// Host mirror of the applied strain under a constant strain rate (the same
+// operations as the device: eps0 + (s - s0) rdt).
+static void rate_eps_sync(lsm_ctx *c)
+{
+    if (c->rate_on) c->eps = c->rate_eps0 + (double)(c->steps - c->rate_step0) * c->rate_dt;
+}
+
+// Graphs bake the kernel arguments; drop them when the loading changes.
+static void drop_graphs(lsm_ctx *c)
+{
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second);
+    c->graphs.clear();
+}
+
 lsm_status lsm_apply_strain(lsm_ctx *c, double eps)
 {
     if (!c) return fail(nullptr, LSM_EINVAL, "null context");
@@ -194,6 +208,23 @@ lsm_status lsm_apply_strain(lsm_ctx *c, double eps)
     cudaError_t e = lsm::launch_apply_strain(*c, c->eps, eps);
     if (e != cudaSuccess) return cuda_fail(c, e, "apply_strain");
     c->eps = eps;
+    if (c->rate_on) {  // the ramp continues from the new strain
+        c->rate_eps0 = eps;
+        c->rate_step0 = c->steps;
+        drop_graphs(c);
+    }
+    return LSM_OK;
+}
+
+lsm_status lsm_set_strain_rate(lsm_ctx *c, double rate)
+{
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    if (!std::isfinite(rate)) return fail(c, LSM_EINVAL, "strain rate must be finite");
+    c->rate_on = rate != 0.0;
+    c->rate_eps0 = c->eps;
+    c->rate_step0 = c->steps;
+    c->rate_dt = rate * c->h.dt;
+    drop_graphs(c);
     return LSM_OK;
 }
 
@@ -208,6 +239,7 @@ lsm_status lsm_step(lsm_ctx *c, int64_t nsteps)
     if (e != cudaSuccess) return cuda_fail(c, e, "step");
     c->nsamples += 1;
     c->steps += nsteps;
+    rate_eps_sync(c);
     return LSM_OK;
 }
 
@@ -227,6 +259,7 @@ lsm_status lsm_relax(lsm_ctx *c, double tol, int64_t max_steps, int64_t check_ev
         if (e != cudaSuccess) return cuda_fail(c, e, "relax");
         done += nb;
         c->steps += nb;
+        rate_eps_sync(c);
         lsm::DeviceSample smp;
         e = cudaMemcpyAsync(&smp, c->scratch_sample, sizeof(smp), cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);

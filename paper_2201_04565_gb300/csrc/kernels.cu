@@ -25,6 +25,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include "dfloat.cuh"
 #include "lsm_internal.h"
 
 namespace lsm {
@@ -261,6 +262,29 @@ k_drift(int64_t n, double *__restrict__ x, double *__restrict__ v, const double 
     }
 }
 
+// Constant strain rate (Section 3.1): before the spring pass of the step that
+// completes step count s, each grip's x takes the strain eps0 + (s - s0) rdt
+// (the steps completed so far are *d_step; no other kernel of the step runs
+// concurrently). xf: the fixed-point copy, when the path keeps one.
+__global__ void k_rate_grips(int64_t ng, int64_t n, const int32_t *__restrict__ glist, double *__restrict__ x,
+                             const double *__restrict__ Xx, const long long *__restrict__ d_step, double eps0,
+                             long long s0, double rdt, double xc, long long *__restrict__ xf, int S,
+                             int *__restrict__ status)
+{
+    const int64_t q = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (q >= ng) return;
+    const int64_t p = glist[q];
+    const double eps = ad(eps0, ml((double)(*d_step + 1 - s0), rdt));
+    const double X = Xx[p];
+    const double xp = ad(X, ml(eps, sb(X, xc)));
+    x[p] = xp;
+    if (xf) {
+        bool over = false;
+        xf[p] = dbl_to_fix(xp, S, over);
+        if (over) atomicOr(status, 2);
+    }
+}
+
 // Load increment (Sections 2.3, 3.1).
 __global__ void __launch_bounds__(TPB)
 k_apply_strain(int64_t n, double *__restrict__ x, double *__restrict__ v, double *__restrict__ a,
@@ -284,9 +308,10 @@ k_apply_strain(int64_t n, double *__restrict__ x, double *__restrict__ v, double
 // Fold the per-block partials into one sample, in a fixed order.
 __global__ void __launch_bounds__(RED_THREADS)
 k_reduce(const double *__restrict__ ps, int64_t nbs, const double *__restrict__ pp, int64_t nbp,
-         const double *__restrict__ d_eps, const unsigned long long *__restrict__ nbroken,
+         double *d_eps, const unsigned long long *__restrict__ nbroken,
          long long *__restrict__ d_step, long long add_steps, double omega, double grip_area,
-         DeviceSample *__restrict__ dst, long long *__restrict__ counter, int64_t cap)
+         DeviceSample *__restrict__ dst, long long *__restrict__ counter, int64_t cap, int rate_on,
+         double rate_eps0, long long rate_step0, double rate_dt)
 {
     __shared__ double sh[RED_THREADS / 32];
     double acc[6];
@@ -309,6 +334,8 @@ k_reduce(const double *__restrict__ ps, int64_t nbs, const double *__restrict__ 
     const double RES = block_max(acc[5], sh);
     if (threadIdx.x == 0) {
         DeviceSample smp;
+        const long long stp = *d_step + add_steps;
+        if (rate_on) *d_eps = ad(rate_eps0, ml((double)(stp - rate_step0), rate_dt));
         smp.eps = *d_eps;
         smp.sigma_vir = (W - MV) / omega;
         smp.sigma_grip = R / grip_area;
@@ -316,7 +343,6 @@ k_reduce(const double *__restrict__ ps, int64_t nbs, const double *__restrict__ 
         smp.ke = KE;
         smp.residual = RES;
         smp.n_broken = (long long)*nbroken;
-        const long long stp = *d_step + add_steps;
         *d_step = stp;
         smp.step = stp;
         if (counter) {
@@ -365,7 +391,7 @@ void free_device(Ctx &c)
         if (p) cudaFree(p);
     void *tptrs[] = {c.tx[0], c.tx[1], c.tvh[0], c.tvh[1], c.tvobs, c.tph, c.tmask, c.tbrk, c.tmass,
                      c.tinvm, c.tdf, c.tsbase, c.texport, c.texport_brk, c.xf, c.sdir, c.imass, c.fsx,
-                     c.tmask3};
+                     c.tmask3, c.grip_list};
     for (void *p : tptrs)
         if (p) cudaFree(p);
     c.tsbase = nullptr;
@@ -379,6 +405,7 @@ void free_device(Ctx &c)
     c.tdf = nullptr;
     c.tph = c.tmask = nullptr;
     c.tmask3 = nullptr;
+    c.grip_list = nullptr;
     c.tbrk = nullptr;
     c.x = c.v = c.a = c.mass = c.Xx = nullptr;
     c.fixm = c.grip = nullptr;
@@ -578,6 +605,16 @@ cudaError_t upload(Ctx &c)
     LSM_TRY(cudaMemsetAsync(c.fs, 0, (size_t)h.dim * (m ? m : 1) * sizeof(double), st));
     // host vectors above must stay alive until the copies finish
     LSM_TRY(cudaStreamSynchronize(st));
+    {  // particles with a prescribed x (constant strain-rate loading)
+        std::vector<int32_t> gl;
+        for (int64_t p = 0; p < n; p++)
+            if (h.fixm[p] & 1u) gl.push_back((int32_t)p);
+        c.ngrip = (int64_t)gl.size();
+        LSM_TRY(dalloc(&c.grip_list, gl.size()));
+        if (!gl.empty())
+            LSM_TRY(cudaMemcpyAsync(c.grip_list, gl.data(), gl.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        LSM_TRY(cudaStreamSynchronize(st));
+    }
     c.fixcsr = (h.precision == LSM_PREC_F32 || h.precision == LSM_PREC_DF) && !h.offv.empty() &&
                (int64_t)h.sdir.size() == m;
     if (c.fixcsr) LSM_TRY(fixcsr_upload(c));
@@ -630,7 +667,8 @@ static void reduce(Ctx &c, DeviceSample *dst, long long *counter, long long add_
     const int64_t nbp = c.tile ? c.ntiles : c.nblk_p;
     k_reduce<<<1, RED_THREADS, 0, c.stream>>>(c.part_s, nbs, c.part_p, nbp, c.d_eps, c.d_nbroken,
                                               c.d_step, add_steps, c.h.omega, c.h.grip_area, dst,
-                                              counter, c.sample_cap);
+                                              counter, c.sample_cap, c.rate_on, c.rate_eps0, c.rate_step0,
+                                              c.rate_dt);
 }
 
 template <int DIM>
@@ -641,6 +679,10 @@ static void enqueue_steps(Ctx &c, int64_t nsteps, bool record)
     if (c.fixcsr) fixcsr_refresh(c);
     for (int64_t t = 0; t < nsteps; t++) {
         const bool last = t == nsteps - 1;
+        if (c.rate_on && c.ngrip)
+            k_rate_grips<<<grid_of(c.ngrip), TPB, 0, c.stream>>>(c.ngrip, c.n, c.grip_list, c.x, c.Xx, c.d_step,
+                                                                c.rate_eps0, c.rate_step0, c.rate_dt, c.h.xc,
+                                                                c.fixcsr ? c.xf : nullptr, c.fix_S, c.d_status);
         if (last) {
             springs<DIM, true, true>(c);
             gather<DIM, G_END, true>(c);

@@ -157,6 +157,13 @@ struct Ctx {
     int tcur = 0;
     int64_t ntiles = 0;
 
+    // constant strain-rate loading: eps(s) = rate_eps0 + (s - rate_step0) rate_dt
+    bool rate_on = false;
+    double rate_eps0 = 0.0, rate_dt = 0.0;
+    long long rate_step0 = 0;
+    int32_t *grip_list = nullptr;  // spring-list path: particles with a prescribed x
+    int64_t ngrip = 0;
+
     double eps = 0.0;  // host mirror of the applied strain
     int64_t steps = 0; // host mirror of the step counter
     int64_t launches = 0;  // kernels launched (graph nodes included)

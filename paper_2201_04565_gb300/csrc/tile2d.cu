@@ -133,6 +133,11 @@ static TileArgs tile_args(Ctx &c)
     A.gamma = c.h.damping;
     A.a = c.h.a;
     A.grip_mode = c.h.grip_mode;
+    A.rate_on = c.rate_on;
+    A.rate_eps0 = c.rate_eps0;
+    A.rate_dt = c.rate_dt;
+    A.rate_step0 = c.rate_step0;
+    A.xc = c.h.xc;
     A.d_step = c.d_step;
     A.t_off = 0;
     A.first_break = c.d_first_break;

@@ -60,8 +60,11 @@ struct Tile3Args {
     int S;
     long long a_fix;
     float p48, p24, p0;
-    double dt;
+    double dt, a, xc;
     int grip_mode;
+    int rate_on;  // constant strain rate: grips at rate_eps0 + (s - rate_step0) rate_dt
+    double rate_eps0, rate_dt;
+    long long rate_step0;
     const long long *d_step;
     int64_t t_off;
     unsigned long long *first_break, *nbroken;
@@ -73,6 +76,15 @@ struct Tile3Args {
     float oo2[2];   // |o|^2 per shell as floats (F32 mode)
     float fa;       // lattice spacing as a float (F32 mode)
 };
+
+// x of a grip at the strain of the step being computed (constant strain rate)
+__device__ __forceinline__ double rate_grip_x(const Tile3Args &A, int gx)
+{
+    const long long s = *A.d_step + A.t_off + 1 - A.rate_step0;
+    const double eps = __dadd_rn(A.rate_eps0, __dmul_rn((double)s, A.rate_dt));
+    const double X = __dmul_rn((double)gx, A.a);
+    return __dadd_rn(X, __dmul_rn(eps, __dsub_rn(X, A.xc)));
+}
 
 template <int MODE>
 __device__ __forceinline__ void load_voxel(const Tile3Args &A, int x0, int y0, int z0, int rx, int ry, int rz,
@@ -95,6 +107,7 @@ __device__ __forceinline__ void load_voxel(const Tile3Args &A, int x0, int y0, i
                 const bool fixed = grip && (c == 0 || A.grip_mode == 1);
                 if (MODE == T_STEP && !fixed) px[c] = fma(A.dt, A.vh_in[c * A.nv + g], px[c]);
             }
+            if (MODE == T_STEP && grip && A.rate_on) px[0] = rate_grip_x(A, gx);
         }
     }
 #pragma unroll
@@ -286,6 +299,7 @@ k_tile3d(Tile3Args A)
             double xr = A.x_in[q];
             const double vh = MODE == T_INIT ? A.v_obs[q] : A.vh_in[q];
             if (MODE == T_STEP && !fixed) xr = fma(A.dt, vh, xr);
+            if (MODE == T_STEP && c == 0 && grip && A.rate_on) xr = rate_grip_x(A, gx);
             if (MODE == T_STEP) A.x_out[q] = xr;
             if (fixed) {
                 if (MODE == T_STEP) A.vh_out[q] = 0.0;
@@ -383,7 +397,13 @@ Tile3Args tile3_args(Ctx &c)
     A.p24 = ldexpf(1.0f, 24 - c.fix_S);
     A.p0 = ldexpf(1.0f, -c.fix_S);
     A.dt = c.h.dt;
+    A.a = c.h.a;
+    A.xc = c.h.xc;
     A.grip_mode = c.h.grip_mode;
+    A.rate_on = c.rate_on;
+    A.rate_eps0 = c.rate_eps0;
+    A.rate_dt = c.rate_dt;
+    A.rate_step0 = c.rate_step0;
     A.d_step = c.d_step;
     A.first_break = c.d_first_break;
     A.nbroken = c.d_nbroken;

@@ -115,6 +115,9 @@ struct TileArgs {
     float p48, p24, p0;        // 2^(48-S), 2^(24-S), 2^-S
     double dt, hdt, gamma, a;
     int grip_mode;
+    int rate_on;               // constant strain rate: grips at rate_eps0 + (s - rate_step0) rate_dt
+    double rate_eps0, rate_dt, xc;
+    long long rate_step0;
     const long long *d_step;  // steps completed before this graph launch
     int64_t t_off;            // index of this step within the launch
     unsigned long long *first_break, *nbroken;
@@ -260,6 +263,12 @@ __device__ __forceinline__ void load_pixel(const TileArgs &A, int x0, int y0, in
             py = A.x_in[A.np + g];
             if (MODE == T_STEP) {
                 const bool grip = gx == 0 || gx == A.nx - 1;
+                if (grip && A.rate_on) {  // grip x at the strain of this step
+                    const long long s = *A.d_step + A.t_off + 1 - A.rate_step0;
+                    const double eps = ad(A.rate_eps0, ml((double)s, A.rate_dt));
+                    const double X = ml((double)gx, A.a);
+                    px = ad(X, ml(eps, sb(X, A.xc)));
+                }
                 if (!grip) {
                     if constexpr (PREC == LSM_PREC_EXACT64) px = ad(px, ml(A.dt, A.vh_in[g]));
                     else px = fma(A.dt, A.vh_in[g], px);

@@ -79,6 +79,7 @@ SIGNATURES = [
     ("lsm_observe", C.c_int, [_P, C.POINTER(lsm_sample)]),
     ("lsm_synchronize", C.c_int, [_P]),
     ("lsm_fields", C.c_int, [_P, C.c_double, _P, _P]),
+    ("lsm_set_strain_rate", C.c_int, [_P, C.c_double]),
     ("lsm_counters", C.c_int, [_P, _P, _P, _P]),
     ("lsm_spring_energy_static", C.c_int, [_I32, _I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
 ]
@@ -267,6 +268,10 @@ def lsm_observe(h):
     return s.as_dict()
 
 
+def lsm_set_strain_rate(h, rate):
+    _check(load_library().lsm_set_strain_rate(h, float(rate)), h)
+
+
 def lsm_fields(h, cell_volume=0.0, stress=True, strain=True):
     """Per-particle virial stress and Lagrangian strain, each [ncomp, n]
     (2D: xx, yy, xy; 3D: xx, yy, zz, xy, xz, yz); None for an output not asked for."""
@@ -354,6 +359,9 @@ class Specimen:
 
     def observe(self):
         return lsm_observe(self.h)
+
+    def set_strain_rate(self, rate):
+        lsm_set_strain_rate(self.h, rate)
 
     def fields(self, cell_volume=0.0):
         return lsm_fields(self.h, cell_volume)

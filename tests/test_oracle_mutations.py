@@ -43,6 +43,8 @@ MUTATIONS = {
     "triangular row height": ("const double h = a * sqrt(3.0) * 0.5;", "const double h = a * sqrt(2.0) * 0.5;"),
     "triangular neighbour parity": ("jx = (ix) + ((iy) & 1 ? 0 : -1) + ((t) == 2);",
                                     "jx = (ix) + ((iy) & 1 ? -1 : 0) + ((t) == 2);"),
+    "strain-rate step index": ("const double eps = o->rate_eps0 + (double)(o->step + 1 - o->rate_step0) * o->rate_dt;",
+                               "const double eps = o->rate_eps0 + (double)(o->step - o->rate_step0) * o->rate_dt;"),
     "dropped z term": ("if (dim == 3) r2 = r2 + d[2] * d[2];\n        double r = sqrt(r2);\n        double c_s",
                        "double r = sqrt(r2);\n        double c_s"),
 }

@@ -650,3 +650,37 @@ def test_triangular_lattice_modulus_and_poisson_ratio(oracle_mod):
     mid = np.argmin((X[0] - X[0].mean()) ** 2 + (X[1] - X[1].mean()) ** 2)
     assert st_f[0, mid] / eps == pytest.approx(2.0 / math.sqrt(3.0), rel=1e-3)
     assert abs(st_f[1, mid]) < 1e-3 * eps
+
+
+# --------------------------------------------------- constant strain rate
+
+def test_strain_rate_equals_per_step_grip_increments(oracle_mod):
+    """Constant strain-rate loading (grips moved every step) is the same
+    trajectory, bit for bit, as one grips-only load increment of rate dt per
+    step; the applied strain after s steps is eps0 + s rate dt exactly; an
+    increment in between restarts the ramp from the new strain."""
+    img = inclusion_image(20, 14, 2.0, 4.0, 0.3, 9)
+    k, e, m = two_phase_materials()
+    a = oracle_mod.Oracle.from_image(img, k, e, m, load_mode=1)
+    b = oracle_mod.Oracle.from_image(img, k, e, m, load_mode=1)
+    rate, dt = 2e-2, 0.01
+    a.set_strain_rate(rate)
+    eps_b = 0.0
+    for s in range(1, 151):
+        b.apply_strain(0.0 + float(s) * (rate * dt))
+        b.step(1)
+        if s % 50 == 0:
+            a.step(50)
+            assert a.observe()["eps"] == b.observe()["eps"] == float(s) * (rate * dt)
+    xa, va, _ = a.state()
+    xb, vb, _ = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    X = a.topology()["X"]
+    grips = a.topology()["grip"] > 0
+    eps = 150 * (rate * dt)
+    xc = 0.5 * (img.shape[1] - 1)
+    assert np.array_equal(xa[0, grips], X[0, grips] + eps * (X[0, grips] - xc))
+    # an explicit increment restarts the ramp
+    a.apply_strain(0.05)
+    a.step(10)
+    assert a.observe()["eps"] == 0.05 + 10.0 * (rate * dt)
