@@ -442,8 +442,8 @@ def test_strain_rate_loading_matches_oracle(oracle_mod, L, path, precision, dim)
         k, e, m = one_phase_materials(1.0, 0.03)
     o = oracle_mod.Oracle.from_image(img, k, e, m, load_mode=1)
     g = L.Specimen.from_image(img, k, e, m, precision=precision, path=path, load_mode=1)
-    o.set_strain_rate(0.5)
-    g.set_strain_rate(0.5)
+    o.set_strain_rate(0.05)
+    g.set_strain_rate(0.05)
     for _ in range(6):
         o.step(20)
         g.step(20)
@@ -452,7 +452,7 @@ def test_strain_rate_loading_matches_oracle(oracle_mod, L, path, precision, dim)
     for _ in range(6):
         o.step(20)
         g.step(20)
-    assert g.samples()[-1]["eps"] == o.observe()["eps"] == 0.08 + 120.0 * (0.5 * 0.01)
+    assert g.samples()[-1]["eps"] == o.observe()["eps"] == 0.08 + 120.0 * (0.05 * 0.01)
     xg, vg = g.state()
     xo, vo, _ = o.state()
     mo = o.broken()[0]
