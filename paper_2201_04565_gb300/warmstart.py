@@ -84,16 +84,18 @@ class Fields:
 
 
 def save_params(net, path):
-    """Network parameters as BF16 bit patterns (uint16 .npy): the convolutions
-    compute in BF16, so this keeps every weight the forward pass uses."""
-    p = net.get_params().astype(np.float32).view(np.uint32).astype(np.uint64)
-    bits = ((p + 0x7FFF + ((p >> 16) & 1)) >> 16).astype(np.uint16)
-    np.save(path, bits)
+    """Network parameters (FP32 master copy, .npy): the convolutions use
+    their BF16 rounding, the biases and the head use them as they are."""
+    np.save(path, net.get_params().astype(np.float32))
 
 
 def load_params(net, path):
-    bits = np.load(path).astype(np.uint32) << 16
-    net.set_params(bits.view(np.float32))
+    """Parameters from save_params; a uint16 file holds BF16 bit patterns
+    (an earlier format, which rounds the biases and the head too)."""
+    p = np.load(path)
+    if p.dtype == np.uint16:
+        p = (p.astype(np.uint32) << 16).view(np.float32)
+    net.set_params(p.astype(np.float32))
 
 
 @_on_work_stream
@@ -215,13 +217,16 @@ def _predict_du(net, f, bt, eps_before, deps, xb, out, du, chunk):
 
 @_on_work_stream
 def compare(images, k, e, m, net, first_inc, increments, deps=1e-3, tol=1e-8, max_steps=400000, check_every=50,
-            precision="df64", plain_every=1, log=None):
+            precision="df64", plain_every=1, log=None, gate=True):
     """Wall time per increment of three arms on the same specimens, each run
     from the unloaded state through first_inc - 1 unmeasured increments, then
     `increments` measured ones, all relaxed to the same tolerance:
       plain    one single-specimen context per specimen, one after another;
       batched  all specimens in one lsm_batch;
-      warm     batched, with the network's prediction added before relaxing.
+      warm     batched, with the network's prediction added before relaxing
+               (gate: only for specimens with no broken spring yet; after the
+               first break the prediction slowed the relaxation down, see the
+               design notes).
     Returns per-arm seconds and steps."""
     torch = _torch()
     S = len(images)
@@ -247,6 +252,10 @@ def compare(images, k, e, m, net, first_inc, increments, deps=1e-3, tol=1e-8, ma
                 _predict_du(net, f, bt, (i - 1) * deps, deps, xb, out, du, chunk)
             bt.apply_strain(i * deps)
             if arm == "warm":
+                if gate:  # no prediction for specimens that have started to fracture
+                    for q in range(S):
+                        if bt.broken(q)[1] >= 0:
+                            du[q].zero_()
                 nnmod.check(nnmod.lib().lsm_batch_add_displacements(bt.h, nnmod.ptr(du), H, W), bt.h, batch=True)
             st, taken, conv = bt.relax(tol, max_steps, check_every)
             torch.cuda.synchronize()
