@@ -7,13 +7,15 @@
 // its prediction only moves the starting point of the relaxation, which then
 // runs to the same force-residual tolerance as without it.
 //
-// Convolutions are implicit GEMMs on mma.sync m16n8k16 (BF16 in, FP32
-// accumulate), with cp.async double-buffered, XOR-swizzled shared tiles and
-// ldmatrix fragment loads:
-//   forward   M = pixels, N = Cout, K = taps x Cin   (bias + ReLU epilogue)
+// Convolutions are implicit GEMMs (BF16 in, FP32 accumulate):
+//   forward   M = pixels, N = Cout, K = taps x Cin (bias + ReLU epilogue), on
+//             the 5th-generation tensor cores (tcgen05.mma, accumulators in
+//             tensor memory)
 //   dgrad     the forward kernel with 180-degree rotated, transposed weights
 //   wgrad     M = Cout, N = taps x Cin, K = pixels, split over pixel chunks,
-//             partial tiles folded in a fixed order (deterministic)
+//             partial tiles folded in a fixed order (deterministic), on
+//             mma.sync m16n8k16 with cp.async double-buffered, XOR-swizzled
+//             shared tiles and ldmatrix fragment loads
 // Everything else (pooling, upsampling, head, loss, Adam, data preparation)
 // is plain elementwise or fixed-order reduction kernels.
 #include <cuda_bf16.h>
@@ -75,132 +77,210 @@ __device__ __forceinline__ void mma16816(float *c, unsigned a0, unsigned a1, uns
 __device__ __forceinline__ int swz(int row, int chunk) { return row * 32 + ((chunk ^ ((row >> 1) & 3)) << 3); }
 
 // ---------------------------------------------------------- conv forward
+//
+// Implicit GEMM on the 5th-generation tensor cores: tcgen05.mma (kind::f16,
+// BF16 operands in shared memory, FP32 accumulators in tensor memory). A CTA
+// of 128 threads owns 128 output pixels (TMEM lanes) x BN output channels
+// (TMEM columns). The K loop runs over taps x 32-channel chunks: the threads
+// copy the chunk (each thread its pixel's shifted input row, zero outside the
+// image, and a share of the BN weight rows) with cp.async into a two-stage
+// buffer of 8-row x 16-byte core matrices (K-major, no swizzle); thread 0
+// issues two K = 16 MMAs per chunk and commits them to the stage's mbarrier,
+// and a stage is refilled only after its barrier reports those MMAs done.
+// The epilogue reads the accumulator back with tcgen05.ld (each warp its 32
+// lanes), adds the bias, applies the ReLU and stores BF16. Every mbarrier
+// wait is bounded: on expiry the CTA raises g_conv_timeout, skips the
+// epilogue, frees its TMEM and returns; later CTAs return at once.
 
-constexpr int CBM = 128, CBK = 32;
+__device__ int g_conv_timeout;
+
+constexpr int TCM = 128, TCK = 32;
+constexpr int TC_WAIT = 1 << 20;
+
+// shared-memory matrix descriptor (no swizzle; K-major core matrices; LBO
+// = stride between core matrices along K, SBO = along M or N)
+__device__ __forceinline__ uint64_t tc_sdesc(unsigned addr, unsigned lbo, unsigned sbo)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor: D FP32, A and B BF16, both K-major, M x N
+__host__ __device__ constexpr unsigned tc_idesc(int m, int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ bool tc_wait(unsigned bar, unsigned parity)
+{
+    unsigned done = 0;
+    for (int it = 0; it < TC_WAIT && !done; it++)
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity));
+    return done != 0;
+}
+
+// byte offset of (row, 16-byte chunk) in a stage of rows x 32 channels:
+// core matrix (row / 8, chunk) at ((row / 8) * 4 + chunk) * 128, row (row % 8) * 16
+__device__ __forceinline__ unsigned tc_off(int row, int chunk)
+{
+    return (unsigned)((((row >> 3) << 2) + chunk) * 128 + (row & 7) * 16);
+}
 
 template <int BN>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 k_conv_fwd(const bf16 *__restrict__ in, int in_cs, int in_c0, int Cin, const bf16 *__restrict__ W,
            const float *__restrict__ bias, bf16 *__restrict__ out, int out_cs, int out_c0, int Cout, int B, int H,
            int Wd, int taps, int relu)
 {
-    __shared__ __align__(128) bf16 sA[2][CBM * CBK];
-    __shared__ __align__(128) bf16 sB[2][BN * CBK];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int HW = H * Wd;
-    const int M = B * HW;
-    const int m0 = blockIdx.x * CBM, n0 = blockIdx.y * BN;
-    const int kchunks = Cin / CBK;
-    const int KT = taps * kchunks;
+    __shared__ __align__(1024) unsigned char sA[2][TCM * TCK * 2];
+    __shared__ __align__(1024) unsigned char sB[2][BN * TCK * 2];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ unsigned tbase;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) s_abort = *(volatile int *)&g_conv_timeout;  // an earlier CTA gave up
+    __syncthreads();
+    if (s_abort) return;
+    const int HW = H * Wd, M = B * HW;
+    const int m0 = blockIdx.x * TCM, n0 = blockIdx.y * BN;
+    const int kch = Cin / TCK, KT = taps * kch;
+    const int m = m0 + tid;
+    const bool mv = m < M;
+    const int mm = mv ? m : 0;
+    const int pb = mm / HW, prem = mm - pb * HW, py = prem / Wd, px = prem - py * Wd;
 
-    int arow[2], achk[2], ab[2], ay[2], ax[2];
-    bool am[2];
-#pragma unroll
-    for (int i = 0; i < 2; i++) {
-        const int c = tid + 256 * i;
-        arow[i] = c >> 2;
-        achk[i] = c & 3;
-        const int m = m0 + arow[i];
-        am[i] = m < M;
-        const int mm = am[i] ? m : 0;
-        ab[i] = mm / HW;
-        const int rem = mm - ab[i] * HW;
-        ay[i] = rem / Wd;
-        ax[i] = rem - ay[i] * Wd;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)),
+                     "r"(BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const unsigned tmem = tbase;
+
     auto load = [&](int kt, int buf) {
-        const int tap = kt / kchunks, ci0 = (kt - tap * kchunks) * CBK;
+        const int tap = kt / kch, ci0 = (kt - tap * kch) * TCK;
         const int dy = taps == 9 ? tap / 3 - 1 : 0, dx = taps == 9 ? tap % 3 - 1 : 0;
+        const int yy = py + dy, xx = px + dx;
+        const bool v = mv && yy >= 0 && yy < H && xx >= 0 && xx < Wd;
+        const bf16 *src = v ? in + ((int64_t)(pb * H + yy) * Wd + xx) * in_cs + in_c0 + ci0 : in;
+        const unsigned a = smem_u32(&sA[buf][0]);
 #pragma unroll
-        for (int i = 0; i < 2; i++) {
-            const int yy = ay[i] + dy, xx = ax[i] + dx;
-            const bool v = am[i] && yy >= 0 && yy < H && xx >= 0 && xx < Wd;
-            const bf16 *src = v ? in + ((int64_t)(ab[i] * H + yy) * Wd + xx) * in_cs + in_c0 + ci0 + achk[i] * 8 : in;
-            cp_async16(smem_u32(&sA[buf][swz(arow[i], achk[i])]), src, v);
-        }
-        if (tid < BN * 4) {
-            const int r = tid >> 2, ch = tid & 3, co = n0 + r;
-            const bool v = co < Cout;
-            const bf16 *src = v ? W + ((int64_t)co * taps + tap) * Cin + ci0 + ch * 8 : W;
-            cp_async16(smem_u32(&sB[buf][swz(r, ch)]), src, v);
+        for (int c = 0; c < 4; c++) cp_async16(a + tc_off(tid, c), v ? src + 8 * c : in, v);
+        const unsigned b = smem_u32(&sB[buf][0]);
+        for (int e = tid; e < BN * 4; e += 128) {
+            const int r = e >> 2, c = e & 3, co = n0 + r;
+            const bool wv = co < Cout;
+            cp_async16(b + tc_off(r, c), wv ? W + ((int64_t)co * taps + tap) * Cin + ci0 + 8 * c : W, wv);
         }
     };
 
-    constexpr int NT = BN / 16;  // n8 tiles per warp (warp covers BN / 2 columns)
-    float acc[2][NT][4];
-#pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < NT; j++)
-#pragma unroll
-            for (int q = 0; q < 4; q++) acc[i][j][q] = 0.0f;
-    const int wm = warp & 3, wn = warp >> 2;
-
+    bool ok = true;
     load(0, 0);
     cp_commit();
-    for (int kt = 0; kt < KT; kt++) {
-        if (kt + 1 < KT) load(kt + 1, (kt + 1) & 1);
+    for (int kt = 0; kt < KT && ok; kt++) {
+        const int buf = kt & 1;
+        if (kt + 1 < KT) {
+            const int nb = (kt + 1) & 1;
+            if (kt >= 1) ok = tc_wait(smem_u32(&mbar[nb]), (unsigned)(((kt - 1) >> 1) & 1));  // chunk kt-1's MMAs
+            if (!ok) break;
+            load(kt + 1, nb);
+        }
         cp_commit();
         cp_wait<1>();
+        asm volatile("fence.proxy.async.shared::cta;");  // the copies, visible to the tensor core
         __syncthreads();
-        const int buf = kt & 1;
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const unsigned id = tc_idesc(TCM, BN);
 #pragma unroll
-        for (int ks = 0; ks < 2; ks++) {
-            unsigned a[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; mt++) {
-                const int row = wm * 32 + mt * 16 + (lane & 15);
-                const int chk = ks * 2 + (lane >> 4);
-                ldm_x4(a[mt][0], a[mt][1], a[mt][2], a[mt][3], smem_u32(&sA[buf][swz(row, chk)]));
+            for (int ks = 0; ks < 2; ks++) {
+                const uint64_t ad = tc_sdesc(smem_u32(&sA[buf][0]) + ks * 256, 128, 512);
+                const uint64_t bd = tc_sdesc(smem_u32(&sB[buf][0]) + ks * 256, 128, 512);
+                const unsigned accum = (kt > 0 || ks > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(id), "r"(accum));
             }
-            unsigned b[NT][2];
-#pragma unroll
-            for (int jj = 0; jj < NT / 2; jj++) {
-                const int nrow = wn * (BN / 2) + jj * 16 + (lane & 7) + ((lane >> 4) << 3);
-                const int chk = ks * 2 + ((lane >> 3) & 1);
-                ldm_x4(b[2 * jj][0], b[2 * jj][1], b[2 * jj + 1][0], b[2 * jj + 1][1],
-                       smem_u32(&sB[buf][swz(nrow, chk)]));
-            }
-#pragma unroll
-            for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-                for (int j = 0; j < NT; j++) mma16816(acc[mt][j], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b[j][0], b[j][1]);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&mbar[buf])));
         }
-        __syncthreads();
     }
-    const int g = lane >> 2, tg = lane & 3;
+    // the last commit covers every earlier MMA of this thread
+    if (ok && KT > 0) ok = tc_wait(smem_u32(&mbar[(KT - 1) & 1]), (unsigned)(((KT - 1) >> 1) & 1));
+    if (!ok) {
+        if (tid == 0) atomicOr(&g_conv_timeout, 1);
+    } else {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int mo = m0 + 32 * warp + lane;
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            unsigned r[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(tmem + ((unsigned)(32 * warp) << 16) + (unsigned)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            const int n = n0 + c0;
+            if (mo < M && n < Cout) {
+                __align__(16) __nv_bfloat162 h[8];
 #pragma unroll
-    for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-        for (int j = 0; j < NT; j++) {
-            const int n = n0 + wn * (BN / 2) + j * 8 + 2 * tg;
-            if (n >= Cout) continue;
-            const float b0 = bias ? bias[n] : 0.0f, b1 = bias ? bias[n + 1] : 0.0f;
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const int m = m0 + wm * 32 + mt * 16 + g + 8 * h;
-                if (m >= M) continue;
-                float v0 = acc[mt][j][2 * h] + b0, v1 = acc[mt][j][2 * h + 1] + b1;
-                if (relu) {
-                    v0 = fmaxf(v0, 0.0f);
-                    v1 = fmaxf(v1, 0.0f);
+                for (int j = 0; j < 8; j++) {
+                    float v0 = __uint_as_float(r[2 * j]) + (bias ? bias[n + 2 * j] : 0.0f);
+                    float v1 = __uint_as_float(r[2 * j + 1]) + (bias ? bias[n + 2 * j + 1] : 0.0f);
+                    if (relu) {
+                        v0 = fmaxf(v0, 0.0f);
+                        v1 = fmaxf(v1, 0.0f);
+                    }
+                    h[j] = __floats2bfloat162_rn(v0, v1);
                 }
-                *(__nv_bfloat162 *)(out + (int64_t)m * out_cs + out_c0 + n) = __floats2bfloat162_rn(v0, v1);
+                uint4 *dst = (uint4 *)(out + (int64_t)mo * out_cs + out_c0 + n);
+                dst[0] = *(const uint4 *)&h[0];
+                dst[1] = *(const uint4 *)&h[4];
             }
         }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
 }
 
 cudaError_t conv_fwd(const bf16 *in, int in_cs, int in_c0, int Cin, const bf16 *W, const float *bias, bf16 *out,
                      int out_cs, int out_c0, int Cout, int B, int H, int Wd, int taps, bool relu, cudaStream_t st)
 {
-    if (Cin % CBK || Cout % 32 || (in_cs | in_c0 | out_cs | out_c0) % 8) return cudaErrorInvalidValue;
+    if (Cin % TCK || Cout % 32 || (in_cs | in_c0 | out_cs | out_c0) % 8) return cudaErrorInvalidValue;
     const int M = B * H * Wd;
-    const dim3 grid((M + CBM - 1) / CBM, Cout % 64 == 0 ? Cout / 64 : Cout / 32);
-    if (Cout % 64 == 0)
-        k_conv_fwd<64><<<grid, 256, 0, st>>>(in, in_cs, in_c0, Cin, W, bias, out, out_cs, out_c0, Cout, B, H, Wd, taps, relu);
+    if (M == 0) return cudaSuccess;
+    const int BN = Cout % 128 == 0 ? 128 : (Cout % 64 == 0 ? 64 : 32);
+    const dim3 grid((M + TCM - 1) / TCM, Cout / BN);
+    if (BN == 128)
+        k_conv_fwd<128><<<grid, 128, 0, st>>>(in, in_cs, in_c0, Cin, W, bias, out, out_cs, out_c0, Cout, B, H, Wd, taps, relu);
+    else if (BN == 64)
+        k_conv_fwd<64><<<grid, 128, 0, st>>>(in, in_cs, in_c0, Cin, W, bias, out, out_cs, out_c0, Cout, B, H, Wd, taps, relu);
     else
-        k_conv_fwd<32><<<grid, 256, 0, st>>>(in, in_cs, in_c0, Cin, W, bias, out, out_cs, out_c0, Cout, B, H, Wd, taps, relu);
+        k_conv_fwd<32><<<grid, 128, 0, st>>>(in, in_cs, in_c0, Cin, W, bias, out, out_cs, out_c0, Cout, B, H, Wd, taps, relu);
     return cudaGetLastError();
+}
+
+cudaError_t conv_timeout(bool *flag, cudaStream_t st)
+{
+    int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_conv_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    *flag = v != 0;
+    return e;
 }
 
 // ------------------------------------------------------------ conv wgrad
@@ -998,6 +1078,15 @@ lsm_status lsm_unet_forward(lsm_unet *u, const void *in, float *out, int32_t bat
     return e == cudaSuccess ? LSM_OK : ncuda(u, e, "forward");
 }
 
+// LSM_ETIMEOUT if a tensor-core convolution gave up a bounded wait
+static lsm_status conv_status(lsm_unet *u, cudaStream_t st = nullptr)
+{
+    bool t = false;
+    const cudaError_t e = lsm::nn::conv_timeout(&t, u ? u->st : st);
+    if (e != cudaSuccess) return ncuda(u, e, "convolution status");
+    return t ? nfail(u, LSM_ETIMEOUT, "a tensor-core convolution gave up waiting for its MMAs") : LSM_OK;
+}
+
 lsm_status lsm_unet_gradients(lsm_unet *u, const void *in, const float *target, int32_t batch, float *loss,
                               float *grad)
 {
@@ -1007,7 +1096,8 @@ lsm_status lsm_unet_gradients(lsm_unet *u, const void *in, const float *target, 
     if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, u->loss, 4, cudaMemcpyDeviceToHost, u->st);
     if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad, u->G, u->nparam * 4, cudaMemcpyDeviceToHost, u->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(u->st);
-    return e == cudaSuccess ? LSM_OK : ncuda(u, e, "gradients");
+    if (e != cudaSuccess) return ncuda(u, e, "gradients");
+    return conv_status(u);
 }
 
 lsm_status lsm_unet_train_step(lsm_unet *u, const void *in, const float *target, int32_t batch, float lr, float *loss)
@@ -1019,6 +1109,7 @@ lsm_status lsm_unet_train_step(lsm_unet *u, const void *in, const float *target,
     if (e == cudaSuccess && loss) {
         e = cudaMemcpyAsync(loss, u->loss, 4, cudaMemcpyDeviceToHost, u->st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(u->st);
+        if (e == cudaSuccess) return conv_status(u);
     }
     return e == cudaSuccess ? LSM_OK : ncuda(u, e, "train_step");
 }
@@ -1067,9 +1158,10 @@ lsm_status lsm_nn_conv_forward(const void *in, int32_t in_cs, int32_t in_c0, int
     const cudaError_t e = lsm::nn::conv_fwd((const lsm::nn::bf16 *)in, in_cs, in_c0, Cin, (const lsm::nn::bf16 *)W,
                                             bias, (lsm::nn::bf16 *)out, out_cs, out_c0, Cout, B, H, Wd, taps, relu != 0,
                                             (cudaStream_t)stream);
-    return e == cudaSuccess ? LSM_OK
-                            : nfail(nullptr, e == cudaErrorInvalidValue ? LSM_EINVAL : LSM_ECUDA,
-                                    std::string("conv_forward: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess)
+        return nfail(nullptr, e == cudaErrorInvalidValue ? LSM_EINVAL : LSM_ECUDA,
+                     std::string("conv_forward: ") + cudaGetErrorString(e));
+    return conv_status(nullptr, (cudaStream_t)stream);
 }
 
 lsm_status lsm_nn_conv_wgrad(const void *grad, int32_t Cout, const void *in, int32_t in_cs, int32_t in_c0, int32_t Cin,
