@@ -373,6 +373,7 @@ static cudaError_t launch_bt(BatchCtx &b, int64_t t0, int64_t t1)
     static bool configured = false;
     if (!configured) {
         BT_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        BT_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
         configured = true;
     }
     const int64_t ntl = t1 - t0;

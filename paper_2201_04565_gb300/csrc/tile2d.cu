@@ -27,8 +27,13 @@
 
 namespace lsm {
 
+// 3 CTAs of 16 warps per SM for the double-float time step (the register
+// budget that leaves, 42 per thread, is what the kernel needs without spills)
+template <int TY, int PREC, bool SAMPLE>
+__host__ __device__ constexpr int tile_min_ctas() { return PREC == LSM_PREC_DF && !SAMPLE && TY >= 16 ? 3 : 1; }
+
 template <int TX, int TY, int PREC, int MODE, bool SAMPLE>
-__global__ void __launch_bounds__(tile_threads<TY, PREC, SAMPLE>())
+__global__ void __launch_bounds__(tile_threads<TY, PREC, SAMPLE>(), (tile_min_ctas<TY, PREC, SAMPLE>()))
 k_tile2d(TileArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -157,6 +162,10 @@ static cudaError_t launch_tile(Ctx &c, TileArgs A)
     static bool configured = false;  // per template instance
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        // all of the unified L1 / shared storage as shared memory: the CTAs per
+        // SM are bounded by shared memory and registers, not by the carveout
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
         configured = true;
     }
