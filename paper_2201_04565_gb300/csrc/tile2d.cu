@@ -27,17 +27,25 @@
 
 namespace lsm {
 
-// 3 CTAs of 16 warps per SM for the double-float time step (the register
-// budget that leaves, 42 per thread, is what the kernel needs without spills)
+// CTAs per SM the time-step kernels are compiled for: 3 of 16 warps for the
+// double-float step, 6 of 8 warps for the FP32 and FAST64 steps, 5 for the
+// exact FP64 step (the register budgets that leave, 42 and 51 per thread, hold
+// each kernel without spills)
 template <int TY, int PREC, bool SAMPLE>
-__host__ __device__ constexpr int tile_min_ctas() { return PREC == LSM_PREC_DF && !SAMPLE && TY >= 16 ? 3 : 1; }
+__host__ __device__ constexpr int tile_min_ctas()
+{
+    return SAMPLE || TY < 16                                       ? 1
+           : PREC == LSM_PREC_DF                                   ? 3
+           : PREC == LSM_PREC_F32 || PREC == LSM_PREC_FAST64 ? 6
+                                                                   : 5;
+}
 
-template <int TX, int TY, int PREC, int MODE, bool SAMPLE>
+template <int TX, int TY, int PREC, int MODE, bool SAMPLE, bool RATE>
 __global__ void __launch_bounds__(tile_threads<TY, PREC, SAMPLE>(), (tile_min_ctas<TY, PREC, SAMPLE>()))
 k_tile2d(TileArgs A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    tile_body<TX, TY, PREC, MODE, SAMPLE>(A, blockIdx.x, blockIdx.y,
+    tile_body<TX, TY, PREC, MODE, SAMPLE, RATE>(A, blockIdx.x, blockIdx.y,
                                                 (int64_t)blockIdx.y * gridDim.x + blockIdx.x, smem_raw);
 }
 
@@ -154,10 +162,10 @@ static TileArgs tile_args(Ctx &c)
     return A;
 }
 
-template <int PREC, int MODE, bool SAMPLE>
+template <int PREC, int MODE, bool SAMPLE, bool RATE>
 static cudaError_t launch_tile(Ctx &c, TileArgs A)
 {
-    auto kern = k_tile2d<TILE_X, TILE_Y, PREC, MODE, SAMPLE>;
+    auto kern = k_tile2d<TILE_X, TILE_Y, PREC, MODE, SAMPLE, RATE>;
     const size_t smem = tile_smem_bytes<TILE_X, TILE_Y>(PREC);
     static bool configured = false;  // per template instance
     if (!configured) {
@@ -174,15 +182,24 @@ static cudaError_t launch_tile(Ctx &c, TileArgs A)
     return cudaSuccess;
 }
 
+// constant strain-rate loading is a separate instance of the time step, so
+// that the ordinary step carries none of its code (registers)
+template <int MODE, bool SAMPLE, bool RATE>
+static cudaError_t launch_tile_p(Ctx &c, TileArgs A)
+{
+    switch (c.h.precision) {
+    case LSM_PREC_FAST64: return launch_tile<LSM_PREC_FAST64, MODE, SAMPLE, RATE>(c, A);
+    case LSM_PREC_F32: return launch_tile<LSM_PREC_F32, MODE, SAMPLE, RATE>(c, A);
+    case LSM_PREC_DF: return launch_tile<LSM_PREC_DF, MODE, SAMPLE, RATE>(c, A);
+    default: return launch_tile<LSM_PREC_EXACT64, MODE, SAMPLE, RATE>(c, A);
+    }
+}
+
 template <int MODE, bool SAMPLE>
 static cudaError_t launch_tile_prec(Ctx &c, TileArgs A)
 {
-    switch (c.h.precision) {
-    case LSM_PREC_FAST64: return launch_tile<LSM_PREC_FAST64, MODE, SAMPLE>(c, A);
-    case LSM_PREC_F32: return launch_tile<LSM_PREC_F32, MODE, SAMPLE>(c, A);
-    case LSM_PREC_DF: return launch_tile<LSM_PREC_DF, MODE, SAMPLE>(c, A);
-    default: return launch_tile<LSM_PREC_EXACT64, MODE, SAMPLE>(c, A);
-    }
+    if (MODE == T_STEP && c.rate_on) return launch_tile_p<MODE, SAMPLE, true>(c, A);
+    return launch_tile_p<MODE, SAMPLE, false>(c, A);
 }
 
 cudaError_t tile_enqueue_steps(Ctx &c, int64_t nsteps, int start_buf)

@@ -244,7 +244,7 @@ __device__ __forceinline__ void eval_spring(const TileArgs &A, int rp, int rq, i
 // positions drifted by dt vh (step mode): as doubles in the FP64 modes, as
 // fixed-point copies in the F32/DF modes. The drifted position is also
 // returned (the owning thread keeps it in registers for the integration).
-template <int PREC, int MODE, int RX>
+template <int PREC, int MODE, int RX, bool RATE>
 __device__ __forceinline__ void load_pixel(const TileArgs &A, int x0, int y0, int rx, int ry, double *sx,
                                            double *sy, long long *sxf, long long *syf, uint8_t *sph,
                                            uint8_t *smk, bool &over, double &opx, double &opy)
@@ -263,7 +263,7 @@ __device__ __forceinline__ void load_pixel(const TileArgs &A, int x0, int y0, in
             py = A.x_in[A.np + g];
             if (MODE == T_STEP) {
                 const bool grip = gx == 0 || gx == A.nx - 1;
-                if (grip && A.rate_on) {  // grip x at the strain of this step
+                if (RATE && grip) {  // constant strain rate: grip x at the strain of this step
                     const long long s = *A.d_step + A.t_off + 1 - A.rate_step0;
                     const double eps = ad(A.rate_eps0, ml((double)s, A.rate_dt));
                     const double X = ml((double)gx, A.a);
@@ -295,7 +295,7 @@ __device__ __forceinline__ void load_pixel(const TileArgs &A, int x0, int y0, in
 
 // One CTA step of one 32 x TY tile (tile coordinates bx, by; tile_id indexes
 // the per-tile partial sums); warp w handles tile rows w, w + 8, ...
-template <int TX, int TY, int PREC, int MODE, bool SAMPLE>
+template <int TX, int TY, int PREC, int MODE, bool SAMPLE, bool RATE = false>
 __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int64_t tile_id,
                                           unsigned char *smem_raw)
 {
@@ -361,11 +361,11 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
     for (int k = 0; k < KR; k++) {
         const int ry = warp + k * NW;
         if (ry < RY)
-            load_pixel<PREC, MODE, RX>(A, x0, y0, lane + 1, ry, sx, sy, sxf, syf, sph, smk, over, opx[k], opy[k]);
+            load_pixel<PREC, MODE, RX, RATE>(A, x0, y0, lane + 1, ry, sx, sy, sxf, syf, sph, smk, over, opx[k], opy[k]);
     }
     for (int q = tid; q < 2 * RY; q += NT) {
         double hx, hy;
-        load_pixel<PREC, MODE, RX>(A, x0, y0, (q & 1) ? TX + 1 : 0, q >> 1, sx, sy, sxf, syf, sph, smk, over, hx,
+        load_pixel<PREC, MODE, RX, RATE>(A, x0, y0, (q & 1) ? TX + 1 : 0, q >> 1, sx, sy, sxf, syf, sph, smk, over, hx,
                                    hy);
     }
     if (FIX && over) atomicOr(A.status, 2);
