@@ -86,7 +86,7 @@ struct BatchCtx {
 // ----------------------------------------------------------------- kernels
 
 template <int TY, int PREC, int MODE, bool SAMPLE>
-__global__ void __launch_bounds__(tile_threads<TY, PREC, SAMPLE>())
+__global__ void __launch_bounds__(tile_threads<TY, PREC, SAMPLE>(), (tile_min_ctas<TY, PREC, SAMPLE>()))
 k_tile2d_batch(TileArgs base, const BatchTile *__restrict__ tiles, int64_t t0, int64_t t1,
                const SpecDesc *__restrict__ specs, double *X0, double *X1, double *V0, double *V1, double *VOBS,
                const uint8_t *PH, uint8_t *MASK, long long *BRK, unsigned long long *fb,

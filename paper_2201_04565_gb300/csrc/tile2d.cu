@@ -27,19 +27,6 @@
 
 namespace lsm {
 
-// CTAs per SM the time-step kernels are compiled for: 3 of 16 warps for the
-// double-float step, 6 of 8 warps for the FP32 and FAST64 steps, 5 for the
-// exact FP64 step (the register budgets that leave, 42 and 51 per thread, hold
-// each kernel without spills)
-template <int TY, int PREC, bool SAMPLE>
-__host__ __device__ constexpr int tile_min_ctas()
-{
-    return SAMPLE || TY < 16                                       ? 1
-           : PREC == LSM_PREC_DF                                   ? 3
-           : PREC == LSM_PREC_F32 || PREC == LSM_PREC_FAST64 ? 6
-                                                                   : 5;
-}
-
 template <int TX, int TY, int PREC, int MODE, bool SAMPLE, bool RATE>
 __global__ void __launch_bounds__(tile_threads<TY, PREC, SAMPLE>(), (tile_min_ctas<TY, PREC, SAMPLE>()))
 k_tile2d(TileArgs A)
