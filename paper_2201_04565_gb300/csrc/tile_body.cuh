@@ -126,19 +126,20 @@ struct TileArgs {
     int64_t ntiles;
 };
 
-// CTAs per SM the 16-row tile kernels are compiled for: 3 of 16 warps for
-// the double-float time step, 6 of 8 warps for the FP32 and FAST64 steps, 5
-// for the exact FP64 step, 4 of 8 warps for every sample step (the register
-// budgets that leave, 42, 51 and 64 per thread, hold each kernel without
-// spills, up to 12 bytes in the batched FP32 step)
+// CTAs per SM the 8- and 16-row tile kernels are compiled for: 3 of 16
+// warps for the 16-row double-float time step, 6 of 8 warps for the other
+// double-float, FP32 and FAST64 steps, 5 for the exact FP64 step, 4 of 8
+// warps for every sample step (the register budgets that leave, 42, 51 and 64
+// per thread, hold each kernel without spills, up to 12 bytes in the batched
+// FP32 step)
 template <int TY, int PREC, bool SAMPLE>
 __host__ __device__ constexpr int tile_min_ctas()
 {
-    return TY != 16                                                ? 1
-           : SAMPLE                                                ? 4
-           : PREC == LSM_PREC_DF                                   ? 3
-           : PREC == LSM_PREC_F32 || PREC == LSM_PREC_FAST64 ? 6
-                                                                   : 5;
+    return TY != 8 && TY != 16       ? 1
+           : SAMPLE                  ? 4
+           : PREC == LSM_PREC_DF     ? (TY == 16 ? 3 : 6)
+           : PREC == LSM_PREC_EXACT64 ? 5
+                                     : 6;
 }
 
 // Force on the lower endpoint of one spring (rp -> rq, forward slot), with
