@@ -107,8 +107,8 @@ def algorithmic_bytes(n, m, dim):
 # keyed by precision mode, with the sha1 prefix of the kernel source it was
 # taken on; once the kernel changes, traffic reports null until re-measured.
 NCU_TRAFFIC = {
-    # profiles/k_tile2d_df64_2d_2048_two_phase.md: 142.7 MB read + 96.6 MB written
-    "df64": (239.29e6, "9805704431aa"),
+    # profiles/k_tile2d_df64_2d_2048_two_phase.md: 142.7 MB read + 96.9 MB written
+    "df64": (239.56e6, "6435741d92d8"),
 }
 
 # Warp instructions executed by one time-step launch (ncu smsp__inst_executed.sum,
@@ -116,13 +116,15 @@ NCU_TRAFFIC = {
 # part (152 SMs x 4 schedulers x 1 warp instruction per cycle at the SM clock)
 # this gives the instruction-issue roofline, the one the fixed-point modes
 # are bound by.
-NCU_INSTRUCTIONS = {}
+NCU_INSTRUCTIONS = {
+    "df64": (153721568, "6435741d92d8"),
+}
 
 # Binding unit of each mode's time-step kernel, from ncu on the same workload
 # (see the profile summaries), for the roofline's "limiter" note.
 LIMITER = {
-    "df64": "instruction issue (ncu: 74% of issue slots busy, FP64 pipe 32%, DRAM 16% of peak)",
-    "f32": "instruction issue and latency (ncu: 70% issue, LSU 47%, DRAM 27% of peak)",
+    "df64": "instruction issue (ncu: 71% of issue slots busy, FP64 pipe 33%, DRAM 17% of peak)",
+    "f32": "instruction issue and latency (ncu: 69% issue, LSU 47%, FP64 pipe 42%, DRAM 28% of peak)",
     "fast64": "FP64 pipe (ncu: 86% busy)",
     "exact64": "FP64 pipe (ncu: 88% busy; correctly rounded sqrt and divide)",
 }
@@ -315,7 +317,7 @@ def run_batch512(args, rank=0, world=1, plain_every=8):
     stream = torch.cuda.Stream()
     bt = bmod.Batch(imgs, k, e, m, dt=0.01, damping=0.1, precision=prec, stream=stream.cuda_stream)
     msum = sum(mm for _, mm in bt.sizes)
-    tune = bt.autotune(4)
+    tune = bt.autotune(10)
     torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as td

@@ -40,10 +40,12 @@ const char *lsm_batch_last_error(const lsm_batch *b);
  * NULL). */
 lsm_status lsm_batch_sizes(lsm_batch *b, int32_t spec, int32_t *count, int64_t *n, int64_t *m);
 
-/* Time a few steps of every candidate schedule (tile height 8/16/32, grid of
- * one CTA per tile or a persistent grid, natural or largest-specimen-first tile
- * order) on a copy of the current state, keep the fastest, and restore the
- * state. Outputs (may be NULL): chosen tile height, grid size (0 = one CTA per
+/* Time steps_per_trial steps of every candidate schedule (tile height
+ * 8/16/32, grid of one CTA per tile or a persistent grid of 4 or 8 CTAs per
+ * SM, natural or largest-specimen-first tile order) on a copy of the current
+ * state, after a warm-up that brings the GPU to its load clocks, in two
+ * sweeps; keep the schedule with the fastest trial and restore the state.
+ * Outputs (may be NULL): chosen tile height, grid size (0 = one CTA per
  * tile), order (0 natural, 1 largest first) and its time per step in ms. */
 lsm_status lsm_batch_autotune(lsm_batch *b, int32_t steps_per_trial, int32_t *tile_y, int32_t *grid,
                               int32_t *order, double *ms_per_step);

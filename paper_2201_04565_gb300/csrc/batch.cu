@@ -1040,27 +1040,41 @@ lsm_status lsm_batch_autotune(lsm_batch *b, int32_t steps_per_trial, int32_t *ti
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int tys[3] = {8, 16, 32};
-    for (int it = 0; it < 3 && e == cudaSuccess; it++)
-        for (int ord = 0; ord < 2 && e == cudaSuccess; ord++) {
-            e = lsm::build_tiles(*b, tys[it], ord);
-            const int grids[3] = {0, nsm * 4, nsm * 8};
-            for (int gi = 0; gi < 3 && e == cudaSuccess; gi++) {
-                b->grid = grids[gi];
-                e = lsm::batch_steps_graph(*b, steps_per_trial, 0, 0, 0.0);  // warm (captures the graph)
-                if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-                if (e == cudaSuccess) e = lsm::batch_steps_graph(*b, steps_per_trial, 0, 0, 0.0);
-                if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                float ms = 0.0f;
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-                if (e == cudaSuccess && ms / steps_per_trial < best) {
-                    best = ms / steps_per_trial;
-                    bty = tys[it];
-                    bgrid = grids[gi];
-                    bord = ord;
+    // Two sweeps over the 18 schedules, each keeping its faster trial; the
+    // GPU is brought to its load clocks first (steps of the current
+    // schedule), so that the first candidates are not timed at idle clocks.
+    double tbest[3][2][3];
+    for (int it = 0; it < 3; it++)
+        for (int ord = 0; ord < 2; ord++)
+            for (int gi = 0; gi < 3; gi++) tbest[it][ord][gi] = 1e300;
+    if (e == cudaSuccess) e = lsm::build_tiles(*b, b->tile_y, b->order);
+    for (int w = 0; w < 4 && e == cudaSuccess; w++) e = lsm::batch_steps_graph(*b, steps_per_trial, 0, 0, 0.0);
+    for (int sweep = 0; sweep < 2 && e == cudaSuccess; sweep++)
+        for (int it = 0; it < 3 && e == cudaSuccess; it++)
+            for (int ord = 0; ord < 2 && e == cudaSuccess; ord++) {
+                e = lsm::build_tiles(*b, tys[it], ord);
+                const int grids[3] = {0, nsm * 4, nsm * 8};
+                for (int gi = 0; gi < 3 && e == cudaSuccess; gi++) {
+                    b->grid = grids[gi];
+                    e = lsm::batch_steps_graph(*b, steps_per_trial, 0, 0, 0.0);  // warm (captures the graph)
+                    if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+                    if (e == cudaSuccess) e = lsm::batch_steps_graph(*b, steps_per_trial, 0, 0, 0.0);
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    float ms = 0.0f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    if (e == cudaSuccess && ms / steps_per_trial < tbest[it][ord][gi]) tbest[it][ord][gi] = ms / steps_per_trial;
                 }
             }
-        }
+    for (int it = 0; it < 3; it++)
+        for (int ord = 0; ord < 2; ord++)
+            for (int gi = 0; gi < 3; gi++)
+                if (tbest[it][ord][gi] < best) {
+                    best = tbest[it][ord][gi];
+                    bty = tys[it];
+                    bgrid = gi == 0 ? 0 : nsm * 4 * gi;
+                    bord = ord;
+                }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     // restore the state and apply the winner
