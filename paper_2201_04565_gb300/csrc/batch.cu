@@ -284,10 +284,17 @@ static cudaError_t balloc(T **p, size_t count)
     return cudaMalloc((void **)p, (count ? count : 1) * sizeof(T));
 }
 
-static void batch_free(BatchCtx &b)
+// Captured step graphs bake in the tile list, the grid and the buffers; any
+// change of those drops them.
+static void drop_graphs(BatchCtx &b)
 {
     for (auto &kv : b.graphs) cudaGraphExecDestroy(kv.second);
     b.graphs.clear();
+}
+
+static void batch_free(BatchCtx &b)
+{
+    drop_graphs(b);
     void *ptrs[] = {b.X[0], b.X[1], b.VH[0], b.VH[1], b.VOBS, b.PH, b.MASK, b.BRK, b.SBASE, b.specs, b.tiles,
                     b.part_s, b.part_p, b.fb, b.nb, b.status, b.nactive, b.d_nsamp, b.samples, b.scratch,
                     b.d_eps2, b.types, b.tdf, b.tmass, b.tcoef, b.export_buf};
@@ -335,8 +342,7 @@ static cudaError_t build_tiles(BatchCtx &b, int ty, int order)
     BT_TRY(cudaStreamSynchronize(b.stream));
     b.tile_y = ty;
     b.order = order;
-    for (auto &kv : b.graphs) cudaGraphExecDestroy(kv.second);
-    b.graphs.clear();
+    drop_graphs(b);
     return cudaSuccess;
 }
 
@@ -635,8 +641,7 @@ lsm_status grow_samples(lsm_batch *b)
     cudaFree(b->samples);
     b->samples = ns;
     b->cap = nc;
-    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
-    b->graphs.clear();
+    drop_graphs(*b);
     return LSM_OK;
 }
 
@@ -751,6 +756,7 @@ lsm_status lsm_batch_set_schedule(lsm_batch *b, int32_t tile_y, int32_t grid, in
     if (!b) return bfail(nullptr, LSM_EINVAL, "null batch");
     if ((tile_y != 8 && tile_y != 16 && tile_y != 32) || grid < 0 || (order != 0 && order != 1))
         return bfail(b, LSM_EINVAL, "tile_y must be 8, 16 or 32; grid >= 0; order 0 or 1");
+    if (grid != b->grid) lsm::drop_graphs(*b);
     b->grid = grid;
     if (tile_y != b->tile_y || order != b->order) {
         cudaError_t e = lsm::build_tiles(*b, tile_y, order);
@@ -1056,6 +1062,7 @@ lsm_status lsm_batch_autotune(lsm_batch *b, int32_t steps_per_trial, int32_t *ti
                 const int grids[3] = {0, nsm * 4, nsm * 8};
                 for (int gi = 0; gi < 3 && e == cudaSuccess; gi++) {
                     b->grid = grids[gi];
+                    lsm::drop_graphs(*b);  // the cached graphs hold the previous grid
                     e = lsm::batch_steps_graph(*b, steps_per_trial, 0, 0, 0.0);  // warm (captures the graph)
                     if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
                     if (e == cudaSuccess) e = lsm::batch_steps_graph(*b, steps_per_trial, 0, 0, 0.0);
