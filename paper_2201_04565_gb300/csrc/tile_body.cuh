@@ -16,9 +16,9 @@ namespace lsm {
 namespace {
 
 // Threads per CTA for a tile of height TY: one warp per tile row, up to 16
-// warps for the double-float time step (measured best: occupancy is limited
-// by registers and shared memory) and 8 otherwise (fewer warps per barrier;
-// the sample step needs more registers).
+// warps for the double-float time step (16- and 32-row tiles of the batched
+// kernel) and 8 otherwise (fewer warps per barrier; the sample step needs
+// more registers).
 template <int TY, int PREC, bool SAMPLE>
 __host__ __device__ constexpr int tile_threads()
 {
