@@ -105,12 +105,13 @@ cudaError_t tile_export(Ctx &c, bool steps)
 constexpr int TILE_X = 32;
 
 // Tile height: 8 rows of one warp each (6 CTAs per SM) for the double-float
-// mode, 16 rows otherwise (measured fastest per mode on the 2048 x 2048
-// composite).
-template <int PREC>
-constexpr int tile_y() { return PREC == LSM_PREC_DF ? 8 : 16; }
-
-static int tile_y_of(int prec) { return prec == LSM_PREC_DF ? tile_y<LSM_PREC_DF>() : tile_y<LSM_PREC_F32>(); }
+// steps without a sample, 16 rows otherwise (measured fastest per mode on the
+// 2048 x 2048 composite). Only sample steps write per-tile partial sums, so
+// the partials always come from 16-row tiles (half as many block reductions
+// as 8-row tiles would need).
+constexpr int TILE_Y_SAMPLE = 16;
+template <int PREC, bool SAMPLE>
+constexpr int tile_y() { return PREC == LSM_PREC_DF && !SAMPLE ? 8 : TILE_Y_SAMPLE; }
 
 static TileArgs tile_args(Ctx &c)
 {
@@ -160,7 +161,7 @@ static TileArgs tile_args(Ctx &c)
 template <int PREC, int MODE, bool SAMPLE, bool RATE>
 static cudaError_t launch_tile(Ctx &c, TileArgs A)
 {
-    constexpr int TILE_Y = tile_y<PREC>();
+    constexpr int TILE_Y = tile_y<PREC, SAMPLE>();
     auto kern = k_tile2d<TILE_X, TILE_Y, PREC, MODE, SAMPLE, RATE>;
     const size_t smem = tile_smem_bytes<TILE_X, TILE_Y>(PREC);
     static bool configured = false;  // per template instance
@@ -245,8 +246,7 @@ cudaError_t tile_apply_strain(Ctx &c, double eps_old, double eps_new)
 
 int64_t tile_count(const Ctx &c)
 {
-    const int ty = tile_y_of(c.h.precision);
-    return (int64_t)((c.h.nx + TILE_X - 1) / TILE_X) * ((c.h.ny + ty - 1) / ty);
+    return (int64_t)((c.h.nx + TILE_X - 1) / TILE_X) * ((c.h.ny + TILE_Y_SAMPLE - 1) / TILE_Y_SAMPLE);
 }
 
 }  // namespace lsm

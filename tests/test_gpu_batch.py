@@ -39,9 +39,9 @@ def test_batch_matches_single_specimens(B, oracle_mod, precision):
     imgs = _images()
     k, e, m = two_phase_materials()
     bt = batch.Batch(imgs, k, e, m, precision=precision)
-    # the single-specimen tile height of this mode (8 rows in df64, 16
-    # otherwise), so that the per-tile sample partials group the same terms
-    bt.set_schedule(8 if precision == "df64" else 16, 0, 0)
+    # 16-row tiles, the tile height of the single-specimen sample steps, so
+    # that the per-tile sample partials group the same terms
+    bt.set_schedule(16, 0, 0)
     singles = [lsm.Specimen.from_image(im, k, e, m, precision=precision) for im in imgs]
     for i in range(1, 41):
         bt.apply_strain(i * 2.5e-3)
