@@ -107,8 +107,12 @@ def algorithmic_bytes(n, m, dim):
 # keyed by precision mode, with the sha1 prefix of the kernel source it was
 # taken on; once the kernel changes, traffic reports null until re-measured.
 NCU_TRAFFIC = {
-    # profiles/k_tile2d_df64_2d_2048_two_phase.md: 142.7 MB read + 96.9 MB written
-    "df64": (239.56e6, "6435741d92d8"),
+    # profiles/k_tile2d_step_2d_2048_two_phase.md (DRAM read + write of one
+    # time-step launch, ncu, the same 2048 x 2048 workload)
+    "df64": (239.89e6, "826c1ec80efa"),
+    "f32": (238.04e6, "826c1ec80efa"),
+    "fast64": (237.41e6, "826c1ec80efa"),
+    "exact64": (238.16e6, "826c1ec80efa"),
 }
 
 # Warp instructions executed by one time-step launch (ncu smsp__inst_executed.sum,
@@ -117,13 +121,16 @@ NCU_TRAFFIC = {
 # this gives the instruction-issue roofline, the one the fixed-point modes
 # are bound by.
 NCU_INSTRUCTIONS = {
-    "df64": (153721568, "6435741d92d8"),
+    "df64": (160383328, "826c1ec80efa"),
+    "f32": (88946351, "826c1ec80efa"),
+    "fast64": (94464248, "826c1ec80efa"),
+    "exact64": (195704900, "826c1ec80efa"),
 }
 
 # Binding unit of each mode's time-step kernel, from ncu on the same workload
 # (see the profile summaries), for the roofline's "limiter" note.
 LIMITER = {
-    "df64": "instruction issue (ncu: 71% of issue slots busy, FP64 pipe 33%, DRAM 17% of peak)",
+    "df64": "instruction issue (ncu: 80% of issue slots busy, FP64 pipe 37%, DRAM 19% of peak)",
     "f32": "instruction issue and latency (ncu: 69% issue, LSU 47%, FP64 pipe 42%, DRAM 28% of peak)",
     "fast64": "FP64 pipe (ncu: 86% busy)",
     "exact64": "FP64 pipe (ncu: 88% busy; correctly rounded sqrt and divide)",
