@@ -259,11 +259,7 @@ def run_gpu(args, rank, world):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": dtype,
         "data": "synthetic (seeded two-phase inclusion image; the paper's specimen files are not used)",
-        "config": {"workload": WORKLOAD["name"], "image": "%dx%d" % (WORKLOAD["nx"], WORKLOAD["ny"]),
-                   "particles": spec.n, "springs": spec.m, "time_steps_per_bench_step": nst,
-                   "dt": WORKLOAD["dt"], "damping": WORKLOAD["damping"], "precision": args.precision,
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (%.0f MB of state and springs per time step)" % (algb / 1e6)},
+        "config": _config_2d(spec.n, spec.m, spec.dim, args.precision, world),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
                      "kernel": "k_tile2d (one launch per time step)",
@@ -415,6 +411,17 @@ def run_foam256(args):
     return out
 
 
+def _config_2d(n, m, dim, precision, world):
+    """The bench line's config for the 2048 x 2048 workload (shared by the
+    library arm and the oracle arm)."""
+    return {"workload": WORKLOAD["name"], "image": "%dx%d" % (WORKLOAD["nx"], WORKLOAD["ny"]),
+            "particles": n, "springs": m, "time_steps_per_bench_step": WORKLOAD["steps_per_increment"],
+            "dt": WORKLOAD["dt"], "damping": WORKLOAD["damping"], "precision": precision,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "inputs larger than L2 (%.0f MB of state and springs per time step)"
+                  % (algorithmic_bytes(n, m, dim) / 1e6)}
+
+
 def run_oracle_sample(budget_s=12.0, threads=1):
     """The FP64 CPU oracle on the same workload: one strain increment, then as
     many time steps as fit in about budget_s seconds, on `threads` host
@@ -436,7 +443,7 @@ def run_oracle_sample(budget_s=12.0, threads=1):
     return {"value": o.m * nsteps / dt, "unit": UNIT, "cores": used, "kind": "oracle",
             "sample": "%d time steps of the full 2048x2048 workload after one 1e-3 strain increment "
                       "(plain C FP64 oracle, %d host thread%s)" % (nsteps, used, "" if used == 1 else "s"),
-            "seconds": dt, "steps": nsteps}
+            "seconds": dt, "steps": nsteps, "n": o.n, "m": o.m}
 
 
 def cpu_baseline():
@@ -445,6 +452,9 @@ def cpu_baseline():
     cores = os.cpu_count() or 1
     out = run_oracle_sample(budget_s=15.0, threads=cores)
     one = run_oracle_sample(budget_s=10.0, threads=1)
+    for q in (out, one):
+        q.pop("n")
+        q.pop("m")
     out["single_thread"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
     return out
 
@@ -474,7 +484,7 @@ def main():
                "ms_per_step": 1e3 * base["seconds"] / base["steps"] * WORKLOAD["steps_per_increment"],
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                "data": "synthetic (seeded two-phase inclusion image)",
-               "config": {"workload": WORKLOAD["name"], "image": "2048x2048"},
+               "config": _config_2d(base.pop("n"), base.pop("m"), 2, args.precision, world),
                "cpu_baseline": base,
                "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(out))
