@@ -281,6 +281,22 @@ lsm_status lsm_fields(lsm_ctx *ctx, double cell_volume, double *stress, double *
  * pending device status. */
 lsm_status lsm_synchronize(lsm_ctx *ctx);
 
+/* Checkpoint and resume (a lifecycle call of this library; the paper's
+ * solver only writes dump files, Section 3.1). lsm_save synchronises ctx and
+ * writes to `path` (overwritten) the built network and the complete dynamic
+ * state: positions and velocities as the time-step kernels hold them, broken
+ * flags and break steps, step count, applied strain, strain-rate settings and
+ * every recorded sample, with a checksum. lsm_load rebuilds a context from
+ * such a file on `stream` (a cudaStream_t; NULL = a library-owned stream)
+ * and restores that state, so that every later call gives results identical
+ * bit for bit to those of the saved context. Errors: LSM_EINVAL for a null
+ * argument, an unreadable, truncated, corrupt or foreign file (checked before
+ * any device work) or a write failure; LSM_ENONFINITE / LSM_ECUDA as
+ * lsm_synchronize; LSM_ENOMEM. The file is tied to this library version and
+ * byte order. */
+lsm_status lsm_save(lsm_ctx *ctx, const char *path);
+lsm_status lsm_load(const char *path, void *stream, lsm_ctx **out);
+
 /* Counters for throughput accounting: time steps taken, spring updates
  * (springs x steps) and CUDA kernels launched by the library (graph nodes
  * included). Any output may be NULL. */

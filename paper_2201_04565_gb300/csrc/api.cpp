@@ -485,6 +485,60 @@ lsm_status lsm_synchronize(lsm_ctx *c)
     return device_status(c);
 }
 
+lsm_status lsm_save(lsm_ctx *c, const char *path)
+{
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    if (!path) return fail(c, LSM_EINVAL, "null path");
+    lsm_status st = device_status(c);
+    if (st != LSM_OK) return st;
+    std::string err;
+    cudaError_t e;
+    try {
+        e = lsm::checkpoint_save(*c, path, err);
+    } catch (const std::bad_alloc &) {
+        return fail(c, LSM_ENOMEM, "host allocation failed during save");
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "save");
+    if (!err.empty()) return fail(c, LSM_EINVAL, err);
+    return LSM_OK;
+}
+
+lsm_status lsm_load(const char *path, void *stream, lsm_ctx **out)
+{
+    if (!path || !out) return fail(nullptr, LSM_EINVAL, "path and out are required");
+    *out = nullptr;
+    lsm_ctx *c = new (std::nothrow) lsm_ctx();
+    if (!c) return fail(nullptr, LSM_ENOMEM, "host allocation failed");
+    lsm::CkptState s;
+    std::string err;
+    bool ok;
+    try {
+        ok = lsm::checkpoint_read(path, c->h, s, err);
+    } catch (const std::bad_alloc &) {
+        delete c;
+        return fail(nullptr, LSM_ENOMEM, "host allocation failed during load");
+    }
+    if (!ok) {
+        delete c;
+        return fail(nullptr, LSM_EINVAL, err);
+    }
+    lsm_ctx *built = nullptr;
+    lsm_status st = finish_build(c, stream, &built, (int)s.path);  // frees c on failure
+    if (st != LSM_OK) return st;
+    if (built->tile != (s.tile != 0)) {
+        lsm_destroy(built);
+        return fail(nullptr, LSM_EINVAL, "checkpoint was written by a different kernel path");
+    }
+    cudaError_t e = lsm::checkpoint_restore(*built, s, err);
+    if (e != cudaSuccess || !err.empty()) {
+        const std::string msg = e != cudaSuccess ? std::string("load: ") + cudaGetErrorString(e) : err;
+        lsm_destroy(built);
+        return fail(nullptr, e != cudaSuccess ? LSM_ECUDA : LSM_EINVAL, msg);
+    }
+    *out = built;
+    return LSM_OK;
+}
+
 lsm_status lsm_counters(lsm_ctx *c, int64_t *steps, int64_t *spring_updates,
                         int64_t *kernel_launches)
 {

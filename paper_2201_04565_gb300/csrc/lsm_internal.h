@@ -171,6 +171,29 @@ struct Ctx {
     std::map<int64_t, cudaGraphExec_t> graphs;
 };
 
+// checkpoint.cpp: lsm_save / lsm_load
+struct CkptState {
+    uint32_t path = 0, tile = 0;  // build path (0 automatic, 1 spring list); ran on a tile path
+    double eps = 0.0;
+    int64_t steps = 0, nsamples = 0, launches = 0;
+    int32_t rate_on = 0;
+    double rate_eps0 = 0.0, rate_dt = 0.0;
+    long long rate_step0 = 0;
+    long long d_step = 0;
+    unsigned long long first_break = 0, nbroken = 0;
+    int32_t status = 0;
+    double d_eps = 0.0;
+    long long d_nsamples = 0;
+    std::vector<DeviceSample> samples;
+    std::vector<std::vector<uint8_t>> bufs;  // the path's state buffers
+};
+// device -> file; err set (and cudaSuccess returned) on an I/O failure
+cudaError_t checkpoint_save(Ctx &c, const char *path, std::string &err);
+// file -> host (no device work); false with err on a malformed file
+bool checkpoint_read(const char *path, HostNet &h, CkptState &s, std::string &err);
+// host -> the device buffers of a context freshly built from the same network
+cudaError_t checkpoint_restore(Ctx &c, const CkptState &s, std::string &err);
+
 // api.cpp: message returned by lsm_last_error(NULL) on this thread
 void set_thread_error(const char *msg);
 

@@ -80,6 +80,8 @@ SIGNATURES = [
     ("lsm_synchronize", C.c_int, [_P]),
     ("lsm_fields", C.c_int, [_P, C.c_double, _P, _P]),
     ("lsm_set_strain_rate", C.c_int, [_P, C.c_double]),
+    ("lsm_save", C.c_int, [_P, C.c_char_p]),
+    ("lsm_load", C.c_int, [C.c_char_p, _P, C.POINTER(_P)]),
     ("lsm_counters", C.c_int, [_P, _P, _P, _P]),
     ("lsm_spring_energy_static", C.c_int, [_I32, _I64, _I64, _P, _P, _P, _P, _P, _P, _P, _P]),
 ]
@@ -287,6 +289,18 @@ def lsm_synchronize(h):
     _check(load_library().lsm_synchronize(h), h)
 
 
+def lsm_save(h, path):
+    """Checkpoint the context to a file (network and complete state)."""
+    _check(load_library().lsm_save(h, os.fsencode(path)), h)
+
+
+def lsm_load(path, stream=None):
+    """Context handle rebuilt from a checkpoint file, in the saved state."""
+    h = C.c_void_p()
+    _check(load_library().lsm_load(os.fsencode(path), stream, C.byref(h)))
+    return h
+
+
 def lsm_counters(h):
     st, su, kl = C.c_int64(), C.c_int64(), C.c_int64()
     _check(load_library().lsm_counters(h, C.byref(st), C.byref(su), C.byref(kl)), h)
@@ -315,6 +329,13 @@ class Specimen:
     @classmethod
     def from_network(cls, X, si, sj, k, r0, rc2, **kw):
         return cls(lsm_build_network(X, si, sj, k, r0, rc2, **kw))
+
+    @classmethod
+    def load(cls, path, stream=None):
+        return cls(lsm_load(path, stream))
+
+    def save(self, path):
+        lsm_save(self.h, path)
 
     def close(self):
         if self.h is not None and self.h.value:
