@@ -87,6 +87,17 @@ lsm_status lsm_nn_conv_forward(const void *in, int32_t in_cs, int32_t in_c0, int
                                const float *bias, void *out, int32_t out_cs, int32_t out_c0, int32_t Cout, int32_t B,
                                int32_t H, int32_t Wd, int32_t taps, int32_t relu, void *stream);
 
+/* Fault injection and diagnostics: the number of polls after which a bounded
+ * mbarrier wait of the tensor-core convolution's pipeline gives up (0: at
+ * once; < 0 restores the default, 2^20, about a second at most). A
+ * convolution that gives up waits for the copies and MMAs it has issued
+ * (bounded by the default limit), frees its tensor memory, leaves its output
+ * incomplete and makes the call that launched it return LSM_ETIMEOUT once;
+ * the next call runs normally. Tests set 0 to exercise that path without a
+ * GPU fault. Applies to later launches (stream-ordered on `stream`, then
+ * synchronised). */
+lsm_status lsm_nn_set_wait_limit(int32_t polls, void *stream);
+
 /* dW[n][tap][ci] = sum_p grad[p][n] in[p shifted by tap][ci], db[n] = sum_p
  * grad[p][n] (db may be NULL); grad dense NHWC bf16 [B][H][W][Cout];
  * scratch: device fp32 workspace of scratch_floats (>= Cout * taps * Cin). */

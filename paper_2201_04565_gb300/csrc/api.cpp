@@ -88,7 +88,7 @@ lsm_status ensure_sample_room(Ctx *c)
     if (c->nsamples < c->sample_cap) return LSM_OK;
     int64_t cap = c->sample_cap * 2;
     lsm::DeviceSample *ns = nullptr;
-    cudaError_t e = cudaMalloc((void **)&ns, cap * sizeof(lsm::DeviceSample));
+    cudaError_t e = lsm::dev_malloc((void **)&ns, cap * sizeof(lsm::DeviceSample));
     if (e != cudaSuccess) return fail(c, LSM_ENOMEM, "sample buffer growth failed");
     e = cudaMemcpyAsync(ns, c->samples, c->sample_cap * sizeof(lsm::DeviceSample),
                         cudaMemcpyDeviceToDevice, c->stream);
@@ -113,6 +113,7 @@ extern "C" {
 
 lsm_status lsm_build_from_image(const lsm_desc *desc, lsm_ctx **out)
 {
+    lsm::NvtxRange nvtx_("lsm_build_from_image");
     if (!desc || !out) return fail(nullptr, LSM_EINVAL, "desc and out are required");
     *out = nullptr;
     if (desc->precision < LSM_PREC_EXACT64 || desc->precision > LSM_PREC_DF)
@@ -140,6 +141,7 @@ lsm_status lsm_build_from_image(const lsm_desc *desc, lsm_ctx **out)
 
 lsm_status lsm_build_network(const lsm_net_desc *desc, lsm_ctx **out)
 {
+    lsm::NvtxRange nvtx_("lsm_build_network");
     if (!desc || !out) return fail(nullptr, LSM_EINVAL, "desc and out are required");
     *out = nullptr;
     if (desc->precision < LSM_PREC_EXACT64 || desc->precision > LSM_PREC_DF)
@@ -202,6 +204,7 @@ static void drop_graphs(lsm_ctx *c)
 
 lsm_status lsm_apply_strain(lsm_ctx *c, double eps)
 {
+    lsm::NvtxRange nvtx_("lsm_apply_strain");
     if (!c) return fail(nullptr, LSM_EINVAL, "null context");
     if (!(1.0 + eps > 0.0) || !std::isfinite(eps))
         return fail(c, LSM_EINVAL, "strain must be finite with 1 + eps > 0");
@@ -230,6 +233,7 @@ lsm_status lsm_set_strain_rate(lsm_ctx *c, double rate)
 
 lsm_status lsm_step(lsm_ctx *c, int64_t nsteps)
 {
+    lsm::NvtxRange nvtx_("lsm_step");
     if (!c) return fail(nullptr, LSM_EINVAL, "null context");
     if (nsteps < 1) return fail(c, LSM_EINVAL, "nsteps must be >= 1");
     if (nsteps > 100000) return fail(c, LSM_EINVAL, "nsteps per call is limited to 100000");
@@ -246,6 +250,7 @@ lsm_status lsm_step(lsm_ctx *c, int64_t nsteps)
 lsm_status lsm_relax(lsm_ctx *c, double tol, int64_t max_steps, int64_t check_every,
                      int64_t *taken)
 {
+    lsm::NvtxRange nvtx_("lsm_relax");
     if (!c) return fail(nullptr, LSM_EINVAL, "null context");
     if (!(tol >= 0) || max_steps < 0 || check_every < 1 || check_every > 100000)
         return fail(c, LSM_EINVAL, "need tol >= 0, max_steps >= 0, 1 <= check_every <= 100000");
@@ -326,6 +331,7 @@ lsm_status lsm_stress_strain(lsm_ctx *c, double *eps, double *sigma, int64_t cap
 lsm_status lsm_broken_mask(lsm_ctx *c, uint8_t *out, int64_t cap, int64_t *m,
                            int64_t *first_break_step)
 {
+    lsm::NvtxRange nvtx_("lsm_broken_mask");
     if (!c) return fail(nullptr, LSM_EINVAL, "null context");
     if (!out || cap < c->m) return fail(c, LSM_EINVAL, "output buffer smaller than the spring count");
     lsm_status st = device_status(c);
@@ -367,6 +373,7 @@ lsm_status lsm_break_steps(lsm_ctx *c, int64_t *out, int64_t cap)
 
 lsm_status lsm_get_state(lsm_ctx *c, double *x, double *v)
 {
+    lsm::NvtxRange nvtx_("lsm_get_state");
     if (!c) return fail(nullptr, LSM_EINVAL, "null context");
     lsm_status st = device_status(c);
     if (st != LSM_OK) return st;
@@ -396,6 +403,7 @@ lsm_status lsm_get_state(lsm_ctx *c, double *x, double *v)
 
 lsm_status lsm_set_state(lsm_ctx *c, const double *x, const double *v)
 {
+    lsm::NvtxRange nvtx_("lsm_set_state");
     if (!c) return fail(nullptr, LSM_EINVAL, "null context");
     const size_t bytes = (size_t)c->dim * c->n * sizeof(double);
     cudaError_t e = cudaSuccess;
@@ -448,6 +456,7 @@ lsm_status lsm_topology(lsm_ctx *c, int32_t *si, int32_t *sj, double *k, double 
 
 lsm_status lsm_observe(lsm_ctx *c, lsm_sample *out)
 {
+    lsm::NvtxRange nvtx_("lsm_observe");
     if (!c || !out) return fail(c, LSM_EINVAL, "null argument");
     cudaError_t e = lsm::launch_observe(*c, c->scratch_sample);
     if (e == cudaSuccess)
@@ -459,6 +468,7 @@ lsm_status lsm_observe(lsm_ctx *c, lsm_sample *out)
 
 lsm_status lsm_fields(lsm_ctx *c, double cell_volume, double *stress, double *strain)
 {
+    lsm::NvtxRange nvtx_("lsm_fields");
     if (!c) return fail(nullptr, LSM_EINVAL, "null context");
     lsm_status st = device_status(c);
     if (st != LSM_OK) return st;
@@ -487,6 +497,7 @@ lsm_status lsm_synchronize(lsm_ctx *c)
 
 lsm_status lsm_save(lsm_ctx *c, const char *path)
 {
+    lsm::NvtxRange nvtx_("lsm_save");
     if (!c) return fail(nullptr, LSM_EINVAL, "null context");
     if (!path) return fail(c, LSM_EINVAL, "null path");
     lsm_status st = device_status(c);
@@ -505,6 +516,7 @@ lsm_status lsm_save(lsm_ctx *c, const char *path)
 
 lsm_status lsm_load(const char *path, void *stream, lsm_ctx **out)
 {
+    lsm::NvtxRange nvtx_("lsm_load");
     if (!path || !out) return fail(nullptr, LSM_EINVAL, "path and out are required");
     *out = nullptr;
     lsm_ctx *c = new (std::nothrow) lsm_ctx();

@@ -281,7 +281,7 @@ __global__ void k_batch_set_eps(SpecDesc *specs, const double *eps2, int S)
 template <typename T>
 static cudaError_t balloc(T **p, size_t count)
 {
-    return cudaMalloc((void **)p, (count ? count : 1) * sizeof(T));
+    return lsm::dev_malloc((void **)p, (count ? count : 1) * sizeof(T));
 }
 
 // Captured step graphs bake in the tile list, the grid and the buffers; any
@@ -629,7 +629,7 @@ lsm_status grow_samples(lsm_batch *b)
     if (b->nsamples < b->cap) return LSM_OK;
     const int64_t nc = b->cap * 2;
     lsm::DeviceSample *ns = nullptr;
-    cudaError_t e = cudaMalloc((void **)&ns, (size_t)b->S * nc * sizeof(lsm::DeviceSample));
+    cudaError_t e = lsm::dev_malloc((void **)&ns, (size_t)b->S * nc * sizeof(lsm::DeviceSample));
     if (e != cudaSuccess) return bfail(b, LSM_ENOMEM, "sample buffer growth failed");
     e = cudaMemcpy2DAsync(ns, nc * sizeof(lsm::DeviceSample), b->samples, b->cap * sizeof(lsm::DeviceSample),
                           b->cap * sizeof(lsm::DeviceSample), b->S, cudaMemcpyDeviceToDevice, b->stream);
@@ -651,6 +651,7 @@ extern "C" {
 
 lsm_status lsm_build_batch(const lsm_desc *descs, int32_t count, lsm_batch **out)
 {
+    lsm::NvtxRange nvtx_("lsm_build_batch");
     if (!descs || !out || count < 1) return bfail(nullptr, LSM_EINVAL, "descs, out and count >= 1 are required");
     *out = nullptr;
     const lsm_desc &d0 = descs[0];
@@ -767,6 +768,7 @@ lsm_status lsm_batch_set_schedule(lsm_batch *b, int32_t tile_y, int32_t grid, in
 
 lsm_status lsm_batch_apply_strain(lsm_batch *b, const double *eps)
 {
+    lsm::NvtxRange nvtx_("lsm_batch_apply_strain");
     if (!b || !eps) return bfail(b, LSM_EINVAL, "null argument");
     std::vector<double> e2(2 * b->S);
     for (int s = 0; s < b->S; s++) {
@@ -791,6 +793,7 @@ lsm_status lsm_batch_apply_strain(lsm_batch *b, const double *eps)
 
 lsm_status lsm_batch_step(lsm_batch *b, int64_t nsteps)
 {
+    lsm::NvtxRange nvtx_("lsm_batch_step");
     if (!b) return bfail(nullptr, LSM_EINVAL, "null batch");
     if (nsteps < 1 || nsteps > 100000) return bfail(b, LSM_EINVAL, "nsteps must be in 1..100000");
     lsm_status st = grow_samples(b);
@@ -809,6 +812,7 @@ lsm_status lsm_batch_step(lsm_batch *b, int64_t nsteps)
 lsm_status lsm_batch_relax(lsm_batch *b, double tol, int64_t max_steps, int64_t check_every, int64_t *taken,
                            int32_t *converged)
 {
+    lsm::NvtxRange nvtx_("lsm_batch_relax");
     if (!b) return bfail(nullptr, LSM_EINVAL, "null batch");
     if (!(tol >= 0) || max_steps < 1 || check_every < 1 || check_every > 100000)
         return bfail(b, LSM_EINVAL, "need tol >= 0, max_steps >= 1, 1 <= check_every <= 100000");
@@ -952,7 +956,7 @@ lsm_status lsm_batch_broken_mask(lsm_batch *b, int32_t spec, uint8_t *out, int64
     if (b->export_cap < b->m[spec]) {
         if (b->export_buf) cudaFree(b->export_buf);
         b->export_buf = nullptr;
-        e = cudaMalloc((void **)&b->export_buf, b->m[spec] ? b->m[spec] : 1);
+        e = lsm::dev_malloc((void **)&b->export_buf, b->m[spec] ? b->m[spec] : 1);
         if (e != cudaSuccess) return bfail(b, LSM_ENOMEM, "export buffer");
         b->export_cap = b->m[spec];
     }
@@ -992,6 +996,7 @@ static bool uniform_size(lsm_batch *b, int32_t H, int32_t W)
 
 lsm_status lsm_batch_fields(lsm_batch *b, float *u, uint8_t *phase, int32_t H, int32_t W)
 {
+    lsm::NvtxRange nvtx_("lsm_batch_fields");
     if (!b || !u) return bfail(b, LSM_EINVAL, "null argument");
     if (!uniform_size(b, H, W)) return bfail(b, LSM_EINVAL, "every specimen must be H x W");
     const unsigned grid = (unsigned)std::min<int64_t>(b->T, 152 * 16);
@@ -1004,6 +1009,7 @@ lsm_status lsm_batch_fields(lsm_batch *b, float *u, uint8_t *phase, int32_t H, i
 
 lsm_status lsm_batch_add_displacements(lsm_batch *b, const float *du, int32_t H, int32_t W)
 {
+    lsm::NvtxRange nvtx_("lsm_batch_add_displacements");
     if (!b || !du) return bfail(b, LSM_EINVAL, "null argument");
     if (!uniform_size(b, H, W)) return bfail(b, LSM_EINVAL, "every specimen must be H x W");
     const unsigned grid = (unsigned)std::min<int64_t>(b->T, 152 * 16);
@@ -1018,6 +1024,7 @@ lsm_status lsm_batch_add_displacements(lsm_batch *b, const float *du, int32_t H,
 lsm_status lsm_batch_autotune(lsm_batch *b, int32_t steps_per_trial, int32_t *tile_y, int32_t *grid, int32_t *order,
                               double *ms_per_step)
 {
+    lsm::NvtxRange nvtx_("lsm_batch_autotune");
     if (!b) return bfail(nullptr, LSM_EINVAL, "null batch");
     if (steps_per_trial < 1 || steps_per_trial > 1000) return bfail(b, LSM_EINVAL, "steps_per_trial in 1..1000");
     // save the state the trials will advance
@@ -1029,7 +1036,7 @@ lsm_status lsm_batch_autotune(lsm_batch *b, int32_t steps_per_trial, int32_t *ti
     std::vector<unsigned long long> fb0(b->S), nb0(b->S);
     cudaError_t e = cudaSuccess;
     for (int q = 0; q < 7 && e == cudaSuccess; q++) {
-        e = cudaMalloc(&bk[q], sz[q]);
+        e = lsm::dev_malloc(&bk[q], sz[q]);
         if (e == cudaSuccess) e = cudaMemcpyAsync(bk[q], src[q], sz[q], cudaMemcpyDeviceToDevice, b->stream);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(sd0.data(), b->specs, b->S * sizeof(lsm::SpecDesc), cudaMemcpyDeviceToHost, b->stream);

@@ -346,7 +346,7 @@ cudaError_t checkpoint_restore(Ctx &c, const CkptState &s, std::string &err)
         int64_t cap = c.sample_cap > 0 ? c.sample_cap : 1024;
         while (cap < s.nsamples) cap *= 2;
         DeviceSample *ns = nullptr;
-        e = cudaMalloc((void **)&ns, (size_t)cap * sizeof(DeviceSample));
+        e = lsm::dev_malloc((void **)&ns, (size_t)cap * sizeof(DeviceSample));
         if (e != cudaSuccess) return e;
         e = cudaStreamSynchronize(st);
         cudaFree(c.samples);

@@ -315,11 +315,11 @@ cudaError_t fixcsr_upload(Ctx &c)
     for (int64_t p = 0; p < n; p++) im[p] = 1.0 / h.mass[p];
     const size_t fsz = c.h.precision == LSM_PREC_F32 ? sizeof(float) : sizeof(ff);
     cudaError_t e;
-    if ((e = cudaMalloc((void **)&c.xf, (dn ? dn : 1) * sizeof(long long))) != cudaSuccess) return e;
-    if ((e = cudaMalloc((void **)&c.sdir, m ? m : 1)) != cudaSuccess) return e;
-    if ((e = cudaMalloc((void **)&c.imass, (n ? n : 1) * sizeof(double))) != cudaSuccess) return e;
-    if ((e = cudaMalloc((void **)&c.tdf, (tdf.size() ? tdf.size() : 1) * sizeof(TypeDF))) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&c.fsx, (size_t)h.dim * (m ? m : 1) * fsz)) != cudaSuccess) return e;
+    if ((e = lsm::dev_malloc((void **)&c.xf, (dn ? dn : 1) * sizeof(long long))) != cudaSuccess) return e;
+    if ((e = lsm::dev_malloc((void **)&c.sdir, m ? m : 1)) != cudaSuccess) return e;
+    if ((e = lsm::dev_malloc((void **)&c.imass, (n ? n : 1) * sizeof(double))) != cudaSuccess) return e;
+    if ((e = lsm::dev_malloc((void **)&c.tdf, (tdf.size() ? tdf.size() : 1) * sizeof(TypeDF))) != cudaSuccess) return e;
+    if ((e = lsm::dev_malloc(&c.fsx, (size_t)h.dim * (m ? m : 1) * fsz)) != cudaSuccess) return e;
     cudaStream_t st = c.stream;
     if (m && (e = cudaMemcpyAsync(c.sdir, h.sdir.data(), m, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
     if ((e = cudaMemcpyAsync(c.imass, im.data(), n * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;

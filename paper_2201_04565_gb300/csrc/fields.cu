@@ -184,7 +184,7 @@ __global__ void k_fields_compact(int64_t n, int64_t np, int dim, const int64_t *
 template <typename T>
 cudaError_t up(T **dst, const T *src, size_t count, cudaStream_t st)
 {
-    cudaError_t e = cudaMalloc((void **)dst, (count ? count : 1) * sizeof(T));
+    cudaError_t e = lsm::dev_malloc((void **)dst, (count ? count : 1) * sizeof(T));
     if (e != cudaSuccess || !count) return e;
     return cudaMemcpyAsync(*dst, src, count * sizeof(T), cudaMemcpyHostToDevice, st);
 }
@@ -211,7 +211,7 @@ cudaError_t fields_compute(Ctx &c, double cell)
     cudaStream_t st = c.stream;
     cudaError_t e;
     if (!c.fout) {
-        if ((e = cudaMalloc((void **)&c.fout, (size_t)2 * nq * (n ? n : 1) * sizeof(double))) != cudaSuccess) return e;
+        if ((e = lsm::dev_malloc((void **)&c.fout, (size_t)2 * nq * (n ? n : 1) * sizeof(double))) != cudaSuccess) return e;
         if ((e = up(&c.fX, h.X.data(), (size_t)h.dim * n, st)) != cudaSuccess) return e;
         if (c.tile) {
             // spring lists and the incidence CSR, built here once
@@ -234,8 +234,8 @@ cudaError_t fields_compute(Ctx &c, double cell)
             if ((e = up(&c.fstype, h.stype.data(), h.stype.size(), st)) != cudaSuccess) return e;
             if ((e = up(&c.fmass, h.mass.data(), h.mass.size(), st)) != cudaSuccess) return e;
             if ((e = up(&c.fpix, h.pix.data(), h.pix.size(), st)) != cudaSuccess) return e;
-            if ((e = cudaMalloc((void **)&c.fx, (size_t)h.dim * (n ? n : 1) * sizeof(double))) != cudaSuccess) return e;
-            if ((e = cudaMalloc((void **)&c.fv, (size_t)h.dim * (n ? n : 1) * sizeof(double))) != cudaSuccess) return e;
+            if ((e = lsm::dev_malloc((void **)&c.fx, (size_t)h.dim * (n ? n : 1) * sizeof(double))) != cudaSuccess) return e;
+            if ((e = lsm::dev_malloc((void **)&c.fv, (size_t)h.dim * (n ? n : 1) * sizeof(double))) != cudaSuccess) return e;
             // the host vectors above must outlive their copies
             if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
         }

@@ -375,7 +375,7 @@ const char *last_fail_site() { return g_fail_site; }
 template <typename T>
 static cudaError_t dalloc(T **p, size_t count)
 {
-    return cudaMalloc((void **)p, (count ? count : 1) * sizeof(T));
+    return lsm::dev_malloc((void **)p, (count ? count : 1) * sizeof(T));
 }
 
 void free_device(Ctx &c)

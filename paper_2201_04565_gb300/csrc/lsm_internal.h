@@ -17,13 +17,39 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstdlib>
 #include <map>
 #include <string>
 #include <vector>
 
 #include "../../include/lsm.h"
+#include "nvtx_range.h"
 
 namespace lsm {
+
+// Every device allocation of the library. LSM_MAX_ALLOC_BYTES (environment,
+// bytes; unset or 0 = no limit) caps a single allocation: larger requests
+// fail as if the device were out of memory, which exercises the error and
+// clean-up paths of builds without exhausting a real device (fault
+// injection for tests).
+inline cudaError_t dev_malloc_bytes(void **p, size_t bytes)
+{
+    const char *cap = std::getenv("LSM_MAX_ALLOC_BYTES");
+    if (cap && *cap) {
+        const unsigned long long lim = std::strtoull(cap, nullptr, 10);
+        if (lim > 0 && bytes > lim) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
+template <typename T>
+inline cudaError_t dev_malloc(T **p, size_t bytes)
+{
+    return dev_malloc_bytes((void **)p, bytes);
+}
 
 struct SpringType {
     double k, r0, rc2, kr0;

@@ -30,6 +30,7 @@
 
 #include "../../include/lsm_nn.h"
 #include "nn_internal.h"
+#include "nvtx_range.h"
 
 namespace lsm {
 namespace nn {
@@ -89,13 +90,17 @@ __device__ __forceinline__ int swz(int row, int chunk) { return row * 32 + ((chu
 // and a stage is refilled only after its barrier reports those MMAs done.
 // The epilogue reads the accumulator back with tcgen05.ld (each warp its 32
 // lanes), adds the bias, applies the ReLU and stores BF16. Every mbarrier
-// wait is bounded: on expiry the CTA raises g_conv_timeout, skips the
-// epilogue, frees its TMEM and returns; later CTAs return at once.
+// wait is bounded (g_conv_wait_limit polls, one thread per CTA, its result
+// shared through a barrier so that the CTA decides as one): on expiry the CTA
+// raises g_conv_timeout, waits for its copies and (bounded again, with the
+// default limit) for the MMAs it has issued, skips the epilogue, frees its
+// TMEM and returns; later CTAs return at once.
 
 __device__ int g_conv_timeout;
 
 constexpr int TCM = 128, TCK = 32;
 constexpr int TC_WAIT = 1 << 20;
+__device__ int g_conv_wait_limit = TC_WAIT;
 
 // shared-memory matrix descriptor (no swizzle; K-major core matrices; LBO
 // = stride between core matrices along K, SBO = along M or N)
@@ -111,10 +116,10 @@ __host__ __device__ constexpr unsigned tc_idesc(int m, int n)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(m >> 4) << 24);
 }
 
-__device__ __forceinline__ bool tc_wait(unsigned bar, unsigned parity)
+__device__ __forceinline__ bool tc_wait(unsigned bar, unsigned parity, int limit)
 {
     unsigned done = 0;
-    for (int it = 0; it < TC_WAIT && !done; it++)
+    for (int it = 0; it < limit && !done; it++)
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
             : "=r"(done)
@@ -184,14 +189,19 @@ k_conv_fwd(const bf16 *__restrict__ in, int in_cs, int in_c0, int Cin, const bf1
         }
     };
 
+    const int limit = g_conv_wait_limit;
     bool ok = true;
+    int last = -1;  // last chunk whose MMAs were committed
     load(0, 0);
     cp_commit();
     for (int kt = 0; kt < KT && ok; kt++) {
         const int buf = kt & 1;
         if (kt + 1 < KT) {
             const int nb = (kt + 1) & 1;
-            if (kt >= 1) ok = tc_wait(smem_u32(&mbar[nb]), (unsigned)(((kt - 1) >> 1) & 1));  // chunk kt-1's MMAs
+            if (kt >= 1) {  // chunk kt-1's MMAs, which read stage nb
+                const bool w = tid != 0 || tc_wait(smem_u32(&mbar[nb]), (unsigned)(((kt - 1) >> 1) & 1), limit);
+                ok = __syncthreads_and(w) != 0;
+            }
             if (!ok) break;
             load(kt + 1, nb);
         }
@@ -215,11 +225,22 @@ k_conv_fwd(const bf16 *__restrict__ in, int in_cs, int in_c0, int Cin, const bf1
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(&mbar[buf])));
         }
+        last = kt;
     }
     // the last commit covers every earlier MMA of this thread
-    if (ok && KT > 0) ok = tc_wait(smem_u32(&mbar[(KT - 1) & 1]), (unsigned)(((KT - 1) >> 1) & 1));
+    if (ok && KT > 0) {
+        const bool w = tid != 0 || tc_wait(smem_u32(&mbar[(KT - 1) & 1]), (unsigned)(((KT - 1) >> 1) & 1), limit);
+        ok = __syncthreads_and(w) != 0;
+    }
     if (!ok) {
-        if (tid == 0) atomicOr(&g_conv_timeout, 1);
+        // gave up: no copy into shared memory and no MMA into tensor memory
+        // may still be running when the CTA frees them
+        cp_wait<0>();
+        if (tid == 0) {
+            atomicOr(&g_conv_timeout, 1);
+            if (last >= 0) tc_wait(smem_u32(&mbar[last & 1]), (unsigned)((last >> 1) & 1), TC_WAIT);
+        }
+        __syncthreads();
     } else {
         asm volatile("tcgen05.fence::after_thread_sync;");
         const int mo = m0 + 32 * warp + lane;
@@ -280,6 +301,19 @@ cudaError_t conv_timeout(bool *flag, cudaStream_t st)
     cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_conv_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     *flag = v != 0;
+    if (e == cudaSuccess && v) {  // reported once; later convolutions run again
+        const int zero = 0;
+        e = cudaMemcpyToSymbolAsync(g_conv_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    return e;
+}
+
+cudaError_t conv_set_wait_limit(int polls, cudaStream_t st)
+{
+    const int v = polls >= 0 ? polls : TC_WAIT;
+    cudaError_t e = cudaMemcpyToSymbolAsync(g_conv_wait_limit, &v, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e;
 }
 
@@ -1071,6 +1105,7 @@ lsm_status lsm_unet_set_params(lsm_unet *u, const float *host, int64_t n)
 
 lsm_status lsm_unet_forward(lsm_unet *u, const void *in, float *out, int32_t batch)
 {
+    lsm::NvtxRange nvtx_("lsm_unet_forward");
     if (!batch_ok(u, batch) || !in || !out) return nfail(u, LSM_EINVAL, "bad arguments");
     cudaError_t e = lsm::nn::unet_forward(*u, batch, (const lsm::nn::bf16 *)in);
     if (e == cudaSuccess)
@@ -1090,6 +1125,7 @@ static lsm_status conv_status(lsm_unet *u, cudaStream_t st = nullptr)
 lsm_status lsm_unet_gradients(lsm_unet *u, const void *in, const float *target, int32_t batch, float *loss,
                               float *grad)
 {
+    lsm::NvtxRange nvtx_("lsm_unet_gradients");
     if (!batch_ok(u, batch) || !in || !target) return nfail(u, LSM_EINVAL, "bad arguments");
     cudaError_t e = lsm::nn::unet_forward(*u, batch, (const lsm::nn::bf16 *)in);
     if (e == cudaSuccess) e = lsm::nn::unet_backward(*u, batch, target);
@@ -1102,6 +1138,7 @@ lsm_status lsm_unet_gradients(lsm_unet *u, const void *in, const float *target, 
 
 lsm_status lsm_unet_train_step(lsm_unet *u, const void *in, const float *target, int32_t batch, float lr, float *loss)
 {
+    lsm::NvtxRange nvtx_("lsm_unet_train_step");
     if (!batch_ok(u, batch) || !in || !target || !(lr > 0)) return nfail(u, LSM_EINVAL, "bad arguments");
     cudaError_t e = lsm::nn::unet_forward(*u, batch, (const lsm::nn::bf16 *)in);
     if (e == cudaSuccess) e = lsm::nn::unet_backward(*u, batch, target);
@@ -1117,6 +1154,7 @@ lsm_status lsm_unet_train_step(lsm_unet *u, const void *in, const float *target,
 lsm_status lsm_unet_prepare_input(const uint8_t *phase, const float *u, const float *eps, float deps, int32_t S,
                                   int32_t H, int32_t W, double a, void *in, void *stream)
 {
+    lsm::NvtxRange nvtx_("lsm_unet_prepare_input");
     if (!phase || !u || !eps || !in || S < 1 || H < 1 || W < 1 || !(deps != 0.0f))
         return nfail(nullptr, LSM_EINVAL, "prepare_input: bad arguments");
     const int64_t n = (int64_t)S * H * W;
@@ -1162,6 +1200,13 @@ lsm_status lsm_nn_conv_forward(const void *in, int32_t in_cs, int32_t in_c0, int
         return nfail(nullptr, e == cudaErrorInvalidValue ? LSM_EINVAL : LSM_ECUDA,
                      std::string("conv_forward: ") + cudaGetErrorString(e));
     return conv_status(nullptr, (cudaStream_t)stream);
+}
+
+lsm_status lsm_nn_set_wait_limit(int32_t polls, void *stream)
+{
+    const cudaError_t e = lsm::nn::conv_set_wait_limit(polls, (cudaStream_t)stream);
+    if (e != cudaSuccess) return nfail(nullptr, LSM_ECUDA, std::string("set_wait_limit: ") + cudaGetErrorString(e));
+    return LSM_OK;
 }
 
 lsm_status lsm_nn_conv_wgrad(const void *grad, int32_t Cout, const void *in, int32_t in_cs, int32_t in_c0, int32_t Cin,

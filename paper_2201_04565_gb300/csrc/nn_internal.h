@@ -20,9 +20,14 @@ typedef __nv_bfloat16 bf16;
 cudaError_t conv_fwd(const bf16 *in, int in_cs, int in_c0, int Cin, const bf16 *W, const float *bias, bf16 *out,
                      int out_cs, int out_c0, int Cout, int B, int H, int Wd, int taps, bool relu, cudaStream_t st);
 
-// Whether a tensor-core convolution gave up a bounded wait since the library
-// loaded (the affected outputs are incomplete). Synchronises the stream.
+// Whether a tensor-core convolution gave up a bounded wait since the last
+// query (the affected outputs are incomplete); clears the flag. Synchronises
+// the stream.
 cudaError_t conv_timeout(bool *flag, cudaStream_t st);
+
+// Polls of each bounded mbarrier wait in the tensor-core convolution
+// (0: give up at once; < 0: the default, 2^20).
+cudaError_t conv_set_wait_limit(int polls, cudaStream_t st);
 
 // dW[n][tap][ci] (+= over pixel splits, then folded in a fixed order) and
 // db[n] from grad_pre (gradient at the conv output before activation).

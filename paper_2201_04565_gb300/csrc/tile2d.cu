@@ -86,11 +86,11 @@ cudaError_t tile_export(Ctx &c, bool steps)
     if (c.dim == 3) return tile3_export(c, steps);
     if (c.m == 0) return cudaSuccess;
     if (!c.texport) {
-        cudaError_t e = cudaMalloc((void **)&c.texport, c.m);
+        cudaError_t e = lsm::dev_malloc((void **)&c.texport, c.m);
         if (e != cudaSuccess) return e;
     }
     if (steps && !c.texport_brk) {
-        cudaError_t e = cudaMalloc((void **)&c.texport_brk, c.m * sizeof(long long));
+        cudaError_t e = lsm::dev_malloc((void **)&c.texport_brk, c.m * sizeof(long long));
         if (e != cudaSuccess) return e;
     }
     const unsigned g = (unsigned)((c.tnp + 255) / 256);

@@ -458,7 +458,7 @@ ff split_ff3(double v)
 template <typename T>
 cudaError_t dal(T **p, size_t count)
 {
-    return cudaMalloc((void **)p, (count ? count : 1) * sizeof(T));
+    return lsm::dev_malloc((void **)p, (count ? count : 1) * sizeof(T));
 }
 
 }  // namespace
@@ -583,11 +583,11 @@ cudaError_t tile3_export(Ctx &c, bool steps)
 {
     if (c.m == 0) return cudaSuccess;
     if (!c.texport) {
-        cudaError_t e = cudaMalloc((void **)&c.texport, c.m);
+        cudaError_t e = lsm::dev_malloc((void **)&c.texport, c.m);
         if (e != cudaSuccess) return e;
     }
     if (steps && !c.texport_brk) {
-        cudaError_t e = cudaMalloc((void **)&c.texport_brk, c.m * sizeof(long long));
+        cudaError_t e = lsm::dev_malloc((void **)&c.texport_brk, c.m * sizeof(long long));
         if (e != cudaSuccess) return e;
     }
     const unsigned g = (unsigned)((c.tnp + 255) / 256);

@@ -29,6 +29,7 @@ SIGNATURES = [
                                       _I32, _I32, _P]),
     ("lsm_nn_conv_wgrad", C.c_int, [_P, _I32, _P, _I32, _I32, _I32, _I32, _I32, _I32, _I32, _P, _P, _P, _I64,
                                     _P]),
+    ("lsm_nn_set_wait_limit", C.c_int, [_I32, _P]),
     ("lsm_batch_fields", C.c_int, [_P, _P, _P, _I32, _I32]),
     ("lsm_batch_add_displacements", C.c_int, [_P, _P, _I32, _I32]),
 ]

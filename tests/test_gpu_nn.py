@@ -56,6 +56,40 @@ def test_conv_forward_matches_reference(env, cin, cout, taps, relu):
     assert np.all(err <= 2 ** -7 * np.abs(ref) + 1e-6 * np.abs(ref).max())
 
 
+def test_conv_wait_timeout_is_reported_and_recovers(env):
+    """Fault injection without a GPU fault: with a wait limit of 0 polls the
+    tensor-core convolution's first bounded mbarrier wait gives up at once;
+    the CTA drains the MMAs it issued, frees its tensor memory and the call
+    returns LSM_ETIMEOUT. At the default limit the next call on the same
+    buffers computes the right result."""
+    torch, nn = env
+    from paper_2201_04565_gb300 import lsm
+    rng = np.random.default_rng(3)
+    B, H, W, cin, cout = 2, 16, 16, 64, 64
+    x = R.bf16(rng.standard_normal((B, H, W, cin)))
+    Wt = R.bf16(0.2 * rng.standard_normal((cout, 9, cin)))
+    b = rng.standard_normal(cout).astype(np.float32).astype(np.float64)
+    out = torch.zeros((B, H, W, cout), dtype=torch.bfloat16, device="cuda")
+    tb = torch.from_numpy(b.astype(np.float32)).cuda()
+    tx, tw = _bf(torch, x), _bf(torch, Wt)
+    L = nn.lib()
+
+    def run():
+        return L.lsm_nn_conv_forward(nn.ptr(tx), cin, 0, cin, nn.ptr(tw), nn.ptr(tb), nn.ptr(out), cout, 0,
+                                     cout, B, H, W, 9, 0, None)
+
+    nn.check(L.lsm_nn_set_wait_limit(0, None))
+    try:
+        assert run() == lsm.LSM_ETIMEOUT
+    finally:
+        nn.check(L.lsm_nn_set_wait_limit(-1, None))
+    nn.check(run())
+    torch.cuda.synchronize()
+    got = out.float().cpu().numpy().astype(np.float64)
+    ref = R.bf16(R.conv(x, Wt.reshape(cout, 3, 3, cin), b))
+    assert np.all(np.abs(got - ref) <= 2 ** -7 * np.abs(ref) + 1e-6 * np.abs(ref).max())
+
+
 @pytest.mark.parametrize("cin,cout,taps", [(64, 64, 9), (32, 256, 9), (96, 32, 1)])
 def test_conv_wgrad_matches_reference(env, cin, cout, taps):
     torch, nn = env
