@@ -422,17 +422,26 @@ def _config_2d(n, m, dim, precision, world):
                   % (algorithmic_bytes(n, m, dim) / 1e6)}
 
 
-def run_oracle_sample(budget_s=12.0, threads=1):
-    """The FP64 CPU oracle on the same workload: one strain increment, then as
-    many time steps as fit in about budget_s seconds, on `threads` host
-    threads (the oracle's threaded spring pass gives the same bits)."""
+def run_oracle_sample(budget_s=12.0, threads=1, foam=False):
+    """The FP64 CPU oracle on the same workload (the 2048 x 2048 composite, or
+    with foam=True the 256^3 foam): one strain increment, then as many time
+    steps as fit in about budget_s seconds, on `threads` host threads (the
+    oracle's threaded spring pass gives the same bits)."""
     import oracle
     oracle.build_oracle()
-    img = inclusion_image(WORKLOAD["nx"], WORKLOAD["ny"], *WORKLOAD["r"], WORKLOAD["frac"], WORKLOAD["seed"])
-    k, e, m = two_phase_materials()
-    o = oracle.Oracle.from_image(img, k, e, m, dt=WORKLOAD["dt"], damping=WORKLOAD["damping"])
+    if foam:
+        from gen.images import foam_volume, one_phase_materials
+        img = foam_volume(256, 4.0, 0.35, seed=2)
+        k, e, m = one_phase_materials(1.0, 0.04)
+        o = oracle.Oracle.from_image(img, k, e, m, dt=0.01, damping=0.1, grip_mode=1)
+        eps, what = -1e-3, "256^3 foam"
+    else:
+        img = inclusion_image(WORKLOAD["nx"], WORKLOAD["ny"], *WORKLOAD["r"], WORKLOAD["frac"], WORKLOAD["seed"])
+        k, e, m = two_phase_materials()
+        o = oracle.Oracle.from_image(img, k, e, m, dt=WORKLOAD["dt"], damping=WORKLOAD["damping"])
+        eps, what = WORKLOAD["eps_inc"], "2048x2048"
     used = o.set_threads(threads)
-    o.apply_strain(WORKLOAD["eps_inc"])
+    o.apply_strain(eps)
     t0 = time.perf_counter()
     o.step(1)
     one = time.perf_counter() - t0
@@ -441,17 +450,17 @@ def run_oracle_sample(budget_s=12.0, threads=1):
     o.step(nsteps)
     dt = time.perf_counter() - t0
     return {"value": o.m * nsteps / dt, "unit": UNIT, "cores": used, "kind": "oracle",
-            "sample": "%d time steps of the full 2048x2048 workload after one 1e-3 strain increment "
-                      "(plain C FP64 oracle, %d host thread%s)" % (nsteps, used, "" if used == 1 else "s"),
+            "sample": "%d time steps of the full %s workload after one %g strain increment "
+                      "(plain C FP64 oracle, %d host thread%s)" % (nsteps, what, eps, used, "" if used == 1 else "s"),
             "seconds": dt, "steps": nsteps, "n": o.n, "m": o.m}
 
 
-def cpu_baseline():
+def cpu_baseline(foam=False):
     """The oracle on all host cores (threaded spring pass), with the
     single-threaded figure beside it."""
     cores = os.cpu_count() or 1
-    out = run_oracle_sample(budget_s=15.0, threads=cores)
-    one = run_oracle_sample(budget_s=10.0, threads=1)
+    out = run_oracle_sample(budget_s=15.0, threads=cores, foam=foam)
+    one = run_oracle_sample(budget_s=10.0, threads=1, foam=foam)
     for q in (out, one):
         q.pop("n")
         q.pop("m")
@@ -506,7 +515,10 @@ def main():
         return 0
     if args.workload == "foam256":
         if rank == 0:
-            print(json.dumps(run_foam256(args)))
+            out = run_foam256(args)
+            if world == 1 and not args.no_cpu_baseline:
+                out["cpu_baseline"] = cpu_baseline(foam=True)
+            print(json.dumps(out))
         if world > 1:
             import torch.distributed as td
             td.destroy_process_group()
