@@ -86,7 +86,7 @@ __device__ __forceinline__ double rate_grip_x(const Tile3Args &A, int gx)
     return __dadd_rn(X, __dmul_rn(eps, __dsub_rn(X, A.xc)));
 }
 
-template <int MODE>
+template <int MODE, bool RATE>
 __device__ __forceinline__ void load_voxel(const Tile3Args &A, int x0, int y0, int z0, int rx, int ry, int rz,
                                            Smem3 &S, bool &over)
 {
@@ -107,7 +107,7 @@ __device__ __forceinline__ void load_voxel(const Tile3Args &A, int x0, int y0, i
                 const bool fixed = grip && (c == 0 || A.grip_mode == 1);
                 if (MODE == T_STEP && !fixed) px[c] = fma(A.dt, A.vh_in[c * A.nv + g], px[c]);
             }
-            if (MODE == T_STEP && grip && A.rate_on) px[0] = rate_grip_x(A, gx);
+            if (RATE && MODE == T_STEP && grip) px[0] = rate_grip_x(A, gx);
         }
     }
 #pragma unroll
@@ -163,7 +163,9 @@ __device__ __forceinline__ bool spring3(const Tile3Args &A, const long long *dl,
     return true;
 }
 
-template <int PREC, int MODE, bool SAMPLE>
+// RATE: constant strain-rate loading (a separate instance, so that the
+// ordinary step carries none of its code)
+template <int PREC, int MODE, bool SAMPLE, bool RATE>
 __global__ void __launch_bounds__(T3N)
 k_tile3d(Tile3Args A)
 {
@@ -193,7 +195,7 @@ k_tile3d(Tile3Args A)
     bool over = false;
     for (int e = tid; e < R3N; e += T3N) {
         const int rx = e % R3X, ry = (e / R3X) % R3Y, rz = e / (R3X * R3Y);
-        load_voxel<MODE>(A, x0, y0, z0, rx, ry, rz, S, over);
+        load_voxel<MODE, RATE>(A, x0, y0, z0, rx, ry, rz, S, over);
     }
     if (over) atomicOr(A.status, 2);
     __syncthreads();
@@ -299,7 +301,7 @@ k_tile3d(Tile3Args A)
             double xr = A.x_in[q];
             const double vh = MODE == T_INIT ? A.v_obs[q] : A.vh_in[q];
             if (MODE == T_STEP && !fixed) xr = fma(A.dt, vh, xr);
-            if (MODE == T_STEP && c == 0 && grip && A.rate_on) xr = rate_grip_x(A, gx);
+            if (RATE && MODE == T_STEP && c == 0 && grip) xr = rate_grip_x(A, gx);
             if (MODE == T_STEP) A.x_out[q] = xr;
             if (fixed) {
                 if (MODE == T_STEP) A.vh_out[q] = 0.0;
@@ -426,10 +428,10 @@ Tile3Args tile3_args(Ctx &c)
     return A;
 }
 
-template <int PREC, int MODE, bool SAMPLE>
+template <int PREC, int MODE, bool SAMPLE, bool RATE>
 cudaError_t launch3(Ctx &c, Tile3Args A)
 {
-    auto kern = k_tile3d<PREC, MODE, SAMPLE>;
+    auto kern = k_tile3d<PREC, MODE, SAMPLE, RATE>;
     static bool configured = false;  // per template instance
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem3));
@@ -445,8 +447,14 @@ cudaError_t launch3(Ctx &c, Tile3Args A)
 template <int MODE, bool SAMPLE>
 cudaError_t launch3_prec(Ctx &c, Tile3Args A)
 {
-    if (c.h.precision == LSM_PREC_F32) return launch3<LSM_PREC_F32, MODE, SAMPLE>(c, A);
-    return launch3<LSM_PREC_DF, MODE, SAMPLE>(c, A);
+    if constexpr (MODE == T_STEP) {
+        if (c.rate_on) {
+            if (c.h.precision == LSM_PREC_F32) return launch3<LSM_PREC_F32, MODE, SAMPLE, true>(c, A);
+            return launch3<LSM_PREC_DF, MODE, SAMPLE, true>(c, A);
+        }
+    }
+    if (c.h.precision == LSM_PREC_F32) return launch3<LSM_PREC_F32, MODE, SAMPLE, false>(c, A);
+    return launch3<LSM_PREC_DF, MODE, SAMPLE, false>(c, A);
 }
 
 ff split_ff3(double v)
