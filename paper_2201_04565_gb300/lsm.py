@@ -227,9 +227,15 @@ def lsm_stress_strain(h):
     return eps, sig
 
 
-def lsm_broken_mask(h):
+def lsm_broken_mask(h, out=None):
+    """Broken flags in canonical spring order and the first break step.
+    out: optional uint8 host array of at least m entries (e.g. page-locked
+    memory reused across calls); a new array otherwise."""
     n, m, _ = lsm_sizes(h)
-    out = np.empty(max(m, 1), np.uint8)
+    if out is None:
+        out = np.empty(max(m, 1), np.uint8)
+    elif out.dtype != np.uint8 or out.ndim != 1 or not out.flags.c_contiguous or out.size < max(m, 1):
+        raise ValueError("out must be a contiguous uint8 array of at least %d entries" % max(m, 1))
     mm, fb = C.c_int64(), C.c_int64()
     _check(load_library().lsm_broken_mask(h, _ptr(out), out.size, C.byref(mm), C.byref(fb)), h)
     return out[:m], fb.value
@@ -369,8 +375,8 @@ class Specimen:
     def stress_strain(self):
         return lsm_stress_strain(self.h)
 
-    def broken(self):
-        return lsm_broken_mask(self.h)
+    def broken(self, out=None):
+        return lsm_broken_mask(self.h, out)
 
     def break_steps(self):
         return lsm_break_steps(self.h)
