@@ -109,10 +109,10 @@ def algorithmic_bytes(n, m, dim):
 NCU_TRAFFIC = {
     # profiles/k_tile2d_step_2d_2048_two_phase.md (DRAM read + write of one
     # time-step launch, ncu, the same 2048 x 2048 workload)
-    "df64": (239.89e6, "826c1ec80efa"),
-    "f32": (238.04e6, "826c1ec80efa"),
-    "fast64": (237.41e6, "826c1ec80efa"),
-    "exact64": (238.16e6, "826c1ec80efa"),
+    "df64": (239.80e6, "023b81ce7d44"),
+    "f32": (237.74e6, "023b81ce7d44"),
+    "fast64": (237.67e6, "023b81ce7d44"),
+    "exact64": (238.63e6, "023b81ce7d44"),
 }
 
 # Warp instructions executed by one time-step launch (ncu smsp__inst_executed.sum,
@@ -121,10 +121,10 @@ NCU_TRAFFIC = {
 # this gives the instruction-issue roofline, the one the fixed-point modes
 # are bound by.
 NCU_INSTRUCTIONS = {
-    "df64": (160383328, "826c1ec80efa"),
-    "f32": (88946351, "826c1ec80efa"),
-    "fast64": (94464248, "826c1ec80efa"),
-    "exact64": (195704900, "826c1ec80efa"),
+    "df64": (160383328, "023b81ce7d44"),
+    "f32": (88946351, "023b81ce7d44"),
+    "fast64": (94464248, "023b81ce7d44"),
+    "exact64": (195704900, "023b81ce7d44"),
 }
 
 # Binding unit of each mode's time-step kernel, from ncu on the same workload
