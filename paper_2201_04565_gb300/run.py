@@ -7,7 +7,8 @@
 
 single: a 2D two-phase inclusion composite (fused tile kernel, or the
 spring-list kernels with --path 1); foam: a 3D one-phase foam under
-compression (spring-list kernels); batch: uneven 2D specimens (sides 32 to
+compression (voxel tile kernel in df64 / f32, spring-list kernels in the FP64
+modes); batch: uneven 2D specimens (sides 32 to
 --max-side) in one batched context; unet: training iterations of the
 warm-start network on random inputs. Each case runs a displacement-controlled
 tension (or compression) test of --increments load increments of --steps time
