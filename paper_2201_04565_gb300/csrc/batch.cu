@@ -27,6 +27,8 @@ struct SpecDesc {
     int64_t pbase;    // first pixel of the specimen in the concatenated grids
     int64_t tbase;    // first tile of the specimen in the tile list
     int64_t ntiles;   // tiles of the specimen
+    int64_t sbase;    // first tile of the specimen in the sample-step tile list
+    int64_t nstiles;  // its tiles there
     double xc, omega, grip_area;
     double eps;       // applied strain
     int cur;          // current ping-pong buffer
@@ -62,6 +64,8 @@ struct BatchCtx {
     int64_t *SBASE = nullptr;
     SpecDesc *specs = nullptr;
     BatchTile *tiles = nullptr;
+    BatchTile *stiles = nullptr;  // 16-row tiles of the sample steps (== tiles when tile_y is 16)
+    int64_t TS = 0;               // tiles in that list (the per-tile partials)
     double *part_s = nullptr, *part_p = nullptr;
     unsigned long long *fb = nullptr, *nb = nullptr;
     int *status = nullptr, *nactive = nullptr;
@@ -150,7 +154,7 @@ k_batch_reduce(SpecDesc *specs, const double *__restrict__ ps, const double *__r
     SpecDesc &sd = specs[s];
     if (relax && !sd.active) return;
     double acc[6] = {0, 0, 0, 0, 0, 0};
-    for (int64_t t = sd.tbase + threadIdx.x; t < sd.tbase + sd.ntiles; t += 256) {
+    for (int64_t t = sd.sbase + threadIdx.x; t < sd.sbase + sd.nstiles; t += 256) {
         acc[0] += ps[t];
         acc[1] += ps[T + t];
         acc[2] += pp[t];
@@ -295,6 +299,8 @@ static void drop_graphs(BatchCtx &b)
 static void batch_free(BatchCtx &b)
 {
     drop_graphs(b);
+    if (b.stiles && b.stiles != b.tiles) cudaFree(b.stiles);
+    b.stiles = nullptr;
     void *ptrs[] = {b.X[0], b.X[1], b.VH[0], b.VH[1], b.VOBS, b.PH, b.MASK, b.BRK, b.SBASE, b.specs, b.tiles,
                     b.part_s, b.part_p, b.fb, b.nb, b.status, b.nactive, b.d_nsamp, b.samples, b.scratch,
                     b.d_eps2, b.types, b.tdf, b.tmass, b.tcoef, b.export_buf};
@@ -309,34 +315,49 @@ static ff split_ff_b(double v)
 }
 
 // (Re)build the tile list for tile height ty and order (0 natural, 1 largest
-// specimen first), and the per-tile partial buffers.
+// specimen first), the 16-row list of the sample steps (the same list when ty
+// is 16: the per-tile sample reductions would double on 8-row tiles) and the
+// per-tile partial buffers, which only sample steps write.
 static cudaError_t build_tiles(BatchCtx &b, int ty, int order)
 {
+    constexpr int TYS = 16;
     std::vector<int> sorder(b.S);
     std::iota(sorder.begin(), sorder.end(), 0);
     if (order == 1)
         std::stable_sort(sorder.begin(), sorder.end(),
                          [&](int p, int q) { return (int64_t)b.nx[p] * b.ny[p] > (int64_t)b.nx[q] * b.ny[q]; });
-    std::vector<BatchTile> tl;
+    std::vector<BatchTile> tl, ts;
     std::vector<SpecDesc> sd(b.S);
     BT_TRY(cudaMemcpyAsync(sd.data(), b.specs, b.S * sizeof(SpecDesc), cudaMemcpyDeviceToHost, b.stream));
     BT_TRY(cudaStreamSynchronize(b.stream));
     for (int s : sorder) {
-        const int tx = (b.nx[s] + 31) / 32, tyn = (b.ny[s] + ty - 1) / ty;
+        const int tx = (b.nx[s] + 31) / 32, tyn = (b.ny[s] + ty - 1) / ty, tys = (b.ny[s] + TYS - 1) / TYS;
         sd[s].tbase = (int64_t)tl.size();
         sd[s].ntiles = (int64_t)tx * tyn;
         for (int by = 0; by < tyn; by++)
             for (int bx = 0; bx < tx; bx++) tl.push_back(BatchTile{s, bx, by, 0});
+        sd[s].sbase = (int64_t)ts.size();
+        sd[s].nstiles = (int64_t)tx * tys;
+        for (int by = 0; by < tys; by++)
+            for (int bx = 0; bx < tx; bx++) ts.push_back(BatchTile{s, bx, by, 0});
     }
+    if (b.stiles && b.stiles != b.tiles) cudaFree(b.stiles);
     if (b.tiles) cudaFree(b.tiles);
     if (b.part_s) cudaFree(b.part_s);
     if (b.part_p) cudaFree(b.part_p);
-    b.tiles = nullptr;
+    b.tiles = b.stiles = nullptr;
     b.part_s = b.part_p = nullptr;
     b.T = (int64_t)tl.size();
+    b.TS = (int64_t)ts.size();
     BT_TRY(balloc(&b.tiles, tl.size()));
-    BT_TRY(balloc(&b.part_s, 2 * tl.size()));
-    BT_TRY(balloc(&b.part_p, 4 * tl.size()));
+    if (ty == TYS) {
+        b.stiles = b.tiles;
+    } else {
+        BT_TRY(balloc(&b.stiles, ts.size()));
+        BT_TRY(cudaMemcpyAsync(b.stiles, ts.data(), ts.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b.stream));
+    }
+    BT_TRY(balloc(&b.part_s, 2 * ts.size()));
+    BT_TRY(balloc(&b.part_p, 4 * ts.size()));
     BT_TRY(cudaMemcpyAsync(b.tiles, tl.data(), tl.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b.stream));
     BT_TRY(cudaMemcpyAsync(b.specs, sd.data(), b.S * sizeof(SpecDesc), cudaMemcpyHostToDevice, b.stream));
     BT_TRY(cudaStreamSynchronize(b.stream));
@@ -367,12 +388,12 @@ static TileArgs batch_base_args(BatchCtx &b)
     A.status = b.status;
     A.part_s = b.part_s;
     A.part_p = b.part_p;
-    A.ntiles = b.T;
+    A.ntiles = b.TS;  // partial sums come from the sample-step tile list
     return A;
 }
 
 template <int TY, int PREC, int MODE, bool SAMPLE>
-static cudaError_t launch_bt(BatchCtx &b, int64_t t0, int64_t t1)
+static cudaError_t launch_bt(BatchCtx &b, const BatchTile *tiles, int64_t t0, int64_t t1)
 {
     auto kern = k_tile2d_batch<TY, PREC, MODE, SAMPLE>;
     const size_t smem = tile_smem_bytes<32, TY>(PREC);
@@ -385,25 +406,31 @@ static cudaError_t launch_bt(BatchCtx &b, int64_t t0, int64_t t1)
     const int64_t ntl = t1 - t0;
     if (ntl <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)(b.grid > 0 && b.grid < ntl ? b.grid : ntl);
-    kern<<<grid, tile_threads<TY, PREC, SAMPLE>(), smem, b.stream>>>(batch_base_args(b), b.tiles, t0, t1, b.specs, b.X[0], b.X[1],
+    kern<<<grid, tile_threads<TY, PREC, SAMPLE>(), smem, b.stream>>>(batch_base_args(b), tiles, t0, t1, b.specs, b.X[0], b.X[1],
                                                  b.VH[0], b.VH[1], b.VOBS, b.PH, b.MASK, b.BRK, b.fb, b.nb);
     b.launches += 1;
     return cudaGetLastError();
 }
 
+// Steps without a sample run on the tile list of the schedule's height;
+// sample steps on the 16-row list (t0, t1 index the list used).
 template <int MODE, bool SAMPLE>
 static cudaError_t launch_b(BatchCtx &b, int64_t t0, int64_t t1)
 {
-#define BT_PREC(TYV)                                                                              \
+#define BT_PREC(TYV, TL)                                                                          \
     switch (b.prec) {                                                                             \
-    case LSM_PREC_EXACT64: return launch_bt<TYV, LSM_PREC_EXACT64, MODE, SAMPLE>(b, t0, t1);      \
-    case LSM_PREC_FAST64: return launch_bt<TYV, LSM_PREC_FAST64, MODE, SAMPLE>(b, t0, t1);        \
-    case LSM_PREC_F32: return launch_bt<TYV, LSM_PREC_F32, MODE, SAMPLE>(b, t0, t1);              \
-    default: return launch_bt<TYV, LSM_PREC_DF, MODE, SAMPLE>(b, t0, t1);                         \
+    case LSM_PREC_EXACT64: return launch_bt<TYV, LSM_PREC_EXACT64, MODE, SAMPLE>(b, TL, t0, t1);  \
+    case LSM_PREC_FAST64: return launch_bt<TYV, LSM_PREC_FAST64, MODE, SAMPLE>(b, TL, t0, t1);    \
+    case LSM_PREC_F32: return launch_bt<TYV, LSM_PREC_F32, MODE, SAMPLE>(b, TL, t0, t1);          \
+    default: return launch_bt<TYV, LSM_PREC_DF, MODE, SAMPLE>(b, TL, t0, t1);                     \
     }
-    if (b.tile_y == 8) { BT_PREC(8) }
-    if (b.tile_y == 32) { BT_PREC(32) }
-    BT_PREC(16)
+    if constexpr (SAMPLE) {
+        BT_PREC(16, b.stiles)
+    } else {
+        if (b.tile_y == 8) { BT_PREC(8, b.tiles) }
+        if (b.tile_y == 32) { BT_PREC(32, b.tiles) }
+        BT_PREC(16, b.tiles)
+    }
 #undef BT_PREC
 }
 
@@ -412,12 +439,12 @@ static cudaError_t enqueue_batch_steps(BatchCtx &b, int64_t nsteps, int record, 
 {
     const unsigned sg = (unsigned)((b.S + 255) / 256);
     for (int64_t t = 0; t < nsteps; t++) {
-        cudaError_t e = t == nsteps - 1 ? launch_b<T_STEP, true>(b, 0, b.T) : launch_b<T_STEP, false>(b, 0, b.T);
+        cudaError_t e = t == nsteps - 1 ? launch_b<T_STEP, true>(b, 0, b.TS) : launch_b<T_STEP, false>(b, 0, b.T);
         if (e != cudaSuccess) return e;
         k_batch_flip<<<sg, 256, 0, b.stream>>>(b.specs, b.S);
         b.launches += 1;
     }
-    k_batch_reduce<<<b.S, 256, 0, b.stream>>>(b.specs, b.part_s, b.part_p, b.T, b.nb,
+    k_batch_reduce<<<b.S, 256, 0, b.stream>>>(b.specs, b.part_s, b.part_p, b.TS, b.nb,
                                                record ? b.samples : b.scratch, b.cap, b.d_nsamp, record, relax, tol,
                                                b.nactive);
     b.launches += 1;

@@ -34,14 +34,15 @@ def _images():
 
 
 @pytest.mark.parametrize("precision", ["exact64", "df64"])
-def test_batch_matches_single_specimens(B, oracle_mod, precision):
+@pytest.mark.parametrize("tile_y", [8, 16])
+def test_batch_matches_single_specimens(B, oracle_mod, precision, tile_y):
+    """Positions, velocities, breaks bit-identical; samples to 1e-12 (sample
+    steps run on 16-row tiles in both paths, whatever the steps' tiling)."""
     batch, lsm = B
     imgs = _images()
     k, e, m = two_phase_materials()
     bt = batch.Batch(imgs, k, e, m, precision=precision)
-    # 16-row tiles, the tile height of the single-specimen sample steps, so
-    # that the per-tile sample partials group the same terms
-    bt.set_schedule(16, 0, 0)
+    bt.set_schedule(tile_y, 0, 0)
     singles = [lsm.Specimen.from_image(im, k, e, m, precision=precision) for im in imgs]
     for i in range(1, 41):
         bt.apply_strain(i * 2.5e-3)
