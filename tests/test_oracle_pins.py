@@ -338,6 +338,30 @@ def test_square_lattice_modulus_tends_to_three_halves_k(oracle_mod):
     assert ob["sigma_vir"] == pytest.approx(ob["sigma_grip"] * (1 + eps), rel=1e-8)
 
 
+def test_cubic_lattice_modulus_tends_to_five_halves_k(oracle_mod):
+    """Uniform cubic lattice with its 3 face and 6 edge-diagonal springs per
+    particle, equal k: the affine continuum limit has C11 = 3k, C12 = C44 = k
+    (per bond, k r0^2 n_i n_j n_k n_l over the cell volume), so uniaxial stress
+    gives E = (C11 - C12)(C11 + 2 C12) / (C11 + C12) = 2.5 k. The free lateral
+    surfaces soften finite cubes by O(1/n); a fit E(n) = E + c1/n + c2/n^2
+    over n = 16, 24, 32 recovers the limit."""
+    k_tab, e_tab, mass = one_phase_materials(1.0, 0.5)
+    ns, es = [16, 24, 32], []
+    eps = 1e-6
+    for n in ns:
+        o = oracle_mod.Oracle.from_image(np.ones((n, n, n), np.uint8), k_tab, e_tab, mass, dt=0.3, damping=0.15)
+        o.apply_strain(eps)
+        st, _ = o.relax(tol=1e-13, max_steps=400000, check_every=100)
+        assert st == 0
+        ob = o.observe()
+        assert ob["sigma_vir"] == pytest.approx(ob["sigma_grip"] * (1 + eps), rel=1e-8)
+        es.append(ob["sigma_grip"] / eps)
+    assert es[0] < es[1] < es[2] < 2.5  # softer surfaces, less so as n grows
+    A = np.array([[1.0, 1.0 / n, 1.0 / n ** 2] for n in ns])
+    e_inf = np.linalg.solve(A, np.array(es))[0]
+    assert e_inf == pytest.approx(2.5, rel=2e-3)
+
+
 def test_relaxed_energy_not_above_affine_energy(oracle_mod):
     """Minimum potential energy: with the grips fixed, the relaxed two-phase
     state stores no more energy than the affine field at the same strain."""
