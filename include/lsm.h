@@ -81,7 +81,8 @@ enum { LSM_PREC_EXACT64 = 0, LSM_PREC_FAST64 = 1, LSM_PREC_F32 = 2, LSM_PREC_DF 
  *  nx, ny, nz   image size; nz is ignored (taken as 1) when dim == 2. nx >= 2.
  *  phase        host, nx*ny*nz bytes, x fastest: 0 = void (no particle),
  *               1..nphase = material phase. Copied during the build.
- *  nphase       number of phases (1..255).
+ *  nphase       number of phases (1..181: the 2 nphase^2 spring types are
+ *               indexed by 16 bits; the tile kernels take up to 8).
  *  k_tab        host, nphase*nphase doubles, row-major, entry
  *               [(pi-1)*nphase + (pj-1)]: spring constant between phases pi, pj.
  *  epsc_tab     same layout: critical strain; rc = r0 (1 + eps_c) (Table of
