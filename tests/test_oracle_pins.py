@@ -362,6 +362,29 @@ def test_cubic_lattice_modulus_tends_to_five_halves_k(oracle_mod):
     assert e_inf == pytest.approx(2.5, rel=2e-3)
 
 
+def test_cubic_lattice_poisson_ratio_is_one_quarter(oracle_mod):
+    """The same cube under uniaxial stress along x contracts laterally with
+    nu = C12 / (C11 + C12) = 1/4, equally in y and z (cubic symmetry): an
+    affine fit of the displacement over the central 6 x 6 x 6 particles of a
+    24^3 specimen, away from the free surfaces."""
+    n = 24
+    k_tab, e_tab, mass = one_phase_materials(1.0, 0.5)
+    o = oracle_mod.Oracle.from_image(np.ones((n, n, n), np.uint8), k_tab, e_tab, mass, dt=0.3, damping=0.15)
+    eps = 1e-6
+    o.apply_strain(eps)
+    st, _ = o.relax(tol=1e-13, max_steps=400000, check_every=100)
+    assert st == 0
+    x, _, _ = o.state()
+    X = o.topology()["X"]
+    c = (n - 1) / 2.0
+    mid = np.all(np.abs(X - c) <= 2.5, axis=0)
+    A = np.vstack([X[0, mid], X[1, mid], X[2, mid], np.ones(mid.sum())]).T
+    grad = np.linalg.lstsq(A, (x - X)[:, mid].T, rcond=None)[0]
+    nu_y, nu_z = -grad[1, 1] / grad[0, 0], -grad[2, 2] / grad[0, 0]
+    assert nu_y == pytest.approx(0.25, rel=1e-2)
+    assert nu_z == pytest.approx(nu_y, rel=1e-6)
+
+
 def test_relaxed_energy_not_above_affine_energy(oracle_mod):
     """Minimum potential energy: with the grips fixed, the relaxed two-phase
     state stores no more energy than the affine field at the same strain."""
