@@ -91,7 +91,7 @@ def test_pins_catch_mutation(tmp_path, name):
     old, new = MUTATIONS[name]
     mod = _mutant(tmp_path, name, old, new)
     failed = []
-    slow = ("relax", "modulus", "energy_not_above")
+    slow = ("relax", "modulus", "poisson", "energy_not_above")
     calls = sorted(_pin_calls(), key=lambda c: any(q in c[0] for q in slow))
     for pin_name, fn, kw in calls:  # cheap pins first; stop at the first catch
         try:
