@@ -413,6 +413,80 @@ def run_foam256(args):
     return out
 
 
+def run_next_rows(args):
+    """The next rows of the scope on the 2048 x 2048 composite, one line
+    each: the paper's triangular packing (lattice 1, spring-list kernels in
+    the fixed-point modes), constant strain-rate loading of the grips (the
+    tile kernel's rate instance; rate * dt * 20 = 1e-3 per 20 steps, as the
+    increments of the main line), and the per-particle stress and strain
+    fields (lsm_fields, particles per second). Same timing rules: warm-up
+    first, CUDA events on the library's stream, inputs larger than L2."""
+    import torch
+    from paper_2201_04565_gb300 import lsm
+    stream = torch.cuda.Stream()
+    img = inclusion_image(WORKLOAD["nx"], WORKLOAD["ny"], *WORKLOAD["r"], WORKLOAD["frac"], WORKLOAD["seed"])
+    k, e, m = two_phase_materials()
+    nst = WORKLOAD["steps_per_increment"]
+    hbm, peak_src = _peaks()
+    out = {}
+
+    def timed(spec, per_inc):
+        for q in range(args.warmup):
+            per_inc(q + 1)
+        spec.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for q in range(args.steps):
+            per_inc(args.warmup + q + 1)
+        b.record(stream)
+        stream.synchronize()
+        return a.elapsed_time(b)
+
+    def line(spec, ms, label, kernel):
+        per_step = ms / (args.steps * nst)
+        algb = algorithmic_bytes(spec.n, spec.m, 2)
+        return {"value": spec.m * nst * args.steps / (ms * 1e-3), "unit": UNIT, "particles": spec.n,
+                "springs": spec.m, "time_step_ms": per_step, "kernel": kernel,
+                "roofline": {"bound": "hbm", "achieved": algb / (per_step * 1e-3) / 1e9, "peak": hbm,
+                             "unit": "GB/s", "frac": algb / (per_step * 1e-3) / 1e9 / hbm,
+                             "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)"},
+                "workload": label}
+
+    tri = lsm.Specimen.from_image(img, k, e, m, dt=WORKLOAD["dt"], damping=WORKLOAD["damping"],
+                                  precision=args.precision, lattice=1, stream=stream.cuda_stream)
+
+    def tri_inc(i):
+        tri.apply_strain(i * WORKLOAD["eps_inc"])
+        tri.step(nst)
+    out["triangular_2048"] = line(tri, timed(tri, tri_inc), "2048x2048 image, triangular packing",
+                                  "k_springs_fix + k_gather_fix")
+    tri.close()
+
+    sq = lsm.Specimen.from_image(img, k, e, m, dt=WORKLOAD["dt"], damping=WORKLOAD["damping"],
+                                 precision=args.precision, stream=stream.cuda_stream)
+    sq.apply_strain(WORKLOAD["eps_inc"])
+    sq.set_strain_rate(WORKLOAD["eps_inc"] / (nst * WORKLOAD["dt"]))
+    out["strain_rate_2048"] = line(sq, timed(sq, lambda i: sq.step(nst)),
+                                   "2048x2048 composite, grips at a constant strain rate",
+                                   "k_tile2d (rate-loading instance)")
+    sq.fields()  # first call allocates the field buffers
+    sq.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(3, min(args.steps, 20))
+    a.record(stream)
+    for _ in range(reps):
+        sq.fields()
+    b.record(stream)
+    stream.synchronize()
+    ms = a.elapsed_time(b) / reps
+    out["fields_2048"] = {"value": sq.n / (ms * 1e-3), "unit": "particles/s", "ms_per_call": ms,
+                          "particles": sq.n, "note": "lsm_fields: per-particle virial stress and Lagrangian "
+                          "strain, including the device-to-host copy of both fields (2 x 3 x n doubles)"}
+    sq.close()
+    return {"workload": "next_rows_2048", "precision": args.precision, "steps": args.steps,
+            "warmup": args.warmup, **out}
+
+
 def _config_2d(n, m, dim, precision, world):
     """The bench line's config for the 2048 x 2048 workload (shared by the
     library arm and the oracle arm)."""
@@ -479,7 +553,7 @@ def main():
     ap.add_argument("--precision", default="df64", choices=["exact64", "fast64", "f32", "df64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--workload", default="2d_2048", choices=["2d_2048", "batch512", "foam256"])
+    ap.add_argument("--workload", default="2d_2048", choices=["2d_2048", "batch512", "foam256", "next_rows"])
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -511,6 +585,13 @@ def main():
         res = run_batch512(args, rank, world)
         if rank == 0:
             print(json.dumps(res))
+        if world > 1:
+            import torch.distributed as td
+            td.destroy_process_group()
+        return 0
+    if args.workload == "next_rows":
+        if rank == 0:
+            print(json.dumps(run_next_rows(args)))
         if world > 1:
             import torch.distributed as td
             td.destroy_process_group()
