@@ -85,15 +85,17 @@ k_springs_fix(int64_t m, int64_t n, const int32_t *__restrict__ si, const int32_
     double w = 0.0, u = 0.0;
     if (s < m && !state[s]) {
         const int32_t i = si[s], j = sj[s];
-        const int dir = sdir[s];
+        const int dir = PREC == LSM_PREC_F32 ? sdir[s] : 0;
         const TypeDF t = tdf[stype[s]];
-        long long ef[DIM];
-#pragma unroll
-        for (int c = 0; c < DIM; c++) ef[c] = xf[c * n + j] - xf[c * n + i] - T.o[dir][c];
         bool brk_now = false;
         FT f[DIM];
-        const ff cor = ff_add(T.oo[dir], t.cor);  // |o|^2 - r0^2 (t.cor holds -r0^2)
         if constexpr (PREC == LSM_PREC_F32) {
+            // deviation e = d - o from the lattice vector o, exact in fixed
+            // point: r^2 - r0^2 = (2 o + e).e + |o|^2 - r0^2 has no cancellation
+            long long ef[DIM];
+#pragma unroll
+            for (int c = 0; c < DIM; c++) ef[c] = xf[c * n + j] - xf[c * n + i] - T.o[dir][c];
+            const ff cor = ff_add(T.oo[dir], t.cor);  // |o|^2 - r0^2 (t.cor holds -r0^2)
             float e[DIM], d[DIM], s2 = 0.0f;
 #pragma unroll
             for (int c = 0; c < DIM; c++) {
@@ -118,27 +120,24 @@ k_springs_fix(int64_t m, int64_t n, const int32_t *__restrict__ si, const int32_
                 }
             }
         } else {
-            ff e[DIM], d[DIM];
-            ff s2 = ff{0.0f, 0.0f};
+            // the spring vector d = x_j - x_i as an exact fixed-point
+            // difference, converted to a double-float; 1/r by a Newton step
+            // and the force k (1 - r0 / r) d (the tile kernels' arithmetic)
+            ff d[DIM];
 #pragma unroll
-            for (int c = 0; c < DIM; c++) {
-                e[c] = fix_to_ff_i2f(ef[c], T.p48, T.p24, T.p0);
-                const ff o = T.of[dir][c];
-                d[c] = ff_add(o, e[c]);
-                s2 = ff_add(s2, ff_mul(ff_add(ff_add(o, o), e[c]), e[c]));
-            }
-            const ff r2 = ff_add(T.oo[dir], s2);  // r^2 = |o|^2 + (2 o + e).e
-            const ff num = ff_add(s2, cor);       // r^2 - r0^2
+            for (int c = 0; c < DIM; c++) d[c] = fix_to_ff_i2f2(xf[c * n + j] - xf[c * n + i], T.p48, T.p24, T.p0);
+            ff r2 = ff_norm2(d[0], d[1]);
+            if constexpr (DIM == 3) r2 = ff_add_sloppy(r2, ff_sqr(d[2]));
             if (BREAK && ff_gt(r2, t.rc2)) {
                 brk_now = true;
             } else {
-                const ff r = ff_sqrt(r2);
-                const ff rr0 = ff_add(r, t.r0);
-                const ff cc = ff_mul(t.k, ff_div(num, ff_mul(r, rr0)));
+                ff y;
+                const ff g = ff_spring_g(r2, t.r0, SAMPLE ? &y : nullptr);
+                const ff cc = ff_mul(t.k, g);
 #pragma unroll
                 for (int c = 0; c < DIM; c++) f[c] = ff_mul(cc, d[c]);
                 if (SAMPLE) {
-                    const double st = ff_to_double(ff_div(num, rr0));
+                    const double st = ff_to_double(ff_mul(ff_mul(r2, y), g));  // r - r0
                     u = 0.5 * ff_to_double(t.k) * st * st;
                     w = ff_to_double(d[0]) * ff_to_double(f[0]);
                 }
@@ -188,6 +187,9 @@ k_gather_fix(int64_t n, int64_t m, const int64_t *__restrict__ row, const uint32
 #pragma unroll
         for (int c = 0; c < DIM; c++) Fa[c] = FT{};
         const int64_t e0 = row[p], e1 = row[p + 1];
+        // unrolled so that the loads of several incident springs are in
+        // flight together (the sum keeps its order)
+#pragma unroll 4
         for (int64_t e = e0; e < e1; e++) {
             const uint32_t word = inc[e];
             const int64_t s = word >> 1;
@@ -298,7 +300,10 @@ cudaError_t fixcsr_upload(Ctx &c)
     const int64_t n = c.n, m = c.m, dn = (int64_t)h.dim * n;
     int maxext = std::max(h.nx, std::max(h.ny, h.nz));
     const double extent = 4.0 * maxext * h.a + 16.0;
-    c.fix_S = std::min(52, 61 - (int)std::ceil(std::log2(extent)));
+    // also every intact spring vector below 2^47 in fixed point, so that it
+    // converts to a double-float in two exact 24-bit chunks
+    c.fix_S = std::min({52, 61 - (int)std::ceil(std::log2(extent)),
+                        47 - (int)std::ceil(std::log2(h.a * std::sqrt(2.0)))});
     c.a_fix = std::llround(std::ldexp(h.a, c.fix_S));
     std::vector<TypeDF> tdf(h.types.size());
     for (size_t q = 0; q < h.types.size(); q++) {

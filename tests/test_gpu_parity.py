@@ -327,8 +327,12 @@ def test_fields_3d_match_oracle(oracle_mod, L):
 def test_triangular_packing_parity(oracle_mod, L, precision):
     """The paper's triangular packing (lattice 1) on the spring-list kernels:
     exact64 bit-identical through fracture, fast64/df64 at the 1e-10 bar with
-    the same broken set, f32 error stated; the lattice vectors (a/2, a sqrt3/2)
-    are not exact in fixed point, which the df64 path absorbs in e."""
+    the same broken set, f32 error stated. The increments (2.1e-3) never land
+    on the stiff phase's critical strain 0.05: there, the horizontal springs of
+    a homogeneous stiff region stay exactly affine, every one of them sits
+    within rounding of rc, and the strict break test is decided by the last
+    bit of the positions, which only the bit-identical exact64 mode
+    reproduces."""
     img = inclusion_image(40, 36, 2.0, 5.0, 0.3, 21)
     img[16:19, 0:12] = 0  # a notch from the left edge (mode-I set-up)
     k, e, m = two_phase_materials()
@@ -337,7 +341,7 @@ def test_triangular_packing_parity(oracle_mod, L, precision):
     assert (g.n, g.m) == (o.n, o.m)
     to, tg = o.topology(), g.topology()
     assert np.array_equal(to["si"], tg["si"]) and np.array_equal(to["sj"], tg["sj"])
-    so = _run_schedule(o, g, 25, 20, 2e-3)  # 500 steps to 5% strain
+    so = _run_schedule(o, g, 25, 20, 2.1e-3)  # 500 steps to 5.25% strain
     xg, vg = g.state()
     xo, vo, _ = o.state()
     if precision == "exact64":
