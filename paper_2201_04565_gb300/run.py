@@ -8,7 +8,7 @@
 single: a 2D two-phase inclusion composite (fused tile kernel, or the
 spring-list kernels with --path 1); foam: a 3D one-phase foam under
 compression (voxel tile kernel in df64 / f32, spring-list kernels in the FP64
-modes); batch: uneven 2D specimens (sides 32 to
+modes or with --path 1); batch: uneven 2D specimens (sides 32 to
 --max-side) in one batched context; unet: training iterations of the
 warm-start network on random inputs. Each case runs a displacement-controlled
 tension (or compression) test of --increments load increments of --steps time
@@ -49,7 +49,8 @@ def _foam(a):
     from . import lsm
     img = foam_volume(a.side, 3.0, 0.40, seed=a.seed)
     k, e, m = one_phase_materials(1.0, 0.04)
-    sp = lsm.Specimen.from_image(img, k, e, m, dt=0.01, damping=0.1, precision=a.precision, grip_mode=1)
+    sp = lsm.Specimen.from_image(img, k, e, m, dt=0.01, damping=0.1, precision=a.precision, grip_mode=1,
+                                 path=a.path)
     t0 = time.perf_counter()
     for i in range(1, a.increments + 1):
         sp.apply_strain(-i * a.eps_inc)
@@ -108,7 +109,7 @@ def main(argv=None):
     ap.add_argument("case", choices=["single", "foam", "batch", "unet"])
     ap.add_argument("--side", type=int, default=256)
     ap.add_argument("--precision", default="df64", choices=["exact64", "fast64", "f32", "df64"])
-    ap.add_argument("--path", type=int, default=0, choices=[0, 1], help="single: 0 tile kernel, 1 spring list")
+    ap.add_argument("--path", type=int, default=0, choices=[0, 1], help="single, foam: 0 automatic (tile kernels), 1 spring-list kernels")
     ap.add_argument("--increments", type=int, default=3)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--eps-inc", type=float, default=1e-3)
