@@ -203,22 +203,31 @@ lsm_status lsm_apply_strain(lsm_ctx *ctx, double eps);
  * is a cached CUDA graph per nsteps). */
 lsm_status lsm_step(lsm_ctx *ctx, int64_t nsteps);
 
-/* Relax to a force residual: run steps in batches of check_every until the
- * sample residual is <= tol; records one sample per batch... only the last
- * batch's sample is kept. *taken = steps run. Synchronises after every batch.
- * Returns LSM_OK, or LSM_ENOTCONV after max_steps. */
+/* Relax to a force residual (the quasi-static limit of the damped dynamics,
+ * Section 2.2): run steps in batches of check_every until the residual
+ * (max over free components of max(|F|, |v|)) of a batch's last step is
+ * <= tol, or max_steps steps are taken; then record one sample, of the final
+ * state. *taken (may be NULL) = steps run. Synchronises after every batch.
+ * Returns LSM_OK, LSM_ENOTCONV after max_steps (state and sample are those
+ * reached), LSM_EINVAL for tol < 0, max_steps < 0 or check_every outside
+ * 1..100000, or a pending device status. */
 lsm_status lsm_relax(lsm_ctx *ctx, double tol, int64_t max_steps, int64_t check_every,
                      int64_t *taken);
 
-/* Copy up to cap recorded samples' (eps, sigma_vir) pairs; *count = number
- * recorded (may exceed cap). Synchronises. */
+/* The stress-strain curve: copy up to cap recorded samples' (eps,
+ * sigma_vir) pairs (applied engineering strain; xx virial stress, Eq. 7,
+ * over the reference box, tension > 0) into the caller's arrays (either may
+ * be NULL when cap is 0); *count = number recorded (may exceed cap).
+ * Synchronises. */
 lsm_status lsm_stress_strain(lsm_ctx *ctx, double *eps, double *sigma, int64_t cap,
                              int64_t *count);
 
-/* Copy up to cap full samples. Synchronises. */
+/* Copy up to cap full samples (lsm_sample) into out; *count = number
+ * recorded (may exceed cap). Synchronises. */
 lsm_status lsm_samples(lsm_ctx *ctx, lsm_sample *out, int64_t cap, int64_t *count);
 
-/* Broken-spring mask in canonical spring order: out[s] = 1 if broken.
+/* Broken-spring mask (Section 2.3 break test; Section 4: broken springs
+ * are kept and give no force) in canonical spring order: out[s] = 1 if broken.
  * cap >= m is required (LSM_EINVAL otherwise); *m = spring count;
  * *first_break_step = index of the first step in which any spring broke,
  * -1 if none. Any output pointer may be NULL except out. Synchronises. */
