@@ -57,10 +57,13 @@ lsm_status lsm_batch_set_schedule(lsm_batch *b, int32_t tile_y, int32_t grid, in
  * (host array), as lsm_apply_strain does for one specimen. */
 lsm_status lsm_batch_apply_strain(lsm_batch *b, const double *eps);
 
-/* nsteps time steps of every specimen, then one sample per specimen. */
+/* nsteps time steps of every specimen (force Eq. 2, break test, damped
+ * velocity Verlet Eqs. 3-5, as lsm_step), then one sample per specimen.
+ * Stream-ordered (a cached CUDA graph per nsteps). */
 lsm_status lsm_batch_step(lsm_batch *b, int64_t nsteps);
 
-/* Relax every specimen to a force residual: steps in batches of check_every;
+/* Relax every specimen to a force residual (the quasi-static limit of the
+ * damped dynamics, Section 2.2): steps in batches of check_every;
  * after each batch every specimen whose residual is <= tol stops stepping.
  * Returns when all have converged or after max_steps steps. taken[i] (host,
  * may be NULL) = steps specimen i ran; converged[i] = 1 if it met tol. One
