@@ -236,11 +236,12 @@ def run_gpu(args, rank, world):
         inc += 1
         spec.apply_strain(inc * WORKLOAD["eps_inc"])
         spec.step(nst)
-        samples = spec.samples()
+        sample = spec.last_sample()
         mask, _ = spec.broken(mask_host)
     t1 = time.perf_counter()
+    assert sample["step"] == inc * nst
     e2e_value = spec.m * nst * e2e_steps * world / (t1 - t0)
-    d2h = mask.nbytes + 64  # broken mask + the new sample (the binding copies all samples)
+    d2h = mask.nbytes + 64  # broken mask + the step's sample (lsm_sample_last: one 64-byte record)
 
     hbm, peak_src = _peaks()
     units = spec.m * nst * args.steps * world
@@ -279,18 +280,80 @@ def run_gpu(args, rank, world):
         variants = {}
         for mode in ("exact64", "fast64", "f32", "df64"):
             if mode == args.precision:
-                variants[mode] = {"value": value, "time_step_ms": per_step_ms}
+                variants[mode] = {"value": value, "time_step_ms": per_step_ms, "clocks": clk}
                 continue
             sp = _build_specimen(lsm, mode, stream)
-            for q in range(1, 3):
+            for q in range(1, 4):
                 sp.apply_strain(q * WORKLOAD["eps_inc"])
                 sp.step(nst)
             sp.synchronize()
-            vm, vinc = _time_increments(sp, stream, 3, 5)
-            variants[mode] = {"value": sp.m * nst * 5 / (vm * 1e-3), "time_step_ms": statistics.mean(vinc) / nst}
+            vclk = ClockSampler(dev)
+            vclk.start()
+            vm, vinc = _time_increments(sp, stream, 4, 10)
+            variants[mode] = {"value": sp.m * nst * 10 / (vm * 1e-3), "time_step_ms": statistics.mean(vinc) / nst,
+                              "increments_timed": 10, "clocks": vclk.stop()}
             sp.close()
         out["variants"] = variants
     return out
+
+
+def run_curves_subset(args, stride=4, incs=80, nst=20):
+    """Converged stress-strain curves per second on a fixed subset of the
+    512-specimen batch (every stride-th specimen of the seeded set: sides
+    32..512 px, 10-50% inclusions), tension to 8% strain in 80 increments of
+    20 time steps. Batched arm: one lsm_batch for the whole subset (one
+    tile-kernel launch per time step for all specimens, graph-captured,
+    autotuned schedule). Plain arm: one single-specimen context per
+    specimen, run one after another. Both arms are timed through the API on
+    the host clock, per-increment host work included, build and autotuning
+    excluded; every specimen of the subset runs in both arms (nothing is
+    extrapolated)."""
+    import torch
+    from gen.images import batch_specimens
+    from paper_2201_04565_gb300 import batch as bmod
+    from paper_2201_04565_gb300 import lsm
+    prec = args.precision
+    imgs = batch_specimens(512)[::stride]
+    k, e, m = two_phase_materials()
+    stream = torch.cuda.Stream()
+    bt = bmod.Batch(imgs, k, e, m, dt=0.01, damping=0.1, precision=prec, stream=stream.cuda_stream)
+    msum = sum(mm for _, mm in bt.sizes)
+    t0 = time.perf_counter()
+    tune = bt.autotune(10)
+    t_tune = time.perf_counter() - t0
+    bt.synchronize()
+    t0 = time.perf_counter()
+    for i in range(1, incs + 1):
+        bt.apply_strain(i * 1e-3)
+        bt.step(nst)
+    bt.synchronize()
+    t_batch = time.perf_counter() - t0
+    bt.close()
+    t_plain = 0.0
+    for im in imgs:
+        sp = lsm.Specimen.from_image(im, k, e, m, dt=0.01, damping=0.1, precision=prec,
+                                     stream=stream.cuda_stream)
+        sp.synchronize()
+        t0 = time.perf_counter()
+        for i in range(1, incs + 1):
+            sp.apply_strain(i * 1e-3)
+            sp.step(nst)
+        sp.synchronize()
+        t_plain += time.perf_counter() - t0
+        sp.close()
+    return {"metric": "converged stress-strain curves/s, batched vs plain per-specimen contexts",
+            "workload": "batch512_two_phase subset: every %dth specimen (%d of 512), tension to %g%% strain"
+                        % (stride, len(imgs), incs * 0.1),
+            "specimens": len(imgs), "springs_total": msum, "increments": incs, "time_steps_per_increment": nst,
+            "precision": prec,
+            "batched": {"curves_per_s": len(imgs) / t_batch, "seconds": t_batch,
+                        "spring_updates_per_s": msum * incs * nst / t_batch,
+                        "schedule": tune, "autotune_seconds": t_tune},
+            "plain": {"curves_per_s": len(imgs) / t_plain, "seconds": t_plain,
+                      "spring_updates_per_s": msum * incs * nst / t_plain},
+            "speedup": t_plain / t_batch,
+            "warm_start": "not in this line: the learned warm start needs a network trained on "
+                          "method-generated data (minutes of GPU time); measured separately"}
 
 
 def run_batch512(args, rank=0, world=1, plain_every=8):
@@ -554,9 +617,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--workload", default="2d_2048", choices=["2d_2048", "batch512", "foam256", "next_rows"])
+    ap.add_argument("--no-curves", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.gpus != world:
+        # one process per GPU: --gpus N is launched as N torchrun ranks
+        print("bench.py: --gpus %d but WORLD_SIZE=%d; launch N>1 under torchrun with --nproc-per-node N"
+              % (args.gpus, world), file=sys.stderr)
+        return 2
     if args.warmup < 3:
         args.warmup = 3
 
@@ -569,7 +638,7 @@ def main():
                "ms_per_step": 1e3 * base["seconds"] / base["steps"] * WORKLOAD["steps_per_increment"],
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                "data": "synthetic (seeded two-phase inclusion image)",
-               "config": _config_2d(base.pop("n"), base.pop("m"), 2, args.precision, world),
+               "config": _config_2d(base.pop("n"), base.pop("m"), 2, "f64", world),
                "cpu_baseline": base,
                "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(out))
@@ -607,6 +676,8 @@ def main():
             td.destroy_process_group()
         return 0
     out = run_gpu(args, rank, world)
+    if rank == 0 and world == 1 and not args.no_curves:
+        out["curves"] = run_curves_subset(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     if world > 1:

@@ -226,6 +226,12 @@ lsm_status lsm_stress_strain(lsm_ctx *ctx, double *eps, double *sigma, int64_t c
  * recorded (may exceed cap). Synchronises. */
 lsm_status lsm_samples(lsm_ctx *ctx, lsm_sample *out, int64_t cap, int64_t *count);
 
+/* Copy only the most recent sample into *out (64 bytes, whatever the number
+ * recorded): the per-increment read of a load curve (Section 3.1 records the
+ * stress at each output step). Errors: LSM_EINVAL for a null argument or
+ * when no sample has been recorded yet. Synchronises. */
+lsm_status lsm_sample_last(lsm_ctx *ctx, lsm_sample *out);
+
 /* Broken-spring mask (Section 2.3 break test; Section 4: broken springs
  * are kept and give no force) in canonical spring order: out[s] = 1 if broken.
  * cap >= m is required (LSM_EINVAL otherwise); *m = spring count;
@@ -313,8 +319,8 @@ lsm_status lsm_load(const char *path, void *stream, lsm_ctx **out);
 lsm_status lsm_counters(lsm_ctx *ctx, int64_t *steps, int64_t *spring_updates,
                         int64_t *kernel_launches);
 
-/* Potential energy (Eq. 1) and virial sum of the intact springs of a network
- * at given positions, with no device memory allocated by the library.
+/* Potential energy and virial sum of the intact springs of a network at
+ * given positions, with no device memory allocated by the library.
  *
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory -- code that runs inside a memory pool or
@@ -329,7 +335,7 @@ lsm_status lsm_counters(lsm_ctx *ctx, int64_t *steps, int64_t *spring_updates,
  *   broken   m bytes, nonzero = broken (skipped); NULL = all intact.
  *   out      2 doubles written: out[0] = sum 1/2 k (r - r0)^2,
  *            out[1] = sum (x_j - x_i)_x f_x with f = k (r - r0)/r (x_j - x_i)
- *            (so sigma_xx = (out[1] - sum m v_x^2) / Omega, Eq. 7).
+ *            (so sigma_xx = (out[1] - sum m v_x^2) / Omega).
  *   stream   cudaStream_t (NULL = default stream). The call is stream
  *            ordered and returns before the result is ready.
  * Scratch: per-chunk partial sums live in a file-scope device array of
@@ -338,6 +344,9 @@ lsm_status lsm_counters(lsm_ctx *ctx, int64_t *steps, int64_t *spring_updates,
  * (cudaGetSymbolAddress) with the device current, so make the first call on
  * each device before any stream capture. Every call shares the array and
  * fully rewrites the part it reads; calls that overlap on the GPU race on it.
+ * The looked-up address is kept for the life of the process: after a reset of
+ * a device (cudaDeviceReset, or a reset of its primary context) this entry
+ * point must not be called on that device again in the same process.
  * Errors: LSM_EINVAL for bad sizes or null arrays (message in
  * lsm_last_error(NULL)), LSM_ECUDA if a launch fails. */
 lsm_status lsm_spring_energy_static(int32_t dim, int64_t n, int64_t m, const double *x,

@@ -312,6 +312,20 @@ lsm_status lsm_samples(lsm_ctx *c, lsm_sample *out, int64_t cap, int64_t *count)
     return LSM_OK;
 }
 
+lsm_status lsm_sample_last(lsm_ctx *c, lsm_sample *out)
+{
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    if (!out) return fail(c, LSM_EINVAL, "null output");
+    lsm_status st = device_status(c);
+    if (st != LSM_OK) return st;
+    if (c->nsamples < 1) return fail(c, LSM_EINVAL, "no sample recorded yet");
+    cudaError_t e = cudaMemcpyAsync(out, c->samples + (c->nsamples - 1), sizeof(lsm_sample),
+                                    cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sample");
+    return LSM_OK;
+}
+
 lsm_status lsm_stress_strain(lsm_ctx *c, double *eps, double *sigma, int64_t cap, int64_t *count)
 {
     if (!c) return fail(nullptr, LSM_EINVAL, "null context");

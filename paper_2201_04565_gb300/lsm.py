@@ -71,6 +71,7 @@ SIGNATURES = [
     ("lsm_relax", C.c_int, [_P, _D, _I64, _I64, _P]),
     ("lsm_stress_strain", C.c_int, [_P, _P, _P, _I64, _P]),
     ("lsm_samples", C.c_int, [_P, _P, _I64, _P]),
+    ("lsm_sample_last", C.c_int, [_P, C.POINTER(lsm_sample)]),
     ("lsm_broken_mask", C.c_int, [_P, _P, _I64, _P, _P]),
     ("lsm_break_steps", C.c_int, [_P, _P, _I64]),
     ("lsm_get_state", C.c_int, [_P, _P, _P]),
@@ -216,6 +217,13 @@ def lsm_samples(h):
     buf = (lsm_sample * max(cnt.value, 1))()
     _check(load_library().lsm_samples(h, buf, cnt.value, C.byref(cnt)), h)
     return [buf[q].as_dict() for q in range(cnt.value)]
+
+
+def lsm_sample_last(h):
+    """The most recent sample only (one 64-byte copy)."""
+    out = lsm_sample()
+    _check(load_library().lsm_sample_last(h, C.byref(out)), h)
+    return out.as_dict()
 
 
 def lsm_stress_strain(h):
@@ -371,6 +379,9 @@ class Specimen:
 
     def samples(self):
         return lsm_samples(self.h)
+
+    def last_sample(self):
+        return lsm_sample_last(self.h)
 
     def stress_strain(self):
         return lsm_stress_strain(self.h)

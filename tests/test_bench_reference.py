@@ -22,6 +22,7 @@ def test_reference_arm_json_line():
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["config"]["workload"] == "2d_2048_two_phase"
     assert d["config"]["particles"] == 4194304 and d["config"]["springs"] == 16764930
+    assert d["config"]["precision"] == "f64" and d["dtype"] == "f64"  # the oracle computes in FP64
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0

@@ -50,7 +50,26 @@ def _run_schedule(o, g, incs, steps, eps_inc):
 
 
 def _rel(a, b):
+    """Normwise relative position error: max |a - b| / max |b|."""
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _rel_u(a, b, X):
+    """The same error relative to the largest displacement b - X (about 1e3
+    stricter than _rel at full image sizes, where |x| reaches the width)."""
+    return np.abs(a - b).max() / max(np.abs(b - X).max(), 1e-300)
+
+
+def _min_margin(o):
+    """Smallest (rc^2 - r^2) / rc^2 over the oracle's intact springs at its
+    current positions: how close the break test came to a tie."""
+    t = o.topology()
+    x = o.state()[0]
+    intact = o.broken()[0] == 0
+    d = x[:, t["sj"]] - x[:, t["si"]]
+    r2 = (d * d).sum(axis=0)
+    m = (t["rc2"] - r2) / t["rc2"]
+    return float(m[intact].min()) if intact.any() else np.inf
 
 
 def test_topology_matches_oracle(oracle_mod, L):
@@ -131,14 +150,61 @@ def test_c0_fast_modes_within_tolerance(oracle_mod, L, path, precision):
     so = _run_schedule(o, g, 50, 20, 1e-3)  # 1000 steps
     xg, _ = g.state()
     xo, _, _ = o.state()
+    print("%s path %d after 1000 steps: |dx|/|x| = %.3e, |dx|/|u| = %.3e"
+          % (precision, path, _rel(xg, xo), _rel_u(xg, xo, o.topology()["X"])))
     assert _rel(xg, xo) <= 1e-10
     mo, _, fo = o.broken()
     mg, fg = g.broken()
+    assert mo.sum() > 0, "the schedule must reach fracture"
     assert np.array_equal(mg, mo) and fg == fo
     sg = g.samples()
     first = next((i for i, s in enumerate(so) if s["n_broken"] > 0), len(so))
     for a, b in zip(sg[:first], so[:first]):
         assert a["sigma_vir"] == pytest.approx(b["sigma_vir"], rel=1e-6)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_c0_df64_full_schedule(oracle_mod, L, path):
+    """df64, the benchmark's mode, through the whole 64x64 schedule (100
+    increments of 1e-3, 20 damped steps each: 2,000 steps, fracture from step
+    620 on) against the oracle: positions within 1e-10 after 1,000 steps and
+    at the end, the identical broken set, break steps and first-break step,
+    and sigma-epsilon within 1e-6 before the first break. Prints the error
+    relative to the displacement and the smallest break-test margin the
+    oracle's intact springs showed at the increments' ends."""
+    img = inclusion_image(64, 64, 3.0, 8.0, 0.30, 0)
+    o, g = _pair(oracle_mod, L, img, two_phase_materials(), precision="df64", path=path,
+                 dt=0.01, damping=0.1)
+    X = o.topology()["X"]
+    so, margin = [], np.inf
+    for i in range(1, 101):
+        o.apply_strain(i * 1e-3)
+        g.apply_strain(i * 1e-3)
+        o.step(20)
+        g.step(20)
+        so.append(o.observe())
+        margin = min(margin, _min_margin(o))
+        if i == 50:
+            xg, xo = g.state()[0], o.state()[0]
+            print("df64 path %d, 1000 steps: |dx|/|x| = %.3e, |dx|/|u| = %.3e"
+                  % (path, _rel(xg, xo), _rel_u(xg, xo, X)))
+            assert _rel(xg, xo) <= 1e-10
+    xg, xo = g.state()[0], o.state()[0]
+    print("df64 path %d, 2000 steps: |dx|/|x| = %.3e, |dx|/|u| = %.3e; smallest intact margin "
+          "(rc^2 - r^2)/rc^2 = %.3e" % (path, _rel(xg, xo), _rel_u(xg, xo, X), margin))
+    assert _rel(xg, xo) <= 1e-10
+    mo, bo, fo = o.broken()
+    mg, fg = g.broken()
+    assert fo == 620 and mo.sum() > 0
+    assert np.array_equal(mg, mo) and fg == fo
+    assert np.array_equal(g.break_steps(), bo)
+    sg = g.samples()
+    assert len(sg) == 100
+    first = next(i for i, s_ in enumerate(so) if s_["n_broken"] > 0)
+    for a, b in zip(sg[:first], so[:first]):
+        assert a["sigma_vir"] == pytest.approx(b["sigma_vir"], rel=1e-6)
+    for a, b in zip(sg, so):
+        assert a["n_broken"] == b["n_broken"]
 
 
 @pytest.mark.parametrize("path", PATHS)
@@ -285,8 +351,12 @@ def test_df64_general_lattice_spacing(oracle_mod, L, path, a):
     _run_schedule(o, g, 30, 20, 2e-3)
     xg, _ = g.state()
     xo, _, _ = o.state()
+    print("df64 a=%g path %d: |dx|/|x| = %.3e, |dx|/|u| = %.3e"
+          % (a, path, _rel(xg, xo), _rel_u(xg, xo, o.topology()["X"])))
     assert _rel(xg, xo) <= 1e-10
-    assert np.array_equal(g.broken()[0], o.broken()[0])
+    mo = o.broken()[0]
+    assert mo.sum() > 0, "the schedule must reach fracture"
+    assert np.array_equal(g.broken()[0], mo)
 
 
 @pytest.mark.parametrize("path", PATHS)
