@@ -100,8 +100,11 @@ enum { LSM_PREC_EXACT64 = 0, LSM_PREC_FAST64 = 1, LSM_PREC_F32 = 2, LSM_PREC_DF 
  *  precision    LSM_PREC_* (see above).
  *  path         0 = automatic (square-lattice images with up to 8 phases
  *               run the fused tile kernels: every mode in 2D, the F32 and DF
- *               modes in 3D; everything else runs the general spring-list
- *               kernels); 1 = always the general spring-list kernels.
+ *               modes in 3D; in 2D the F32 and DF time steps without a sample
+ *               run the register-resident strip kernel, bit-identical to the
+ *               tile kernel; everything else runs the general spring-list
+ *               kernels); 1 = always the general spring-list kernels;
+ *               2 = as 0, but every 2D time step on the tile kernel.
  *  stream       cudaStream_t to order work on (NULL = the library creates one).
  *  lattice      0 = square (2D) / cubic (3D) lattice as above; 1 = the
  *               paper's triangular packing (2D only, Section 1: six first

@@ -51,6 +51,9 @@ lsm_status finish_build(lsm_ctx *c, void *stream, lsm_ctx **out, int path = 0)
     const bool fixmode = c->h.precision == LSM_PREC_F32 || c->h.precision == LSM_PREC_DF;
     c->tile = path != 1 && c->h.nx > 0 && c->h.lattice == 0 && c->h.nphase >= 1 && c->h.nphase <= 8 &&
               (c->h.dim == 2 || (c->h.dim == 3 && fixmode));
+    // 2D fixed-point modes: steps without a sample on the strip kernel
+    // (path 2 keeps every step on the tile kernel; same bits either way)
+    c->strip = c->tile && path != 2 && lsm::strip_supported(*c);
     if (stream) {
         c->stream = (cudaStream_t)stream;
     } else {
@@ -132,9 +135,9 @@ lsm_status lsm_build_from_image(const lsm_desc *desc, lsm_ctx **out)
         delete c;
         return fail(nullptr, LSM_EINVAL, err);
     }
-    if (desc->path != 0 && desc->path != 1) {
+    if (desc->path < 0 || desc->path > 2) {
         delete c;
-        return fail(nullptr, LSM_EINVAL, "path must be 0 (automatic) or 1 (spring-list kernels)");
+        return fail(nullptr, LSM_EINVAL, "path must be 0 (automatic), 1 (spring-list kernels) or 2 (tile kernel for every 2D step)");
     }
     return finish_build(c, desc->stream, out, desc->path);
 }

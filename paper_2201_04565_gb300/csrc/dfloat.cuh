@@ -26,18 +26,16 @@ namespace lsm {
 // finite).
 __device__ __forceinline__ long long dbl_to_fix(double x, int S, bool &over)
 {
+    // x 2^S = m53 2^(e - 1075 + S); with the 53-bit significand moved to the
+    // top of a 64-bit word (m = m53 2^11) that is m >> (1086 - e - S), one
+    // logical right shift (zero or subnormal x: a shift of 64 or more, 0)
     const long long b = __double_as_longlong(x);
     const int e = (int)((b >> 52) & 0x7FF);
-    const long long m = (b & 0x000FFFFFFFFFFFFFLL) | 0x0010000000000000LL;
-    const int sh = e - 1075 + S;
-    over |= sh > 9;  // |x| >= 2^(62-S) (also catches inf / nan)
-    long long f;
-    if (sh >= 0)
-        f = m << (sh > 9 ? 9 : sh);
-    else
-        f = sh > -63 ? (m >> (-sh)) : 0LL;
-    if (e == 0) f = 0;  // zero or subnormal
-    return b < 0 ? -f : f;
+    const unsigned long long m = ((unsigned long long)b << 11) | 0x8000000000000000ULL;
+    const int rs = 1086 - e - S;
+    over |= rs < 2;  // |x| >= 2^(62-S) (also catches inf / nan)
+    const unsigned long long f = rs >= 64 ? 0ull : (m >> (rs < 2 ? 2 : rs));
+    return b < 0 ? -(long long)f : (long long)f;
 }
 
 // Float with the top 24 significant bits of u * 2^-S (u > 0), truncated;
@@ -126,6 +124,16 @@ __device__ __forceinline__ bool dbl_finite_bits(double d)
     return ((unsigned)(__double_as_longlong(d) >> 32) & 0x7FF00000u) != 0x7FF00000u;
 }
 
+// Reciprocal square root estimate of a positive normal float: the hardware
+// approximation (about 2^-22.9 relative; subnormal inputs flush to zero),
+// which every caller refines by Newton steps.
+__device__ __forceinline__ float rsqrt_approx(float a)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a));
+    return y;
+}
+
 // -- error-free transformations and double-float arithmetic ----------------
 
 __device__ __forceinline__ ff two_sum(float a, float b)
@@ -169,6 +177,18 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b)
     p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
     p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
     return fast_two_sum(p.hi, p.lo);
+}
+
+// a * b without the final renormalisation: (p, e) with p = fl(a.hi b.hi)
+// and |e| within a few units of 2^-24 |p|, a valid unevaluated sum for
+// the callers that only multiply or add it further (the neglected a.lo b.lo
+// is below 2^-46 relative, as in ff_mul).
+__device__ __forceinline__ ff ff_mul_un(ff a, ff b)
+{
+    ff p = two_prod(a.hi, b.hi);
+    p.lo = __fmaf_rn(a.hi, b.lo, p.lo);
+    p.lo = __fmaf_rn(a.lo, b.hi, p.lo);
+    return p;
 }
 
 __device__ __forceinline__ ff ff_mul_f(ff a, float b)
@@ -217,10 +237,12 @@ __device__ __forceinline__ ff fix_to_ff_i2f(long long v, float p48, float p24, f
 // exactly because the chunks do not overlap.
 __device__ __forceinline__ ff fix_to_ff_i2f2(long long v, float p48, float p24, float p0)
 {
-    const long long h = v >> 24;
-    if ((unsigned long long)(h + 0x800000LL) < 0x1000000ULL) {
-        const float a = __fmul_rn(__int2float_rn((int)h), p24);
-        const float b = __fmul_rn(__int2float_rn((int)(v & 0xFFFFFFLL)), p0);
+    // |v| < 2^47 <=> the high word lies in [-2^15, 2^15)
+    const int hw = (int)(v >> 32);
+    if ((unsigned)(hw + 0x8000) < 0x10000u) {
+        const int h = (int)__funnelshift_r((unsigned)v, (unsigned)hw, 24);  // v >> 24, 24 significant bits
+        const float a = __fmul_rn(__int2float_rn(h), p24);
+        const float b = __fmul_rn(__int2float_rn((int)((unsigned)v & 0xFFFFFFu)), p0);
         return fast_two_sum(a, b);
     }
     return fix_to_ff_i2f(v, p48, p24, p0);
@@ -266,7 +288,7 @@ __device__ __forceinline__ ff ff_norm2(ff a, ff b)
 // 1 - r0 y0 is exact up to the small terms summed in float. *y receives 1/r.
 __device__ __forceinline__ ff ff_spring_g(ff r2, ff r0, ff *y)
 {
-    float y0 = rsqrtf(r2.hi);
+    float y0 = rsqrt_approx(r2.hi);
     y0 = __fmul_rn(y0, __fmaf_rn(-0.5f * r2.hi, __fmul_rn(y0, y0), 1.5f));
     const ff t = ff_mul(r2, two_prod(y0, y0));
     const float rho = __fsub_rn(__fsub_rn(1.0f, t.hi), t.lo);

@@ -148,6 +148,7 @@ struct Ctx {
 
     // 2D tile path (image lattices): state on the pixel grid, ping-pong
     bool tile = false;
+    bool strip = false;                   // time steps without a sample on the strip kernel
     int tile_nphase = 0;
     int64_t tnp = 0;                      // pixels
     double *tx[2] = {nullptr, nullptr};   // [2][tnp] positions
@@ -254,6 +255,10 @@ cudaError_t tile3_init_accel(Ctx &c);
 cudaError_t tile3_observe(Ctx &c);
 cudaError_t tile3_export(Ctx &c, bool steps);
 int64_t tile3_count(const Ctx &c);
+
+// strip2d.cu: does this context's 2D tile path run its plain time steps on
+// the register-resident strip kernel (square lattice, F32 / DF modes)?
+bool strip_supported(const Ctx &c);
 
 // tile2d.cu
 cudaError_t tile_enqueue_steps(Ctx &c, int64_t nsteps, int start_buf);

@@ -142,6 +142,95 @@ __host__ __device__ constexpr int tile_min_ctas()
                                      : 6;
 }
 
+// Cascaded double-float sum (Ogita, Rump and Oishi, 2005) of a particle's
+// spring forces in the canonical order: a TwoSum chain over the high parts,
+// with their errors and the low parts summed in float. value() is the sum
+// as a double (exact conversion of both parts, one FP64 addition).
+struct DfSum {
+    float hs, el;
+    __device__ __forceinline__ void first_neg(ff t)
+    {
+        hs = -t.hi;
+        el = -t.lo;
+    }
+    __device__ __forceinline__ void sub(ff o)
+    {
+        const ff t = two_sum(hs, -o.hi);
+        hs = t.hi;
+        el = __fadd_rn(el, __fsub_rn(t.lo, o.lo));
+    }
+    __device__ __forceinline__ void add(ff o)
+    {
+        const ff t = two_sum(hs, o.hi);
+        hs = t.hi;
+        el = __fadd_rn(el, __fadd_rn(t.lo, o.lo));
+    }
+    __device__ __forceinline__ double value() const { return f2d_bits(hs) + f2d_bits(el); }
+};
+
+// The fixed-point modes' spring arithmetic, shared by every 2D kernel that
+// evaluates springs (tile, strip and batched kernels), so that all of them
+// produce the same bits. Input: the exact fixed-point spring vector
+// (dxq, dyq) = x_q - x_p of an intact spring of type t in forward slot
+// `slot`. Returns true when the break test (TEST) fires: r^2 > rc^2, the
+// force is then left at zero. Otherwise writes the force on the lower
+// endpoint, f = k (1 - r0/r) d (Eq. 2), and with SAMPLE the spring's x
+// component d_x and its stretch r - r0.
+
+// Double-float force: d as a double-float (two exact 24-bit chunks), 1/r by
+// one double-float Newton step, k (r - r0) / r = k (1 - r0 / r).
+template <bool TEST, bool SAMPLE>
+__device__ __forceinline__ bool spring_df(long long dxq, long long dyq, const TypeDF &t, const TileArgs &A,
+                                          ff &fx, ff &fy, ff &dx, ff &st)
+{
+    const ff dxf = fix_to_ff_i2f2(dxq, A.p48, A.p24, A.p0);
+    const ff dyf = fix_to_ff_i2f2(dyq, A.p48, A.p24, A.p0);
+    const ff r2 = ff_norm2(dxf, dyf);
+    if (TEST && ff_gt(r2, t.rc2)) return true;
+    ff y;
+    const ff g = ff_spring_g(r2, t.r0, SAMPLE ? &y : nullptr);
+    const ff c = ff_mul_un(t.k, g);  // the products stay unnormalised: they are only
+    fx = ff_mul_un(c, dxf);          // multiplied or summed further (DfSum)
+    fy = ff_mul_un(c, dyf);
+    if (SAMPLE) {
+        dx = dxf;
+        st = ff_mul(ff_mul(r2, y), g);  // r - r0
+    }
+    return false;
+}
+
+// Single-precision force: the deviation e = d - o from the slot's lattice
+// vector o is exact in fixed point, so r^2 - |o|^2 = (2 o + e).e carries no
+// cancellation in float. Products are explicitly rounded (no contraction
+// with the caller's sums, whatever the kernel).
+template <bool TEST, bool SAMPLE>
+__device__ __forceinline__ bool spring_f32(long long dxq, long long dyq, int slot, const TypeDF &t,
+                                           const ff (*soff)[3], const TileArgs &A, float &fx, float &fy,
+                                           float &dx, float &st)
+{
+    const int ox_i = slot == 0 ? 1 : (slot == 1 ? -1 : (slot == 2 ? 0 : 1));
+    const int oy_i = slot == 0 ? 0 : 1;
+    const long long exf = dxq - (long long)ox_i * A.a_fix;
+    const long long eyf = dyq - (long long)oy_i * A.a_fix;
+    const float ex = fix_to_float_i2f(exf, A.p24, A.p0), ey = fix_to_float_i2f(eyf, A.p24, A.p0);
+    const float ox = soff[slot][0].hi, oy = soff[slot][1].hi;
+    const float dxf = __fadd_rn(ox, ex), dyf = __fadd_rn(oy, ey);
+    const float num = __fmaf_rn(__fadd_rn(__fmul_rn(2.0f, ox), ex), ex,
+                                __fmaf_rn(__fadd_rn(__fmul_rn(2.0f, oy), ey), ey, t.cor.hi));
+    const float r2f = __fadd_rn(soff[slot][2].hi, num);
+    if (TEST && r2f > t.rc2.hi) return true;
+    const float ir = rsqrt_approx(r2f);
+    const float s = __fdividef(num, __fmaf_rn(r2f, ir, t.r0.hi));  // r - r0
+    const float c = __fmul_rn(__fmul_rn(t.k.hi, s), ir);
+    fx = __fmul_rn(c, dxf);
+    fy = __fmul_rn(c, dyf);
+    if (SAMPLE) {
+        dx = dxf;
+        st = s;
+    }
+    return false;
+}
+
 // Force on the lower endpoint of one spring (rp -> rq, forward slot), with
 // the break test. Writes the force into sf; OWNER adds the sample sums and
 // records a break (only the tile owning the lower endpoint does).
@@ -196,52 +285,20 @@ __device__ __forceinline__ void eval_spring(const TileArgs &A, int rp, int rq, i
         } else {
             const TypeDF t = sdf[ti];
             if constexpr (PREC == LSM_PREC_F32) {
-                // exact spring vector d = o + e from the fixed-point positions;
-                // e is the deviation from the lattice vector o, so
-                // r^2 - |o|^2 = (2 o + e).e carries no cancellation in float
-                const int dx = slot == 0 ? 1 : (slot == 1 ? -1 : (slot == 2 ? 0 : 1));
-                const int dy = slot == 0 ? 0 : 1;
-                const long long exf = sxf[rq] - sxf[rp] - (long long)dx * A.a_fix;
-                const long long eyf = syf[rq] - syf[rp] - (long long)dy * A.a_fix;
-                const float ex = fix_to_float_i2f(exf, A.p24, A.p0), ey = fix_to_float_i2f(eyf, A.p24, A.p0);
-                const float ox = soff[slot][0].hi, oy = soff[slot][1].hi;
-                const float dxf = ox + ex, dyf = oy + ey;
-                const float num = fmaf(2.0f * ox + ex, ex, fmaf(2.0f * oy + ey, ey, t.cor.hi));
-                const float r2f = soff[slot][2].hi + num;
-                if (MODE == T_STEP && r2f > t.rc2.hi) {
-                    brk_now = true;
-                } else {
-                    const float ir = rsqrtf(r2f);
-                    const float st = __fdividef(num, fmaf(r2f, ir, t.r0.hi));  // r - r0
-                    const float c = t.k.hi * st * ir;
-                    fx = c * dxf;
-                    fy = c * dyf;
-                    if (SAMPLE && OWNER) {  // double-float sums: no FP64 pipe work per spring
-                        u_acc = ff_add_f(u_acc, 0.5f * t.k.hi * st * st);
-                        w_acc = ff_add_f(w_acc, dxf * fx);
-                    }
+                float dxf, st;
+                brk_now = spring_f32<MODE == T_STEP, SAMPLE && OWNER>(sxf[rq] - sxf[rp], syf[rq] - syf[rp], slot,
+                                                                      t, soff, A, fx, fy, dxf, st);
+                if (SAMPLE && OWNER && !brk_now) {  // double-float sums: no FP64 pipe work per spring
+                    u_acc = ff_add_f(u_acc, 0.5f * t.k.hi * st * st);
+                    w_acc = ff_add_f(w_acc, dxf * fx);
                 }
             } else {  // LSM_PREC_DF
-                // the spring vector d = x_j - x_i as an exact fixed-point
-                // difference, converted to a double-float; 1/r by Newton and
-                // k (r - r0) / r = k (1 - r0 / r), the same cancellation as
-                // FP64's k (r - r0) / r, resolved at 2^-46 instead of 2^-53
-                const ff dxf = fix_to_ff_i2f2(sxf[rq] - sxf[rp], A.p48, A.p24, A.p0);
-                const ff dyf = fix_to_ff_i2f2(syf[rq] - syf[rp], A.p48, A.p24, A.p0);
-                const ff r2 = ff_norm2(dxf, dyf);
-                if (MODE == T_STEP && ff_gt(r2, t.rc2)) {
-                    brk_now = true;
-                } else {
-                    ff y;
-                    const ff g = ff_spring_g(r2, t.r0, SAMPLE && OWNER ? &y : nullptr);
-                    const ff c = ff_mul(t.k, g);
-                    fx = ff_mul(c, dxf);
-                    fy = ff_mul(c, dyf);
-                    if (SAMPLE && OWNER) {  // double-float sums: no FP64 pipe work per spring
-                        const ff st = ff_mul(ff_mul(r2, y), g);  // r - r0
-                        u_acc = ff_add_sloppy(u_acc, ff_mul(ff_mul_f(t.k, 0.5f), ff_sqr(st)));
-                        w_acc = ff_add_sloppy(w_acc, ff_mul(dxf, fx));
-                    }
+                ff dxf, st;
+                brk_now = spring_df<MODE == T_STEP, SAMPLE && OWNER>(sxf[rq] - sxf[rp], syf[rq] - syf[rp], t, A,
+                                                                     fx, fy, dxf, st);
+                if (SAMPLE && OWNER && !brk_now) {  // double-float sums: no FP64 pipe work per spring
+                    u_acc = ff_add_sloppy(u_acc, ff_mul(ff_mul_f(t.k, 0.5f), ff_sqr(st)));
+                    w_acc = ff_add_sloppy(w_acc, ff_mul(dxf, fx));
                 }
             }
         }
@@ -458,38 +515,25 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
                 F[c] = acc;
             }
         } else if constexpr (PREC == LSM_PREC_DF) {
-            // cascaded summation (Ogita, Rump and Oishi, 2005): a TwoSum
-            // chain over the high parts, their errors and the low parts summed
-            // in float; same fixed order as above
+            // cascaded summation in the fixed order above (DfSum)
 #pragma unroll
             for (int c = 0; c < 2; c++) {
-                const ff t3 = sf[(c * 4 + 3) * NS + s3];
-                float hs = -t3.hi, el = -t3.lo;
-                const ff in2 = sf[(c * 4 + 2) * NS + s2], in1 = sf[(c * 4 + 1) * NS + s1],
-                         in0 = sf[(c * 4 + 0) * NS + s0];
-                ff t = two_sum(hs, -in2.hi);
-                hs = t.hi;
-                el = __fadd_rn(el, __fsub_rn(t.lo, in2.lo));
-                t = two_sum(hs, -in1.hi);
-                hs = t.hi;
-                el = __fadd_rn(el, __fsub_rn(t.lo, in1.lo));
-                t = two_sum(hs, -in0.hi);
-                hs = t.hi;
-                el = __fadd_rn(el, __fsub_rn(t.lo, in0.lo));
+                DfSum acc;
+                acc.first_neg(sf[(c * 4 + 3) * NS + s3]);
+                acc.sub(sf[(c * 4 + 2) * NS + s2]);
+                acc.sub(sf[(c * 4 + 1) * NS + s1]);
+                acc.sub(sf[(c * 4 + 0) * NS + s0]);
 #pragma unroll
-                for (int sl = 0; sl < 4; sl++) {
-                    const ff o = sf[(c * 4 + sl) * NS + rp];
-                    t = two_sum(hs, o.hi);
-                    hs = t.hi;
-                    el = __fadd_rn(el, __fadd_rn(t.lo, o.lo));
-                }
-                F[c] = f2d_bits(hs) + f2d_bits(el);
-                Ff[c] = __fadd_rn(hs, el);
-                Fd[c] = ff{hs, el};
+                for (int sl = 0; sl < 4; sl++) acc.add(sf[(c * 4 + sl) * NS + rp]);
+                F[c] = acc.value();
+                Ff[c] = __fadd_rn(acc.hs, acc.el);
+                Fd[c] = ff{acc.hs, acc.el};
             }
         } else {
 #pragma unroll
             for (int c = 0; c < 2; c++) {
+                // (o0 - i3) + (o1 - i2) + (o2 - i1) + (o3 - i0), outgoing slot
+                // s paired with the incoming spring of slot 3 - s
                 FT acc = sf[(c * 4 + 0) * NS + rp] - sf[(c * 4 + 3) * NS + s3];
                 acc += sf[(c * 4 + 1) * NS + rp] - sf[(c * 4 + 2) * NS + s2];
                 acc += sf[(c * 4 + 2) * NS + rp] - sf[(c * 4 + 1) * NS + s1];
@@ -609,6 +653,10 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
     }
 }
 
+
+// strip2d.cu: the register-resident time step (fixed-point modes, square
+// lattice, steps without a sample); bit-identical to the tile kernel's step.
+cudaError_t launch_strip(Ctx &c, const TileArgs &A);
 
 // Pixel-grid broken flags -> canonical spring order (defined in tile2d.cu).
 __global__ void k_tile_export(int nx, int ny, int64_t np, const uint8_t *__restrict__ phase,

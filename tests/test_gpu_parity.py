@@ -341,6 +341,44 @@ def test_tile_and_spring_list_paths_agree_bitwise(L):
     assert np.array_equal(outs[0][1][0], outs[1][1][0])
 
 
+@pytest.mark.parametrize("precision", ["df64", "f32"])
+def test_strip_and_tile_kernels_agree_bitwise(L, precision):
+    """The register-resident strip kernel (path 0, steps without a sample)
+    and the tile kernel (path 2, every step) perform the same operations in
+    the same order: states, velocities, broken sets, break steps and samples
+    are identical, through fracture, on ragged and voided images, with
+    roller and clamped grips, affine increments and constant strain-rate
+    loading, and on images narrower than a warp or one row high."""
+    k, e, m = two_phase_materials()
+    rng = np.random.default_rng(3)
+    cases = [(inclusion_image(100, 77, 2.0, 6.0, 0.3, 41), {}),
+             (inclusion_image(70, 45, 2.0, 5.0, 0.35, 42), {"grip_mode": 1}),
+             (rng.integers(0, 3, size=(45, 70)).astype(np.uint8), {}),
+             (inclusion_image(31, 9, 1.0, 2.0, 0.3, 43), {"a": 1.3}),
+             (np.ones((1, 40), np.uint8), {}),
+             (np.ones((3, 257), np.uint8), {})]
+    for ci, (img, kw) in enumerate(cases):
+        outs = []
+        for path in (0, 2):
+            g = L.Specimen.from_image(img, k, e, m, precision=precision, path=path, **kw)
+            for i in range(1, 31):
+                g.apply_strain(i * 3e-3)
+                g.step(10)
+            g.set_strain_rate(0.2)
+            for _ in range(5):
+                g.step(10)
+            x, v = g.state()
+            outs.append((x, v, g.broken(), g.break_steps(), g.samples()))
+            g.close()
+        (xa, va, ba, sa, ma), (xb, vb, bb, sb, mb) = outs
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb), ci
+        assert np.array_equal(ba[0], bb[0]) and ba[1] == bb[1], ci
+        assert np.array_equal(sa, sb), ci
+        assert ma == mb, ci
+        if ci == 0:
+            assert ba[0].sum() > 0, "the schedule must reach fracture"
+
+
 @pytest.mark.parametrize("path,a", [(0, 1.3), (0, 0.5), (1, 1.3)])
 def test_df64_general_lattice_spacing(oracle_mod, L, path, a):
     """df64 with a lattice spacing whose lattice vectors are not (1.3) or are
