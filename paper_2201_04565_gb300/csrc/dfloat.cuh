@@ -283,15 +283,21 @@ __device__ __forceinline__ ff ff_norm2(ff a, ff b)
 
 // The spring factor g = 1 - r0 / r from r^2 (double-float) and r0, with
 // y = 1/r to about 2^-46: the float reciprocal square root y0 (one float
-// Newton step), rho = 1 - r^2 y0^2 formed in double-float arithmetic, and
-// r0 / r = r0 y0 (1 + rho / 2). The product r0.hi y0 is exact (TwoProd), so
-// 1 - r0 y0 is exact up to the small terms summed in float. *y receives 1/r.
+// Newton step), the residual rho = 1 - r^2 y0^2, and r0 / r = r0 y0 (1 +
+// rho / 2). With y0^2 = q + qe exactly (TwoProd), rho is three fused
+// multiply-adds: 1 - r2.hi q is formed exactly before its one rounding
+// (r2.hi q lies within a few float ulps of 1, so about 26 significant bits
+// survive the cancellation), then the terms r2.hi qe and r2.lo q of order
+// 2^-24 follow (r2.lo qe, below 2^-47, is dropped). The product r0.hi y0 is
+// exact (TwoProd), so 1 - r0 y0 is exact up to the small terms summed in
+// float. *y receives 1/r.
 __device__ __forceinline__ ff ff_spring_g(ff r2, ff r0, ff *y)
 {
     float y0 = rsqrt_approx(r2.hi);
     y0 = __fmul_rn(y0, __fmaf_rn(-0.5f * r2.hi, __fmul_rn(y0, y0), 1.5f));
-    const ff t = ff_mul(r2, two_prod(y0, y0));
-    const float rho = __fsub_rn(__fsub_rn(1.0f, t.hi), t.lo);
+    const ff q = two_prod(y0, y0);
+    const float rho =
+        __fmaf_rn(-r2.lo, q.hi, __fmaf_rn(-r2.hi, q.lo, __fmaf_rn(-r2.hi, q.hi, 1.0f)));
     const ff p = two_prod(r0.hi, y0);
     float t2 = __fmaf_rn(-r0.lo, y0, -p.lo);
     t2 = __fmaf_rn(-0.5f * p.hi, rho, t2);

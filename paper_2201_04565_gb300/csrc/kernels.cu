@@ -465,6 +465,7 @@ static cudaError_t upload_tile(Ctx &c)
     c.tnp = np;
     c.tile_nphase = h.nphase;
     c.ntiles = tile_count(c);
+    if (c.strip) LSM_TRY(strip_geometry(c));
     std::vector<double> X(2 * np);
     for (int64_t g = 0; g < np; g++) {
         X[g] = (g % h.nx) * h.a;
@@ -515,8 +516,11 @@ static cudaError_t upload_tile(Ctx &c)
     LSM_TRY(dalloc(&c.tinvm, 4 * h.nphase));
     LSM_TRY(dalloc(&c.tdf, tdf.size()));
     LSM_TRY(dalloc(&c.tsbase, np));
-    LSM_TRY(dalloc(&c.part_s, 2 * c.ntiles));
-    LSM_TRY(dalloc(&c.part_p, 4 * c.ntiles));
+    {  // partial sums: per tile (tile kernel samples) or per strip (strip samples)
+        const int64_t np_ = std::max<int64_t>(c.ntiles, c.nstrips);
+        LSM_TRY(dalloc(&c.part_s, 2 * np_));
+        LSM_TRY(dalloc(&c.part_p, 4 * np_));
+    }
     LSM_TRY(upload_common(c));
     cudaStream_t st = c.stream;
     for (int b = 0; b < 2; b++) {
@@ -661,10 +665,13 @@ static void gather(Ctx &c)
         c.h.damping, c.part_p, c.nblk_p, c.d_status, c.d_step);
 }
 
-static void reduce(Ctx &c, DeviceSample *dst, long long *counter, long long add_steps)
+// Fold the partial sums of the last sample kernel into one sample. strips:
+// they came from a strip-kernel step (one partial per strip), not from the
+// tile kernel (one per tile) or the spring-list kernels (one per block).
+static void reduce(Ctx &c, DeviceSample *dst, long long *counter, long long add_steps, bool strips = false)
 {
-    const int64_t nbs = c.tile ? c.ntiles : (c.m ? c.nblk_s : 1);
-    const int64_t nbp = c.tile ? c.ntiles : c.nblk_p;
+    const int64_t nbs = strips ? c.nstrips : c.tile ? c.ntiles : (c.m ? c.nblk_s : 1);
+    const int64_t nbp = strips ? c.nstrips : c.tile ? c.ntiles : c.nblk_p;
     k_reduce<<<1, RED_THREADS, 0, c.stream>>>(c.part_s, nbs, c.part_p, nbp, c.d_eps, c.d_nbroken,
                                               c.d_step, add_steps, c.h.omega, c.h.grip_area, dst,
                                               counter, c.sample_cap, c.rate_on, c.rate_eps0, c.rate_step0,
@@ -701,10 +708,11 @@ static cudaError_t enqueue_tile_steps(Ctx &c, int64_t nsteps, bool record)
 {
     cudaError_t e = c.dim == 3 ? tile3_enqueue_steps(c, nsteps, c.tcur) : tile_enqueue_steps(c, nsteps, c.tcur);
     if (e != cudaSuccess) return e;
+    const bool strips = c.dim == 2 && c.strip;  // the sample step ran on the strip kernel
     if (record)
-        reduce(c, c.samples, c.d_nsamples, nsteps);
+        reduce(c, c.samples, c.d_nsamples, nsteps, strips);
     else
-        reduce(c, c.scratch_sample, nullptr, nsteps);
+        reduce(c, c.scratch_sample, nullptr, nsteps, strips);
     return cudaGetLastError();
 }
 

@@ -148,7 +148,9 @@ struct Ctx {
 
     // 2D tile path (image lattices): state on the pixel grid, ping-pong
     bool tile = false;
-    bool strip = false;                   // time steps without a sample on the strip kernel
+    bool strip = false;                   // 2D time steps on the strip kernel (strip2d.cu)
+    int strip_R = 0, strip_nsx = 0;       // rows per strip, strips across
+    int64_t nstrips = 0;                  // strips (= partial sums of a strip sample step)
     int tile_nphase = 0;
     int64_t tnp = 0;                      // pixels
     double *tx[2] = {nullptr, nullptr};   // [2][tnp] positions
@@ -259,6 +261,7 @@ int64_t tile3_count(const Ctx &c);
 // strip2d.cu: does this context's 2D tile path run its plain time steps on
 // the register-resident strip kernel (square lattice, F32 / DF modes)?
 bool strip_supported(const Ctx &c);
+cudaError_t strip_geometry(Ctx &c);  // strip_R, strip_nsx, nstrips for this device
 
 // tile2d.cu
 cudaError_t tile_enqueue_steps(Ctx &c, int64_t nsteps, int start_buf);

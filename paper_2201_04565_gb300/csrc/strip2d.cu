@@ -92,9 +92,9 @@ __device__ __forceinline__ PixRaw strip_fetch(const TileArgs &A, int gx, int gy)
 // The fetched pixel at the start of the step: position drifted by dt vh on
 // free components (a grip's x stays, or follows the constant strain rate);
 // an owned pixel's drifted position is written to x_out (pixel index g).
-template <bool RATE>
+template <bool RATE, bool SAMPLE>
 __device__ __forceinline__ PixFix strip_make(const TileArgs &A, const PixRaw &r, int gx, int64_t g, bool own,
-                                             bool &over)
+                                             bool &over, bool &bad)
 {
     PixFix p{0, 0, 0u};
     if (!r.ph) return p;
@@ -111,6 +111,7 @@ __device__ __forceinline__ PixFix strip_make(const TileArgs &A, const PixRaw &r,
     if (own) {
         A.x_out[g] = px;
         A.x_out[A.np + g] = py;
+        if (SAMPLE) bad |= !dbl_finite_bits(px) || !dbl_finite_bits(py);
     }
     p.xf = dbl_to_fix(px, A.S, over);
     p.yf = dbl_to_fix(py, A.S, over);
@@ -119,45 +120,95 @@ __device__ __forceinline__ PixFix strip_make(const TileArgs &A, const PixRaw &r,
 }
 
 // Force on the lower endpoint p of the spring p -> q in forward slot `slot`
-// (zero if either pixel holds no particle or the spring is broken); returns
-// true when the break test fires in this step.
-template <int PREC, typename FT>
-__device__ __forceinline__ bool strip_spring(const TileArgs &A, const PixFix &p, const PixFix &q, int slot,
-                                             const TypeDF *sdf, const ff (*soff)[3], FT &fx, FT &fy)
+// (zero if either pixel holds no particle or the spring is broken). Returns
+// S_NONE (no spring, or broken before), S_BREAK (the break test fires in
+// this step) or S_FORCE; with SAMPLE and S_FORCE also the spring's d_x, its
+// stretch r - r0 and its type.
+enum { S_NONE = 0, S_BREAK = 1, S_FORCE = 2 };
+
+template <int PREC, bool SAMPLE, typename FT>
+__device__ __forceinline__ int strip_spring(const TileArgs &A, const PixFix &p, const PixFix &q, int slot,
+                                            const TypeDF *sdf, const ff (*soff)[3], FT &fx, FT &fy, FT &dx,
+                                            FT &st, TypeDF &t)
 {
     fx = FT{};
     fy = FT{};
     const unsigned pp = p.pm & 0xffu, pq = q.pm & 0xffu;
-    if (!pp || !pq || ((p.pm >> (8 + slot)) & 1u)) return false;
-    const TypeDF t = sdf[(((int)(pp - 1) * A.nphase) + (int)(pq - 1)) * 2 + (slot & 1)];
-    if constexpr (PREC == LSM_PREC_DF) {
-        ff dx, st;
-        return spring_df<true, false>(q.xf - p.xf, q.yf - p.yf, t, A, fx, fy, dx, st);
-    } else {
-        float dx, st;
-        return spring_f32<true, false>(q.xf - p.xf, q.yf - p.yf, slot, t, soff, A, fx, fy, dx, st);
+    if (!pp || !pq || ((p.pm >> (8 + slot)) & 1u)) return S_NONE;
+    t = sdf[(((int)(pp - 1) * A.nphase) + (int)(pq - 1)) * 2 + (slot & 1)];
+    bool b;
+    if constexpr (PREC == LSM_PREC_DF)
+        b = spring_df<true, SAMPLE>(q.xf - p.xf, q.yf - p.yf, t, A, fx, fy, dx, st);
+    else
+        b = spring_f32<true, SAMPLE>(q.xf - p.xf, q.yf - p.yf, slot, t, soff, A, fx, fy, dx, st);
+    return b ? S_BREAK : S_FORCE;
+}
+
+// The sample sums of one intact spring: potential energy 1/2 k (r - r0)^2
+// and the virial term d_x f_x (the tile kernel's terms). A lane sums a
+// whole column of its strip, so the double-float sums take the accurate
+// addition (a few units of 2^-48 relative per term) rather than the
+// one-TwoSum form a tile's two rows per thread can afford.
+template <typename FT>
+__device__ __forceinline__ void spring_sample(ff &u, ff &w, const TypeDF &t, FT dx, FT fx, FT st);
+template <>
+__device__ __forceinline__ void spring_sample<ff>(ff &u, ff &w, const TypeDF &t, ff dx, ff fx, ff st)
+{
+    u = ff_add(u, ff_mul(ff_mul_f(t.k, 0.5f), ff_sqr(st)));
+    w = ff_add(w, ff_mul(dx, fx));
+}
+template <>
+__device__ __forceinline__ void spring_sample<float>(ff &u, ff &w, const TypeDF &t, float dx, float fx, float st)
+{
+    u = ff_add_f(u, 0.5f * t.k.hi * st * st);
+    w = ff_add_f(w, dx * fx);
+}
+
+__device__ __forceinline__ ff warp_sum_ff(ff v)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        const ff w{__shfl_xor_sync(FULL, v.hi, o), __shfl_xor_sync(FULL, v.lo, o)};
+        v = ff_add_sloppy(v, w);
     }
+    return v;
+}
+
+__device__ __forceinline__ float warp_max_f(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
+    return v;
 }
 
 }  // namespace
 
 // CTAs per SM the strip kernel is compiled for (its register budget without
-// spills: 80 registers in F32, 102 in DF).
-template <int PREC>
-constexpr int strip_min_ctas() { return PREC == LSM_PREC_DF ? 5 : 6; }
+// spills: 80 registers in the F32 time step, 102 in the DF one and in the
+// sample steps).
+template <int PREC, bool SAMPLE>
+constexpr int strip_min_ctas() { return PREC == LSM_PREC_DF || SAMPLE ? 5 : 6; }
 
-template <int PREC, bool RATE>
-__global__ void __launch_bounds__(32 * STRIP_WARPS, strip_min_ctas<PREC>())
+// SAMPLE: the last step of an lsm_step call also writes the full-step
+// velocity v(t+dt) = vh + dt/2 a and the strip's partial sums of the sample
+// (virial and potential energy of the owned springs, m v_x^2, kinetic
+// energy, right-grip reaction, residual) at index `strip` of the partial
+// arrays (stride A.ntiles = the number of strips), as the tile kernel does
+// per tile.
+template <int PREC, bool RATE, bool SAMPLE>
+__global__ void __launch_bounds__(32 * STRIP_WARPS, strip_min_ctas<PREC, SAMPLE>())
 k_strip2d(TileArgs A, int R, int nsx)
 {
     using FT = typename std::conditional<PREC == LSM_PREC_F32, float, ff>::type;
     __shared__ TypeDF sdf[128];
     __shared__ Coef4 scoef[8];
+    __shared__ float smassf[8];
     __shared__ ff soff[4][3];  // per slot: o_x, o_y, |o|^2 (F32)
     const int tid = threadIdx.x, lane = tid & 31;
     const int nt = 2 * A.nphase * A.nphase;
     for (int q = tid; q < nt; q += 32 * STRIP_WARPS) sdf[q] = A.tdf[q];
-    if (tid < A.nphase) scoef[tid] = A.coef[tid];
+    if (tid < A.nphase) {
+        scoef[tid] = A.coef[tid];
+        smassf[tid] = (float)A.mass[tid];
+    }
     if (PREC == LSM_PREC_F32 && tid < 4) {
         const int dx = tid == 0 ? 1 : (tid == 1 ? -1 : (tid == 2 ? 0 : 1));
         const int dy = tid == 0 ? 0 : 1;
@@ -175,12 +226,18 @@ k_strip2d(TileArgs A, int R, int nsx)
     const int y1 = min(y0 + R, A.ny);
     const int gx = sx * STRIP_OWN - 1 + lane;  // lanes 0 and 31: the neighbour columns
     const bool owner = lane >= 1 && lane <= STRIP_OWN && gx < A.nx;
+    const bool grip = gx == 0 || gx == A.nx - 1;
+    const bool fixy = grip && A.grip_mode == 1;
     const long long step_now = *A.d_step + A.t_off;
-    bool over = false;
+    bool over = false, bad = false;
+    // sample sums; m v_x^2 and the kinetic energy are float terms (2^-24
+    // relative each, as in the tile kernel) summed as double-floats
+    ff w_acc{0.0f, 0.0f}, u_acc{0.0f, 0.0f}, reactf{0.0f, 0.0f}, mvx2{0.0f, 0.0f}, ke{0.0f, 0.0f};
+    float resf = 0.0f;
 
     // row y0 - 1: its springs into row y0 are evaluated, it is not owned
     PixRaw raw = strip_fetch(A, gx, y0 - 1);
-    PixFix P = strip_make<RATE>(A, raw, gx, 0, false, over);
+    PixFix P = strip_make<RATE, SAMPLE>(A, raw, gx, 0, false, over, bad);
     raw = strip_fetch(A, gx, y0);
     double vcx = 0.0, vcy = 0.0;
     FT p1x{}, p1y{}, p2x{}, p2y{}, p3x{}, p3y{};  // previous row's slot 1-3 forces
@@ -189,8 +246,9 @@ k_strip2d(TileArgs A, int R, int nsx)
         const bool own = y >= y0;  // warp-uniform
         // 1. row y + 1 (fetched last iteration), then fetch row y + 2
         const double vnx = raw.vx, vny = raw.vy;
-        const PixFix N = strip_make<RATE>(A, raw, gx, (int64_t)(y + 1) * A.nx + gx, owner && y + 1 < y1, over);
-        raw = strip_fetch(A, gx, y + 2 < y1 + 1 ? y + 2 : -1);
+        const PixFix N =
+            strip_make<RATE, SAMPLE>(A, raw, gx, (int64_t)(y + 1) * A.nx + gx, owner && y + 1 < y1, over, bad);
+        raw = strip_fetch(A, gx, y + 2 <= y1 ? y + 2 : -1);
 
         // 2. the forward springs of row y; the shuffles that wrap around the
         // warp (lane 31's right and lane 0's left neighbour) carry no particle
@@ -199,8 +257,11 @@ k_strip2d(TileArgs A, int R, int nsx)
         PixFix q3 = shfl_pix(N, lane + 1);
         if (lane == 31) q0.pm = q3.pm = 0u;
         if (lane == 0) q1.pm = 0u;
-        FT f0x, f0y;
-        const bool b0 = strip_spring<PREC>(A, P, q0, 0, sdf, soff, f0x, f0y);
+        const bool sum_springs = SAMPLE && own && owner;
+        FT f0x, f0y, dx, st;
+        TypeDF t;
+        const int s0 = strip_spring<PREC, SAMPLE>(A, P, q0, 0, sdf, soff, f0x, f0y, dx, st, t);
+        if (sum_springs && s0 == S_FORCE) spring_sample(u_acc, w_acc, t, dx, f0x, st);
         const FT i0x = shfl_ft(f0x, lane - 1), i0y = shfl_ft(f0y, lane - 1);
         const FT i3x = shfl_ft(p3x, lane - 1), i3y = shfl_ft(p3y, lane - 1);
         const FT i1x = shfl_ft(p1x, lane + 1), i1y = shfl_ft(p1y, lane + 1);
@@ -223,13 +284,18 @@ k_strip2d(TileArgs A, int R, int nsx)
             sy_ = f0y - i3y;
         }
         FT f1x, f1y, f2x, f2y, f3x, f3y;
-        const bool b1 = strip_spring<PREC>(A, P, q1, 1, sdf, soff, f1x, f1y);
-        const bool b2 = strip_spring<PREC>(A, P, N, 2, sdf, soff, f2x, f2y);
-        const bool b3 = strip_spring<PREC>(A, P, q3, 3, sdf, soff, f3x, f3y);
+        const int s1 = strip_spring<PREC, SAMPLE>(A, P, q1, 1, sdf, soff, f1x, f1y, dx, st, t);
+        if (sum_springs && s1 == S_FORCE) spring_sample(u_acc, w_acc, t, dx, f1x, st);
+        const int s2 = strip_spring<PREC, SAMPLE>(A, P, N, 2, sdf, soff, f2x, f2y, dx, st, t);
+        if (sum_springs && s2 == S_FORCE) spring_sample(u_acc, w_acc, t, dx, f2x, st);
+        const int s3 = strip_spring<PREC, SAMPLE>(A, P, q3, 3, sdf, soff, f3x, f3y, dx, st, t);
+        if (sum_springs && s3 == S_FORCE) spring_sample(u_acc, w_acc, t, dx, f3x, st);
 
         // 3. gather + integrate the owned particle (gx, y)
         if (own) {
             double F[2];
+            float Ff[2];  // F as floats (sample statistics without FP64 work)
+            ff Fx;        // F_x as a double-float (the grip reaction)
             if constexpr (PREC == LSM_PREC_DF) {
                 ax.add(f1x);
                 ax.add(f2x);
@@ -239,6 +305,9 @@ k_strip2d(TileArgs A, int R, int nsx)
                 ay.add(f3y);
                 F[0] = ax.value();
                 F[1] = ay.value();
+                Ff[0] = __fadd_rn(ax.hs, ax.el);
+                Ff[1] = __fadd_rn(ay.hs, ay.el);
+                Fx = ff{ax.hs, ax.el};
             } else {
                 sx_ += f1x - p2x;
                 sy_ += f1y - p2y;
@@ -248,15 +317,40 @@ k_strip2d(TileArgs A, int R, int nsx)
                 sy_ += f3y - i0y;
                 F[0] = f2d_bits(sx_);
                 F[1] = f2d_bits(sy_);
+                Ff[0] = sx_;
+                Ff[1] = sy_;
+                Fx = ff{sx_, 0.0f};
             }
             if (owner && (P.pm & 0xffu)) {
                 const int64_t g = (int64_t)y * A.nx + gx;
-                const Coef4 k4 = scoef[(P.pm & 0xffu) - 1];
-                const bool grip = gx == 0 || gx == A.nx - 1;
-                const bool fixy = grip && A.grip_mode == 1;
-                A.vh_out[g] = grip ? 0.0 : fma(k4.c2, F[0], k4.c1 * vcx);
-                A.vh_out[A.np + g] = fixy ? 0.0 : fma(k4.c2, F[1], k4.c1 * vcy);
-                const int nb = (int)b0 | ((int)b1 << 1) | ((int)b2 << 2) | ((int)b3 << 3);
+                const int ph = (int)(P.pm & 0xffu) - 1;
+                const Coef4 k4 = scoef[ph];
+                if (SAMPLE && gx == A.nx - 1) reactf = ff_add(reactf, ff_neg(Fx));
+                const double vh[2] = {vcx, vcy};
+                const bool fixed[2] = {grip, fixy};
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    const int64_t q = c * A.np + g;
+                    if (fixed[c]) {
+                        A.vh_out[q] = 0.0;
+                        if (SAMPLE) A.v_obs[q] = 0.0;
+                        continue;
+                    }
+                    A.vh_out[q] = fma(k4.c2, F[c], k4.c1 * vh[c]);
+                    if (SAMPLE) {
+                        const double vn = fma(k4.c2h, F[c], k4.c1h * vh[c]);
+                        A.v_obs[q] = vn;
+                        // float statistics (residual, KE, m v_x^2), as the tile kernel
+                        const float vf = d2f_bits(vn);
+                        resf = fmaxf(resf, fmaxf(fabsf(Ff[c]), fabsf(vf)));
+                        const float mv2 = __fmul_rn(__fmul_rn(smassf[ph], vf), vf);
+                        ke = ff_add_f(ke, __fmul_rn(0.5f, mv2));
+                        if (c == 0) mvx2 = ff_add_f(mvx2, mv2);
+                        bad |= !dbl_finite_bits(vn);
+                    }
+                }
+                const int nb = (int)(s0 == S_BREAK) | ((int)(s1 == S_BREAK) << 1) | ((int)(s2 == S_BREAK) << 2) |
+                               ((int)(s3 == S_BREAK) << 3);
                 if (nb) {
                     A.mask[g] = (uint8_t)((P.pm >> 8) | (unsigned)nb);
 #pragma unroll
@@ -283,35 +377,64 @@ k_strip2d(TileArgs A, int R, int nsx)
         vcy = vny;
     }
     if (__any_sync(FULL, over) && lane == 0) atomicOr(A.status, 2);
+    if (SAMPLE) {
+        if (__any_sync(FULL, bad) && lane == 0) atomicOr(A.status, 1);
+        const ff tw = warp_sum_ff(w_acc), tu = warp_sum_ff(u_acc), tr = warp_sum_ff(reactf);
+        const ff tm = warp_sum_ff(mvx2), tk = warp_sum_ff(ke);
+        const float tres = warp_max_f(resf);
+        if (lane == 0) {
+            A.part_s[strip] = ff_to_double(tw);
+            A.part_s[A.ntiles + strip] = ff_to_double(tu);
+            A.part_p[strip] = ff_to_double(tm);
+            A.part_p[A.ntiles + strip] = ff_to_double(tk);
+            A.part_p[2 * A.ntiles + strip] = ff_to_double(tr);
+            A.part_p[3 * A.ntiles + strip] = f2d_bits(tres);
+        }
+    }
 }
 
 // ------------------------------------------------------------------ host
 
 namespace {
 
-template <int PREC, bool RATE>
-cudaError_t launch_strip_t(Ctx &c, const TileArgs &A)
+// Warps of the time-step instance that fit on the device at once.
+template <int PREC>
+cudaError_t strip_resident(int &resident)
 {
-    auto kern = k_strip2d<PREC, RATE>;
-    static int resident = 0;  // warps per device of this instance (occupancy x SMs)
-    if (!resident) {
+    static int cached = 0;  // per precision
+    if (!cached) {
         int dev = 0, nsm = 0, nb = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 32 * STRIP_WARPS, 0);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_strip2d<PREC, false, false>,
+                                                              32 * STRIP_WARPS, 0);
         if (e != cudaSuccess) return e;
-        resident = std::max(1, nb * STRIP_WARPS * nsm);
+        cached = std::max(1, nb * STRIP_WARPS * nsm);
     }
-    // strip height: one warp per strip, as many strips as fit on the device
-    // at once (one wave), but at least 8 rows per strip
-    const int nsx = (c.h.nx + STRIP_OWN - 1) / STRIP_OWN;
-    const int rows_target = std::max(1, resident / nsx);
-    const int R = std::max(8, (c.h.ny + rows_target - 1) / rows_target);
-    const int nsy = (c.h.ny + R - 1) / R;
-    const int64_t nstrips = (int64_t)nsx * nsy;
-    const unsigned grid = (unsigned)((nstrips + STRIP_WARPS - 1) / STRIP_WARPS);
-    kern<<<grid, 32 * STRIP_WARPS, 0, c.stream>>>(A, R, nsx);
+    resident = cached;
     return cudaSuccess;
+}
+
+template <int PREC, bool RATE, bool SAMPLE>
+void launch_strip_t(Ctx &c, TileArgs A)
+{
+    if (SAMPLE) A.ntiles = c.nstrips;  // partial-sum stride
+    const unsigned grid = (unsigned)((c.nstrips + STRIP_WARPS - 1) / STRIP_WARPS);
+    k_strip2d<PREC, RATE, SAMPLE><<<grid, 32 * STRIP_WARPS, 0, c.stream>>>(A, c.strip_R, c.strip_nsx);
+}
+
+template <bool SAMPLE>
+void launch_strip_s(Ctx &c, const TileArgs &A)
+{
+    const bool rate = c.rate_on;
+    if (c.h.precision == LSM_PREC_DF) {
+        if (rate) launch_strip_t<LSM_PREC_DF, true, SAMPLE>(c, A);
+        else launch_strip_t<LSM_PREC_DF, false, SAMPLE>(c, A);
+    } else {
+        if (rate) launch_strip_t<LSM_PREC_F32, true, SAMPLE>(c, A);
+        else launch_strip_t<LSM_PREC_F32, false, SAMPLE>(c, A);
+    }
 }
 
 }  // namespace
@@ -322,12 +445,29 @@ bool strip_supported(const Ctx &c)
            (c.h.precision == LSM_PREC_DF || c.h.precision == LSM_PREC_F32);
 }
 
-cudaError_t launch_strip(Ctx &c, const TileArgs &A)
+// Strip geometry: one warp per strip of 30 owned columns and R rows, as many
+// strips as fit on the device at once (one wave), but at least 8 rows each.
+cudaError_t strip_geometry(Ctx &c)
 {
-    const bool rate = c.rate_on;
-    if (c.h.precision == LSM_PREC_DF)
-        return rate ? launch_strip_t<LSM_PREC_DF, true>(c, A) : launch_strip_t<LSM_PREC_DF, false>(c, A);
-    return rate ? launch_strip_t<LSM_PREC_F32, true>(c, A) : launch_strip_t<LSM_PREC_F32, false>(c, A);
+    int resident = 0;
+    cudaError_t e = c.h.precision == LSM_PREC_DF ? strip_resident<LSM_PREC_DF>(resident)
+                                                 : strip_resident<LSM_PREC_F32>(resident);
+    if (e != cudaSuccess) return e;
+    const int nsx = (c.h.nx + STRIP_OWN - 1) / STRIP_OWN;
+    const int rows_target = std::max(1, resident / nsx);
+    const int R = std::max(8, (c.h.ny + rows_target - 1) / rows_target);
+    const int nsy = (c.h.ny + R - 1) / R;
+    c.strip_R = R;
+    c.strip_nsx = nsx;
+    c.nstrips = (int64_t)nsx * nsy;
+    return cudaSuccess;
+}
+
+cudaError_t launch_strip(Ctx &c, const TileArgs &A, bool sample)
+{
+    if (sample) launch_strip_s<true>(c, A);
+    else launch_strip_s<false>(c, A);
+    return cudaSuccess;
 }
 
 }  // namespace lsm

@@ -209,9 +209,10 @@ cudaError_t tile_enqueue_steps(Ctx &c, int64_t nsteps, int start_buf)
         A.vh_in = c.tvh[cur];
         A.x_out = c.tx[cur ^ 1];
         A.vh_out = c.tvh[cur ^ 1];
-        cudaError_t e = t == nsteps - 1 ? launch_tile_prec<T_STEP, true>(c, A)
-                        : c.strip       ? launch_strip(c, A)
-                                        : launch_tile_prec<T_STEP, false>(c, A);
+        const bool last = t == nsteps - 1;
+        cudaError_t e = c.strip ? launch_strip(c, A, last)
+                        : last  ? launch_tile_prec<T_STEP, true>(c, A)
+                                : launch_tile_prec<T_STEP, false>(c, A);
         if (e != cudaSuccess) return e;
         cur ^= 1;
     }

@@ -655,8 +655,9 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
 
 
 // strip2d.cu: the register-resident time step (fixed-point modes, square
-// lattice, steps without a sample); bit-identical to the tile kernel's step.
-cudaError_t launch_strip(Ctx &c, const TileArgs &A);
+// lattice); its positions, velocities and breaks are bit-identical to the
+// tile kernel's (sample sums: per strip instead of per tile).
+cudaError_t launch_strip(Ctx &c, const TileArgs &A, bool sample);
 
 // Pixel-grid broken flags -> canonical spring order (defined in tile2d.cu).
 __global__ void k_tile_export(int nx, int ny, int64_t np, const uint8_t *__restrict__ phase,

@@ -100,11 +100,13 @@ def load_params(net, path):
 
 @_on_work_stream
 def generate(images, k, e, m, increments, deps=1e-3, tol=1e-6, max_steps=200000, check_every=50,
-             precision="f32", log=None):
+             precision="f32", log=None, pre_fracture=False):
     """Run every specimen through `increments` load increments with the batched
     relaxation and return the samples on the device:
     U [N][2][H][W] (displacement before), phase [S][H][W], spec [N] (specimen
-    index of each sample), eps [N] (strain before), T [N][H][W][2] (target)."""
+    index of each sample), eps [N] (strain before), T [N][H][W][2] (target).
+    pre_fracture: keep only the increments that end with no broken spring in
+    their specimen (the model the gated warm start uses)."""
     torch = _torch()
     S = len(images)
     H, W = images[0].shape
@@ -118,6 +120,7 @@ def generate(images, k, e, m, increments, deps=1e-3, tol=1e-6, max_steps=200000,
     spec = torch.arange(N, device="cuda", dtype=torch.int64) % S
     eps_b = torch.empty(N, dtype=torch.float32, device="cuda")
     loaded = torch.empty_like(f.u)
+    intact = torch.ones(N, dtype=torch.bool, device="cuda")
     steps = []
     t0 = time.perf_counter()
     for i in range(increments):
@@ -136,8 +139,13 @@ def generate(images, k, e, m, increments, deps=1e-3, tol=1e-6, max_steps=200000,
         if log:
             log("increment %d: mean steps %d, converged %d/%d, %.1fs" % (i + 1, steps[-1], conv.sum(), S,
                                                                          time.perf_counter() - t0))
+        if pre_fracture:
+            intact[i * S:(i + 1) * S] = torch.tensor([bt.broken(q)[1] < 0 for q in range(S)], device="cuda")
     torch.cuda.synchronize()
     bt.close()
+    if pre_fracture:
+        keep = torch.nonzero(intact).flatten()
+        U, T, spec, eps_b = U[keep].contiguous(), T[keep].contiguous(), spec[keep].contiguous(), eps_b[keep].contiguous()
     return dict(U=U, T=T, phase=phase, spec=spec, eps=eps_b, deps=deps, H=H, W=W, steps=steps,
                 seconds=time.perf_counter() - t0)
 
@@ -294,6 +302,56 @@ def compare(images, k, e, m, net, first_inc, increments, deps=1e-3, tol=1e-8, ma
     res["speedup_warm_vs_plain"] = res["plain"]["seconds_per_increment"] / res["warm"]["seconds_per_increment"]
     res["speedup_batched_vs_plain"] = res["plain"]["seconds_per_increment"] / res["batched"]["seconds_per_increment"]
     res["speedup_warm_vs_batched"] = res["batched"]["seconds_per_increment"] / res["warm"]["seconds_per_increment"]
+    return res
+
+
+@_on_work_stream
+def steps_to_tolerance(images, k, e, m, net, increments, deps=1e-3, tol=1e-8, max_steps=400000, check_every=50,
+                       precision="df64", gate=True, log=None):
+    """Steps the batched relaxation needs per increment, without the network
+    (arm "batched") and with its prediction added after each load step (arm
+    "warm"; gate: only for specimens with no broken spring yet), both to the
+    same force-residual tolerance, from the unloaded state through
+    `increments` increments. Returns per arm: steps [increment][specimen],
+    converged flags, wall seconds per increment, the final positions of
+    every specimen and its last sample."""
+    torch = _torch()
+    S = len(images)
+    H, W = images[0].shape
+    res = {}
+    for arm in ("batched", "warm"):
+        bt = bmod.Batch(images, k, e, m, precision=precision, stream=_stream(), **RELAX)
+        f = Fields(S, H, W)
+        f.read(bt, with_phase=True)
+        chunk = net.max_batch
+        xb = torch.empty((chunk, H, W, 32), dtype=torch.bfloat16, device="cuda")
+        out = torch.empty((chunk, H, W, 2), dtype=torch.float32, device="cuda")
+        du = torch.empty((S, 2, H, W), dtype=torch.float32, device="cuda")
+        steps, conv_all, secs = [], [], []
+        for i in range(1, increments + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if arm == "warm":
+                f.read(bt)  # state before the increment
+                _predict_du(net, f, bt, (i - 1) * deps, deps, xb, out, du, chunk)
+            bt.apply_strain(i * deps)
+            if arm == "warm":
+                if gate:
+                    for q in range(S):
+                        if bt.broken(q)[1] >= 0:
+                            du[q].zero_()
+                nnmod.check(nnmod.lib().lsm_batch_add_displacements(bt.h, nnmod.ptr(du), H, W), bt.h, batch=True)
+            st, taken, conv = bt.relax(tol, max_steps, check_every)
+            torch.cuda.synchronize()
+            secs.append(time.perf_counter() - t0)
+            steps.append([int(t) for t in taken])
+            conv_all.append([bool(c) for c in conv])
+            if log:
+                log("%s increment %d: %.2fs, steps %d (mean)" % (arm, i, secs[-1], int(np.mean(taken))))
+        res[arm] = dict(steps=steps, converged=conv_all, seconds=secs,
+                        x=[bt.state(q)[0] for q in range(S)], last=[bt.samples(q)[-1] for q in range(S)],
+                        first_break=[bt.broken(q)[1] for q in range(S)])
+        bt.close()
     return res
 
 

@@ -36,8 +36,12 @@ def _images():
 @pytest.mark.parametrize("precision", ["exact64", "df64"])
 @pytest.mark.parametrize("tile_y", [8, 16])
 def test_batch_matches_single_specimens(B, oracle_mod, precision, tile_y):
-    """Positions, velocities, breaks bit-identical; samples to 1e-12 (sample
-    steps run on 16-row tiles in both paths, whatever the steps' tiling)."""
+    """Positions, velocities, breaks bit-identical. Samples: exact64 to
+    1e-12 (its sample steps run on 16-row tiles in both paths, whatever the
+    steps' tiling); in df64 the single-specimen path sums its samples per
+    strip (strip kernel) and the batch per tile, so the stress agrees to the
+    double-float sums' 1e-10 plus the float kinetic term m v_x^2 (2^-24 per
+    particle): 1e-9."""
     batch, lsm = B
     imgs = _images()
     k, e, m = two_phase_materials()
@@ -63,7 +67,8 @@ def test_batch_matches_single_specimens(B, oracle_mod, precision, tile_y):
         assert len(sb) == len(ss) == 40
         for a, b in zip(sb, ss):
             assert a["step"] == b["step"] and a["n_broken"] == b["n_broken"] and a["eps"] == b["eps"]
-            assert a["sigma_vir"] == pytest.approx(b["sigma_vir"], rel=1e-12, abs=1e-300)
+            rel = 1e-12 if precision == "exact64" else 1e-9
+            assert a["sigma_vir"] == pytest.approx(b["sigma_vir"], rel=rel, abs=1e-300)
     assert any_break
     if precision == "exact64":  # and the oracle itself
         o = oracle_mod.Oracle.from_image(imgs[2], k, e, m)

@@ -343,12 +343,16 @@ def test_tile_and_spring_list_paths_agree_bitwise(L):
 
 @pytest.mark.parametrize("precision", ["df64", "f32"])
 def test_strip_and_tile_kernels_agree_bitwise(L, precision):
-    """The register-resident strip kernel (path 0, steps without a sample)
-    and the tile kernel (path 2, every step) perform the same operations in
-    the same order: states, velocities, broken sets, break steps and samples
-    are identical, through fracture, on ragged and voided images, with
-    roller and clamped grips, affine increments and constant strain-rate
-    loading, and on images narrower than a warp or one row high."""
+    """The register-resident strip kernel (path 0) and the tile kernel
+    (path 2) perform the same operations in the same order on every particle
+    and spring: states, velocities, broken sets and break steps are
+    identical, through fracture, on ragged and voided images, with roller
+    and clamped grips, affine increments and constant strain-rate loading,
+    and on images narrower than a warp or one row high. The samples' sums
+    are grouped per strip in one and per tile in the other: the double-float
+    sums (virial, energy, reaction) agree to 1e-10; the kinetic terms are
+    float statistics (2^-24 relative per particle, see the tile kernel), so
+    the kinetic energy agrees to 1e-6; the residual (a maximum) exactly."""
     k, e, m = two_phase_materials()
     rng = np.random.default_rng(3)
     cases = [(inclusion_image(100, 77, 2.0, 6.0, 0.3, 41), {}),
@@ -374,7 +378,13 @@ def test_strip_and_tile_kernels_agree_bitwise(L, precision):
         assert np.array_equal(xa, xb) and np.array_equal(va, vb), ci
         assert np.array_equal(ba[0], bb[0]) and ba[1] == bb[1], ci
         assert np.array_equal(sa, sb), ci
-        assert ma == mb, ci
+        assert len(ma) == len(mb) == 35, ci
+        for a_, b_ in zip(ma, mb):
+            for key in ("eps", "n_broken", "step", "residual"):
+                assert a_[key] == b_[key], (ci, key)
+            for key in ("sigma_vir", "sigma_grip", "pe"):
+                assert a_[key] == pytest.approx(b_[key], rel=1e-10, abs=1e-300), (ci, key)
+            assert a_["ke"] == pytest.approx(b_["ke"], rel=1e-6, abs=1e-300), ci
         if ci == 0:
             assert ba[0].sum() > 0, "the schedule must reach fracture"
 
