@@ -127,6 +127,14 @@ NCU_INSTRUCTIONS = {
     "exact64": (195704900, "023b81ce7d44"),
 }
 
+# Time-step kernel of each mode on the 2D image lattice.
+KERNEL = {
+    "df64": "k_strip2d (register-resident strip kernel, one launch per time step)",
+    "f32": "k_strip2d (register-resident strip kernel, one launch per time step)",
+    "fast64": "k_tile2d (tile kernel, one launch per time step)",
+    "exact64": "k_tile2d (tile kernel, one launch per time step)",
+}
+
 # Binding unit of each mode's time-step kernel, from ncu on the same workload
 # (see the profile summaries), for the roofline's "limiter" note.
 LIMITER = {
@@ -138,11 +146,12 @@ LIMITER = {
 
 
 def _kernel_tag():
-    """sha1 prefix of the tile kernel's sources (the kernel body lives in the
-    header shared with the batched kernel)."""
+    """sha1 prefix of the 2D time-step kernels' sources (the strip kernel of
+    the fixed-point modes, the tile kernel of the FP64 modes, and the
+    arithmetic they share)."""
     import hashlib
     h = hashlib.sha1()
-    for name in ("tile2d.cu", "tile_body.cuh", "dfloat.cuh"):
+    for name in ("strip2d.cu", "tile2d.cu", "tile_body.cuh", "dfloat.cuh"):
         with open(os.path.join(ROOT, "paper_2201_04565_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
@@ -265,7 +274,7 @@ def run_gpu(args, rank, world):
         "config": _config_2d(spec.n, spec.m, spec.dim, args.precision, world),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic,
-                     "kernel": "k_tile2d (one launch per time step)",
+                     "kernel": KERNEL.get(args.precision),
                      "algorithmic_bytes_per_launch": algb, "launch_ms": per_step_ms,
                      "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)",
                      "limiter": LIMITER.get(args.precision)},
@@ -479,7 +488,7 @@ def run_foam256(args):
 def run_next_rows(args):
     """The next rows of the scope on the 2048 x 2048 composite, one line
     each: the paper's triangular packing (lattice 1, spring-list kernels in
-    the fixed-point modes), constant strain-rate loading of the grips (the
+    the fixed-point modes: strip kernel on the packing's site grid), constant strain-rate loading of the grips (the
     tile kernel's rate instance; rate * dt * 20 = 1e-3 per 20 steps, as the
     increments of the main line), and the per-particle stress and strain
     fields (lsm_fields, particles per second). Same timing rules: warm-up
@@ -522,7 +531,7 @@ def run_next_rows(args):
         tri.apply_strain(i * WORKLOAD["eps_inc"])
         tri.step(nst)
     out["triangular_2048"] = line(tri, timed(tri, tri_inc), "2048x2048 image, triangular packing",
-                                  "k_springs_fix + k_gather_fix")
+                                  "k_strip2d (triangular packing: site grid, three forward slots)")
     tri.close()
 
     sq = lsm.Specimen.from_image(img, k, e, m, dt=WORKLOAD["dt"], damping=WORKLOAD["damping"],
@@ -531,7 +540,7 @@ def run_next_rows(args):
     sq.set_strain_rate(WORKLOAD["eps_inc"] / (nst * WORKLOAD["dt"]))
     out["strain_rate_2048"] = line(sq, timed(sq, lambda i: sq.step(nst)),
                                    "2048x2048 composite, grips at a constant strain rate",
-                                   "k_tile2d (rate-loading instance)")
+                                   KERNEL.get(args.precision, "k_tile2d") + ", rate-loading instance")
     sq.fields()  # first call allocates the field buffers
     sq.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

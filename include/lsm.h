@@ -67,9 +67,10 @@ typedef enum {
  *  LSM_PREC_DF: as LSM_PREC_F32, but the spring force and the gather use
  *      double-float arithmetic (pairs of floats, 48 significant bits), so
  *      forces carry about 1e-14 relative error while the FP64 pipe only does
- *      the integration. For image builds DF and F32 run on the fused 2D tile
- *      kernel, on the 3D voxel tile kernel, or (path 1, triangular packing)
- *      on the spring-list kernels with the same fixed-point spring vectors.
+ *      the integration. For image builds DF and F32 run on the 2D strip or
+ *      tile kernels (square lattice), the strip kernel (triangular
+ *      packing), the 3D voxel tile kernel, or (path 1) the spring-list
+ *      kernels with the same fixed-point spring vectors.
  *      Network builds have no lattice vectors:
  *      there F32 forms the spring vector in double and DF runs as
  *      LSM_PREC_FAST64. */
@@ -98,13 +99,19 @@ enum { LSM_PREC_EXACT64 = 0, LSM_PREC_FAST64 = 1, LSM_PREC_F32 = 2, LSM_PREC_DF 
  *               about the specimen centre, then sets the grips;
  *               1 = only the grips move.
  *  precision    LSM_PREC_* (see above).
- *  path         0 = automatic (square-lattice images with up to 8 phases
- *               run the fused tile kernels: every mode in 2D, the F32 and DF
- *               modes in 3D; in 2D the F32 and DF time steps without a sample
- *               run the register-resident strip kernel, bit-identical to the
- *               tile kernel; everything else runs the general spring-list
- *               kernels); 1 = always the general spring-list kernels;
- *               2 = as 0, but every 2D time step on the tile kernel.
+ *  path         0 = automatic: images with up to 8 phases run on the grid
+ *               of their pixels or sites. Square lattice: the fused tile
+ *               kernel in every mode; in the F32 and DF modes, when the
+ *               image is large enough for its strips to fill the device,
+ *               the time steps run on the register-resident strip kernel
+ *               instead (the same positions, velocities and breaks; sample
+ *               sums grouped per strip). Triangular packing (F32, DF): the
+ *               strip kernel. 3D (F32, DF): the voxel tile kernel.
+ *               Everything else: the general spring-list kernels.
+ *               1 = always the general spring-list kernels;
+ *               2 = as 0, but every square-lattice 2D step on the tile kernel;
+ *               3 = as 0, but the 2D F32 / DF steps on the strip kernel
+ *               whatever the image size.
  *  stream       cudaStream_t to order work on (NULL = the library creates one).
  *  lattice      0 = square (2D) / cubic (3D) lattice as above; 1 = the
  *               paper's triangular packing (2D only, Section 1: six first

@@ -49,11 +49,18 @@ lsm_status finish_build(lsm_ctx *c, void *stream, lsm_ctx **out, int path = 0)
     // the voxel tile kernel in the fixed-point modes (the FP64 modes stay on
     // the spring-list kernels, see tile3d.cu)
     const bool fixmode = c->h.precision == LSM_PREC_F32 || c->h.precision == LSM_PREC_DF;
-    c->tile = path != 1 && c->h.nx > 0 && c->h.lattice == 0 && c->h.nphase >= 1 && c->h.nphase <= 8 &&
-              (c->h.dim == 2 || (c->h.dim == 3 && fixmode));
-    // 2D fixed-point modes: steps without a sample on the strip kernel
-    // (path 2 keeps every step on the tile kernel; same bits either way)
-    c->strip = c->tile && path != 2 && lsm::strip_supported(*c);
+    // the triangular packing (2D, fixed-point modes, path 0) runs on the
+    // strip kernel alone, its state on the grid of its sites
+    c->tri = (path == 0 || path == 3) && c->h.nx > 0 && c->h.lattice == 1 && c->h.dim == 2 && fixmode && c->h.nphase >= 1 &&
+             c->h.nphase <= 8;
+    c->tile = c->tri || (path != 1 && c->h.nx > 0 && c->h.lattice == 0 && c->h.nphase >= 1 && c->h.nphase <= 8 &&
+                         (c->h.dim == 2 || (c->h.dim == 3 && fixmode)));
+    // 2D fixed-point modes: time steps on the strip kernel when its strips
+    // fill the device (path 2: the square lattice's tile kernel always; path
+    // 3: the strip kernel always; same states either way)
+    c->strip = c->tile && (c->tri || path != 2) && lsm::strip_supported(*c);
+    c->strip_forced = path == 3;
+    c->path_req = path;
     if (stream) {
         c->stream = (cudaStream_t)stream;
     } else {
@@ -135,9 +142,10 @@ lsm_status lsm_build_from_image(const lsm_desc *desc, lsm_ctx **out)
         delete c;
         return fail(nullptr, LSM_EINVAL, err);
     }
-    if (desc->path < 0 || desc->path > 2) {
+    if (desc->path < 0 || desc->path > 3) {
         delete c;
-        return fail(nullptr, LSM_EINVAL, "path must be 0 (automatic), 1 (spring-list kernels) or 2 (tile kernel for every 2D step)");
+        return fail(nullptr, LSM_EINVAL, "path must be 0 (automatic), 1 (spring-list kernels), 2 (2D tile kernel) or "
+                                         "3 (2D strip kernel)");
     }
     return finish_build(c, desc->stream, out, desc->path);
 }
@@ -405,7 +413,7 @@ lsm_status lsm_get_state(lsm_ctx *c, double *x, double *v)
         if (e != cudaSuccess) return cuda_fail(c, e, "get_state");
         for (int cc = 0; cc < c->dim; cc++)
             for (int64_t p = 0; p < c->n; p++) {
-                const int64_t g = c->h.pix[p];
+                const int64_t g = c->tgidx[p];
                 if (x) x[cc * c->n + p] = gx[cc * c->tnp + g];
                 if (v) v[cc * c->n + p] = gv[cc * c->tnp + g];
             }
@@ -436,7 +444,7 @@ lsm_status lsm_set_state(lsm_ctx *c, const double *x, const double *v)
         if (e != cudaSuccess) return cuda_fail(c, e, "set_state");
         for (int cc = 0; cc < c->dim; cc++)
             for (int64_t p = 0; p < c->n; p++) {
-                const int64_t g = c->h.pix[p];
+                const int64_t g = c->tgidx[p];
                 if (x) gx[cc * c->tnp + g] = x[cc * c->n + p];
                 if (v) gv[cc * c->tnp + g] = v[cc * c->n + p];
             }

@@ -989,7 +989,7 @@ lsm_status lsm_batch_broken_mask(lsm_batch *b, int32_t spec, uint8_t *out, int64
     }
     const int64_t np = (int64_t)b->nx[spec] * b->ny[spec], P = b->pbase[spec];
     lsm::k_tile_export<<<(unsigned)((np + 255) / 256), 256, 0, b->stream>>>(
-        b->nx[spec], b->ny[spec], np, b->PH + P, b->MASK + P, b->BRK + 4 * P, b->SBASE + P, b->export_buf, nullptr);
+        b->nx[spec], b->ny[spec], np, b->PH + P, b->MASK + P, b->BRK + 4 * P, b->SBASE + P, b->export_buf, nullptr, 0);
     unsigned long long fb = 0;
     if (b->m[spec]) e = cudaMemcpyAsync(out, b->export_buf, b->m[spec], cudaMemcpyDeviceToHost, b->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&fb, b->fb + spec, sizeof(fb), cudaMemcpyDeviceToHost, b->stream);

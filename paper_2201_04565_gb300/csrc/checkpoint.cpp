@@ -7,7 +7,8 @@
 //   the HostNet: scalars in a fixed order, then each vector as u64 count +
 //   raw elements (X, mass, fixm, grip, si, sj, stype, types, pix, phase,
 //   sdir, offv)
-//   u32 path (0: kernels chosen by the build rule, 1: spring-list kernels),
+//   u32 path (the build's path request: 0 kernels chosen by the build rule,
+//            1 spring-list kernels, 2 2D tile kernel, 3 2D strip kernel),
 //   u32 tile (the context ran on a tile path)
 //   host mirrors: eps, steps, nsamples, launches, the strain-rate settings
 //   device scalars: step, first break, broken count, status, eps, sample count
@@ -168,7 +169,7 @@ std::vector<std::pair<void *, size_t>> state_buffers(Ctx &c)
 cudaError_t checkpoint_save(Ctx &c, const char *path, std::string &err)
 {
     CkptState s;
-    s.path = c.tile ? 0 : 1;
+    s.path = c.tile ? (uint32_t)c.path_req : 1;  // 0 automatic, 2 tile kernel, 3 strip kernel
     s.tile = c.tile ? 1 : 0;
     s.eps = c.eps;
     s.steps = c.steps;
@@ -314,7 +315,7 @@ bool checkpoint_read(const char *path, HostNet &h, CkptState &s, std::string &er
     bool fine = h.dim >= 2 && h.dim <= 3 && h.n >= 0 && h.m >= 0 && h.X.size() == (size_t)h.dim * n &&
                 h.mass.size() == n && h.fixm.size() == n && h.grip.size() == n && h.si.size() == m &&
                 h.sj.size() == m && h.stype.size() == m && (int64_t)s.samples.size() == s.nsamples &&
-                h.precision >= LSM_PREC_EXACT64 && h.precision <= LSM_PREC_DF && (s.path == 0 || s.path == 1);
+                h.precision >= LSM_PREC_EXACT64 && h.precision <= LSM_PREC_DF && s.path <= 3;
     for (size_t q = 0; fine && q < m; q++)
         fine = h.si[q] >= 0 && h.sj[q] >= 0 && (size_t)h.si[q] < n && (size_t)h.sj[q] < n &&
                h.stype[q] < h.types.size();

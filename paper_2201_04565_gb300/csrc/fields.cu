@@ -233,7 +233,11 @@ cudaError_t fields_compute(Ctx &c, double cell)
             if ((e = up(&c.fsj, h.sj.data(), h.sj.size(), st)) != cudaSuccess) return e;
             if ((e = up(&c.fstype, h.stype.data(), h.stype.size(), st)) != cudaSuccess) return e;
             if ((e = up(&c.fmass, h.mass.data(), h.mass.size(), st)) != cudaSuccess) return e;
-            if ((e = up(&c.fpix, h.pix.data(), h.pix.size(), st)) != cudaSuccess) return e;
+            if (c.dim == 2) {  // grid index of each particle (pixel, or site of the packing)
+                if ((e = up(&c.fpix, c.tgidx.data(), c.tgidx.size(), st)) != cudaSuccess) return e;
+            } else if ((e = up(&c.fpix, h.pix.data(), h.pix.size(), st)) != cudaSuccess) {
+                return e;
+            }
             if ((e = lsm::dev_malloc((void **)&c.fx, (size_t)h.dim * (n ? n : 1) * sizeof(double))) != cudaSuccess) return e;
             if ((e = lsm::dev_malloc((void **)&c.fv, (size_t)h.dim * (n ? n : 1) * sizeof(double))) != cudaSuccess) return e;
             // the host vectors above must outlive their copies

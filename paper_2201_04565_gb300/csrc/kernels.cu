@@ -461,18 +461,49 @@ static ff split_ff(double v)
 static cudaError_t upload_tile(Ctx &c)
 {
     const HostNet &h = c.h;
-    const int64_t np = (int64_t)h.nx * h.ny;
+    // the tile grid: the pixel grid, or the triangular packing's sites (rows
+    // of nx sites at y = iy h; odd rows use the first nx - 1, shifted by a/2)
+    const double hrow = h.a * std::sqrt(3.0) * 0.5;
+    c.tgnx = h.nx;
+    c.tgny = h.ny;
+    c.tgidx.assign(h.n, 0);
+    std::vector<uint8_t> gphase;
+    if (c.tri) {
+        int64_t rows = 0;
+        for (int64_t p = 0; p < h.n; p++) rows = std::max<int64_t>(rows, std::llround(h.X[h.n + p] / hrow) + 1);
+        c.tgny = (int)rows;
+        gphase.assign((size_t)c.tgnx * c.tgny, 0);
+        for (int64_t p = 0; p < h.n; p++) {
+            const int64_t iy = std::llround(h.X[h.n + p] / hrow);
+            const int64_t ix = std::llround(h.X[p] / h.a - ((iy & 1) ? 0.5 : 0.0));
+            c.tgidx[p] = iy * c.tgnx + ix;
+            gphase[c.tgidx[p]] = h.phase[h.pix[p]];
+        }
+    } else {
+        for (int64_t p = 0; p < h.n; p++) c.tgidx[p] = h.pix[p];
+    }
+    const uint8_t *gph = c.tri ? gphase.data() : h.phase.data();
+    const int64_t np = (int64_t)c.tgnx * c.tgny;
     c.tnp = np;
     c.tile_nphase = h.nphase;
-    c.ntiles = tile_count(c);
-    if (c.strip) LSM_TRY(strip_geometry(c));
+    c.ntiles = c.tri ? 0 : tile_count(c);
+    if (c.strip) {
+        bool fills = true;
+        LSM_TRY(strip_geometry(c, &fills));
+        if (!fills && !c.tri && !c.strip_forced) {  // small image: the tile kernel
+            c.strip = false;
+            c.nstrips = 0;
+        }
+    }
+    if (c.tri) c.ntiles = c.nstrips;  // the packing's samples all come from the strip kernel
     std::vector<double> X(2 * np);
     for (int64_t g = 0; g < np; g++) {
-        X[g] = (g % h.nx) * h.a;
-        X[np + g] = (g / h.nx) * h.a;
+        const int64_t ix = g % c.tgnx, iy = g / c.tgnx;
+        X[g] = c.tri ? (ix + ((iy & 1) ? 0.5 : 0.0)) * h.a : ix * h.a;
+        X[np + g] = c.tri ? iy * hrow : iy * h.a;
     }
     std::vector<double> mtab(h.nphase, 1.0), itab(h.nphase, 1.0);
-    for (int64_t p = 0; p < h.n; p++) mtab[h.phase[h.pix[p]] - 1] = h.mass[p];
+    for (int64_t p = 0; p < h.n; p++) mtab[gph[c.tgidx[p]] - 1] = h.mass[p];
     itab.assign(4 * h.nphase, 0.0);  // per phase: 1 - dt g/m, dt/m, 1 - dt/2 g/m, dt/2 / m
     for (int q = 0; q < h.nphase; q++) {
         const double dt = h.dt, hdt = 0.5 * h.dt, g = h.damping, m = mtab[q];
@@ -489,16 +520,20 @@ static cudaError_t upload_tile(Ctx &c)
     c.fix_S = 61 - (int)std::ceil(std::log2(extent));
     c.fix_S = std::min(c.fix_S, 47 - (int)std::ceil(std::log2(h.a * std::sqrt(2.0))));
     c.a_fix = std::llround(std::ldexp(h.a, c.fix_S));
+    c.h_fix = std::llround(std::ldexp(hrow, c.fix_S));
     std::vector<int64_t> sbase(np, 0);
-    for (int64_t s = h.m - 1; s >= 0; s--) sbase[h.pix[h.si[s]]] = s;
+    for (int64_t s = h.m - 1; s >= 0; s--) sbase[c.tgidx[h.si[s]]] = s;
     std::vector<TypeDF> tdf(h.types.size());
     for (size_t q = 0; q < h.types.size(); q++) {
         const SpringType &t = h.types[q];
-        const double shell = (q & 1) ? 2.0 : 1.0;  // type id = pair * 2 + (shell - 1)
-        const double aa = (double)c.a_fix * std::ldexp(1.0, -c.fix_S);  // lattice spacing as used
+        // the type's lattice vector o as the F32 kernels use it (fixed point):
+        // square lattice (a, 0) or (a, a) by shell; triangular packing (a, 0)
+        // for the row spring, (a/2, h) for the other two
+        const double ox = std::ldexp((double)(c.tri && (q & 1) ? (c.a_fix >> 1) : c.a_fix), -c.fix_S);
+        const double oy = (q & 1) ? std::ldexp((double)(c.tri ? c.h_fix : c.a_fix), -c.fix_S) : 0.0;
         // |o|^2 - r0^2 with the products' rounding errors kept (fma)
         const double p = t.r0 * t.r0, pe = std::fma(t.r0, t.r0, -p);
-        const double o2 = shell * aa * aa, o2e = shell * std::fma(aa, aa, -(aa * aa));
+        const double o2 = ox * ox + oy * oy, o2e = std::fma(ox, ox, -(ox * ox)) + std::fma(oy, oy, -(oy * oy));
         tdf[q].k = split_ff(t.k);
         tdf[q].r0 = split_ff(t.r0);
         tdf[q].rc2 = split_ff(t.rc2);
@@ -528,7 +563,7 @@ static cudaError_t upload_tile(Ctx &c)
         LSM_TRY(cudaMemsetAsync(c.tvh[b], 0, 2 * np * sizeof(double), st));
     }
     LSM_TRY(cudaMemsetAsync(c.tvobs, 0, 2 * np * sizeof(double), st));
-    LSM_TRY(cudaMemcpyAsync(c.tph, h.phase.data(), np, cudaMemcpyHostToDevice, st));
+    LSM_TRY(cudaMemcpyAsync(c.tph, gph, np, cudaMemcpyHostToDevice, st));
     LSM_TRY(cudaMemsetAsync(c.tmask, 0, np, st));
     LSM_TRY(cudaMemsetAsync(c.tbrk, 0xff, 4 * np * sizeof(long long), st));
     LSM_TRY(cudaMemcpyAsync(c.tmass, mtab.data(), h.nphase * sizeof(double), cudaMemcpyHostToDevice, st));

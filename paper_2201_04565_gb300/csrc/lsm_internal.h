@@ -149,6 +149,12 @@ struct Ctx {
     // 2D tile path (image lattices): state on the pixel grid, ping-pong
     bool tile = false;
     bool strip = false;                   // 2D time steps on the strip kernel (strip2d.cu)
+    bool strip_forced = false;            // path 3: the strip kernel whatever the image size
+    int path_req = 0;                     // the build's path request (kept by checkpoints)
+    bool tri = false;                     // tile path of the triangular packing (strip kernel only)
+    int tgnx = 0, tgny = 0;               // 2D tile grid: pixels, or sites (nx per row, rows) of the packing
+    std::vector<int64_t> tgidx;           // [n] grid index of each particle (host)
+    long long h_fix = 0;                  // packing: row height a sqrt(3)/2 in fixed point
     int strip_R = 0, strip_nsx = 0;       // rows per strip, strips across
     int64_t nstrips = 0;                  // strips (= partial sums of a strip sample step)
     int tile_nphase = 0;
@@ -261,7 +267,7 @@ int64_t tile3_count(const Ctx &c);
 // strip2d.cu: does this context's 2D tile path run its plain time steps on
 // the register-resident strip kernel (square lattice, F32 / DF modes)?
 bool strip_supported(const Ctx &c);
-cudaError_t strip_geometry(Ctx &c);  // strip_R, strip_nsx, nstrips for this device
+cudaError_t strip_geometry(Ctx &c, bool *fills);  // strip_R, strip_nsx, nstrips for this device
 
 // tile2d.cu
 cudaError_t tile_enqueue_steps(Ctx &c, int64_t nsteps, int start_buf);

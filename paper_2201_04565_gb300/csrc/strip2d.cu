@@ -73,8 +73,11 @@ __device__ __forceinline__ ff shfl_ft<ff>(ff v, int src)
     return ff{__shfl_sync(FULL, v.hi, src), __shfl_sync(FULL, v.lo, src)};
 }
 
-// Issue the loads of pixel (gx, gy); x and vh are read whatever the phase
-// (the state arrays cover every pixel) so that no load waits on another.
+// Issue the loads of pixel (gx, gy); x and the velocity are read whatever
+// the phase (the state arrays cover every pixel) so that no load waits on
+// another. VOBS: the full-step velocity (initial acceleration, observation)
+// instead of the half-step one.
+template <bool VOBS = false>
 __device__ __forceinline__ PixRaw strip_fetch(const TileArgs &A, int gx, int gy)
 {
     PixRaw r{0.0, 0.0, 0.0, 0.0, 0u, 0u};
@@ -84,31 +87,46 @@ __device__ __forceinline__ PixRaw strip_fetch(const TileArgs &A, int gx, int gy)
     r.mk = A.mask[g];
     r.x = A.x_in[g];
     r.y = A.x_in[A.np + g];
-    r.vx = A.vh_in[g];
-    r.vy = A.vh_in[A.np + g];
+    const double *v = VOBS ? A.v_obs : A.vh_in;
+    r.vx = v[g];
+    r.vy = v[A.np + g];
     return r;
 }
 
 // The fetched pixel at the start of the step: position drifted by dt vh on
 // free components (a grip's x stays, or follows the constant strain rate);
 // an owned pixel's drifted position is written to x_out (pixel index g).
-template <bool RATE, bool SAMPLE>
-__device__ __forceinline__ PixFix strip_make(const TileArgs &A, const PixRaw &r, int gx, int64_t g, bool own,
-                                             bool &over, bool &bad)
+// Reference x of site (gx, row parity par): gx a on the square lattice,
+// (gx + par / 2) a on the triangular packing.
+template <int LAT>
+__device__ __forceinline__ double site_X(const TileArgs &A, int gx, int par)
+{
+    if constexpr (LAT == 0) return ml((double)gx, A.a);
+    else return ml(ad((double)gx, par ? 0.5 : 0.0), A.a);
+}
+
+// Drift (time steps only): the position moved by dt vh on free components;
+// a grip (first or last site of its row, row length C) keeps its x, or
+// follows the constant strain rate.
+template <bool RATE, bool SAMPLE, int LAT, int MODE>
+__device__ __forceinline__ PixFix strip_make(const TileArgs &A, const PixRaw &r, int gx, int par, int C, int64_t g,
+                                             bool own, bool &over, bool &bad)
 {
     PixFix p{0, 0, 0u};
     if (!r.ph) return p;
     double px = r.x, py = r.y;
-    const bool grip = gx == 0 || gx == A.nx - 1;
-    if (RATE && grip) {  // constant strain rate: grip x at the strain of this step
-        const long long s = *A.d_step + A.t_off + 1 - A.rate_step0;
-        const double eps = ad(A.rate_eps0, ml((double)s, A.rate_dt));
-        const double X = ml((double)gx, A.a);
-        px = ad(X, ml(eps, sb(X, A.xc)));
+    const bool grip = gx == 0 || gx == C - 1;
+    if (MODE == T_STEP) {
+        if (RATE && grip) {  // constant strain rate: grip x at the strain of this step
+            const long long s = *A.d_step + A.t_off + 1 - A.rate_step0;
+            const double eps = ad(A.rate_eps0, ml((double)s, A.rate_dt));
+            const double X = site_X<LAT>(A, gx, par);
+            px = ad(X, ml(eps, sb(X, A.xc)));
+        }
+        if (!grip) px = fma(A.dt, r.vx, px);
+        if (!(grip && A.grip_mode == 1)) py = fma(A.dt, r.vy, py);
     }
-    if (!grip) px = fma(A.dt, r.vx, px);
-    if (!(grip && A.grip_mode == 1)) py = fma(A.dt, r.vy, py);
-    if (own) {
+    if (MODE == T_STEP && own) {
         A.x_out[g] = px;
         A.x_out[A.np + g] = py;
         if (SAMPLE) bad |= !dbl_finite_bits(px) || !dbl_finite_bits(py);
@@ -126,7 +144,11 @@ __device__ __forceinline__ PixFix strip_make(const TileArgs &A, const PixRaw &r,
 // stretch r - r0 and its type.
 enum { S_NONE = 0, S_BREAK = 1, S_FORCE = 2 };
 
-template <int PREC, bool SAMPLE, typename FT>
+// Slots: square lattice (+1,0), (-1,+1), (0,+1), (+1,+1), type shell
+// slot & 1; triangular packing (+1, same row), (-1/2, next row), (+1/2,
+// next row), shell 0 for the row spring and 1 for the other two (their
+// fixed-point lattice vectors share one |o|^2, the F32 correction term).
+template <int PREC, bool SAMPLE, bool TEST, int LAT, typename FT>
 __device__ __forceinline__ int strip_spring(const TileArgs &A, const PixFix &p, const PixFix &q, int slot,
                                             const TypeDF *sdf, const ff (*soff)[3], FT &fx, FT &fy, FT &dx,
                                             FT &st, TypeDF &t)
@@ -135,12 +157,19 @@ __device__ __forceinline__ int strip_spring(const TileArgs &A, const PixFix &p, 
     fy = FT{};
     const unsigned pp = p.pm & 0xffu, pq = q.pm & 0xffu;
     if (!pp || !pq || ((p.pm >> (8 + slot)) & 1u)) return S_NONE;
-    t = sdf[(((int)(pp - 1) * A.nphase) + (int)(pq - 1)) * 2 + (slot & 1)];
+    const int shell = LAT == 0 ? (slot & 1) : (slot != 0);
+    t = sdf[(((int)(pp - 1) * A.nphase) + (int)(pq - 1)) * 2 + shell];
     bool b;
-    if constexpr (PREC == LSM_PREC_DF)
-        b = spring_df<true, SAMPLE>(q.xf - p.xf, q.yf - p.yf, t, A, fx, fy, dx, st);
-    else
-        b = spring_f32<true, SAMPLE>(q.xf - p.xf, q.yf - p.yf, slot, t, soff, A, fx, fy, dx, st);
+    if constexpr (PREC == LSM_PREC_DF) {
+        b = spring_df<TEST, SAMPLE>(q.xf - p.xf, q.yf - p.yf, t, A, fx, fy, dx, st);
+    } else if constexpr (LAT == 0) {
+        b = spring_f32<TEST, SAMPLE>(q.xf - p.xf, q.yf - p.yf, slot, t, soff, A, fx, fy, dx, st);
+    } else {
+        const long long ah = A.a_fix >> 1;
+        const long long ofx = slot == 0 ? A.a_fix : (slot == 1 ? -ah : ah), ofy = slot == 0 ? 0 : A.h_fix;
+        b = spring_f32_o<TEST, SAMPLE>(q.xf - p.xf, q.yf - p.yf, ofx, ofy, soff[slot][0].hi, soff[slot][1].hi,
+                                       soff[slot][2].hi, t, A, fx, fy, dx, st);
+    }
     return b ? S_BREAK : S_FORCE;
 }
 
@@ -187,17 +216,24 @@ __device__ __forceinline__ float warp_max_f(float v)
 template <int PREC, bool SAMPLE>
 constexpr int strip_min_ctas() { return PREC == LSM_PREC_DF || SAMPLE ? 5 : 6; }
 
-// SAMPLE: the last step of an lsm_step call also writes the full-step
-// velocity v(t+dt) = vh + dt/2 a and the strip's partial sums of the sample
-// (virial and potential energy of the owned springs, m v_x^2, kinetic
-// energy, right-grip reaction, residual) at index `strip` of the partial
-// arrays (stride A.ntiles = the number of strips), as the tile kernel does
-// per tile.
-template <int PREC, bool RATE, bool SAMPLE>
+// LAT: 0 square lattice (4 forward slots), 1 triangular packing (3; rows
+// alternate between nx sites and nx - 1 sites shifted by half a spacing).
+// MODE: T_STEP (a time step), T_INIT (the initial acceleration: half-step
+// velocity from the current forces, no drift, no break test), T_OBSERVE (the
+// sample of the current state). SAMPLE: the last step of an lsm_step call,
+// or an observation, also writes the full-step velocity v(t+dt) = vh + dt/2
+// a (steps) and the strip's partial sums of the sample (virial and
+// potential energy of the owned springs, m v_x^2, kinetic energy,
+// right-grip reaction, residual) at index `strip` of the partial arrays
+// (stride A.ntiles = the number of strips), as the tile kernel does per
+// tile.
+template <int PREC, bool RATE, bool SAMPLE, int LAT, int MODE>
 __global__ void __launch_bounds__(32 * STRIP_WARPS, strip_min_ctas<PREC, SAMPLE>())
 k_strip2d(TileArgs A, int R, int nsx)
 {
     using FT = typename std::conditional<PREC == LSM_PREC_F32, float, ff>::type;
+    constexpr bool TEST = MODE == T_STEP;
+    constexpr bool VOBS = MODE != T_STEP;
     __shared__ TypeDF sdf[128];
     __shared__ Coef4 scoef[8];
     __shared__ float smassf[8];
@@ -210,9 +246,16 @@ k_strip2d(TileArgs A, int R, int nsx)
         smassf[tid] = (float)A.mass[tid];
     }
     if (PREC == LSM_PREC_F32 && tid < 4) {
-        const int dx = tid == 0 ? 1 : (tid == 1 ? -1 : (tid == 2 ? 0 : 1));
-        const int dy = tid == 0 ? 0 : 1;
-        const ff ox = fix_to_ff((long long)dx * A.a_fix, A.S), oy = fix_to_ff((long long)dy * A.a_fix, A.S);
+        long long ofx, ofy;
+        if (LAT == 0) {
+            ofx = (tid == 0 ? 1 : (tid == 1 ? -1 : (tid == 2 ? 0 : 1))) * A.a_fix;
+            ofy = (tid == 0 ? 0 : 1) * A.a_fix;
+        } else {
+            const long long ah = A.a_fix >> 1;
+            ofx = tid == 0 ? A.a_fix : (tid == 1 ? -ah : ah);
+            ofy = tid == 0 ? 0 : A.h_fix;
+        }
+        const ff ox = fix_to_ff(ofx, A.S), oy = fix_to_ff(ofy, A.S);
         soff[tid][0] = ox;
         soff[tid][1] = oy;
         soff[tid][2] = ff_add(ff_mul(ox, ox), ff_mul(oy, oy));
@@ -226,70 +269,113 @@ k_strip2d(TileArgs A, int R, int nsx)
     const int y1 = min(y0 + R, A.ny);
     const int gx = sx * STRIP_OWN - 1 + lane;  // lanes 0 and 31: the neighbour columns
     const bool owner = lane >= 1 && lane <= STRIP_OWN && gx < A.nx;
-    const bool grip = gx == 0 || gx == A.nx - 1;
-    const bool fixy = grip && A.grip_mode == 1;
-    const long long step_now = *A.d_step + A.t_off;
+    const long long step_now = MODE == T_STEP ? *A.d_step + A.t_off : 0;
     bool over = false, bad = false;
     // sample sums; m v_x^2 and the kinetic energy are float terms (2^-24
     // relative each, as in the tile kernel) summed as double-floats
     ff w_acc{0.0f, 0.0f}, u_acc{0.0f, 0.0f}, reactf{0.0f, 0.0f}, mvx2{0.0f, 0.0f}, ke{0.0f, 0.0f};
     float resf = 0.0f;
+    // row length (sites) of row y: nx, or nx - 1 on odd rows of the packing
+    auto row_len = [&](int y) { return LAT == 0 ? A.nx : A.nx - (y & 1); };
 
     // row y0 - 1: its springs into row y0 are evaluated, it is not owned
-    PixRaw raw = strip_fetch(A, gx, y0 - 1);
-    PixFix P = strip_make<RATE, SAMPLE>(A, raw, gx, 0, false, over, bad);
-    raw = strip_fetch(A, gx, y0);
+    PixRaw raw = strip_fetch<VOBS>(A, gx, y0 - 1);
+    PixFix P = strip_make<RATE, SAMPLE, LAT, MODE>(A, raw, gx, (y0 - 1) & 1, row_len(y0 - 1), 0, false, over, bad);
+    raw = strip_fetch<VOBS>(A, gx, y0);
     double vcx = 0.0, vcy = 0.0;
-    FT p1x{}, p1y{}, p2x{}, p2y{}, p3x{}, p3y{};  // previous row's slot 1-3 forces
+    FT p1x{}, p1y{}, p2x{}, p2y{}, p3x{}, p3y{};  // previous row's forces (slots 1..3)
 
     for (int y = y0 - 1; y < y1; y++) {
         const bool own = y >= y0;  // warp-uniform
+        const int par = y & 1;     // row parity (triangular packing)
         // 1. row y + 1 (fetched last iteration), then fetch row y + 2
         const double vnx = raw.vx, vny = raw.vy;
-        const PixFix N =
-            strip_make<RATE, SAMPLE>(A, raw, gx, (int64_t)(y + 1) * A.nx + gx, owner && y + 1 < y1, over, bad);
-        raw = strip_fetch(A, gx, y + 2 <= y1 ? y + 2 : -1);
+        const PixFix N = strip_make<RATE, SAMPLE, LAT, MODE>(A, raw, gx, par ^ 1, row_len(y + 1),
+                                                             (int64_t)(y + 1) * A.nx + gx, owner && y + 1 < y1,
+                                                             over, bad);
+        raw = strip_fetch<VOBS>(A, gx, y + 2 <= y1 ? y + 2 : -1);
 
         // 2. the forward springs of row y; the shuffles that wrap around the
         // warp (lane 31's right and lane 0's left neighbour) carry no particle
         PixFix q0 = shfl_pix(P, lane + 1);
-        PixFix q1 = shfl_pix(N, lane - 1);
-        PixFix q3 = shfl_pix(N, lane + 1);
-        if (lane == 31) q0.pm = q3.pm = 0u;
-        if (lane == 0) q1.pm = 0u;
+        if (lane == 31) q0.pm = 0u;
+        PixFix q1, q3;
+        if constexpr (LAT == 0) {
+            q1 = shfl_pix(N, lane - 1);
+            q3 = shfl_pix(N, lane + 1);
+            if (lane == 31) q3.pm = 0u;
+            if (lane == 0) q1.pm = 0u;
+        } else {  // targets (gx - 1 + par, y + 1) and (gx + par, y + 1)
+            q1 = shfl_pix(N, lane - 1 + par);
+            q3 = par ? shfl_pix(N, lane + 1) : N;
+            if (lane == 0 && !par) q1.pm = 0u;
+            if (lane == 31 && par) q3.pm = 0u;
+        }
         const bool sum_springs = SAMPLE && own && owner;
         FT f0x, f0y, dx, st;
         TypeDF t;
-        const int s0 = strip_spring<PREC, SAMPLE>(A, P, q0, 0, sdf, soff, f0x, f0y, dx, st, t);
+        const int s0 = strip_spring<PREC, SAMPLE, TEST, LAT>(A, P, q0, 0, sdf, soff, f0x, f0y, dx, st, t);
         if (sum_springs && s0 == S_FORCE) spring_sample(u_acc, w_acc, t, dx, f0x, st);
         const FT i0x = shfl_ft(f0x, lane - 1), i0y = shfl_ft(f0y, lane - 1);
-        const FT i3x = shfl_ft(p3x, lane - 1), i3y = shfl_ft(p3y, lane - 1);
-        const FT i1x = shfl_ft(p1x, lane + 1), i1y = shfl_ft(p1y, lane + 1);
+        // incoming springs of row y - 1
+        FT i3x, i3y, i1x, i1y, i2x, i2y;
+        if constexpr (LAT == 0) {
+            i3x = shfl_ft(p3x, lane - 1);
+            i3y = shfl_ft(p3y, lane - 1);
+            i1x = shfl_ft(p1x, lane + 1);
+            i1y = shfl_ft(p1y, lane + 1);
+            i2x = p2x;
+            i2y = p2y;
+        } else {  // from (gx - pp, y - 1) in slot 2 and (gx + 1 - pp, y - 1) in slot 1, pp = (y - 1) & 1
+            const int pp = par ^ 1;
+            i2x = shfl_ft(p2x, lane - pp);
+            i2y = shfl_ft(p2y, lane - pp);
+            i1x = shfl_ft(p1x, lane + 1 - pp);
+            i1y = shfl_ft(p1y, lane + 1 - pp);
+        }
 
         DfSum ax, ay;
         float sx_ = 0.0f, sy_ = 0.0f;
         if constexpr (PREC == LSM_PREC_DF) {
-            ax.first_neg(i3x);
-            ax.sub(p2x);
+            if constexpr (LAT == 0) {  // canonical: slot 3, 2, 1 of row y - 1, slot 0 of row y
+                ax.first_neg(i3x);
+                ax.sub(i2x);
+                ay.first_neg(i3y);
+                ay.sub(i2y);
+            } else {  // canonical: slot 2, slot 1 of row y - 1, slot 0 of row y
+                ax.first_neg(i2x);
+                ay.first_neg(i2y);
+            }
             ax.sub(i1x);
             ax.sub(i0x);
             ax.add(f0x);
-            ay.first_neg(i3y);
-            ay.sub(p2y);
             ay.sub(i1y);
             ay.sub(i0y);
             ay.add(f0y);
         } else {
-            sx_ = f0x - i3x;
-            sy_ = f0y - i3y;
+            if constexpr (LAT == 0) {
+                sx_ = f0x - i3x;
+                sy_ = f0y - i3y;
+            } else {
+                sx_ = f0x - i2x;
+                sy_ = f0y - i2y;
+            }
         }
-        FT f1x, f1y, f2x, f2y, f3x, f3y;
-        const int s1 = strip_spring<PREC, SAMPLE>(A, P, q1, 1, sdf, soff, f1x, f1y, dx, st, t);
-        if (sum_springs && s1 == S_FORCE) spring_sample(u_acc, w_acc, t, dx, f1x, st);
-        const int s2 = strip_spring<PREC, SAMPLE>(A, P, N, 2, sdf, soff, f2x, f2y, dx, st, t);
-        if (sum_springs && s2 == S_FORCE) spring_sample(u_acc, w_acc, t, dx, f2x, st);
-        const int s3 = strip_spring<PREC, SAMPLE>(A, P, q3, 3, sdf, soff, f3x, f3y, dx, st, t);
-        if (sum_springs && s3 == S_FORCE) spring_sample(u_acc, w_acc, t, dx, f3x, st);
+        FT f1x, f1y, f2x, f2y, f3x{}, f3y{};
+        int s1, s2, s3 = S_NONE;
+        if constexpr (LAT == 0) {
+            s1 = strip_spring<PREC, SAMPLE, TEST, LAT>(A, P, q1, 1, sdf, soff, f1x, f1y, dx, st, t);
+            if (sum_springs && s1 == S_FORCE) spring_sample(u_acc, w_acc, t, dx, f1x, st);
+            s2 = strip_spring<PREC, SAMPLE, TEST, LAT>(A, P, N, 2, sdf, soff, f2x, f2y, dx, st, t);
+            if (sum_springs && s2 == S_FORCE) spring_sample(u_acc, w_acc, t, dx, f2x, st);
+            s3 = strip_spring<PREC, SAMPLE, TEST, LAT>(A, P, q3, 3, sdf, soff, f3x, f3y, dx, st, t);
+            if (sum_springs && s3 == S_FORCE) spring_sample(u_acc, w_acc, t, dx, f3x, st);
+        } else {
+            s1 = strip_spring<PREC, SAMPLE, TEST, LAT>(A, P, q1, 1, sdf, soff, f1x, f1y, dx, st, t);
+            if (sum_springs && s1 == S_FORCE) spring_sample(u_acc, w_acc, t, dx, f1x, st);
+            s2 = strip_spring<PREC, SAMPLE, TEST, LAT>(A, P, q3, 2, sdf, soff, f2x, f2y, dx, st, t);
+            if (sum_springs && s2 == S_FORCE) spring_sample(u_acc, w_acc, t, dx, f2x, st);
+        }
 
         // 3. gather + integrate the owned particle (gx, y)
         if (own) {
@@ -299,22 +385,31 @@ k_strip2d(TileArgs A, int R, int nsx)
             if constexpr (PREC == LSM_PREC_DF) {
                 ax.add(f1x);
                 ax.add(f2x);
-                ax.add(f3x);
                 ay.add(f1y);
                 ay.add(f2y);
-                ay.add(f3y);
+                if constexpr (LAT == 0) {
+                    ax.add(f3x);
+                    ay.add(f3y);
+                }
                 F[0] = ax.value();
                 F[1] = ay.value();
                 Ff[0] = __fadd_rn(ax.hs, ax.el);
                 Ff[1] = __fadd_rn(ay.hs, ay.el);
                 Fx = ff{ax.hs, ax.el};
             } else {
-                sx_ += f1x - p2x;
-                sy_ += f1y - p2y;
-                sx_ += f2x - i1x;
-                sy_ += f2y - i1y;
-                sx_ += f3x - i0x;
-                sy_ += f3y - i0y;
+                if constexpr (LAT == 0) {
+                    sx_ += f1x - i2x;
+                    sy_ += f1y - i2y;
+                    sx_ += f2x - i1x;
+                    sy_ += f2y - i1y;
+                    sx_ += f3x - i0x;
+                    sy_ += f3y - i0y;
+                } else {
+                    sx_ += f1x - i1x;
+                    sy_ += f1y - i1y;
+                    sx_ += f2x - i0x;
+                    sy_ += f2y - i0y;
+                }
                 F[0] = f2d_bits(sx_);
                 F[1] = f2d_bits(sy_);
                 Ff[0] = sx_;
@@ -325,33 +420,44 @@ k_strip2d(TileArgs A, int R, int nsx)
                 const int64_t g = (int64_t)y * A.nx + gx;
                 const int ph = (int)(P.pm & 0xffu) - 1;
                 const Coef4 k4 = scoef[ph];
-                if (SAMPLE && gx == A.nx - 1) reactf = ff_add(reactf, ff_neg(Fx));
+                const bool grip = gx == 0 || gx == row_len(y) - 1;
+                const bool fixy = grip && A.grip_mode == 1;
+                if (SAMPLE && gx == row_len(y) - 1) reactf = ff_add(reactf, ff_neg(Fx));  // right grip
                 const double vh[2] = {vcx, vcy};
                 const bool fixed[2] = {grip, fixy};
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
                     const int64_t q = c * A.np + g;
                     if (fixed[c]) {
-                        A.vh_out[q] = 0.0;
-                        if (SAMPLE) A.v_obs[q] = 0.0;
+                        if (MODE == T_STEP) A.vh_out[q] = 0.0;
+                        if (MODE == T_STEP && SAMPLE) A.v_obs[q] = 0.0;
                         continue;
                     }
-                    A.vh_out[q] = fma(k4.c2, F[c], k4.c1 * vh[c]);
+                    double vn;
+                    if (MODE == T_OBSERVE) {
+                        vn = vh[c];  // the stored full-step velocity
+                    } else {
+                        vn = fma(k4.c2h, F[c], k4.c1h * vh[c]);
+                        if (MODE == T_INIT) {
+                            A.vh_out[q] = vn;  // vh = v + dt/2 a(x)
+                            continue;
+                        }
+                        A.vh_out[q] = fma(k4.c2, F[c], k4.c1 * vh[c]);
+                    }
                     if (SAMPLE) {
-                        const double vn = fma(k4.c2h, F[c], k4.c1h * vh[c]);
-                        A.v_obs[q] = vn;
+                        if (MODE == T_STEP) A.v_obs[q] = vn;
                         // float statistics (residual, KE, m v_x^2), as the tile kernel
                         const float vf = d2f_bits(vn);
                         resf = fmaxf(resf, fmaxf(fabsf(Ff[c]), fabsf(vf)));
                         const float mv2 = __fmul_rn(__fmul_rn(smassf[ph], vf), vf);
                         ke = ff_add_f(ke, __fmul_rn(0.5f, mv2));
                         if (c == 0) mvx2 = ff_add_f(mvx2, mv2);
-                        bad |= !dbl_finite_bits(vn);
+                        if (MODE == T_STEP) bad |= !dbl_finite_bits(vn);
                     }
                 }
                 const int nb = (int)(s0 == S_BREAK) | ((int)(s1 == S_BREAK) << 1) | ((int)(s2 == S_BREAK) << 2) |
                                ((int)(s3 == S_BREAK) << 3);
-                if (nb) {
+                if (MODE == T_STEP && nb) {
                     A.mask[g] = (uint8_t)((P.pm >> 8) | (unsigned)nb);
 #pragma unroll
                     for (int slot = 0; slot < 4; slot++) {
@@ -398,16 +504,16 @@ k_strip2d(TileArgs A, int R, int nsx)
 namespace {
 
 // Warps of the time-step instance that fit on the device at once.
-template <int PREC>
+template <int PREC, int LAT>
 cudaError_t strip_resident(int &resident)
 {
-    static int cached = 0;  // per precision
+    static int cached = 0;  // per instance
     if (!cached) {
         int dev = 0, nsm = 0, nb = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_strip2d<PREC, false, false>,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_strip2d<PREC, false, false, LAT, T_STEP>,
                                                               32 * STRIP_WARPS, 0);
         if (e != cudaSuccess) return e;
         cached = std::max(1, nb * STRIP_WARPS * nsm);
@@ -416,24 +522,23 @@ cudaError_t strip_resident(int &resident)
     return cudaSuccess;
 }
 
-template <int PREC, bool RATE, bool SAMPLE>
+template <int PREC, bool RATE, bool SAMPLE, int LAT, int MODE>
 void launch_strip_t(Ctx &c, TileArgs A)
 {
     if (SAMPLE) A.ntiles = c.nstrips;  // partial-sum stride
     const unsigned grid = (unsigned)((c.nstrips + STRIP_WARPS - 1) / STRIP_WARPS);
-    k_strip2d<PREC, RATE, SAMPLE><<<grid, 32 * STRIP_WARPS, 0, c.stream>>>(A, c.strip_R, c.strip_nsx);
+    k_strip2d<PREC, RATE, SAMPLE, LAT, MODE><<<grid, 32 * STRIP_WARPS, 0, c.stream>>>(A, c.strip_R, c.strip_nsx);
 }
 
-template <bool SAMPLE>
-void launch_strip_s(Ctx &c, const TileArgs &A)
+template <int PREC, int LAT>
+void launch_strip_step(Ctx &c, const TileArgs &A, bool sample)
 {
-    const bool rate = c.rate_on;
-    if (c.h.precision == LSM_PREC_DF) {
-        if (rate) launch_strip_t<LSM_PREC_DF, true, SAMPLE>(c, A);
-        else launch_strip_t<LSM_PREC_DF, false, SAMPLE>(c, A);
+    if (c.rate_on) {
+        if (sample) launch_strip_t<PREC, true, true, LAT, T_STEP>(c, A);
+        else launch_strip_t<PREC, true, false, LAT, T_STEP>(c, A);
     } else {
-        if (rate) launch_strip_t<LSM_PREC_F32, true, SAMPLE>(c, A);
-        else launch_strip_t<LSM_PREC_F32, false, SAMPLE>(c, A);
+        if (sample) launch_strip_t<PREC, false, true, LAT, T_STEP>(c, A);
+        else launch_strip_t<PREC, false, false, LAT, T_STEP>(c, A);
     }
 }
 
@@ -441,32 +546,59 @@ void launch_strip_s(Ctx &c, const TileArgs &A)
 
 bool strip_supported(const Ctx &c)
 {
-    return c.dim == 2 && c.h.lattice == 0 &&
+    return c.dim == 2 && (c.h.lattice == 0 || c.h.lattice == 1) &&
            (c.h.precision == LSM_PREC_DF || c.h.precision == LSM_PREC_F32);
 }
 
 // Strip geometry: one warp per strip of 30 owned columns and R rows, as many
-// strips as fit on the device at once (one wave), but at least 8 rows each.
-cudaError_t strip_geometry(Ctx &c)
+// strips as fit on the device at once (one wave), but at least 8 rows each
+// (2 on the triangular packing, which has no tile kernel to fall back to).
+// *fills: whether those strips occupy the whole device (otherwise the
+// square lattice's tile kernel, with more CTAs in flight, is the faster
+// choice: a warp's row-by-row sweep is latency-bound when few run).
+cudaError_t strip_geometry(Ctx &c, bool *fills)
 {
     int resident = 0;
-    cudaError_t e = c.h.precision == LSM_PREC_DF ? strip_resident<LSM_PREC_DF>(resident)
-                                                 : strip_resident<LSM_PREC_F32>(resident);
+    const bool df = c.h.precision == LSM_PREC_DF;
+    cudaError_t e = c.tri ? (df ? strip_resident<LSM_PREC_DF, 1>(resident) : strip_resident<LSM_PREC_F32, 1>(resident))
+                          : (df ? strip_resident<LSM_PREC_DF, 0>(resident) : strip_resident<LSM_PREC_F32, 0>(resident));
     if (e != cudaSuccess) return e;
-    const int nsx = (c.h.nx + STRIP_OWN - 1) / STRIP_OWN;
+    const int nsx = (c.tgnx + STRIP_OWN - 1) / STRIP_OWN;
     const int rows_target = std::max(1, resident / nsx);
-    const int R = std::max(8, (c.h.ny + rows_target - 1) / rows_target);
-    const int nsy = (c.h.ny + R - 1) / R;
+    const int R = std::max(c.tri ? 2 : 8, (c.tgny + rows_target - 1) / rows_target);
+    const int nsy = (c.tgny + R - 1) / R;
     c.strip_R = R;
     c.strip_nsx = nsx;
     c.nstrips = (int64_t)nsx * nsy;
+    if (fills) *fills = c.nstrips >= resident;
     return cudaSuccess;
 }
 
 cudaError_t launch_strip(Ctx &c, const TileArgs &A, bool sample)
 {
-    if (sample) launch_strip_s<true>(c, A);
-    else launch_strip_s<false>(c, A);
+    const bool df = c.h.precision == LSM_PREC_DF;
+    if (c.tri) {
+        if (df) launch_strip_step<LSM_PREC_DF, 1>(c, A, sample);
+        else launch_strip_step<LSM_PREC_F32, 1>(c, A, sample);
+    } else {
+        if (df) launch_strip_step<LSM_PREC_DF, 0>(c, A, sample);
+        else launch_strip_step<LSM_PREC_F32, 0>(c, A, sample);
+    }
+    return cudaSuccess;
+}
+
+// The triangular packing's initial acceleration and observation (the square
+// lattice runs both on the tile kernel).
+cudaError_t launch_strip_mode(Ctx &c, const TileArgs &A, int mode)
+{
+    const bool df = c.h.precision == LSM_PREC_DF;
+    if (mode == T_INIT) {
+        if (df) launch_strip_t<LSM_PREC_DF, false, false, 1, T_INIT>(c, A);
+        else launch_strip_t<LSM_PREC_F32, false, false, 1, T_INIT>(c, A);
+    } else {
+        if (df) launch_strip_t<LSM_PREC_DF, false, true, 1, T_OBSERVE>(c, A);
+        else launch_strip_t<LSM_PREC_F32, false, true, 1, T_OBSERVE>(c, A);
+    }
     return cudaSuccess;
 }
 

@@ -25,6 +25,8 @@
 // force in single precision or in double-float arithmetic, integrating in FP64.
 #include "tile_body.cuh"
 
+#include <cmath>
+
 namespace lsm {
 
 template <int TX, int TY, int PREC, int MODE, bool SAMPLE, bool RATE>
@@ -36,19 +38,23 @@ k_tile2d(TileArgs A)
                                                 (int64_t)blockIdx.y * gridDim.x + blockIdx.x, smem_raw);
 }
 
-// Load increment on the pixel grid (Sections 2.3, 3.1).
+// Load increment on the pixel grid, or on the triangular packing's sites
+// (tri: rows alternate between nx sites at x = ix a and nx - 1 sites at
+// x = (ix + 1/2) a; a row's first and last site are its grips) (Sections
+// 2.3, 3.1).
 __global__ void k_tile_strain(int nx, int ny, int64_t np, double *x, double *vh, double *v_obs,
                               const uint8_t *phase, double a, double xc, double scale, double eps,
-                              int affine, double *d_eps)
+                              int affine, double *d_eps, int tri)
 {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g == 0) *d_eps = eps;
     if (g >= np || !phase[g]) return;
     const int gx = (int)(g % nx);
+    const int odd = tri ? (int)((g / nx) & 1) : 0;
     double xp = x[g];
     if (affine) xp = ad(xc, ml(sb(xp, xc), scale));
-    if (gx == 0 || gx == nx - 1) {
-        const double X = gx * a;
+    if (gx == 0 || gx == nx - 1 - odd) {
+        const double X = odd ? ml(ad((double)gx, 0.5), a) : gx * a;
         xp = ad(X, ml(eps, sb(X, xc)));
         vh[g] = 0.0;
         v_obs[g] = 0.0;
@@ -62,16 +68,22 @@ __global__ void k_tile_strain(int nx, int ny, int64_t np, double *x, double *vh,
 __global__ void k_tile_export(int nx, int ny, int64_t np, const uint8_t *__restrict__ phase,
                               const uint8_t *__restrict__ mask, const long long *__restrict__ brk,
                               const int64_t *__restrict__ sbase, uint8_t *__restrict__ out_mask,
-                              long long *__restrict__ out_brk)
+                              long long *__restrict__ out_brk, int tri)
 {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= np || !phase[g]) return;
     const int gx = (int)(g % nx), gy = (int)(g / nx);
     int64_t b = sbase[g];
     const uint8_t mk = mask[g];
+    const int odd = gy & 1;
 #pragma unroll
     for (int slot = 0; slot < 4; slot++) {
-        const int dx = slot == 0 ? 1 : (slot == 1 ? -1 : (slot == 2 ? 0 : 1));
+        // square: (+1,0), (-1,+1), (0,+1), (+1,+1); packing: (+1, same row),
+        // then the next row's sites at x -/+ a/2 (no fourth slot); the
+        // packing's padding site (last of an odd row) has phase 0
+        if (tri && slot == 3) break;
+        const int dx = tri ? (slot == 0 ? 1 : (slot == 1 ? odd - 1 : odd))
+                           : (slot == 0 ? 1 : (slot == 1 ? -1 : (slot == 2 ? 0 : 1)));
         const int dy = slot == 0 ? 0 : 1;
         const int qx = gx + dx, qy = gy + dy;
         if (qx < 0 || qx >= nx || qy >= ny || !phase[(int64_t)qy * nx + qx]) continue;
@@ -94,8 +106,9 @@ cudaError_t tile_export(Ctx &c, bool steps)
         if (e != cudaSuccess) return e;
     }
     const unsigned g = (unsigned)((c.tnp + 255) / 256);
-    k_tile_export<<<g, 256, 0, c.stream>>>(c.h.nx, c.h.ny, c.tnp, c.tph, c.tmask, c.tbrk, c.tsbase,
-                                           steps ? nullptr : c.texport, steps ? c.texport_brk : nullptr);
+    k_tile_export<<<g, 256, 0, c.stream>>>(c.tgnx, c.tgny, c.tnp, c.tph, c.tmask, c.tbrk, c.tsbase,
+                                           steps ? nullptr : c.texport, steps ? c.texport_brk : nullptr,
+                                           c.tri ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -116,8 +129,8 @@ constexpr int tile_y() { return PREC == LSM_PREC_DF && !SAMPLE ? 8 : TILE_Y_SAMP
 static TileArgs tile_args(Ctx &c)
 {
     TileArgs A;
-    A.nx = c.h.nx;
-    A.ny = c.h.ny;
+    A.nx = c.tgnx;
+    A.ny = c.tgny;
     A.nphase = c.tile_nphase;
     A.np = c.tnp;
     A.x_in = c.tx[c.tcur];
@@ -134,6 +147,8 @@ static TileArgs tile_args(Ctx &c)
     A.coef = (const Coef4 *)c.tinvm;
     A.S = c.fix_S;
     A.a_fix = c.a_fix;
+    A.h_fix = c.h_fix;
+    A.hrow = c.h.a * std::sqrt(3.0) * 0.5;
     A.p48 = ldexpf(1.0f, 48 - c.fix_S);
     A.p24 = ldexpf(1.0f, 24 - c.fix_S);
     A.p0 = ldexpf(1.0f, -c.fix_S);
@@ -223,7 +238,7 @@ cudaError_t tile_init_accel(Ctx &c)
 {
     TileArgs A = tile_args(c);
     A.vh_out = c.tvh[c.tcur];  // vh = v + dt/2 a, written in place of the current buffer
-    cudaError_t e = launch_tile_prec<T_INIT, false>(c, A);
+    cudaError_t e = c.tri ? launch_strip_mode(c, A, T_INIT) : launch_tile_prec<T_INIT, false>(c, A);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -231,7 +246,7 @@ cudaError_t tile_init_accel(Ctx &c)
 cudaError_t tile_observe(Ctx &c)
 {
     TileArgs A = tile_args(c);
-    cudaError_t e = launch_tile_prec<T_OBSERVE, true>(c, A);
+    cudaError_t e = c.tri ? launch_strip_mode(c, A, T_OBSERVE) : launch_tile_prec<T_OBSERVE, true>(c, A);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -240,9 +255,9 @@ cudaError_t tile_apply_strain(Ctx &c, double eps_old, double eps_new)
 {
     const double scale = (1.0 + eps_new) / (1.0 + eps_old);
     const unsigned g = (unsigned)((c.tnp + 255) / 256);
-    k_tile_strain<<<g, 256, 0, c.stream>>>(c.h.nx, c.h.ny, c.tnp, c.tx[c.tcur], c.tvh[c.tcur], c.tvobs,
+    k_tile_strain<<<g, 256, 0, c.stream>>>(c.tgnx, c.tgny, c.tnp, c.tx[c.tcur], c.tvh[c.tcur], c.tvobs,
                                            c.tph, c.h.a, c.h.xc, scale, eps_new, c.h.load_mode == 0,
-                                           c.d_eps);
+                                           c.d_eps, c.tri ? 1 : 0);
     return cudaGetLastError();
 }
 

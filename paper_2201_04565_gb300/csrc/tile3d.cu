@@ -483,6 +483,9 @@ cudaError_t tile3_upload(Ctx &c)
     c.tnp = nv;
     c.tile_nphase = h.nphase;
     c.ntiles = tile3_count(c);
+    c.tgidx.assign(h.pix.begin(), h.pix.end());  // grid index of each particle: its voxel
+    c.tgnx = h.nx;                                // rows of nx voxels, x fastest (the load
+    c.tgny = h.ny * h.nz;                         // increment's kernel works per row)
     std::vector<double> X(3 * nv);
     for (int64_t g = 0; g < nv; g++) {
         X[g] = (g % h.nx) * h.a;

@@ -112,6 +112,8 @@ struct TileArgs {
     const Coef4 *coef;         // per phase integration coefficients
     int S;                     // fixed-point scale: positions as x * 2^S
     long long a_fix;           // lattice spacing in fixed point
+    long long h_fix;           // triangular packing: row height a sqrt(3)/2 in fixed point
+    double hrow;               // triangular packing: row height
     float p48, p24, p0;        // 2^(48-S), 2^(24-S), 2^-S
     double dt, hdt, gamma, a;
     int grip_mode;
@@ -203,21 +205,20 @@ __device__ __forceinline__ bool spring_df(long long dxq, long long dyq, const Ty
 // vector o is exact in fixed point, so r^2 - |o|^2 = (2 o + e).e carries no
 // cancellation in float. Products are explicitly rounded (no contraction
 // with the caller's sums, whatever the kernel).
+// (ofx, ofy): the slot's lattice vector in fixed point, (ox, oy, oo) the
+// same as floats with |o|^2; t.cor = |o|^2 - r0^2 for that vector.
 template <bool TEST, bool SAMPLE>
-__device__ __forceinline__ bool spring_f32(long long dxq, long long dyq, int slot, const TypeDF &t,
-                                           const ff (*soff)[3], const TileArgs &A, float &fx, float &fy,
-                                           float &dx, float &st)
+__device__ __forceinline__ bool spring_f32_o(long long dxq, long long dyq, long long ofx, long long ofy, float ox,
+                                             float oy, float oo, const TypeDF &t, const TileArgs &A, float &fx,
+                                             float &fy, float &dx, float &st)
 {
-    const int ox_i = slot == 0 ? 1 : (slot == 1 ? -1 : (slot == 2 ? 0 : 1));
-    const int oy_i = slot == 0 ? 0 : 1;
-    const long long exf = dxq - (long long)ox_i * A.a_fix;
-    const long long eyf = dyq - (long long)oy_i * A.a_fix;
+    const long long exf = dxq - ofx;
+    const long long eyf = dyq - ofy;
     const float ex = fix_to_float_i2f(exf, A.p24, A.p0), ey = fix_to_float_i2f(eyf, A.p24, A.p0);
-    const float ox = soff[slot][0].hi, oy = soff[slot][1].hi;
     const float dxf = __fadd_rn(ox, ex), dyf = __fadd_rn(oy, ey);
     const float num = __fmaf_rn(__fadd_rn(__fmul_rn(2.0f, ox), ex), ex,
                                 __fmaf_rn(__fadd_rn(__fmul_rn(2.0f, oy), ey), ey, t.cor.hi));
-    const float r2f = __fadd_rn(soff[slot][2].hi, num);
+    const float r2f = __fadd_rn(oo, num);
     if (TEST && r2f > t.rc2.hi) return true;
     const float ir = rsqrt_approx(r2f);
     const float s = __fdividef(num, __fmaf_rn(r2f, ir, t.r0.hi));  // r - r0
@@ -229,6 +230,18 @@ __device__ __forceinline__ bool spring_f32(long long dxq, long long dyq, int slo
         st = s;
     }
     return false;
+}
+
+// The square lattice's forward slots (+1,0), (-1,+1), (0,+1), (+1,+1).
+template <bool TEST, bool SAMPLE>
+__device__ __forceinline__ bool spring_f32(long long dxq, long long dyq, int slot, const TypeDF &t,
+                                           const ff (*soff)[3], const TileArgs &A, float &fx, float &fy,
+                                           float &dx, float &st)
+{
+    const int ox_i = slot == 0 ? 1 : (slot == 1 ? -1 : (slot == 2 ? 0 : 1));
+    const int oy_i = slot == 0 ? 0 : 1;
+    return spring_f32_o<TEST, SAMPLE>(dxq, dyq, (long long)ox_i * A.a_fix, (long long)oy_i * A.a_fix,
+                                      soff[slot][0].hi, soff[slot][1].hi, soff[slot][2].hi, t, A, fx, fy, dx, st);
 }
 
 // Force on the lower endpoint of one spring (rp -> rq, forward slot), with
@@ -658,12 +671,13 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
 // lattice); its positions, velocities and breaks are bit-identical to the
 // tile kernel's (sample sums: per strip instead of per tile).
 cudaError_t launch_strip(Ctx &c, const TileArgs &A, bool sample);
+cudaError_t launch_strip_mode(Ctx &c, const TileArgs &A, int mode);  // T_INIT / T_OBSERVE, triangular packing
 
 // Pixel-grid broken flags -> canonical spring order (defined in tile2d.cu).
 __global__ void k_tile_export(int nx, int ny, int64_t np, const uint8_t *__restrict__ phase,
                               const uint8_t *__restrict__ mask, const long long *__restrict__ brk,
                               const int64_t *__restrict__ sbase, uint8_t *__restrict__ out_mask,
-                              long long *__restrict__ out_brk);
+                              long long *__restrict__ out_brk, int tri);
 
 // Shared memory of tile_body (dynamic part).
 template <int TX, int TY>

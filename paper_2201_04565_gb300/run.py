@@ -109,9 +109,9 @@ def main(argv=None):
     ap.add_argument("case", choices=["single", "foam", "batch", "unet"])
     ap.add_argument("--side", type=int, default=256)
     ap.add_argument("--precision", default="df64", choices=["exact64", "fast64", "f32", "df64"])
-    ap.add_argument("--path", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--path", type=int, default=0, choices=[0, 1, 2, 3],
                     help="single, foam: 0 automatic (tile and strip kernels), 1 spring-list kernels, "
-                         "2 (single) tile kernel for every step")
+                         "2 (single) tile kernel for every step, 3 (single) strip kernel for every step")
     ap.add_argument("--increments", type=int, default=3)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--eps-inc", type=float, default=1e-3)

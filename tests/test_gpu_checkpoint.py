@@ -66,6 +66,8 @@ CASES = [
     dict(kind="2d", prec="df64"),
     dict(kind="2d", prec="f32", path=1),
     dict(kind="2d", prec="fast64", lattice=1),
+    dict(kind="2d", prec="df64", lattice=1),
+    dict(kind="2d", prec="f32", lattice=1, rate=0.05),
     dict(kind="3d", prec="df64"),
     dict(kind="3d", prec="exact64"),
     dict(kind="net", prec="exact64"),

@@ -163,7 +163,7 @@ def test_c0_fast_modes_within_tolerance(oracle_mod, L, path, precision):
         assert a["sigma_vir"] == pytest.approx(b["sigma_vir"], rel=1e-6)
 
 
-@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("path", [0, 1, 3])  # automatic (tile kernel at 64 x 64), spring lists, strip kernel
 def test_c0_df64_full_schedule(oracle_mod, L, path):
     """df64, the benchmark's mode, through the whole 64x64 schedule (100
     increments of 1e-3, 20 damped steps each: 2,000 steps, fracture from step
@@ -343,7 +343,7 @@ def test_tile_and_spring_list_paths_agree_bitwise(L):
 
 @pytest.mark.parametrize("precision", ["df64", "f32"])
 def test_strip_and_tile_kernels_agree_bitwise(L, precision):
-    """The register-resident strip kernel (path 0) and the tile kernel
+    """The register-resident strip kernel (path 3) and the tile kernel
     (path 2) perform the same operations in the same order on every particle
     and spring: states, velocities, broken sets and break steps are
     identical, through fracture, on ragged and voided images, with roller
@@ -363,7 +363,7 @@ def test_strip_and_tile_kernels_agree_bitwise(L, precision):
              (np.ones((3, 257), np.uint8), {})]
     for ci, (img, kw) in enumerate(cases):
         outs = []
-        for path in (0, 2):
+        for path in (3, 2):  # strip kernel whatever the size, tile kernel
             g = L.Specimen.from_image(img, k, e, m, precision=precision, path=path, **kw)
             for i in range(1, 31):
                 g.apply_strain(i * 3e-3)
@@ -441,11 +441,14 @@ def test_fields_3d_match_oracle(oracle_mod, L):
     assert np.abs(eg[ok] - eo[ok]).max() <= 1e-12 * np.abs(eo[ok]).max()
 
 
-@pytest.mark.parametrize("precision", ["exact64", "fast64", "df64", "f32"])
-def test_triangular_packing_parity(oracle_mod, L, precision):
-    """The paper's triangular packing (lattice 1) on the spring-list kernels:
-    exact64 bit-identical through fracture, fast64/df64 at the 1e-10 bar with
-    the same broken set, f32 error stated. The increments (2.1e-3) never land
+@pytest.mark.parametrize("precision,path", [("exact64", 0), ("fast64", 0), ("df64", 0), ("f32", 0),
+                                            ("df64", 1), ("f32", 1)])
+def test_triangular_packing_parity(oracle_mod, L, precision, path):
+    """The paper's triangular packing (lattice 1): df64/f32 on the strip
+    kernel over the packing's site grid (path 0) and on the spring-list
+    kernels (path 1), exact64/fast64 on the spring-list kernels: exact64
+    bit-identical through fracture, fast64/df64 at the 1e-10 bar with the
+    same broken set, f32 error stated. The increments (2.1e-3) never land
     on the stiff phase's critical strain 0.05: there, the horizontal springs of
     a homogeneous stiff region stay exactly affine, every one of them sits
     within rounding of rc, and the strict break test is decided by the last
@@ -455,7 +458,7 @@ def test_triangular_packing_parity(oracle_mod, L, precision):
     img[16:19, 0:12] = 0  # a notch from the left edge (mode-I set-up)
     k, e, m = two_phase_materials()
     o = oracle_mod.Oracle.from_image(img, k, e, m, lattice=1)
-    g = L.Specimen.from_image(img, k, e, m, precision=precision, lattice=1)
+    g = L.Specimen.from_image(img, k, e, m, precision=precision, lattice=1, path=path)
     assert (g.n, g.m) == (o.n, o.m)
     to, tg = o.topology(), g.topology()
     assert np.array_equal(to["si"], tg["si"]) and np.array_equal(to["sj"], tg["sj"])
@@ -480,6 +483,50 @@ def test_triangular_packing_parity(oracle_mod, L, precision):
     first = next((i for i, s in enumerate(so) if s["n_broken"] > 0), len(so))
     for a_, b_ in zip(sg[:first], so[:first]):
         assert a_["sigma_vir"] == pytest.approx(b_["sigma_vir"], rel=1e-6)
+
+
+@pytest.mark.parametrize("a,grip_mode,precision", [(1.3, 1, "df64"), (0.7, 0, "f32"), (1.0, 0, "df64")])
+def test_triangular_strip_kernel_geometry(oracle_mod, L, a, grip_mode, precision):
+    """The packing on the strip kernel with a spacing whose row height is no
+    exact float (and, at 1.3 and 0.7, an odd fixed-point spacing for the
+    F32 lattice vectors), clamped and roller grips, a voided image wider
+    than two strips, strained through fracture: df64 at the 1e-10 bar with
+    the same broken set and break steps; f32 within its stated bound; the
+    per-particle fields (observation path) within 1e-8."""
+    rng = np.random.default_rng(7)
+    img = inclusion_image(75, 41, 2.0, 5.0, 0.3, 23)
+    img[rng.random(img.shape) < 0.03] = 0  # scattered voids
+    k, e, m = two_phase_materials()
+    o = oracle_mod.Oracle.from_image(img, k, e, m, lattice=1, a=a, grip_mode=grip_mode)
+    g = L.Specimen.from_image(img, k, e, m, precision=precision, lattice=1, a=a, grip_mode=grip_mode)
+    so = _run_schedule(o, g, 25, 20, 2.1e-3)
+    xg, _ = g.state()
+    xo, _, _ = o.state()
+    X = o.topology()["X"]
+    mo, bo, fo = o.broken()
+    assert mo.sum() > 0
+    if precision == "f32":
+        assert _rel_u(xg, xo, X) < 1e-3
+        return
+    print("triangular df64 a=%g: |dx|/|x| = %.3e, |dx|/|u| = %.3e" % (a, _rel(xg, xo), _rel_u(xg, xo, X)))
+    assert _rel(xg, xo) <= 1e-10
+    mg, fg = g.broken()
+    assert np.array_equal(mg, mo) and fg == fo
+    assert np.array_equal(g.break_steps(), bo)
+    sg = g.samples()
+    first = next((i for i, s_ in enumerate(so) if s_["n_broken"] > 0), len(so))
+    for a_, b_ in zip(sg[:first], so[:first]):
+        assert a_["sigma_vir"] == pytest.approx(b_["sigma_vir"], rel=1e-6)
+    cell = a * a * np.sqrt(3.0) / 2
+    st_o, sn_o = o.fields(cell)
+    st_g, sn_g = g.fields()
+    ok = ~np.isnan(sn_o)
+    assert np.array_equal(np.isnan(sn_g), np.isnan(sn_o))
+    assert np.abs(st_g - st_o).max() <= 1e-8 * np.abs(st_o).max()
+    assert np.abs(sn_g[ok] - sn_o[ok]).max() <= 1e-8 * np.abs(sn_o[ok]).max()
+    # an observation of the current state equals the last sample's stress
+    ob = g.observe()
+    assert ob["sigma_vir"] == pytest.approx(sg[-1]["sigma_vir"], rel=1e-9)
 
 
 def test_triangular_fields_match_oracle(oracle_mod, L):
