@@ -107,12 +107,13 @@ def algorithmic_bytes(n, m, dim):
 # keyed by precision mode, with the sha1 prefix of the kernel source it was
 # taken on; once the kernel changes, traffic reports null until re-measured.
 NCU_TRAFFIC = {
-    # profiles/k_tile2d_step_2d_2048_two_phase.md (DRAM read + write of one
-    # time-step launch, ncu, the same 2048 x 2048 workload)
-    "df64": (239.80e6, "023b81ce7d44"),
-    "f32": (237.74e6, "023b81ce7d44"),
-    "fast64": (237.67e6, "023b81ce7d44"),
-    "exact64": (238.63e6, "023b81ce7d44"),
+    # profiles/k_strip2d_df64_2d_2048_two_phase.md and ncu --metrics
+    # dram__bytes_read.sum,dram__bytes_write.sum on one time-step launch of
+    # each mode (the same 2048 x 2048 workload)
+    "df64": (238.4e6, "c2b3cbe44956"),
+    "f32": (239.9e6, "c2b3cbe44956"),
+    "fast64": (236.0e6, "c2b3cbe44956"),
+    "exact64": (236.6e6, "c2b3cbe44956"),
 }
 
 # Warp instructions executed by one time-step launch (ncu smsp__inst_executed.sum,
@@ -121,10 +122,19 @@ NCU_TRAFFIC = {
 # this gives the instruction-issue roofline, the one the fixed-point modes
 # are bound by.
 NCU_INSTRUCTIONS = {
-    "df64": (160383328, "023b81ce7d44"),
-    "f32": (88946351, "023b81ce7d44"),
-    "fast64": (94464248, "023b81ce7d44"),
-    "exact64": (195704900, "023b81ce7d44"),
+    "df64": (136150237, "c2b3cbe44956"),
+    "f32": (80702847, "c2b3cbe44956"),
+    "fast64": (94464248, "c2b3cbe44956"),
+    "exact64": (195597796, "c2b3cbe44956"),
+}
+
+# Binding unit of each mode's time-step kernel, from ncu on the same workload
+# (see the profile summaries), for the roofline's "limiter" note.
+LIMITER = {
+    "df64": "instruction issue (ncu: 75% of issue slots busy, FP64 pipe 40%, DRAM 20% of peak)",
+    "f32": "instruction issue (ncu: 71% of issue slots busy, FP64 pipe 48%, DRAM 30% of peak)",
+    "fast64": "FP64 pipe (ncu: 86% busy)",
+    "exact64": "FP64 pipe (ncu: 88% busy; correctly rounded sqrt and divide)",
 }
 
 # Time-step kernel of each mode on the 2D image lattice.
@@ -133,15 +143,6 @@ KERNEL = {
     "f32": "k_strip2d (register-resident strip kernel, one launch per time step)",
     "fast64": "k_tile2d (tile kernel, one launch per time step)",
     "exact64": "k_tile2d (tile kernel, one launch per time step)",
-}
-
-# Binding unit of each mode's time-step kernel, from ncu on the same workload
-# (see the profile summaries), for the roofline's "limiter" note.
-LIMITER = {
-    "df64": "instruction issue (ncu: 80% of issue slots busy, FP64 pipe 37%, DRAM 19% of peak)",
-    "f32": "instruction issue and latency (ncu: 69% issue, LSU 47%, FP64 pipe 42%, DRAM 28% of peak)",
-    "fast64": "FP64 pipe (ncu: 86% busy)",
-    "exact64": "FP64 pipe (ncu: 88% busy; correctly rounded sqrt and divide)",
 }
 
 

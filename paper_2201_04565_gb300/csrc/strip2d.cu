@@ -553,9 +553,10 @@ bool strip_supported(const Ctx &c)
 // Strip geometry: one warp per strip of 30 owned columns and R rows, as many
 // strips as fit on the device at once (one wave), but at least 8 rows each
 // (2 on the triangular packing, which has no tile kernel to fall back to).
-// *fills: whether those strips occupy the whole device (otherwise the
-// square lattice's tile kernel, with more CTAs in flight, is the faster
-// choice: a warp's row-by-row sweep is latency-bound when few run).
+// *fills: whether the image is large enough for strips of 8 rows to occupy
+// the whole device (otherwise the square lattice's tile kernel, with more
+// CTAs in flight, is the faster choice: a warp's row-by-row sweep is
+// latency-bound when few run).
 cudaError_t strip_geometry(Ctx &c, bool *fills)
 {
     int resident = 0;
@@ -570,7 +571,8 @@ cudaError_t strip_geometry(Ctx &c, bool *fills)
     c.strip_R = R;
     c.strip_nsx = nsx;
     c.nstrips = (int64_t)nsx * nsy;
-    if (fills) *fills = c.nstrips >= resident;
+    // fills: strips of 8 rows would outnumber the device's resident warps
+    if (fills) *fills = (int64_t)nsx * ((c.tgny + 7) / 8) >= resident;
     return cudaSuccess;
 }
 

@@ -29,7 +29,8 @@ def _single(a):
     from . import lsm
     img = inclusion_image(a.side, a.side, 10.0, 60.0, 0.30, a.seed)
     k, e, m = two_phase_materials()
-    sp = lsm.Specimen.from_image(img, k, e, m, dt=0.01, damping=0.1, precision=a.precision, path=a.path)
+    sp = lsm.Specimen.from_image(img, k, e, m, dt=0.01, damping=0.1, precision=a.precision, path=a.path,
+                                 lattice=a.lattice)
     t0 = time.perf_counter()
     for i in range(1, a.increments + 1):
         sp.apply_strain(i * a.eps_inc)
@@ -112,6 +113,8 @@ def main(argv=None):
     ap.add_argument("--path", type=int, default=0, choices=[0, 1, 2, 3],
                     help="single, foam: 0 automatic (tile and strip kernels), 1 spring-list kernels, "
                          "2 (single) tile kernel for every step, 3 (single) strip kernel for every step")
+    ap.add_argument("--lattice", type=int, default=0, choices=[0, 1],
+                    help="single: 0 square lattice, 1 the paper's triangular packing")
     ap.add_argument("--increments", type=int, default=3)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--eps-inc", type=float, default=1e-3)
