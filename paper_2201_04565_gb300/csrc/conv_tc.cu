@@ -1,0 +1,785 @@
+// conv_tc.cu -- the U-Net's convolutions on the 5th-generation tensor cores.
+//
+// Both kernels are implicit GEMMs with BF16 operands staged by the tensor
+// memory accelerator (TMA) into swizzled shared memory and FP32 accumulators
+// in tensor memory (TMEM):
+//
+//   forward   D[pixel][co] = sum over (tap, ci) of in[pixel shifted by tap][ci]
+//             W[co][tap][ci]; M = 128 pixels (a bx x by patch of one image),
+//             N = BN output channels, K = taps x Cin in chunks of KC = 64
+//             (or 32) channels of one tap. Both operands K-major: the input
+//             patch is one 4D TMA box (channels, x, y, image) at the tap's
+//             shifted origin, whose out-of-image part the TMA fills with
+//             zeros (the convolution's zero padding), and the weights one 2D
+//             box. Persistent CTAs walk a static list of tiles; warp 0 issues
+//             the copies into an S-stage ring, warp 1 the MMAs, and warps
+//             2-5 drain the accumulator (bias, ReLU, BF16 stores), which is
+//             double-buffered in TMEM so that the next tile's MMAs overlap
+//             the epilogue.
+//   wgrad     D[tap, ci][co] = sum over pixels p of in[p shifted by tap][ci]
+//             grad[p][co]; M = 128 rows of (tap, ci), N = BN output channels,
+//             K = pixels in patches of 64. Both operands MN-major (channels
+//             contiguous), copied by TMA boxes of KC channels x 64 pixels;
+//             the pixel patches are split over CTAs and each split's tile
+//             stored as a partial, folded afterwards in a fixed order (so the
+//             result does not depend on timing).
+//
+// Every mbarrier wait is bounded (g_conv_wait_limit polls): a role that gives
+// up raises g_conv_timeout and a flag in shared memory that the CTA's other
+// roles see in their own waits; the CTA then waits (bounded again, with the
+// default limit) for the copies and MMAs it has issued, frees its TMEM and
+// returns, and the host reports the convolution as timed out.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "nn_internal.h"
+
+namespace lsm {
+namespace nn {
+
+__device__ int g_conv_timeout;
+
+constexpr int TC_WAIT = 1 << 20;
+__device__ int g_conv_wait_limit = TC_WAIT;
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ unsigned cv_smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity)
+{
+    unsigned done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for the phase of the given parity, at most `limit` polls; gives up
+// early once another role of the CTA has given up.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, int limit, const volatile int *abort)
+{
+    for (int it = 0; it < limit; it++) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 31) == 31 && *abort) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// TMA tile loads into this CTA's shared memory, completing on an mbarrier
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap *map, unsigned bar, int c0, int c1,
+                                            int c2, int c3)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, "
+        "%6}], [%2];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap *map, unsigned bar, int c0, int c1)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+        "[%2];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1)
+        : "memory");
+}
+__device__ __forceinline__ void tma_prefetch(const CUtensorMap *map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
+}
+
+// Shared-memory matrix descriptor: start address, leading and stride byte
+// offsets (16-byte units), descriptor version 1 (bit 46), swizzle mode in
+// bits 61-63 (2: 128-byte, 4: 64-byte). K-major swizzled tiles: rows of one
+// swizzle width, 8-row groups SBO apart (LBO unused). MN-major swizzled
+// tiles: K rows of one swizzle width holding consecutive M (or N) elements,
+// 8-row groups SBO apart along K, blocks of one swizzle width LBO apart
+// along M (or N).
+__device__ __forceinline__ uint64_t sdesc_sw(unsigned addr, unsigned lbo, unsigned sbo, unsigned mode)
+{
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46) | ((uint64_t)mode << 61);
+}
+
+// Instruction descriptor of kind::f16: D FP32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 = 1, 10-12 = 1), A / B MN-major (bits 15 / 16), N / 8 (bits
+// 17-22), M / 16 (bits 24-28).
+__host__ __device__ constexpr unsigned idesc_bf16(int m, int n, bool mn_major)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | (mn_major ? (1u << 15) | (1u << 16) : 0u) |
+           ((unsigned)(n >> 3) << 17) | ((unsigned)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(unsigned tmem, uint64_t ad, uint64_t bd, unsigned id, unsigned accum)
+{
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(id), "r"(accum));
+}
+__device__ __forceinline__ void mma_commit(unsigned bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// 32 lanes x 16 columns of FP32 from TMEM (this warp's lane quarter)
+__device__ __forceinline__ void tmem_ld16(unsigned addr, unsigned *v)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(unsigned *slot, int cols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(cv_smem_u32(slot)),
+                 "r"(cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_free(unsigned tmem, int cols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// a role gives up: the CTA's flag and the device-wide one the host reads
+__device__ __forceinline__ void give_up(volatile int *abort)
+{
+    *abort = 1;
+    atomicOr(&g_conv_timeout, 1);
+}
+
+// the wait variant for draining after a give-up: never cut short
+__device__ __forceinline__ bool mbar_wait_plain(unsigned bar, unsigned parity, int limit)
+{
+    for (int it = 0; it < limit; it++)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
+
+// patch mt of the image grid: image b, top-left (x0, y0) of a bx x by patch
+__device__ __forceinline__ void patch_of(int mt, int ntx, int nty, int bx, int by, int &b, int &y0, int &x0)
+{
+    const int per = ntx * nty;
+    b = mt / per;
+    const int r = mt - b * per, ty = r / ntx;
+    y0 = ty * by;
+    x0 = (r - ty * ntx) * bx;
+}
+
+// ---------------------------------------------------------- conv forward
+
+constexpr int FW_THREADS = 192;  // warp 0 copies, warp 1 MMAs, warps 2-5 epilogue
+
+__host__ __device__ constexpr int fwd_stages(int BN, int KC)
+{
+    return (196608 / ((128 + BN) * KC * 2)) < 8 ? (196608 / ((128 + BN) * KC * 2)) : 8;
+}
+
+template <int BN, int KC>
+struct FwdCfg {
+    static constexpr int S = fwd_stages(BN, KC);
+    static constexpr unsigned ROW = KC * 2;  // bytes per operand row: one swizzle width
+    static constexpr unsigned A_BYTES = 128 * ROW, B_BYTES = BN * ROW, STAGE = A_BYTES + B_BYTES;
+    static constexpr unsigned SMEM = S * STAGE + 1024;  // + slack to align the ring to 1024 bytes
+    static constexpr unsigned SW = KC == 64 ? 2u : 4u;   // 128- or 64-byte swizzle
+};
+
+// out[b, y, x, out_c0 + co] = act(bias[co] + sum over taps, ci of
+// in[b, y + dy, x + dx, ci] W[co][tap][ci]), zero outside the image.
+template <int BN, int KC>
+__global__ void __launch_bounds__(FW_THREADS, 1)
+k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_w,
+              const float *__restrict__ bias, bf16 *__restrict__ out, int out_cs, int out_c0, int Cout, int Cin,
+              int B, int H, int Wd, int taps, int relu, int bx, int by, int ntx, int nty)
+{
+    using C = FwdCfg<BN, KC>;
+    constexpr int S = C::S;
+    extern __shared__ unsigned char fw_smem[];
+    __shared__ __align__(8) uint64_t full[S], empty[S], tfull[2], tempty[2], drain;
+    __shared__ unsigned tbase;
+    __shared__ int s_abort;
+    volatile int *abort = &s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) s_abort = *(volatile int *)&g_conv_timeout;  // an earlier CTA gave up
+    __syncthreads();
+    if (s_abort) return;
+    const unsigned ring = (cv_smem_u32(fw_smem) + 1023u) & ~1023u;
+    if (warp == 0) tmem_alloc(&tbase, 2 * BN);
+    if (tid == 32) {
+        for (int s = 0; s < S; s++) {
+            mbar_init(cv_smem_u32(&full[s]), 1);
+            mbar_init(cv_smem_u32(&empty[s]), 1);
+        }
+        for (int a = 0; a < 2; a++) {
+            mbar_init(cv_smem_u32(&tfull[a]), 1);
+            mbar_init(cv_smem_u32(&tempty[a]), 4);  // one arrival per epilogue warp
+        }
+        mbar_init(cv_smem_u32(&drain), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = tbase;
+    const int kch = Cin / KC, KT = taps * kch;
+    const int nnt = Cout / BN, ntiles = ntx * nty * B * nnt;
+    const int limit = g_conv_wait_limit;
+    int issued = 0;  // warp 0, lane 0: stage fills issued
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tma_prefetch(&tm_in);
+            tma_prefetch(&tm_w);
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int mt = t / nnt, n0 = (t - mt * nnt) * BN;
+                int b, y0, x0;
+                patch_of(mt, ntx, nty, bx, by, b, y0, x0);
+                for (int kt = 0; kt < KT; kt++) {
+                    const int s = issued % S, u = issued / S;
+                    if (u > 0 && !mbar_wait(cv_smem_u32(&empty[s]), (unsigned)((u - 1) & 1), limit, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    const int tap = kt / kch, ci0 = (kt - tap * kch) * KC;
+                    const int dy = taps == 9 ? tap / 3 - 1 : 0, dx = taps == 9 ? tap % 3 - 1 : 0;
+                    const unsigned fb = cv_smem_u32(&full[s]), a = ring + (unsigned)s * C::STAGE;
+                    mbar_expect_tx(fb, C::STAGE);
+                    tma_load_4d(a, &tm_in, fb, ci0, x0 + dx, y0 + dy, b);
+                    tma_load_2d(a + C::A_BYTES, &tm_w, fb, tap * Cin + ci0, n0);
+                    issued++;
+                }
+            }
+            if (!ok) give_up(abort);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const unsigned id = idesc_bf16(128, BN, false);
+            bool ok = true;
+            int it = 0, tc = 0;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, tc++) {
+                const int acc = tc & 1, ua = tc >> 1;
+                if (ua > 0 && !mbar_wait(cv_smem_u32(&tempty[acc]), (unsigned)((ua - 1) & 1), limit, abort)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const unsigned d = tmem + (unsigned)(acc * BN);
+                for (int kt = 0; kt < KT; kt++, it++) {
+                    const int s = it % S, u = it / S;
+                    if (!mbar_wait(cv_smem_u32(&full[s]), (unsigned)(u & 1), limit, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const unsigned a = ring + (unsigned)s * C::STAGE, bb = a + C::A_BYTES;
+#pragma unroll
+                    for (int ks = 0; ks < KC / 16; ks++)
+                        mma_bf16(d, sdesc_sw(a + ks * 32, 16, 8 * C::ROW, C::SW),
+                                 sdesc_sw(bb + ks * 32, 16, 8 * C::ROW, C::SW), id, (kt > 0 || ks > 0) ? 1u : 0u);
+                    mma_commit(cv_smem_u32(&empty[s]));  // the stage is free once these MMAs are done
+                }
+                if (!ok) break;
+                mma_commit(cv_smem_u32(&tfull[acc]));  // the tile's accumulator is complete
+            }
+            if (!ok) give_up(abort);
+        }
+    } else {
+        // warps 2-5: TMEM lane quarter warp % 4 holds tile rows 32 (warp % 4) + lane
+        const int q = warp & 3, m = 32 * q + lane;
+        int tc = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, tc++) {
+            const int acc = tc & 1, ua = tc >> 1;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(cv_smem_u32(&tfull[acc]), (unsigned)(ua & 1), limit, abort);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0) give_up(abort);
+                break;
+            }
+            tc_fence_after();
+            const int mt = t / nnt, n0 = (t - mt * nnt) * BN;
+            int b, y0, x0;
+            patch_of(mt, ntx, nty, bx, by, b, y0, x0);
+            const int x = x0 + (m & (bx - 1)), y = y0 + m / bx;  // bx: a power of two
+            const bool v = x < Wd && y < H;
+            bf16 *dst = out + ((int64_t)(b * H + y) * Wd + x) * out_cs + out_c0 + n0;
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                unsigned r[16];
+                tmem_ld16(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(acc * BN + c0), r);
+                if (v) {
+                    __align__(16) __nv_bfloat162 h[8];
+#pragma unroll
+                    for (int j = 0; j < 8; j++) {
+                        float v0 = __uint_as_float(r[2 * j]) + (bias ? bias[n0 + c0 + 2 * j] : 0.0f);
+                        float v1 = __uint_as_float(r[2 * j + 1]) + (bias ? bias[n0 + c0 + 2 * j + 1] : 0.0f);
+                        if (relu) {
+                            v0 = fmaxf(v0, 0.0f);
+                            v1 = fmaxf(v1, 0.0f);
+                        }
+                        h[j] = __floats2bfloat162_rn(v0, v1);
+                    }
+                    uint4 *o = (uint4 *)(dst + c0);
+                    o[0] = *(const uint4 *)&h[0];
+                    o[1] = *(const uint4 *)&h[4];
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(cv_smem_u32(&tempty[acc]));  // the accumulator may be overwritten
+        }
+    }
+    __syncthreads();
+    if (s_abort) {
+        // gave up: no copy into shared memory and no MMA into tensor memory
+        // may still be running when the CTA frees them
+        if (tid == 0)
+            for (int j = issued > S ? issued - S : 0; j < issued; j++)
+                mbar_wait_plain(cv_smem_u32(&full[j % S]), (unsigned)((j / S) & 1), TC_WAIT);
+        if (tid == 32) {
+            mma_commit(cv_smem_u32(&drain));  // arrives once every MMA issued so far is done
+            mbar_wait_plain(cv_smem_u32(&drain), 0u, TC_WAIT);
+        }
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        tmem_free(tmem, 2 * BN);
+    }
+}
+
+// ------------------------------------------------------------ conv wgrad
+
+constexpr int WG_THREADS = 128;  // warp 0 copies, warp 1 MMAs, all four the epilogue
+constexpr int WG_STAGES = 4;
+constexpr int WG_PIX = 64;  // pixels (K) per stage
+
+template <int BN, int KCA, int KCB>
+struct WgdCfg {
+    static constexpr unsigned A_ROW = KCA * 2, B_ROW = KCB * 2;                // bytes per pixel row of a box
+    static constexpr unsigned A_BOX = WG_PIX * A_ROW, B_BOX = WG_PIX * B_ROW;  // one TMA box
+    static constexpr unsigned A_BYTES = 128 * WG_PIX * 2, B_BYTES = BN * WG_PIX * 2;
+    static constexpr unsigned STAGE = A_BYTES + B_BYTES;
+    static constexpr unsigned SMEM = WG_STAGES * STAGE + 1024;
+    static constexpr unsigned A_SW = KCA == 64 ? 2u : 4u, B_SW = KCB == 64 ? 2u : 4u;
+};
+
+// part[split][co][tap * Cin + ci] = sum over the split's pixel patches of
+// in[p shifted by tap][ci] grad[p][co] (zero outside the image). Tile: 128
+// rows (tap, ci) from blockIdx.x, BN output channels from blockIdx.y; the
+// split's patches from blockIdx.z.
+template <int BN, int KCA, int KCB>
+__global__ void __launch_bounds__(WG_THREADS, 1)
+k_conv_wgrad_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_g, int Cout,
+                int Cin, int taps, int bx, int by, int ntx, int nty, int npatch, int per_split,
+                float *__restrict__ part)
+{
+    using C = WgdCfg<BN, KCA, KCB>;
+    constexpr int S = WG_STAGES;
+    extern __shared__ unsigned char wg_smem[];
+    __shared__ __align__(8) uint64_t full[S], empty[S], done, drain;
+    __shared__ unsigned tbase;
+    __shared__ int s_abort;
+    volatile int *abort = &s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) s_abort = *(volatile int *)&g_conv_timeout;  // an earlier CTA gave up
+    __syncthreads();
+    if (s_abort) return;
+    const unsigned ring = (cv_smem_u32(wg_smem) + 1023u) & ~1023u;
+    const int K = taps * Cin, kk0 = blockIdx.x * 128, n0 = blockIdx.y * BN;
+    const int p0 = blockIdx.z * per_split, p1 = min(npatch, p0 + per_split), KT = p1 > p0 ? p1 - p0 : 0;
+    const int nA = min(128, K - kk0) / KCA;  // boxes holding rows of this tile (KCA divides Cin)
+    if (warp == 0) tmem_alloc(&tbase, BN);
+    if (tid == 32) {
+        for (int s = 0; s < S; s++) {
+            mbar_init(cv_smem_u32(&full[s]), 1);
+            mbar_init(cv_smem_u32(&empty[s]), 1);
+        }
+        mbar_init(cv_smem_u32(&done), 1);
+        mbar_init(cv_smem_u32(&drain), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = tbase;
+    const int limit = g_conv_wait_limit;
+    int issued = 0;
+
+    if (tid == 0) {
+        tma_prefetch(&tm_in);
+        tma_prefetch(&tm_g);
+        const unsigned bytes = (unsigned)nA * C::A_BOX + C::B_BYTES;
+        for (int kt = 0; kt < KT; kt++) {
+            const int s = kt % S, u = kt / S;
+            if (u > 0 && !mbar_wait(cv_smem_u32(&empty[s]), (unsigned)((u - 1) & 1), limit, abort)) {
+                give_up(abort);
+                break;
+            }
+            int b, y0, x0;
+            patch_of(p0 + kt, ntx, nty, bx, by, b, y0, x0);
+            const unsigned fb = cv_smem_u32(&full[s]), a = ring + (unsigned)s * C::STAGE;
+            mbar_expect_tx(fb, bytes);
+            for (int r = 0; r < nA; r++) {
+                const int kk = kk0 + r * KCA, tap = kk / Cin, ci0 = kk - tap * Cin;
+                const int dy = taps == 9 ? tap / 3 - 1 : 0, dx = taps == 9 ? tap % 3 - 1 : 0;
+                tma_load_4d(a + (unsigned)r * C::A_BOX, &tm_in, fb, ci0, x0 + dx, y0 + dy, b);
+            }
+#pragma unroll
+            for (int j = 0; j < BN / KCB; j++)
+                tma_load_4d(a + C::A_BYTES + (unsigned)j * C::B_BOX, &tm_g, fb, n0 + j * KCB, x0, y0, b);
+            issued++;
+        }
+    } else if (tid == 32) {
+        const unsigned id = idesc_bf16(128, BN, true);
+        bool ok = true;
+        for (int kt = 0; kt < KT; kt++) {
+            const int s = kt % S, u = kt / S;
+            if (!mbar_wait(cv_smem_u32(&full[s]), (unsigned)(u & 1), limit, abort)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const unsigned a = ring + (unsigned)s * C::STAGE, bb = a + C::A_BYTES;
+#pragma unroll
+            for (int ks = 0; ks < WG_PIX / 16; ks++)  // 16 pixels = two 8-row groups per MMA
+                mma_bf16(tmem, sdesc_sw(a + ks * 16 * C::A_ROW, C::A_BOX, 8 * C::A_ROW, C::A_SW),
+                         sdesc_sw(bb + ks * 16 * C::B_ROW, C::B_BOX, 8 * C::B_ROW, C::B_SW), id,
+                         (kt > 0 || ks > 0) ? 1u : 0u);
+            mma_commit(cv_smem_u32(&empty[s]));
+        }
+        if (ok) mma_commit(cv_smem_u32(&done));
+        else give_up(abort);
+    }
+    __syncwarp();
+    // epilogue: warp w holds rows 32 w + lane of the tile
+    int ok = 1;
+    if (lane == 0) {
+        ok = !s_abort;
+        if (ok && KT > 0) {
+            ok = mbar_wait(cv_smem_u32(&done), 0u, limit, abort);
+            if (!ok) give_up(abort);
+        }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (ok) {
+        const int kk = kk0 + 32 * warp + lane;
+        float *dst = part + ((int64_t)blockIdx.z * Cout + n0) * K + kk;
+        if (KT == 0) {  // an empty split contributes zeros
+            if (kk < K)
+                for (int c = 0; c < BN; c++) dst[(int64_t)c * K] = 0.0f;
+        } else {
+            tc_fence_after();
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                unsigned r[16];
+                tmem_ld16(tmem + ((unsigned)(32 * warp) << 16) + (unsigned)c0, r);
+                if (kk < K)
+#pragma unroll
+                    for (int j = 0; j < 16; j++) dst[(int64_t)(c0 + j) * K] = __uint_as_float(r[j]);
+            }
+        }
+    }
+    __syncthreads();
+    if (s_abort) {
+        if (tid == 0)
+            for (int j = issued > S ? issued - S : 0; j < issued; j++)
+                mbar_wait_plain(cv_smem_u32(&full[j % S]), (unsigned)((j / S) & 1), TC_WAIT);
+        if (tid == 32) {
+            mma_commit(cv_smem_u32(&drain));
+            mbar_wait_plain(cv_smem_u32(&drain), 0u, TC_WAIT);
+        }
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        tmem_free(tmem, BN);
+    }
+}
+
+// out[i] = sum over splits s (in order) of part[s][i]
+__global__ void k_conv_fold(const float *__restrict__ part, int64_t n, int splits, float *__restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.0f;
+    for (int q = 0; q < splits; q++) s += part[(int64_t)q * n + i];
+    out[i] = s;
+}
+
+// per-split column sums of grad (the bias gradient): part[split][c]
+__global__ void k_conv_bias_part(const bf16 *__restrict__ grad, int g_cs, int C, int M, int pix_per_split,
+                                 float *__restrict__ part)
+{
+    const int p0 = blockIdx.x * pix_per_split, p1 = min(M, p0 + pix_per_split);
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float s = 0.0f;
+        for (int p = p0; p < p1; p++) s += __bfloat162float(grad[(int64_t)p * g_cs + c]);
+        part[(int64_t)blockIdx.x * C + c] = s;
+    }
+}
+
+// ------------------------------------------------------------------ host
+
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// NHWC activation (C channels of cs-wide pixel rows starting at base) as a
+// 4D map (channel, x, y, image); box (kc channels, bx, by, 1), swizzled to
+// the box's row width, zeros outside the tensor.
+static cudaError_t act_map(CUtensorMap *m, const bf16 *base, int C, int cs, int B, int H, int W, int kc, int bx,
+                           int by)
+{
+    auto enc = tmap_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    if ((uintptr_t)base % 16) return cudaErrorMisalignedAddress;
+    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t strides[3] = {(cuuint64_t)cs * 2, (cuuint64_t)W * cs * 2, (cuuint64_t)H * W * cs * 2};
+    const cuuint32_t box[4] = {(cuuint32_t)kc, (cuuint32_t)bx, (cuuint32_t)by, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)base, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           kc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// weights [Cout][K] (K = taps x Cin, K-major rows) as a 2D map; box (kc, bn)
+static cudaError_t weight_map(CUtensorMap *m, const bf16 *W, int K, int Cout, int kc, int bn)
+{
+    auto enc = tmap_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    if ((uintptr_t)W % 16) return cudaErrorMisalignedAddress;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)Cout};
+    const cuuint64_t strides[1] = {(cuuint64_t)K * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kc, (cuuint32_t)bn};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)W, dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           kc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+static int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int d = 0;
+        if (cudaGetDevice(&d) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) !=
+                                                    cudaSuccess || n <= 0)
+            n = 1;
+    }
+    return n;
+}
+
+// patch of `pix` pixels (a power of two): bx = the smallest power of two
+// >= W (at most pix), by = pix / bx
+static void patch_shape(int W, int pix, int &bx, int &by)
+{
+    bx = 1;
+    while (bx < W && bx < pix) bx *= 2;
+    by = pix / bx;
+}
+
+// largest of 256, 128, 64, 32 that divides c (c a multiple of 32)
+static int tile_n(int c) { return c % 256 == 0 ? 256 : c % 128 == 0 ? 128 : c % 64 == 0 ? 64 : 32; }
+
+template <typename Kern>
+static cudaError_t smem_attr(Kern k, unsigned bytes, bool &done)
+{
+    if (done) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+template <int BN, int KC>
+static cudaError_t launch_fwd(const CUtensorMap &ti, const CUtensorMap &tw, const float *bias, bf16 *out, int out_cs,
+                              int out_c0, int Cout, int Cin, int B, int H, int Wd, int taps, int relu, int bx, int by,
+                              int ntx, int nty, cudaStream_t st)
+{
+    static bool attr = false;
+    cudaError_t e = smem_attr(k_conv_fwd_tc<BN, KC>, FwdCfg<BN, KC>::SMEM, attr);
+    if (e != cudaSuccess) return e;
+    const int64_t ntiles = (int64_t)ntx * nty * B * (Cout / BN);
+    const int grid = (int)std::min<int64_t>(ntiles, sm_count());
+    k_conv_fwd_tc<BN, KC><<<grid, FW_THREADS, FwdCfg<BN, KC>::SMEM, st>>>(ti, tw, bias, out, out_cs, out_c0, Cout,
+                                                                         Cin, B, H, Wd, taps, relu, bx, by, ntx, nty);
+    return cudaGetLastError();
+}
+
+cudaError_t conv_fwd(const bf16 *in, int in_cs, int in_c0, int Cin, const bf16 *W, const float *bias, bf16 *out,
+                     int out_cs, int out_c0, int Cout, int B, int H, int Wd, int taps, bool relu, cudaStream_t st)
+{
+    if (Cin % 32 || Cout % 32 || (in_cs | in_c0 | out_cs | out_c0) % 8 || (taps != 1 && taps != 9))
+        return cudaErrorInvalidValue;
+    if ((int64_t)B * H * Wd == 0) return cudaSuccess;
+    const int KC = Cin % 64 == 0 ? 64 : 32, BN = tile_n(Cout);
+    int bx, by;
+    patch_shape(Wd, 128, bx, by);
+    const int ntx = (Wd + bx - 1) / bx, nty = (H + by - 1) / by;
+    if ((int64_t)ntx * nty * B * (Cout / BN) > INT32_MAX) return cudaErrorInvalidValue;
+    CUtensorMap ti, tw;
+    cudaError_t e = act_map(&ti, in + in_c0, Cin, in_cs, B, H, Wd, KC, bx, by);
+    if (e == cudaSuccess) e = weight_map(&tw, W, taps * Cin, Cout, KC, BN);
+    if (e != cudaSuccess) return e;
+#define FWD_CASE(bn, kc)                                                                                         \
+    if (BN == bn && KC == kc)                                                                                    \
+        return launch_fwd<bn, kc>(ti, tw, bias, out, out_cs, out_c0, Cout, Cin, B, H, Wd, taps, relu ? 1 : 0, bx, \
+                                  by, ntx, nty, st);
+    FWD_CASE(256, 64)
+    FWD_CASE(128, 64)
+    FWD_CASE(64, 64)
+    FWD_CASE(32, 64)
+    FWD_CASE(256, 32)
+    FWD_CASE(128, 32)
+    FWD_CASE(64, 32)
+    FWD_CASE(32, 32)
+#undef FWD_CASE
+    return cudaErrorInvalidValue;
+}
+
+template <int BN, int KCA, int KCB>
+static cudaError_t launch_wgrad(dim3 grid, const CUtensorMap &ti, const CUtensorMap &tg, int Cout, int Cin, int taps,
+                                int bx, int by, int ntx, int nty, int npatch, int per_split, float *part,
+                                cudaStream_t st)
+{
+    static bool attr = false;
+    cudaError_t e = smem_attr(k_conv_wgrad_tc<BN, KCA, KCB>, WgdCfg<BN, KCA, KCB>::SMEM, attr);
+    if (e != cudaSuccess) return e;
+    k_conv_wgrad_tc<BN, KCA, KCB><<<grid, WG_THREADS, WgdCfg<BN, KCA, KCB>::SMEM, st>>>(
+        ti, tg, Cout, Cin, taps, bx, by, ntx, nty, npatch, per_split, part);
+    return cudaGetLastError();
+}
+
+cudaError_t conv_wgrad(const bf16 *grad, int g_cs, int Cout, const bf16 *in, int in_cs, int in_c0, int Cin, int B,
+                       int H, int Wd, int taps, float *dW, float *db, float *scratch, size_t scratch_floats,
+                       cudaStream_t st)
+{
+    if (Cin % 32 || Cout % 32 || (g_cs | in_cs | in_c0) % 8 || (taps != 1 && taps != 9)) return cudaErrorInvalidValue;
+    const int64_t M = (int64_t)B * H * Wd;
+    const int64_t K = (int64_t)taps * Cin, per = (int64_t)Cout * K;
+    if ((size_t)per > scratch_floats) return cudaErrorMemoryAllocation;
+    if (M == 0) {
+        cudaError_t e = cudaMemsetAsync(dW, 0, per * sizeof(float), st);
+        if (e == cudaSuccess && db) e = cudaMemsetAsync(db, 0, Cout * sizeof(float), st);
+        return e;
+    }
+    const int KCA = Cin % 64 == 0 ? 64 : 32, BN = tile_n(Cout), KCB = BN % 64 == 0 ? 64 : 32;
+    int bx, by;
+    patch_shape(Wd, WG_PIX, bx, by);
+    const int ntx = (Wd + bx - 1) / bx, nty = (H + by - 1) / by;
+    const int64_t npatch64 = (int64_t)ntx * nty * B;
+    if (npatch64 > INT32_MAX) return cudaErrorInvalidValue;
+    const int npatch = (int)npatch64;
+    // pixel splits: enough CTAs to fill the SMs (two per SM where shared
+    // memory allows), bounded by the scratch for the partial tiles
+    const int mt = (int)((K + 127) / 128), nt = Cout / BN;
+    const bool two = (BN == 32 ? WgdCfg<32, 64, 32>::SMEM : BN == 64 ? WgdCfg<64, 64, 64>::SMEM : 1u << 20) <= 113 * 1024;
+    const int64_t target = (int64_t)sm_count() * (two ? 2 : 1);
+    int64_t splits = std::max<int64_t>(1, (target + mt * nt - 1) / (mt * nt));
+    splits = std::min<int64_t>(splits, npatch);
+    while (splits > 1 && (size_t)(splits * per) > scratch_floats) splits = (splits + 1) / 2;
+    if ((size_t)(splits * per) > scratch_floats) splits = 1;
+    const int per_split = (int)((npatch + splits - 1) / splits);
+    splits = (npatch + per_split - 1) / per_split;
+    CUtensorMap ti, tg;
+    cudaError_t e = act_map(&ti, in + in_c0, Cin, in_cs, B, H, Wd, KCA, bx, by);
+    if (e == cudaSuccess) e = act_map(&tg, grad, Cout, g_cs, B, H, Wd, KCB, bx, by);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((unsigned)mt, (unsigned)nt, (unsigned)splits);
+#define WG_CASE(bn, kca, kcb)                                                                                       \
+    if (BN == bn && KCA == kca && KCB == kcb)                                                                       \
+        e = launch_wgrad<bn, kca, kcb>(grid, ti, tg, Cout, Cin, taps, bx, by, ntx, nty, npatch, per_split, scratch, \
+                                       st);                                                                         \
+    else
+    WG_CASE(256, 64, 64)
+    WG_CASE(128, 64, 64)
+    WG_CASE(64, 64, 64)
+    WG_CASE(32, 64, 32)
+    WG_CASE(256, 32, 64)
+    WG_CASE(128, 32, 64)
+    WG_CASE(64, 32, 64)
+    WG_CASE(32, 32, 32)
+    e = cudaErrorInvalidValue;
+#undef WG_CASE
+    if (e != cudaSuccess) return e;
+    k_conv_fold<<<(unsigned)((per + 255) / 256), 256, 0, st>>>(scratch, per, (int)splits, dW);
+    if (db) {
+        int64_t bs = (M + 1023) / 1024;
+        if (bs > 1024) bs = 1024;
+        const int bpp = (int)((M + bs - 1) / bs);
+        k_conv_bias_part<<<(unsigned)bs, 256, 0, st>>>(grad, g_cs, Cout, (int)M, bpp, scratch);
+        k_conv_fold<<<(unsigned)((Cout + 255) / 256), 256, 0, st>>>(scratch, Cout, (int)bs, db);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t conv_timeout(bool *flag, cudaStream_t st)
+{
+    int v = 0;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_conv_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    *flag = v != 0;
+    if (e == cudaSuccess && v) {  // reported once; later convolutions run again
+        const int zero = 0;
+        e = cudaMemcpyToSymbolAsync(g_conv_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    return e;
+}
+
+cudaError_t conv_set_wait_limit(int polls, cudaStream_t st)
+{
+    const int v = polls >= 0 ? polls : TC_WAIT;
+    cudaError_t e = cudaMemcpyToSymbolAsync(g_conv_wait_limit, &v, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+}
+
+}  // namespace nn
+}  // namespace lsm

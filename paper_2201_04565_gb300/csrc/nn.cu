@@ -7,20 +7,18 @@
 // its prediction only moves the starting point of the relaxation, which then
 // runs to the same force-residual tolerance as without it.
 //
-// Convolutions are implicit GEMMs (BF16 in, FP32 accumulate):
-//   forward   M = pixels, N = Cout, K = taps x Cin (bias + ReLU epilogue), on
-//             the 5th-generation tensor cores (tcgen05.mma, accumulators in
-//             tensor memory)
+// Convolutions are implicit GEMMs on the 5th-generation tensor cores (BF16
+// operands staged by TMA, FP32 accumulators in tensor memory; conv_tc.cu):
+//   forward   M = pixels, N = Cout, K = taps x Cin (bias + ReLU epilogue)
 //   dgrad     the forward kernel with 180-degree rotated, transposed weights
-//   wgrad     M = Cout, N = taps x Cin, K = pixels, split over pixel chunks,
-//             partial tiles folded in a fixed order (deterministic), on
-//             mma.sync m16n8k16 with cp.async double-buffered, XOR-swizzled
-//             shared tiles and ldmatrix fragment loads
+//   wgrad     M = taps x Cin, N = Cout, K = pixels, split over pixel patches,
+//             partial tiles folded in a fixed order (deterministic)
 // Everything else (pooling, upsampling, head, loss, Adam, data preparation)
 // is plain elementwise or fixed-order reduction kernels.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -35,369 +33,6 @@
 namespace lsm {
 namespace nn {
 
-// ------------------------------------------------------------ PTX helpers
-
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void cp_async16(unsigned dst, const void *src, bool valid)
-{
-    const int sz = valid ? 16 : 0;  // 0: fill the 16 bytes with zeros, read nothing
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(sz));
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_wait()
-{
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
-
-__device__ __forceinline__ void ldm_x4(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3, unsigned addr)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-__device__ __forceinline__ void ldm_x4_t(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3, unsigned addr)
-{
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
-}
-__device__ __forceinline__ void mma16816(float *c, unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
-                                         unsigned b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
-// 64-byte rows of 4 16-byte chunks: chunk position XOR-ed with (row / 2) % 4,
-// so the 8 rows an ldmatrix reads hit 8 distinct bank groups.
-__device__ __forceinline__ int swz(int row, int chunk) { return row * 32 + ((chunk ^ ((row >> 1) & 3)) << 3); }
-
-// ---------------------------------------------------------- conv forward
-//
-// Implicit GEMM on the 5th-generation tensor cores: tcgen05.mma (kind::f16,
-// BF16 operands in shared memory, FP32 accumulators in tensor memory). A CTA
-// of 128 threads owns 128 output pixels (TMEM lanes) x BN output channels
-// (TMEM columns). The K loop runs over taps x 32-channel chunks: the threads
-// copy the chunk (each thread its pixel's shifted input row, zero outside the
-// image, and a share of the BN weight rows) with cp.async into a two-stage
-// buffer of 8-row x 16-byte core matrices (K-major, no swizzle); thread 0
-// issues two K = 16 MMAs per chunk and commits them to the stage's mbarrier,
-// and a stage is refilled only after its barrier reports those MMAs done.
-// The epilogue reads the accumulator back with tcgen05.ld (each warp its 32
-// lanes), adds the bias, applies the ReLU and stores BF16. Every mbarrier
-// wait is bounded (g_conv_wait_limit polls, one thread per CTA, its result
-// shared through a barrier so that the CTA decides as one): on expiry the CTA
-// raises g_conv_timeout, waits for its copies and (bounded again, with the
-// default limit) for the MMAs it has issued, skips the epilogue, frees its
-// TMEM and returns; later CTAs return at once.
-
-__device__ int g_conv_timeout;
-
-constexpr int TCM = 128, TCK = 32;
-constexpr int TC_WAIT = 1 << 20;
-__device__ int g_conv_wait_limit = TC_WAIT;
-
-// shared-memory matrix descriptor (no swizzle; K-major core matrices; LBO
-// = stride between core matrices along K, SBO = along M or N)
-__device__ __forceinline__ uint64_t tc_sdesc(unsigned addr, unsigned lbo, unsigned sbo)
-{
-    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
-}
-
-// instruction descriptor: D FP32, A and B BF16, both K-major, M x N
-__host__ __device__ constexpr unsigned tc_idesc(int m, int n)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(m >> 4) << 24);
-}
-
-__device__ __forceinline__ bool tc_wait(unsigned bar, unsigned parity, int limit)
-{
-    unsigned done = 0;
-    for (int it = 0; it < limit && !done; it++)
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity));
-    return done != 0;
-}
-
-// byte offset of (row, 16-byte chunk) in a stage of rows x 32 channels:
-// core matrix (row / 8, chunk) at ((row / 8) * 4 + chunk) * 128, row (row % 8) * 16
-__device__ __forceinline__ unsigned tc_off(int row, int chunk)
-{
-    return (unsigned)((((row >> 3) << 2) + chunk) * 128 + (row & 7) * 16);
-}
-
-template <int BN>
-__global__ void __launch_bounds__(128)
-k_conv_fwd(const bf16 *__restrict__ in, int in_cs, int in_c0, int Cin, const bf16 *__restrict__ W,
-           const float *__restrict__ bias, bf16 *__restrict__ out, int out_cs, int out_c0, int Cout, int B, int H,
-           int Wd, int taps, int relu)
-{
-    __shared__ __align__(1024) unsigned char sA[2][TCM * TCK * 2];
-    __shared__ __align__(1024) unsigned char sB[2][BN * TCK * 2];
-    __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ unsigned tbase;
-    __shared__ int s_abort;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (tid == 0) s_abort = *(volatile int *)&g_conv_timeout;  // an earlier CTA gave up
-    __syncthreads();
-    if (s_abort) return;
-    const int HW = H * Wd, M = B * HW;
-    const int m0 = blockIdx.x * TCM, n0 = blockIdx.y * BN;
-    const int kch = Cin / TCK, KT = taps * kch;
-    const int m = m0 + tid;
-    const bool mv = m < M;
-    const int mm = mv ? m : 0;
-    const int pb = mm / HW, prem = mm - pb * HW, py = prem / Wd, px = prem - py * Wd;
-
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)),
-                     "r"(BN));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
-        asm volatile("fence.mbarrier_init.release.cluster;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const unsigned tmem = tbase;
-
-    auto load = [&](int kt, int buf) {
-        const int tap = kt / kch, ci0 = (kt - tap * kch) * TCK;
-        const int dy = taps == 9 ? tap / 3 - 1 : 0, dx = taps == 9 ? tap % 3 - 1 : 0;
-        const int yy = py + dy, xx = px + dx;
-        const bool v = mv && yy >= 0 && yy < H && xx >= 0 && xx < Wd;
-        const bf16 *src = v ? in + ((int64_t)(pb * H + yy) * Wd + xx) * in_cs + in_c0 + ci0 : in;
-        const unsigned a = smem_u32(&sA[buf][0]);
-#pragma unroll
-        for (int c = 0; c < 4; c++) cp_async16(a + tc_off(tid, c), v ? src + 8 * c : in, v);
-        const unsigned b = smem_u32(&sB[buf][0]);
-        for (int e = tid; e < BN * 4; e += 128) {
-            const int r = e >> 2, c = e & 3, co = n0 + r;
-            const bool wv = co < Cout;
-            cp_async16(b + tc_off(r, c), wv ? W + ((int64_t)co * taps + tap) * Cin + ci0 + 8 * c : W, wv);
-        }
-    };
-
-    const int limit = g_conv_wait_limit;
-    bool ok = true;
-    int last = -1;  // last chunk whose MMAs were committed
-    load(0, 0);
-    cp_commit();
-    for (int kt = 0; kt < KT && ok; kt++) {
-        const int buf = kt & 1;
-        if (kt + 1 < KT) {
-            const int nb = (kt + 1) & 1;
-            if (kt >= 1) {  // chunk kt-1's MMAs, which read stage nb
-                const bool w = tid != 0 || tc_wait(smem_u32(&mbar[nb]), (unsigned)(((kt - 1) >> 1) & 1), limit);
-                ok = __syncthreads_and(w) != 0;
-            }
-            if (!ok) break;
-            load(kt + 1, nb);
-        }
-        cp_commit();
-        cp_wait<1>();
-        asm volatile("fence.proxy.async.shared::cta;");  // the copies, visible to the tensor core
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const unsigned id = tc_idesc(TCM, BN);
-#pragma unroll
-            for (int ks = 0; ks < 2; ks++) {
-                const uint64_t ad = tc_sdesc(smem_u32(&sA[buf][0]) + ks * 256, 128, 512);
-                const uint64_t bd = tc_sdesc(smem_u32(&sB[buf][0]) + ks * 256, 128, 512);
-                const unsigned accum = (kt > 0 || ks > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(id), "r"(accum));
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&mbar[buf])));
-        }
-        last = kt;
-    }
-    // the last commit covers every earlier MMA of this thread
-    if (ok && KT > 0) {
-        const bool w = tid != 0 || tc_wait(smem_u32(&mbar[(KT - 1) & 1]), (unsigned)(((KT - 1) >> 1) & 1), limit);
-        ok = __syncthreads_and(w) != 0;
-    }
-    if (!ok) {
-        // gave up: no copy into shared memory and no MMA into tensor memory
-        // may still be running when the CTA frees them
-        cp_wait<0>();
-        if (tid == 0) {
-            atomicOr(&g_conv_timeout, 1);
-            if (last >= 0) tc_wait(smem_u32(&mbar[last & 1]), (unsigned)((last >> 1) & 1), TC_WAIT);
-        }
-        __syncthreads();
-    } else {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const int mo = m0 + 32 * warp + lane;
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-            unsigned r[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                "[%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15])
-                : "r"(tmem + ((unsigned)(32 * warp) << 16) + (unsigned)c0));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-            const int n = n0 + c0;
-            if (mo < M && n < Cout) {
-                __align__(16) __nv_bfloat162 h[8];
-#pragma unroll
-                for (int j = 0; j < 8; j++) {
-                    float v0 = __uint_as_float(r[2 * j]) + (bias ? bias[n + 2 * j] : 0.0f);
-                    float v1 = __uint_as_float(r[2 * j + 1]) + (bias ? bias[n + 2 * j + 1] : 0.0f);
-                    if (relu) {
-                        v0 = fmaxf(v0, 0.0f);
-                        v1 = fmaxf(v1, 0.0f);
-                    }
-                    h[j] = __floats2bfloat162_rn(v0, v1);
-                }
-                uint4 *dst = (uint4 *)(out + (int64_t)mo * out_cs + out_c0 + n);
-                dst[0] = *(const uint4 *)&h[0];
-                dst[1] = *(const uint4 *)&h[4];
-            }
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
-}
-
-cudaError_t conv_fwd(const bf16 *in, int in_cs, int in_c0, int Cin, const bf16 *W, const float *bias, bf16 *out,
-                     int out_cs, int out_c0, int Cout, int B, int H, int Wd, int taps, bool relu, cudaStream_t st)
-{
-    if (Cin % TCK || Cout % 32 || (in_cs | in_c0 | out_cs | out_c0) % 8) return cudaErrorInvalidValue;
-    const int M = B * H * Wd;
-    if (M == 0) return cudaSuccess;
-    const int BN = Cout % 128 == 0 ? 128 : (Cout % 64 == 0 ? 64 : 32);
-    const dim3 grid((M + TCM - 1) / TCM, Cout / BN);
-    if (BN == 128)
-        k_conv_fwd<128><<<grid, 128, 0, st>>>(in, in_cs, in_c0, Cin, W, bias, out, out_cs, out_c0, Cout, B, H, Wd, taps, relu);
-    else if (BN == 64)
-        k_conv_fwd<64><<<grid, 128, 0, st>>>(in, in_cs, in_c0, Cin, W, bias, out, out_cs, out_c0, Cout, B, H, Wd, taps, relu);
-    else
-        k_conv_fwd<32><<<grid, 128, 0, st>>>(in, in_cs, in_c0, Cin, W, bias, out, out_cs, out_c0, Cout, B, H, Wd, taps, relu);
-    return cudaGetLastError();
-}
-
-cudaError_t conv_timeout(bool *flag, cudaStream_t st)
-{
-    int v = 0;
-    cudaError_t e = cudaMemcpyFromSymbolAsync(&v, g_conv_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    *flag = v != 0;
-    if (e == cudaSuccess && v) {  // reported once; later convolutions run again
-        const int zero = 0;
-        e = cudaMemcpyToSymbolAsync(g_conv_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    }
-    return e;
-}
-
-cudaError_t conv_set_wait_limit(int polls, cudaStream_t st)
-{
-    const int v = polls >= 0 ? polls : TC_WAIT;
-    cudaError_t e = cudaMemcpyToSymbolAsync(g_conv_wait_limit, &v, sizeof(int), 0, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    return e;
-}
-
-// ------------------------------------------------------------ conv wgrad
-
-constexpr int WPIX = 32;  // pixels per k step
-
-// part[split][co][tap * Cin + ci] = sum over the split's pixels of
-// grad[p][co] * in[p shifted by tap][ci]; 32 x 32 output tile per CTA.
-__global__ void __launch_bounds__(128)
-k_conv_wgrad(const bf16 *__restrict__ grad, int g_cs, int Cout, const bf16 *__restrict__ in, int in_cs, int in_c0,
-             int Cin, int B, int H, int Wd, int taps, int pix_per_split, float *__restrict__ part)
-{
-    __shared__ __align__(128) bf16 sG[2][WPIX * 32];
-    __shared__ __align__(128) bf16 sI[2][WPIX * 32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int HW = H * Wd, M = B * HW;
-    const int cit = Cin / 32;
-    const int tap = blockIdx.x / cit, ci0 = (blockIdx.x - tap * cit) * 32;
-    const int co0 = blockIdx.y * 32;
-    const int p0 = blockIdx.z * pix_per_split, p1 = min(M, p0 + pix_per_split);
-    const int dy = taps == 9 ? tap / 3 - 1 : 0, dx = taps == 9 ? tap % 3 - 1 : 0;
-    const int lrow = tid >> 2, lchk = tid & 3;  // one 16-byte chunk of each tile per thread
-    auto load = [&](int p, int buf) {
-        const int m = p + lrow;
-        const bool vm = m < p1;
-        const int mm = vm ? m : 0;
-        const int b = mm / HW, rem = mm - b * HW, y = rem / Wd, x = rem - (rem / Wd) * Wd;
-        const bf16 *sg = vm ? grad + (int64_t)mm * g_cs + co0 + lchk * 8 : grad;
-        cp_async16(smem_u32(&sG[buf][swz(lrow, lchk)]), sg, vm);
-        const int yy = y + dy, xx = x + dx;
-        const bool vi = vm && yy >= 0 && yy < H && xx >= 0 && xx < Wd;
-        const bf16 *si = vi ? in + ((int64_t)(b * H + yy) * Wd + xx) * in_cs + in_c0 + ci0 + lchk * 8 : in;
-        cp_async16(smem_u32(&sI[buf][swz(lrow, lchk)]), si, vi);
-    };
-    float acc[2][4];
-#pragma unroll
-    for (int j = 0; j < 2; j++)
-#pragma unroll
-        for (int q = 0; q < 4; q++) acc[j][q] = 0.0f;
-    const int wm = warp & 1, wn = warp >> 1;  // 2 x 2 warps of 16 x 16
-    const int nk = (p1 - p0 + WPIX - 1) / WPIX;
-    if (nk > 0) {
-        load(p0, 0);
-        cp_commit();
-    }
-    for (int k = 0; k < nk; k++) {
-        if (k + 1 < nk) load(p0 + (k + 1) * WPIX, (k + 1) & 1);
-        cp_commit();
-        cp_wait<1>();
-        __syncthreads();
-        const int buf = k & 1;
-#pragma unroll
-        for (int ks = 0; ks < 2; ks++) {
-            unsigned a0, a1, a2, a3, b0, b1, b2, b3;
-            {  // A = grad^T: rows co, k = pixels; stored [pixel][co]
-                const int prow = ks * 16 + (lane & 7) + ((lane >> 4) << 3);
-                const int chk = wm * 2 + ((lane >> 3) & 1);
-                ldm_x4_t(a0, a1, a2, a3, smem_u32(&sG[buf][swz(prow, chk)]));
-            }
-            {  // B = shifted input: k = pixels, n = ci; stored [pixel][ci]
-                const int prow = ks * 16 + (lane & 7) + (((lane >> 3) & 1) << 3);
-                const int chk = wn * 2 + (lane >> 4);
-                ldm_x4_t(b0, b1, b2, b3, smem_u32(&sI[buf][swz(prow, chk)]));
-            }
-            mma16816(acc[0], a0, a1, a2, a3, b0, b1);
-            mma16816(acc[1], a0, a1, a2, a3, b2, b3);
-        }
-        __syncthreads();
-    }
-    const int g = lane >> 2, tg = lane & 3;
-    const int64_t K = (int64_t)taps * Cin;
-    float *dst = part + (int64_t)blockIdx.z * Cout * K;
-#pragma unroll
-    for (int j = 0; j < 2; j++)
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int co = co0 + wm * 16 + g + 8 * h;
-            const int ci = ci0 + wn * 16 + j * 8 + 2 * tg;
-            dst[(int64_t)co * K + (int64_t)tap * Cin + ci] = acc[j][2 * h];
-            dst[(int64_t)co * K + (int64_t)tap * Cin + ci + 1] = acc[j][2 * h + 1];
-        }
-}
-
 // out[i] = sum over splits s (in order) of part[s][i].
 __global__ void k_fold(const float *__restrict__ part, int64_t n, int splits, float *__restrict__ out)
 {
@@ -406,44 +41,6 @@ __global__ void k_fold(const float *__restrict__ part, int64_t n, int splits, fl
     float s = 0.0f;
     for (int q = 0; q < splits; q++) s += part[(int64_t)q * n + i];
     out[i] = s;
-}
-
-// Per-split column sums of grad (bias gradient): part[split][c].
-__global__ void k_bias_part(const bf16 *__restrict__ grad, int g_cs, int C, int M, int pix_per_split,
-                            float *__restrict__ part)
-{
-    const int p0 = blockIdx.x * pix_per_split, p1 = min(M, p0 + pix_per_split);
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        float s = 0.0f;
-        for (int p = p0; p < p1; p++) s += __bfloat162float(grad[(int64_t)p * g_cs + c]);
-        part[(int64_t)blockIdx.x * C + c] = s;
-    }
-}
-
-cudaError_t conv_wgrad(const bf16 *grad, int g_cs, int Cout, const bf16 *in, int in_cs, int in_c0, int Cin, int B,
-                       int H, int Wd, int taps, float *dW, float *db, float *scratch, size_t scratch_floats,
-                       cudaStream_t st)
-{
-    if (Cin % 32 || Cout % 32 || (g_cs | in_cs | in_c0) % 8) return cudaErrorInvalidValue;
-    const int M = B * H * Wd;
-    const int64_t K = (int64_t)taps * Cin;
-    const int64_t per = (int64_t)Cout * K;
-    int splits = (M + 4095) / 4096;
-    if (splits > 256) splits = 256;
-    while (splits > 1 && (size_t)splits * per > scratch_floats) splits /= 2;
-    if ((size_t)per > scratch_floats) return cudaErrorMemoryAllocation;
-    const int pps = ((M + splits - 1) / splits + WPIX - 1) / WPIX * WPIX;
-    const dim3 grid((unsigned)(taps * (Cin / 32)), (unsigned)(Cout / 32), (unsigned)splits);
-    k_conv_wgrad<<<grid, 128, 0, st>>>(grad, g_cs, Cout, in, in_cs, in_c0, Cin, B, H, Wd, taps, pps, scratch);
-    k_fold<<<(unsigned)((per + 255) / 256), 256, 0, st>>>(scratch, per, splits, dW);
-    if (db) {
-        int bs = (M + 1023) / 1024;
-        if (bs > 1024) bs = 1024;
-        const int bpp = (M + bs - 1) / bs;
-        k_bias_part<<<bs, 256, 0, st>>>(grad, g_cs, Cout, M, bpp, scratch);
-        k_fold<<<(unsigned)((Cout + 255) / 256), 256, 0, st>>>(scratch, Cout, bs, db);
-    }
-    return cudaGetLastError();
 }
 
 // Wr[ci][tap'][co] = W[co][taps - 1 - tap'][ci]

@@ -26,11 +26,17 @@ def _bf(torch, a):
     return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).cuda()
 
 
-@pytest.mark.parametrize("cin,cout,taps,relu", [(64, 64, 9, 1), (96, 32, 9, 0), (32, 128, 1, 1), (384, 128, 9, 1)])
-def test_conv_forward_matches_reference(env, cin, cout, taps, relu):
+@pytest.mark.parametrize("cin,cout,taps,relu,B,H,W", [(64, 64, 9, 1, 2, 8, 12), (96, 32, 9, 0, 2, 8, 12),
+                                                       (32, 128, 1, 1, 2, 8, 12), (384, 128, 9, 1, 2, 8, 12),
+                                                       (32, 256, 9, 1, 2, 16, 32), (192, 384, 9, 0, 1, 5, 70),
+                                                       (64, 96, 9, 1, 3, 33, 130), (128, 64, 1, 0, 2, 4, 3)])
+def test_conv_forward_matches_reference(env, cin, cout, taps, relu, B, H, W):
+    """The tensor-core forward convolution (patches of 128 pixels: whole,
+    ragged and narrower than the image, 32- and 64-channel K chunks, output
+    tiles of 32 to 256 channels, one or several per row) against the
+    reference, on channel slices of wider tensors."""
     torch, nn = env
-    rng = np.random.default_rng(cin + cout)
-    B, H, W = 2, 8, 12
+    rng = np.random.default_rng(cin + cout + W)
     cs_in, c0_in, cs_out, c0_out = cin + 32, 32, cout + 64, 64  # channel slices of wider tensors
     x = R.bf16(rng.standard_normal((B, H, W, cs_in)))
     Wt = R.bf16(0.2 * rng.standard_normal((cout, taps, cin)))
@@ -90,11 +96,17 @@ def test_conv_wait_timeout_is_reported_and_recovers(env):
     assert np.all(np.abs(got - ref) <= 2 ** -7 * np.abs(ref) + 1e-6 * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("cin,cout,taps", [(64, 64, 9), (32, 256, 9), (96, 32, 1)])
-def test_conv_wgrad_matches_reference(env, cin, cout, taps):
+@pytest.mark.parametrize("cin,cout,taps,B,H,W", [(64, 64, 9, 2, 9, 14), (32, 256, 9, 2, 9, 14),
+                                                  (96, 32, 1, 2, 9, 14), (128, 64, 9, 2, 40, 37),
+                                                  (256, 160, 9, 1, 20, 21), (32, 32, 9, 2, 32, 64),
+                                                  (192, 128, 9, 1, 16, 130)])
+def test_conv_wgrad_matches_reference(env, cin, cout, taps, B, H, W):
+    """The tensor-core weight gradient (tiles of 128 (tap, input channel)
+    rows, the last one partly filled, x 32 to 256 output channels; patches of
+    64 pixels, whole and ragged; one or several pixel splits) against the
+    reference."""
     torch, nn = env
     rng = np.random.default_rng(7 + cin)
-    B, H, W = 2, 9, 14  # ragged pixel count
     x = R.bf16(rng.standard_normal((B, H, W, cin)))
     g = R.bf16(rng.standard_normal((B, H, W, cout)))
     dW = torch.zeros(cout * taps * cin, dtype=torch.float32, device="cuda")
