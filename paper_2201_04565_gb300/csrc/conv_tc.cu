@@ -28,7 +28,9 @@
 // up raises g_conv_timeout and a flag in shared memory that the CTA's other
 // roles see in their own waits; the CTA then waits (bounded again, with the
 // default limit) for the copies and MMAs it has issued, frees its TMEM and
-// returns, and the host reports the convolution as timed out.
+// returns, and the host reports the convolution as timed out. (Grids are
+// about one wave, so CTAs do not consult each other: each one runs into its
+// own bounded waits.)
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -211,6 +213,38 @@ struct FwdCfg {
     static constexpr unsigned SW = KC == 64 ? 2u : 4u;   // 128- or 64-byte swizzle
 };
 
+// Epilogue of one output pixel (b, y, x) of a tile, this thread's TMEM lane
+// (taddr: its first accumulator column): bias, ReLU, BF16 stores of BN
+// channels from n0; nothing is stored for a pixel outside the image.
+template <int BN>
+__device__ __forceinline__ void fwd_store_row(unsigned taddr, bf16 *__restrict__ out, int out_cs, int out_c0, int n0,
+                                              const float *__restrict__ bias, int relu, int b, int x, int y, int H,
+                                              int Wd)
+{
+    const bool v = x < Wd && y < H;
+    bf16 *dst = out + ((int64_t)(b * H + y) * Wd + x) * out_cs + out_c0 + n0;
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        unsigned r[16];
+        tmem_ld16(taddr + (unsigned)c0, r);  // the whole warp, converged
+        if (v) {
+            __align__(16) __nv_bfloat162 h[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                float v0 = __uint_as_float(r[2 * j]) + (bias ? bias[n0 + c0 + 2 * j] : 0.0f);
+                float v1 = __uint_as_float(r[2 * j + 1]) + (bias ? bias[n0 + c0 + 2 * j + 1] : 0.0f);
+                if (relu) {
+                    v0 = fmaxf(v0, 0.0f);
+                    v1 = fmaxf(v1, 0.0f);
+                }
+                h[j] = __floats2bfloat162_rn(v0, v1);
+            }
+            uint4 *o = (uint4 *)(dst + c0);
+            o[0] = *(const uint4 *)&h[0];
+            o[1] = *(const uint4 *)&h[4];
+        }
+    }
+}
+
 // out[b, y, x, out_c0 + co] = act(bias[co] + sum over taps, ci of
 // in[b, y + dy, x + dx, ci] W[co][tap][ci]), zero outside the image.
 template <int BN, int KC>
@@ -227,9 +261,7 @@ k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__
     __shared__ int s_abort;
     volatile int *abort = &s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (tid == 0) s_abort = *(volatile int *)&g_conv_timeout;  // an earlier CTA gave up
-    __syncthreads();
-    if (s_abort) return;
+    if (tid == 0) s_abort = 0;
     const unsigned ring = (cv_smem_u32(fw_smem) + 1023u) & ~1023u;
     if (warp == 0) tmem_alloc(&tbase, 2 * BN);
     if (tid == 32) {
@@ -262,19 +294,20 @@ k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__
                 const int mt = t / nnt, n0 = (t - mt * nnt) * BN;
                 int b, y0, x0;
                 patch_of(mt, ntx, nty, bx, by, b, y0, x0);
-                for (int kt = 0; kt < KT; kt++) {
-                    const int s = issued % S, u = issued / S;
-                    if (u > 0 && !mbar_wait(cv_smem_u32(&empty[s]), (unsigned)((u - 1) & 1), limit, abort)) {
-                        ok = false;
-                        break;
-                    }
-                    const int tap = kt / kch, ci0 = (kt - tap * kch) * KC;
+                for (int tap = 0; tap < taps && ok; tap++) {
                     const int dy = taps == 9 ? tap / 3 - 1 : 0, dx = taps == 9 ? tap % 3 - 1 : 0;
-                    const unsigned fb = cv_smem_u32(&full[s]), a = ring + (unsigned)s * C::STAGE;
-                    mbar_expect_tx(fb, C::STAGE);
-                    tma_load_4d(a, &tm_in, fb, ci0, x0 + dx, y0 + dy, b);
-                    tma_load_2d(a + C::A_BYTES, &tm_w, fb, tap * Cin + ci0, n0);
-                    issued++;
+                    for (int ci0 = 0; ci0 < Cin; ci0 += KC) {
+                        const int s = issued % S, u = issued / S;
+                        if (u > 0 && !mbar_wait(cv_smem_u32(&empty[s]), (unsigned)((u - 1) & 1), limit, abort)) {
+                            ok = false;
+                            break;
+                        }
+                        const unsigned fb = cv_smem_u32(&full[s]), a = ring + (unsigned)s * C::STAGE;
+                        mbar_expect_tx(fb, C::STAGE);
+                        tma_load_4d(a, &tm_in, fb, ci0, x0 + dx, y0 + dy, b);
+                        tma_load_2d(a + C::A_BYTES, &tm_w, fb, tap * Cin + ci0, n0);
+                        issued++;
+                    }
                 }
             }
             if (!ok) give_up(abort);
@@ -282,6 +315,7 @@ k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__
     } else if (warp == 1) {
         if (lane == 0) {
             const unsigned id = idesc_bf16(128, BN, false);
+            const uint64_t desc0 = sdesc_sw(ring, 16, 8 * C::ROW, C::SW);
             bool ok = true;
             int it = 0, tc = 0;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, tc++) {
@@ -299,11 +333,10 @@ k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__
                         break;
                     }
                     tc_fence_after();
-                    const unsigned a = ring + (unsigned)s * C::STAGE, bb = a + C::A_BYTES;
+                    const uint64_t ad = desc0 + (uint64_t)(((unsigned)s * C::STAGE) >> 4), bd = ad + (C::A_BYTES >> 4);
 #pragma unroll
                     for (int ks = 0; ks < KC / 16; ks++)
-                        mma_bf16(d, sdesc_sw(a + ks * 32, 16, 8 * C::ROW, C::SW),
-                                 sdesc_sw(bb + ks * 32, 16, 8 * C::ROW, C::SW), id, (kt > 0 || ks > 0) ? 1u : 0u);
+                        mma_bf16(d, ad + 2 * ks, bd + 2 * ks, id, (kt > 0 || ks > 0) ? 1u : 0u);
                     mma_commit(cv_smem_u32(&empty[s]));  // the stage is free once these MMAs are done
                 }
                 if (!ok) break;
@@ -328,29 +361,8 @@ k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__
             const int mt = t / nnt, n0 = (t - mt * nnt) * BN;
             int b, y0, x0;
             patch_of(mt, ntx, nty, bx, by, b, y0, x0);
-            const int x = x0 + (m & (bx - 1)), y = y0 + m / bx;  // bx: a power of two
-            const bool v = x < Wd && y < H;
-            bf16 *dst = out + ((int64_t)(b * H + y) * Wd + x) * out_cs + out_c0 + n0;
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                unsigned r[16];
-                tmem_ld16(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(acc * BN + c0), r);
-                if (v) {
-                    __align__(16) __nv_bfloat162 h[8];
-#pragma unroll
-                    for (int j = 0; j < 8; j++) {
-                        float v0 = __uint_as_float(r[2 * j]) + (bias ? bias[n0 + c0 + 2 * j] : 0.0f);
-                        float v1 = __uint_as_float(r[2 * j + 1]) + (bias ? bias[n0 + c0 + 2 * j + 1] : 0.0f);
-                        if (relu) {
-                            v0 = fmaxf(v0, 0.0f);
-                            v1 = fmaxf(v1, 0.0f);
-                        }
-                        h[j] = __floats2bfloat162_rn(v0, v1);
-                    }
-                    uint4 *o = (uint4 *)(dst + c0);
-                    o[0] = *(const uint4 *)&h[0];
-                    o[1] = *(const uint4 *)&h[4];
-                }
-            }
+            fwd_store_row<BN>(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(acc * BN), out, out_cs, out_c0, n0, bias,
+                              relu, b, x0 + (m & (bx - 1)), y0 + m / bx, H, Wd);  // bx: a power of two
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(cv_smem_u32(&tempty[acc]));  // the accumulator may be overwritten
@@ -365,6 +377,176 @@ k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__
                 mbar_wait_plain(cv_smem_u32(&full[j % S]), (unsigned)((j / S) & 1), TC_WAIT);
         if (tid == 32) {
             mma_commit(cv_smem_u32(&drain));  // arrives once every MMA issued so far is done
+            mbar_wait_plain(cv_smem_u32(&drain), 0u, TC_WAIT);
+        }
+        __syncthreads();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        tmem_free(tmem, 2 * BN);
+    }
+}
+
+// -------------------------------------------- conv forward, halo variant
+//
+// For 3x3 convolutions whose weight block (BN output channels x 9 taps x
+// Cin) fits in shared memory beside the ring: the CTA loads it once and
+// keeps it; per K chunk of KC input channels a stage holds the tile's input
+// with its halo as three copies, one per horizontal tap offset dx, each
+// bx x (by + 2) pixels from (x0 + dx, y0 - 1). The MMAs of tap (dy, dx) read
+// the copy dx from row (dy + 1) bx on: pixel (c, r) of the tile is then row
+// (r + dy + 1) bx + c, and as bx is a multiple of 8 every operand starts on
+// a swizzle-pattern boundary. A stage is 3 bx (by + 2) rows instead of the
+// 9 x 128 rows of one copy per tap. CTA i serves output-channel tile
+// i % nnt and every (grid / nnt)-th pixel patch.
+
+constexpr int HL_MAXST = 4;
+
+template <int BN, int KC>
+__global__ void __launch_bounds__(FW_THREADS, 1)
+k_conv_fwd_halo(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_w,
+                const float *__restrict__ bias, bf16 *__restrict__ out, int out_cs, int out_c0, int Cout, int Cin,
+                int B, int H, int Wd, int relu, int bx, int by, int ntx, int nty, int S)
+{
+    constexpr unsigned ROW = KC * 2, SW = KC == 64 ? 2u : 4u, WBLK = BN * ROW;
+    extern __shared__ unsigned char hl_smem[];
+    __shared__ __align__(8) uint64_t full[HL_MAXST], empty[HL_MAXST], tfull[2], tempty[2], wfull, drain;
+    __shared__ unsigned tbase;
+    __shared__ int s_abort;
+    volatile int *abort = &s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) s_abort = 0;
+    const int nch = Cin / KC;
+    const unsigned wres = (cv_smem_u32(hl_smem) + 1023u) & ~1023u;  // resident weights
+    const unsigned dxbuf = (unsigned)(bx * (by + 2)) * ROW, abytes = 3 * dxbuf;
+    const unsigned ring = wres + 9u * (unsigned)nch * WBLK;
+    if (warp == 0) tmem_alloc(&tbase, 2 * BN);
+    if (tid == 32) {
+        for (int q = 0; q < S; q++) {
+            mbar_init(cv_smem_u32(&full[q]), 1);
+            mbar_init(cv_smem_u32(&empty[q]), 1);
+        }
+        for (int a = 0; a < 2; a++) {
+            mbar_init(cv_smem_u32(&tfull[a]), 1);
+            mbar_init(cv_smem_u32(&tempty[a]), 4);
+        }
+        mbar_init(cv_smem_u32(&wfull), 1);
+        mbar_init(cv_smem_u32(&drain), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = tbase;
+    const int nnt = Cout / BN, n0 = (blockIdx.x % nnt) * BN;
+    const int mt0 = blockIdx.x / nnt, mstep = gridDim.x / nnt, nmt = ntx * nty * B;
+    const int limit = g_conv_wait_limit;
+    int issued = 0;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tma_prefetch(&tm_in);
+            tma_prefetch(&tm_w);
+            const unsigned wb = cv_smem_u32(&wfull);
+            mbar_expect_tx(wb, 9u * (unsigned)nch * WBLK);
+            for (int tap = 0; tap < 9; tap++)
+                for (int ch = 0; ch < nch; ch++)
+                    tma_load_2d(wres + (unsigned)(tap * nch + ch) * WBLK, &tm_w, wb, tap * Cin + ch * KC, n0);
+            bool ok = true;
+            for (int mt = mt0; mt < nmt && ok; mt += mstep) {
+                int b, y0, x0;
+                patch_of(mt, ntx, nty, bx, by, b, y0, x0);
+                for (int ch = 0; ch < nch; ch++) {
+                    const int s = issued % S, u = issued / S;
+                    if (u > 0 && !mbar_wait(cv_smem_u32(&empty[s]), (unsigned)((u - 1) & 1), limit, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    const unsigned fb = cv_smem_u32(&full[s]), a = ring + (unsigned)s * abytes;
+                    mbar_expect_tx(fb, abytes);
+#pragma unroll
+                    for (int dx = -1; dx <= 1; dx++)
+                        tma_load_4d(a + (unsigned)(dx + 1) * dxbuf, &tm_in, fb, ch * KC, x0 + dx, y0 - 1, b);
+                    issued++;
+                }
+            }
+            if (!ok) give_up(abort);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const unsigned id = idesc_bf16(128, BN, false);
+            const uint64_t adesc0 = sdesc_sw(ring, 16, 8 * ROW, SW), wdesc0 = sdesc_sw(wres, 16, 8 * ROW, SW);
+            const unsigned dxq = dxbuf >> 4, rq = ((unsigned)bx * ROW) >> 4;  // tap offsets, 16-byte units
+            const unsigned wq = WBLK >> 4, tq = (unsigned)nch * wq;
+            bool ok = mbar_wait(cv_smem_u32(&wfull), 0u, limit, abort);
+            int it = 0, tc = 0;
+            for (int mt = mt0; mt < nmt && ok; mt += mstep, tc++) {
+                const int acc = tc & 1, ua = tc >> 1;
+                if (ua > 0 && !mbar_wait(cv_smem_u32(&tempty[acc]), (unsigned)((ua - 1) & 1), limit, abort)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const unsigned d = tmem + (unsigned)(acc * BN);
+                for (int ch = 0; ch < nch; ch++, it++) {
+                    const int s = it % S, u = it / S;
+                    if (!mbar_wait(cv_smem_u32(&full[s]), (unsigned)(u & 1), limit, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    // descriptors as 64-bit values; offsets add to the address
+                    // field (16-byte units, addresses below 256 KB)
+                    const uint64_t ad = adesc0 + (uint64_t)(((unsigned)s * abytes) >> 4);
+                    const uint64_t bd = wdesc0 + (uint64_t)(ch * wq);
+#pragma unroll
+                    for (int tap = 0; tap < 9; tap++) {  // tap = (dy + 1) * 3 + dx + 1
+                        const uint64_t at = ad + (uint64_t)((tap % 3) * dxq + (tap / 3) * rq);
+                        const uint64_t bt = bd + (uint64_t)(tap * tq);
+#pragma unroll
+                        for (int ks = 0; ks < KC / 16; ks++)
+                            mma_bf16(d, at + 2 * ks, bt + 2 * ks, id, (tap > 0 || ks > 0 || ch > 0) ? 1u : 0u);
+                    }
+                    mma_commit(cv_smem_u32(&empty[s]));
+                }
+                if (!ok) break;
+                mma_commit(cv_smem_u32(&tfull[acc]));
+            }
+            if (!ok) give_up(abort);
+        }
+    } else {
+        const int q = warp & 3, m = 32 * q + lane;
+        int tc = 0;
+        for (int mt = mt0; mt < nmt; mt += mstep, tc++) {
+            const int acc = tc & 1, ua = tc >> 1;
+            int ok = 1;
+            if (lane == 0) ok = mbar_wait(cv_smem_u32(&tfull[acc]), (unsigned)(ua & 1), limit, abort);
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0) give_up(abort);
+                break;
+            }
+            tc_fence_after();
+            int b, y0, x0;
+            patch_of(mt, ntx, nty, bx, by, b, y0, x0);
+            fwd_store_row<BN>(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(acc * BN), out, out_cs, out_c0, n0, bias,
+                              relu, b, x0 + (m & (bx - 1)), y0 + m / bx, H, Wd);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(cv_smem_u32(&tempty[acc]));
+        }
+    }
+    __syncthreads();
+    if (s_abort) {
+        if (tid == 0) {
+            mbar_wait_plain(cv_smem_u32(&wfull), 0u, TC_WAIT);
+            for (int j = issued > S ? issued - S : 0; j < issued; j++)
+                mbar_wait_plain(cv_smem_u32(&full[j % S]), (unsigned)((j / S) & 1), TC_WAIT);
+        }
+        if (tid == 32) {
+            mma_commit(cv_smem_u32(&drain));
             mbar_wait_plain(cv_smem_u32(&drain), 0u, TC_WAIT);
         }
         __syncthreads();
@@ -411,9 +593,7 @@ k_conv_wgrad_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant
     __shared__ int s_abort;
     volatile int *abort = &s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (tid == 0) s_abort = *(volatile int *)&g_conv_timeout;  // an earlier CTA gave up
-    __syncthreads();
-    if (s_abort) return;
+    if (tid == 0) s_abort = 0;
     const unsigned ring = (cv_smem_u32(wg_smem) + 1023u) & ~1023u;
     const int K = taps * Cin, kk0 = blockIdx.x * 128, n0 = blockIdx.y * BN;
     const int p0 = blockIdx.z * per_split, p1 = min(npatch, p0 + per_split), KT = p1 > p0 ? p1 - p0 : 0;
@@ -439,28 +619,48 @@ k_conv_wgrad_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant
         tma_prefetch(&tm_in);
         tma_prefetch(&tm_g);
         const unsigned bytes = (unsigned)nA * C::A_BOX + C::B_BYTES;
+        // the tile's A boxes: input channel chunk and tap shift, the same for
+        // every patch (at most 128 / KCA of them)
+        int bci[128 / KCA], bdx[128 / KCA], bdy[128 / KCA];
+#pragma unroll
+        for (int r = 0; r < 128 / KCA; r++) {
+            const int kk = kk0 + r * KCA, tap = kk / Cin;
+            bci[r] = kk - tap * Cin;
+            bdy[r] = taps == 9 ? tap / 3 - 1 : 0;
+            bdx[r] = taps == 9 ? tap % 3 - 1 : 0;
+        }
+        int b, y0, x0;  // the current patch, advanced in patch order
+        patch_of(p0, ntx, nty, bx, by, b, y0, x0);
+        const int xe = ntx * bx, ye = nty * by;
         for (int kt = 0; kt < KT; kt++) {
             const int s = kt % S, u = kt / S;
             if (u > 0 && !mbar_wait(cv_smem_u32(&empty[s]), (unsigned)((u - 1) & 1), limit, abort)) {
                 give_up(abort);
                 break;
             }
-            int b, y0, x0;
-            patch_of(p0 + kt, ntx, nty, bx, by, b, y0, x0);
             const unsigned fb = cv_smem_u32(&full[s]), a = ring + (unsigned)s * C::STAGE;
             mbar_expect_tx(fb, bytes);
-            for (int r = 0; r < nA; r++) {
-                const int kk = kk0 + r * KCA, tap = kk / Cin, ci0 = kk - tap * Cin;
-                const int dy = taps == 9 ? tap / 3 - 1 : 0, dx = taps == 9 ? tap % 3 - 1 : 0;
-                tma_load_4d(a + (unsigned)r * C::A_BOX, &tm_in, fb, ci0, x0 + dx, y0 + dy, b);
-            }
+#pragma unroll
+            for (int r = 0; r < 128 / KCA; r++)
+                if (r < nA) tma_load_4d(a + (unsigned)r * C::A_BOX, &tm_in, fb, bci[r], x0 + bdx[r], y0 + bdy[r], b);
 #pragma unroll
             for (int j = 0; j < BN / KCB; j++)
                 tma_load_4d(a + C::A_BYTES + (unsigned)j * C::B_BOX, &tm_g, fb, n0 + j * KCB, x0, y0, b);
             issued++;
+            x0 += bx;
+            if (x0 >= xe) {
+                x0 = 0;
+                y0 += by;
+                if (y0 >= ye) {
+                    y0 = 0;
+                    b++;
+                }
+            }
         }
     } else if (tid == 32) {
         const unsigned id = idesc_bf16(128, BN, true);
+        const uint64_t adesc0 = sdesc_sw(ring, C::A_BOX, 8 * C::A_ROW, C::A_SW);
+        const uint64_t bdesc0 = sdesc_sw(ring + C::A_BYTES, C::B_BOX, 8 * C::B_ROW, C::B_SW);
         bool ok = true;
         for (int kt = 0; kt < KT; kt++) {
             const int s = kt % S, u = kt / S;
@@ -469,12 +669,11 @@ k_conv_wgrad_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant
                 break;
             }
             tc_fence_after();
-            const unsigned a = ring + (unsigned)s * C::STAGE, bb = a + C::A_BYTES;
+            const uint64_t ad = adesc0 + (uint64_t)(((unsigned)s * C::STAGE) >> 4);
+            const uint64_t bd = bdesc0 + (uint64_t)(((unsigned)s * C::STAGE) >> 4);
 #pragma unroll
             for (int ks = 0; ks < WG_PIX / 16; ks++)  // 16 pixels = two 8-row groups per MMA
-                mma_bf16(tmem, sdesc_sw(a + ks * 16 * C::A_ROW, C::A_BOX, 8 * C::A_ROW, C::A_SW),
-                         sdesc_sw(bb + ks * 16 * C::B_ROW, C::B_BOX, 8 * C::B_ROW, C::B_SW), id,
-                         (kt > 0 || ks > 0) ? 1u : 0u);
+                mma_bf16(tmem, ad + ks * (C::A_ROW), bd + ks * (C::B_ROW), id, (kt > 0 || ks > 0) ? 1u : 0u);
             mma_commit(cv_smem_u32(&empty[s]));
         }
         if (ok) mma_commit(cv_smem_u32(&done));
@@ -527,25 +726,48 @@ k_conv_wgrad_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant
     }
 }
 
-// out[i] = sum over splits s (in order) of part[s][i]
+// out[i] = sum over splits s (in order) of part[s][i]; eight loads in
+// flight, added in split order
 __global__ void k_conv_fold(const float *__restrict__ part, int64_t n, int splits, float *__restrict__ out)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float s = 0.0f;
-    for (int q = 0; q < splits; q++) s += part[(int64_t)q * n + i];
+    int q = 0;
+    for (; q + 8 <= splits; q += 8) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) v[j] = part[(int64_t)(q + j) * n + i];
+#pragma unroll
+        for (int j = 0; j < 8; j++) s += v[j];
+    }
+    for (; q < splits; q++) s += part[(int64_t)q * n + i];
     out[i] = s;
 }
 
-// per-split column sums of grad (the bias gradient): part[split][c]
-__global__ void k_conv_bias_part(const bf16 *__restrict__ grad, int g_cs, int C, int M, int pix_per_split,
-                                 float *__restrict__ part)
+// Per-split column sums of grad (the bias gradient): part[split][c]. The
+// block's 256 threads take channel c = t % C and every (256 / C)-th pixel
+// of the split from t / C on; the partial sums are added in that order.
+__global__ void __launch_bounds__(256) k_conv_bias_part(const bf16 *__restrict__ grad, int g_cs, int C, int M,
+                                                        int pix_per_split, float *__restrict__ part)
 {
+    __shared__ float red[256];
     const int p0 = blockIdx.x * pix_per_split, p1 = min(M, p0 + pix_per_split);
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    const int t = threadIdx.x;
+    const int lanes = C < 256 ? 256 / C : 1;  // threads per channel
+    for (int cb = 0; cb < C; cb += 256 / lanes) {
+        const int c = cb + t % (256 / lanes), sub = t / (256 / lanes);
         float s = 0.0f;
-        for (int p = p0; p < p1; p++) s += __bfloat162float(grad[(int64_t)p * g_cs + c]);
-        part[(int64_t)blockIdx.x * C + c] = s;
+        if (c < C)
+            for (int p = p0 + sub; p < p1; p += lanes) s += __bfloat162float(grad[(int64_t)p * g_cs + c]);
+        red[t] = s;
+        __syncthreads();
+        if (sub == 0 && c < C) {
+            float r = red[t];
+            for (int j = 1; j < lanes; j++) r += red[t + j * (256 / lanes)];
+            part[(int64_t)blockIdx.x * C + c] = r;
+        }
+        __syncthreads();
     }
 }
 
@@ -652,6 +874,43 @@ static cudaError_t launch_fwd(const CUtensorMap &ti, const CUtensorMap &tw, cons
     return cudaGetLastError();
 }
 
+// Shared memory of the halo variant: resident weights + stages (0: does not
+// fit with two stages).
+static unsigned halo_smem(int Cin, int BN, int KC, int bx, int by, int &S)
+{
+    const unsigned budget = 227u * 1024u - 1024u - 256u;  // less alignment slack and static barriers
+    const unsigned wbytes = 9u * (unsigned)(Cin / KC) * (unsigned)(BN * KC * 2);
+    const unsigned abytes = 3u * (unsigned)(bx * (by + 2) * KC * 2);
+    if (wbytes + 2 * abytes > budget) return 0;
+    S = (int)std::min<unsigned>(HL_MAXST, (budget - wbytes) / abytes);
+    return 1024u + wbytes + (unsigned)S * abytes;
+}
+
+template <int BN, int KC>
+static cudaError_t launch_halo(const bf16 *in, int in_cs, int in_c0, int Cin, const bf16 *W, const float *bias,
+                               bf16 *out, int out_cs, int out_c0, int Cout, int B, int H, int Wd, int relu, int bx,
+                               int by, unsigned smem, int S, cudaStream_t st)
+{
+    static unsigned attr = 0;  // per instance: the largest dynamic shared memory configured
+    if (smem > attr) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_conv_fwd_halo<BN, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    const int ntx = (Wd + bx - 1) / bx, nty = (H + by - 1) / by;
+    const int64_t nmt = (int64_t)ntx * nty * B;
+    const int nnt = Cout / BN;
+    const int per = (int)std::min<int64_t>(nmt, std::max(1, sm_count() / nnt));
+    CUtensorMap ti, tw;
+    cudaError_t e = act_map(&ti, in + in_c0, Cin, in_cs, B, H, Wd, KC, bx, by + 2);
+    if (e == cudaSuccess) e = weight_map(&tw, W, 9 * Cin, Cout, KC, BN);
+    if (e != cudaSuccess) return e;
+    k_conv_fwd_halo<BN, KC><<<nnt * per, FW_THREADS, smem, st>>>(ti, tw, bias, out, out_cs, out_c0, Cout, Cin, B, H,
+                                                                 Wd, relu, bx, by, ntx, nty, S);
+    return cudaGetLastError();
+}
+
 cudaError_t conv_fwd(const bf16 *in, int in_cs, int in_c0, int Cin, const bf16 *W, const float *bias, bf16 *out,
                      int out_cs, int out_c0, int Cout, int B, int H, int Wd, int taps, bool relu, cudaStream_t st)
 {
@@ -659,6 +918,25 @@ cudaError_t conv_fwd(const bf16 *in, int in_cs, int in_c0, int Cin, const bf16 *
         return cudaErrorInvalidValue;
     if ((int64_t)B * H * Wd == 0) return cudaSuccess;
     const int KC = Cin % 64 == 0 ? 64 : 32, BN = tile_n(Cout);
+    if (taps == 9 && BN <= 64) {  // the halo variant where its weight block fits
+        const int hbx = Wd > 8 ? 16 : 8, hby = 128 / hbx;
+        int S = 0;
+        const unsigned smem = halo_smem(Cin, BN, KC, hbx, hby, S);
+        if (smem && (int64_t)((Wd + hbx - 1) / hbx) * ((H + hby - 1) / hby) * B <= INT32_MAX) {
+            const int r = relu ? 1 : 0;
+            if (BN == 64 && KC == 64)
+                return launch_halo<64, 64>(in, in_cs, in_c0, Cin, W, bias, out, out_cs, out_c0, Cout, B, H, Wd, r, hbx,
+                                           hby, smem, S, st);
+            if (BN == 32 && KC == 64)
+                return launch_halo<32, 64>(in, in_cs, in_c0, Cin, W, bias, out, out_cs, out_c0, Cout, B, H, Wd, r, hbx,
+                                           hby, smem, S, st);
+            if (BN == 64 && KC == 32)
+                return launch_halo<64, 32>(in, in_cs, in_c0, Cin, W, bias, out, out_cs, out_c0, Cout, B, H, Wd, r, hbx,
+                                           hby, smem, S, st);
+            return launch_halo<32, 32>(in, in_cs, in_c0, Cin, W, bias, out, out_cs, out_c0, Cout, B, H, Wd, r, hbx,
+                                       hby, smem, S, st);
+        }
+    }
     int bx, by;
     patch_shape(Wd, 128, bx, by);
     const int ntx = (Wd + bx - 1) / bx, nty = (H + by - 1) / by;
