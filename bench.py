@@ -102,18 +102,18 @@ def algorithmic_bytes(n, m, dim):
     return n * 32 * dim + 10 * m
 
 
-# DRAM traffic of one time-step launch of the fused 2D tile kernel on the
+# DRAM traffic of one time-step launch of each mode's 2D kernel on the
 # 2048 x 2048 workload, from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by precision mode, with the sha1 prefix of the kernel source it was
 # taken on; once the kernel changes, traffic reports null until re-measured.
 NCU_TRAFFIC = {
-    # profiles/k_strip2d_df64_2d_2048_two_phase.md and ncu --metrics
-    # dram__bytes_read.sum,dram__bytes_write.sum on one time-step launch of
-    # each mode (the same 2048 x 2048 workload)
-    "df64": (238.4e6, "c2b3cbe44956"),
-    "f32": (239.9e6, "c2b3cbe44956"),
-    "fast64": (236.0e6, "c2b3cbe44956"),
-    "exact64": (236.6e6, "c2b3cbe44956"),
+    # profiles/time_step_per_mode_2d_2048_two_phase.md: ncu --metrics
+    # dram__bytes_read.sum,dram__bytes_write.sum on three time-step launches
+    # of each mode (the same 2048 x 2048 workload), mean
+    "df64": (238.3e6, "1fd3ea8b6336"),
+    "f32": (239.9e6, "1fd3ea8b6336"),
+    "fast64": (236.2e6, "1fd3ea8b6336"),
+    "exact64": (236.7e6, "1fd3ea8b6336"),
 }
 
 # Warp instructions executed by one time-step launch (ncu smsp__inst_executed.sum,
@@ -122,17 +122,17 @@ NCU_TRAFFIC = {
 # this gives the instruction-issue roofline, the one the fixed-point modes
 # are bound by.
 NCU_INSTRUCTIONS = {
-    "df64": (136150237, "c2b3cbe44956"),
-    "f32": (80702847, "c2b3cbe44956"),
-    "fast64": (94464248, "c2b3cbe44956"),
-    "exact64": (195597796, "c2b3cbe44956"),
+    "df64": (118713091, "1fd3ea8b6336"),
+    "f32": (78677658, "1fd3ea8b6336"),
+    "fast64": (94464248, "1fd3ea8b6336"),
+    "exact64": (195572908, "1fd3ea8b6336"),
 }
 
 # Binding unit of each mode's time-step kernel, from ncu on the same workload
 # (see the profile summaries), for the roofline's "limiter" note.
 LIMITER = {
-    "df64": "instruction issue (ncu: 75% of issue slots busy, FP64 pipe 40%, DRAM 20% of peak)",
-    "f32": "instruction issue (ncu: 71% of issue slots busy, FP64 pipe 48%, DRAM 30% of peak)",
+    "df64": "instruction issue (ncu: 74% of issue slots busy, FP64 pipe 45%, DRAM 22% of peak)",
+    "f32": "instruction issue (ncu: 72% of issue slots busy, FP64 pipe 50%, DRAM 32% of peak)",
     "fast64": "FP64 pipe (ncu: 86% busy)",
     "exact64": "FP64 pipe (ncu: 88% busy; correctly rounded sqrt and divide)",
 }

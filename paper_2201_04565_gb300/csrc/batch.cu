@@ -382,7 +382,6 @@ static TileArgs batch_base_args(BatchCtx &b)
     A.grip_mode = b.grip_mode;
     A.S = b.fix_S;
     A.a_fix = b.a_fix;
-    A.p48 = ldexpf(1.0f, 48 - b.fix_S);
     A.p24 = ldexpf(1.0f, 24 - b.fix_S);
     A.p0 = ldexpf(1.0f, -b.fix_S);
     A.status = b.status;
@@ -509,6 +508,7 @@ static cudaError_t batch_upload(BatchCtx &b, const std::vector<HostNet> &nets, c
     for (int s = 0; s < S; s++) maxext = std::max(maxext, std::max(b.nx[s], b.ny[s]));
     const double extent = 4.0 * maxext * b.a + 16.0;
     b.fix_S = std::min(61 - (int)std::ceil(std::log2(extent)), 47 - (int)std::ceil(std::log2(b.a * std::sqrt(2.0))));
+    b.fix_S = std::min(b.fix_S, 47 - (int)std::floor(std::log2(max_critical_length(h0.types))));
     b.a_fix = std::llround(std::ldexp(b.a, b.fix_S));
     for (int q = 0; q < 2; q++) {
         BT_TRY(balloc(&b.X[q], 2 * NP));

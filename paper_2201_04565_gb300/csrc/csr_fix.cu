@@ -29,7 +29,7 @@ struct FixTab {
     ff of[9][3];        // o as double-floats
     ff oo[9];           // |o|^2
     int S;
-    float p48, p24, p0;
+    float p24, p0;
 };
 
 namespace {
@@ -125,7 +125,7 @@ k_springs_fix(int64_t m, int64_t n, const int32_t *__restrict__ si, const int32_
             // and the force k (1 - r0 / r) d (the tile kernels' arithmetic)
             ff d[DIM];
 #pragma unroll
-            for (int c = 0; c < DIM; c++) d[c] = fix_to_ff_i2f2(xf[c * n + j] - xf[c * n + i], T.p48, T.p24, T.p0);
+            for (int c = 0; c < DIM; c++) d[c] = fix_to_ff_i2f2(xf[c * n + j] - xf[c * n + i], T.p24, T.p0);
             ff r2 = ff_norm2(d[0], d[1]);
             if constexpr (DIM == 3) r2 = ff_add_sloppy(r2, ff_sqr(d[2]));
             if (BREAK && ff_gt(r2, t.rc2)) {
@@ -277,7 +277,6 @@ static FixTab fix_tab(const Ctx &c)
 {
     FixTab T{};
     T.S = c.fix_S;
-    T.p48 = ldexpf(1.0f, 48 - c.fix_S);
     T.p24 = ldexpf(1.0f, 24 - c.fix_S);
     T.p0 = ldexpf(1.0f, -c.fix_S);
     const int no = (int)c.h.offv.size() / 3;

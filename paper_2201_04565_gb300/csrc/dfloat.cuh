@@ -221,31 +221,20 @@ __device__ __forceinline__ ff ff_sqrt(ff a)
     return fast_two_sum(x, __fmul_rn(d.hi, __fmul_rn(0.5f, y)));
 }
 
-// v * 2^-S as a double-float from three exact 24-bit chunks
-// (p48 = 2^(48-S), p24 = 2^(24-S), p0 = 2^-S); |v| < 2^63.
-__device__ __forceinline__ ff fix_to_ff_i2f(long long v, float p48, float p24, float p0)
+// v * 2^-S as a double-float from two 24-bit chunks, v = h 2^24 + l with
+// h = floor(v / 2^24) and 0 <= l < 2^24. For |v| < 2^48 both chunks convert
+// exactly and do not overlap, so Fast2Sum returns RN(v 2^-S) and the exact
+// remainder. Up to |v| < 2^55 the result is v rounded to about 2^-24
+// relative (h rounds); beyond, h wraps. The callers choose S so that every
+// spring that can still be intact (length up to its critical length) has
+// |v| < 2^48, and a vector that rounds here is longer than every critical
+// length, so the break test decides it the same way.
+__device__ __forceinline__ ff fix_to_ff_i2f2(long long v, float p24, float p0)
 {
-    const float a = __fmul_rn(__int2float_rn((int)(v >> 48)), p48);
-    const float b = __fmul_rn(__int2float_rn((int)((v >> 24) & 0xFFFFFFLL)), p24);
-    const float c = __fmul_rn(__int2float_rn((int)(v & 0xFFFFFFLL)), p0);
-    const ff s = two_sum(a, b);
-    return fast_two_sum(s.hi, __fadd_rn(s.lo, c));
-}
-
-// Same value as fix_to_ff_i2f; |v| < 2^47 (the common case for spring
-// deviations) takes two 24-bit chunks, whose float sum Fast2Sum represents
-// exactly because the chunks do not overlap.
-__device__ __forceinline__ ff fix_to_ff_i2f2(long long v, float p48, float p24, float p0)
-{
-    // |v| < 2^47 <=> the high word lies in [-2^15, 2^15)
-    const int hw = (int)(v >> 32);
-    if ((unsigned)(hw + 0x8000) < 0x10000u) {
-        const int h = (int)__funnelshift_r((unsigned)v, (unsigned)hw, 24);  // v >> 24, 24 significant bits
-        const float a = __fmul_rn(__int2float_rn(h), p24);
-        const float b = __fmul_rn(__int2float_rn((int)((unsigned)v & 0xFFFFFFu)), p0);
-        return fast_two_sum(a, b);
-    }
-    return fix_to_ff_i2f(v, p48, p24, p0);
+    const int h = (int)__funnelshift_r((unsigned)v, (unsigned)(v >> 32), 24);  // v >> 24
+    const float a = __fmul_rn(__int2float_rn(h), p24);
+    const float b = __fmul_rn(__int2float_rn((int)((unsigned)v & 0xFFFFFFu)), p0);
+    return fast_two_sum(a, b);
 }
 
 // a^2 for a double-float a.
@@ -282,26 +271,29 @@ __device__ __forceinline__ ff ff_norm2(ff a, ff b)
 }
 
 // The spring factor g = 1 - r0 / r from r^2 (double-float) and r0, with
-// y = 1/r to about 2^-46: the float reciprocal square root y0 (one float
-// Newton step), the residual rho = 1 - r^2 y0^2, and r0 / r = r0 y0 (1 +
-// rho / 2). With y0^2 = q + qe exactly (TwoProd), rho is three fused
-// multiply-adds: 1 - r2.hi q is formed exactly before its one rounding
-// (r2.hi q lies within a few float ulps of 1, so about 26 significant bits
-// survive the cancellation), then the terms r2.hi qe and r2.lo q of order
-// 2^-24 follow (r2.lo qe, below 2^-47, is dropped). The product r0.hi y0 is
-// exact (TwoProd), so 1 - r0 y0 is exact up to the small terms summed in
-// float. *y receives 1/r.
+// y = 1/r to about 2^-45: the hardware reciprocal square root estimate y0
+// (relative error below 2^-22.9), the residual rho = 1 - r^2 y0^2, and one
+// double-float Newton step, r0 / r = r0 y0 (1 + rho / 2), whose neglected
+// term 3/8 rho^2 stays near 2^-45.2. With y0^2 = q + qe exactly (TwoProd),
+// rho is three fused multiply-adds: 1 - r2.hi q is formed exactly before
+// its one rounding (r2.hi q lies within about 2^-21.9 of 1), then the terms
+// r2.hi qe and r2.lo q of order 2^-24 follow (r2.lo qe, below 2^-47, is
+// dropped). The product r0.hi y0 = p is exact (TwoProd), so 1 - r0 y0 is
+// exact up to the small terms summed in float. 1 - p.hi needs no TwoSum:
+// Fast2Sum(1, -p.hi) is exact for every 0 < p.hi < 2^24, by Dekker's
+// condition for p.hi <= 1, and above 1 because 1 - p.hi is then a multiple
+// of ulp(p.hi) below 2^24 ulp(p.hi), so the subtraction is exact and the
+// error term 0. *y receives 1/r.
 __device__ __forceinline__ ff ff_spring_g(ff r2, ff r0, ff *y)
 {
-    float y0 = rsqrt_approx(r2.hi);
-    y0 = __fmul_rn(y0, __fmaf_rn(-0.5f * r2.hi, __fmul_rn(y0, y0), 1.5f));
+    const float y0 = rsqrt_approx(r2.hi);
     const ff q = two_prod(y0, y0);
     const float rho =
         __fmaf_rn(-r2.lo, q.hi, __fmaf_rn(-r2.hi, q.lo, __fmaf_rn(-r2.hi, q.hi, 1.0f)));
     const ff p = two_prod(r0.hi, y0);
     float t2 = __fmaf_rn(-r0.lo, y0, -p.lo);
     t2 = __fmaf_rn(-0.5f * p.hi, rho, t2);
-    const ff s = two_sum(1.0f, -p.hi);
+    const ff s = fast_two_sum(1.0f, -p.hi);
     if (y) *y = fast_two_sum(y0, __fmul_rn(__fmul_rn(0.5f, y0), rho));
     return fast_two_sum(s.hi, __fadd_rn(s.lo, t2));
 }

@@ -513,12 +513,13 @@ static cudaError_t upload_tile(Ctx &c)
         itab[4 * q + 3] = hdt / m;
     }
     // fixed-point scale: |x| stays below 2^(62 - S) for strains up to +300%,
-    // and spring vectors up to 2 r0 of the diagonal spring (a sqrt 2) stay
-    // below 2^(48 - S), where their conversion to double-float takes the
-    // two-chunk path
+    // spring vectors up to 2 r0 of the diagonal spring (a sqrt 2) and up to
+    // every critical length stay below 2^(48 - S), where their conversion to
+    // double-float is exact
     const double extent = 4.0 * (double)(h.nx > h.ny ? h.nx : h.ny) * h.a + 16.0;
     c.fix_S = 61 - (int)std::ceil(std::log2(extent));
     c.fix_S = std::min(c.fix_S, 47 - (int)std::ceil(std::log2(h.a * std::sqrt(2.0))));
+    c.fix_S = std::min(c.fix_S, 47 - (int)std::floor(std::log2(max_critical_length(h.types))));
     c.a_fix = std::llround(std::ldexp(h.a, c.fix_S));
     c.h_fix = std::llround(std::ldexp(hrow, c.fix_S));
     std::vector<int64_t> sbase(np, 0);

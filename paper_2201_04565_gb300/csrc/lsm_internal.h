@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <cstdlib>
 #include <map>
 #include <string>
@@ -54,6 +55,17 @@ inline cudaError_t dev_malloc(T **p, size_t bytes)
 struct SpringType {
     double k, r0, rc2, kr0;
 };
+
+// The longest critical length rc = sqrt(rc2) of a type table (at least 1):
+// the fixed-point scale keeps every spring vector up to it exactly
+// convertible.
+inline double max_critical_length(const std::vector<SpringType> &types)
+{
+    double r = 1.0;
+    for (const SpringType &t : types)
+        if (t.rc2 > r * r) r = std::sqrt(t.rc2);
+    return r;
+}
 
 // A double-float: the unevaluated sum hi + lo of two floats.
 struct ff {

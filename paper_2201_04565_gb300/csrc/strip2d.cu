@@ -77,19 +77,21 @@ __device__ __forceinline__ ff shfl_ft<ff>(ff v, int src)
 // the phase (the state arrays cover every pixel) so that no load waits on
 // another. VOBS: the full-step velocity (initial acceleration, observation)
 // instead of the half-step one.
+// Pixel indices are 32-bit: the kernel runs on grids of fewer than 2^30
+// pixels (strip_supported), so that np + g fits too.
 template <bool VOBS = false>
 __device__ __forceinline__ PixRaw strip_fetch(const TileArgs &A, int gx, int gy)
 {
     PixRaw r{0.0, 0.0, 0.0, 0.0, 0u, 0u};
     if (gx < 0 || gx >= A.nx || gy < 0 || gy >= A.ny) return r;
-    const int64_t g = (int64_t)gy * A.nx + gx;
+    const int g = gy * A.nx + gx, gyc = (int)A.np + g;
     r.ph = A.phase[g];
     r.mk = A.mask[g];
     r.x = A.x_in[g];
-    r.y = A.x_in[A.np + g];
+    r.y = A.x_in[gyc];
     const double *v = VOBS ? A.v_obs : A.vh_in;
     r.vx = v[g];
-    r.vy = v[A.np + g];
+    r.vy = v[gyc];
     return r;
 }
 
@@ -109,7 +111,7 @@ __device__ __forceinline__ double site_X(const TileArgs &A, int gx, int par)
 // a grip (first or last site of its row, row length C) keeps its x, or
 // follows the constant strain rate.
 template <bool RATE, bool SAMPLE, int LAT, int MODE>
-__device__ __forceinline__ PixFix strip_make(const TileArgs &A, const PixRaw &r, int gx, int par, int C, int64_t g,
+__device__ __forceinline__ PixFix strip_make(const TileArgs &A, const PixRaw &r, int gx, int par, int C, int g,
                                              bool own, bool &over, bool &bad)
 {
     PixFix p{0, 0, 0u};
@@ -128,7 +130,7 @@ __device__ __forceinline__ PixFix strip_make(const TileArgs &A, const PixRaw &r,
     }
     if (MODE == T_STEP && own) {
         A.x_out[g] = px;
-        A.x_out[A.np + g] = py;
+        A.x_out[(int)A.np + g] = py;
         if (SAMPLE) bad |= !dbl_finite_bits(px) || !dbl_finite_bits(py);
     }
     p.xf = dbl_to_fix(px, A.S, over);
@@ -284,6 +286,15 @@ k_strip2d(TileArgs A, int R, int nsx)
     raw = strip_fetch<VOBS>(A, gx, y0);
     double vcx = 0.0, vcy = 0.0;
     FT p1x{}, p1y{}, p2x{}, p2y{}, p3x{}, p3y{};  // previous row's forces (slots 1..3)
+    // square lattice: the slot-0 target (gx + 1, y) is the previous row's
+    // slot-3 target (gx + 1, (y - 1) + 1), kept from its shuffle (not in the
+    // sample step, whose sums need the registers)
+    constexpr bool CARRY = LAT == 0 && !SAMPLE;
+    PixFix q0n;
+    if constexpr (CARRY) {
+        q0n = shfl_pix(P, lane + 1);
+        if (lane == 31) q0n.pm = 0u;
+    }
 
     for (int y = y0 - 1; y < y1; y++) {
         const bool own = y >= y0;  // warp-uniform
@@ -291,14 +302,19 @@ k_strip2d(TileArgs A, int R, int nsx)
         // 1. row y + 1 (fetched last iteration), then fetch row y + 2
         const double vnx = raw.vx, vny = raw.vy;
         const PixFix N = strip_make<RATE, SAMPLE, LAT, MODE>(A, raw, gx, par ^ 1, row_len(y + 1),
-                                                             (int64_t)(y + 1) * A.nx + gx, owner && y + 1 < y1,
+                                                             (y + 1) * A.nx + gx, owner && y + 1 < y1,
                                                              over, bad);
         raw = strip_fetch<VOBS>(A, gx, y + 2 <= y1 ? y + 2 : -1);
 
         // 2. the forward springs of row y; the shuffles that wrap around the
         // warp (lane 31's right and lane 0's left neighbour) carry no particle
-        PixFix q0 = shfl_pix(P, lane + 1);
-        if (lane == 31) q0.pm = 0u;
+        PixFix q0;
+        if constexpr (CARRY) {
+            q0 = q0n;
+        } else {
+            q0 = shfl_pix(P, lane + 1);
+            if (lane == 31) q0.pm = 0u;
+        }
         PixFix q1, q3;
         if constexpr (LAT == 0) {
             q1 = shfl_pix(N, lane - 1);
@@ -417,7 +433,7 @@ k_strip2d(TileArgs A, int R, int nsx)
                 Fx = ff{sx_, 0.0f};
             }
             if (owner && (P.pm & 0xffu)) {
-                const int64_t g = (int64_t)y * A.nx + gx;
+                const int g = y * A.nx + gx;
                 const int ph = (int)(P.pm & 0xffu) - 1;
                 const Coef4 k4 = scoef[ph];
                 const bool grip = gx == 0 || gx == row_len(y) - 1;
@@ -427,7 +443,7 @@ k_strip2d(TileArgs A, int R, int nsx)
                 const bool fixed[2] = {grip, fixy};
 #pragma unroll
                 for (int c = 0; c < 2; c++) {
-                    const int64_t q = c * A.np + g;
+                    const int q = c * (int)A.np + g;
                     if (fixed[c]) {
                         if (MODE == T_STEP) A.vh_out[q] = 0.0;
                         if (MODE == T_STEP && SAMPLE) A.v_obs[q] = 0.0;
@@ -479,6 +495,7 @@ k_strip2d(TileArgs A, int R, int nsx)
         p3x = f3x;
         p3y = f3y;
         P = N;
+        if constexpr (CARRY) q0n = q3;
         vcx = vnx;
         vcy = vny;
     }
@@ -503,23 +520,38 @@ k_strip2d(TileArgs A, int R, int nsx)
 
 namespace {
 
-// Warps of the time-step instance that fit on the device at once.
-template <int PREC, int LAT>
-cudaError_t strip_resident(int &resident)
+// Warps of a time-step kernel that fit on the device at once.
+template <typename Kern>
+cudaError_t kernel_resident(Kern k, int &cached, int &resident)
 {
-    static int cached = 0;  // per instance
     if (!cached) {
         int dev = 0, nsm = 0, nb = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_strip2d<PREC, false, false, LAT, T_STEP>,
-                                                              32 * STRIP_WARPS, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 32 * STRIP_WARPS, 0);
         if (e != cudaSuccess) return e;
         cached = std::max(1, nb * STRIP_WARPS * nsm);
     }
     resident = cached;
     return cudaSuccess;
+}
+
+template <int PREC, int LAT>
+cudaError_t strip_resident(int &resident)
+{
+    static int cached = 0;  // per instance
+    return kernel_resident(k_strip2d<PREC, false, false, LAT, T_STEP>, cached, resident);
+}
+
+// Strips of `own` columns and R rows, one wave of `resident` warps, at least
+// rmin rows each; fills: strips of 8 rows would outnumber the resident warps.
+void strip_shape(int nx, int ny, int own, int resident, int rmin, int &R, int &nsx, int64_t &nstrips, bool &fills)
+{
+    nsx = (nx + own - 1) / own;
+    const int rows_target = std::max(1, resident / nsx);
+    R = std::max(rmin, (ny + rows_target - 1) / rows_target);
+    nstrips = (int64_t)nsx * ((ny + R - 1) / R);
+    fills = (int64_t)nsx * ((ny + 7) / 8) >= resident;
 }
 
 template <int PREC, bool RATE, bool SAMPLE, int LAT, int MODE>
@@ -547,7 +579,8 @@ void launch_strip_step(Ctx &c, const TileArgs &A, bool sample)
 bool strip_supported(const Ctx &c)
 {
     return c.dim == 2 && (c.h.lattice == 0 || c.h.lattice == 1) &&
-           (c.h.precision == LSM_PREC_DF || c.h.precision == LSM_PREC_F32);
+           (c.h.precision == LSM_PREC_DF || c.h.precision == LSM_PREC_F32) &&
+           2 * (int64_t)c.h.nx * c.h.ny < ((int64_t)1 << 30);  // 32-bit indices (the packing has < 2 ny rows)
 }
 
 // Strip geometry: one warp per strip of 30 owned columns and R rows, as many
@@ -564,15 +597,9 @@ cudaError_t strip_geometry(Ctx &c, bool *fills)
     cudaError_t e = c.tri ? (df ? strip_resident<LSM_PREC_DF, 1>(resident) : strip_resident<LSM_PREC_F32, 1>(resident))
                           : (df ? strip_resident<LSM_PREC_DF, 0>(resident) : strip_resident<LSM_PREC_F32, 0>(resident));
     if (e != cudaSuccess) return e;
-    const int nsx = (c.tgnx + STRIP_OWN - 1) / STRIP_OWN;
-    const int rows_target = std::max(1, resident / nsx);
-    const int R = std::max(c.tri ? 2 : 8, (c.tgny + rows_target - 1) / rows_target);
-    const int nsy = (c.tgny + R - 1) / R;
-    c.strip_R = R;
-    c.strip_nsx = nsx;
-    c.nstrips = (int64_t)nsx * nsy;
-    // fills: strips of 8 rows would outnumber the device's resident warps
-    if (fills) *fills = (int64_t)nsx * ((c.tgny + 7) / 8) >= resident;
+    bool f = false;
+    strip_shape(c.tgnx, c.tgny, STRIP_OWN, resident, c.tri ? 2 : 8, c.strip_R, c.strip_nsx, c.nstrips, f);
+    if (fills) *fills = f;
     return cudaSuccess;
 }
 

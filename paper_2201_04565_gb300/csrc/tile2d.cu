@@ -149,7 +149,6 @@ static TileArgs tile_args(Ctx &c)
     A.a_fix = c.a_fix;
     A.h_fix = c.h_fix;
     A.hrow = c.h.a * std::sqrt(3.0) * 0.5;
-    A.p48 = ldexpf(1.0f, 48 - c.fix_S);
     A.p24 = ldexpf(1.0f, 24 - c.fix_S);
     A.p0 = ldexpf(1.0f, -c.fix_S);
     A.dt = c.h.dt;

@@ -59,7 +59,7 @@ struct Tile3Args {
     const Coef4 *coef;
     int S;
     long long a_fix;
-    float p48, p24, p0;
+    float p24, p0;
     double dt, a, xc;
     int grip_mode;
     int rate_on;  // constant strain rate: grips at rate_eps0 + (s - rate_step0) rate_dt
@@ -125,14 +125,14 @@ __device__ __forceinline__ bool spring3(const Tile3Args &A, const long long *dl,
     if constexpr (PREC == LSM_PREC_DF) {
         ff d[3];
 #pragma unroll
-        for (int c = 0; c < 3; c++) d[c] = fix_to_ff_i2f2(du[c] - dl[c], A.p48, A.p24, A.p0);
+        for (int c = 0; c < 3; c++) d[c] = fix_to_ff_i2f2(du[c] - dl[c], A.p24, A.p0);
         const ff r2 = ff_add_sloppy(ff_norm2(d[0], d[1]), ff_sqr(d[2]));
         if (TEST && ff_gt(r2, t.rc2)) return false;
         ff y;
         const ff g = ff_spring_g(r2, t.r0, sample ? &y : nullptr);
-        const ff cc = ff_mul(t.k, g);
+        const ff cc = ff_mul_un(t.k, g);  // unnormalised: only multiplied or summed further
 #pragma unroll
-        for (int c = 0; c < 3; c++) f[c] = ff_mul(cc, d[c]);
+        for (int c = 0; c < 3; c++) f[c] = ff_mul_un(cc, d[c]);
         if (sample) {  // double-float sums: no FP64 pipe work per spring
             const ff st = ff_mul(ff_mul(r2, y), g);  // r - r0
             u = ff_add_sloppy(u, ff_mul(ff_mul_f(t.k, 0.5f), ff_sqr(st)));
@@ -395,7 +395,6 @@ Tile3Args tile3_args(Ctx &c)
     A.coef = (const Coef4 *)c.tinvm;
     A.S = c.fix_S;
     A.a_fix = c.a_fix;
-    A.p48 = ldexpf(1.0f, 48 - c.fix_S);
     A.p24 = ldexpf(1.0f, 24 - c.fix_S);
     A.p0 = ldexpf(1.0f, -c.fix_S);
     A.dt = c.h.dt;

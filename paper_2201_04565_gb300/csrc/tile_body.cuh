@@ -114,7 +114,7 @@ struct TileArgs {
     long long a_fix;           // lattice spacing in fixed point
     long long h_fix;           // triangular packing: row height a sqrt(3)/2 in fixed point
     double hrow;               // triangular packing: row height
-    float p48, p24, p0;        // 2^(48-S), 2^(24-S), 2^-S
+    float p24, p0;             // 2^(24-S), 2^-S
     double dt, hdt, gamma, a;
     int grip_mode;
     int rate_on;               // constant strain rate: grips at rate_eps0 + (s - rate_step0) rate_dt
@@ -185,8 +185,8 @@ template <bool TEST, bool SAMPLE>
 __device__ __forceinline__ bool spring_df(long long dxq, long long dyq, const TypeDF &t, const TileArgs &A,
                                           ff &fx, ff &fy, ff &dx, ff &st)
 {
-    const ff dxf = fix_to_ff_i2f2(dxq, A.p48, A.p24, A.p0);
-    const ff dyf = fix_to_ff_i2f2(dyq, A.p48, A.p24, A.p0);
+    const ff dxf = fix_to_ff_i2f2(dxq, A.p24, A.p0);
+    const ff dyf = fix_to_ff_i2f2(dyq, A.p24, A.p0);
     const ff r2 = ff_norm2(dxf, dyf);
     if (TEST && ff_gt(r2, t.rc2)) return true;
     ff y;

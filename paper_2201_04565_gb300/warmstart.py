@@ -279,7 +279,7 @@ def compare(images, k, e, m, net, first_inc, increments, deps=1e-3, tol=1e-8, ma
     # plain arm: one context per specimen (every plain_every-th specimen, scaled)
     sub = list(range(0, S, plain_every))
     tot = [0.0] * increments
-    st_all = []
+    st_inc = [[] for _ in range(increments)]
     for q in sub:
         sp = lsm.Specimen.from_image(images[q], k, e, m, precision=precision, stream=_stream(), **RELAX)
         for i in range(1, first_inc + increments):
@@ -290,15 +290,19 @@ def compare(images, k, e, m, net, first_inc, increments, deps=1e-3, tol=1e-8, ma
             torch.cuda.synchronize()
             if i >= first_inc:
                 tot[i - first_inc] += time.perf_counter() - t0
-                st_all.append(taken)
+                st_inc[i - first_inc].append(taken)
         sp.close()
     scale = S / len(sub)
-    res["plain"] = dict(seconds=[t * scale for t in tot], steps_mean=float(np.mean(st_all)),
+    res["plain"] = dict(seconds=[t * scale for t in tot], steps_mean=[float(np.mean(q)) for q in st_inc],
                         sample="%d of %d specimens run, time scaled by the specimen count" % (len(sub), S))
+    # a curve = 100 increments (10% strain); with first_inc 1 and 100
+    # measured increments every curve was run to its end (no extrapolation)
+    res["full_curves"] = first_inc == 1 and increments >= 100
     for arm in ("plain", "batched", "warm"):
         per_inc = float(np.mean(res[arm]["seconds"]))
         res[arm]["seconds_per_increment"] = per_inc
-        res[arm]["curves_per_s"] = S / (per_inc * 100.0)  # a curve = 100 increments (10% strain)
+        res[arm]["seconds_total"] = float(np.sum(res[arm]["seconds"]))
+        res[arm]["curves_per_s"] = S / (per_inc * 100.0)
     res["speedup_warm_vs_plain"] = res["plain"]["seconds_per_increment"] / res["warm"]["seconds_per_increment"]
     res["speedup_batched_vs_plain"] = res["plain"]["seconds_per_increment"] / res["batched"]["seconds_per_increment"]
     res["speedup_warm_vs_batched"] = res["batched"]["seconds_per_increment"] / res["warm"]["seconds_per_increment"]
@@ -375,6 +379,10 @@ def main(argv=None):
     ap.add_argument("--plain-every", type=int, default=8)
     ap.add_argument("--data-tol", type=float, default=1e-6)
     ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--check-every", type=int, default=50, help="comparison: residual checked every n steps")
+    ap.add_argument("--pre-fracture", action="store_true",
+                    help="train on the increments that end before their specimen's first break")
+    ap.add_argument("--data-precision", default="f32", choices=["f32", "df64"])
     ap.add_argument("--save", default=None)
     ap.add_argument("--load", default=None, help="skip training: BF16 weights from save_params")
     a = ap.parse_args(argv)
@@ -386,14 +394,16 @@ def main(argv=None):
     k, e, m = two_phase_materials()
     train_imgs = [] if a.load else warmstart_specimens(range(a.train_specimens), side=a.side)
     val_imgs = warmstart_specimens(range(2000, 2000 + a.val_specimens), side=a.side)
-    vdata = generate(val_imgs, k, e, m, a.val_increments, tol=a.data_tol, log=log)
+    vdata = generate(val_imgs, k, e, m, a.val_increments, tol=a.data_tol, log=log, precision=a.data_precision,
+                     pre_fracture=a.pre_fracture)
     if a.load:
         net = nnmod.UNet(a.side, a.side, 16, stream=_stream())
         load_params(net, a.load)
         data = dict(U=vdata["U"][:0], seconds=0.0, steps=[0])
         tinfo, terr = dict(loaded=a.load), float("nan")
     else:
-        data = generate(train_imgs, k, e, m, a.train_increments, tol=a.data_tol, log=log)
+        data = generate(train_imgs, k, e, m, a.train_increments, tol=a.data_tol, log=log,
+                        precision=a.data_precision, pre_fracture=a.pre_fracture)
         net, tinfo = train(data, steps=a.train_steps, log=log)
         terr = relative_error(net, {**data, "U": data["U"][:512], "T": data["T"][:512],
                                     "spec": data["spec"][:512], "eps": data["eps"][:512]})
@@ -403,7 +413,7 @@ def main(argv=None):
         save_params(net, a.save)
     eval_imgs = warmstart_specimens(range(1000, 1000 + a.eval_specimens), side=a.side)
     cmp = compare(eval_imgs, k, e, m, net, a.eval_first, a.eval_increments, tol=a.tol, plain_every=a.plain_every,
-                  log=log)
+                  check_every=a.check_every, log=log)
     out = dict(workload="warmstart_%dx%d_x%d" % (a.side, a.side, a.eval_specimens),
                data=dict(samples=int(data["U"].shape[0]), specimens=a.train_specimens,
                          increments=a.train_increments, tol=a.data_tol, seconds=data["seconds"],
