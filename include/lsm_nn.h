@@ -9,13 +9,16 @@
  * non-affine displacement, strain increment) to the displacement the plain
  * damped relaxation adds after an affine load step. Its prediction only moves
  * the relaxation's starting point; the relaxation then runs to the same
- * force-residual tolerance, so the answer never depends on the network and a
- * poor prediction only costs steps.
+ * force-residual tolerance, so for an increment in which no spring breaks the
+ * answer does not depend on the network (to that tolerance) and a poor
+ * prediction only costs steps. Breaks are tested at every step of the
+ * relaxation, so in an increment where springs break the changed transient
+ * can change which of them break.
  *
  * Arithmetic: BF16 weights and activations, FP32 accumulation on the tensor
- * cores (forward and data-gradient convolutions: tcgen05.mma with the
- * accumulator in tensor memory; weight gradients: mma.sync m16n8k16), FP32
- * master weights and Adam moments.
+ * cores (forward, data-gradient and weight-gradient convolutions:
+ * tcgen05.mma with operands staged by TMA and the accumulator in tensor
+ * memory), FP32 master weights and Adam moments.
  * All tensor arguments are DEVICE pointers owned by the caller:
  *   network input   bf16 [B][H][W][32], channels 0..6 used (see
  *                   lsm_unet_prepare_input), the rest zero;

@@ -299,10 +299,12 @@ cudaError_t fixcsr_upload(Ctx &c)
     const int64_t n = c.n, m = c.m, dn = (int64_t)h.dim * n;
     int maxext = std::max(h.nx, std::max(h.ny, h.nz));
     const double extent = 4.0 * maxext * h.a + 16.0;
-    // also every intact spring vector below 2^47 in fixed point, so that it
-    // converts to a double-float in two exact 24-bit chunks
+    // also every intact spring vector (up to the longest critical length)
+    // below 2^48 in fixed point, so that it converts to a double-float in two
+    // exact 24-bit chunks
     c.fix_S = std::min({52, 61 - (int)std::ceil(std::log2(extent)),
-                        47 - (int)std::ceil(std::log2(h.a * std::sqrt(2.0)))});
+                        47 - (int)std::ceil(std::log2(h.a * std::sqrt(2.0))),
+                        47 - (int)std::floor(std::log2(max_critical_length(h.types)))});
     c.a_fix = std::llround(std::ldexp(h.a, c.fix_S));
     std::vector<TypeDF> tdf(h.types.size());
     for (size_t q = 0; q < h.types.size(); q++) {

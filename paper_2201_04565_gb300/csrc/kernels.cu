@@ -313,7 +313,9 @@ k_reduce(const double *__restrict__ ps, int64_t nbs, const double *__restrict__ 
          DeviceSample *__restrict__ dst, long long *__restrict__ counter, int64_t cap, int rate_on,
          double rate_eps0, long long rate_step0, double rate_dt)
 {
-    __shared__ double sh[RED_THREADS / 32];
+    constexpr int NW = RED_THREADS / 32;
+    __shared__ double sh[6][NW];
+    __shared__ double tot[6];
     double acc[6];
     for (int q = 0; q < 6; q++) acc[q] = 0.0;
     for (int64_t b = threadIdx.x; b < nbs; b += RED_THREADS) {
@@ -326,12 +328,24 @@ k_reduce(const double *__restrict__ ps, int64_t nbs, const double *__restrict__ 
         acc[4] += pp[2 * nbp + b];
         acc[5] = fmax(acc[5], pp[3 * nbp + b]);
     }
-    const double W = block_sum(acc[0], sh);
-    const double U = block_sum(acc[1], sh);
-    const double MV = block_sum(acc[2], sh);
-    const double KE = block_sum(acc[3], sh);
-    const double R = block_sum(acc[4], sh);
-    const double RES = block_max(acc[5], sh);
+    // the six block reductions of block_sum / block_max side by side (same
+    // order: a warp xor tree, then the warps in order, one value per thread)
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int q = 0; q < 5; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+        acc[5] = fmax(acc[5], __shfl_xor_sync(0xffffffffu, acc[5], o));
+    }
+    if ((threadIdx.x & 31) == 0)
+        for (int q = 0; q < 6; q++) sh[q][threadIdx.x >> 5] = acc[q];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int q = threadIdx.x;
+        double t = 0.0;
+        for (int k = 0; k < NW; k++) t = q == 5 ? fmax(t, sh[q][k]) : t + sh[q][k];
+        tot[q] = t;
+    }
+    __syncthreads();
+    const double W = tot[0], U = tot[1], MV = tot[2], KE = tot[3], R = tot[4], RES = tot[5];
     if (threadIdx.x == 0) {
         DeviceSample smp;
         const long long stp = *d_step + add_steps;

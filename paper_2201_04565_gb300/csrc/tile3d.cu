@@ -503,6 +503,7 @@ cudaError_t tile3_upload(Ctx &c)
     const int maxext = std::max(h.nx, std::max(h.ny, h.nz));
     c.fix_S = 61 - (int)std::ceil(std::log2(4.0 * maxext * h.a + 16.0));
     c.fix_S = std::min(c.fix_S, 47 - (int)std::ceil(std::log2(h.a * std::sqrt(2.0))));
+    c.fix_S = std::min(c.fix_S, 47 - (int)std::floor(std::log2(max_critical_length(h.types))));
     c.a_fix = std::llround(std::ldexp(h.a, c.fix_S));
     const double aa = std::ldexp((double)c.a_fix, -c.fix_S);
     std::vector<TypeDF> tdf(h.types.size());

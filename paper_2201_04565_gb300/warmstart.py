@@ -11,7 +11,11 @@ One training sample is one strain increment of one specimen:
           u_relaxed - u_loaded (lsm_unet_prepare_target).
 At use, the prediction is added to the loaded state before the relaxation
 (lsm_batch_add_displacements); the relaxation then runs to the usual
-force-residual tolerance, so the result does not depend on the network.
+force-residual tolerance, so the result of an increment without breaks does
+not depend on the network (to that tolerance). Breaks are tested at every
+step of the relaxation, so where springs break the changed transient can
+change which of them break; the comparison records each arm's outcome
+(stresses, broken springs, first breaks) beside its cost.
 """
 from __future__ import annotations
 
@@ -250,7 +254,7 @@ def compare(images, k, e, m, net, first_inc, increments, deps=1e-3, tol=1e-8, ma
         xb = torch.empty((chunk, H, W, 32), dtype=torch.bfloat16, device="cuda")
         out = torch.empty((chunk, H, W, 2), dtype=torch.float32, device="cuda")
         du = torch.empty((S, 2, H, W), dtype=torch.float32, device="cuda")
-        times, steps, nconv = [], [], 0
+        times, steps, nconv, sig = [], [], 0, []
         for i in range(1, first_inc + increments):
             measured = i >= first_inc
             torch.cuda.synchronize()
@@ -271,15 +275,20 @@ def compare(images, k, e, m, net, first_inc, increments, deps=1e-3, tol=1e-8, ma
                 times.append(time.perf_counter() - t0)
                 steps.append(taken.tolist())
                 nconv += int(conv.sum())
+                # outcome, outside the timed region: each specimen's stress
+                sig.append([bt.samples(q)[-1]["sigma_vir"] for q in range(S)])
                 if log:
                     log("%s increment %d: %.2fs, mean steps %d" % (arm, i, times[-1], int(np.mean(taken))))
-        res[arm] = dict(seconds=times, steps_mean=[float(np.mean(s)) for s in steps], converged=nconv,
-                        of=S * increments)
+        brk = [bt.broken(q) for q in range(S)]
+        res[arm] = dict(seconds=times, steps_mean=[float(np.mean(s)) for s in steps],
+                        steps_max=[int(np.max(s)) for s in steps], converged=nconv, of=S * increments,
+                        sigma=sig, n_broken=[int(b[0].sum()) for b in brk], first_break=[int(b[1]) for b in brk])
         bt.close()
     # plain arm: one context per specimen (every plain_every-th specimen, scaled)
     sub = list(range(0, S, plain_every))
     tot = [0.0] * increments
     st_inc = [[] for _ in range(increments)]
+    p_sig, p_brk, p_fb, p_conv = [[] for _ in range(increments)], [], [], 0
     for q in sub:
         sp = lsm.Specimen.from_image(images[q], k, e, m, precision=precision, stream=_stream(), **RELAX)
         for i in range(1, first_inc + increments):
@@ -291,9 +300,16 @@ def compare(images, k, e, m, net, first_inc, increments, deps=1e-3, tol=1e-8, ma
             if i >= first_inc:
                 tot[i - first_inc] += time.perf_counter() - t0
                 st_inc[i - first_inc].append(taken)
+                p_conv += int(stq == lsm.LSM_OK)
+                p_sig[i - first_inc].append(sp.last_sample()["sigma_vir"])
+        b = sp.broken()
+        p_brk.append(int(b[0].sum()))
+        p_fb.append(int(b[1]))
         sp.close()
     scale = S / len(sub)
     res["plain"] = dict(seconds=[t * scale for t in tot], steps_mean=[float(np.mean(q)) for q in st_inc],
+                        steps_max=[int(np.max(q)) for q in st_inc], converged=p_conv, of=len(sub) * increments,
+                        sigma=p_sig, n_broken=p_brk, first_break=p_fb,
                         sample="%d of %d specimens run, time scaled by the specimen count" % (len(sub), S))
     # a curve = 100 increments (10% strain); with first_inc 1 and 100
     # measured increments every curve was run to its end (no extrapolation)
