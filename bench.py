@@ -110,10 +110,10 @@ NCU_TRAFFIC = {
     # profiles/time_step_per_mode_2d_2048_two_phase.md: ncu --metrics
     # dram__bytes_read.sum,dram__bytes_write.sum on three time-step launches
     # of each mode (the same 2048 x 2048 workload), mean
-    "df64": (238.3e6, "1fd3ea8b6336"),
-    "f32": (239.9e6, "1fd3ea8b6336"),
-    "fast64": (236.2e6, "1fd3ea8b6336"),
-    "exact64": (236.7e6, "1fd3ea8b6336"),
+    "df64": (238.4e6, "7bf539b11c13"),
+    "f32": (240.0e6, "7bf539b11c13"),
+    "fast64": (236.2e6, "7bf539b11c13"),
+    "exact64": (236.7e6, "7bf539b11c13"),
 }
 
 # Warp instructions executed by one time-step launch (ncu smsp__inst_executed.sum,
@@ -122,17 +122,17 @@ NCU_TRAFFIC = {
 # this gives the instruction-issue roofline, the one the fixed-point modes
 # are bound by.
 NCU_INSTRUCTIONS = {
-    "df64": (118713091, "1fd3ea8b6336"),
-    "f32": (78677658, "1fd3ea8b6336"),
-    "fast64": (94464248, "1fd3ea8b6336"),
-    "exact64": (195572908, "1fd3ea8b6336"),
+    "df64": (110424291, "7bf539b11c13"),
+    "f32": (75999866, "7bf539b11c13"),
+    "fast64": (94464248, "7bf539b11c13"),
+    "exact64": (195572908, "7bf539b11c13"),
 }
 
 # Binding unit of each mode's time-step kernel, from ncu on the same workload
 # (see the profile summaries), for the roofline's "limiter" note.
 LIMITER = {
-    "df64": "instruction issue (ncu: 74% of issue slots busy, FP64 pipe 45%, DRAM 22% of peak)",
-    "f32": "instruction issue (ncu: 72% of issue slots busy, FP64 pipe 50%, DRAM 32% of peak)",
+    "df64": "instruction issue (ncu: 74% of issue slots busy, FP64 pipe 48%, DRAM 24% of peak)",
+    "f32": "instruction issue (ncu: 72% of issue slots busy, FP64 pipe 52%, DRAM 33% of peak)",
     "fast64": "FP64 pipe (ncu: 86% busy)",
     "exact64": "FP64 pipe (ncu: 88% busy; correctly rounded sqrt and divide)",
 }

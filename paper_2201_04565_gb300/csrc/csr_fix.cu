@@ -206,9 +206,9 @@ k_gather_fix(int64_t n, int64_t m, const int64_t *__restrict__ row, const uint32
 #pragma unroll
         for (int c = 0; c < DIM; c++) {
             if constexpr (PREC == LSM_PREC_F32)
-                F[c] = f2d_bits(Fa[c]);
+                F[c] = f2d_force(Fa[c]);
             else
-                F[c] = ff_to_double(Fa[c]);
+                F[c] = f2d_force(Fa[c].hi) + f2d_force(Fa[c].lo);
         }
         const uint8_t fx = fixm[p];
         const double mp = mass[p], im = imass[p];

@@ -103,6 +103,22 @@ __device__ __forceinline__ double f2d_bits(float f)
     return __longlong_as_double((long long)bits);
 }
 
+// f2d_bits for the forces the integration takes, in fewer integer
+// operations: the same double for every finite float (subnormals flush to a
+// signed zero); an infinity or NaN, which only a step from positions already
+// out of range can produce, gives a finite value of magnitude at least 2^128,
+// so that the next step's fixed-point conversion reports the state as out of
+// range (LSM_ENONFINITE).
+__device__ __forceinline__ double f2d_force(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned ax = u & 0x7FFFFFFFu, sign = u & 0x80000000u;
+    const bool tiny = ax < 0x00800000u;                                    // zero or subnormal
+    const unsigned hi = tiny ? sign : (((ax >> 3) + (896u << 20)) | sign);  // exponent rebiased by 1023 - 127
+    const unsigned lo = tiny ? 0u : (u << 29);
+    return __hiloint2double((int)hi, (int)lo);
+}
+
 // Double -> float with integer operations, truncating the significand
 // (|x| below the float range gives a signed zero, above it infinity).
 __device__ __forceinline__ float d2f_bits(double d)
@@ -268,6 +284,28 @@ __device__ __forceinline__ ff ff_norm2(ff a, ff b)
     float l = __fmaf_rn(__fadd_rn(a.hi, a.hi), a.lo, __fadd_rn(e1, e2));
     l = __fmaf_rn(__fadd_rn(b.hi, b.hi), b.lo, l);
     return fast_two_sum(s.hi, __fadd_rn(s.lo, l));
+}
+
+// ff_norm2 without the final renormalisation: (hi, lo) with hi + lo = a^2 +
+// b^2 to about 2^-46 relative, hi within a few float ulps of the sum (the
+// callers only compare it with a bound or take its reciprocal square root).
+__device__ __forceinline__ ff ff_norm2_un(ff a, ff b)
+{
+    const float p1 = __fmul_rn(a.hi, a.hi), e1 = __fmaf_rn(a.hi, a.hi, -p1);
+    const float p2 = __fmul_rn(b.hi, b.hi), e2 = __fmaf_rn(b.hi, b.hi, -p2);
+    const ff s = two_sum(p1, p2);
+    float l = __fmaf_rn(__fadd_rn(a.hi, a.hi), a.lo, __fadd_rn(e1, e2));
+    l = __fmaf_rn(__fadd_rn(b.hi, b.hi), b.lo, l);
+    return ff{s.hi, __fadd_rn(s.lo, l)};
+}
+
+// a > b for an unnormalised a and a double-float b: the sign of (a.hi -
+// b.hi) + (a.lo - b.lo). Near a tie a.hi - b.hi is exact (Sterbenz: the two
+// lie within a factor 2), so the decision is resolved to the low parts'
+// precision, about 2^-46 relative; far from a tie the high parts decide.
+__device__ __forceinline__ bool ff_gt_un(ff a, ff b)
+{
+    return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo)) > 0.0f;
 }
 
 // The spring factor g = 1 - r0 / r from r^2 (double-float) and r0, with

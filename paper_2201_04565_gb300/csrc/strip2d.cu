@@ -426,8 +426,8 @@ k_strip2d(TileArgs A, int R, int nsx)
                     sx_ += f2x - i0x;
                     sy_ += f2y - i0y;
                 }
-                F[0] = f2d_bits(sx_);
-                F[1] = f2d_bits(sy_);
+                F[0] = f2d_force(sx_);
+                F[1] = f2d_force(sy_);
                 Ff[0] = sx_;
                 Ff[1] = sy_;
                 Fx = ff{sx_, 0.0f};

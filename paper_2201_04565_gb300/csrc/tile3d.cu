@@ -296,7 +296,7 @@ k_tile3d(Tile3Args A)
         for (int c = 0; c < 3; c++) {
             const bool fixed = grip && (c == 0 || A.grip_mode == 1);
             const int64_t q = c * A.nv + g;
-            const double F = f2d_bits(hs[c]) + f2d_bits(el[c]);
+            const double F = f2d_force(hs[c]) + f2d_force(el[c]);
             const float Ff = __fadd_rn(hs[c], el[c]);
             double xr = A.x_in[q];
             const double vh = MODE == T_INIT ? A.v_obs[q] : A.vh_in[q];

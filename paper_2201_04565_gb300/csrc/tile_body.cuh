@@ -167,7 +167,7 @@ struct DfSum {
         hs = t.hi;
         el = __fadd_rn(el, __fadd_rn(t.lo, o.lo));
     }
-    __device__ __forceinline__ double value() const { return f2d_bits(hs) + f2d_bits(el); }
+    __device__ __forceinline__ double value() const { return f2d_force(hs) + f2d_force(el); }
 };
 
 // The fixed-point modes' spring arithmetic, shared by every 2D kernel that
@@ -187,8 +187,8 @@ __device__ __forceinline__ bool spring_df(long long dxq, long long dyq, const Ty
 {
     const ff dxf = fix_to_ff_i2f2(dxq, A.p24, A.p0);
     const ff dyf = fix_to_ff_i2f2(dyq, A.p24, A.p0);
-    const ff r2 = ff_norm2(dxf, dyf);
-    if (TEST && ff_gt(r2, t.rc2)) return true;
+    const ff r2 = ff_norm2_un(dxf, dyf);
+    if (TEST && ff_gt_un(r2, t.rc2)) return true;
     ff y;
     const ff g = ff_spring_g(r2, t.r0, SAMPLE ? &y : nullptr);
     const ff c = ff_mul_un(t.k, g);  // the products stay unnormalised: they are only
@@ -552,7 +552,7 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
                 acc += sf[(c * 4 + 2) * NS + rp] - sf[(c * 4 + 1) * NS + s1];
                 acc += sf[(c * 4 + 3) * NS + rp] - sf[(c * 4 + 0) * NS + s0];
                 if constexpr (PREC == LSM_PREC_F32) {
-                    F[c] = f2d_bits(acc);
+                    F[c] = f2d_force(acc);
                     Ff[c] = acc;
                     Fd[c] = ff{acc, 0.0f};
                 } else {
