@@ -126,16 +126,17 @@ k_springs_fix(int64_t m, int64_t n, const int32_t *__restrict__ si, const int32_
             ff d[DIM];
 #pragma unroll
             for (int c = 0; c < DIM; c++) d[c] = fix_to_ff_i2f2(xf[c * n + j] - xf[c * n + i], T.p24, T.p0);
-            ff r2 = ff_norm2(d[0], d[1]);
-            if constexpr (DIM == 3) r2 = ff_add_sloppy(r2, ff_sqr(d[2]));
-            if (BREAK && ff_gt(r2, t.rc2)) {
+            ff r2;
+            if constexpr (DIM == 3) r2 = ff_norm3_un(d[0], d[1], d[2]);
+            else r2 = ff_norm2_un(d[0], d[1]);
+            if (BREAK && ff_gt_un(r2, t.rc2)) {
                 brk_now = true;
             } else {
                 ff y;
                 const ff g = ff_spring_g(r2, t.r0, SAMPLE ? &y : nullptr);
-                const ff cc = ff_mul(t.k, g);
+                const ff cc = ff_mul_un(t.k, g);  // unnormalised: only multiplied or summed further
 #pragma unroll
-                for (int c = 0; c < DIM; c++) f[c] = ff_mul(cc, d[c]);
+                for (int c = 0; c < DIM; c++) f[c] = ff_mul_un(cc, d[c]);
                 if (SAMPLE) {
                     const double st = ff_to_double(ff_mul(ff_mul(r2, y), g));  // r - r0
                     u = 0.5 * ff_to_double(t.k) * st * st;

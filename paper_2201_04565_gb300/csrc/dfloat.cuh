@@ -299,6 +299,21 @@ __device__ __forceinline__ ff ff_norm2_un(ff a, ff b)
     return ff{s.hi, __fadd_rn(s.lo, l)};
 }
 
+// a^2 + b^2 + c^2 in the same form as ff_norm2_un: exact float squares of
+// the high parts (TwoProd), two TwoSums, the small terms in float.
+__device__ __forceinline__ ff ff_norm3_un(ff a, ff b, ff c)
+{
+    const float p1 = __fmul_rn(a.hi, a.hi), e1 = __fmaf_rn(a.hi, a.hi, -p1);
+    const float p2 = __fmul_rn(b.hi, b.hi), e2 = __fmaf_rn(b.hi, b.hi, -p2);
+    const float p3 = __fmul_rn(c.hi, c.hi), e3 = __fmaf_rn(c.hi, c.hi, -p3);
+    const ff s = two_sum(p1, p2);
+    const ff t = two_sum(s.hi, p3);
+    float l = __fmaf_rn(__fadd_rn(a.hi, a.hi), a.lo, __fadd_rn(__fadd_rn(e1, e2), e3));
+    l = __fmaf_rn(__fadd_rn(b.hi, b.hi), b.lo, l);
+    l = __fmaf_rn(__fadd_rn(c.hi, c.hi), c.lo, l);
+    return ff{t.hi, __fadd_rn(__fadd_rn(t.lo, s.lo), l)};
+}
+
 // a > b for an unnormalised a and a double-float b: the sign of (a.hi -
 // b.hi) + (a.lo - b.lo). Near a tie a.hi - b.hi is exact (Sterbenz: the two
 // lie within a factor 2), so the decision is resolved to the low parts'

@@ -126,8 +126,8 @@ __device__ __forceinline__ bool spring3(const Tile3Args &A, const long long *dl,
         ff d[3];
 #pragma unroll
         for (int c = 0; c < 3; c++) d[c] = fix_to_ff_i2f2(du[c] - dl[c], A.p24, A.p0);
-        const ff r2 = ff_add_sloppy(ff_norm2(d[0], d[1]), ff_sqr(d[2]));
-        if (TEST && ff_gt(r2, t.rc2)) return false;
+        const ff r2 = ff_norm3_un(d[0], d[1], d[2]);
+        if (TEST && ff_gt_un(r2, t.rc2)) return false;
         ff y;
         const ff g = ff_spring_g(r2, t.r0, sample ? &y : nullptr);
         const ff cc = ff_mul_un(t.k, g);  // unnormalised: only multiplied or summed further
