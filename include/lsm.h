@@ -65,9 +65,13 @@ typedef enum {
  *      point), spring force evaluated and gathered in single precision,
  *      positions and velocities integrated in double.
  *  LSM_PREC_DF: as LSM_PREC_F32, but the spring force and the gather use
- *      double-float arithmetic (pairs of floats, 48 significant bits), so
- *      forces carry about 1e-14 relative error while the FP64 pipe only does
- *      the integration. For image builds DF and F32 run on the 2D strip or
+ *      double-float arithmetic (pairs of floats, 48 significant bits; 1/r by
+ *      one double-float Newton step, about 2^-45), so forces carry about
+ *      3e-14 relative error while the FP64 pipe only does the integration.
+ *      In both fixed-point modes every spring vector up to the longest
+ *      critical length converts exactly, and a non-finite force (which only
+ *      positions already out of range can produce) is reported by the next
+ *      step's range check as LSM_ENONFINITE. For image builds DF and F32 run on the 2D strip or
  *      tile kernels (square lattice), the strip kernel (triangular
  *      packing), the 3D voxel tile kernel, or (path 1) the spring-list
  *      kernels with the same fixed-point spring vectors.
