@@ -25,7 +25,6 @@
 // force in single precision or in double-float arithmetic, integrating in FP64.
 #include "tile_body.cuh"
 
-#include <algorithm>
 #include <cmath>
 
 namespace lsm {
@@ -43,29 +42,24 @@ k_tile2d(TileArgs A)
 // (tri: rows alternate between nx sites at x = ix a and nx - 1 sites at
 // x = (ix + 1/2) a; a row's first and last site are its grips) (Sections
 // 2.3, 3.1).
-// One thread per grid column gx (blockIdx.x), rows gy from blockIdx.y with a
-// stride of gridDim.y: no division by the row length.
 __global__ void k_tile_strain(int nx, int ny, int64_t np, double *x, double *vh, double *v_obs,
                               const uint8_t *phase, double a, double xc, double scale, double eps,
                               int affine, double *d_eps, int tri)
 {
-    const int gx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gx == 0 && blockIdx.y == 0) *d_eps = eps;
-    if (gx >= nx) return;
-    for (int gy = blockIdx.y; gy < ny; gy += gridDim.y) {
-        const int64_t g = (int64_t)gy * nx + gx;
-        if (!phase[g]) continue;
-        const int odd = tri ? (gy & 1) : 0;
-        double xp = x[g];
-        if (affine) xp = ad(xc, ml(sb(xp, xc), scale));
-        if (gx == 0 || gx == nx - 1 - odd) {
-            const double X = odd ? ml(ad((double)gx, 0.5), a) : gx * a;
-            xp = ad(X, ml(eps, sb(X, xc)));
-            vh[g] = 0.0;
-            v_obs[g] = 0.0;
-        }
-        x[g] = xp;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g == 0) *d_eps = eps;
+    if (g >= np || !phase[g]) return;
+    const int gx = (int)(g % nx);
+    const int odd = tri ? (int)((g / nx) & 1) : 0;
+    double xp = x[g];
+    if (affine) xp = ad(xc, ml(sb(xp, xc), scale));
+    if (gx == 0 || gx == nx - 1 - odd) {
+        const double X = odd ? ml(ad((double)gx, 0.5), a) : gx * a;
+        xp = ad(X, ml(eps, sb(X, xc)));
+        vh[g] = 0.0;
+        v_obs[g] = 0.0;
     }
+    x[g] = xp;
 }
 
 // Pixel-grid broken flags / break steps -> canonical spring order. sbase[g]
@@ -259,7 +253,7 @@ cudaError_t tile_observe(Ctx &c)
 cudaError_t tile_apply_strain(Ctx &c, double eps_old, double eps_new)
 {
     const double scale = (1.0 + eps_new) / (1.0 + eps_old);
-    const dim3 g((unsigned)((c.tgnx + 255) / 256), (unsigned)std::min(c.tgny, 65535));
+    const unsigned g = (unsigned)((c.tnp + 255) / 256);
     k_tile_strain<<<g, 256, 0, c.stream>>>(c.tgnx, c.tgny, c.tnp, c.tx[c.tcur], c.tvh[c.tcur], c.tvobs,
                                            c.tph, c.h.a, c.h.xc, scale, eps_new, c.h.load_mode == 0,
                                            c.d_eps, c.tri ? 1 : 0);

@@ -61,6 +61,36 @@ def test_non_finite_state_is_reported(L, kind, prec, path, where):
     h.close()
 
 
+@pytest.mark.parametrize("kind,prec,path", [("2d", "df64", 3), ("2d", "df64", 2), ("2d", "f32", 3),
+                                            ("2d", "exact64", 0), ("3d", "df64", 0)])
+def test_coincident_particles_are_reported(L, kind, prec, path):
+    """Two neighbours moved onto the same point: the spring between them has
+    r = 0 and its force is not finite. In the fixed-point modes the force's
+    conversion to double makes that a finite value of at least 2^128, so the
+    next step's positions leave the fixed-point range; in the FP64 modes the
+    velocities become non-finite. Either way the next synchronising call
+    returns LSM_ENONFINITE, and the library stays usable."""
+    g = _specimen(L, kind, prec, path)
+    X = g.state()[0]
+    d = X[:, 1:] - X[:, :-1]
+    same_line = np.all(d[1:] == 0.0, axis=0)
+    cand = np.flatnonzero(same_line & (d[0] > 0) & (X[0, :-1] > X[0].min()) & (X[0, 1:] < X[0].max()))
+    p = cand[len(cand) // 2]  # an interior particle whose +x neighbour is the next particle
+    x, v = g.state()
+    x[:, p] = x[:, p + 1]
+    g.set_state(x, v)
+    g.step(3)
+    with pytest.raises(L.LsmError) as ei:
+        g.synchronize()
+    assert ei.value.status == L.LSM_ENONFINITE
+    g.close()
+    h = _specimen(L, kind, prec, path)
+    h.step(2)
+    h.synchronize()
+    assert np.all(np.isfinite(h.state()[0]))
+    h.close()
+
+
 def test_allocation_cap_reports_enomem_without_leaking(L, monkeypatch):
     import torch
     img = inclusion_image(512, 512, 5.0, 20.0, 0.3, 3)
