@@ -148,11 +148,11 @@ KERNEL = {
 
 def _kernel_tag():
     """sha1 prefix of the 2D time-step kernels' sources (the strip kernel of
-    the fixed-point modes, the tile kernel of the FP64 modes, and the
-    arithmetic they share)."""
+    the fixed-point modes and its sweep, the tile kernel of the FP64 modes,
+    and the arithmetic they share)."""
     import hashlib
     h = hashlib.sha1()
-    for name in ("strip2d.cu", "tile2d.cu", "tile_body.cuh", "dfloat.cuh"):
+    for name in ("strip2d.cu", "strip_body.cuh", "tile2d.cu", "tile_body.cuh", "dfloat.cuh"):
         with open(os.path.join(ROOT, "paper_2201_04565_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]

@@ -42,15 +42,23 @@ lsm_status lsm_batch_sizes(lsm_batch *b, int32_t spec, int32_t *count, int64_t *
 
 /* Time steps_per_trial steps of every candidate schedule (tile height
  * 8/16/32, grid of one CTA per tile or a persistent grid of 4 or 8 CTAs per
- * SM, natural or largest-specimen-first tile order) on a copy of the current
+ * SM, natural or largest-specimen-first tile order; in the F32 and DF modes
+ * also the strip schedules -8/-16/-32, below) on a copy of the current
  * state, after a warm-up that brings the GPU to its load clocks, in two
  * sweeps; keep the schedule with the fastest trial and restore the state.
- * Outputs (may be NULL): chosen tile height, grid size (0 = one CTA per
- * tile), order (0 natural, 1 largest first) and its time per step in ms. */
+ * Outputs (may be NULL): chosen tile height (negative: strips of that many
+ * rows), grid size (0 = one CTA per tile), order (0 natural, 1 largest
+ * first) and its time per step in ms. */
 lsm_status lsm_batch_autotune(lsm_batch *b, int32_t steps_per_trial, int32_t *tile_y, int32_t *grid,
                               int32_t *order, double *ms_per_step);
 
-/* Set the schedule explicitly (tile_y 8, 16 or 32; grid >= 0; order 0 or 1). */
+/* Set the schedule explicitly: tile_y 8, 16 or 32 (tiles of 32 columns and
+ * that many rows, one CTA each), or -8, -16, -32 (F32 and DF modes, every
+ * specimen below 2^29 pixels): the steps without a sample run as one warp
+ * per strip of 30 owned columns and 8, 16 or 32 rows, the register-resident
+ * sweep of the single-specimen strip kernel, while load increments and
+ * sample steps keep 16-row tiles; the states are the same bits either way.
+ * grid >= 0 (tiles only); order 0 or 1. LSM_EINVAL otherwise. */
 lsm_status lsm_batch_set_schedule(lsm_batch *b, int32_t tile_y, int32_t grid, int32_t order);
 
 /* Load increment of every specimen to the absolute strains eps[0..count-1]

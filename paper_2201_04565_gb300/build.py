@@ -17,7 +17,7 @@ LIB = os.path.join(HERE, "liblsm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 SOURCES = ["kernels.cu", "batch.cu", "tile2d.cu", "strip2d.cu", "tile3d.cu", "static_scratch.cu", "csr_fix.cu", "fields.cu", "nn.cu", "conv_tc.cu", "build.cpp", "checkpoint.cpp", "api.cpp"]
-HEADERS = ["lsm_internal.h", "dfloat.cuh", "tile_body.cuh", "nn_internal.h", "nvtx_range.h"]
+HEADERS = ["lsm_internal.h", "dfloat.cuh", "tile_body.cuh", "strip_body.cuh", "nn_internal.h", "nvtx_range.h"]
 
 
 def _nvcc():

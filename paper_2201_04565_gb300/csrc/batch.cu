@@ -18,7 +18,7 @@
 #include <vector>
 
 #include "../../include/lsm_nn.h"
-#include "tile_body.cuh"
+#include "strip_body.cuh"
 
 namespace lsm {
 
@@ -54,9 +54,12 @@ struct BatchCtx {
     std::vector<std::vector<int64_t>> pix;  // particle -> pixel (empty: identity)
     std::vector<double> eps;                // host mirror
     int64_t NP = 0;                         // pixels in all specimens
-    // schedule
-    int tile_y = 16, grid = 0, order = 0;
+    // schedule: tiles of tile_y rows, or (strip_r > 0, fixed-point modes)
+    // the plain steps on strips of strip_r rows
+    int tile_y = 16, grid = 0, order = 0, strip_r = 0;
     int64_t T = 0;
+    BatchTile *strips = nullptr;  // (spec, sx, sy) of every strip
+    int64_t NSTRIP = 0;
     // device memory
     double *X[2] = {nullptr, nullptr}, *VH[2] = {nullptr, nullptr}, *VOBS = nullptr;
     uint8_t *PH = nullptr, *MASK = nullptr;
@@ -122,6 +125,50 @@ k_tile2d_batch(TileArgs base, const BatchTile *__restrict__ tiles, int64_t t0, i
         A.t_off = 0;
         tile_body<32, TY, PREC, MODE, SAMPLE>(A, bt.bx, bt.by, t, smem_raw);
         __syncthreads();
+    }
+}
+
+// A plain time step (no sample) of the batch on strips: one warp per strip
+// of 30 owned columns and R rows of one specimen (entries (spec, sx, sy) of
+// `strips`; the schedule's grid does not apply), the single-specimen strip
+// kernel's sweep on that specimen's arrays. Same states as the tile kernel, so the sample steps stay on the
+// tile list.
+template <int PREC>
+__global__ void __launch_bounds__(32 * STRIP_WARPS, 5)
+k_strip2d_batch(TileArgs base, const BatchTile *__restrict__ strips, int64_t n, int R,
+                const SpecDesc *__restrict__ specs, double *X0, double *X1, double *V0, double *V1, double *VOBS,
+                const uint8_t *PH, uint8_t *MASK, long long *BRK, unsigned long long *fb, unsigned long long *nb)
+{
+    __shared__ TypeDF sdf[128];
+    __shared__ Coef4 scoef[8];
+    __shared__ float smassf[8];
+    __shared__ ff soff[4][3];
+    strip_tables<PREC, 0>(base, sdf, scoef, smassf, soff);
+    __syncthreads();
+    const int64_t q = (int64_t)blockIdx.x * STRIP_WARPS + (threadIdx.x >> 5);
+    if (q >= n) return;  // whole warps only
+    {
+        const BatchTile st = strips[q];
+        const SpecDesc &sd = specs[st.spec];
+        if (!sd.active) return;  // uniform over the warp
+        TileArgs A = base;
+        const int64_t P = sd.pbase;
+        A.nx = sd.nx;
+        A.ny = sd.ny;
+        A.np = (int64_t)sd.nx * sd.ny;
+        A.x_in = (sd.cur ? X1 : X0) + 2 * P;
+        A.x_out = (sd.cur ? X0 : X1) + 2 * P;
+        A.vh_in = (sd.cur ? V1 : V0) + 2 * P;
+        A.vh_out = (sd.cur ? V0 : V1) + 2 * P;
+        A.v_obs = VOBS + 2 * P;
+        A.phase = PH + P;
+        A.mask = MASK + P;
+        A.brk = BRK + 4 * P;
+        A.first_break = fb + st.spec;
+        A.nbroken = nb + st.spec;
+        A.d_step = &specs[st.spec].steps;
+        A.t_off = 0;
+        strip_run<PREC, false, false, 0, T_STEP>(A, R, st.bx, st.by * R, 0, sdf, scoef, smassf, soff);
     }
 }
 
@@ -302,8 +349,8 @@ static void batch_free(BatchCtx &b)
     if (b.stiles && b.stiles != b.tiles) cudaFree(b.stiles);
     b.stiles = nullptr;
     void *ptrs[] = {b.X[0], b.X[1], b.VH[0], b.VH[1], b.VOBS, b.PH, b.MASK, b.BRK, b.SBASE, b.specs, b.tiles,
-                    b.part_s, b.part_p, b.fb, b.nb, b.status, b.nactive, b.d_nsamp, b.samples, b.scratch,
-                    b.d_eps2, b.types, b.tdf, b.tmass, b.tcoef, b.export_buf};
+                    b.strips, b.part_s, b.part_p, b.fb, b.nb, b.status, b.nactive, b.d_nsamp, b.samples,
+                    b.scratch, b.d_eps2, b.types, b.tdf, b.tmass, b.tcoef, b.export_buf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -317,16 +364,21 @@ static ff split_ff_b(double v)
 // (Re)build the tile list for tile height ty and order (0 natural, 1 largest
 // specimen first), the 16-row list of the sample steps (the same list when ty
 // is 16: the per-tile sample reductions would double on 8-row tiles) and the
-// per-tile partial buffers, which only sample steps write.
+// per-tile partial buffers, which only sample steps write. ty = -R (R 8, 16
+// or 32): the plain steps run on strips of 30 owned columns and R rows, in
+// the same specimen order, and the tiles (load increments, sample steps,
+// fields) are 16 rows high.
 static cudaError_t build_tiles(BatchCtx &b, int ty, int order)
 {
+    const int strip_r = ty < 0 ? -ty : 0;
+    if (strip_r) ty = 16;
     constexpr int TYS = 16;
     std::vector<int> sorder(b.S);
     std::iota(sorder.begin(), sorder.end(), 0);
     if (order == 1)
         std::stable_sort(sorder.begin(), sorder.end(),
                          [&](int p, int q) { return (int64_t)b.nx[p] * b.ny[p] > (int64_t)b.nx[q] * b.ny[q]; });
-    std::vector<BatchTile> tl, ts;
+    std::vector<BatchTile> tl, ts, sl;
     std::vector<SpecDesc> sd(b.S);
     BT_TRY(cudaMemcpyAsync(sd.data(), b.specs, b.S * sizeof(SpecDesc), cudaMemcpyDeviceToHost, b.stream));
     BT_TRY(cudaStreamSynchronize(b.stream));
@@ -340,13 +392,25 @@ static cudaError_t build_tiles(BatchCtx &b, int ty, int order)
         sd[s].nstiles = (int64_t)tx * tys;
         for (int by = 0; by < tys; by++)
             for (int bx = 0; bx < tx; bx++) ts.push_back(BatchTile{s, bx, by, 0});
+        if (strip_r) {
+            const int nsx = (b.nx[s] + STRIP_OWN - 1) / STRIP_OWN, nsy = (b.ny[s] + strip_r - 1) / strip_r;
+            for (int sy = 0; sy < nsy; sy++)
+                for (int sx = 0; sx < nsx; sx++) sl.push_back(BatchTile{s, sx, sy, 0});
+        }
     }
     if (b.stiles && b.stiles != b.tiles) cudaFree(b.stiles);
     if (b.tiles) cudaFree(b.tiles);
+    if (b.strips) cudaFree(b.strips);
     if (b.part_s) cudaFree(b.part_s);
     if (b.part_p) cudaFree(b.part_p);
-    b.tiles = b.stiles = nullptr;
+    b.tiles = b.stiles = b.strips = nullptr;
     b.part_s = b.part_p = nullptr;
+    b.NSTRIP = 0;
+    if (strip_r) {
+        BT_TRY(balloc(&b.strips, sl.size()));
+        BT_TRY(cudaMemcpyAsync(b.strips, sl.data(), sl.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b.stream));
+        b.NSTRIP = (int64_t)sl.size();
+    }
     b.T = (int64_t)tl.size();
     b.TS = (int64_t)ts.size();
     BT_TRY(balloc(&b.tiles, tl.size()));
@@ -362,9 +426,20 @@ static cudaError_t build_tiles(BatchCtx &b, int ty, int order)
     BT_TRY(cudaMemcpyAsync(b.specs, sd.data(), b.S * sizeof(SpecDesc), cudaMemcpyHostToDevice, b.stream));
     BT_TRY(cudaStreamSynchronize(b.stream));
     b.tile_y = ty;
+    b.strip_r = strip_r;
     b.order = order;
     drop_graphs(b);
     return cudaSuccess;
+}
+
+// Whether the batch can take strip schedules: the fixed-point modes, and
+// specimens small enough for the strip sweep's 32-bit pixel indices.
+static bool batch_strips_ok(const BatchCtx &b)
+{
+    if (b.prec != LSM_PREC_DF && b.prec != LSM_PREC_F32) return false;
+    for (int s = 0; s < b.S; s++)
+        if (2 * (int64_t)b.nx[s] * b.ny[s] >= ((int64_t)1 << 30)) return false;
+    return true;
 }
 
 static TileArgs batch_base_args(BatchCtx &b)
@@ -389,6 +464,18 @@ static TileArgs batch_base_args(BatchCtx &b)
     A.part_p = b.part_p;
     A.ntiles = b.TS;  // partial sums come from the sample-step tile list
     return A;
+}
+
+template <int PREC>
+static cudaError_t launch_bs(BatchCtx &b)
+{
+    if (b.NSTRIP <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((b.NSTRIP + STRIP_WARPS - 1) / STRIP_WARPS);  // one warp per strip
+    k_strip2d_batch<PREC><<<grid, 32 * STRIP_WARPS, 0, b.stream>>>(batch_base_args(b), b.strips, b.NSTRIP, b.strip_r,
+                                                                    b.specs, b.X[0], b.X[1], b.VH[0], b.VH[1], b.VOBS,
+                                                                    b.PH, b.MASK, b.BRK, b.fb, b.nb);
+    b.launches += 1;
+    return cudaGetLastError();
 }
 
 template <int TY, int PREC, int MODE, bool SAMPLE>
@@ -426,6 +513,10 @@ static cudaError_t launch_b(BatchCtx &b, int64_t t0, int64_t t1)
     if constexpr (SAMPLE) {
         BT_PREC(16, b.stiles)
     } else {
+        if (MODE == T_STEP && b.strip_r > 0) {  // the plain steps on strips
+            if (b.prec == LSM_PREC_F32) return launch_bs<LSM_PREC_F32>(b);
+            return launch_bs<LSM_PREC_DF>(b);
+        }
         if (b.tile_y == 8) { BT_PREC(8, b.tiles) }
         if (b.tile_y == 32) { BT_PREC(32, b.tiles) }
         BT_PREC(16, b.tiles)
@@ -782,11 +873,15 @@ lsm_status lsm_batch_sizes(lsm_batch *b, int32_t spec, int32_t *count, int64_t *
 lsm_status lsm_batch_set_schedule(lsm_batch *b, int32_t tile_y, int32_t grid, int32_t order)
 {
     if (!b) return bfail(nullptr, LSM_EINVAL, "null batch");
-    if ((tile_y != 8 && tile_y != 16 && tile_y != 32) || grid < 0 || (order != 0 && order != 1))
-        return bfail(b, LSM_EINVAL, "tile_y must be 8, 16 or 32; grid >= 0; order 0 or 1");
+    const int ay = tile_y < 0 ? -tile_y : tile_y;
+    if ((ay != 8 && ay != 16 && ay != 32) || grid < 0 || (order != 0 && order != 1))
+        return bfail(b, LSM_EINVAL, "tile_y must be 8, 16 or 32 (or -8, -16, -32: strips); grid >= 0; order 0 or 1");
+    if (tile_y < 0 && !lsm::batch_strips_ok(*b))
+        return bfail(b, LSM_EINVAL, "strip schedules need the F32 or DF mode and specimens below 2^29 pixels");
     if (grid != b->grid) lsm::drop_graphs(*b);
     b->grid = grid;
-    if (tile_y != b->tile_y || order != b->order) {
+    const int cur = b->strip_r ? -b->strip_r : b->tile_y;
+    if (tile_y != cur || order != b->order) {
         cudaError_t e = lsm::build_tiles(*b, tile_y, order);
         if (e != cudaSuccess) return bcuda(b, e, "schedule");
     }
@@ -1072,29 +1167,34 @@ lsm_status lsm_batch_autotune(lsm_batch *b, int32_t steps_per_trial, int32_t *ti
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     const int64_t launches0 = b->launches;
     double best = 1e300;
-    int bty = b->tile_y, bgrid = b->grid, bord = b->order;
+    const int cur_ty = b->strip_r ? -b->strip_r : b->tile_y;
+    int bty = cur_ty, bgrid = b->grid, bord = b->order;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int tys[3] = {8, 16, 32};
-    // Two sweeps over the 18 schedules, each keeping its faster trial; the
-    // GPU is brought to its load clocks first (steps of the current
+    // tile heights 8, 16, 32, and in the fixed-point modes strips of 8, 16
+    // or 32 rows (-R)
+    const int tys[6] = {8, 16, 32, -8, -16, -32};
+    const int nty = lsm::batch_strips_ok(*b) ? 6 : 3;
+    // Two sweeps over the 18 (36) schedules, each keeping its faster trial;
+    // the GPU is brought to its load clocks first (steps of the current
     // schedule), so that the first candidates are not timed at idle clocks.
-    double tbest[3][2][3];
-    for (int it = 0; it < 3; it++)
+    double tbest[6][2][3];
+    for (int it = 0; it < 6; it++)
         for (int ord = 0; ord < 2; ord++)
             for (int gi = 0; gi < 3; gi++) tbest[it][ord][gi] = 1e300;
-    if (e == cudaSuccess) e = lsm::build_tiles(*b, b->tile_y, b->order);
+    if (e == cudaSuccess) e = lsm::build_tiles(*b, cur_ty, b->order);
     for (int w = 0; w < 4 && e == cudaSuccess; w++) e = lsm::batch_steps_graph(*b, steps_per_trial, 0, 0, 0.0);
     for (int sweep = 0; sweep < 2 && e == cudaSuccess; sweep++)
-        for (int it = 0; it < 3 && e == cudaSuccess; it++)
+        for (int it = 0; it < nty && e == cudaSuccess; it++)
             for (int ord = 0; ord < 2 && e == cudaSuccess; ord++) {
                 e = lsm::build_tiles(*b, tys[it], ord);
                 const int grids[3] = {0, nsm * 4, nsm * 8};
                 for (int gi = 0; gi < 3 && e == cudaSuccess; gi++) {
+                    if (tys[it] < 0 && gi > 0) continue;  // strips: one warp each, the grid does not apply
                     b->grid = grids[gi];
                     lsm::drop_graphs(*b);  // the cached graphs hold the previous grid
                     e = lsm::batch_steps_graph(*b, steps_per_trial, 0, 0, 0.0);  // warm (captures the graph)
@@ -1107,7 +1207,7 @@ lsm_status lsm_batch_autotune(lsm_batch *b, int32_t steps_per_trial, int32_t *ti
                     if (e == cudaSuccess && ms / steps_per_trial < tbest[it][ord][gi]) tbest[it][ord][gi] = ms / steps_per_trial;
                 }
             }
-    for (int it = 0; it < 3; it++)
+    for (int it = 0; it < nty; it++)
         for (int ord = 0; ord < 2; ord++)
             for (int gi = 0; gi < 3; gi++)
                 if (tbest[it][ord][gi] < best) {

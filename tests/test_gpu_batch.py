@@ -33,10 +33,11 @@ def _images():
     return imgs
 
 
-@pytest.mark.parametrize("precision", ["exact64", "df64"])
-@pytest.mark.parametrize("tile_y", [8, 16])
+@pytest.mark.parametrize("precision,tile_y", [("exact64", 8), ("exact64", 16), ("df64", 8), ("df64", 16),
+                                              ("df64", -8), ("df64", -16)])
 def test_batch_matches_single_specimens(B, oracle_mod, precision, tile_y):
-    """Positions, velocities, breaks bit-identical. Samples: exact64 to
+    """Positions, velocities, breaks bit-identical, on 8- and 16-row tiles and
+    (df64; tile_y < 0) on the batched strip sweep. Samples: exact64 to
     1e-12 (its sample steps run on 16-row tiles in both paths, whatever the
     steps' tiling); in df64 the single-specimen path sums its samples per
     strip (strip kernel) and the batch per tile, so the stress agrees to the
@@ -124,23 +125,28 @@ def test_schedules_and_autotune_are_state_neutral(B):
     imgs = _images()
     k, e, m = two_phase_materials()
     outs = []
-    for sched in [(8, 0, 0), (32, 152 * 4, 1), None]:
+    for sched in [(8, 0, 0), (32, 152 * 4, 1), (-32, 0, 1), None]:
         bt = batch.Batch(imgs, k, e, m, precision="df64")
         bt.apply_strain(0.01)
         bt.step(7)
         if sched is None:
             info = bt.autotune(3)
-            assert info["tile_y"] in (8, 16, 32) and info["ms_per_step"] > 0
+            assert info["tile_y"] in (8, 16, 32, -8, -16, -32) and info["ms_per_step"] > 0
         else:
             bt.set_schedule(*sched)
         for i in range(2, 20):
             bt.apply_strain(i * 5e-3)
             bt.step(9)
         outs.append([bt.state(q)[0] for q in range(len(imgs))])
-    for a, b in zip(outs[0], outs[1]):
-        assert np.array_equal(a, b)
-    for a, b in zip(outs[0], outs[2]):
-        assert np.array_equal(a, b)
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            assert np.array_equal(a, b)
+    # strips are a fixed-point-mode schedule
+    bt = batch.Batch(imgs, k, e, m, precision="exact64")
+    with pytest.raises(lsm.LsmError) as ei:
+        bt.set_schedule(-16, 0, 0)
+    assert ei.value.status == lsm.LSM_EINVAL
+    bt.close()
 
 
 def test_batch_relax_matches_single_relax(B):
