@@ -690,7 +690,10 @@ static cudaError_t batch_upload(BatchCtx &b, const std::vector<HostNet> &nets, c
     BT_TRY(cudaMemcpyAsync(b.tmass, mtab.data(), b.nphase * sizeof(double), cudaMemcpyHostToDevice, st));
     BT_TRY(cudaMemcpyAsync(b.tcoef, coef.data(), 4 * b.nphase * sizeof(double), cudaMemcpyHostToDevice, st));
     BT_TRY(cudaStreamSynchronize(st));
-    BT_TRY(build_tiles(b, 16, 1));
+    // default schedule: largest specimens first, plain steps on 16-row
+    // strips in the fixed-point modes (what the autotuner picks on the
+    // benchmark's batches), 16-row tiles otherwise
+    BT_TRY(build_tiles(b, batch_strips_ok(b) ? -16 : 16, 1));
     // initial acceleration of every specimen (vh = v + dt/2 a(0))
     {
         cudaError_t ei = launch_b<T_INIT, false>(b, 0, b.T);
