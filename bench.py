@@ -110,10 +110,10 @@ NCU_TRAFFIC = {
     # profiles/time_step_per_mode_2d_2048_two_phase.md: ncu --metrics
     # dram__bytes_read.sum,dram__bytes_write.sum on three time-step launches
     # of each mode (the same 2048 x 2048 workload), mean
-    "df64": (238.6e6, "e44f2ad8e3e1"),
-    "f32": (240.2e6, "e44f2ad8e3e1"),
-    "fast64": (236.1e6, "e44f2ad8e3e1"),
-    "exact64": (236.2e6, "e44f2ad8e3e1"),
+    "df64": (238.5e6, "d2f239a7a909"),
+    "f32": (240.0e6, "d2f239a7a909"),
+    "fast64": (236.3e6, "d2f239a7a909"),
+    "exact64": (236.5e6, "d2f239a7a909"),
 }
 
 # Warp instructions executed by one time-step launch (ncu smsp__inst_executed.sum,
@@ -122,10 +122,10 @@ NCU_TRAFFIC = {
 # this gives the instruction-issue roofline, the one the fixed-point modes
 # are bound by.
 NCU_INSTRUCTIONS = {
-    "df64": (110424291, "e44f2ad8e3e1"),
-    "f32": (75999866, "e44f2ad8e3e1"),
-    "fast64": (94464248, "e44f2ad8e3e1"),
-    "exact64": (195572908, "e44f2ad8e3e1"),
+    "df64": (110408352, "d2f239a7a909"),
+    "f32": (75982754, "d2f239a7a909"),
+    "fast64": (94464248, "d2f239a7a909"),
+    "exact64": (195572908, "d2f239a7a909"),
 }
 
 # Binding unit of each mode's time-step kernel, from ncu on the same workload

@@ -59,8 +59,8 @@ lsm_status lsm_batch_autotune(lsm_batch *b, int32_t steps_per_trial, int32_t *ti
  * sweep of the single-specimen strip kernel, while load increments and
  * sample steps keep 16-row tiles; the states are the same bits either way.
  * grid >= 0 (tiles only); order 0 or 1. LSM_EINVAL otherwise. A new batch
- * starts with strips of 16 rows (F32, DF) or 16-row tiles, largest specimens
- * first, grid 0. */
+ * starts with strips of 16 rows (F32, DF, when they outnumber the warps the
+ * device holds at once) or 16-row tiles, largest specimens first, grid 0. */
 lsm_status lsm_batch_set_schedule(lsm_batch *b, int32_t tile_y, int32_t grid, int32_t order);
 
 /* Load increment of every specimen to the absolute strains eps[0..count-1]

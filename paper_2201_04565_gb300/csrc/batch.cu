@@ -466,6 +466,24 @@ static TileArgs batch_base_args(BatchCtx &b)
     return A;
 }
 
+// Whether strips of R rows outnumber the warps of the batched strip kernel
+// that fit on the device at once.
+static bool batch_strips_fill(const BatchCtx &b, int R)
+{
+    int dev = 0, nsm = 0, nb = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_strip2d_batch<LSM_PREC_DF>, 32 * STRIP_WARPS, 0) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int64_t strips = 0;
+    for (int s = 0; s < b.S; s++)
+        strips += (int64_t)((b.nx[s] + STRIP_OWN - 1) / STRIP_OWN) * ((b.ny[s] + R - 1) / R);
+    return strips >= (int64_t)nb * STRIP_WARPS * nsm;
+}
+
 template <int PREC>
 static cudaError_t launch_bs(BatchCtx &b)
 {
@@ -691,9 +709,10 @@ static cudaError_t batch_upload(BatchCtx &b, const std::vector<HostNet> &nets, c
     BT_TRY(cudaMemcpyAsync(b.tcoef, coef.data(), 4 * b.nphase * sizeof(double), cudaMemcpyHostToDevice, st));
     BT_TRY(cudaStreamSynchronize(st));
     // default schedule: largest specimens first, plain steps on 16-row
-    // strips in the fixed-point modes (what the autotuner picks on the
-    // benchmark's batches), 16-row tiles otherwise
-    BT_TRY(build_tiles(b, batch_strips_ok(b) ? -16 : 16, 1));
+    // strips in the fixed-point modes when the strips fill the device (what
+    // the autotuner picks on the benchmark's batches; a warp sweeping a strip
+    // is latency-bound when few run), 16-row tiles otherwise
+    BT_TRY(build_tiles(b, batch_strips_ok(b) && batch_strips_fill(b, 16) ? -16 : 16, 1));
     // initial acceleration of every specimen (vh = v + dt/2 a(0))
     {
         cudaError_t ei = launch_b<T_INIT, false>(b, 0, b.T);
