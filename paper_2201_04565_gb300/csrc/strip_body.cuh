@@ -178,23 +178,24 @@ __device__ __forceinline__ int strip_spring(const TileArgs &A, const PixFix &p, 
     return b ? S_BREAK : S_FORCE;
 }
 
-// The sample sums of one intact spring: potential energy 1/2 k (r - r0)^2
-// and the virial term d_x f_x (the tile kernel's terms). A lane sums a
-// whole column of its strip, so the double-float sums take the accurate
-// addition (a few units of 2^-48 relative per term) rather than the
-// one-TwoSum form a tile's two rows per thread can afford.
+// The sample sums of one intact spring: the potential energy and the
+// virial term d_x f_x (the tile kernel's terms). The double-float form sums
+// k (r - r0)^2, halved once at the end (exactly), with the one-TwoSum
+// addition: its error, a few units of 2^-48 of the terms' magnitudes per
+// addition, stays near 3e-12 of the sum over the up to ~200 terms a lane
+// accumulates along its strip.
 template <typename FT>
 __device__ __forceinline__ void spring_sample(ff &u, ff &w, const TypeDF &t, FT dx, FT fx, FT st);
 template <>
 __device__ __forceinline__ void spring_sample<ff>(ff &u, ff &w, const TypeDF &t, ff dx, ff fx, ff st)
 {
-    u = ff_add(u, ff_mul(ff_mul_f(t.k, 0.5f), ff_sqr(st)));
-    w = ff_add(w, ff_mul(dx, fx));
+    u = ff_add_sloppy(u, ff_mul(t.k, ff_sqr(st)));
+    w = ff_add_sloppy(w, ff_mul(dx, fx));
 }
 template <>
 __device__ __forceinline__ void spring_sample<float>(ff &u, ff &w, const TypeDF &t, float dx, float fx, float st)
 {
-    u = ff_add_f(u, 0.5f * t.k.hi * st * st);
+    u = ff_add_f(u, t.k.hi * st * st);
     w = ff_add_f(w, dx * fx);
 }
 
@@ -503,7 +504,7 @@ __device__ __forceinline__ void strip_run(const TileArgs &A, int R, int sx, int 
         const float tres = warp_max_f(resf);
         if (lane == 0) {
             A.part_s[part] = ff_to_double(tw);
-            A.part_s[A.ntiles + part] = ff_to_double(tu);
+            A.part_s[A.ntiles + part] = 0.5 * ff_to_double(tu);  // the 1/2 of 1/2 k (r - r0)^2, exact
             A.part_p[part] = ff_to_double(tm);
             A.part_p[A.ntiles + part] = ff_to_double(tk);
             A.part_p[2 * A.ntiles + part] = ff_to_double(tr);
