@@ -54,10 +54,10 @@ lsm_status lsm_batch_autotune(lsm_batch *b, int32_t steps_per_trial, int32_t *ti
 
 /* Set the schedule explicitly: tile_y 8, 16 or 32 (tiles of 32 columns and
  * that many rows, one CTA each), or -8, -16, -32 (F32 and DF modes, every
- * specimen below 2^29 pixels): the steps without a sample run as one warp
- * per strip of 30 owned columns and 8, 16 or 32 rows, the register-resident
- * sweep of the single-specimen strip kernel, while load increments and
- * sample steps keep 16-row tiles; the states are the same bits either way.
+ * specimen below 2^29 pixels): the time steps run as one warp per strip of
+ * 30 owned columns and 8, 16 or 32 rows, the register-resident sweep of the
+ * single-specimen strip kernel (sample sums per strip), while load
+ * increments keep 16-row tiles; the states are the same bits either way.
  * grid >= 0 (tiles only); order 0 or 1. LSM_EINVAL otherwise. A new batch
  * starts with strips of 16 rows (F32, DF, when they outnumber the warps the
  * device holds at once) or 16-row tiles, largest specimens first, grid 0. */

@@ -128,12 +128,14 @@ k_tile2d_batch(TileArgs base, const BatchTile *__restrict__ tiles, int64_t t0, i
     }
 }
 
-// A plain time step (no sample) of the batch on strips: one warp per strip
-// of 30 owned columns and R rows of one specimen (entries (spec, sx, sy) of
-// `strips`; the schedule's grid does not apply), the single-specimen strip
-// kernel's sweep on that specimen's arrays. Same states as the tile kernel, so the sample steps stay on the
-// tile list.
-template <int PREC>
+// A time step of the batch on strips: one warp per strip of 30 owned
+// columns and R rows of one specimen (entries (spec, sx, sy) of `strips`;
+// the schedule's grid does not apply), the single-specimen strip kernel's
+// sweep on that specimen's arrays; a sample step writes the strip's partial
+// sums at its index q in the strip list (stride base.ntiles, the number of
+// strips; each specimen's strips are contiguous, its range sbase/nstiles).
+// Same states as the tile kernel.
+template <int PREC, bool SAMPLE>
 __global__ void __launch_bounds__(32 * STRIP_WARPS, 5)
 k_strip2d_batch(TileArgs base, const BatchTile *__restrict__ strips, int64_t n, int R,
                 const SpecDesc *__restrict__ specs, double *X0, double *X1, double *V0, double *V1, double *VOBS,
@@ -168,7 +170,7 @@ k_strip2d_batch(TileArgs base, const BatchTile *__restrict__ strips, int64_t n, 
         A.nbroken = nb + st.spec;
         A.d_step = &specs[st.spec].steps;
         A.t_off = 0;
-        strip_run<PREC, false, false, 0, T_STEP>(A, R, st.bx, st.by * R, 0, sdf, scoef, smassf, soff);
+        strip_run<PREC, false, SAMPLE, 0, T_STEP>(A, R, st.bx, st.by * R, q, sdf, scoef, smassf, soff);
     }
 }
 
@@ -392,8 +394,10 @@ static cudaError_t build_tiles(BatchCtx &b, int ty, int order)
         sd[s].nstiles = (int64_t)tx * tys;
         for (int by = 0; by < tys; by++)
             for (int bx = 0; bx < tx; bx++) ts.push_back(BatchTile{s, bx, by, 0});
-        if (strip_r) {
+        if (strip_r) {  // the sample steps too: the specimen's strips give its partial sums
             const int nsx = (b.nx[s] + STRIP_OWN - 1) / STRIP_OWN, nsy = (b.ny[s] + strip_r - 1) / strip_r;
+            sd[s].sbase = (int64_t)sl.size();
+            sd[s].nstiles = (int64_t)nsx * nsy;
             for (int sy = 0; sy < nsy; sy++)
                 for (int sx = 0; sx < nsx; sx++) sl.push_back(BatchTile{s, sx, sy, 0});
         }
@@ -412,7 +416,7 @@ static cudaError_t build_tiles(BatchCtx &b, int ty, int order)
         b.NSTRIP = (int64_t)sl.size();
     }
     b.T = (int64_t)tl.size();
-    b.TS = (int64_t)ts.size();
+    b.TS = strip_r ? (int64_t)sl.size() : (int64_t)ts.size();  // partial sums per sample-step unit
     BT_TRY(balloc(&b.tiles, tl.size()));
     if (ty == TYS) {
         b.stiles = b.tiles;
@@ -420,8 +424,8 @@ static cudaError_t build_tiles(BatchCtx &b, int ty, int order)
         BT_TRY(balloc(&b.stiles, ts.size()));
         BT_TRY(cudaMemcpyAsync(b.stiles, ts.data(), ts.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b.stream));
     }
-    BT_TRY(balloc(&b.part_s, 2 * ts.size()));
-    BT_TRY(balloc(&b.part_p, 4 * ts.size()));
+    BT_TRY(balloc(&b.part_s, 2 * b.TS));
+    BT_TRY(balloc(&b.part_p, 4 * b.TS));
     BT_TRY(cudaMemcpyAsync(b.tiles, tl.data(), tl.size() * sizeof(BatchTile), cudaMemcpyHostToDevice, b.stream));
     BT_TRY(cudaMemcpyAsync(b.specs, sd.data(), b.S * sizeof(SpecDesc), cudaMemcpyHostToDevice, b.stream));
     BT_TRY(cudaStreamSynchronize(b.stream));
@@ -462,7 +466,7 @@ static TileArgs batch_base_args(BatchCtx &b)
     A.status = b.status;
     A.part_s = b.part_s;
     A.part_p = b.part_p;
-    A.ntiles = b.TS;  // partial sums come from the sample-step tile list
+    A.ntiles = b.TS;  // partial sums come from the sample-step tiles or strips
     return A;
 }
 
@@ -473,7 +477,7 @@ static bool batch_strips_fill(const BatchCtx &b, int R)
     int dev = 0, nsm = 0, nb = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_strip2d_batch<LSM_PREC_DF>, 32 * STRIP_WARPS, 0) !=
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_strip2d_batch<LSM_PREC_DF, false>, 32 * STRIP_WARPS, 0) !=
             cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -484,12 +488,12 @@ static bool batch_strips_fill(const BatchCtx &b, int R)
     return strips >= (int64_t)nb * STRIP_WARPS * nsm;
 }
 
-template <int PREC>
+template <int PREC, bool SAMPLE>
 static cudaError_t launch_bs(BatchCtx &b)
 {
     if (b.NSTRIP <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)((b.NSTRIP + STRIP_WARPS - 1) / STRIP_WARPS);  // one warp per strip
-    k_strip2d_batch<PREC><<<grid, 32 * STRIP_WARPS, 0, b.stream>>>(batch_base_args(b), b.strips, b.NSTRIP, b.strip_r,
+    k_strip2d_batch<PREC, SAMPLE><<<grid, 32 * STRIP_WARPS, 0, b.stream>>>(batch_base_args(b), b.strips, b.NSTRIP, b.strip_r,
                                                                     b.specs, b.X[0], b.X[1], b.VH[0], b.VH[1], b.VOBS,
                                                                     b.PH, b.MASK, b.BRK, b.fb, b.nb);
     b.launches += 1;
@@ -528,13 +532,13 @@ static cudaError_t launch_b(BatchCtx &b, int64_t t0, int64_t t1)
     case LSM_PREC_F32: return launch_bt<TYV, LSM_PREC_F32, MODE, SAMPLE>(b, TL, t0, t1);          \
     default: return launch_bt<TYV, LSM_PREC_DF, MODE, SAMPLE>(b, TL, t0, t1);                     \
     }
+    if (MODE == T_STEP && b.strip_r > 0) {  // time steps on strips
+        if (b.prec == LSM_PREC_F32) return launch_bs<LSM_PREC_F32, SAMPLE>(b);
+        return launch_bs<LSM_PREC_DF, SAMPLE>(b);
+    }
     if constexpr (SAMPLE) {
         BT_PREC(16, b.stiles)
     } else {
-        if (MODE == T_STEP && b.strip_r > 0) {  // the plain steps on strips
-            if (b.prec == LSM_PREC_F32) return launch_bs<LSM_PREC_F32>(b);
-            return launch_bs<LSM_PREC_DF>(b);
-        }
         if (b.tile_y == 8) { BT_PREC(8, b.tiles) }
         if (b.tile_y == 32) { BT_PREC(32, b.tiles) }
         BT_PREC(16, b.tiles)

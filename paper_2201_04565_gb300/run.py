@@ -212,7 +212,7 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--count", type=int, default=64, help="batch: number of specimens")
     ap.add_argument("--max-side", type=int, default=512, help="batch: largest specimen side")
-    ap.add_argument("--tile-y", type=int, default=16, help="batch: tile height (8, 16 or 32)")
+    ap.add_argument("--tile-y", type=int, default=16, help="batch: tile height (8, 16 or 32), or -8, -16, -32 for strips")
     ap.add_argument("--batch", type=int, default=8, help="unet: batch size")
     ap.add_argument("--iters", type=int, default=3, help="unet: training iterations; conv: timed calls per layer")
     ap.add_argument("--layer", type=int, default=-1, help="conv: only this convolution (0..13)")
