@@ -107,13 +107,12 @@ def algorithmic_bytes(n, m, dim):
 # keyed by precision mode, with the sha1 prefix of the kernel source it was
 # taken on; once the kernel changes, traffic reports null until re-measured.
 NCU_TRAFFIC = {
-    # profiles/time_step_per_mode_2d_2048_two_phase.md: ncu --metrics
-    # dram__bytes_read.sum,dram__bytes_write.sum on three time-step launches
-    # of each mode (the same 2048 x 2048 workload), mean
-    "df64": (238.5e6, "d2f239a7a909"),
-    "f32": (240.0e6, "d2f239a7a909"),
-    "fast64": (236.3e6, "d2f239a7a909"),
-    "exact64": (236.5e6, "d2f239a7a909"),
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on three
+    # time-step launches of each mode (the same 2048 x 2048 workload), mean
+    "df64": (238.5e6, "327784ee7cef"),
+    "f32": (240.1e6, "327784ee7cef"),
+    "fast64": (236.3e6, "327784ee7cef"),
+    "exact64": (236.9e6, "327784ee7cef"),
 }
 
 # Warp instructions executed by one time-step launch (ncu smsp__inst_executed.sum,
@@ -122,10 +121,10 @@ NCU_TRAFFIC = {
 # this gives the instruction-issue roofline, the one the fixed-point modes
 # are bound by.
 NCU_INSTRUCTIONS = {
-    "df64": (110408352, "d2f239a7a909"),
-    "f32": (75982754, "d2f239a7a909"),
-    "fast64": (94464248, "d2f239a7a909"),
-    "exact64": (195572908, "d2f239a7a909"),
+    "df64": (110408352, "327784ee7cef"),
+    "f32": (75982754, "327784ee7cef"),
+    "fast64": (94464248, "327784ee7cef"),
+    "exact64": (195572908, "327784ee7cef"),
 }
 
 # Binding unit of each mode's time-step kernel, from ncu on the same workload
