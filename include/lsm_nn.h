@@ -87,7 +87,10 @@ lsm_status lsm_unet_prediction_to_displacement(const float *pred, float deps, in
 /* The implicit-GEMM convolution kernels on their own (tests):
  * out[b,y,x,out_c0+n] = act(bias[n] + sum_{tap,ci} in[b,y+dy,x+dx,in_c0+ci] W[n][tap][ci])
  * (taps 9: 3x3 with zero padding; taps 1: 1x1), NHWC bf16 with channel
- * strides in_cs/out_cs; Cin, Cout multiples of 32; relu 0/1. */
+ * strides in_cs/out_cs; Cin, Cout multiples of 32; relu 0/1. Channel
+ * strides and offsets are multiples of 8 and bias (fp32, device, may be
+ * NULL) is 16-byte aligned, else LSM_EINVAL; the output tile is staged in
+ * shared memory and written by TMA stores. */
 lsm_status lsm_nn_conv_forward(const void *in, int32_t in_cs, int32_t in_c0, int32_t Cin, const void *W,
                                const float *bias, void *out, int32_t out_cs, int32_t out_c0, int32_t Cout, int32_t B,
                                int32_t H, int32_t Wd, int32_t taps, int32_t relu, void *stream);

@@ -110,6 +110,24 @@ __device__ __forceinline__ void tma_prefetch(const CUtensorMap *map)
 {
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
 }
+// TMA tile store from this CTA's shared memory (bulk async-group completion);
+// the part of the box outside the tensor is not written
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, unsigned src, int c0, int c1, int c2, int c3)
+{
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(
+                     (uint64_t)map),
+                 "r"(src), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// at most one of this thread's bulk groups still reading shared memory
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// every bulk group of this thread complete (writes performed)
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// this thread's shared-memory writes made visible to the TMA (async proxy)
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// barrier 1 over the 128 epilogue threads (barrier 0 is __syncthreads)
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: start address, leading and stride byte
 // offsets (16-byte units), descriptor version 1 (bit 46), swizzle mode in
@@ -145,6 +163,18 @@ __device__ __forceinline__ void mma_commit(unsigned bar)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
 }
+
+// 32 lanes x 16 columns of FP32 from TMEM (this warp's lane quarter), not
+// waited for (tmem_wait_ld before the registers are read)
+__device__ __forceinline__ void tmem_ld16_nw(unsigned addr, unsigned *v)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(addr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // 32 lanes x 16 columns of FP32 from TMEM (this warp's lane quarter)
 __device__ __forceinline__ void tmem_ld16(unsigned addr, unsigned *v)
@@ -204,43 +234,79 @@ __host__ __device__ constexpr int fwd_stages(int BN, int KC)
     return (196608 / ((128 + BN) * KC * 2)) < 8 ? (196608 / ((128 + BN) * KC * 2)) : 8;
 }
 
+// Output staging of the epilogue: blocks of SB = min(BN, 64) channels of the
+// tile's 128 pixels, in two alternating shared-memory buffers, each stored
+// by one TMA copy (box SB channels x bx x by).
+__host__ __device__ constexpr int out_block(int BN) { return BN < 64 ? BN : 64; }
+__host__ __device__ constexpr unsigned out_staging(int BN) { return 2u * 128u * (unsigned)out_block(BN) * 2u; }
+
 template <int BN, int KC>
 struct FwdCfg {
     static constexpr int S = fwd_stages(BN, KC);
     static constexpr unsigned ROW = KC * 2;  // bytes per operand row: one swizzle width
     static constexpr unsigned A_BYTES = 128 * ROW, B_BYTES = BN * ROW, STAGE = A_BYTES + B_BYTES;
-    static constexpr unsigned SMEM = S * STAGE + 1024;  // + slack to align the ring to 1024 bytes
-    static constexpr unsigned SW = KC == 64 ? 2u : 4u;   // 128- or 64-byte swizzle
+    // ring, output staging, + slack to align the ring to 1024 bytes
+    static constexpr unsigned SMEM = S * STAGE + out_staging(BN) + 1024;
+    static constexpr unsigned SW = KC == 64 ? 2u : 4u;  // 128- or 64-byte swizzle
 };
 
-// Epilogue of one output pixel (b, y, x) of a tile, this thread's TMEM lane
-// (taddr: its first accumulator column): bias, ReLU, BF16 stores of BN
-// channels from n0; nothing is stored for a pixel outside the image.
+// Epilogue of one tile, run by the 128 epilogue threads; this thread holds
+// pixel m of the tile (TMEM lane m, taddr: its lane quarter's first
+// accumulator column). Per block of SB channels: the accumulator columns
+// (all loads issued, one wait), bias and ReLU, BF16 into a staging buffer
+// in the TMA's swizzled layout (16-byte chunk j of row m at chunk j ^ (m & 7)
+// for 128-byte rows, j ^ ((m >> 1) & 3) for 64-byte rows), then thread 0 of
+// the group stores the block with one TMA copy at (n0 + block, x0, y0, b),
+// which leaves out the pixels outside the image. The two staging buffers
+// alternate (`blk` counts the blocks this thread has staged); before one is
+// rewritten, the copy that read it two blocks earlier must have finished
+// reading (wait_group.read 1).
 template <int BN>
-__device__ __forceinline__ void fwd_store_row(unsigned taddr, bf16 *__restrict__ out, int out_cs, int out_c0, int n0,
-                                              const float *__restrict__ bias, int relu, int b, int x, int y, int H,
-                                              int Wd)
+__device__ __forceinline__ void fwd_epilogue(unsigned taddr, unsigned stage, const CUtensorMap *tm_out, int n0,
+                                             const float *__restrict__ bias, int relu, int b, int x0, int y0, int m,
+                                             bool leader, int &blk)
 {
-    const bool v = x < Wd && y < H;
-    bf16 *dst = out + ((int64_t)(b * H + y) * Wd + x) * out_cs + out_c0 + n0;
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-        unsigned r[16];
-        tmem_ld16(taddr + (unsigned)c0, r);  // the whole warp, converged
-        if (v) {
-            __align__(16) __nv_bfloat162 h[8];
+    constexpr int SB = out_block(BN), CH = SB / 8;  // channels per block, 16-byte chunks per row
+    constexpr unsigned RB = SB * 2, BUF = 128u * RB;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += SB, blk++) {
+        unsigned r[SB];
 #pragma unroll
-            for (int j = 0; j < 8; j++) {
-                float v0 = __uint_as_float(r[2 * j]) + (bias ? bias[n0 + c0 + 2 * j] : 0.0f);
-                float v1 = __uint_as_float(r[2 * j + 1]) + (bias ? bias[n0 + c0 + 2 * j + 1] : 0.0f);
+        for (int c = 0; c < SB; c += 16) tmem_ld16_nw(taddr + (unsigned)(c0 + c), r + c);
+        float4 bv[SB / 4];
+#pragma unroll
+        for (int k = 0; k < SB / 4; k++)
+            bv[k] = bias ? __ldg((const float4 *)(bias + n0 + c0) + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        tmem_wait_ld();
+        if (leader) bulk_wait_read1();
+        epi_bar();  // the buffer of this block is free
+        const unsigned buf = stage + (unsigned)(blk & 1) * BUF + (unsigned)m * RB;
+#pragma unroll
+        for (int j = 0; j < CH; j++) {
+            const float *bj = reinterpret_cast<const float *>(bv) + 8 * j;
+            unsigned w[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                float v0 = __uint_as_float(r[8 * j + 2 * e]) + bj[2 * e];
+                float v1 = __uint_as_float(r[8 * j + 2 * e + 1]) + bj[2 * e + 1];
                 if (relu) {
                     v0 = fmaxf(v0, 0.0f);
                     v1 = fmaxf(v1, 0.0f);
                 }
-                h[j] = __floats2bfloat162_rn(v0, v1);
+                const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                w[e] = *reinterpret_cast<const unsigned *>(&h);
             }
-            uint4 *o = (uint4 *)(dst + c0);
-            o[0] = *(const uint4 *)&h[0];
-            o[1] = *(const uint4 *)&h[4];
+            const unsigned sw = SB == 64 ? (unsigned)(m & 7) : (unsigned)((m >> 1) & 3);
+            const unsigned a = buf + (((unsigned)j ^ sw) << 4);
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]),
+                         "r"(w[3])
+                         : "memory");
+        }
+        fence_proxy_async();
+        epi_bar();  // the block is staged
+        if (leader) {
+            tma_store_4d(tm_out, stage + (unsigned)(blk & 1) * BUF, n0 + c0, x0, y0, b);
+            bulk_commit();
         }
     }
 }
@@ -250,7 +316,7 @@ __device__ __forceinline__ void fwd_store_row(unsigned taddr, bf16 *__restrict__
 template <int BN, int KC>
 __global__ void __launch_bounds__(FW_THREADS, 1)
 k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_w,
-              const float *__restrict__ bias, bf16 *__restrict__ out, int out_cs, int out_c0, int Cout, int Cin,
+              const __grid_constant__ CUtensorMap tm_out, const float *__restrict__ bias, bf16 *__restrict__ out, int out_cs, int out_c0, int Cout, int Cin,
               int B, int H, int Wd, int taps, int relu, int bx, int by, int ntx, int nty)
 {
     using C = FwdCfg<BN, KC>;
@@ -258,7 +324,7 @@ k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__
     extern __shared__ unsigned char fw_smem[];
     __shared__ __align__(8) uint64_t full[S], empty[S], tfull[2], tempty[2], drain;
     __shared__ unsigned tbase;
-    __shared__ int s_abort;
+    __shared__ int s_abort, s_eok;
     volatile int *abort = &s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) s_abort = 0;
@@ -280,6 +346,7 @@ k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__
     __syncthreads();
     tc_fence_after();
     const unsigned tmem = tbase;
+    const unsigned ostage = ring + (unsigned)S * C::STAGE;  // output staging (1024-byte aligned)
     const int kch = Cin / KC, KT = taps * kch;
     const int nnt = Cout / BN, ntiles = ntx * nty * B * nnt;
     const int limit = g_conv_wait_limit;
@@ -347,26 +414,29 @@ k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__
     } else {
         // warps 2-5: TMEM lane quarter warp % 4 holds tile rows 32 (warp % 4) + lane
         const int q = warp & 3, m = 32 * q + lane;
-        int tc = 0;
+        const bool leader = warp == 2 && lane == 0;  // issues the group's TMA stores
+        int tc = 0, blk = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, tc++) {
             const int acc = tc & 1, ua = tc >> 1;
-            int ok = 1;
-            if (lane == 0) ok = mbar_wait(cv_smem_u32(&tfull[acc]), (unsigned)(ua & 1), limit, abort);
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) {
-                if (lane == 0) give_up(abort);
+            // one wait for the four warps, so that all of them take the same
+            // branch (the epilogue's named barriers need all 128 threads)
+            if (leader) s_eok = mbar_wait(cv_smem_u32(&tfull[acc]), (unsigned)(ua & 1), limit, abort) ? 1 : 0;
+            epi_bar();
+            if (!*(volatile int *)&s_eok) {
+                if (leader) give_up(abort);
                 break;
             }
             tc_fence_after();
             const int mt = t / nnt, n0 = (t - mt * nnt) * BN;
             int b, y0, x0;
             patch_of(mt, ntx, nty, bx, by, b, y0, x0);
-            fwd_store_row<BN>(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(acc * BN), out, out_cs, out_c0, n0, bias,
-                              relu, b, x0 + (m & (bx - 1)), y0 + m / bx, H, Wd);  // bx: a power of two
+            fwd_epilogue<BN>(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(acc * BN), ostage, &tm_out, n0, bias,
+                             relu, b, x0, y0, m, leader, blk);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(cv_smem_u32(&tempty[acc]));  // the accumulator may be overwritten
         }
+        if (leader) bulk_wait_all();  // the output stores are done before the CTA ends
     }
     __syncthreads();
     if (s_abort) {
@@ -407,14 +477,14 @@ constexpr int HL_MAXST = 4;
 template <int BN, int KC>
 __global__ void __launch_bounds__(FW_THREADS, 1)
 k_conv_fwd_halo(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_w,
-                const float *__restrict__ bias, bf16 *__restrict__ out, int out_cs, int out_c0, int Cout, int Cin,
+                const __grid_constant__ CUtensorMap tm_out, const float *__restrict__ bias, bf16 *__restrict__ out, int out_cs, int out_c0, int Cout, int Cin,
                 int B, int H, int Wd, int relu, int bx, int by, int ntx, int nty, int S)
 {
     constexpr unsigned ROW = KC * 2, SW = KC == 64 ? 2u : 4u, WBLK = BN * ROW;
     extern __shared__ unsigned char hl_smem[];
     __shared__ __align__(8) uint64_t full[HL_MAXST], empty[HL_MAXST], tfull[2], tempty[2], wfull, drain;
     __shared__ unsigned tbase;
-    __shared__ int s_abort;
+    __shared__ int s_abort, s_eok;
     volatile int *abort = &s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) s_abort = 0;
@@ -422,6 +492,7 @@ k_conv_fwd_halo(const __grid_constant__ CUtensorMap tm_in, const __grid_constant
     const unsigned wres = (cv_smem_u32(hl_smem) + 1023u) & ~1023u;  // resident weights
     const unsigned dxbuf = (unsigned)(bx * (by + 2)) * ROW, abytes = 3 * dxbuf;
     const unsigned ring = wres + 9u * (unsigned)nch * WBLK;
+    const unsigned ostage = ring + (unsigned)S * abytes;  // output staging (1024-byte aligned)
     if (warp == 0) tmem_alloc(&tbase, 2 * BN);
     if (tid == 32) {
         for (int q = 0; q < S; q++) {
@@ -518,25 +589,28 @@ k_conv_fwd_halo(const __grid_constant__ CUtensorMap tm_in, const __grid_constant
         }
     } else {
         const int q = warp & 3, m = 32 * q + lane;
-        int tc = 0;
+        const bool leader = warp == 2 && lane == 0;  // issues the group's TMA stores
+        int tc = 0, blk = 0;
         for (int mt = mt0; mt < nmt; mt += mstep, tc++) {
             const int acc = tc & 1, ua = tc >> 1;
-            int ok = 1;
-            if (lane == 0) ok = mbar_wait(cv_smem_u32(&tfull[acc]), (unsigned)(ua & 1), limit, abort);
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) {
-                if (lane == 0) give_up(abort);
+            // one wait for the four warps, so that all of them take the same
+            // branch (the epilogue's named barriers need all 128 threads)
+            if (leader) s_eok = mbar_wait(cv_smem_u32(&tfull[acc]), (unsigned)(ua & 1), limit, abort) ? 1 : 0;
+            epi_bar();
+            if (!*(volatile int *)&s_eok) {
+                if (leader) give_up(abort);
                 break;
             }
             tc_fence_after();
             int b, y0, x0;
             patch_of(mt, ntx, nty, bx, by, b, y0, x0);
-            fwd_store_row<BN>(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(acc * BN), out, out_cs, out_c0, n0, bias,
-                              relu, b, x0 + (m & (bx - 1)), y0 + m / bx, H, Wd);
+            fwd_epilogue<BN>(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(acc * BN), ostage, &tm_out, n0, bias,
+                             relu, b, x0, y0, m, leader, blk);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(cv_smem_u32(&tempty[acc]));
         }
+        if (leader) bulk_wait_all();  // the output stores are done before the CTA ends
     }
     __syncthreads();
     if (s_abort) {
@@ -867,10 +941,14 @@ static cudaError_t launch_fwd(const CUtensorMap &ti, const CUtensorMap &tw, cons
     static bool attr = false;
     cudaError_t e = smem_attr(k_conv_fwd_tc<BN, KC>, FwdCfg<BN, KC>::SMEM, attr);
     if (e != cudaSuccess) return e;
+    CUtensorMap to;  // output: blocks of out_block(BN) channels x the tile's patch
+    e = act_map(&to, out + out_c0, Cout, out_cs, B, H, Wd, out_block(BN), bx, by);
+    if (e != cudaSuccess) return e;
     const int64_t ntiles = (int64_t)ntx * nty * B * (Cout / BN);
     const int grid = (int)std::min<int64_t>(ntiles, sm_count());
-    k_conv_fwd_tc<BN, KC><<<grid, FW_THREADS, FwdCfg<BN, KC>::SMEM, st>>>(ti, tw, bias, out, out_cs, out_c0, Cout,
-                                                                         Cin, B, H, Wd, taps, relu, bx, by, ntx, nty);
+    k_conv_fwd_tc<BN, KC><<<grid, FW_THREADS, FwdCfg<BN, KC>::SMEM, st>>>(ti, tw, to, bias, out, out_cs, out_c0,
+                                                                         Cout, Cin, B, H, Wd, taps, relu, bx, by, ntx,
+                                                                         nty);
     return cudaGetLastError();
 }
 
@@ -878,12 +956,13 @@ static cudaError_t launch_fwd(const CUtensorMap &ti, const CUtensorMap &tw, cons
 // fit with two stages).
 static unsigned halo_smem(int Cin, int BN, int KC, int bx, int by, int &S)
 {
-    const unsigned budget = 227u * 1024u - 1024u - 256u;  // less alignment slack and static barriers
+    // less alignment slack, static barriers and the output staging
+    const unsigned budget = 227u * 1024u - 1024u - 256u - out_staging(BN);
     const unsigned wbytes = 9u * (unsigned)(Cin / KC) * (unsigned)(BN * KC * 2);
     const unsigned abytes = 3u * (unsigned)(bx * (by + 2) * KC * 2);
     if (wbytes + 2 * abytes > budget) return 0;
     S = (int)std::min<unsigned>(HL_MAXST, (budget - wbytes) / abytes);
-    return 1024u + wbytes + (unsigned)S * abytes;
+    return 1024u + wbytes + (unsigned)S * abytes + out_staging(BN);
 }
 
 template <int BN, int KC>
@@ -902,12 +981,13 @@ static cudaError_t launch_halo(const bf16 *in, int in_cs, int in_c0, int Cin, co
     const int64_t nmt = (int64_t)ntx * nty * B;
     const int nnt = Cout / BN;
     const int per = (int)std::min<int64_t>(nmt, std::max(1, sm_count() / nnt));
-    CUtensorMap ti, tw;
+    CUtensorMap ti, tw, to;
     cudaError_t e = act_map(&ti, in + in_c0, Cin, in_cs, B, H, Wd, KC, bx, by + 2);
     if (e == cudaSuccess) e = weight_map(&tw, W, 9 * Cin, Cout, KC, BN);
+    if (e == cudaSuccess) e = act_map(&to, out + out_c0, Cout, out_cs, B, H, Wd, out_block(BN), bx, by);
     if (e != cudaSuccess) return e;
-    k_conv_fwd_halo<BN, KC><<<nnt * per, FW_THREADS, smem, st>>>(ti, tw, bias, out, out_cs, out_c0, Cout, Cin, B, H,
-                                                                 Wd, relu, bx, by, ntx, nty, S);
+    k_conv_fwd_halo<BN, KC><<<nnt * per, FW_THREADS, smem, st>>>(ti, tw, to, bias, out, out_cs, out_c0, Cout, Cin, B,
+                                                                 H, Wd, relu, bx, by, ntx, nty, S);
     return cudaGetLastError();
 }
 
@@ -916,6 +996,7 @@ cudaError_t conv_fwd(const bf16 *in, int in_cs, int in_c0, int Cin, const bf16 *
 {
     if (Cin % 32 || Cout % 32 || (in_cs | in_c0 | out_cs | out_c0) % 8 || (taps != 1 && taps != 9))
         return cudaErrorInvalidValue;
+    if ((uintptr_t)bias % 16) return cudaErrorInvalidValue;  // read as float4
     if ((int64_t)B * H * Wd == 0) return cudaSuccess;
     const int KC = Cin % 64 == 0 ? 64 : 32, BN = tile_n(Cout);
     if (taps == 9 && BN <= 64) {  // the halo variant where its weight block fits

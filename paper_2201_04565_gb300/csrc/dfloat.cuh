@@ -314,13 +314,16 @@ __device__ __forceinline__ ff ff_norm3_un(ff a, ff b, ff c)
     return ff{t.hi, __fadd_rn(__fadd_rn(t.lo, s.lo), l)};
 }
 
-// a > b for an unnormalised a and a double-float b: the sign of (a.hi -
-// b.hi) + (a.lo - b.lo). Near a tie a.hi - b.hi is exact (Sterbenz: the two
-// lie within a factor 2), so the decision is resolved to the low parts'
-// precision, about 2^-46 relative; far from a tie the high parts decide.
+// a > b for an unnormalised a and a double-float b: the sign of X + Y with
+// X = fl(a.hi - b.hi), Y = fl(a.lo - b.lo), taken as the exact comparison
+// X > -Y (the rounded sum fl(X + Y) has the sign of X + Y, so this is the
+// same decision in one operation fewer). Near a tie a.hi - b.hi is exact
+// (Sterbenz: the two lie within a factor 2), so the decision is resolved to
+// the low parts' precision, about 2^-46 relative; far from a tie the high
+// parts decide.
 __device__ __forceinline__ bool ff_gt_un(ff a, ff b)
 {
-    return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo)) > 0.0f;
+    return __fsub_rn(a.hi, b.hi) > __fsub_rn(b.lo, a.lo);
 }
 
 // The spring factor g = 1 - r0 / r from r^2 (double-float) and r0, with
