@@ -254,6 +254,26 @@ lsm_status lsm_sample_last(lsm_ctx *ctx, lsm_sample *out);
 lsm_status lsm_broken_mask(lsm_ctx *ctx, uint8_t *out, int64_t cap, int64_t *m,
                            int64_t *first_break_step);
 
+/* Pipelined readback of a loading loop's results (no counterpart in the
+ * paper, whose program reads its outputs between steps): enqueues, behind
+ * the work already on the context's stream, a snapshot of the canonical
+ * broken-spring mask (as lsm_broken_mask) and a copy of it into out_mask
+ * (cap >= m bytes) and of the most recent sample (as lsm_sample_last) into
+ * *out_sample, and returns without synchronising. The copies run on a
+ * second stream of the context and overlap the steps enqueued after this
+ * call; the host buffers hold the results once lsm_readback_wait returns
+ * (page-locked buffers for the overlap; pageable ones make the copy
+ * synchronous). Two snapshots alternate: the third call's snapshot waits,
+ * on the device, for the first call's copy. out_mask or out_sample may be
+ * NULL (not both); the buffers must stay valid and unread until
+ * lsm_readback_wait. Errors: LSM_EINVAL (null or short buffers, no sample
+ * yet), LSM_ECUDA; a pending device status is reported by lsm_readback_wait. */
+lsm_status lsm_readback_async(lsm_ctx *ctx, uint8_t *out_mask, int64_t cap, lsm_sample *out_sample);
+
+/* Wait for every readback enqueued by lsm_readback_async, then report a
+ * pending device status (LSM_ENONFINITE) like the synchronising calls. */
+lsm_status lsm_readback_wait(lsm_ctx *ctx);
+
 /* Per-spring step index of the break (-1 = intact), canonical order, m
  * entries. Synchronises. */
 lsm_status lsm_break_steps(lsm_ctx *ctx, int64_t *out, int64_t cap);

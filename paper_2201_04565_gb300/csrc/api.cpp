@@ -103,6 +103,8 @@ lsm_status ensure_sample_room(Ctx *c)
     e = cudaMemcpyAsync(ns, c->samples, c->sample_cap * sizeof(lsm::DeviceSample),
                         cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    // a readback in flight may still copy a sample out of the old buffer
+    if (e == cudaSuccess && c->rb_stream) e = cudaStreamSynchronize(c->rb_stream);
     if (e != cudaSuccess) {
         cudaFree(ns);
         return cuda_fail(c, e, "sample buffer growth");
@@ -377,6 +379,66 @@ lsm_status lsm_broken_mask(lsm_ctx *c, uint8_t *out, int64_t cap, int64_t *m,
     if (m) *m = c->m;
     if (first_break_step) *first_break_step = fb == ~0ull ? -1 : (int64_t)fb;
     return LSM_OK;
+}
+
+lsm_status lsm_readback_async(lsm_ctx *c, uint8_t *out_mask, int64_t cap, lsm_sample *out_sample)
+{
+    lsm::NvtxRange nvtx_("lsm_readback_async");
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    if ((!out_mask && !out_sample) || (out_mask && cap < c->m))
+        return fail(c, LSM_EINVAL, "need a mask buffer of at least m bytes or a sample");
+    if (out_sample && c->nsamples < 1) return fail(c, LSM_EINVAL, "no sample recorded yet");
+    cudaError_t e = cudaSuccess;
+    if (!c->rb_stream) {
+        e = cudaStreamCreateWithFlags(&c->rb_stream, cudaStreamNonBlocking);
+        for (int k = 0; k < 2 && e == cudaSuccess; k++) {
+            e = cudaEventCreateWithFlags(&c->rb_ready[k], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->rb_done[k], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "readback setup");
+    }
+    const int k = (int)(c->rb_count & 1);
+    if (out_mask && c->m && !c->rb_buf[k]) {
+        e = lsm::dev_malloc((void **)&c->rb_buf[k], c->m);
+        if (e != cudaSuccess) return cuda_fail(c, e, "readback buffer");
+    }
+    // the snapshot of two readbacks ago must be copied out before it is
+    // rewritten: the context's stream waits for it on the device
+    if (c->rb_used[k]) e = cudaStreamWaitEvent(c->stream, c->rb_done[k], 0);
+    if (e == cudaSuccess && out_mask && c->m) {
+        if (c->tile) {
+            // the export kernel writes the canonical mask straight into the
+            // snapshot (its staging pointer is swapped for the call)
+            uint8_t *staging = c->texport;
+            c->texport = c->rb_buf[k];
+            e = lsm::tile_export(*c, false);
+            c->texport = staging;
+        } else {
+            e = cudaMemcpyAsync(c->rb_buf[k], c->state, c->m, cudaMemcpyDeviceToDevice, c->stream);
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(c->rb_ready[k], c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->rb_stream, c->rb_ready[k], 0);
+    if (e == cudaSuccess && out_mask && c->m)
+        e = cudaMemcpyAsync(out_mask, c->rb_buf[k], c->m, cudaMemcpyDeviceToHost, c->rb_stream);
+    if (e == cudaSuccess && out_sample)
+        e = cudaMemcpyAsync(out_sample, c->samples + (c->nsamples - 1), sizeof(lsm_sample), cudaMemcpyDeviceToHost,
+                            c->rb_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->rb_done[k], c->rb_stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "readback_async");
+    c->rb_used[k] = true;
+    c->rb_count++;
+    return LSM_OK;
+}
+
+lsm_status lsm_readback_wait(lsm_ctx *c)
+{
+    if (!c) return fail(nullptr, LSM_EINVAL, "null context");
+    if (c->rb_stream) {
+        const cudaError_t e = cudaStreamSynchronize(c->rb_stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "readback_wait");
+    }
+    return device_status(c);
 }
 
 lsm_status lsm_break_steps(lsm_ctx *c, int64_t *out, int64_t cap)

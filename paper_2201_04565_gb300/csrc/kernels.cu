@@ -397,6 +397,19 @@ void free_device(Ctx &c)
     fields_free(c);
     for (auto &kv : c.graphs) cudaGraphExecDestroy(kv.second);
     c.graphs.clear();
+    if (c.rb_stream) {
+        cudaStreamSynchronize(c.rb_stream);
+        cudaStreamDestroy(c.rb_stream);
+        c.rb_stream = nullptr;
+    }
+    for (int k = 0; k < 2; k++) {
+        if (c.rb_buf[k]) cudaFree(c.rb_buf[k]);
+        if (c.rb_ready[k]) cudaEventDestroy(c.rb_ready[k]);
+        if (c.rb_done[k]) cudaEventDestroy(c.rb_done[k]);
+        c.rb_buf[k] = nullptr;
+        c.rb_ready[k] = c.rb_done[k] = nullptr;
+        c.rb_used[k] = false;
+    }
     void *ptrs[] = {c.x, c.v, c.a, c.mass, c.Xx, c.fixm, c.grip, c.si, c.sj, c.stype, c.types,
                     c.state, c.brk, c.row, c.inc, c.fs, c.part_s, c.part_p, c.d_step,
                     c.d_first_break, c.d_nbroken, c.d_status, c.d_eps, c.d_nsamples, c.samples,

@@ -201,6 +201,15 @@ struct Ctx {
     int64_t *fpix = nullptr;              // [n] pixel of each particle
     uint8_t *texport = nullptr;           // [m] staging for canonical-order exports
     long long *texport_brk = nullptr;     // [m] staging for break steps
+
+    // asynchronous readback (lsm_readback_async): a second stream for the
+    // device-to-host copies, two device snapshots of the canonical mask with
+    // their events (ready: snapshot written on `stream`; done: copied out)
+    cudaStream_t rb_stream = nullptr;
+    uint8_t *rb_buf[2] = {nullptr, nullptr};
+    cudaEvent_t rb_ready[2] = {nullptr, nullptr}, rb_done[2] = {nullptr, nullptr};
+    bool rb_used[2] = {false, false};
+    int64_t rb_count = 0;
     int tcur = 0;
     int64_t ntiles = 0;
 

@@ -73,6 +73,8 @@ SIGNATURES = [
     ("lsm_samples", C.c_int, [_P, _P, _I64, _P]),
     ("lsm_sample_last", C.c_int, [_P, C.POINTER(lsm_sample)]),
     ("lsm_broken_mask", C.c_int, [_P, _P, _I64, _P, _P]),
+    ("lsm_readback_async", C.c_int, [_P, _P, _I64, _P]),
+    ("lsm_readback_wait", C.c_int, [_P]),
     ("lsm_break_steps", C.c_int, [_P, _P, _I64]),
     ("lsm_get_state", C.c_int, [_P, _P, _P]),
     ("lsm_set_state", C.c_int, [_P, _P, _P]),
@@ -249,6 +251,32 @@ def lsm_broken_mask(h, out=None):
     return out[:m], fb.value
 
 
+def lsm_readback_async(h, out_mask=None, out_sample=None):
+    """Enqueue the canonical broken mask into out_mask (contiguous uint8 host
+    array of at least m entries) and the latest sample into out_sample (a
+    writable host buffer of 64 bytes, e.g. a uint8 array); both page-locked
+    for the copies to overlap later steps. Returns at once; the buffers hold
+    the results after lsm_readback_wait, and must be kept alive until then."""
+    _, m, _ = lsm_sizes(h)
+    if out_mask is not None and (out_mask.dtype != np.uint8 or out_mask.ndim != 1 or
+                                 not out_mask.flags.c_contiguous or out_mask.size < max(m, 1)):
+        raise ValueError("out_mask must be a contiguous uint8 array of at least %d entries" % max(m, 1))
+    if out_sample is not None and (not out_sample.flags.c_contiguous or out_sample.nbytes < C.sizeof(lsm_sample)
+                                   or not out_sample.flags.writeable):
+        raise ValueError("out_sample must be a writable contiguous buffer of %d bytes" % C.sizeof(lsm_sample))
+    cap = 0 if out_mask is None else out_mask.size
+    _check(load_library().lsm_readback_async(h, _ptr(out_mask), cap, _ptr(out_sample)), h)
+
+
+def lsm_readback_wait(h):
+    _check(load_library().lsm_readback_wait(h), h)
+
+
+def sample_from_buffer(buf):
+    """The lsm_sample record in a host buffer filled by lsm_readback_async."""
+    return lsm_sample.from_buffer_copy(bytes(memoryview(buf).cast("B")[:C.sizeof(lsm_sample)])).as_dict()
+
+
 def lsm_break_steps(h):
     _, m, _ = lsm_sizes(h)
     out = np.empty(max(m, 1), np.int64)
@@ -388,6 +416,12 @@ class Specimen:
 
     def broken(self, out=None):
         return lsm_broken_mask(self.h, out)
+
+    def readback_async(self, out_mask=None, out_sample=None):
+        lsm_readback_async(self.h, out_mask, out_sample)
+
+    def readback_wait(self):
+        lsm_readback_wait(self.h)
 
     def break_steps(self):
         return lsm_break_steps(self.h)
