@@ -8,7 +8,7 @@ bad arguments are refused."""
 import numpy as np
 import pytest
 
-from gen.images import inclusion_image, two_phase_materials
+from gen.images import foam_volume, inclusion_image, one_phase_materials, two_phase_materials
 
 pytestmark = pytest.mark.gpu
 
@@ -24,16 +24,23 @@ def env():
     return torch, lsm
 
 
-def _spec(lsm, path, prec="df64"):
+def _spec(lsm, path, prec="df64", kind="2d"):
+    if kind == "3d":
+        img = foam_volume(14, 1.5, 0.6, seed=21)
+        k, e, m = one_phase_materials(1.0, 0.02)
+        return lsm.Specimen.from_image(img, k, e, m, precision=prec, path=path)
     img = inclusion_image(48, 40, 3.0, 6.0, 0.3, 11)
     k, e, m = two_phase_materials()
-    return lsm.Specimen.from_image(img, k, e, m, precision=prec, path=path)
+    return lsm.Specimen.from_image(img, k, e, m, precision=prec, path=path, lattice=1 if kind == "tri" else 0)
 
 
-@pytest.mark.parametrize("path,prec", [(0, "df64"), (0, "exact64"), (1, "df64"), (3, "f32")])
-def test_readback_matches_synchronous_calls(env, path, prec):
+@pytest.mark.parametrize("path,prec,kind", [(0, "df64", "2d"), (0, "exact64", "2d"), (1, "df64", "2d"),
+                                            (3, "f32", "2d"), (0, "df64", "tri"), (0, "df64", "3d")])
+def test_readback_matches_synchronous_calls(env, path, prec, kind):
+    """2D tile kernel (df64, exact64), spring-list kernels, strip kernel,
+    triangular packing (strip kernel on its site grid), 3D voxel tile kernel."""
     torch, lsm = env
-    a, b = _spec(lsm, path, prec), _spec(lsm, path, prec)  # pipelined / synchronous twins
+    a, b = _spec(lsm, path, prec, kind), _spec(lsm, path, prec, kind)  # pipelined / synchronous twins
     n_inc, nst, deps = 12, 20, 0.01  # large increments: springs break within the run
     masks = [torch.empty(max(a.m, 1), dtype=torch.uint8, pin_memory=True).numpy() for _ in range(n_inc)]
     samples = [torch.empty(64, dtype=torch.uint8, pin_memory=True).numpy() for _ in range(n_inc)]
