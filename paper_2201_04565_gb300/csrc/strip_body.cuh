@@ -112,22 +112,18 @@ __device__ __forceinline__ double site_X(const TileArgs &A, int gx, int par)
 
 // Drift (time steps only): the position moved by dt vh on free components;
 // a grip (first or last site of its row, row length C) keeps its x, or
-// follows the constant strain rate.
+// follows the constant strain rate (rate_x: this lane's grip x at the strain
+// of this step for the row's parity, from strip_rate_x).
 template <bool RATE, bool SAMPLE, int LAT, int MODE>
-__device__ __forceinline__ PixFix strip_make(const TileArgs &A, const PixRaw &r, int gx, int par, int C, int g,
-                                             bool own, bool &over, bool &bad)
+__device__ __forceinline__ PixFix strip_make(const TileArgs &A, const PixRaw &r, int gx, int C, int g, bool own,
+                                             double rate_x, bool &over, bool &bad)
 {
     PixFix p{0, 0, 0u};
     if (!r.ph) return p;
     double px = r.x, py = r.y;
     const bool grip = gx == 0 || gx == C - 1;
     if (MODE == T_STEP) {
-        if (RATE && grip) {  // constant strain rate: grip x at the strain of this step
-            const long long s = *A.d_step + A.t_off + 1 - A.rate_step0;
-            const double eps = ad(A.rate_eps0, ml((double)s, A.rate_dt));
-            const double X = site_X<LAT>(A, gx, par);
-            px = ad(X, ml(eps, sb(X, A.xc)));
-        }
+        if (RATE && grip) px = rate_x;
         if (!grip) px = fma(A.dt, r.vx, px);
         if (!(grip && A.grip_mode == 1)) py = fma(A.dt, r.vy, py);
     }
@@ -140,6 +136,20 @@ __device__ __forceinline__ PixFix strip_make(const TileArgs &A, const PixRaw &r,
     p.yf = dbl_to_fix(py, A.S, over);
     p.pm = r.ph | (r.mk << 8);
     return p;
+}
+
+// Constant strain rate: the x of a grip in column gx at the strain of the
+// step being computed, eps = eps0 + (s - s0) rate dt, x = X + eps (X - xc),
+// for rows of parity par (the same correctly rounded operations as the tile
+// kernel). It depends on the step and the column only, so a strip computes
+// it once per row parity instead of once per row.
+template <int LAT>
+__device__ __forceinline__ double strip_rate_x(const TileArgs &A, int gx, int par)
+{
+    const long long s = *A.d_step + A.t_off + 1 - A.rate_step0;
+    const double eps = ad(A.rate_eps0, ml((double)s, A.rate_dt));
+    const double X = site_X<LAT>(A, gx, par);
+    return ad(X, ml(eps, sb(X, A.xc)));
 }
 
 // Force on the lower endpoint p of the spring p -> q in forward slot `slot`
@@ -277,9 +287,16 @@ __device__ __forceinline__ void strip_run(const TileArgs &A, int R, int sx, int 
     // row length (sites) of row y: nx, or nx - 1 on odd rows of the packing
     auto row_len = [&](int y) { return LAT == 0 ? A.nx : A.nx - (y & 1); };
 
+    // grip x under the constant strain rate, per row parity (used by grip lanes)
+    double rate_x0 = 0.0, rate_x1 = 0.0;
+    if constexpr (RATE && MODE == T_STEP) {
+        rate_x0 = strip_rate_x<LAT>(A, gx, 0);
+        rate_x1 = LAT == 0 ? rate_x0 : strip_rate_x<LAT>(A, gx, 1);
+    }
     // row y0 - 1: its springs into row y0 are evaluated, it is not owned
     PixRaw raw = strip_fetch<VOBS>(A, gx, y0 - 1);
-    PixFix P = strip_make<RATE, SAMPLE, LAT, MODE>(A, raw, gx, (y0 - 1) & 1, row_len(y0 - 1), 0, false, over, bad);
+    PixFix P = strip_make<RATE, SAMPLE, LAT, MODE>(A, raw, gx, row_len(y0 - 1), 0, false, ((y0 - 1) & 1) ? rate_x1 : rate_x0,
+                                                   over, bad);
     raw = strip_fetch<VOBS>(A, gx, y0);
     double vcx = 0.0, vcy = 0.0;
     FT p1x{}, p1y{}, p2x{}, p2y{}, p3x{}, p3y{};  // previous row's forces (slots 1..3)
@@ -298,9 +315,8 @@ __device__ __forceinline__ void strip_run(const TileArgs &A, int R, int sx, int 
         const int par = y & 1;     // row parity (triangular packing)
         // 1. row y + 1 (fetched last iteration), then fetch row y + 2
         const double vnx = raw.vx, vny = raw.vy;
-        const PixFix N = strip_make<RATE, SAMPLE, LAT, MODE>(A, raw, gx, par ^ 1, row_len(y + 1),
-                                                             (y + 1) * A.nx + gx, owner && y + 1 < y1,
-                                                             over, bad);
+        const PixFix N = strip_make<RATE, SAMPLE, LAT, MODE>(A, raw, gx, row_len(y + 1), (y + 1) * A.nx + gx,
+                                                             owner && y + 1 < y1, par ? rate_x0 : rate_x1, over, bad);
         raw = strip_fetch<VOBS>(A, gx, y + 2 <= y1 ? y + 2 : -1);
 
         // 2. the forward springs of row y; the shuffles that wrap around the

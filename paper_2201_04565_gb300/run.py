@@ -36,8 +36,12 @@ def _single(a):
     sp = lsm.Specimen.from_image(img, k, e, m, dt=0.01, damping=0.1, precision=a.precision, path=a.path,
                                  lattice=a.lattice)
     t0 = time.perf_counter()
+    if a.rate:  # one increment, then the grips at a constant strain rate (eps_inc per `steps` steps)
+        sp.apply_strain(a.eps_inc)
+        sp.set_strain_rate(a.eps_inc / (a.steps * 0.01))
     for i in range(1, a.increments + 1):
-        sp.apply_strain(i * a.eps_inc)
+        if not a.rate:
+            sp.apply_strain(i * a.eps_inc)
         sp.step(a.steps)
     sp.synchronize()
     dt = time.perf_counter() - t0
@@ -209,6 +213,8 @@ def main(argv=None):
     ap.add_argument("--increments", type=int, default=3)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--eps-inc", type=float, default=1e-3)
+    ap.add_argument("--rate", action="store_true",
+                    help="single: after the first increment, grips at a constant strain rate instead of increments")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--count", type=int, default=64, help="batch: number of specimens")
     ap.add_argument("--max-side", type=int, default=512, help="batch: largest specimen side")
