@@ -109,10 +109,10 @@ def algorithmic_bytes(n, m, dim):
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on three
     # time-step launches of each mode (the same 2048 x 2048 workload), mean
-    "df64": (238.6e6, "2e12a37fcbed"),
-    "f32": (240.1e6, "2e12a37fcbed"),
-    "fast64": (236.1e6, "2e12a37fcbed"),
-    "exact64": (236.8e6, "2e12a37fcbed"),
+    "df64": (238.3e6, "fb4674afee96"),
+    "f32": (240.2e6, "fb4674afee96"),
+    "fast64": (235.9e6, "fb4674afee96"),
+    "exact64": (236.6e6, "fb4674afee96"),
 }
 
 # Warp instructions executed by one time-step launch (ncu smsp__inst_executed.sum,
@@ -121,10 +121,10 @@ NCU_TRAFFIC = {
 # this gives the instruction-issue roofline, the one the fixed-point modes
 # are bound by.
 NCU_INSTRUCTIONS = {
-    "df64": (109831443, "2e12a37fcbed"),
-    "f32": (75982754, "2e12a37fcbed"),
-    "fast64": (94464248, "2e12a37fcbed"),
-    "exact64": (195572908, "2e12a37fcbed"),
+    "df64": (109831443, "fb4674afee96"),
+    "f32": (75982754, "fb4674afee96"),
+    "fast64": (94464248, "fb4674afee96"),
+    "exact64": (195572908, "fb4674afee96"),
 }
 
 # Binding unit of each mode's time-step kernel, from ncu on the same workload

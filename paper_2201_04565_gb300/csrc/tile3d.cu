@@ -77,7 +77,8 @@ struct Tile3Args {
     float fa;       // lattice spacing as a float (F32 mode)
 };
 
-// x of a grip at the strain of the step being computed (constant strain rate)
+// x of a grip at the strain of the step being computed (constant strain
+// rate); the kernel evaluates it for the two grip columns once per thread
 __device__ __forceinline__ double rate_grip_x(const Tile3Args &A, int gx)
 {
     const long long s = *A.d_step + A.t_off + 1 - A.rate_step0;
@@ -86,9 +87,10 @@ __device__ __forceinline__ double rate_grip_x(const Tile3Args &A, int gx)
     return __dadd_rn(X, __dmul_rn(eps, __dsub_rn(X, A.xc)));
 }
 
+// rate_l, rate_r: the grips' x under the constant strain rate (RATE)
 template <int MODE, bool RATE>
 __device__ __forceinline__ void load_voxel(const Tile3Args &A, int x0, int y0, int z0, int rx, int ry, int rz,
-                                           Smem3 &S, bool &over)
+                                           Smem3 &S, bool &over, double rate_l, double rate_r)
 {
     const int gx = x0 - 1 + rx, gy = y0 - 1 + ry, gz = z0 - 1 + rz;
     const int e = rx + R3X * (ry + R3Y * rz);
@@ -107,7 +109,7 @@ __device__ __forceinline__ void load_voxel(const Tile3Args &A, int x0, int y0, i
                 const bool fixed = grip && (c == 0 || A.grip_mode == 1);
                 if (MODE == T_STEP && !fixed) px[c] = fma(A.dt, A.vh_in[c * A.nv + g], px[c]);
             }
-            if (RATE && MODE == T_STEP && grip) px[0] = rate_grip_x(A, gx);
+            if (RATE && MODE == T_STEP && grip) px[0] = gx == 0 ? rate_l : rate_r;
         }
     }
 #pragma unroll
@@ -193,9 +195,14 @@ k_tile3d(Tile3Args A)
 
     // 1. region (block + one-voxel halo) into shared memory
     bool over = false;
+    double rate_l = 0.0, rate_r = 0.0;  // grips' x under the constant strain rate
+    if constexpr (RATE && MODE == T_STEP) {
+        rate_l = rate_grip_x(A, 0);
+        rate_r = rate_grip_x(A, A.nx - 1);
+    }
     for (int e = tid; e < R3N; e += T3N) {
         const int rx = e % R3X, ry = (e / R3X) % R3Y, rz = e / (R3X * R3Y);
-        load_voxel<MODE, RATE>(A, x0, y0, z0, rx, ry, rz, S, over);
+        load_voxel<MODE, RATE>(A, x0, y0, z0, rx, ry, rz, S, over, rate_l, rate_r);
     }
     if (over) atomicOr(A.status, 2);
     __syncthreads();
@@ -301,7 +308,7 @@ k_tile3d(Tile3Args A)
             double xr = A.x_in[q];
             const double vh = MODE == T_INIT ? A.v_obs[q] : A.vh_in[q];
             if (MODE == T_STEP && !fixed) xr = fma(A.dt, vh, xr);
-            if (RATE && MODE == T_STEP && c == 0 && grip) xr = rate_grip_x(A, gx);
+            if (RATE && MODE == T_STEP && c == 0 && grip) xr = gx == 0 ? rate_l : rate_r;
             if (MODE == T_STEP) A.x_out[q] = xr;
             if (fixed) {
                 if (MODE == T_STEP) A.vh_out[q] = 0.0;

@@ -326,14 +326,28 @@ __device__ __forceinline__ void eval_spring(const TileArgs &A, int rp, int rq, i
     sf[(1 * 4 + slot) * NS + rp] = fy;
 }
 
+// Constant strain rate: x of a grip in column gx at the strain of the step
+// being computed, eps = eps0 + (s - s0) rate dt, x = X + eps (X - xc)
+// (correctly rounded operations); the kernels evaluate it for the two grip
+// columns once and pass the results to the region load.
+__device__ __forceinline__ double tile_rate_x(const TileArgs &A, int gx)
+{
+    const long long s = *A.d_step + A.t_off + 1 - A.rate_step0;
+    const double eps = ad(A.rate_eps0, ml((double)s, A.rate_dt));
+    const double X = ml((double)gx, A.a);
+    return ad(X, ml(eps, sb(X, A.xc)));
+}
+
 // Region pixel (rx, ry) -> shared memory: phase, broken mask, and the
 // positions drifted by dt vh (step mode): as doubles in the FP64 modes, as
 // fixed-point copies in the F32/DF modes. The drifted position is also
 // returned (the owning thread keeps it in registers for the integration).
+// rate_l, rate_r: the grips' x under the constant strain rate (RATE).
 template <int PREC, int MODE, int RX, bool RATE>
 __device__ __forceinline__ void load_pixel(const TileArgs &A, int x0, int y0, int rx, int ry, double *sx,
                                            double *sy, long long *sxf, long long *syf, uint8_t *sph,
-                                           uint8_t *smk, bool &over, double &opx, double &opy)
+                                           uint8_t *smk, bool &over, double &opx, double &opy, double rate_l,
+                                           double rate_r)
 {
     constexpr bool FIX = PREC == LSM_PREC_F32 || PREC == LSM_PREC_DF;
     const int gx = x0 - 1 + rx, gy = y0 - 1 + ry;
@@ -349,12 +363,7 @@ __device__ __forceinline__ void load_pixel(const TileArgs &A, int x0, int y0, in
             py = A.x_in[A.np + g];
             if (MODE == T_STEP) {
                 const bool grip = gx == 0 || gx == A.nx - 1;
-                if (RATE && grip) {  // constant strain rate: grip x at the strain of this step
-                    const long long s = *A.d_step + A.t_off + 1 - A.rate_step0;
-                    const double eps = ad(A.rate_eps0, ml((double)s, A.rate_dt));
-                    const double X = ml((double)gx, A.a);
-                    px = ad(X, ml(eps, sb(X, A.xc)));
-                }
+                if (RATE && grip) px = gx == 0 ? rate_l : rate_r;  // constant strain rate
                 if (!grip) {
                     if constexpr (PREC == LSM_PREC_EXACT64) px = ad(px, ml(A.dt, A.vh_in[g]));
                     else px = fma(A.dt, A.vh_in[g], px);
@@ -443,16 +452,22 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
     constexpr int KR = (RY + NW - 1) / NW;
     double opx[KR], opy[KR];
     bool over = false;
+    double rate_l = 0.0, rate_r = 0.0;  // grips' x under the constant strain rate
+    if constexpr (RATE && MODE == T_STEP) {
+        rate_l = tile_rate_x(A, 0);
+        rate_r = tile_rate_x(A, A.nx - 1);
+    }
 #pragma unroll
     for (int k = 0; k < KR; k++) {
         const int ry = warp + k * NW;
         if (ry < RY)
-            load_pixel<PREC, MODE, RX, RATE>(A, x0, y0, lane + 1, ry, sx, sy, sxf, syf, sph, smk, over, opx[k], opy[k]);
+            load_pixel<PREC, MODE, RX, RATE>(A, x0, y0, lane + 1, ry, sx, sy, sxf, syf, sph, smk, over, opx[k], opy[k],
+                                             rate_l, rate_r);
     }
     for (int q = tid; q < 2 * RY; q += NT) {
         double hx, hy;
         load_pixel<PREC, MODE, RX, RATE>(A, x0, y0, (q & 1) ? TX + 1 : 0, q >> 1, sx, sy, sxf, syf, sph, smk, over, hx,
-                                   hy);
+                                         hy, rate_l, rate_r);
     }
     if (FIX && over) atomicOr(A.status, 2);
     for (int e = tid; e < NS; e += NT) snew[e] = 0;
