@@ -229,9 +229,11 @@ __device__ __forceinline__ void patch_of(int mt, int ntx, int nty, int bx, int b
 
 constexpr int FW_THREADS = 192;  // warp 0 copies, warp 1 MMAs, warps 2-5 epilogue
 
-__host__ __device__ constexpr int fwd_stages(int BN, int KC)
+// stages of MT input boxes (128 pixels x KC channels each) and one weight
+// box (BN x KC) in a ring of at most 192 KB, at most 8
+__host__ __device__ constexpr int fwd_stages(int BN, int KC, int MT)
 {
-    return (196608 / ((128 + BN) * KC * 2)) < 8 ? (196608 / ((128 + BN) * KC * 2)) : 8;
+    return (196608 / ((128 * MT + BN) * KC * 2)) < 8 ? (196608 / ((128 * MT + BN) * KC * 2)) : 8;
 }
 
 // Output staging of the epilogue: blocks of SB = min(BN, 64) channels of the
@@ -240,11 +242,11 @@ __host__ __device__ constexpr int fwd_stages(int BN, int KC)
 __host__ __device__ constexpr int out_block(int BN) { return BN < 64 ? BN : 64; }
 __host__ __device__ constexpr unsigned out_staging(int BN) { return 2u * 128u * (unsigned)out_block(BN) * 2u; }
 
-template <int BN, int KC>
+template <int BN, int KC, int MT>
 struct FwdCfg {
-    static constexpr int S = fwd_stages(BN, KC);
+    static constexpr int S = fwd_stages(BN, KC, MT);
     static constexpr unsigned ROW = KC * 2;  // bytes per operand row: one swizzle width
-    static constexpr unsigned A_BYTES = 128 * ROW, B_BYTES = BN * ROW, STAGE = A_BYTES + B_BYTES;
+    static constexpr unsigned A_BYTES = 128 * ROW, B_BYTES = BN * ROW, STAGE = MT * A_BYTES + B_BYTES;
     // ring, output staging, + slack to align the ring to 1024 bytes
     static constexpr unsigned SMEM = S * STAGE + out_staging(BN) + 1024;
     static constexpr unsigned SW = KC == 64 ? 2u : 4u;  // 128- or 64-byte swizzle
@@ -313,14 +315,20 @@ __device__ __forceinline__ void fwd_epilogue(unsigned taddr, unsigned stage, con
 
 // out[b, y, x, out_c0 + co] = act(bias[co] + sum over taps, ci of
 // in[b, y + dy, x + dx, ci] W[co][tap][ci]), zero outside the image.
-template <int BN, int KC>
+// A work item is MT consecutive pixel patches (M tiles) of one output-channel
+// tile: each stage holds the MT input boxes and one weight box, which the MT
+// accumulators share, so MT = 2 reads the weights once per two patches. A
+// patch past the last one (odd count) is read as zeros (its boxes lie
+// outside the tensor) and not stored.
+template <int BN, int KC, int MT>
 __global__ void __launch_bounds__(FW_THREADS, 1)
 k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_w,
               const __grid_constant__ CUtensorMap tm_out, const float *__restrict__ bias, bf16 *__restrict__ out, int out_cs, int out_c0, int Cout, int Cin,
               int B, int H, int Wd, int taps, int relu, int bx, int by, int ntx, int nty)
 {
-    using C = FwdCfg<BN, KC>;
+    using C = FwdCfg<BN, KC, MT>;
     constexpr int S = C::S;
+    constexpr int ACC = MT * BN;  // TMEM columns of one work item's accumulators
     extern __shared__ unsigned char fw_smem[];
     __shared__ __align__(8) uint64_t full[S], empty[S], tfull[2], tempty[2], drain;
     __shared__ unsigned tbase;
@@ -329,7 +337,7 @@ k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) s_abort = 0;
     const unsigned ring = (cv_smem_u32(fw_smem) + 1023u) & ~1023u;
-    if (warp == 0) tmem_alloc(&tbase, 2 * BN);
+    if (warp == 0) tmem_alloc(&tbase, 2 * ACC);
     if (tid == 32) {
         for (int s = 0; s < S; s++) {
             mbar_init(cv_smem_u32(&full[s]), 1);
@@ -348,7 +356,8 @@ k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__
     const unsigned tmem = tbase;
     const unsigned ostage = ring + (unsigned)S * C::STAGE;  // output staging (1024-byte aligned)
     const int kch = Cin / KC, KT = taps * kch;
-    const int nnt = Cout / BN, ntiles = ntx * nty * B * nnt;
+    const int nmt = ntx * nty * B, nmi = (nmt + MT - 1) / MT;  // patches, work items per channel tile
+    const int nnt = Cout / BN, ntiles = nmi * nnt;
     const int limit = g_conv_wait_limit;
     int issued = 0;  // warp 0, lane 0: stage fills issued
 
@@ -358,9 +367,10 @@ k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__
             tma_prefetch(&tm_w);
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const int mt = t / nnt, n0 = (t - mt * nnt) * BN;
-                int b, y0, x0;
-                patch_of(mt, ntx, nty, bx, by, b, y0, x0);
+                const int mi = t / nnt, n0 = (t - mi * nnt) * BN;
+                int b[MT], y0[MT], x0[MT];
+#pragma unroll
+                for (int j = 0; j < MT; j++) patch_of(mi * MT + j, ntx, nty, bx, by, b[j], y0[j], x0[j]);
                 for (int tap = 0; tap < taps && ok; tap++) {
                     const int dy = taps == 9 ? tap / 3 - 1 : 0, dx = taps == 9 ? tap % 3 - 1 : 0;
                     for (int ci0 = 0; ci0 < Cin; ci0 += KC) {
@@ -371,8 +381,10 @@ k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__
                         }
                         const unsigned fb = cv_smem_u32(&full[s]), a = ring + (unsigned)s * C::STAGE;
                         mbar_expect_tx(fb, C::STAGE);
-                        tma_load_4d(a, &tm_in, fb, ci0, x0 + dx, y0 + dy, b);
-                        tma_load_2d(a + C::A_BYTES, &tm_w, fb, tap * Cin + ci0, n0);
+#pragma unroll
+                        for (int j = 0; j < MT; j++)
+                            tma_load_4d(a + (unsigned)j * C::A_BYTES, &tm_in, fb, ci0, x0[j] + dx, y0[j] + dy, b[j]);
+                        tma_load_2d(a + MT * C::A_BYTES, &tm_w, fb, tap * Cin + ci0, n0);
                         issued++;
                     }
                 }
@@ -392,7 +404,7 @@ k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__
                     break;
                 }
                 tc_fence_after();
-                const unsigned d = tmem + (unsigned)(acc * BN);
+                const unsigned d = tmem + (unsigned)(acc * ACC);
                 for (int kt = 0; kt < KT; kt++, it++) {
                     const int s = it % S, u = it / S;
                     if (!mbar_wait(cv_smem_u32(&full[s]), (unsigned)(u & 1), limit, abort)) {
@@ -400,10 +412,14 @@ k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t ad = desc0 + (uint64_t)(((unsigned)s * C::STAGE) >> 4), bd = ad + (C::A_BYTES >> 4);
+                    const uint64_t ad = desc0 + (uint64_t)(((unsigned)s * C::STAGE) >> 4);
+                    const uint64_t bd = ad + ((MT * C::A_BYTES) >> 4);
 #pragma unroll
                     for (int ks = 0; ks < KC / 16; ks++)
-                        mma_bf16(d, ad + 2 * ks, bd + 2 * ks, id, (kt > 0 || ks > 0) ? 1u : 0u);
+#pragma unroll
+                        for (int j = 0; j < MT; j++)
+                            mma_bf16(d + (unsigned)(j * BN), ad + ((j * C::A_BYTES) >> 4) + 2 * ks, bd + 2 * ks, id,
+                                     (kt > 0 || ks > 0) ? 1u : 0u);
                     mma_commit(cv_smem_u32(&empty[s]));  // the stage is free once these MMAs are done
                 }
                 if (!ok) break;
@@ -427,11 +443,14 @@ k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__
                 break;
             }
             tc_fence_after();
-            const int mt = t / nnt, n0 = (t - mt * nnt) * BN;
-            int b, y0, x0;
-            patch_of(mt, ntx, nty, bx, by, b, y0, x0);
-            fwd_epilogue<BN>(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(acc * BN), ostage, &tm_out, n0, bias,
-                             relu, b, x0, y0, m, leader, blk);
+            const int mi = t / nnt, n0 = (t - mi * nnt) * BN;
+#pragma unroll 1
+            for (int j = 0; j < MT && mi * MT + j < nmt; j++) {  // uniform over the 128 threads
+                int b, y0, x0;
+                patch_of(mi * MT + j, ntx, nty, bx, by, b, y0, x0);
+                fwd_epilogue<BN>(tmem + ((unsigned)(32 * q) << 16) + (unsigned)(acc * ACC + j * BN), ostage, &tm_out,
+                                 n0, bias, relu, b, x0, y0, m, leader, blk);
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(cv_smem_u32(&tempty[acc]));  // the accumulator may be overwritten
@@ -455,7 +474,7 @@ k_conv_fwd_tc(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__
     __syncthreads();
     if (warp == 0) {
         __syncwarp();
-        tmem_free(tmem, 2 * BN);
+        tmem_free(tmem, 2 * ACC);
     }
 }
 
@@ -933,23 +952,42 @@ static cudaError_t smem_attr(Kern k, unsigned bytes, bool &done)
     return e;
 }
 
+template <int BN, int KC, int MT>
+static cudaError_t launch_fwd_mt(const CUtensorMap &ti, const CUtensorMap &tw, const CUtensorMap &to,
+                                 const float *bias, bf16 *out, int out_cs, int out_c0, int Cout, int Cin, int B, int H,
+                                 int Wd, int taps, int relu, int bx, int by, int ntx, int nty, cudaStream_t st)
+{
+    using Cfg = FwdCfg<BN, KC, MT>;
+    static bool attr = false;
+    const cudaError_t e = smem_attr(k_conv_fwd_tc<BN, KC, MT>, Cfg::SMEM, attr);
+    if (e != cudaSuccess) return e;
+    const int64_t nmt = (int64_t)ntx * nty * B, items = (nmt + MT - 1) / MT * (Cout / BN);
+    const int grid = (int)std::min<int64_t>(items, sm_count());
+    k_conv_fwd_tc<BN, KC, MT><<<grid, FW_THREADS, Cfg::SMEM, st>>>(ti, tw, to, bias, out, out_cs, out_c0, Cout, Cin,
+                                                                    B, H, Wd, taps, relu, bx, by, ntx, nty);
+    return cudaGetLastError();
+}
+
+// Two patches per work item (the weight boxes shared) once there are more
+// patches than SMs (output tiles up to 128 channels: two double-buffered
+// accumulators fit in tensor memory); one below that, where halving the
+// work items would idle SMs.
 template <int BN, int KC>
 static cudaError_t launch_fwd(const CUtensorMap &ti, const CUtensorMap &tw, const float *bias, bf16 *out, int out_cs,
                               int out_c0, int Cout, int Cin, int B, int H, int Wd, int taps, int relu, int bx, int by,
                               int ntx, int nty, cudaStream_t st)
 {
-    static bool attr = false;
-    cudaError_t e = smem_attr(k_conv_fwd_tc<BN, KC>, FwdCfg<BN, KC>::SMEM, attr);
-    if (e != cudaSuccess) return e;
     CUtensorMap to;  // output: blocks of out_block(BN) channels x the tile's patch
-    e = act_map(&to, out + out_c0, Cout, out_cs, B, H, Wd, out_block(BN), bx, by);
+    const cudaError_t e = act_map(&to, out + out_c0, Cout, out_cs, B, H, Wd, out_block(BN), bx, by);
     if (e != cudaSuccess) return e;
-    const int64_t ntiles = (int64_t)ntx * nty * B * (Cout / BN);
-    const int grid = (int)std::min<int64_t>(ntiles, sm_count());
-    k_conv_fwd_tc<BN, KC><<<grid, FW_THREADS, FwdCfg<BN, KC>::SMEM, st>>>(ti, tw, to, bias, out, out_cs, out_c0,
-                                                                         Cout, Cin, B, H, Wd, taps, relu, bx, by, ntx,
-                                                                         nty);
-    return cudaGetLastError();
+    const int64_t nmt = (int64_t)ntx * nty * B;
+    if constexpr (BN <= 128) {
+        if (nmt * (Cout / BN) > sm_count())
+            return launch_fwd_mt<BN, KC, 2>(ti, tw, to, bias, out, out_cs, out_c0, Cout, Cin, B, H, Wd, taps, relu, bx,
+                                            by, ntx, nty, st);
+    }
+    return launch_fwd_mt<BN, KC, 1>(ti, tw, to, bias, out, out_cs, out_c0, Cout, Cin, B, H, Wd, taps, relu, bx, by,
+                                    ntx, nty, st);
 }
 
 // Shared memory of the halo variant: resident weights + stages (0: does not

@@ -30,14 +30,18 @@ def _bf(torch, a):
                                                        (32, 128, 1, 1, 2, 8, 12), (384, 128, 9, 1, 2, 8, 12),
                                                        (32, 256, 9, 1, 2, 16, 32), (192, 384, 9, 0, 1, 5, 70),
                                                        (64, 96, 9, 1, 3, 33, 130), (128, 64, 1, 0, 2, 4, 3),
-                                                       (32, 64, 9, 1, 2, 20, 8), (64, 32, 9, 0, 1, 17, 5)])
+                                                       (32, 64, 9, 1, 2, 20, 8), (64, 32, 9, 0, 1, 17, 5),
+                                                       (64, 128, 9, 1, 1, 153, 100), (32, 64, 1, 0, 2, 160, 64)])
 def test_conv_forward_matches_reference(env, cin, cout, taps, relu, B, H, W):
     """The tensor-core forward convolution against the reference, on channel
     slices of wider tensors: patches of 128 pixels (whole, ragged, narrower
     than the image), 32- and 64-channel K chunks, output tiles of 32 to 256
     channels, one or several; the variant with resident weights and halo
     copies (3x3, up to 64 output channels a tile, patches 16 or 8 pixels wide)
-    and the one streaming weights per tap (1x1, wider output tiles)."""
+    and the one streaming weights per tap (1x1, wider output tiles), with two
+    patches per work item once the patches outnumber the SMs (153 patches:
+    an odd count, the last item's second patch read as zeros and not
+    stored)."""
     torch, nn = env
     rng = np.random.default_rng(cin + cout + W)
     cs_in, c0_in, cs_out, c0_out = cin + 32, 32, cout + 64, 64  # channel slices of wider tensors
