@@ -3,7 +3,8 @@
 The paper's own specimen files are hosted elsewhere and are not used. These
 generators give images of the shapes the paper's workloads have (two-phase 2D
 composites with circular soft inclusions, Section 3.1 "Mode-I fracture of
-Poisson composites"), and the 3D foam and batch shapes the build targets.
+Poisson composites"), plus a 3D voxel foam and batches of uneven 2D
+specimens.
 
 Phase convention: 0 = void (no particle), 1 = stiff matrix, 2 = soft
 inclusion. Arrays are indexed [y, x] in 2D and [z, y, x] in 3D, so that a
@@ -130,8 +131,8 @@ def paper_table_materials():
     return k_tab, rc / 10.0 - 1.0, np.array([1.0, 1.0])
 
 
-# Named workloads (image recipe + loading schedule). Sizes follow the
-# benchmark configurations of the build.
+# Named workloads (image recipe + loading schedule): the 64^2 parity case,
+# the 2048^2 composite, the 256^3 foam and the 512-specimen batch.
 WORKLOADS = {
     "2d_64": dict(dim=2, nx=64, ny=64, r=(3.0, 8.0), frac=0.30, seed=0,
                   eps_max=0.10, increments=100, steps=20, dt=0.01, damping=0.1),
