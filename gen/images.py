@@ -132,7 +132,7 @@ def paper_table_materials():
 
 
 # Named workloads (image recipe + loading schedule): the 64^2 parity case,
-# the 2048^2 composite, the 256^3 foam and the 512-specimen batch.
+# the 2048^2 composite and the 256^3 foam (the batch: batch_specimens).
 WORKLOADS = {
     "2d_64": dict(dim=2, nx=64, ny=64, r=(3.0, 8.0), frac=0.30, seed=0,
                   eps_max=0.10, increments=100, steps=20, dt=0.01, damping=0.1),
