@@ -7,7 +7,10 @@ increment), element by element over every particle.
     within 1e-10 relative (normwise) and the stress sample within 1e-6; f32
     displacement error stated and bounded;
   - 3D 256^3 foam (5.9M particles, 47.5M springs) under compression: df64 and
-    f32 against the oracle, same bars.
+    f32 against the oracle, same bars;
+  - the paper's triangular packing of the 2048 x 2048 image (4,840,290
+    particles, 14,512,048 springs) on the strip kernel: df64 positions
+    within 1e-10 relative, identical broken set, stress within 1e-6.
 
 Two increments of 20 time steps each: the oracle (threaded, bit-identical to
 its sequential form) finishes them in seconds at these sizes.
@@ -43,9 +46,9 @@ def img3d():
     return foam_volume(256, 4.0, 0.35, seed=2)
 
 
-def _oracle_run(oracle_mod, img, mats, eps_inc, incs=2, steps=20):
+def _oracle_run(oracle_mod, img, mats, eps_inc, incs=2, steps=20, lattice=0):
     k, e, m = mats
-    o = oracle_mod.Oracle.from_image(img, k, e, m)
+    o = oracle_mod.Oracle.from_image(img, k, e, m, lattice=lattice)
     o.set_threads(os.cpu_count() or 1)
     samples = []
     for i in range(1, incs + 1):
@@ -57,9 +60,9 @@ def _oracle_run(oracle_mod, img, mats, eps_inc, incs=2, steps=20):
     return o, x, v, X, samples
 
 
-def _gpu_run(L, img, mats, precision, eps_inc, incs=2, steps=20):
+def _gpu_run(L, img, mats, precision, eps_inc, incs=2, steps=20, lattice=0):
     k, e, m = mats
-    g = L.Specimen.from_image(img, k, e, m, precision=precision, path=0)
+    g = L.Specimen.from_image(img, k, e, m, precision=precision, path=0, lattice=lattice)
     for i in range(1, incs + 1):
         g.apply_strain(i * eps_inc)
         g.step(steps)
@@ -127,3 +130,22 @@ def test_3d_foam256_full_size(L, img3d, ref3d, precision):
         assert rel_u < 1e-4
         for a, b in zip(s, r["s"]):
             assert a["sigma_vir"] == pytest.approx(b["sigma_vir"], rel=1e-3)
+
+
+def test_2d_2048_triangular_full_size(oracle_mod, L, img2d):
+    """The triangular packing at full size, in the strip kernel's launch
+    configuration for it (one wave of strips over the site grid)."""
+    mats = two_phase_materials()
+    o, xo, vo, X, so = _oracle_run(oracle_mod, img2d, mats, 1e-3, lattice=1)
+    mo, _, fo = o.broken()
+    n = o.n
+    x, v, s, mask, first = _gpu_run(L, img2d, mats, "df64", 1e-3, lattice=1)
+    assert x.shape == xo.shape == (2, n) and n == 4840290
+    assert np.array_equal(mask, mo) and first == fo
+    dx = np.abs(x - xo).max()
+    rel_x = dx / np.abs(xo).max()
+    print("2048^2 triangular df64: position error %.3e relative, displacement error %.3e relative"
+          % (rel_x, dx / np.abs(xo - X).max()))
+    assert rel_x <= 1e-10
+    for a, b in zip(s, so):
+        assert a["sigma_vir"] == pytest.approx(b["sigma_vir"], rel=1e-6)
