@@ -529,6 +529,35 @@ def test_triangular_strip_kernel_geometry(oracle_mod, L, a, grip_mode, precision
     assert ob["sigma_vir"] == pytest.approx(sg[-1]["sigma_vir"], rel=1e-9)
 
 
+@pytest.mark.parametrize("grip_mode", [0, 1])
+def test_triangular_strain_rate_matches_oracle(oracle_mod, L, grip_mode):
+    """The packing on the strip kernel under constant strain-rate loading
+    (the grips' x per row parity: odd rows start half a spacing in) through
+    fracture, with a load increment in between: df64 at the 1e-10 bar with
+    the same broken set, the applied strain the oracle's."""
+    img = inclusion_image(75, 41, 2.0, 5.0, 0.3, 29)
+    k, e, m = two_phase_materials()
+    o = oracle_mod.Oracle.from_image(img, k, e, m, lattice=1, load_mode=1, grip_mode=grip_mode)
+    g = L.Specimen.from_image(img, k, e, m, precision="df64", lattice=1, load_mode=1, grip_mode=grip_mode)
+    for s_ in (o, g):
+        s_.set_strain_rate(0.05)
+    for _ in range(6):
+        o.step(20)
+        g.step(20)
+    o.apply_strain(0.08)
+    g.apply_strain(0.08)
+    for _ in range(6):
+        o.step(20)
+        g.step(20)
+    assert g.samples()[-1]["eps"] == o.observe()["eps"]
+    xg, _ = g.state()
+    xo, _, _ = o.state()
+    mo = o.broken()[0]
+    assert mo.sum() > 0
+    assert _rel(xg, xo) <= 1e-10
+    assert np.array_equal(g.broken()[0], mo)
+
+
 def test_triangular_fields_match_oracle(oracle_mod, L):
     img = inclusion_image(30, 26, 2.0, 4.0, 0.3, 22)
     k, e, m = two_phase_materials()
@@ -596,11 +625,12 @@ def test_3d_tile_kernel_spacing_and_grips(oracle_mod, L, a, grip_mode, precision
 
 
 @pytest.mark.parametrize("path,precision,dim", [(0, "exact64", 2), (1, "exact64", 2), (1, "exact64", 3),
-                                                (0, "df64", 3), (1, "df64", 2)])
+                                                (0, "df64", 3), (1, "df64", 2), (2, "df64", 2), (3, "df64", 2)])
 def test_strain_rate_loading_matches_oracle(oracle_mod, L, path, precision, dim):
     """Constant strain-rate loading (grips moved every step) through
     fracture, with a load increment in between that restarts the ramp:
-    exact64 bit-identical, df64 at the 1e-10 bar with the same broken set;
+    exact64 bit-identical, df64 at the 1e-10 bar with the same broken set
+    (2D: tile kernel, strip kernel, spring lists; 3D: voxel tile kernel);
     the samples' applied strain equals the oracle's."""
     if dim == 2:
         img = inclusion_image(36, 28, 2.0, 4.0, 0.3, 31)
