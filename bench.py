@@ -109,7 +109,7 @@ def algorithmic_bytes(n, m, dim):
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on three
     # time-step launches of each mode (the same 2048 x 2048 workload), mean
-    "df64": (238.3e6, "fb4674afee96"),
+    "df64": (238.4e6, "5ebefc3dec19"),
     "f32": (240.2e6, "fb4674afee96"),
     "fast64": (235.9e6, "fb4674afee96"),
     "exact64": (236.6e6, "fb4674afee96"),
@@ -121,7 +121,7 @@ NCU_TRAFFIC = {
 # this gives the instruction-issue roofline, the one the fixed-point modes
 # are bound by.
 NCU_INSTRUCTIONS = {
-    "df64": (109831443, "fb4674afee96"),
+    "df64": (108821973, "5ebefc3dec19"),
     "f32": (75982754, "fb4674afee96"),
     "fast64": (94464248, "fb4674afee96"),
     "exact64": (195572908, "fb4674afee96"),

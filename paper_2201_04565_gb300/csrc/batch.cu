@@ -463,6 +463,7 @@ static TileArgs batch_base_args(BatchCtx &b)
     A.a_fix = b.a_fix;
     A.p24 = ldexpf(1.0f, 24 - b.fix_S);
     A.p0 = ldexpf(1.0f, -b.fix_S);
+    A.df_bias = (unsigned)(896 + 24 - b.fix_S) << 20;
     A.status = b.status;
     A.part_s = b.part_s;
     A.part_p = b.part_p;
@@ -688,9 +689,11 @@ static cudaError_t batch_upload(BatchCtx &b, const std::vector<HostNet> &nets, c
         const double aa = std::ldexp((double)b.a_fix, -b.fix_S);
         const double p = t.r0 * t.r0, pe = std::fma(t.r0, t.r0, -p);
         const double o2 = shell * aa * aa, o2e = shell * std::fma(aa, aa, -(aa * aa));
+        // DF kernels hold lengths in units of 2^(24-S) (exact power-of-two scaling)
+        const double ul = b.prec == LSM_PREC_DF ? std::ldexp(1.0, b.fix_S - 24) : 1.0;
         tdf[q].k = split_ff_b(t.k);
-        tdf[q].r0 = split_ff_b(t.r0);
-        tdf[q].rc2 = split_ff_b(t.rc2);
+        tdf[q].r0 = split_ff_b(t.r0 * ul);
+        tdf[q].rc2 = split_ff_b(t.rc2 * ul * ul);
         tdf[q].cor = split_ff_b((o2 - p) + (o2e - pe));
     }
     for (int q = 0; q < 2; q++) {

@@ -119,6 +119,21 @@ __device__ __forceinline__ double f2d_force(float f)
     return __hiloint2double((int)hi, (int)lo);
 }
 
+// f2d_force for a force held in units of 2^k: the float's value times 2^k
+// as a double, the power of two folded into the exponent rebias
+// (bias = (896 + k) << 20; 896 << 20 is f2d_force), so the unit costs
+// nothing; zero and subnormals give a signed zero, non-finite values a
+// finite value of at least 2^(128 + k), as in f2d_force.
+__device__ __forceinline__ double f2d_force_scaled(float f, unsigned bias)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned ax = u & 0x7FFFFFFFu, sign = u & 0x80000000u;
+    const bool tiny = ax < 0x00800000u;
+    const unsigned hi = tiny ? sign : (((ax >> 3) + bias) | sign);
+    const unsigned lo = tiny ? 0u : (u << 29);
+    return __hiloint2double((int)hi, (int)lo);
+}
+
 // Double -> float with integer operations, truncating the significand
 // (|x| below the float range gives a signed zero, above it infinity).
 __device__ __forceinline__ float d2f_bits(double d)
@@ -250,6 +265,20 @@ __device__ __forceinline__ ff fix_to_ff_i2f2(long long v, float p24, float p0)
     const int h = (int)__funnelshift_r((unsigned)v, (unsigned)(v >> 32), 24);  // v >> 24
     const float a = __fmul_rn(__int2float_rn(h), p24);
     const float b = __fmul_rn(__int2float_rn((int)((unsigned)v & 0xFFFFFFu)), p0);
+    return fast_two_sum(a, b);
+}
+
+// The same value in units of 2^(24-S): v / 2^24 = h + l 2^-24, the high
+// chunk converted without a scale factor and the low one scaled by the exact
+// power 2^-24, joined by Fast2Sum. Every result equals fix_to_ff_i2f2's times
+// 2^(S-24) exactly (scaling by a power of two commutes with the rounding),
+// one multiplication fewer; the DF kernels keep their spring tables, forces
+// and sample sums in this unit (see f2d_force_scaled).
+__device__ __forceinline__ ff fix_to_ff_u24(long long v)
+{
+    const int h = (int)__funnelshift_r((unsigned)v, (unsigned)(v >> 32), 24);  // v >> 24
+    const float a = __int2float_rn(h);
+    const float b = __fmul_rn(__int2float_rn((int)((unsigned)v & 0xFFFFFFu)), 0x1p-24f);
     return fast_two_sum(a, b);
 }
 

@@ -562,9 +562,12 @@ static cudaError_t upload_tile(Ctx &c)
         // |o|^2 - r0^2 with the products' rounding errors kept (fma)
         const double p = t.r0 * t.r0, pe = std::fma(t.r0, t.r0, -p);
         const double o2 = ox * ox + oy * oy, o2e = std::fma(ox, ox, -(ox * ox)) + std::fma(oy, oy, -(oy * oy));
+        // DF kernels hold lengths in units of 2^(24-S): r0 and rc^2 scaled
+        // exactly by powers of two (F32 keeps the plain values)
+        const double ul = h.precision == LSM_PREC_DF ? std::ldexp(1.0, c.fix_S - 24) : 1.0;
         tdf[q].k = split_ff(t.k);
-        tdf[q].r0 = split_ff(t.r0);
-        tdf[q].rc2 = split_ff(t.rc2);
+        tdf[q].r0 = split_ff(t.r0 * ul);
+        tdf[q].rc2 = split_ff(t.rc2 * ul * ul);
         tdf[q].cor = split_ff((o2 - p) + (o2e - pe));
     }
     for (int b = 0; b < 2; b++) {

@@ -420,11 +420,11 @@ __device__ __forceinline__ void strip_run(const TileArgs &A, int R, int sx, int 
                     ax.add(f3x);
                     ay.add(f3y);
                 }
-                F[0] = ax.value();
-                F[1] = ay.value();
-                Ff[0] = __fadd_rn(ax.hs, ax.el);
-                Ff[1] = __fadd_rn(ay.hs, ay.el);
-                Fx = ff{ax.hs, ax.el};
+                F[0] = ax.value(A.df_bias);
+                F[1] = ay.value(A.df_bias);
+                Ff[0] = __fmul_rn(__fadd_rn(ax.hs, ax.el), A.p24);  // back from units of 2^(24-S)
+                Ff[1] = __fmul_rn(__fadd_rn(ay.hs, ay.el), A.p24);
+                Fx = ff{ax.hs, ax.el};  // (in those units)
             } else {
                 if constexpr (LAT == 0) {
                     sx_ += f1x - i2x;
@@ -519,11 +519,13 @@ __device__ __forceinline__ void strip_run(const TileArgs &A, int R, int sx, int 
         const ff tm = warp_sum_ff(mvx2), tk = warp_sum_ff(ke);
         const float tres = warp_max_f(resf);
         if (lane == 0) {
-            A.part_s[part] = ff_to_double(tw);
-            A.part_s[A.ntiles + part] = 0.5 * ff_to_double(tu);  // the 1/2 of 1/2 k (r - r0)^2, exact
+            // DF: virial, energy and reaction from units of 2^(24-S) (exact)
+            const double u = PREC == LSM_PREC_DF ? (double)A.p24 : 1.0;
+            A.part_s[part] = ff_to_double(tw) * (u * u);
+            A.part_s[A.ntiles + part] = 0.5 * ff_to_double(tu) * (u * u);  // the 1/2 of 1/2 k (r - r0)^2, exact
             A.part_p[part] = ff_to_double(tm);
             A.part_p[A.ntiles + part] = ff_to_double(tk);
-            A.part_p[2 * A.ntiles + part] = ff_to_double(tr);
+            A.part_p[2 * A.ntiles + part] = ff_to_double(tr) * u;
             A.part_p[3 * A.ntiles + part] = f2d_bits(tres);
         }
     }

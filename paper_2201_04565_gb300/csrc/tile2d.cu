@@ -151,6 +151,7 @@ static TileArgs tile_args(Ctx &c)
     A.hrow = c.h.a * std::sqrt(3.0) * 0.5;
     A.p24 = ldexpf(1.0f, 24 - c.fix_S);
     A.p0 = ldexpf(1.0f, -c.fix_S);
+    A.df_bias = (unsigned)(896 + 24 - c.fix_S) << 20;
     A.dt = c.h.dt;
     A.hdt = 0.5 * c.h.dt;
     A.gamma = c.h.damping;

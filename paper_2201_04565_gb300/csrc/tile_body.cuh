@@ -115,6 +115,7 @@ struct TileArgs {
     long long h_fix;           // triangular packing: row height a sqrt(3)/2 in fixed point
     double hrow;               // triangular packing: row height
     float p24, p0;             // 2^(24-S), 2^-S
+    unsigned df_bias;          // DF: f2d_force_scaled bias for forces held in units of p24
     double dt, hdt, gamma, a;
     int grip_mode;
     int rate_on;               // constant strain rate: grips at rate_eps0 + (s - rate_step0) rate_dt
@@ -167,7 +168,11 @@ struct DfSum {
         hs = t.hi;
         el = __fadd_rn(el, __fadd_rn(t.lo, o.lo));
     }
-    __device__ __forceinline__ double value() const { return f2d_force(hs) + f2d_force(el); }
+    // the sum as a double; bias: the unit the terms are held in (f2d_force_scaled)
+    __device__ __forceinline__ double value(unsigned bias) const
+    {
+        return f2d_force_scaled(hs, bias) + f2d_force_scaled(el, bias);
+    }
 };
 
 // The fixed-point modes' spring arithmetic, shared by every 2D kernel that
@@ -180,13 +185,16 @@ struct DfSum {
 // component d_x and its stretch r - r0.
 
 // Double-float force: d as a double-float (two exact 24-bit chunks), 1/r by
-// one double-float Newton step, k (r - r0) / r = k (1 - r0 / r).
+// one double-float Newton step, k (r - r0) / r = k (1 - r0 / r). Lengths are
+// held in units of 2^(24-S) (fix_to_ff_u24; the type table's r0 and rc^2 are
+// scaled to match on the host), so the force, d_x and r - r0 come out in that
+// unit too: exactly the unscaled values times 2^(S-24).
 template <bool TEST, bool SAMPLE>
 __device__ __forceinline__ bool spring_df(long long dxq, long long dyq, const TypeDF &t, const TileArgs &A,
                                           ff &fx, ff &fy, ff &dx, ff &st)
 {
-    const ff dxf = fix_to_ff_i2f2(dxq, A.p24, A.p0);
-    const ff dyf = fix_to_ff_i2f2(dyq, A.p24, A.p0);
+    const ff dxf = fix_to_ff_u24(dxq);
+    const ff dyf = fix_to_ff_u24(dyq);
     const ff r2 = ff_norm2_un(dxf, dyf);
     if (TEST && ff_gt_un(r2, t.rc2)) return true;
     ff y;
@@ -553,9 +561,9 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
                 acc.sub(sf[(c * 4 + 0) * NS + s0]);
 #pragma unroll
                 for (int sl = 0; sl < 4; sl++) acc.add(sf[(c * 4 + sl) * NS + rp]);
-                F[c] = acc.value();
-                Ff[c] = __fadd_rn(acc.hs, acc.el);
-                Fd[c] = ff{acc.hs, acc.el};
+                F[c] = acc.value(A.df_bias);
+                Ff[c] = __fmul_rn(__fadd_rn(acc.hs, acc.el), A.p24);  // back from units of 2^(24-S)
+                Fd[c] = ff{acc.hs, acc.el};                            // (in those units)
             }
         } else {
 #pragma unroll
@@ -662,6 +670,12 @@ __device__ __forceinline__ void tile_body(const TileArgs &A, int bx, int by, int
             t3 = bsum_ff<NW>(ff{kef, 0.0f}, sred);
             t4 = bsum_ff<NW>(reactf, sred);
             t5 = bmax_f<NW>(resf, sred);
+            if constexpr (PREC == LSM_PREC_DF) {  // from units of 2^(24-S) (exact)
+                const double u = (double)A.p24;
+                t0 *= u * u;
+                t1 *= u * u;
+                t4 *= u;
+            }
         } else {
             t0 = bsum<NW>(w_acc, sred);
             t1 = bsum<NW>(u_acc, sred);
