@@ -109,10 +109,10 @@ def algorithmic_bytes(n, m, dim):
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on three
     # time-step launches of each mode (the same 2048 x 2048 workload), mean
-    "df64": (238.4e6, "5ebefc3dec19"),
-    "f32": (240.2e6, "fb4674afee96"),
-    "fast64": (235.9e6, "fb4674afee96"),
-    "exact64": (236.6e6, "fb4674afee96"),
+    "df64": (238.3e6, "5ebefc3dec19"),
+    "f32": (240.1e6, "5ebefc3dec19"),
+    "fast64": (236.2e6, "5ebefc3dec19"),
+    "exact64": (236.9e6, "5ebefc3dec19"),
 }
 
 # Warp instructions executed by one time-step launch (ncu smsp__inst_executed.sum,
@@ -122,9 +122,9 @@ NCU_TRAFFIC = {
 # are bound by.
 NCU_INSTRUCTIONS = {
     "df64": (108821973, "5ebefc3dec19"),
-    "f32": (75982754, "fb4674afee96"),
-    "fast64": (94464248, "fb4674afee96"),
-    "exact64": (195572908, "fb4674afee96"),
+    "f32": (75982754, "5ebefc3dec19"),
+    "fast64": (94464248, "5ebefc3dec19"),
+    "exact64": (195572908, "5ebefc3dec19"),
 }
 
 # Binding unit of each mode's time-step kernel, from ncu on the same workload
