@@ -251,6 +251,18 @@ k_tile3d(Tile3Args A)
         const uint16_t mk = S.mk[ep];
         const long long xp[3] = {S.xf[0][ep], S.xf[1][ep], S.xf[2][ep]};
         float hs[3] = {0.0f, 0.0f, 0.0f}, el[3] = {0.0f, 0.0f, 0.0f};
+        // time steps without a sample issue the integration's global loads
+        // here, so their latency hides behind the springs (the sample
+        // instance keeps them late: it has no registers to spare)
+        constexpr bool PRE = MODE == T_STEP && !SAMPLE;
+        double xpre[3], vpre[3];
+        if constexpr (PRE) {
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                xpre[c] = A.x_in[c * A.nv + g];
+                vpre[c] = A.vh_in[c * A.nv + g];
+            }
+        }
         // incoming: source p - o_s, ascending source = descending slot
 #pragma unroll 1
         for (int s = 8; s >= 0; s--) {
@@ -305,8 +317,15 @@ k_tile3d(Tile3Args A)
             const int64_t q = c * A.nv + g;
             const double F = f2d_force(hs[c]) + f2d_force(el[c]);
             const float Ff = __fadd_rn(hs[c], el[c]);
-            double xr = A.x_in[q];
-            const double vh = MODE == T_INIT ? A.v_obs[q] : A.vh_in[q];
+            double xr;
+            double vh;
+            if constexpr (PRE) {
+                xr = xpre[c];
+                vh = vpre[c];
+            } else {
+                xr = A.x_in[q];
+                vh = MODE == T_INIT ? A.v_obs[q] : A.vh_in[q];
+            }
             if (MODE == T_STEP && !fixed) xr = fma(A.dt, vh, xr);
             if (RATE && MODE == T_STEP && c == 0 && grip) xr = gx == 0 ? rate_l : rate_r;
             if (MODE == T_STEP) A.x_out[q] = xr;
